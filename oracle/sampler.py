@@ -1,0 +1,177 @@
+"""Exact i.i.d. draws of Fourier modes from the adaptive importance measure, FP64.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Target (Eq. 59): P(k) = calF(k) Fhat(k) / S over k = 2 pi (m_x/L_x, m_y/L_y, m_z/L_z),
+m in Z^3 \\ {0}, with Fhat of Eq. (54), calF the Debye-Hueckel correction of Eq. (62)
+and S = sum_{k != 0} calF Fhat.
+
+Procedure (the reading of the sampling step of Algorithm 2 used throughout; the
+paper's own sampler is Metropolis-Hastings, Sec. 4.3, while the variance lemma
+(Lemma 4.1) assumes i.i.d. draws, which this gives exactly):
+  Fhat(k) = sum_m A_m prod_a g_{m,a}(n_a),  A_m = pi^{3/2} h w_m f(t_m,0) e^{-3 t_m/2},
+  g_{m,a}(n) = exp(-(2 pi n / L_a)^2 / (4 b_m)),  b_m = e^{t_m}.
+  1. pick the Gaussian m with probability proportional to A_m prod_a theta_{m,a},
+     theta_{m,a} = sum_n g_{m,a}(n)          (alias table over m);
+  2. per axis draw n_a with probability g_{m,a}(n_a) / theta_{m,a}
+     (alias table over |n_a| <= nmax_{m,a}, where g < 1e-18 beyond);
+  3. if n = 0, start the attempt over;
+  4. accept with probability calF(k) / sum_j q_j^2 (calF increases with |k| towards
+     sum q^2), else start over.
+Accepted modes are distributed as P(k).
+
+Random numbers: Philox4x32-10, key = (seed lo, seed hi), counter = (slot l, 8*attempt + j,
+draw lo, draw hi) with j = 0 for the Gaussian index, j = 1, 2, 3 for the axes, j = 4 for
+the acceptance test.  An alias draw from words (x0, x1, x2, x3) takes the index
+floor((x0 2^32 + x1) n / 2^64) and keeps it when u53(x2, x3) < prob[index], else takes
+alias[index].  Alias tables follow Vose (1991) with both work lists used as stacks,
+filled in ascending index order.  The same layout lets a replay reproduce another
+implementation's draws from the same seed.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import philox
+from .sog import SOG, f_tr
+
+LN_1E18 = 41.44653167389282      # ln(1e18): 1-D tables stop where g < 1e-18
+TWO_PI = 6.283185307179586
+MAX_ATTEMPTS = 1 << 20
+
+
+def vose_alias(weights):
+    """Alias table (prob, alias) for the discrete distribution proportional to weights."""
+    w = [float(x) for x in weights]
+    n = len(w)
+    total = 0.0
+    for x in w:
+        total += x
+    scaled = [(x * n) / total for x in w]
+    prob = [0.0] * n
+    alias = list(range(n))
+    small = [i for i in range(n) if scaled[i] < 1.0]
+    large = [i for i in range(n) if scaled[i] >= 1.0]
+    while small and large:
+        lo = small.pop()
+        g = large.pop()
+        prob[lo] = scaled[lo]
+        alias[lo] = g
+        scaled[g] = (scaled[g] + scaled[lo]) - 1.0
+        if scaled[g] < 1.0:
+            small.append(g)
+        else:
+            large.append(g)
+    while large:
+        prob[large.pop()] = 1.0
+    while small:
+        prob[small.pop()] = 1.0
+    return np.asarray(prob, dtype=np.float64), np.asarray(alias, dtype=np.int64)
+
+
+class ModeSampler:
+    """Tables for drawing k from P(k) for one (SOG, box, k_B T, charges) state."""
+
+    def __init__(self, sog: SOG, L, kT: float, Q2: float):
+        self.sog = sog
+        self.L = [float(x) for x in L]
+        self.kT = float(kT)
+        self.Q2 = float(Q2)
+        self.V = (self.L[0] * self.L[1]) * self.L[2]
+        self.tpl = [TWO_PI / x for x in self.L]
+        self.inv_lam2 = 1.0 / (sog.lam * sog.lam)
+        t = sog.t
+        wt = sog.weights
+        self.b = [math.exp(float(x)) for x in t]
+        self.A = [sog.h * float(wt[i]) * math.pi ** 1.5 * float(f_tr(float(t[i]), 0.0, sog.lam))
+                  * math.exp(-1.5 * float(t[i])) for i in range(len(t))]
+        self.axis = []       # per m: list of 3 (nmax, prob, alias)
+        mix = []
+        for i, b in enumerate(self.b):
+            tabs = []
+            prod = 1.0
+            for a in range(3):
+                nmax = int(math.ceil(math.sqrt(4.0 * b * LN_1E18) / self.tpl[a]))
+                g = []
+                for n in range(-nmax, nmax + 1):
+                    kk = self.tpl[a] * n
+                    g.append(math.exp(-(kk * kk) / (4.0 * b)))
+                theta = 0.0
+                for x in g:
+                    theta += x
+                prob, alias = vose_alias(g)
+                tabs.append((nmax, prob, alias))
+                prod = prod * theta
+            self.axis.append(tabs)
+            mix.append(self.A[i] * prod)
+        self.mix_prob, self.mix_alias = vose_alias(mix)
+
+    def accept_ratio(self, k2):
+        """calF(k)/sum q^2 = kT V / (kT V + Q2/(k^2 + lambda^-2))."""
+        A = self.kT * self.V
+        return A / (A + self.Q2 * (1.0 / (k2 + self.inv_lam2)))
+
+    def k2_of(self, m):
+        m = np.asarray(m, dtype=np.float64)
+        kx = self.tpl[0] * m[..., 0]
+        ky = self.tpl[1] * m[..., 1]
+        kz = self.tpl[2] * m[..., 2]
+        return (kx * kx + ky * ky) + kz * kz
+
+    def _alias_pick(self, words, prob, alias, n):
+        i = philox.index_below(words[0], words[1], n)
+        u = philox.u53(words[2], words[3])
+        return np.where(u < prob[i], i, alias[i])
+
+    def draw(self, seed: int, draw_index: int, P: int):
+        """P i.i.d. modes (int32 [P,3]) and the attempt count each slot used."""
+        k0 = np.uint64(seed & 0xFFFFFFFF)
+        k1 = np.uint64((seed >> 32) & 0xFFFFFFFF)
+        c2 = np.uint64(draw_index & 0xFFFFFFFF)
+        c3 = np.uint64((draw_index >> 32) & 0xFFFFFFFF)
+        out = np.zeros((P, 3), dtype=np.int64)
+        attempts = np.zeros(P, dtype=np.int64)
+        todo = np.arange(P, dtype=np.int64)
+        att = 0
+        while todo.size:
+            if att >= MAX_ATTEMPTS:
+                raise RuntimeError("sampler exceeded the attempt limit")
+            slot = todo.astype(np.uint64)
+            words = [philox.philox4x32_10(slot, np.uint64(8 * att + j), c2, c3, k0, k1) for j in range(5)]
+            mi = self._alias_pick(words[0], self.mix_prob, self.mix_alias, len(self.mix_prob))
+            n = np.zeros((todo.size, 3), dtype=np.int64)
+            for a in range(3):
+                for g in np.unique(mi):
+                    sel = mi == g
+                    nmax, prob, alias = self.axis[g][a]
+                    wsel = [x[sel] for x in words[1 + a]]
+                    n[sel, a] = self._alias_pick(wsel, prob, alias, 2 * nmax + 1) - nmax
+            nonzero = np.any(n != 0, axis=1)
+            u = philox.u53(words[4][0], words[4][1])
+            ok = nonzero & (u < self.accept_ratio(self.k2_of(n)))
+            out[todo[ok]] = n[ok]
+            attempts[todo[ok]] = att + 1
+            todo = todo[~ok]
+            att += 1
+        return out.astype(np.int32), attempts
+
+    # --- exact measure (for pins) ---
+    def calF(self, k2):
+        return self.kT * self.V / (self.kT * self.V / self.Q2 + 1.0 / (k2 + self.inv_lam2))
+
+    def fhat(self, k2):
+        k2 = np.asarray(k2, dtype=np.float64)
+        return sum(self.A[i] * np.exp(-k2 / (4.0 * self.b[i])) for i in range(len(self.b)))
+
+    def all_modes(self, tail=1e-17):
+        """Every m != 0 with Fhat(k) above tail * Fhat(0)-scale cutoff: k^2 <= 4 b_max ln(1/tail)."""
+        kmax2 = 4.0 * max(self.b) * math.log(1.0 / tail)
+        nm = [int(math.floor(math.sqrt(kmax2) / self.tpl[a])) + 1 for a in range(3)]
+        g = [np.arange(-nm[a], nm[a] + 1) for a in range(3)]
+        mx, my, mz = np.meshgrid(*g, indexing="ij")
+        m = np.stack([mx.ravel(), my.ravel(), mz.ravel()], axis=1)
+        m = m[np.any(m != 0, axis=1)]
+        m = m[self.k2_of(m) <= kmax2]
+        return m.astype(np.int64)
