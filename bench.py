@@ -1,0 +1,309 @@
+"""Benchmark of the RBSOG force step on GB300: particle-steps/s at N = 1e6.
+
+Workload: Yukawa one-component plasma, N = 1e6 uniform (seeded), Gamma = 0.1, kappa = 2,
+r_c = 3a, P = 500, dt = 0.01, BAOAB Langevin, FP32 forces with FP64 integration (the
+FP64 form is timed beside it).  One step = sample, cell list, near field, structure
+factor, far gather and integration (Algorithm 2), replayed from a CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun each rank advances its own independent replica
+(weak scaling, no collective on the data path); rank 0 prints the line with the
+whole-job throughput and the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2501_10946_gb300 import workloads as W  # noqa: E402
+
+METRIC = "RBSOG particle-steps/s at N=1e6"
+SMS = 152
+MUFU_PER_CLK_SM = 16            # sin/cos/ex2-class special-function results per clock per SM
+KERNELS_PER_STEP = 12
+# DRAM bytes per launch from the committed ncu capture of the current kernel (None: not captured)
+TRAFFIC = {}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10, e2e_steps=5, clocks=None):
+    """Time K steps of one replica; returns the measurements of this rank."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    r = torch.tensor(W.positions(w), device=dev, dtype=torch.float64)
+    v = torch.tensor(W.velocities(w), device=dev, dtype=torch.float64)
+    p = R.make_params(w, precision=precision, seed=w.seed_k + 1000 * rank, device=dev.index)
+    ctx = R.rbsog_init(p, w.N, W.charges(w), W.masses(w))
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    try:
+        R.rbsog_set_state(ctx, r, v, stream=stream)
+        R.rbsog_step(ctx, warmup, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        if clocks is not None:
+            clocks.__enter__()
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        R.rbsog_step(ctx, steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        if clocks is not None:
+            clocks.__exit__()
+        out["ms"] = e0.elapsed_time(e1)
+        energy = R.rbsog_step(ctx, 0, energy=True, stream=stream)
+        out["energy_total"] = energy["total"] if energy else None
+        # kernel-group durations: eager launches with CUDA events on the same stream
+        if profile_steps:
+            R.rbsog_profile(ctx, True)
+            R.rbsog_step(ctx, profile_steps, stream=stream)
+            torch.cuda.synchronize(dev)
+            out["profile"] = R.rbsog_profile_read(ctx)
+            R.rbsog_profile(ctx, False)
+        # end to end through the C ABI with pinned host buffers
+        if e2e_steps:
+            hr = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
+            hv = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
+            hr.copy_(r.cpu())
+            hv.copy_(v.cpu())
+            ho = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
+            R.rbsog_set_state(ctx, hr, hv, stream=stream)
+            R.rbsog_step(ctx, 1, stream=stream)
+            R.rbsog_get_state(ctx, ho, None, stream=stream)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                R.rbsog_set_state(ctx, hr, hv, stream=stream)
+                R.rbsog_step(ctx, 1, stream=stream)
+                R.rbsog_get_state(ctx, ho, None, stream=stream)
+            torch.cuda.synchronize(dev)
+            out["e2e_s"] = time.perf_counter() - t0
+            out["e2e_steps"] = e2e_steps
+            out["e2e_h2d"] = 2 * w.N * 3 * 8
+            out["e2e_d2h"] = w.N * 3 * 8
+    finally:
+        R.rbsog_free(ctx)
+    return out
+
+
+def roofline(prof, w, steps_profiled, pk):
+    """Roofline of the dominant kernel group (rho or far: MUFU-bound sin/cos)."""
+    groups = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(groups, key=lambda k: groups[k][0])
+    ms, n = groups[dom]
+    avg_s = ms / n * 1e-3
+    sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak = SMS * MUFU_PER_CLK_SM * sm_mhz * 1e6 / 1e9           # G MUFU results/s
+    if dom in ("rho", "far"):
+        units = 2.0 * w.N * w.P                                   # one sin and one cos per (particle, mode)
+    elif dom == "near":
+        lam = w.a_ws / w.kappa
+        pairs = w.N * (4.0 / 3.0) * math.pi * w.r_c ** 3 * w.N / w.volume
+        units = pairs * 6.0                                       # rsqrt, exp(-r/lambda) and ~4 exp per pair
+    else:
+        units = None
+    achieved = units / avg_s / 1e9 if units else None
+    return {"kernel": dom, "bound": "alu", "unit": "Gop/s", "achieved": achieved, "peak": peak,
+            "frac": achieved / peak if achieved else None, "traffic": TRAFFIC.get(dom),
+            "peak_basis": f"{SMS} SMs x {MUFU_PER_CLK_SM} MUFU/clk x {sm_mhz:.0f} MHz",
+            "avg_launch_ms": avg_s * 1e3,
+            "groups_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in groups.items()}}
+
+
+def oracle_step_time(w, steps: int = 1):
+    """The FP64 oracle as it stands (cell-list near field, random-batch far field, BAOAB)
+    on this host's cores for `steps` steps of the workload; returns (seconds, threads)."""
+    from oracle import core, integrate
+    from oracle import sog as S
+    from oracle.sampler import ModeSampler
+    r = W.positions(w)
+    v = W.velocities(w)
+    q = W.charges(w)
+    m = W.masses(w)
+    sog = S.build(w.a_ws / w.kappa, w.r_c, w.sog_eps)
+    Q2 = float(np.sum(q * q))
+    S_ = core.S_sum(w.box, sog, w.kT, Q2)
+    ms = ModeSampler(sog, w.box, w.kT, Q2)
+    draws = {"d": 0}
+
+    def force(x):
+        kset, _ = ms.draw(w.seed_k, draws["d"], w.P)
+        draws["d"] += 1
+        Ft, _, _, _ = core.rb_forces(x, q, w.box, w.r_c, sog, kset, w.kT, S=S_)
+        return Ft
+
+    F = force(r)
+    t0 = time.perf_counter()
+    for n in range(steps):
+        r, v, F = integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n, force)
+    return time.perf_counter() - t0, core.num_threads()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--N", type=int, default=1_000_000)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_info()
+    w = W.cfg_large(args.N)
+    pk, pk_kind = peaks()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = max(1, args.steps)
+        secs, thr = oracle_step_time(w, steps)
+        val = w.N * steps / secs
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "particle-steps/s", "n_gpus": 0,
+                "steps": steps, "warmup": 0, "ms_per_step": secs / steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "N": w.N, "P": w.P, "Gamma": w.Gamma, "kappa": w.kappa,
+                           "r_c_over_a": w.r_c / w.a_ws, "ensemble": w.ensemble},
+                "cpu_baseline": {"value": val, "unit": "particle-steps/s", "cores": thr, "kind": "oracle",
+                                 "sample": f"{steps} full step(s) of the N={w.N} workload, FP64 oracle"},
+                "e2e": {"value": val, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    from paper_2501_10946_gb300 import rbsog as R
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        torch.cuda.set_device(0)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    res = rbsog_replica(w, R.RBSOG_FP32, args.steps, args.warmup, rank, torch, R, clocks=clocks,
+                        profile_steps=10 if rank == 0 else 0, e2e_steps=5 if rank == 0 else 0)
+    ms = res["ms"]
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    total = w.N * args.steps * ws
+    value = total / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "N": w.N, "P": w.P, "Gamma": w.Gamma, "kappa": w.kappa,
+                       "r_c_over_a": w.r_c / w.a_ws, "ensemble": w.ensemble, "integrator": "fp64",
+                       "l2": "inputs larger than L2 (state + records > 129 MB)", "parallelism": f"replicas{ws}"}}
+    rf = roofline(res["profile"], w, 10, pk)
+    rf["peak_source"] = pk_kind
+    line["roofline"] = rf
+    line["clocks"] = clocks.summary() if clocks else None
+    line["gpu_launches"] = KERNELS_PER_STEP * args.steps
+    e2e_rate = w.N * res["e2e_steps"] / res["e2e_s"]
+    line["e2e"] = {"value": e2e_rate, "unit": "particle-steps/s", "h2d_bytes_per_step": res["e2e_h2d"],
+                   "d2h_bytes_per_step": res["e2e_d2h"], "path": "rbsog_set_state(host) + rbsog_step(1) + "
+                   "rbsog_get_state(host), pinned buffers"}
+    if not args.no_fp64:
+        r64 = rbsog_replica(w, R.RBSOG_FP64, 3, 1, rank, torch, R, profile_steps=0, e2e_steps=0)
+        line["fp64"] = {"value": w.N * 3 / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"] / 3, "steps": 3}
+    if not args.no_cpu:
+        secs, thr = oracle_step_time(w, 1)
+        line["cpu_baseline"] = {"value": w.N / secs, "unit": "particle-steps/s", "cores": thr, "kind": "oracle",
+                                "sample": f"1 full step of the N={w.N} workload (FP64 oracle, OpenMP)"}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

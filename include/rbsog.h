@@ -1,0 +1,189 @@
+/*
+ * rbsog.h -- C ABI of the GB300 (sm_103a) random batch sum-of-Gaussians force step
+ * for 3-D periodic Yukawa systems (Chen, Liang & Xu, "Random batch sum-of-Gaussians
+ * algorithm for molecular dynamics simulations of Yukawa systems in three dimensions").
+ *
+ * One step of Algorithm 2 on the GPU, every part in hand-written CUDA:
+ *   cell list (counting sort)  ->  near field, Eq. (55) first term, Eqs. (56)-(57)
+ *   k-sampler, Eq. (59)        ->  structure factor rho(k_l) = sum_j q_j e^{i k_l . r_j} (Sec. 2)
+ *   far-force gather, Eq. (60) ->  velocity Verlet or Langevin update (Algorithm 2, last step)
+ * The SOG decomposition (Algorithm 1, Eqs. (27)-(38)) is built on the host at init.
+ *
+ * Conventions for every entry point
+ *   - Status: each call returns RBSOG_OK (0) or a positive RBSOG_E* code; a message
+ *     is available from rbsog_last_error(ctx).  Nothing throws across the ABI, and
+ *     there is no CPU fallback: if the GPU path cannot run, the call fails.
+ *   - Vectors are [N][3] row-major float64 in the caller's particle order.
+ *   - Pointers marked "host or device" may point to host memory (pageable or pinned)
+ *     or to device memory on the context's device (unified addressing decides).
+ *   - Pointers marked "host" must be host memory; "device" must be device memory.
+ *   - The caller owns every pointer it passes; the library copies what it keeps.
+ *     The library owns all of its internal device buffers and frees them in
+ *     rbsog_free.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls that
+ *     take a stream enqueue their work on it and may return before it completes,
+ *     except where marked "synchronous".
+ *   - Reduced units: charge and mass are whatever the caller passes; lengths, kappa
+ *     and Gamma follow Sec. 5.1 (Gamma = Q^2/(a k_B T) with Q = 1, kappa = a/lambda).
+ */
+#ifndef RBSOG_H
+#define RBSOG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define RBSOG_OK 0
+#define RBSOG_EINVAL 1        /* bad argument or parameter (r_c > L/2, P < 1, N < 2, ...) */
+#define RBSOG_ENOMEM 2        /* a device allocation failed */
+#define RBSOG_ECUDA 3         /* a CUDA runtime call or kernel failed */
+#define RBSOG_ETIMEOUT 4      /* a bounded device-side loop hit its limit */
+#define RBSOG_ENOCONV 5       /* the SOG construction found no C1 root / no decomposition */
+#define RBSOG_EUNSUPPORTED 6  /* a valid request this build does not implement */
+#define RBSOG_EOVERFLOW 7     /* a cell holds more particles than the near-field kernel stages */
+
+/* precision */
+#define RBSOG_FP64 0          /* every force and phase in FP64 (parity build) */
+#define RBSOG_FP32 1          /* FP32 pair and phase arithmetic with compensated sums;
+                                 FP64 positions, velocities, integration and energies */
+/* ensemble */
+#define RBSOG_NVE 0           /* velocity Verlet */
+#define RBSOG_LANGEVIN 1      /* BAOAB Langevin, friction langevin_gamma, target k_B T */
+/* sog_mode: how (M1, M2) of Algorithm 1 are chosen */
+#define RBSOG_SOG_MINIMAL 0   /* fewest Gaussians with max |Y - F| <= sog_eps on [r_c, 33 lambda] */
+#define RBSOG_SOG_BOUND 1     /* ceilings of Eqs. (29)-(30) at the C0 root alpha_1 of Eq. (35) */
+#define RBSOG_SOG_TABLE 2     /* sog_M1, sog_M2 given (e.g. a row of Table 1) */
+
+typedef struct rbsog_ctx rbsog_ctx;
+
+typedef struct rbsog_params {
+    double box[3];          /* L_x, L_y, L_z (absolute lengths), each > 0 */
+    double kappa;           /* screening parameter a/lambda (Sec. 5.1), > 0 */
+    double a_ws;            /* Wigner-Seitz radius a; 0 selects (3V/(4 pi N))^(1/3) */
+    double Gamma;           /* bare coupling Q^2/(a k_B T) with Q = 1 (Sec. 5.1) */
+    double kT;              /* > 0 overrides k_B T = 1/(a Gamma) */
+    double r_c;             /* near-field cutoff (absolute), 0 < r_c <= min(L)/2 */
+    double sog_eps;         /* SOG tolerance eps of Algorithm 1, in (0, 0.1] */
+    double dt;              /* time step */
+    double langevin_gamma;  /* Langevin friction (1/time), used with RBSOG_LANGEVIN */
+    uint64_t seed;          /* Philox key for the k-sampler and the Langevin noise */
+    int32_t P;              /* random-batch size, 1 <= P <= 4096 */
+    int32_t precision;      /* RBSOG_FP64 | RBSOG_FP32 */
+    int32_t ensemble;       /* RBSOG_NVE | RBSOG_LANGEVIN */
+    int32_t sog_mode;       /* RBSOG_SOG_MINIMAL | RBSOG_SOG_BOUND | RBSOG_SOG_TABLE */
+    int32_t sog_M1;         /* with RBSOG_SOG_TABLE: M1 of Eq. (37) */
+    int32_t sog_M2;         /* with RBSOG_SOG_TABLE: M2 of Eq. (37) */
+    int32_t device;         /* CUDA device ordinal */
+    int32_t reserved;       /* must be 0 */
+} rbsog_params;
+
+typedef struct rbsog_energy {
+    double U_near;          /* U_N of Eq. (50) over pairs inside r_c */
+    double U_far;           /* random-batch estimate U*_F of Eq. (60) plus the k = 0 term */
+    double U_self;          /* U_self of Eq. (52) */
+    double kinetic;         /* sum_i m_i |v_i|^2 / 2 */
+    double total;           /* U_near + U_far + U_self + kinetic (Eq. 49 plus kinetic energy) */
+    uint64_t step;          /* steps taken since rbsog_set_state */
+} rbsog_energy;
+
+/* Create a context: builds the SOG decomposition of Algorithm 1 on the host, the
+ * sampling tables of P(k) (Eq. 59) and its normalisation S on the device, and
+ * allocates every device buffer for N particles.  q_host and m_host are host arrays
+ * of N charges and N masses (masses > 0), copied.  Synchronous.  On success *out
+ * holds the context; on failure *out is NULL and the message is available from
+ * rbsog_last_error(NULL). */
+int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, const double *m_host,
+               rbsog_ctx **out);
+
+/* Set positions r ([N][3], any real values; wrapped into the box) and velocities v
+ * ([N][3]; NULL = zero), host or device pointers.  Resets the step counter and the
+ * internal particle order.  The force at the new state is computed by the next
+ * rbsog_step or rbsog_forces.  Enqueued on stream. */
+int rbsog_set_state(rbsog_ctx *ctx, const double *r, const double *v, void *stream);
+
+/* Copy positions (wrapped into [0, L)) and velocities to r and v ([N][3], host or
+ * device; either may be NULL) in the caller's particle order, and the step counter
+ * to *step (host; may be NULL).  Synchronous. */
+int rbsog_get_state(rbsog_ctx *ctx, double *r, double *v, uint64_t *step, void *stream);
+
+/* Forces at the current positions (Eq. 55 with the far part estimated by Eq. 60)
+ * from one fresh draw of P modes (or the set injected by rbsog_set_ksample) into
+ * F ([N][3], host or device; NULL = keep internal only).  If e is not NULL the
+ * energies are written to *e and the call is synchronous; otherwise enqueued. */
+int rbsog_forces(rbsog_ctx *ctx, double *F, rbsog_energy *e, void *stream);
+
+/* As rbsog_forces, with the near part (Eq. 55 first term) in F_near and the
+ * random-batch far part (Eq. 60) in F_far; either may be NULL. */
+int rbsog_forces_split(rbsog_ctx *ctx, double *F_near, double *F_far, rbsog_energy *e, void *stream);
+
+/* Advance nsteps >= 0 steps of Algorithm 2 (sample, far force, near force,
+ * integrate).  The step sequence is captured once as a CUDA graph (on an internal
+ * stream) and replayed on `stream`.  If e is not NULL the energies after the last step are written to *e
+ * and the call is synchronous. */
+int rbsog_step(rbsog_ctx *ctx, int32_t nsteps, rbsog_energy *e, void *stream);
+
+/* Inject the next force evaluation's modes: m_host is P triples (m_x, m_y, m_z) of
+ * integers, not all zero, k = 2 pi (m_x/L_x, m_y/L_y, m_z/L_z).  Used once, then
+ * sampling resumes.  P must equal the context's P.  Host pointer; synchronous. */
+int rbsog_set_ksample(rbsog_ctx *ctx, const int32_t *m_host, int32_t P);
+
+/* The modes and coefficients coef_l = S/(P V calF(k_l)) of the last force
+ * evaluation (host arrays of P triples and P doubles; either may be NULL). Synchronous. */
+int rbsog_get_ksample(rbsog_ctx *ctx, int32_t *m_host, double *coef_host);
+
+/* rho(k_l) of the last force evaluation as P (Re, Im) pairs (host).  Synchronous. */
+int rbsog_get_rho(rbsog_ctx *ctx, double *rho_host);
+
+/* The cell list of the last force evaluation: nc[3] cells per axis, cell_start
+ * (n_c^3 + 1 entries) and perm (N entries, the caller's particle index at each
+ * cell-sorted position; within a cell, ascending).  Host arrays; any may be NULL.
+ * Cells: s_a = floor(frac(r_a/L_a) 2^32), c_a = floor(s_a n_a / 2^32), c = c_x +
+ * n_x (c_y + n_y c_z), n_a = floor(L_a / r_c) when >= 3 else 1.  Synchronous. */
+int rbsog_get_cells(rbsog_ctx *ctx, int32_t *nc, uint32_t *cell_start, uint32_t *perm);
+
+/* The SOG decomposition in use (Eq. 37): h, t0, M1, M2, the C1 weight w of m = M2,
+ * lambda, and the sampling normalisation S = sum_{k != 0} calF(k) Fhat(k).  Host
+ * pointers, any may be NULL. */
+int rbsog_get_sog(rbsog_ctx *ctx, double *h, double *t0, int32_t *M1, int32_t *M2, double *w, double *lam,
+                  double *S);
+
+/* Kernel-group timing.  With enable != 0, rbsog_step and rbsog_forces launch their
+ * kernels eagerly (no graph) and record CUDA events on the launching stream around
+ * each of the RBSOG_NPROF groups named by rbsog_profile_name: bin (integrator first
+ * half + cell binning), scan, sort (scatter + per-cell sort), gather, sample, near,
+ * rho, rho_final, far (gather of Eq. 60 + closing half kick), energy.  enable = 0
+ * restores graph replay.  Either call discards collected timings.  Synchronous. */
+#define RBSOG_NPROF 10
+int rbsog_profile(rbsog_ctx *ctx, int32_t enable);
+
+/* Summed event time in milliseconds (ms[RBSOG_NPROF]) and the number of launches
+ * (launches[RBSOG_NPROF]) of each group since the last read, then discards them.
+ * Host arrays.  Synchronous. */
+int rbsog_profile_read(rbsog_ctx *ctx, double *ms, int64_t *launches);
+
+/* Name of profiling group g (0 <= g < RBSOG_NPROF), or "" (static string). */
+const char *rbsog_profile_name(int32_t group);
+
+/* Algorithm 1 on the host alone (no device is touched): the C1 SOG decomposition of
+ * exp(-r/lambda)/r for cutoff r_c and tolerance eps with (M1, M2) chosen by mode
+ * (RBSOG_SOG_*; M1, M2 are read only for RBSOG_SOG_TABLE).  Writes
+ * out6 = {h, t0, M1, M2, w, max |Y - F| on the 2000-point grid of [r_c, 33 lambda]}
+ * (host array of 6 doubles).  RBSOG_ENOCONV when no C1 root or decomposition exists;
+ * the message is then available from rbsog_last_error(NULL). */
+int rbsog_build_sog(double lam, double r_c, double eps, int32_t mode, int32_t M1, int32_t M2, double *out6);
+
+/* Message of the last failed call on ctx (or of the last failed rbsog_init when ctx
+ * is NULL).  The pointer stays valid until the next call on the same context. */
+const char *rbsog_last_error(const rbsog_ctx *ctx);
+
+/* Release every device buffer and graph of ctx.  Synchronous.  NULL is a no-op. */
+void rbsog_free(rbsog_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBSOG_H */

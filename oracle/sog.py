@@ -19,7 +19,7 @@ Algorithm 1 takes delta = r_c and R = 33 lambda.  Three ways to pick (M1, M2):
   * "minimal": the fewest Gaussians whose C1 decomposition has max |Y - F| <= eps on a
                2000-point log grid over [r_c, 33 lambda]; ties broken by the smaller error.
 In every mode t0 is the smallest root in [0, h) of the C1 condition with w from C0
-(Algorithm 1 step 6); roots are bracketed on a 200-point grid and refined by Brent's method.
+(Algorithm 1 step 6); roots are bracketed on a 200-interval grid and refined by bisection to the last bit.
 """
 from __future__ import annotations
 
@@ -27,7 +27,6 @@ import dataclasses
 import math
 
 import numpy as np
-from scipy.optimize import brentq
 from scipy.special import lambertw
 
 SQRT_PI = math.sqrt(math.pi)
@@ -149,23 +148,39 @@ def c1_residual(t0: float, h: float, M1: int, M2: int, lam: float, rc: float) ->
     return float(dyukawa(rc, lam)) - dF
 
 
+def bisect(fun, a: float, b: float, fa: float) -> float:
+    """Bisection on a sign change of fun in [a, b] until the midpoint is no longer
+    strictly inside the bracket (the last representable bit)."""
+    for _ in range(400):
+        mid = 0.5 * (a + b)
+        if not (a < mid < b):
+            break
+        fm = fun(mid)
+        if not math.isfinite(fm) or fm == 0.0:
+            return mid
+        if (fm < 0.0) == (fa < 0.0):
+            a, fa = mid, fm
+        else:
+            b = mid
+    return 0.5 * (a + b)
+
+
 def smallest_root(fun, h: float):
-    """Smallest root of fun on [0, h): sign change on a ROOT_GRID grid, then Brent."""
-    grid = np.linspace(0.0, h, ROOT_GRID + 1)
+    """Smallest root of fun on [0, h): sign change on a ROOT_GRID grid, then bisection."""
+    grid = [h * k / ROOT_GRID for k in range(ROOT_GRID + 1)]
     with np.errstate(over="ignore", under="ignore", invalid="ignore"):
         vals = [fun(x) for x in grid]
-    for k in range(ROOT_GRID):
-        a, b = grid[k], grid[k + 1]
-        fa, fb = vals[k], vals[k + 1]
-        if not (math.isfinite(fa) and math.isfinite(fb)):
-            continue
-        if fa == 0.0:
-            return a
-        if fa * fb < 0.0:
-            with np.errstate(over="ignore", under="ignore", invalid="ignore"):
-                x = brentq(fun, a, b, xtol=1e-300, rtol=4 * np.finfo(float).eps, maxiter=500)
-            if x < h:
-                return x
+        for k in range(ROOT_GRID):
+            a, b = grid[k], grid[k + 1]
+            fa, fb = vals[k], vals[k + 1]
+            if not (math.isfinite(fa) and math.isfinite(fb)):
+                continue
+            if fa == 0.0:
+                return a
+            if fa * fb < 0.0:
+                x = bisect(fun, a, b, fa)
+                if x < h:
+                    return x
     return None
 
 

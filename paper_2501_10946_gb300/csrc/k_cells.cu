@@ -1,0 +1,302 @@
+// Cell list by stable counting sort, fused with the first half of the integrator.
+//
+// Per step (Algorithm 2: integrate, then rebuild the neighbour structure of Eq. 55):
+//   k_bin          v += F dt/2m, drift (BAOAB: half drift, Ornstein-Uhlenbeck, half drift),
+//                  wrap into [0, L), fixed point s = floor(frac(r/L) 2^32) (2^64 in FP64),
+//                  cell c_a = floor(s_a n_a / 2^32), atomic count -> slot within the cell
+//   k_tile_sums    per 4096-cell tile population
+//   k_scan_tiles   exclusive scan -> cell_start; clears the counts for the next build
+//   k_scatter      key = (particle id, previous position) at cell_start + slot
+//   k_sort_cells   each cell's keys ascending by particle id (the order the atomics
+//                  produced is discarded, so the result is deterministic)
+//   k_gather       state and 16/32-byte particle records into the new cell order
+#include "common.cuh"
+#include "kernels.h"
+#include "philox.cuh"
+
+namespace rbsog {
+
+namespace {
+
+__device__ __forceinline__ double wrap_coord(double r, double L) {
+    // r - L floor(r/L), then into [0, L): IEEE operations without contraction
+    double w = __dsub_rn(r, __dmul_rn(L, floor(__ddiv_rn(r, L))));
+    if (w < 0.0) w = __dadd_rn(w, L);
+    if (w >= L) w = __dsub_rn(w, L);
+    return w;
+}
+
+__device__ __forceinline__ double frac01(double r, double L) {
+    double u = __ddiv_rn(r, L);
+    double f = __dsub_rn(u, floor(u));
+    return f >= 1.0 ? 0.0 : f;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_bin(BinArgs a) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.N) return;
+    const uint32_t N = a.N;
+    double r[3] = {a.in.rx[k], a.in.ry[k], a.in.rz[k]};
+    double v[3] = {a.in.vx[k], a.in.vy[k], a.in.vz[k]};
+    const double invm = a.in.invm[k];
+    const uint32_t id = a.in.id[k];
+    if (a.integrate) {
+        double F[3];
+        if (PREC == 1) {
+            const float *Ff = (const float *)a.F;
+            F[0] = Ff[k]; F[1] = Ff[N + k]; F[2] = Ff[2 * (size_t)N + k];
+        } else {
+            const double *Fd = (const double *)a.F;
+            F[0] = Fd[k]; F[1] = Fd[N + k]; F[2] = Fd[2 * (size_t)N + k];
+        }
+        const double hk = 0.5 * a.dt * invm;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[d] += hk * F[d];
+        if (a.integrate == 1) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) r[d] += a.dt * v[d];
+        } else {
+            // B A O A of BAOAB; noise: Philox key = seed, counter = (id, 0x40000000 + j, step)
+            const unsigned long long step = a.ctr->step;
+            const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+            U4 w0 = philox10(id, 0x40000000u, (uint32_t)step, (uint32_t)(step >> 32), k0, k1);
+            U4 w1 = philox10(id, 0x40000001u, (uint32_t)step, (uint32_t)(step >> 32), k0, k1);
+            double u1 = u53_of(w0.x, w0.y), u2 = u53_of(w0.z, w0.w);
+            double rad = sqrt(-2.0 * log(1.0 - u1));
+            double s2, c2;
+            sincospi(2.0 * u2, &s2, &c2);
+            double u3 = u53_of(w1.x, w1.y), u4 = u53_of(w1.z, w1.w);
+            double rad3 = sqrt(-2.0 * log(1.0 - u3));
+            double xi[3] = {rad * c2, rad * s2, rad3 * cospi(2.0 * u4)};
+            const double sig = sqrt((1.0 - a.c1 * a.c1) * a.kT * invm);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                r[d] += 0.5 * a.dt * v[d];
+                v[d] = a.c1 * v[d] + sig * xi[d];
+                r[d] += 0.5 * a.dt * v[d];
+            }
+        }
+    }
+    uint32_t cc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        r[d] = wrap_coord(r[d], a.box.L[d]);
+        double f = frac01(r[d], a.box.L[d]);
+        uint32_t s32;
+        if (PREC == 1) {
+            s32 = (uint32_t)__double2ull_rz(f * 4294967296.0);
+            ((uint32_t *)a.s)[(size_t)d * N + k] = s32;
+        } else {
+            unsigned long long s64 = __double2ull_rz(f * 18446744073709551616.0);
+            ((unsigned long long *)a.s)[(size_t)d * N + k] = s64;
+            s32 = (uint32_t)(s64 >> 32);
+        }
+        cc[d] = (uint32_t)(((unsigned long long)s32 * (unsigned long long)a.box.nc[d]) >> 32);
+    }
+    a.out.rx[k] = r[0]; a.out.ry[k] = r[1]; a.out.rz[k] = r[2];
+    a.out.vx[k] = v[0]; a.out.vy[k] = v[1]; a.out.vz[k] = v[2];
+    a.out.invm[k] = invm;
+    a.out.q[k] = a.in.q[k];
+    a.out.id[k] = id;
+    uint32_t c = cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);
+    a.cell[k] = c;
+    a.slot[k] = atomicAdd(&a.count[c], 1u);
+}
+
+__device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    uint32_t t = (threadIdx.x < 32) ? sh[threadIdx.x] : 0u;
+    if (wid == 0) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) sh[32] = t;
+    __syncthreads();
+    uint32_t out = sh[32];
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(1024) k_tile_sums(const uint32_t *count, int ncell, uint32_t *tile_sums) {
+    __shared__ uint32_t sh[33];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (base + j < ncell) s += count[base + j];
+    s = block_sum_1024(s, sh);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *count, int ncell, const uint32_t *tile_sums,
+                                                     uint32_t *cell_start, uint32_t N) {
+    __shared__ uint32_t sh[33];
+    __shared__ uint32_t wsum[32];
+    // population of the preceding tiles
+    uint32_t pre = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) pre += tile_sums[b];
+    pre = block_sum_1024(pre, sh);
+    const int base = blockIdx.x * kScanTile + threadIdx.x * 4;
+    uint32_t c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c[j] = (base + j < ncell) ? count[base + j] : 0u;
+    uint32_t tot = c[0] + c[1] + c[2] + c[3];
+    // inclusive warp scan of the thread totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = wsum[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        wsum[lane] = wi - w;   // exclusive
+    }
+    __syncthreads();
+    uint32_t run = pre + wsum[wid] + inc - tot;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (base + j < ncell) {
+            cell_start[base + j] = run;
+            count[base + j] = 0u;
+        }
+        run += c[j];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) cell_start[ncell] = N;
+}
+
+__global__ void __launch_bounds__(256) k_scatter(const uint32_t *cell, const uint32_t *slot,
+                                                 const uint32_t *cell_start, const uint32_t *id, uint32_t N,
+                                                 unsigned long long *keys) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    keys[cell_start[cell[k]] + slot[k]] = ((unsigned long long)id[k] << 32) | (unsigned long long)k;
+}
+
+__global__ void __launch_bounds__(256) k_sort_cells(const uint32_t *cell_start, int ncell, unsigned long long *keys,
+                                                    uint32_t *perm_src, DevCounters *ctr) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const uint32_t lo = cell_start[c], hi = cell_start[c + 1];
+    if (hi - lo > (uint32_t)kMaxCellOcc) {
+        atomicOr(&ctr->err, kErrCellOverflow);
+    } else {
+        for (uint32_t i = lo + 1; i < hi; ++i) {
+            unsigned long long key = keys[i];
+            uint32_t j = i;
+            while (j > lo && keys[j - 1] > key) {
+                keys[j] = keys[j - 1];
+                --j;
+            }
+            keys[j] = key;
+        }
+    }
+    for (uint32_t i = lo; i < hi; ++i) perm_src[i] = (uint32_t)keys[i];
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
+    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.N) return;
+    const uint32_t src = g.perm_src[p];
+    const uint32_t N = g.N;
+    g.out.rx[p] = g.in.rx[src]; g.out.ry[p] = g.in.ry[src]; g.out.rz[p] = g.in.rz[src];
+    g.out.vx[p] = g.in.vx[src]; g.out.vy[p] = g.in.vy[src]; g.out.vz[p] = g.in.vz[src];
+    g.out.invm[p] = g.in.invm[src];
+    const double q = g.in.q[src];
+    g.out.q[p] = q;
+    g.out.id[p] = g.in.id[src];
+    if (PREC == 1) {
+        const uint32_t *s = (const uint32_t *)g.s;
+        ((uint4 *)g.rec)[p] = make_uint4(s[src], s[N + src], s[2 * (size_t)N + src], __float_as_uint((float)q));
+    } else {
+        const unsigned long long *s = (const unsigned long long *)g.s;
+        Rec64 r;
+        r.s[0] = s[src]; r.s[1] = s[N + src]; r.s[2] = s[2 * (size_t)N + src];
+        r.q = q;
+        ((Rec64 *)g.rec)[p] = r;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_set_state(const double *r, const double *v, const double *q_user,
+                                                   const double *m_user, State rest, uint32_t N, Box box) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    rest.rx[k] = wrap_coord(r[3 * (size_t)k], box.L[0]);
+    rest.ry[k] = wrap_coord(r[3 * (size_t)k + 1], box.L[1]);
+    rest.rz[k] = wrap_coord(r[3 * (size_t)k + 2], box.L[2]);
+    rest.vx[k] = v ? v[3 * (size_t)k] : 0.0;
+    rest.vy[k] = v ? v[3 * (size_t)k + 1] : 0.0;
+    rest.vz[k] = v ? v[3 * (size_t)k + 2] : 0.0;
+    rest.invm[k] = 1.0 / m_user[k];
+    rest.q[k] = q_user[k];
+    rest.id[k] = k;
+}
+
+__global__ void k_reset_counters(DevCounters *ctr) {
+    ctr->step = 0;
+    ctr->err = 0;
+}
+
+__global__ void __launch_bounds__(256) k_get_state(State rest, uint32_t N, double *r_out, double *v_out) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const size_t u = 3 * (size_t)rest.id[k];
+    if (r_out) { r_out[u] = rest.rx[k]; r_out[u + 1] = rest.ry[k]; r_out[u + 2] = rest.rz[k]; }
+    if (v_out) { v_out[u] = rest.vx[k]; v_out[u + 1] = rest.vy[k]; v_out[u + 2] = rest.vz[k]; }
+}
+
+inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_bin(int prec, const BinArgs &a, cudaStream_t st) {
+    if (prec == 1) k_bin<1><<<blocks_for(a.N, 256), 256, 0, st>>>(a);
+    else k_bin<0><<<blocks_for(a.N, 256), 256, 0, st>>>(a);
+}
+
+void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int ncell, uint32_t N,
+                 cudaStream_t st) {
+    const int tiles = (ncell + kScanTile - 1) / kScanTile;
+    k_tile_sums<<<tiles, 1024, 0, st>>>(count, ncell, tile_sums);
+    k_scan_tiles<<<tiles, 1024, 0, st>>>(count, ncell, tile_sums, cell_start, N);
+}
+
+void launch_scatter_sort(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
+                         uint32_t N, int ncell, unsigned long long *keys, uint32_t *perm_src, DevCounters *ctr,
+                         cudaStream_t st) {
+    k_scatter<<<blocks_for(N, 256), 256, 0, st>>>(cell, slot, cell_start, id, N, keys);
+    k_sort_cells<<<blocks_for((uint32_t)ncell, 256), 256, 0, st>>>(cell_start, ncell, keys, perm_src, ctr);
+}
+
+void launch_gather(int prec, const GatherArgs &g, cudaStream_t st) {
+    if (prec == 1) k_gather<1><<<blocks_for(g.N, 256), 256, 0, st>>>(g);
+    else k_gather<0><<<blocks_for(g.N, 256), 256, 0, st>>>(g);
+}
+
+void launch_set_state(const double *r, const double *v, const double *q_user, const double *m_user, State rest,
+                      uint32_t N, Box box, DevCounters *ctr, cudaStream_t st) {
+    k_set_state<<<blocks_for(N, 256), 256, 0, st>>>(r, v, q_user, m_user, rest, N, box);
+    k_reset_counters<<<1, 1, 0, st>>>(ctr);
+}
+
+void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st) {
+    k_get_state<<<blocks_for(N, 256), 256, 0, st>>>(rest, N, r_out, v_out);
+}
+
+}  // namespace rbsog

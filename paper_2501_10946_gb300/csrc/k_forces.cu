@@ -1,0 +1,521 @@
+// Force kernels of one RBSOG step.
+//
+//   k_near    near field, Eq. (55) first term with F_N1, F_N2 of Eqs. (56)-(57), and
+//             U_N of Eq. (50), over the 27 neighbour cells of each particle (minimum
+//             image by wrapping fixed-point differences).  FP32 build: compensated sums.
+//   k_rho     structure factor rho(k_l) = sum_j q_j exp(i k_l.r_j) (Sec. 2): per block,
+//             lane <-> mode, particles broadcast from shared memory; phases are exact
+//             integer products m.s modulo 2^32 (2^64), so sin/cos see [-pi, pi).
+//   k_rho_fin fixed-order grid reduction, U*_F of Eq. (60) and the gather table.
+//   k_far     F*_i = -q_i sum_l coef_l k_l Im(exp(-i k_l.r_i) rho_l) (Eq. 60), added to
+//             the near force, fused with the closing half kick v += F dt/(2m).
+//   k_energy  fixed-order reduction of the energy partials.
+#include <math_constants.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rbsog {
+
+namespace {
+
+constexpr int kNearThreads = 128;
+constexpr int kRhoThreads = 256;
+constexpr int kRhoTile = 512;       // particles staged per tile (FP32: 8 KB, FP64: 16 KB)
+constexpr int kFarThreads = 256;
+constexpr int kFarTile = 512;       // modes staged per tile
+constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;   // 2 pi / 2^32
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_reduce_sum(T v, T *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    T out = sh[0];
+    __syncthreads();
+    return out;
+}
+
+// ------------------------------------------------------------------ near field
+template <int PREC>
+__global__ void __launch_bounds__(kNearThreads) k_near(NearArgs a) {
+    __shared__ double shU[kNearThreads];
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    double Uthread = 0.0;
+    // an overflowing cell (reported as RBSOG_EOVERFLOW) would make the pair loops quadratic
+    const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
+    if (p < a.N && overflow) {
+        for (int d = 0; d < 3; ++d) {
+            if (PREC == 1) ((float *)a.Fn)[(size_t)d * a.N + p] = 0.f;
+            else ((double *)a.Fn)[(size_t)d * a.N + p] = 0.0;
+        }
+    }
+    if (p < a.N && !overflow) {
+        const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
+        if (PREC == 1) {
+            const uint4 *rec = (const uint4 *)a.rec;
+            const uint4 ri = rec[p];
+            const float qi = __uint_as_float(ri.w);
+            const uint32_t si[3] = {ri.x, ri.y, ri.z};
+            int ci[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                ci[d] = (int)(((unsigned long long)si[d] * (unsigned long long)a.box.nc[d]) >> 32);
+            float Fs[3] = {0.f, 0.f, 0.f}, Fc[3] = {0.f, 0.f, 0.f}, Us = 0.f, Uc = 0.f;
+            const int zlo = nz >= 3 ? -1 : 0, zhi = nz >= 3 ? 1 : 0;
+            const int ylo = ny >= 3 ? -1 : 0, yhi = ny >= 3 ? 1 : 0;
+            const int xlo = nx >= 3 ? -1 : 0, xhi = nx >= 3 ? 1 : 0;
+            for (int dz = zlo; dz <= zhi; ++dz) {
+                const int cz = (ci[2] + dz + nz) % nz;
+                for (int dy = ylo; dy <= yhi; ++dy) {
+                    const int cy = (ci[1] + dy + ny) % ny;
+                    for (int dx = xlo; dx <= xhi; ++dx) {
+                        const int cx = (ci[0] + dx + nx) % nx;
+                        const int c = cx + nx * (cy + ny * cz);
+                        const uint32_t j0 = a.cell_start[c], j1 = a.cell_start[c + 1];
+                        for (uint32_t j = j0; j < j1; ++j) {
+                            if (j == p) continue;
+                            const uint4 rj = rec[j];
+                            const float d0 = (float)(int)(si[0] - rj.x) * a.box.L_2m32f[0];
+                            const float d1 = (float)(int)(si[1] - rj.y) * a.box.L_2m32f[1];
+                            const float d2 = (float)(int)(si[2] - rj.z) * a.box.L_2m32f[2];
+                            const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                            if (r2 < a.nc.rc2_f) {
+                                const float rinv = rsqrtf(r2);
+                                const float r = r2 * rinv;
+                                const float e1 = ex2_approx(-r * a.nc.inv_lam_log2e_f);
+                                float fsog = 0.f, fn2 = 0.f;
+                                for (int g = 0; g < a.nc.mtot; ++g) {
+                                    const float E = ex2_approx(-r2 * a.nc.bl2f[g]);
+                                    fsog = fmaf(a.nc.af[g], E, fsog);
+                                    fn2 = fmaf(a.nc.cf[g], E, fn2);
+                                }
+                                const float qq = qi * __uint_as_float(rj.w);
+                                const float fn1 = e1 * (1.f + r * a.nc.inv_lam_f) * (rinv * rinv * rinv);
+                                const float gsc = qq * (fn1 + fn2);
+                                kahan_add(Fs[0], Fc[0], gsc * d0);
+                                kahan_add(Fs[1], Fc[1], gsc * d1);
+                                kahan_add(Fs[2], Fc[2], gsc * d2);
+                                kahan_add(Us, Uc, 0.5f * qq * (e1 * rinv - fsog));
+                            }
+                        }
+                    }
+                }
+            }
+            float *Fn = (float *)a.Fn;
+            Fn[p] = Fs[0] - Fc[0];
+            Fn[a.N + p] = Fs[1] - Fc[1];
+            Fn[2 * (size_t)a.N + p] = Fs[2] - Fc[2];
+            Uthread = (double)Us - (double)Uc;
+        } else {
+            const Rec64 *rec = (const Rec64 *)a.rec;
+            const Rec64 ri = rec[p];
+            int ci[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                ci[d] = (int)(((ri.s[d] >> 32) * (unsigned long long)a.box.nc[d]) >> 32);
+            double F[3] = {0.0, 0.0, 0.0}, U = 0.0;
+            const int zlo = nz >= 3 ? -1 : 0, zhi = nz >= 3 ? 1 : 0;
+            const int ylo = ny >= 3 ? -1 : 0, yhi = ny >= 3 ? 1 : 0;
+            const int xlo = nx >= 3 ? -1 : 0, xhi = nx >= 3 ? 1 : 0;
+            for (int dz = zlo; dz <= zhi; ++dz) {
+                const int cz = (ci[2] + dz + nz) % nz;
+                for (int dy = ylo; dy <= yhi; ++dy) {
+                    const int cy = (ci[1] + dy + ny) % ny;
+                    for (int dx = xlo; dx <= xhi; ++dx) {
+                        const int cx = (ci[0] + dx + nx) % nx;
+                        const int c = cx + nx * (cy + ny * cz);
+                        const uint32_t j0 = a.cell_start[c], j1 = a.cell_start[c + 1];
+                        for (uint32_t j = j0; j < j1; ++j) {
+                            if (j == p) continue;
+                            const Rec64 rj = rec[j];
+                            double d[3];
+#pragma unroll
+                            for (int e = 0; e < 3; ++e)
+                                d[e] = (double)(long long)(ri.s[e] - rj.s[e]) * a.box.L_2m64[e];
+                            const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (r2 < a.nc.rc2) {
+                                const double r = sqrt(r2);
+                                const double rinv = 1.0 / r;
+                                const double e1 = exp(-r * a.nc.inv_lam);
+                                double fsog = 0.0, fn2 = 0.0;
+                                for (int g = 0; g < a.nc.mtot; ++g) {
+                                    const double E = exp(-r2 * a.nc.b[g]);
+                                    fsog += a.nc.a[g] * E;
+                                    fn2 += a.nc.c[g] * E;
+                                }
+                                const double qq = ri.q * rj.q;
+                                const double fn1 = e1 * (1.0 + r * a.nc.inv_lam) * (rinv * rinv * rinv);
+                                const double gsc = qq * (fn1 + fn2);
+                                F[0] += gsc * d[0];
+                                F[1] += gsc * d[1];
+                                F[2] += gsc * d[2];
+                                U += 0.5 * qq * (e1 * rinv - fsog);
+                            }
+                        }
+                    }
+                }
+            }
+            double *Fn = (double *)a.Fn;
+            Fn[p] = F[0];
+            Fn[a.N + p] = F[1];
+            Fn[2 * (size_t)a.N + p] = F[2];
+            Uthread = U;
+        }
+    }
+    double tot = block_reduce_sum<double>(Uthread, shU);
+    if (threadIdx.x == 0) a.U_part[blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ structure factor
+// Work split of one block: warp w serves mode group g = w % ngroups (32*ML modes of the
+// pass) and particle subset sub = w / ngroups (stride nsub through each tile).
+__device__ __forceinline__ void rho_split(int P, int pass_base, int ML, int &ngroups, int &nsub) {
+    int left = P - pass_base;
+    ngroups = (left + 32 * ML - 1) / (32 * ML);
+    if (ngroups > 8) ngroups = 8;
+    nsub = 8 / ngroups;
+}
+
+template <int ML>
+__global__ void __launch_bounds__(kRhoThreads) k_rho32(RhoArgs a, int chunk) {
+    __shared__ uint4 sp[kRhoTile];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pass_base = blockIdx.y * 256 * ML;
+    int ngroups, nsub;
+    rho_split(a.P, pass_base, ML, ngroups, nsub);
+    const int g = warp % ngroups, sub = warp / ngroups;
+    const bool active = sub < nsub;
+    int mm[ML][3];
+    int lidx[ML];
+#pragma unroll
+    for (int j = 0; j < ML; ++j) {
+        lidx[j] = pass_base + g * 32 * ML + j * 32 + lane;
+        const bool ok = active && lidx[j] < a.P;
+        mm[j][0] = ok ? a.m[3 * lidx[j]] : 0;
+        mm[j][1] = ok ? a.m[3 * lidx[j] + 1] : 0;
+        mm[j][2] = ok ? a.m[3 * lidx[j] + 2] : 0;
+    }
+    float sre[ML], cre[ML], sim[ML], cim[ML];
+#pragma unroll
+    for (int j = 0; j < ML; ++j) sre[j] = cre[j] = sim[j] = cim[j] = 0.f;
+    const uint32_t begin = (uint32_t)blockIdx.x * (uint32_t)chunk;
+    uint32_t end = begin + (uint32_t)chunk;
+    if (end > a.N) end = a.N;
+    const uint4 *rec = (const uint4 *)a.rec;
+    for (uint32_t base = begin; base < end; base += kRhoTile) {
+        const int tn = (int)min((uint32_t)kRhoTile, end - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < tn; t += blockDim.x) sp[t] = rec[base + t];
+        __syncthreads();
+        if (!active) continue;
+        float tre[ML], tim[ML];
+#pragma unroll
+        for (int j = 0; j < ML; ++j) tre[j] = tim[j] = 0.f;
+        for (int i = sub; i < tn; i += nsub) {
+            const uint4 r = sp[i];
+            const float q = __uint_as_float(r.w);
+#pragma unroll
+            for (int j = 0; j < ML; ++j) {
+                const uint32_t th = (uint32_t)mm[j][0] * r.x + (uint32_t)mm[j][1] * r.y + (uint32_t)mm[j][2] * r.z;
+                const float f = (float)(int)th * kTwoPiOver2p32;
+                float sn, cs;
+                __sincosf(f, &sn, &cs);
+                tre[j] = fmaf(q, cs, tre[j]);
+                tim[j] = fmaf(q, sn, tim[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < ML; ++j) {
+            kahan_add(sre[j], cre[j], tre[j]);
+            kahan_add(sim[j], cim[j], tim[j]);
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int j = 0; j < ML; ++j)
+        if (lidx[j] < a.P)
+            a.partial[((size_t)blockIdx.x * 8 + sub) * a.P + lidx[j]] =
+                make_double2((double)sre[j] - (double)cre[j], (double)sim[j] - (double)cim[j]);
+}
+
+__global__ void __launch_bounds__(kRhoThreads) k_rho64(RhoArgs a, int chunk) {
+    __shared__ Rec64 sp[kRhoTile / 2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pass_base = blockIdx.y * 256;
+    int ngroups, nsub;
+    rho_split(a.P, pass_base, 1, ngroups, nsub);
+    const int g = warp % ngroups, sub = warp / ngroups;
+    const bool active = sub < nsub;
+    const int l = pass_base + g * 32 + lane;
+    const bool ok = active && l < a.P;
+    const unsigned long long m0 = (unsigned long long)(long long)(ok ? a.m[3 * l] : 0);
+    const unsigned long long m1 = (unsigned long long)(long long)(ok ? a.m[3 * l + 1] : 0);
+    const unsigned long long m2 = (unsigned long long)(long long)(ok ? a.m[3 * l + 2] : 0);
+    double re = 0.0, im = 0.0;
+    const uint32_t begin = (uint32_t)blockIdx.x * (uint32_t)chunk;
+    uint32_t end = begin + (uint32_t)chunk;
+    if (end > a.N) end = a.N;
+    const Rec64 *rec = (const Rec64 *)a.rec;
+    for (uint32_t base = begin; base < end; base += kRhoTile / 2) {
+        const int tn = (int)min((uint32_t)(kRhoTile / 2), end - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < tn; t += blockDim.x) sp[t] = rec[base + t];
+        __syncthreads();
+        if (!active) continue;
+        for (int i = sub; i < tn; i += nsub) {
+            const Rec64 r = sp[i];
+            const unsigned long long th = m0 * r.s[0] + m1 * r.s[1] + m2 * r.s[2];
+            const double f = (double)(long long)th * 5.421010862427522e-20;   // 2^-64
+            double sn, cs;
+            sincospi(2.0 * f, &sn, &cs);
+            re += r.q * cs;
+            im += r.q * sn;
+        }
+    }
+    if (ok) a.partial[((size_t)blockIdx.x * 8 + sub) * a.P + l] = make_double2(re, im);
+}
+
+// ------------------------------------------------------------------ final reduction
+struct GTab32 {
+    int4 m;      // m_x, m_y, m_z, Im(rho) as float bits
+    float4 f;    // coef k_x, coef k_y, coef k_z, Re(rho)
+};
+struct GTab64 {
+    int4 m;
+    double ck[3];
+    double re, im;
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(1024) k_rho_final(RhoFinalArgs a, int ML) {
+    __shared__ double sh[1024];
+    double u = 0.0;
+    for (int l = threadIdx.x; l < a.P; l += blockDim.x) {
+        const int pass_base = (l / (256 * ML)) * 256 * ML;
+        int left = a.P - pass_base;
+        int ngroups = (left + 32 * ML - 1) / (32 * ML);
+        if (ngroups > 8) ngroups = 8;
+        const int nsub = 8 / ngroups;
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < a.G; ++b)
+            for (int s = 0; s < nsub; ++s) {
+                const double2 v = a.partial[((size_t)b * 8 + s) * a.P + l];
+                re += v.x;
+                im += v.y;
+            }
+        a.rho[l] = make_double2(re, im);
+        const double coef = a.coef[l];
+        u += 0.5 * coef * (re * re + im * im);
+        const int mx = a.m[3 * l], my = a.m[3 * l + 1], mz = a.m[3 * l + 2];
+        const double kx = a.tpl[0] * mx, ky = a.tpl[1] * my, kz = a.tpl[2] * mz;
+        if (PREC == 1) {
+            GTab32 t;
+            t.m = make_int4(mx, my, mz, __float_as_int((float)im));
+            t.f = make_float4((float)(coef * kx), (float)(coef * ky), (float)(coef * kz), (float)re);
+            ((GTab32 *)a.gtab)[l] = t;
+        } else {
+            GTab64 t;
+            t.m = make_int4(mx, my, mz, 0);
+            t.ck[0] = coef * kx; t.ck[1] = coef * ky; t.ck[2] = coef * kz;
+            t.re = re; t.im = im;
+            ((GTab64 *)a.gtab)[l] = t;
+        }
+    }
+    double tot = block_reduce_sum<double>(u, sh);
+    if (threadIdx.x == 0) {
+        *a.Ufar = tot;
+        a.ctr->draw += 1ull;
+        a.ctr->inject = 0;
+    }
+}
+
+// ------------------------------------------------------------------ far gather + kick
+template <int PREC>
+__global__ void __launch_bounds__(kFarThreads) k_far(FarArgs a) {
+    __shared__ double shK[kFarThreads];
+    __shared__ __align__(16) unsigned char smem_raw[kFarTile * sizeof(GTab32)];
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < a.N;
+    double Ff[3] = {0.0, 0.0, 0.0};
+    if (PREC == 1) {
+        GTab32 *tab = (GTab32 *)smem_raw;
+        const uint4 ri = valid ? ((const uint4 *)a.rec)[p] : make_uint4(0, 0, 0, 0);
+        float S[3] = {0.f, 0.f, 0.f}, C[3] = {0.f, 0.f, 0.f};
+        for (int base = 0; base < a.P; base += kFarTile) {
+            const int tn = min(kFarTile, a.P - base);
+            __syncthreads();
+            for (int t = threadIdx.x; t < tn; t += blockDim.x) tab[t] = ((const GTab32 *)a.gtab)[base + t];
+            __syncthreads();
+            for (int l0 = 0; l0 < tn; l0 += 32) {
+                const int l1 = min(tn, l0 + 32);
+                float acc[3] = {0.f, 0.f, 0.f};
+                for (int l = l0; l < l1; ++l) {
+                    const GTab32 t = tab[l];
+                    const uint32_t th = (uint32_t)t.m.x * ri.x + (uint32_t)t.m.y * ri.y + (uint32_t)t.m.z * ri.z;
+                    const float f = (float)(int)th * kTwoPiOver2p32;
+                    float sn, cs;
+                    __sincosf(f, &sn, &cs);
+                    const float gv = cs * __int_as_float(t.m.w) - sn * t.f.w;
+                    acc[0] = fmaf(t.f.x, gv, acc[0]);
+                    acc[1] = fmaf(t.f.y, gv, acc[1]);
+                    acc[2] = fmaf(t.f.z, gv, acc[2]);
+                }
+#pragma unroll
+                for (int d = 0; d < 3; ++d) kahan_add(S[d], C[d], acc[d]);
+            }
+        }
+        const float qi = __uint_as_float(ri.w);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Ff[d] = -(double)qi * ((double)S[d] - (double)C[d]);
+    } else {
+        GTab64 *tab = (GTab64 *)smem_raw;
+        const int tile = (int)(sizeof(smem_raw) / sizeof(GTab64));
+        Rec64 ri;
+        if (valid) ri = ((const Rec64 *)a.rec)[p];
+        else { ri.s[0] = ri.s[1] = ri.s[2] = 0ull; ri.q = 0.0; }
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int base = 0; base < a.P; base += tile) {
+            const int tn = min(tile, a.P - base);
+            __syncthreads();
+            for (int t = threadIdx.x; t < tn; t += blockDim.x) tab[t] = ((const GTab64 *)a.gtab)[base + t];
+            __syncthreads();
+            for (int l = 0; l < tn; ++l) {
+                const GTab64 t = tab[l];
+                const unsigned long long th = (unsigned long long)(long long)t.m.x * ri.s[0] +
+                                              (unsigned long long)(long long)t.m.y * ri.s[1] +
+                                              (unsigned long long)(long long)t.m.z * ri.s[2];
+                const double f = (double)(long long)th * 5.421010862427522e-20;
+                double sn, cs;
+                sincospi(2.0 * f, &sn, &cs);
+                const double gv = cs * t.im - sn * t.re;
+                acc[0] += t.ck[0] * gv;
+                acc[1] += t.ck[1] * gv;
+                acc[2] += t.ck[2] * gv;
+            }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Ff[d] = -ri.q * acc[d];
+    }
+    double K = 0.0;
+    if (valid) {
+        const uint32_t N = a.N;
+        double Fn[3], Ft[3];
+        if (PREC == 1) {
+            const float *fn = (const float *)a.Fn;
+            Fn[0] = fn[p]; Fn[1] = fn[N + p]; Fn[2] = fn[2 * (size_t)N + p];
+        } else {
+            const double *fn = (const double *)a.Fn;
+            Fn[0] = fn[p]; Fn[1] = fn[N + p]; Fn[2] = fn[2 * (size_t)N + p];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Ft[d] = Fn[d] + Ff[d];
+        if (PREC == 1) {
+            float *F = (float *)a.F;
+            F[p] = (float)Ft[0]; F[N + p] = (float)Ft[1]; F[2 * (size_t)N + p] = (float)Ft[2];
+        } else {
+            double *F = (double *)a.F;
+            F[p] = Ft[0]; F[N + p] = Ft[1]; F[2 * (size_t)N + p] = Ft[2];
+        }
+        double v[3] = {a.st.vx[p], a.st.vy[p], a.st.vz[p]};
+        const double invm = a.st.invm[p];
+        if (a.integrate) {
+            const double hk = 0.5 * a.dt * invm;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) v[d] += hk * Ft[d];
+            a.st.vx[p] = v[0]; a.st.vy[p] = v[1]; a.st.vz[p] = v[2];
+        }
+        K = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm;
+        const size_t u = 3 * (size_t)a.st.id[p];
+        if (a.F_user) { a.F_user[u] = Ft[0]; a.F_user[u + 1] = Ft[1]; a.F_user[u + 2] = Ft[2]; }
+        if (a.Fn_user) { a.Fn_user[u] = Fn[0]; a.Fn_user[u + 1] = Fn[1]; a.Fn_user[u + 2] = Fn[2]; }
+        if (a.Ff_user) { a.Ff_user[u] = Ff[0]; a.Ff_user[u + 1] = Ff[1]; a.Ff_user[u + 2] = Ff[2]; }
+    }
+    double tot = block_reduce_sum<double>(K, shK);
+    if (threadIdx.x == 0) a.K_part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_energy(EnergyArgs a) {
+    __shared__ double sh[1024];
+    double u = 0.0, k = 0.0;
+    // fixed-order per-thread strides, then a fixed tree
+    for (int i = threadIdx.x; i < a.nU; i += blockDim.x) u += a.U_part[i];
+    double U = block_reduce_sum<double>(u, sh);
+    for (int i = threadIdx.x; i < a.nK; i += blockDim.x) k += a.K_part[i];
+    double K = block_reduce_sum<double>(k, sh);
+    if (threadIdx.x == 0) {
+        const double Uf = *a.Ufar + a.Ufar0;
+        a.out[0] = U;
+        a.out[1] = Uf;
+        a.out[2] = a.Uself;
+        a.out[3] = K;
+        a.out[4] = U + Uf + a.Uself + K;
+        if (a.advance_step) a.ctr->step += 1ull;
+    }
+}
+
+inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+int rho_ml(int P) { return P <= 256 ? 1 : (P <= 512 ? 2 : 4); }
+
+}  // namespace
+
+int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
+    unsigned nb = blocks_for(a.N, kNearThreads);
+    if (prec == 1) k_near<1><<<nb, kNearThreads, 0, st>>>(a);
+    else k_near<0><<<nb, kNearThreads, 0, st>>>(a);
+    return (int)nb;
+}
+
+int rho_blocks(int prec, uint32_t N, int P) {
+    (void)prec; (void)P;
+    int G = 152 * 4;
+    int byN = (int)((N + 63) / 64);
+    return G < byN ? G : (byN > 0 ? byN : 1);
+}
+
+void launch_rho(int prec, const RhoArgs &a, cudaStream_t st) {
+    const int chunk = (int)((a.N + (uint32_t)a.G - 1) / (uint32_t)a.G);
+    if (prec == 1) {
+        const int ML = rho_ml(a.P);
+        dim3 grid(a.G, (a.P + 256 * ML - 1) / (256 * ML));
+        if (ML == 1) k_rho32<1><<<grid, kRhoThreads, 0, st>>>(a, chunk);
+        else if (ML == 2) k_rho32<2><<<grid, kRhoThreads, 0, st>>>(a, chunk);
+        else k_rho32<4><<<grid, kRhoThreads, 0, st>>>(a, chunk);
+    } else {
+        dim3 grid(a.G, (a.P + 255) / 256);
+        k_rho64<<<grid, kRhoThreads, 0, st>>>(a, chunk);
+    }
+}
+
+void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st) {
+    if (prec == 1) k_rho_final<1><<<1, 1024, 0, st>>>(a, rho_ml(a.P));
+    else k_rho_final<0><<<1, 1024, 0, st>>>(a, 1);
+}
+
+int launch_far(int prec, const FarArgs &a, cudaStream_t st) {
+    unsigned nb = blocks_for(a.N, kFarThreads);
+    if (prec == 1) k_far<1><<<nb, kFarThreads, 0, st>>>(a);
+    else k_far<0><<<nb, kFarThreads, 0, st>>>(a);
+    return (int)nb;
+}
+
+void launch_energy(const EnergyArgs &a, cudaStream_t st) { k_energy<<<1, 1024, 0, st>>>(a); }
+
+}  // namespace rbsog

@@ -1,0 +1,112 @@
+// Importance sampling of Fourier modes from P(k) = calF(k) Fhat(k) / S (Eq. 59),
+// and the normalisation S = sum_{k != 0} calF(k) Fhat(k).
+//
+// Fhat is a sum of Gaussians (Eq. 54) that factorises per axis, so one attempt is:
+//   Gaussian index m      alias table, weights A_m prod_a theta_{m,a}
+//   n_a per axis          alias table of exp(-(2 pi n/L_a)^2 / (4 b_m)), |n| <= nmax_{m,a}
+//   reject n = 0; accept with probability calF(k)/sum q^2 (calF of Eq. 62 is
+//   increasing in |k| with supremum sum q^2)
+// which yields i.i.d. draws from P(k).  Random words: Philox4x32-10, key = seed,
+// counter = (slot, 8 attempt + j, draw lo, draw hi): j = 0 Gaussian, 1..3 axes,
+// 4 acceptance.  An alias draw from words (x0..x3) takes index floor((x0 2^32 + x1)
+// n / 2^64) and keeps it when u53(x2, x3) < prob, else takes the alias.
+#include "common.cuh"
+#include "kernels.h"
+#include "philox.cuh"
+
+namespace rbsog {
+
+namespace {
+
+__device__ __forceinline__ int alias_draw(U4 w, const double *prob, const int *alias, int n) {
+    unsigned long long u = ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
+    int i = (int)__umul64hi(u, (unsigned long long)n);
+    double t = u53_of(w.z, w.w);
+    return (t < prob[i]) ? i : alias[i];
+}
+
+__global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.P) return;
+    int m[3];
+    if (a.ctr->inject) {
+        m[0] = a.inject_m[3 * l]; m[1] = a.inject_m[3 * l + 1]; m[2] = a.inject_m[3 * l + 2];
+    } else {
+        const unsigned long long d = a.ctr->draw;
+        const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+        const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
+        bool done = false;
+        m[0] = 1; m[1] = 0; m[2] = 0;
+        for (int att = 0; att < kMaxAttempts && !done; ++att) {
+            const uint32_t cb = 8u * (uint32_t)att;
+            int g = alias_draw(philox10((uint32_t)l, cb, d0, d1, k0, k1), a.tab.mix_prob, a.tab.mix_alias, a.tab.mtot);
+            int n[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const int off = a.tab.ax_off[3 * g + ax], nm = a.tab.ax_nmax[3 * g + ax];
+                n[ax] = alias_draw(philox10((uint32_t)l, cb + 1u + ax, d0, d1, k0, k1), a.tab.ax_prob + off,
+                                   a.tab.ax_alias + off, 2 * nm + 1) - nm;
+            }
+            if (n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+            U4 wa = philox10((uint32_t)l, cb + 4u, d0, d1, k0, k1);
+            double u = u53_of(wa.x, wa.y);
+            double kx = __dmul_rn(a.tpl[0], (double)n[0]);
+            double ky = __dmul_rn(a.tpl[1], (double)n[1]);
+            double kz = __dmul_rn(a.tpl[2], (double)n[2]);
+            double k2 = __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
+            double g2 = __ddiv_rn(1.0, __dadd_rn(k2, a.inv_lam2));
+            double ratio = __ddiv_rn(a.A, __dadd_rn(a.A, __dmul_rn(a.Q2, g2)));
+            if (u < ratio) {
+                m[0] = n[0]; m[1] = n[1]; m[2] = n[2];
+                done = true;
+            }
+        }
+        if (!done) atomicOr(&a.ctr->err, kErrSampler);
+    }
+    a.m_out[3 * l] = m[0]; a.m_out[3 * l + 1] = m[1]; a.m_out[3 * l + 2] = m[2];
+    // coef = S / (P V calF(k)),  calF = kT V / (kT V / Q2 + 1/(k^2 + lambda^-2))   (Eqs. 60, 62)
+    double kx = a.tpl[0] * m[0], ky = a.tpl[1] * m[1], kz = a.tpl[2] * m[2];
+    double k2 = kx * kx + ky * ky + kz * kz;
+    double calF = a.A / (a.A / a.Q2 + 1.0 / (k2 + a.inv_lam2));
+    a.coef_out[l] = a.S / ((double)a.P * a.V * calF);
+}
+
+// S over the ball |k|^2 <= kmax2: block x = m_x slab; fixed-order reduction.
+__global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
+    __shared__ double sh[256];
+    const int mx = (int)blockIdx.x - a.nmax[0];
+    const double kx = a.tpl[0] * mx;
+    const int ny = 2 * a.nmax[1] + 1, nz = 2 * a.nmax[2] + 1;
+    double acc = 0.0;
+    for (long long t = threadIdx.x; t < (long long)ny * nz; t += blockDim.x) {
+        const int my = (int)(t / nz) - a.nmax[1];
+        const int mz = (int)(t % nz) - a.nmax[2];
+        if (mx == 0 && my == 0 && mz == 0) continue;
+        const double ky = a.tpl[1] * my, kz = a.tpl[2] * mz;
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 > a.kmax2) continue;
+        double fh = 0.0;
+        for (int g = 0; g < a.mtot; ++g) fh += a.A[g] * exp(-k2 * a.inv4b[g]);
+        const double calF = a.kTV / (a.kTV / a.Q2 + 1.0 / (k2 + a.inv_lam2));
+        acc += calF * fh;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+}  // namespace
+
+void launch_sample(const SampleArgs &a, cudaStream_t st) {
+    k_sample<<<(a.P + 127) / 128, 128, 0, st>>>(a);
+}
+
+void launch_S(const SArgs &a, double *partials, cudaStream_t st) {
+    k_S<<<2 * a.nmax[0] + 1, 256, 0, st>>>(a, partials);
+}
+
+}  // namespace rbsog

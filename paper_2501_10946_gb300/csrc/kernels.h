@@ -1,0 +1,137 @@
+// Launchers of the RBSOG kernels (internal to the library).
+#pragma once
+
+#include "common.cuh"
+
+namespace rbsog {
+
+// ---- cell list and integrator, first half (k_cells.cu) ----
+struct BinArgs {
+    State in;                 // rest buffer (cell-sorted order of the last build)
+    State out;                // work buffer, same index k
+    const void *F;            // forces of the rest order, SoA [3][N]: float (FP32) or double (FP64)
+    int integrate;            // 0 none, 1 velocity Verlet (kick + drift), 2 BAOAB (B A O A)
+    double dt, c1, kT;
+    unsigned long long seed;
+    DevCounters *ctr;
+    uint32_t N;
+    Box box;
+    void *s;                  // fixed point [3][N]: uint32 (FP32) or uint64 (FP64)
+    uint32_t *cell, *slot, *count;
+};
+void launch_bin(int prec, const BinArgs &a, cudaStream_t st);
+void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int ncell, uint32_t N,
+                 cudaStream_t st);
+void launch_scatter_sort(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
+                         uint32_t N, int ncell, unsigned long long *keys, uint32_t *perm_src, DevCounters *ctr,
+                         cudaStream_t st);
+struct GatherArgs {
+    State in;                 // work buffer
+    State out;                // rest buffer (new cell-sorted order)
+    const uint32_t *perm_src;
+    const void *s;            // fixed point of the work order
+    void *rec;                // uint4 (FP32) or Rec64 (FP64) records in the new order
+    uint32_t N;
+};
+void launch_gather(int prec, const GatherArgs &g, cudaStream_t st);
+void launch_set_state(const double *r, const double *v, const double *q_user, const double *m_user, State rest,
+                      uint32_t N, Box box, DevCounters *ctr, cudaStream_t st);
+void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st);
+
+// ---- sampler and normalisation (k_sample.cu) ----
+struct SamplerTables {
+    int mtot;
+    const double *mix_prob; const int *mix_alias;     // [mtot]
+    const int *ax_off;        // [mtot*3] offset into ax_prob/ax_alias
+    const int *ax_nmax;       // [mtot*3]
+    const double *ax_prob; const int *ax_alias;
+};
+struct SampleArgs {
+    SamplerTables tab;
+    int P;
+    unsigned long long seed;
+    double tpl[3];            // 2 pi / L
+    double A;                 // k_B T V
+    double Q2;                // sum q^2
+    double inv_lam2;
+    double S, V;
+    DevCounters *ctr;
+    const int *inject_m;      // [P*3]
+    int *m_out;               // [P*3]
+    double *coef_out;         // [P]
+};
+void launch_sample(const SampleArgs &a, cudaStream_t st);
+struct SArgs {
+    int mtot;
+    double A[kMaxGauss], inv4b[kMaxGauss];   // Fhat(k) = sum_m A_m exp(-k^2 inv4b_m)
+    double tpl[3];
+    double kmax2;
+    int nmax[3];
+    double kTV, Q2, inv_lam2;
+};
+void launch_S(const SArgs &a, double *partials, cudaStream_t st);   // partials[2*nmax[0]+1]
+
+// ---- forces (k_forces.cu) ----
+struct NearArgs {
+    NearConsts nc;
+    const void *rec;
+    const uint32_t *cell_start;
+    Box box;
+    uint32_t N;
+    void *Fn;                  // near force SoA [3][N] (float or double)
+    double *U_part;            // per-block near energy
+    const DevCounters *ctr;    // skip the pair loops when the cell build overflowed
+};
+int launch_near(int prec, const NearArgs &a, cudaStream_t st);   // returns #blocks (energy partials)
+struct RhoArgs {
+    const void *rec;
+    uint32_t N;
+    const int *m;              // [P*3]
+    int P;
+    double2 *partial;          // [G][P]
+    int G;
+};
+int rho_blocks(int prec, uint32_t N, int P);
+void launch_rho(int prec, const RhoArgs &a, cudaStream_t st);
+struct RhoFinalArgs {
+    const double2 *partial;
+    int G, P;
+    const int *m;
+    const double *coef;
+    double tpl[3];
+    double2 *rho;              // [P]
+    void *gtab;                // gather table: float (FP32) / double (FP64), [P] x {ckx,cky,ckz,Re,Im} + int m
+    double *Ufar;              // scalar: sum coef |rho|^2 / 2
+    DevCounters *ctr;
+};
+void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st);
+struct FarArgs {
+    const void *rec;
+    uint32_t N;
+    int P;
+    const void *gtab;
+    const int *m;
+    const void *Fn;            // near force (SoA)
+    void *F;                   // total force out (SoA, same precision)
+    State st;                  // rest state (velocities updated when integrate)
+    int integrate;
+    double dt;
+    double *K_part;            // per-block kinetic energy
+    double *F_user;            // optional [N][3] total force in caller order
+    double *Fn_user;           // optional near part
+    double *Ff_user;           // optional far part
+};
+int launch_far(int prec, const FarArgs &a, cudaStream_t st);     // returns #blocks
+struct EnergyArgs {
+    const double *U_part; int nU;
+    const double *K_part; int nK;
+    const double *Ufar;
+    double Ufar0;              // k = 0 term
+    double Uself;
+    double *out;               // [5]: U_near, U_far, U_self, K, total
+    DevCounters *ctr;
+    int advance_step;
+};
+void launch_energy(const EnergyArgs &a, cudaStream_t st);
+
+}  // namespace rbsog

@@ -1,0 +1,688 @@
+// C ABI of the RBSOG force step on GB300: context, initialisation and the step sequence.
+//
+// One force evaluation (Algorithm 2, steps "draw", "far force", "near force"):
+//   bin -> scan -> scatter/sort -> gather      cell list in cell-sorted order
+//   sample                                     P modes from P(k) (Eq. 59)
+//   near                                       Eq. (55) first term
+//   rho -> rho_final                           rho(k_l), U*_F (Eq. 60)
+//   far (+ closing half kick)                  Eq. (60) force, total force
+//   energy                                     Eq. (49) terms and kinetic energy
+// rbsog_step captures this sequence once as a CUDA graph (with the opening half kick
+// and drift fused into "bin") and replays it.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rbsog.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "sog_host.h"
+
+using namespace rbsog;
+
+struct rbsog_ctx {
+    rbsog_params p{};
+    uint32_t N = 0;
+    int prec = 1;
+    std::string err;
+    SogDecomp sog;
+    double lam = 0, kT = 0, a_ws = 0, V = 0, Q2 = 0, qsum = 0, S = 0, Ufar0 = 0, Uself = 0, Fhat0 = 0;
+    Box box{};
+    NearConsts nconsts{};
+    std::vector<double> sA, sb;   // Fhat coefficients A_m and b_m = e^{t_m}
+    // device buffers
+    State rest{}, work{};
+    double *q_user = nullptr, *m_user = nullptr;
+    double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;
+    void *F = nullptr, *Fn = nullptr, *s = nullptr, *rec = nullptr;
+    uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr,
+             *perm_src = nullptr;
+    unsigned long long *keys = nullptr;
+    double *mix_prob = nullptr, *ax_prob = nullptr;
+    int *mix_alias = nullptr, *ax_off = nullptr, *ax_nmax = nullptr, *ax_alias = nullptr;
+    int *modes = nullptr, *inject_m = nullptr;
+    double *coef = nullptr;
+    double2 *partial = nullptr, *rho = nullptr;
+    void *gtab = nullptr;
+    double *Ufar = nullptr, *U_part = nullptr, *K_part = nullptr, *energy = nullptr;
+    int G = 0, nU = 0, nK = 0;
+    DevCounters *ctr = nullptr;
+    std::vector<void *> allocs;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool force_valid = false;
+    SamplerTables tab{};
+    // profiling: events around each kernel group of eager force evaluations
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, std::pair<size_t, size_t>>> prof_spans;   // (group, (start ev, end ev))
+};
+
+static std::string g_init_error;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+int fail(rbsog_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(rbsog_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? RBSOG_ENOMEM : RBSOG_ECUDA, m);
+}
+
+#define CK(call, where)                                    \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(rbsog_ctx *c, T **ptr, size_t count) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e == cudaSuccess) {
+        c->allocs.push_back(p);
+        *ptr = (T *)p;
+    }
+    return e;
+}
+
+bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Vose's alias method, both work lists used as stacks filled in ascending index order.
+void vose(const std::vector<double> &w, std::vector<double> *prob, std::vector<int> *alias) {
+    const int n = (int)w.size();
+    double total = 0.0;
+    for (double x : w) total += x;
+    std::vector<double> sc(n);
+    for (int i = 0; i < n; ++i) sc[i] = (w[i] * n) / total;
+    prob->assign(n, 0.0);
+    alias->resize(n);
+    for (int i = 0; i < n; ++i) (*alias)[i] = i;
+    std::vector<int> small, large;
+    for (int i = 0; i < n; ++i) (sc[i] < 1.0 ? small : large).push_back(i);
+    while (!small.empty() && !large.empty()) {
+        int lo = small.back(); small.pop_back();
+        int g = large.back(); large.pop_back();
+        (*prob)[lo] = sc[lo];
+        (*alias)[lo] = g;
+        sc[g] = (sc[g] + sc[lo]) - 1.0;
+        (sc[g] < 1.0 ? small : large).push_back(g);
+    }
+    while (!large.empty()) { (*prob)[large.back()] = 1.0; large.pop_back(); }
+    while (!small.empty()) { (*prob)[small.back()] = 1.0; small.pop_back(); }
+}
+
+int build_sampler(rbsog_ctx *c) {
+    const double LN_1E18 = 41.44653167389282;
+    const int mt = c->sog.mtot();
+    std::vector<double> mixw(mt), axp;
+    std::vector<int> axa, off(3 * mt), nmax(3 * mt);
+    for (int i = 0; i < mt; ++i) {
+        const double b = c->sb[i];
+        double prod = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            const int nm = (int)std::ceil(std::sqrt(4.0 * b * LN_1E18) / c->box.tpl[a]);
+            std::vector<double> g(2 * nm + 1);
+            double theta = 0.0;
+            for (int n = -nm; n <= nm; ++n) {
+                const double kk = c->box.tpl[a] * n;
+                g[n + nm] = std::exp(-(kk * kk) / (4.0 * b));
+            }
+            for (double x : g) theta += x;
+            std::vector<double> pr;
+            std::vector<int> al;
+            vose(g, &pr, &al);
+            off[3 * i + a] = (int)axp.size();
+            nmax[3 * i + a] = nm;
+            axp.insert(axp.end(), pr.begin(), pr.end());
+            axa.insert(axa.end(), al.begin(), al.end());
+            prod = prod * theta;
+        }
+        mixw[i] = c->sA[i] * prod;
+    }
+    std::vector<double> mp;
+    std::vector<int> ma;
+    vose(mixw, &mp, &ma);
+    CK(dalloc(c, &c->mix_prob, mt), "alloc sampler");
+    CK(dalloc(c, &c->mix_alias, mt), "alloc sampler");
+    CK(dalloc(c, &c->ax_off, 3 * mt), "alloc sampler");
+    CK(dalloc(c, &c->ax_nmax, 3 * mt), "alloc sampler");
+    CK(dalloc(c, &c->ax_prob, axp.size()), "alloc sampler");
+    CK(dalloc(c, &c->ax_alias, axa.size()), "alloc sampler");
+    CK(cudaMemcpy(c->mix_prob, mp.data(), mt * sizeof(double), cudaMemcpyHostToDevice), "upload sampler");
+    CK(cudaMemcpy(c->mix_alias, ma.data(), mt * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
+    CK(cudaMemcpy(c->ax_off, off.data(), 3 * mt * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
+    CK(cudaMemcpy(c->ax_nmax, nmax.data(), 3 * mt * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
+    CK(cudaMemcpy(c->ax_prob, axp.data(), axp.size() * sizeof(double), cudaMemcpyHostToDevice), "upload sampler");
+    CK(cudaMemcpy(c->ax_alias, axa.data(), axa.size() * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
+    c->tab = SamplerTables{mt, c->mix_prob, c->mix_alias, c->ax_off, c->ax_nmax, c->ax_prob, c->ax_alias};
+    return RBSOG_OK;
+}
+
+int compute_S(rbsog_ctx *c) {
+    SArgs a{};
+    a.mtot = c->sog.mtot();
+    double bmax = 0.0;
+    for (int i = 0; i < a.mtot; ++i) {
+        a.A[i] = c->sA[i];
+        a.inv4b[i] = 1.0 / (4.0 * c->sb[i]);
+        if (c->sb[i] > bmax) bmax = c->sb[i];
+    }
+    a.kmax2 = 4.0 * bmax * std::log(1e17);
+    for (int d = 0; d < 3; ++d) {
+        a.tpl[d] = c->box.tpl[d];
+        a.nmax[d] = (int)std::floor(std::sqrt(a.kmax2) / c->box.tpl[d]) + 1;
+    }
+    a.kTV = c->kT * c->V;
+    a.Q2 = c->Q2;
+    a.inv_lam2 = 1.0 / (c->lam * c->lam);
+    const int nb = 2 * a.nmax[0] + 1;
+    double *parts = nullptr;
+    CK(cudaMalloc(&parts, nb * sizeof(double)), "alloc S");
+    launch_S(a, parts, 0);
+    std::vector<double> h(nb);
+    cudaError_t e = cudaMemcpy(h.data(), parts, nb * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(parts);
+    CK(e, "S kernel");
+    double S = 0.0;
+    for (double x : h) S += x;
+    c->S = S;
+    return RBSOG_OK;
+}
+
+const char *kProfNames[RBSOG_NPROF] = {"bin", "scan", "sort", "gather", "sample", "near", "rho", "rho_final",
+                                       "far", "energy"};
+
+// Record a profiling boundary on st (no-op unless profiling); returns the event index.
+size_t prof_mark(rbsog_ctx *c, cudaStream_t st) {
+    if (!c->prof) return 0;
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return 0;
+        c->ev_pool.push_back(e);
+    }
+    cudaEventRecord(c->ev_pool[c->ev_used], st);
+    return c->ev_used++;
+}
+
+struct ProfScope {
+    rbsog_ctx *c;
+    cudaStream_t st;
+    int group;
+    size_t e0;
+    ProfScope(rbsog_ctx *c_, cudaStream_t st_, int g) : c(c_), st(st_), group(g), e0(prof_mark(c_, st_)) {}
+    ~ProfScope() {
+        if (c->prof) c->prof_spans.push_back({group, {e0, prof_mark(c, st)}});
+    }
+};
+
+// Enqueue one force evaluation (and, with integrate != 0, one full step).
+int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double *Fn_user, double *Ff_user,
+            int advance) {
+    const int prec = c->prec;
+    const uint32_t N = c->N;
+    BinArgs b{};
+    b.in = c->rest; b.out = c->work; b.F = c->F; b.integrate = integrate;
+    b.dt = c->p.dt; b.c1 = std::exp(-c->p.langevin_gamma * c->p.dt); b.kT = c->kT; b.seed = c->p.seed;
+    b.ctr = c->ctr; b.N = N; b.box = c->box; b.s = c->s; b.cell = c->cell; b.slot = c->slot; b.count = c->count;
+    { ProfScope ps(c, st, 0); launch_bin(prec, b, st); }
+    { ProfScope ps(c, st, 1); launch_scan(c->count, c->tile_sums, c->cell_start, c->box.ncell, N, st); }
+    {
+        ProfScope ps(c, st, 2);
+        launch_scatter_sort(c->cell, c->slot, c->cell_start, c->work.id, N, c->box.ncell, c->keys, c->perm_src,
+                            c->ctr, st);
+    }
+    GatherArgs g{};
+    g.in = c->work; g.out = c->rest; g.perm_src = c->perm_src; g.s = c->s; g.rec = c->rec; g.N = N;
+    { ProfScope ps(c, st, 3); launch_gather(prec, g, st); }
+    SampleArgs sa{};
+    sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
+    for (int d = 0; d < 3; ++d) sa.tpl[d] = c->box.tpl[d];
+    sa.A = c->kT * c->V; sa.Q2 = c->Q2; sa.inv_lam2 = 1.0 / (c->lam * c->lam); sa.S = c->S; sa.V = c->V;
+    sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
+    { ProfScope ps(c, st, 4); launch_sample(sa, st); }
+    NearArgs na{};
+    na.nc = c->nconsts; na.rec = c->rec; na.cell_start = c->cell_start; na.box = c->box; na.N = N; na.Fn = c->Fn;
+    na.U_part = c->U_part;
+    na.ctr = c->ctr;
+    { ProfScope ps(c, st, 5); c->nU = launch_near(prec, na, st); }
+    RhoArgs ra{};
+    ra.rec = c->rec; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
+    { ProfScope ps(c, st, 6); launch_rho(prec, ra, st); }
+    RhoFinalArgs rf{};
+    rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
+    for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
+    rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
+    { ProfScope ps(c, st, 7); launch_rho_final(prec, rf, st); }
+    FarArgs fa{};
+    fa.rec = c->rec; fa.N = N; fa.P = c->p.P; fa.gtab = c->gtab; fa.m = c->modes; fa.Fn = c->Fn; fa.F = c->F;
+    fa.st = c->rest; fa.integrate = integrate ? 1 : 0; fa.dt = c->p.dt; fa.K_part = c->K_part;
+    fa.F_user = F_user; fa.Fn_user = Fn_user; fa.Ff_user = Ff_user;
+    { ProfScope ps(c, st, 8); c->nK = launch_far(prec, fa, st); }
+    EnergyArgs ea{};
+    ea.U_part = c->U_part; ea.nU = c->nU; ea.K_part = c->K_part; ea.nK = c->nK; ea.Ufar = c->Ufar;
+    ea.Ufar0 = c->Ufar0; ea.Uself = c->Uself; ea.out = c->energy; ea.ctr = c->ctr; ea.advance_step = advance;
+    { ProfScope ps(c, st, 9); launch_energy(ea, st); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return RBSOG_OK;
+}
+
+int check_device_errors(rbsog_ctx *c) {
+    DevCounters h;
+    CK(cudaMemcpy(&h, c->ctr, sizeof h, cudaMemcpyDeviceToHost), "read device status");
+    if (h.err & kErrCellOverflow) return fail(c, RBSOG_EOVERFLOW, "a cell holds more than 4096 particles");
+    if (h.err & kErrSampler) return fail(c, RBSOG_ETIMEOUT, "k-sampler exceeded its attempt limit");
+    return RBSOG_OK;
+}
+
+int read_energy(rbsog_ctx *c, rbsog_energy *e, cudaStream_t st) {
+    double h[5];
+    CK(cudaMemcpyAsync(h, c->energy, sizeof h, cudaMemcpyDeviceToHost, st), "read energy");
+    DevCounters hc;
+    CK(cudaMemcpyAsync(&hc, c->ctr, sizeof hc, cudaMemcpyDeviceToHost, st), "read counters");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    e->U_near = h[0]; e->U_far = h[1]; e->U_self = h[2]; e->kinetic = h[3]; e->total = h[4];
+    e->step = hc.step;
+    return check_device_errors(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, const double *m_host, rbsog_ctx **out) {
+    if (!out) return fail(nullptr, RBSOG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params || !q_host || !m_host) return fail(nullptr, RBSOG_EINVAL, "params, q or m is NULL");
+    const rbsog_params &p = *params;
+    if (N < 2 || N > 0x7fffffffLL) return fail(nullptr, RBSOG_EINVAL, "N must be in [2, 2^31)");
+    for (int d = 0; d < 3; ++d)
+        if (!(p.box[d] > 0)) return fail(nullptr, RBSOG_EINVAL, "box lengths must be > 0");
+    if (!(p.kappa > 0)) return fail(nullptr, RBSOG_EINVAL, "kappa must be > 0");
+    if (p.P < 1 || p.P > 4096) return fail(nullptr, RBSOG_EINVAL, "P must be in [1, 4096]");
+    if (p.precision != RBSOG_FP64 && p.precision != RBSOG_FP32) return fail(nullptr, RBSOG_EINVAL, "bad precision");
+    if (p.ensemble != RBSOG_NVE && p.ensemble != RBSOG_LANGEVIN) return fail(nullptr, RBSOG_EINVAL, "bad ensemble");
+    if (p.sog_mode < 0 || p.sog_mode > 2) return fail(nullptr, RBSOG_EINVAL, "bad sog_mode");
+    if (p.reserved != 0) return fail(nullptr, RBSOG_EINVAL, "reserved must be 0");
+    double Lmin = std::fmin(p.box[0], std::fmin(p.box[1], p.box[2]));
+    if (!(p.r_c > 0) || p.r_c > 0.5 * Lmin) return fail(nullptr, RBSOG_EINVAL, "need 0 < r_c <= min(L)/2");
+    if (!(p.dt >= 0)) return fail(nullptr, RBSOG_EINVAL, "dt must be >= 0");
+    for (int64_t i = 0; i < N; ++i)
+        if (!(m_host[i] > 0) || !std::isfinite(q_host[i])) return fail(nullptr, RBSOG_EINVAL, "masses must be > 0");
+
+    rbsog_ctx *c = new rbsog_ctx();
+    c->p = p;
+    c->N = (uint32_t)N;
+    c->prec = p.precision;
+    c->V = (p.box[0] * p.box[1]) * p.box[2];
+    c->a_ws = p.a_ws > 0 ? p.a_ws : std::cbrt(3.0 * c->V / (4.0 * kPi * (double)N));
+    c->lam = c->a_ws / p.kappa;
+    c->kT = p.kT > 0 ? p.kT : 1.0 / (c->a_ws * p.Gamma);
+    if (!(c->kT > 0) || !std::isfinite(c->kT)) {
+        delete c;
+        return fail(nullptr, RBSOG_EINVAL, "k_B T must be > 0 (Gamma > 0 or kT > 0)");
+    }
+    std::string err;
+    if (!build_sog(c->lam, p.r_c, p.sog_eps, p.sog_mode, p.sog_M1, p.sog_M2, &c->sog, &err)) {
+        delete c;
+        return fail(nullptr, RBSOG_ENOCONV, err);
+    }
+    const int mt = c->sog.mtot();
+    if (mt > kMaxGauss) {
+        delete c;
+        return fail(nullptr, RBSOG_EUNSUPPORTED, "more than 40 Gaussians");
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        c->Q2 += q_host[i] * q_host[i];
+        c->qsum += q_host[i];
+    }
+    if (!(c->Q2 > 0)) {
+        delete c;
+        return fail(nullptr, RBSOG_EINVAL, "all charges are zero");
+    }
+    // box and cells
+    Box &bx = c->box;
+    long long ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        bx.L[d] = p.box[d];
+        int n = (int)std::floor(p.box[d] / p.r_c);
+        bx.nc[d] = n >= 3 ? n : 1;
+        ncell *= bx.nc[d];
+        bx.L_2m32[d] = p.box[d] * 2.3283064365386963e-10;
+        bx.L_2m64[d] = p.box[d] * 5.421010862427522e-20;
+        bx.L_2m32f[d] = (float)bx.L_2m32[d];
+        bx.tpl[d] = 6.283185307179586 / p.box[d];
+    }
+    if (ncell > (1LL << 28)) {
+        delete c;
+        return fail(nullptr, RBSOG_EINVAL, "too many cells (box / r_c too large)");
+    }
+    bx.ncell = (int)ncell;
+    // SOG constants (Eqs. 37, 54, 56-57)
+    const double log2e = 1.4426950408889634;
+    NearConsts &nc = c->nconsts;
+    nc.mtot = mt;
+    nc.inv_lam = 1.0 / c->lam;
+    nc.rc2 = p.r_c * p.r_c;
+    nc.inv_lam_log2e_f = (float)(log2e / c->lam);
+    nc.inv_lam_f = (float)(1.0 / c->lam);
+    nc.rc2_f = (float)nc.rc2;
+    c->Fhat0 = 0.0;
+    double F0 = 0.0;
+    for (int i = 0; i < mt; ++i) {
+        const int m = -c->sog.M1 + i;
+        const double t = c->sog.t0 + m * c->sog.h;
+        const double w = (m == c->sog.M2) ? c->sog.w : 1.0;
+        const double b = std::exp(t);
+        const double f0 = sog_f(t, 0.0, c->lam);
+        const double a = c->sog.h * w * f0;
+        nc.a[i] = a;
+        nc.b[i] = b;
+        nc.c[i] = -2.0 * b * a;
+        nc.af[i] = (float)a;
+        nc.bl2f[i] = (float)(b * log2e);
+        nc.cf[i] = (float)(-2.0 * b * a);
+        const double A = c->sog.h * w * std::pow(kPi, 1.5) * f0 * std::exp(-1.5 * t);
+        c->sA.push_back(A);
+        c->sb.push_back(b);
+        c->Fhat0 += A;
+        F0 += a;
+    }
+    c->Uself = -0.5 * c->Q2 * F0;
+    c->Ufar0 = c->Fhat0 * c->qsum * c->qsum / (2.0 * c->V);
+
+    // device
+    int r = RBSOG_OK;
+    auto bail = [&](int code) {
+        rbsog_free(c);
+        return code;
+    };
+    if (cudaSetDevice(p.device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, RBSOG_ECUDA, "cudaSetDevice failed (no usable CUDA device)");
+    }
+    const size_t n = c->N, n3 = 3 * n;
+    const size_t real = c->prec == RBSOG_FP32 ? 4 : 8;
+    State *sts[2] = {&c->rest, &c->work};
+    for (State *s : sts) {
+        if (dalloc(c, &s->rx, n) || dalloc(c, &s->ry, n) || dalloc(c, &s->rz, n) || dalloc(c, &s->vx, n) ||
+            dalloc(c, &s->vy, n) || dalloc(c, &s->vz, n) || dalloc(c, &s->invm, n) || dalloc(c, &s->q, n) ||
+            dalloc(c, &s->id, n)) {
+            g_init_error = "device allocation failed (state)";
+            return bail(RBSOG_ENOMEM);
+        }
+    }
+    unsigned char *Fb = nullptr, *Fnb = nullptr, *sb = nullptr, *recb = nullptr;
+    const int ntiles = (bx.ncell + kScanTile - 1) / kScanTile;
+    c->G = rho_blocks(c->prec, c->N, p.P);
+    const size_t gtab_bytes = (size_t)p.P * 64;
+    if (dalloc(c, &c->q_user, n) || dalloc(c, &c->m_user, n) || dalloc(c, &c->stage_a, n3) ||
+        dalloc(c, &c->stage_b, n3) || dalloc(c, &c->stage_c, n3) || dalloc(c, &Fb, n3 * real) ||
+        dalloc(c, &Fnb, n3 * real) || dalloc(c, &sb, n3 * real) || dalloc(c, &recb, n * 4 * real) ||
+        dalloc(c, &c->cell, n) || dalloc(c, &c->slot, n) || dalloc(c, &c->count, (size_t)bx.ncell) ||
+        dalloc(c, &c->tile_sums, (size_t)ntiles) || dalloc(c, &c->cell_start, (size_t)bx.ncell + 1) ||
+        dalloc(c, &c->perm_src, n) || dalloc(c, &c->keys, n) || dalloc(c, &c->modes, 3 * (size_t)p.P) ||
+        dalloc(c, &c->inject_m, 3 * (size_t)p.P) || dalloc(c, &c->coef, (size_t)p.P) ||
+        dalloc(c, &c->partial, (size_t)c->G * 8 * p.P) || dalloc(c, &c->rho, (size_t)p.P) ||
+        dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, 1) ||
+        dalloc(c, &c->U_part, (n + 127) / 128 + 1) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
+        dalloc(c, &c->energy, 8) || dalloc(c, &c->ctr, 1)) {
+        g_init_error = "device allocation failed";
+        return bail(RBSOG_ENOMEM);
+    }
+    c->F = Fb; c->Fn = Fnb; c->s = sb; c->rec = recb;
+    if (cudaMemset(c->count, 0, sizeof(uint32_t) * bx.ncell) != cudaSuccess ||
+        cudaMemset(c->ctr, 0, sizeof(DevCounters)) != cudaSuccess ||
+        cudaMemcpy(c->q_user, q_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->m_user, m_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        g_init_error = "device initialisation failed";
+        return bail(RBSOG_ECUDA);
+    }
+    if ((r = build_sampler(c)) != RBSOG_OK) {
+        g_init_error = c->err;
+        return bail(r);
+    }
+    if ((r = compute_S(c)) != RBSOG_OK) {
+        g_init_error = c->err;
+        return bail(r);
+    }
+    // a valid (zero) state so every call is defined before rbsog_set_state
+    if (cudaMemset(c->stage_a, 0, n3 * sizeof(double)) != cudaSuccess) {
+        g_init_error = "device initialisation failed";
+        return bail(RBSOG_ECUDA);
+    }
+    launch_set_state(c->stage_a, nullptr, c->q_user, c->m_user, c->rest, c->N, c->box, c->ctr, 0);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        g_init_error = "device initialisation failed";
+        return bail(RBSOG_ECUDA);
+    }
+    *out = c;
+    return RBSOG_OK;
+}
+
+int rbsog_set_state(rbsog_ctx *c, const double *r, const double *v, void *stream) {
+    if (!c || !r) return fail(c, RBSOG_EINVAL, "ctx or r is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+    const double *rd = r, *vd = v;
+    if (!is_device_ptr(r)) {
+        CK(cudaMemcpyAsync(c->stage_a, r, bytes, cudaMemcpyDefault, st), "copy r");
+        rd = c->stage_a;
+    }
+    if (v && !is_device_ptr(v)) {
+        CK(cudaMemcpyAsync(c->stage_b, v, bytes, cudaMemcpyDefault, st), "copy v");
+        vd = c->stage_b;
+    }
+    launch_set_state(rd, vd, c->q_user, c->m_user, c->rest, c->N, c->box, c->ctr, st);
+    CK(cudaGetLastError(), "set_state");
+    c->force_valid = false;
+    return RBSOG_OK;
+}
+
+int rbsog_get_state(rbsog_ctx *c, double *r, double *v, uint64_t *step, void *stream) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+    launch_get_state(c->rest, c->N, r ? c->stage_a : nullptr, v ? c->stage_b : nullptr, st);
+    CK(cudaGetLastError(), "get_state");
+    if (r) CK(cudaMemcpyAsync(r, c->stage_a, bytes, cudaMemcpyDefault, st), "copy r out");
+    if (v) CK(cudaMemcpyAsync(v, c->stage_b, bytes, cudaMemcpyDefault, st), "copy v out");
+    DevCounters hc;
+    CK(cudaMemcpyAsync(&hc, c->ctr, sizeof hc, cudaMemcpyDeviceToHost, st), "read counters");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    if (step) *step = hc.step;
+    return check_device_errors(c);
+}
+
+static int forces_impl(rbsog_ctx *c, double *F, double *Fn, double *Ff, rbsog_energy *e, void *stream) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+    double *outs[3] = {F, Fn, Ff};
+    double *stage[3] = {c->stage_a, c->stage_b, c->stage_c};
+    double *dev[3] = {nullptr, nullptr, nullptr};
+    for (int i = 0; i < 3; ++i)
+        if (outs[i]) dev[i] = is_device_ptr(outs[i]) ? outs[i] : stage[i];
+    int r = enqueue(c, st, 0, dev[0], dev[1], dev[2], 0);
+    if (r) return r;
+    c->force_valid = true;
+    for (int i = 0; i < 3; ++i)
+        if (outs[i] && dev[i] != outs[i])
+            CK(cudaMemcpyAsync(outs[i], dev[i], bytes, cudaMemcpyDefault, st), "copy forces out");
+    if (e) return read_energy(c, e, st);
+    for (int i = 0; i < 3; ++i)
+        if (outs[i] && dev[i] != outs[i]) CK(cudaStreamSynchronize(st), "synchronize");
+    return RBSOG_OK;
+}
+
+int rbsog_forces(rbsog_ctx *c, double *F, rbsog_energy *e, void *stream) {
+    return forces_impl(c, F, nullptr, nullptr, e, stream);
+}
+
+int rbsog_forces_split(rbsog_ctx *c, double *F_near, double *F_far, rbsog_energy *e, void *stream) {
+    return forces_impl(c, nullptr, F_near, F_far, e, stream);
+}
+
+int rbsog_step(rbsog_ctx *c, int32_t nsteps, rbsog_energy *e, void *stream) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(c, RBSOG_EINVAL, "nsteps < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->force_valid && nsteps > 0) {
+        int r = enqueue(c, st, 0, nullptr, nullptr, nullptr, 0);
+        if (r) return r;
+        c->force_valid = true;
+    }
+    if (c->prof) {
+        const int mode = c->p.ensemble == RBSOG_LANGEVIN ? 2 : 1;
+        for (int i = 0; i < nsteps; ++i) {
+            int r = enqueue(c, st, mode, nullptr, nullptr, nullptr, 1);
+            if (r) return r;
+        }
+        if (e) return read_energy(c, e, st);
+        return RBSOG_OK;
+    }
+    if (nsteps > 0 && !c->graph) {
+        const int mode = c->p.ensemble == RBSOG_LANGEVIN ? 2 : 1;
+        cudaGraph_t g;
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int r = enqueue(c, c->cap_stream, mode, nullptr, nullptr, nullptr, 1);
+        cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+        if (r) return r;
+        CK(e2, "end capture");
+        cudaError_t e3 = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(e3, "graph instantiate");
+    }
+    for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->graph, st), "graph launch");
+    if (e) return read_energy(c, e, st);
+    return RBSOG_OK;
+}
+
+int rbsog_set_ksample(rbsog_ctx *c, const int32_t *m_host, int32_t P) {
+    if (!c || !m_host) return fail(c, RBSOG_EINVAL, "ctx or m is NULL");
+    if (P != c->p.P) return fail(c, RBSOG_EINVAL, "P differs from the context's P");
+    for (int l = 0; l < P; ++l)
+        if (m_host[3 * l] == 0 && m_host[3 * l + 1] == 0 && m_host[3 * l + 2] == 0)
+            return fail(c, RBSOG_EINVAL, "mode (0,0,0) is not in the sampled support");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    CK(cudaMemcpy(c->inject_m, m_host, 3 * sizeof(int32_t) * P, cudaMemcpyHostToDevice), "copy modes");
+    int one = 1;
+    CK(cudaMemcpy(&c->ctr->inject, &one, sizeof(int), cudaMemcpyHostToDevice), "set inject flag");
+    return RBSOG_OK;
+}
+
+int rbsog_get_ksample(rbsog_ctx *c, int32_t *m_host, double *coef_host) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    if (m_host) CK(cudaMemcpy(m_host, c->modes, 3 * sizeof(int32_t) * c->p.P, cudaMemcpyDeviceToHost), "copy modes");
+    if (coef_host) CK(cudaMemcpy(coef_host, c->coef, sizeof(double) * c->p.P, cudaMemcpyDeviceToHost), "copy coef");
+    return check_device_errors(c);
+}
+
+int rbsog_get_rho(rbsog_ctx *c, double *rho_host) {
+    if (!c || !rho_host) return fail(c, RBSOG_EINVAL, "ctx or rho is NULL");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    CK(cudaMemcpy(rho_host, c->rho, sizeof(double2) * c->p.P, cudaMemcpyDeviceToHost), "copy rho");
+    return RBSOG_OK;
+}
+
+int rbsog_get_cells(rbsog_ctx *c, int32_t *nc, uint32_t *cell_start, uint32_t *perm) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    if (nc) for (int d = 0; d < 3; ++d) nc[d] = c->box.nc[d];
+    if (cell_start)
+        CK(cudaMemcpy(cell_start, c->cell_start, sizeof(uint32_t) * ((size_t)c->box.ncell + 1), cudaMemcpyDeviceToHost),
+           "copy cell_start");
+    if (perm) CK(cudaMemcpy(perm, c->rest.id, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToHost), "copy perm");
+    return check_device_errors(c);
+}
+
+int rbsog_get_sog(rbsog_ctx *c, double *h, double *t0, int32_t *M1, int32_t *M2, double *w, double *lam, double *S) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    if (h) *h = c->sog.h;
+    if (t0) *t0 = c->sog.t0;
+    if (M1) *M1 = c->sog.M1;
+    if (M2) *M2 = c->sog.M2;
+    if (w) *w = c->sog.w;
+    if (lam) *lam = c->lam;
+    if (S) *S = c->S;
+    return RBSOG_OK;
+}
+
+int rbsog_profile(rbsog_ctx *c, int32_t enable) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    c->prof = enable != 0;
+    c->ev_used = 0;
+    c->prof_spans.clear();
+    return RBSOG_OK;
+}
+
+int rbsog_profile_read(rbsog_ctx *c, double *ms, int64_t *launches) {
+    if (!c || !ms || !launches) return fail(c, RBSOG_EINVAL, "ctx, ms or launches is NULL");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    for (int g = 0; g < RBSOG_NPROF; ++g) { ms[g] = 0.0; launches[g] = 0; }
+    for (auto &sp : c->prof_spans) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->ev_pool[sp.second.first], c->ev_pool[sp.second.second]), "event time");
+        ms[sp.first] += t;
+        launches[sp.first] += 1;
+    }
+    c->ev_used = 0;
+    c->prof_spans.clear();
+    return RBSOG_OK;
+}
+
+const char *rbsog_profile_name(int32_t group) {
+    return (group >= 0 && group < RBSOG_NPROF) ? kProfNames[group] : "";
+}
+
+int rbsog_build_sog(double lam, double r_c, double eps, int32_t mode, int32_t M1, int32_t M2, double *out6) {
+    if (!out6) return fail(nullptr, RBSOG_EINVAL, "out6 is NULL");
+    if (mode < 0 || mode > 2) return fail(nullptr, RBSOG_EINVAL, "bad sog mode");
+    SogDecomp s;
+    std::string err;
+    if (!build_sog(lam, r_c, eps, mode, M1, M2, &s, &err)) return fail(nullptr, RBSOG_ENOCONV, err);
+    out6[0] = s.h;
+    out6[1] = s.t0;
+    out6[2] = (double)s.M1;
+    out6[3] = (double)s.M2;
+    out6[4] = s.w;
+    out6[5] = sog_max_error(s);
+    return RBSOG_OK;
+}
+
+const char *rbsog_last_error(const rbsog_ctx *c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+void rbsog_free(rbsog_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (void *p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+"""Thin ctypes binding of librbsog (include/rbsog.h): argument marshalling only.
+
+Every function has the C name and signature; device arrays are passed as raw pointers
+(``torch.Tensor.data_ptr()``), host arrays as numpy buffers.  All computation happens in
+the CUDA library.  There is no fallback: if the shared library or a CUDA device is
+missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RBSOG_OK = 0
+RBSOG_FP64, RBSOG_FP32 = 0, 1
+RBSOG_NVE, RBSOG_LANGEVIN = 0, 1
+RBSOG_SOG_MINIMAL, RBSOG_SOG_BOUND, RBSOG_SOG_TABLE = 0, 1, 2
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOCONV", 6: "EUNSUPPORTED",
+          7: "EOVERFLOW"}
+
+
+class rbsog_params(C.Structure):
+    _fields_ = [("box", C.c_double * 3), ("kappa", C.c_double), ("a_ws", C.c_double), ("Gamma", C.c_double),
+                ("kT", C.c_double), ("r_c", C.c_double), ("sog_eps", C.c_double), ("dt", C.c_double),
+                ("langevin_gamma", C.c_double), ("seed", C.c_uint64), ("P", C.c_int32),
+                ("precision", C.c_int32), ("ensemble", C.c_int32), ("sog_mode", C.c_int32),
+                ("sog_M1", C.c_int32), ("sog_M2", C.c_int32), ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class rbsog_energy(C.Structure):
+    _fields_ = [("U_near", C.c_double), ("U_far", C.c_double), ("U_self", C.c_double), ("kinetic", C.c_double),
+                ("total", C.c_double), ("step", C.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RbsogError(RuntimeError):
+    pass
+
+
+_lib = None
+EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
+           "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog",
+           "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_last_error",
+           "rbsog_free"]
+RBSOG_NPROF = 10
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librbsog.so (building it first when asked).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RbsogError(f"librbsog not built: {path}")
+        _build.build()
+    L = C.CDLL(path)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double)
+    L.rbsog_init.argtypes = [C.POINTER(rbsog_params), i64, vp, vp, C.POINTER(vp)]
+    L.rbsog_set_state.argtypes = [vp, vp, vp, vp]
+    L.rbsog_get_state.argtypes = [vp, vp, vp, C.POINTER(C.c_uint64), vp]
+    L.rbsog_forces.argtypes = [vp, vp, C.POINTER(rbsog_energy), vp]
+    L.rbsog_forces_split.argtypes = [vp, vp, vp, C.POINTER(rbsog_energy), vp]
+    L.rbsog_step.argtypes = [vp, i32, C.POINTER(rbsog_energy), vp]
+    L.rbsog_set_ksample.argtypes = [vp, vp, i32]
+    L.rbsog_get_ksample.argtypes = [vp, vp, vp]
+    L.rbsog_get_rho.argtypes = [vp, vp]
+    L.rbsog_get_cells.argtypes = [vp, vp, vp, vp]
+    L.rbsog_get_sog.argtypes = [vp, dp, dp, C.POINTER(i32), C.POINTER(i32), dp, dp, dp]
+    L.rbsog_build_sog.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, i32, vp]
+    L.rbsog_profile.argtypes = [vp, i32]
+    L.rbsog_profile_read.argtypes = [vp, vp, vp]
+    L.rbsog_profile_name.argtypes = [i32]
+    L.rbsog_profile_name.restype = C.c_char_p
+    L.rbsog_last_error.argtypes = [vp]
+    L.rbsog_last_error.restype = C.c_char_p
+    L.rbsog_free.argtypes = [vp]
+    L.rbsog_free.restype = None
+    for name in EXPORTS:
+        if name not in ("rbsog_profile_name", "rbsog_last_error", "rbsog_free"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Raw address of a torch tensor, numpy array, int or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+def _check(ctx, code):
+    if code != RBSOG_OK:
+        msg = load().rbsog_last_error(ctx)
+        raise RbsogError(f"{STATUS.get(code, code)}: {msg.decode() if msg else ''}")
+
+
+def rbsog_init(params: rbsog_params, N: int, q, m):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    out = C.c_void_p()
+    _check(None, load().rbsog_init(C.byref(params), int(N), q.ctypes.data, m.ctypes.data, C.byref(out)))
+    return out.value
+
+
+def rbsog_set_state(ctx, r, v=None, stream=None):
+    _check(ctx, load().rbsog_set_state(ctx, _ptr(r), _ptr(v), _stream(stream)))
+
+
+def rbsog_get_state(ctx, r=None, v=None, stream=None) -> int:
+    step = C.c_uint64(0)
+    _check(ctx, load().rbsog_get_state(ctx, _ptr(r), _ptr(v), C.byref(step), _stream(stream)))
+    return step.value
+
+
+def rbsog_forces(ctx, F=None, energy: bool = False, stream=None):
+    e = rbsog_energy()
+    _check(ctx, load().rbsog_forces(ctx, _ptr(F), C.byref(e) if energy else None, _stream(stream)))
+    return e.as_dict() if energy else None
+
+
+def rbsog_forces_split(ctx, F_near=None, F_far=None, energy: bool = False, stream=None):
+    e = rbsog_energy()
+    _check(ctx, load().rbsog_forces_split(ctx, _ptr(F_near), _ptr(F_far), C.byref(e) if energy else None,
+                                          _stream(stream)))
+    return e.as_dict() if energy else None
+
+
+def rbsog_step(ctx, nsteps: int, energy: bool = False, stream=None):
+    e = rbsog_energy()
+    _check(ctx, load().rbsog_step(ctx, int(nsteps), C.byref(e) if energy else None, _stream(stream)))
+    return e.as_dict() if energy else None
+
+
+def rbsog_set_ksample(ctx, m):
+    m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+    _check(ctx, load().rbsog_set_ksample(ctx, m.ctypes.data, m.shape[0]))
+
+
+def rbsog_get_ksample(ctx, P: int):
+    m = np.zeros((P, 3), dtype=np.int32)
+    coef = np.zeros(P, dtype=np.float64)
+    _check(ctx, load().rbsog_get_ksample(ctx, m.ctypes.data, coef.ctypes.data))
+    return m, coef
+
+
+def rbsog_get_rho(ctx, P: int):
+    rho = np.zeros((P, 2), dtype=np.float64)
+    _check(ctx, load().rbsog_get_rho(ctx, rho.ctypes.data))
+    return rho
+
+
+def rbsog_get_cells(ctx, N: int):
+    nc = np.zeros(3, dtype=np.int32)
+    _check(ctx, load().rbsog_get_cells(ctx, nc.ctypes.data, None, None))
+    start = np.zeros(int(nc[0]) * int(nc[1]) * int(nc[2]) + 1, dtype=np.uint32)
+    perm = np.zeros(N, dtype=np.uint32)
+    _check(ctx, load().rbsog_get_cells(ctx, None, start.ctypes.data, perm.ctypes.data))
+    return nc, start, perm
+
+
+def rbsog_get_sog(ctx) -> dict:
+    h, t0, w, lam, S = (C.c_double() for _ in range(5))
+    M1, M2 = C.c_int32(), C.c_int32()
+    _check(ctx, load().rbsog_get_sog(ctx, C.byref(h), C.byref(t0), C.byref(M1), C.byref(M2), C.byref(w),
+                                     C.byref(lam), C.byref(S)))
+    return dict(h=h.value, t0=t0.value, M1=M1.value, M2=M2.value, w=w.value, lam=lam.value, S=S.value)
+
+
+def rbsog_build_sog(lam: float, r_c: float, eps: float, mode: int = RBSOG_SOG_MINIMAL, M1: int = 0,
+                    M2: int = 0) -> dict:
+    out = np.zeros(6, dtype=np.float64)
+    _check(None, load().rbsog_build_sog(float(lam), float(r_c), float(eps), int(mode), int(M1), int(M2),
+                                        out.ctypes.data))
+    return dict(h=out[0], t0=out[1], M1=int(out[2]), M2=int(out[3]), w=out[4], max_error=out[5])
+
+
+def rbsog_profile(ctx, enable: bool):
+    _check(ctx, load().rbsog_profile(ctx, 1 if enable else 0))
+
+
+def rbsog_profile_read(ctx) -> dict:
+    ms = np.zeros(RBSOG_NPROF, dtype=np.float64)
+    n = np.zeros(RBSOG_NPROF, dtype=np.int64)
+    _check(ctx, load().rbsog_profile_read(ctx, ms.ctypes.data, n.ctypes.data))
+    return {rbsog_profile_name(g): (float(ms[g]), int(n[g])) for g in range(RBSOG_NPROF)}
+
+
+def rbsog_profile_name(group: int) -> str:
+    return load().rbsog_profile_name(int(group)).decode()
+
+
+def rbsog_last_error(ctx=None) -> str:
+    msg = load().rbsog_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def rbsog_free(ctx):
+    if ctx:
+        load().rbsog_free(ctx)
+
+
+def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int | None = None,
+                sog_mode: int = RBSOG_SOG_MINIMAL, M1: int = 0, M2: int = 0, device: int = 0,
+                ensemble: int | None = None, dt: float | None = None) -> rbsog_params:
+    """rbsog_params from a workloads.Workload (plain field copy)."""
+    p = rbsog_params()
+    for d in range(3):
+        p.box[d] = float(w.box[d])
+    p.kappa = float(w.kappa)
+    p.a_ws = float(w.a_ws)
+    p.Gamma = float(w.Gamma)
+    p.kT = 0.0
+    p.r_c = float(w.r_c)
+    p.sog_eps = float(w.sog_eps)
+    p.dt = float(w.dt if dt is None else dt)
+    p.langevin_gamma = float(w.langevin_gamma)
+    p.seed = int(w.seed_k if seed is None else seed)
+    p.P = int(w.P if P is None else P)
+    p.precision = int(precision)
+    if ensemble is None:
+        ensemble = RBSOG_LANGEVIN if w.ensemble == "langevin" else RBSOG_NVE
+    p.ensemble = int(ensemble)
+    p.sog_mode = int(sog_mode)
+    p.sog_M1, p.sog_M2 = int(M1), int(M2)
+    p.device = int(device)
+    p.reserved = 0
+    return p

@@ -1,0 +1,67 @@
+"""Shared helpers of the GPU parity tests: contexts through the C ABI and the oracle's
+reference values on the same seeded inputs."""
+import dataclasses
+import math
+
+import numpy as np
+
+from oracle import core
+from oracle import sog as S
+from paper_2501_10946_gb300 import rbsog as R
+from paper_2501_10946_gb300 import workloads as W
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def require_gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+class Ctx:
+    def __init__(self, w, precision, q=None, m=None, **kw):
+        self.w = w
+        self.q = W.charges(w) if q is None else np.asarray(q, dtype=np.float64)
+        self.m = W.masses(w) if m is None else np.asarray(m, dtype=np.float64)
+        self.params = R.make_params(w, precision=precision, **kw)
+        self.P = self.params.P
+        self.h = R.rbsog_init(self.params, w.N, self.q, self.m)
+
+    def close(self):
+        R.rbsog_free(self.h)
+        self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def oracle_sog(w):
+    return S.build(w.a_ws / w.kappa, w.r_c, w.sog_eps)
+
+
+def oracle_forces(w, r, q, modes, near="cells", idx=None, rho=None, sog=None, S_=None):
+    sog = oracle_sog(w) if sog is None else sog
+    Q2 = float(np.sum(np.asarray(q) ** 2))
+    S_ = core.S_sum(w.box, sog, w.kT, Q2) if S_ is None else S_
+    Ft, Fn, Ff, e = core.rb_forces(r, q, w.box, w.r_c, sog, modes, w.kT, S=S_, near=near, idx=idx, rho_=rho)
+    return Ft, Fn, Ff, e, S_
+
+
+def workload(N, L, kappa=1.0, Gamma=1.0, rc=None, P=64, eps=1e-6, seed=7, box=None, dt=0.01, ensemble="nve"):
+    """A small uniform YOCP workload of the requested shape."""
+    box = (L, L, L) if box is None else tuple(box)
+    V = box[0] * box[1] * box[2]
+    a = W.wigner_seitz(N, V)
+    rc = 2.5 * a if rc is None else rc
+    return W.Workload(f"test_N{N}", N, box, a, kappa, Gamma, rc, eps, P, dt, 10, ensemble, 1.0, "uniform", seed,
+                      seed + 1, seed + 2)
+
+
+def modes_for(w, P, seed):
+    nmax = max(2, int(math.ceil(4.0 * max(w.box) / (2 * math.pi))))
+    return W.random_modes(P, nmax, seed)

@@ -1,0 +1,127 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds and loads, exports
+every entry point include/rbsog.h declares, rejects invalid parameters before touching a
+device, and its host-side SOG construction (Algorithm 1) agrees with the oracle's."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import sog as S
+from paper_2501_10946_gb300 import rbsog as R
+from paper_2501_10946_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "rbsog.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(rbsog_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_function():
+    lib = R.load()
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(R.EXPORTS) == names
+
+
+def test_struct_layouts_match_the_c_header(tmp_path):
+    """ctypes mirrors of rbsog_params / rbsog_energy against the C compiler's own layout."""
+    src = tmp_path / "layout.c"
+    fields_p = [f for f, _ in R.rbsog_params._fields_]
+    fields_e = [f for f, _ in R.rbsog_energy._fields_]
+    body = ['printf("%zu %zu\\n", sizeof(rbsog_params), sizeof(rbsog_energy));']
+    body += [f'printf("%zu\\n", offsetof(rbsog_params, {f}));' for f in fields_p]
+    body += [f'printf("%zu\\n", offsetof(rbsog_energy, {f}));' for f in fields_e]
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rbsog.h"\nint main(void){' +
+                   "".join(body) + "return 0;}\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    vals = [int(x) for x in out]
+    assert vals[0] == C.sizeof(R.rbsog_params) and vals[1] == C.sizeof(R.rbsog_energy)
+    offs = vals[2:]
+    assert offs[:len(fields_p)] == [getattr(R.rbsog_params, f).offset for f in fields_p]
+    assert offs[len(fields_p):] == [getattr(R.rbsog_energy, f).offset for f in fields_e]
+
+
+def base_params():
+    w = W.cfg_small_fp64()
+    return w, R.make_params(w, precision=R.RBSOG_FP64)
+
+
+@pytest.mark.parametrize("field,value", [("r_c", 6.0), ("P", 0), ("P", 5000), ("kappa", 0.0), ("precision", 7),
+                                         ("ensemble", 3), ("sog_mode", 9), ("reserved", 1), ("dt", -1.0)])
+def test_invalid_parameters_are_rejected_on_the_host(field, value):
+    w, p = base_params()
+    setattr(p, field, value)
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_init(p, w.N, W.charges(w), W.masses(w))
+    assert R.rbsog_last_error(None)
+
+
+def test_invalid_sizes_are_rejected():
+    w, p = base_params()
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_init(p, 1, np.ones(1), np.ones(1))
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_init(p, 4, np.ones(4), np.array([1.0, 0.0, 1.0, 1.0]))
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_init(p, 4, np.zeros(4), np.ones(4))
+
+
+def test_sog_table_mode_reproduces_table1_through_the_abi():
+    gold = os.path.join(os.path.dirname(__file__), "golden", "table1_c1_sog.txt")
+    for line in open(gold):
+        if line.startswith("#") or not line.strip():
+            continue
+        e, h, t0, m1, m2, mt, w = line.split()
+        a = R.rbsog_build_sog(0.5773, 5 * 0.5773, float(e), R.RBSOG_SOG_TABLE, int(m1), int(m2))
+        assert abs(a["h"] - float(h)) <= 1e-15
+        assert abs(a["t0"] - float(t0)) <= (1e-13 if float(e) >= 1e-5 else 1e-6)
+        assert abs(a["w"] - float(w)) <= 1e-8 * float(w)
+        assert a["max_error"] <= float(e)
+
+
+@pytest.mark.parametrize("mode,name", [(R.RBSOG_SOG_MINIMAL, "minimal"), (R.RBSOG_SOG_BOUND, "bound")])
+@pytest.mark.parametrize("eps", [1e-3, 1e-5, 1e-7, 1e-9, 1e-11, 1e-13])
+def test_library_sog_equals_oracle_sog(mode, name, eps):
+    """Same (M1, M2); the library's decomposition meets eps and C1 at r_c.  t0 is the root of
+    a residual that is flat for tight eps (and w amplifies it when the narrowest Gaussian is
+    tiny at r_c), so F is compared closely only where the root is well conditioned."""
+    lam, rc = 0.5773, 5 * 0.5773
+    a = R.rbsog_build_sog(lam, rc, eps, mode)
+    o = S.build(lam, rc, eps, name)
+    assert (a["M1"], a["M2"]) == (o.M1, o.M2)
+    assert 0.0 <= a["t0"] < a["h"] and abs(a["h"] - o.h) <= 1e-15
+    lib = S.SOG(lam, rc, eps, a["h"], a["t0"], a["M1"], a["M2"], a["w"])
+    assert lib.max_error() <= eps
+    dy = float(S.dyukawa(rc, lam))
+    assert abs(float(lib.dF(rc)) - dy) <= 1e-12 * abs(dy)
+    assert abs(float(lib.F(rc)) - float(S.yukawa(rc, lam))) <= 1e-14 * float(S.yukawa(rc, lam))
+    if mode == R.RBSOG_SOG_MINIMAL and eps >= 1e-9:
+        r = np.linspace(0.05, 33 * lam, 3000)
+        assert np.max(np.abs(lib.F(r) - o.F(r))) <= 1e-11 * np.max(np.abs(o.F(r)))
+
+
+@pytest.mark.parametrize("wl", [W.cfg_small_fp64, W.cfg_bcc_fp32, W.cfg_large], ids=lambda f: f.__name__)
+def test_library_sog_equals_oracle_on_workloads(wl):
+    w = wl()
+    lam = w.a_ws / w.kappa
+    a = R.rbsog_build_sog(lam, w.r_c, w.sog_eps)
+    o = S.build(lam, w.r_c, w.sog_eps)
+    assert (a["M1"], a["M2"]) == (o.M1, o.M2)
+    assert abs(a["t0"] - o.t0) <= 1e-13 and abs(a["w"] - o.w) <= 1e-13
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(R, "_lib", None)
+    monkeypatch.setattr(R._build, "LIB", str(tmp_path / "nope.so"))
+    with pytest.raises(R.RbsogError):
+        R.load(build_if_missing=False)

@@ -1,0 +1,113 @@
+"""GPU dynamics through rbsog_step (CUDA-graph replay): velocity Verlet and BAOAB
+trajectories against the oracle's integrators with the GPU's k-sets, determinism, and
+energy behaviour."""
+import numpy as np
+import pytest
+
+from gpu_common import Ctx, oracle_forces, oracle_sog, require_gpu, workload
+from oracle import core, integrate
+from paper_2501_10946_gb300 import rbsog as R
+from paper_2501_10946_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    return require_gpu()
+
+
+def gpu_trajectory(w, prec, r0, v0, nsteps):
+    """Positions, velocities and the k-set of every force evaluation, one step at a time."""
+    ks, rs, vs, es = [], [], [], []
+    with Ctx(w, prec) as c:
+        R.rbsog_set_state(c.h, r0, v0)
+        R.rbsog_forces(c.h)
+        ks.append(R.rbsog_get_ksample(c.h, c.P)[0])
+        for _ in range(nsteps):
+            es.append(R.rbsog_step(c.h, 1, energy=True))
+            ks.append(R.rbsog_get_ksample(c.h, c.P)[0])
+            r = np.zeros((w.N, 3))
+            v = np.zeros((w.N, 3))
+            R.rbsog_get_state(c.h, r, v)
+            rs.append(r)
+            vs.append(v)
+    return ks, rs, vs, es
+
+
+def oracle_trajectory(w, r0, v0, ks, nsteps):
+    q = W.charges(w)
+    m = W.masses(w)
+    sog = oracle_sog(w)
+    S_ = core.S_sum(w.box, sog, w.kT, float(np.sum(q * q)))
+    state = {"i": 0}
+
+    def force(x):
+        Ft, _, _, _, _ = oracle_forces(w, x, q, ks[state["i"]], sog=sog, S_=S_)
+        state["i"] += 1
+        return Ft
+
+    r, v = integrate.wrap(r0, w.box), v0.copy()
+    F = force(r)
+    rs, vs = [], []
+    for n in range(nsteps):
+        if w.ensemble == "langevin":
+            r, v, F = integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n, force)
+        else:
+            r, v, F = integrate.vv_step(r, v, F, m, w.box, w.dt, force)
+        rs.append(r)
+        vs.append(v)
+    return rs, vs
+
+
+def box_diff(a, b, L):
+    d = a - b
+    L = np.asarray(L)
+    return d - L * np.round(d / L)
+
+
+@pytest.mark.parametrize("ensemble", ["nve", "langevin"])
+@pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32], ids=["fp64", "fp32"])
+def test_trajectory_parity(prec, ensemble):
+    w = workload(500, 8.0, kappa=1.0, Gamma=1.0, P=64, seed=41, dt=0.002, ensemble=ensemble)
+    r0 = W.positions(w)
+    v0 = W.velocities(w)
+    n = 5
+    ks, rg, vg, _ = gpu_trajectory(w, prec, r0, v0, n)
+    ro, vo = oracle_trajectory(w, r0, v0, ks, n)
+    tol = 1e-11 if prec == R.RBSOG_FP64 else 2e-5
+    for s in range(n):
+        dr = box_diff(rg[s], ro[s], w.box)
+        assert np.max(np.abs(dr)) <= tol * w.box[0], (s, np.max(np.abs(dr)))
+        assert core.rel_l2(vg[s], vo[s]) <= tol * 10, s
+
+
+def test_graph_replay_is_deterministic():
+    w = workload(800, 9.0, P=48, seed=3)
+    outs = []
+    for _ in range(2):
+        with Ctx(w, R.RBSOG_FP32) as c:
+            R.rbsog_set_state(c.h, W.positions(w), W.velocities(w))
+            e = R.rbsog_step(c.h, 7, energy=True)
+            r = np.zeros((w.N, 3))
+            step = R.rbsog_get_state(c.h, r)
+            outs.append((r, e["total"], step))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+    assert outs[0][2] == 7
+
+
+def test_energy_components_after_steps_match_oracle():
+    """After steps, the GPU energies at the final state equal the oracle's on the GPU's k-set."""
+    w = W.cfg_small_fp64()
+    with Ctx(w, R.RBSOG_FP64) as c:
+        R.rbsog_set_state(c.h, W.positions(w), W.velocities(w))
+        e = R.rbsog_step(c.h, 3, energy=True)
+        m, _ = R.rbsog_get_ksample(c.h, c.P)
+        r = np.zeros((w.N, 3))
+        v = np.zeros((w.N, 3))
+        R.rbsog_get_state(c.h, r, v)
+    Ft, Fn, Ff, eo, _ = oracle_forces(w, r, W.charges(w), m)
+    assert abs(e["U_near"] - eo["U_N"]) <= 1e-11 * abs(eo["U_N"])
+    assert abs(e["U_far"] - eo["U_F"]) <= 1e-11 * abs(eo["U_F"])
+    assert abs(e["kinetic"] - integrate.kinetic(v, W.masses(w))) <= 1e-12 * e["kinetic"]
+    assert e["step"] == 3

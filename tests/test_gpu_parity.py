@@ -1,0 +1,168 @@
+"""GPU parity through the C ABI: every step of the force path against the FP64 oracle on
+the same seeded inputs and the same injected k-set.  FP64 build: relative L2 <= 1e-12;
+FP32 build: <= 1e-5; cell lists bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import FP32_TOL, FP64_TOL, Ctx, modes_for, oracle_forces, oracle_sog, require_gpu, workload
+from oracle import core
+from paper_2501_10946_gb300 import rbsog as R
+from paper_2501_10946_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = {R.RBSOG_FP64: FP64_TOL, R.RBSOG_FP32: FP32_TOL}
+PRECS = [pytest.param(R.RBSOG_FP64, id="fp64"), pytest.param(R.RBSOG_FP32, id="fp32")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    return require_gpu()
+
+
+def run_forces(w, prec, r, modes, q=None, split=True):
+    with Ctx(w, prec, q=q) as c:
+        R.rbsog_set_state(c.h, r)
+        R.rbsog_set_ksample(c.h, modes)
+        Fn = np.zeros((w.N, 3))
+        Ff = np.zeros((w.N, 3))
+        e = R.rbsog_forces_split(c.h, Fn, Ff, energy=True)
+        rho = R.rbsog_get_rho(c.h, c.P)
+        m_used, coef = R.rbsog_get_ksample(c.h, c.P)
+        sog = R.rbsog_get_sog(c.h)
+        cells = R.rbsog_get_cells(c.h, w.N)
+    return dict(Fn=Fn, Ff=Ff, e=e, rho=rho, m=m_used, coef=coef, sog=sog, cells=cells)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_workload_parity(prec):
+    """N=1000, L=10, Gamma=1, kappa=1, r_c=3.5a, P=100: near, far, total, rho, coef, energies."""
+    w = W.cfg_small_fp64()
+    r = W.positions(w)
+    q = W.charges(w)
+    modes = modes_for(w, w.P, 11)
+    g = run_forces(w, prec, r, modes)
+    assert np.array_equal(g["m"], modes)
+    Ft, Fn, Ff, e, S_ = oracle_forces(w, r, q, modes)
+    tol = TOL[prec]
+    assert abs(g["sog"]["S"] - S_) <= 1e-13 * S_
+    assert core.rel_l2(g["Fn"], Fn) <= tol
+    assert core.rel_l2(g["Ff"], Ff) <= tol
+    assert core.rel_l2(g["Fn"] + g["Ff"], Ft) <= tol
+    rho = core.rho(r, q, w.box, modes)
+    assert np.max(np.abs(g["rho"] - rho)) <= tol * np.max(np.abs(rho))
+    coef = core.rb_coef(modes, w.box, oracle_sog(w), w.kT, float(np.sum(q * q)), S_)
+    assert np.max(np.abs(g["coef"] - coef) / coef) <= 1e-13
+    for k_gpu, k_or in (("U_near", "U_N"), ("U_far", "U_F"), ("U_self", "U_self")):
+        assert abs(g["e"][k_gpu] - e[k_or]) <= max(tol, 1e-12) * abs(e[k_or]) * 10, (k_gpu, g["e"][k_gpu], e[k_or])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_cell_list_is_bit_exact(prec):
+    w = W.cfg_small_fp64()
+    r = W.positions(w)
+    # edge cases: origin, cell faces (exact in binary for L=10, n=4), L - ulp, negative, beyond L
+    r[0] = [0.0, 0.0, 0.0]
+    r[1] = [2.5, 5.0, 7.5]
+    r[2] = [np.nextafter(10.0, 0.0)] * 3
+    r[3] = [-2.5, 12.5, 10.0]
+    g = run_forces(w, prec, r, modes_for(w, w.P, 3))
+    nc, start, perm = g["cells"]
+    nco = core.n_cells(w.box, w.r_c)
+    assert list(nc) == list(nco)
+    _, start_o, perm_o = core.cell_list(r, w.box, nco)
+    assert np.array_equal(start, start_o)
+    assert np.array_equal(perm, perm_o)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", ["tiny", "ragged", "one_cell", "noncubic", "mixed", "P1", "Pmany", "dense"])
+def test_edge_cases(prec, case):
+    kw = {}
+    q = None
+    if case == "tiny":
+        w = workload(2, 4.0, rc=1.9, P=8)
+    elif case == "ragged":
+        w = workload(1237, 11.0, P=37)
+    elif case == "one_cell":       # fewer than 3 cells per axis: one cell spans the box
+        w = workload(300, 4.0, rc=1.9, P=50)
+    elif case == "noncubic":
+        w = workload(900, 0, box=(8.0, 11.0, 13.5), P=70, rc=2.0)
+    elif case == "mixed":
+        w = workload(800, 9.0, P=64)
+        q = np.random.default_rng(5).choice([-1.0, 1.0, 2.0], size=800)
+    elif case == "P1":
+        w = workload(500, 8.0, P=1)
+    elif case == "Pmany":          # several passes of the structure-factor kernel
+        w = workload(700, 9.0, P=1500)
+    else:                          # dense cells (strong overlap of neighbour lists)
+        w = workload(3000, 6.0, rc=2.0, P=40)
+    r = W.positions(w)
+    qq = W.charges(w) if q is None else q
+    modes = modes_for(w, w.P, 21)
+    g = run_forces(w, prec, r, modes, q=q)
+    Ft, Fn, Ff, e, S_ = oracle_forces(w, r, qq, modes, near="images" if case == "one_cell" else "cells")
+    tol = TOL[prec]
+    assert core.rel_l2(g["Fn"] + g["Ff"], Ft) <= tol
+    assert core.rel_l2(g["Ff"], Ff) <= tol
+    if np.any(Fn != 0):
+        assert core.rel_l2(g["Fn"], Fn) <= tol
+
+
+def test_host_and_device_pointers_agree(gpu):
+    torch = gpu
+    w = workload(600, 8.0, P=32)
+    r = W.positions(w)
+    modes = modes_for(w, w.P, 2)
+    with Ctx(w, R.RBSOG_FP64) as c:
+        R.rbsog_set_state(c.h, r)
+        R.rbsog_set_ksample(c.h, modes)
+        F_host = np.zeros((w.N, 3))
+        R.rbsog_forces(c.h, F_host)
+        rd = torch.tensor(r, device="cuda", dtype=torch.float64)
+        R.rbsog_set_state(c.h, rd)
+        R.rbsog_set_ksample(c.h, modes)
+        Fd = torch.zeros((w.N, 3), device="cuda", dtype=torch.float64)
+        R.rbsog_forces(c.h, Fd, energy=True)
+        assert np.array_equal(Fd.cpu().numpy(), F_host)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_scaled_strong_coupling_bcc(prec):
+    """bcc lattice, Gamma=100, kappa=0.5, r_c=4a, P=200 at 8^3 cells (N=1024)."""
+    base = W.cfg_bcc_fp32()
+    nc = 8
+    N = 2 * nc ** 3
+    L = W.box_for_unit_a(N)
+    import dataclasses
+    w = dataclasses.replace(base, N=N, box=(L, L, L), bcc_cells=nc, name="bcc8")
+    r = W.positions(w)
+    modes = modes_for(w, w.P, 5)
+    g = run_forces(w, prec, r, modes)
+    Ft, Fn, Ff, e, S_ = oracle_forces(w, r, W.charges(w), modes)
+    assert core.rel_l2(g["Fn"] + g["Ff"], Ft) <= TOL[prec]
+
+
+def test_full_size_uniform_fp32_sampled():
+    """N=1e6 uniform, Gamma=0.1, kappa=2, r_c=3a, P=500 in the FP32 build: rho over all
+    particles and the total force on 256 sampled particles against the oracle."""
+    w = W.cfg_large()
+    r = W.positions(w)
+    q = W.charges(w)
+    modes = modes_for(w, w.P, 17)
+    with Ctx(w, R.RBSOG_FP32) as c:
+        R.rbsog_set_state(c.h, r)
+        R.rbsog_set_ksample(c.h, modes)
+        Fn = np.zeros((w.N, 3))
+        Ff = np.zeros((w.N, 3))
+        R.rbsog_forces_split(c.h, Fn, Ff)
+        rho_g = R.rbsog_get_rho(c.h, c.P)
+        S_g = R.rbsog_get_sog(c.h)["S"]
+    rho = core.rho(r, q, w.box, modes)
+    assert np.max(np.abs(rho_g - rho)) <= FP32_TOL * np.max(np.abs(rho))
+    idx = np.random.default_rng(0).choice(w.N, 256, replace=False)
+    Ft, Fno, Ffo, e, S_ = oracle_forces(w, r, q, modes, idx=idx, rho=rho)
+    assert abs(S_g - S_) <= 1e-12 * S_
+    assert core.rel_l2(Fn[idx] + Ff[idx], Ft) <= FP32_TOL
+    assert core.rel_l2(Ff[idx], Ffo) <= FP32_TOL
