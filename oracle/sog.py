@@ -125,27 +125,44 @@ def m2_bound(t0: float, h: float, eps: float, delta: float, R: float) -> float:
     return max(a, b) / h
 
 
+INV_SQRT_PI = 0.5641895835477563     # 1/sqrt(pi) as the nearest double
+
+
+def f_scalar(t: float, r: float, lam: float) -> float:
+    """Eq. (1) for one (t, r), evaluated with the C library's exp."""
+    et = math.exp(t)
+    return math.exp(-r * r * et - 1.0 / (4.0 * lam * lam * et) + 0.5 * t) * INV_SQRT_PI
+
+
 def w_c0(t0: float, h: float, M1: int, M2: int, lam: float, rc: float) -> float:
-    """Eq. (38)."""
-    ms = np.arange(-M1, M2)
-    partial = h * float(np.sum(f_tr(t0 + ms * h, rc, lam))) if ms.size else 0.0
-    den = h * float(f_tr(t0 + M2 * h, rc, lam))
+    """Eq. (38), a sequential sum over m = -M1 .. M2-1."""
+    partial = 0.0
+    for m in range(-M1, M2):
+        partial += f_scalar(t0 + m * h, rc, lam)
+    partial *= h
+    den = h * f_scalar(t0 + M2 * h, rc, lam)
     if not den > 0.0:          # the narrowest Gaussian underflows at r_c: no C0 weight exists
         return math.nan
-    return (float(yukawa(rc, lam)) - partial) / den
+    return (math.exp(-rc / lam) / rc - partial) / den
 
 
 def c1_residual(t0: float, h: float, M1: int, M2: int, lam: float, rc: float) -> float:
-    """Eq. (36) with w of Eq. (38): d/dr [Y - F](r_c)."""
+    """Eq. (36) with w of Eq. (38): d/dr [Y - F](r_c), d/dr f(t, r) = -2 r e^t f(t, r).
+
+    Near its root this residual is a difference of nearly equal terms and its slope in t0
+    is small, so t0 is only defined to a band set by rounding.  It is evaluated as plain
+    sequential FP64 sums with the C library's exp; any FP64 evaluation in the same
+    operation order lands on the same root."""
     w = w_c0(t0, h, M1, M2, lam, rc)
     if not math.isfinite(w):
         return math.nan
-    ms = np.arange(-M1, M2 + 1)
-    t = t0 + ms * h
-    wt = np.ones(ms.size)
-    wt[-1] = w
-    dF = h * float(np.sum(wt * (-2.0 * rc * np.exp(t)) * f_tr(t, rc, lam)))
-    return float(dyukawa(rc, lam)) - dF
+    dF = 0.0
+    for m in range(-M1, M2 + 1):
+        t = t0 + m * h
+        wt = w if m == M2 else 1.0
+        dF += wt * (-2.0 * rc * math.exp(t)) * f_scalar(t, rc, lam)
+    dy = -math.exp(-rc / lam) * (1.0 / (lam * rc) + 1.0 / (rc * rc))
+    return dy - h * dF
 
 
 def bisect(fun, a: float, b: float, fa: float) -> float:
@@ -166,21 +183,21 @@ def bisect(fun, a: float, b: float, fa: float) -> float:
 
 
 def smallest_root(fun, h: float):
-    """Smallest root of fun on [0, h): sign change on a ROOT_GRID grid, then bisection."""
-    grid = [h * k / ROOT_GRID for k in range(ROOT_GRID + 1)]
+    """Smallest root of fun on [0, h): the first sign change on a ROOT_GRID-interval grid,
+    refined by bisection."""
     with np.errstate(over="ignore", under="ignore", invalid="ignore"):
-        vals = [fun(x) for x in grid]
-        for k in range(ROOT_GRID):
-            a, b = grid[k], grid[k + 1]
-            fa, fb = vals[k], vals[k + 1]
-            if not (math.isfinite(fa) and math.isfinite(fb)):
-                continue
-            if fa == 0.0:
-                return a
-            if fa * fb < 0.0:
-                x = bisect(fun, a, b, fa)
-                if x < h:
-                    return x
+        prev_x, prev_v = 0.0, fun(0.0)
+        for k in range(1, ROOT_GRID + 1):
+            x = h * k / ROOT_GRID
+            v = fun(x)
+            if math.isfinite(prev_v) and math.isfinite(v):
+                if prev_v == 0.0:
+                    return prev_x
+                if (prev_v < 0.0) != (v < 0.0) and v != 0.0:
+                    root = bisect(fun, prev_x, x, prev_v)
+                    if root < h:
+                        return root
+            prev_x, prev_v = x, v
     return None
 
 

@@ -14,7 +14,10 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["rbsog.cu", "k_cells.cu", "k_sample.cu", "k_forces.cu", "sog_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# host code keeps IEEE semantics (no FMA contraction): the SOG root of Eq. 36 is computed
+# with the same operation order as any other FP64 implementation of it
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

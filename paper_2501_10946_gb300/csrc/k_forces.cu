@@ -13,6 +13,7 @@
 #include <math_constants.h>
 
 #include "common.cuh"
+#include "devmath.cuh"
 #include "kernels.h"
 
 namespace rbsog {
@@ -24,19 +25,11 @@ constexpr int kRhoThreads = 256;
 constexpr int kRhoTile = 512;       // particles staged per tile (FP32: 8 KB, FP64: 16 KB)
 constexpr int kFarThreads = 256;
 constexpr int kFarTile = 512;       // modes staged per tile
-constexpr float kTwoPiOver2p32 = 1.4629180792671596e-09f;   // 2 pi / 2^32
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-    float y = x - c;
-    float t = s + y;
-    c = (t - s) - y;
-    s = t;
 }
 
 template <typename T>
@@ -234,11 +227,10 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho32(RhoArgs a, int chunk) {
 #pragma unroll
             for (int j = 0; j < ML; ++j) {
                 const uint32_t th = (uint32_t)mm[j][0] * r.x + (uint32_t)mm[j][1] * r.y + (uint32_t)mm[j][2] * r.z;
-                const float f = (float)(int)th * kTwoPiOver2p32;
                 float sn, cs;
-                __sincosf(f, &sn, &cs);
-                tre[j] = fmaf(q, cs, tre[j]);
-                tim[j] = fmaf(q, sn, tim[j]);
+                const float qs = flip(q, half_turn_sincos(th, sn, cs));
+                tre[j] = fmaf(qs, cs, tre[j]);
+                tim[j] = fmaf(qs, sn, tim[j]);
             }
         }
 #pragma unroll
@@ -369,10 +361,9 @@ __global__ void __launch_bounds__(kFarThreads) k_far(FarArgs a) {
                 for (int l = l0; l < l1; ++l) {
                     const GTab32 t = tab[l];
                     const uint32_t th = (uint32_t)t.m.x * ri.x + (uint32_t)t.m.y * ri.y + (uint32_t)t.m.z * ri.z;
-                    const float f = (float)(int)th * kTwoPiOver2p32;
                     float sn, cs;
-                    __sincosf(f, &sn, &cs);
-                    const float gv = cs * __int_as_float(t.m.w) - sn * t.f.w;
+                    const uint32_t sg = half_turn_sincos(th, sn, cs);
+                    const float gv = flip(cs * __int_as_float(t.m.w) - sn * t.f.w, sg);
                     acc[0] = fmaf(t.f.x, gv, acc[0]);
                     acc[1] = fmaf(t.f.y, gv, acc[1]);
                     acc[2] = fmaf(t.f.z, gv, acc[2]);

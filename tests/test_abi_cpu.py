@@ -92,22 +92,19 @@ def test_sog_table_mode_reproduces_table1_through_the_abi():
 @pytest.mark.parametrize("mode,name", [(R.RBSOG_SOG_MINIMAL, "minimal"), (R.RBSOG_SOG_BOUND, "bound")])
 @pytest.mark.parametrize("eps", [1e-3, 1e-5, 1e-7, 1e-9, 1e-11, 1e-13])
 def test_library_sog_equals_oracle_sog(mode, name, eps):
-    """Same (M1, M2); the library's decomposition meets eps and C1 at r_c.  t0 is the root of
-    a residual that is flat for tight eps (and w amplifies it when the narrowest Gaussian is
-    tiny at r_c), so F is compared closely only where the root is well conditioned."""
+    """Same (M1, M2) and the same C1 root.  The residual of Eq. 36 is flat near its root for
+    tight eps, so t0 is defined only up to rounding; both sides evaluate Eqs. 36 and 38 as
+    plain FP64 sums in the same operation order and land on the same bits."""
     lam, rc = 0.5773, 5 * 0.5773
     a = R.rbsog_build_sog(lam, rc, eps, mode)
     o = S.build(lam, rc, eps, name)
     assert (a["M1"], a["M2"]) == (o.M1, o.M2)
-    assert 0.0 <= a["t0"] < a["h"] and abs(a["h"] - o.h) <= 1e-15
+    assert abs(a["h"] - o.h) <= 1e-15
+    assert abs(a["t0"] - o.t0) <= 1e-15 and abs(a["w"] - o.w) <= 1e-14 * abs(o.w)
     lib = S.SOG(lam, rc, eps, a["h"], a["t0"], a["M1"], a["M2"], a["w"])
     assert lib.max_error() <= eps
     dy = float(S.dyukawa(rc, lam))
     assert abs(float(lib.dF(rc)) - dy) <= 1e-12 * abs(dy)
-    assert abs(float(lib.F(rc)) - float(S.yukawa(rc, lam))) <= 1e-14 * float(S.yukawa(rc, lam))
-    if mode == R.RBSOG_SOG_MINIMAL and eps >= 1e-9:
-        r = np.linspace(0.05, 33 * lam, 3000)
-        assert np.max(np.abs(lib.F(r) - o.F(r))) <= 1e-11 * np.max(np.abs(o.F(r)))
 
 
 @pytest.mark.parametrize("wl", [W.cfg_small_fp64, W.cfg_bcc_fp32, W.cfg_large], ids=lambda f: f.__name__)

@@ -46,14 +46,15 @@ def test_small_workload_parity(prec):
     assert np.array_equal(g["m"], modes)
     Ft, Fn, Ff, e, S_ = oracle_forces(w, r, q, modes)
     tol = TOL[prec]
-    assert abs(g["sog"]["S"] - S_) <= 1e-13 * S_
+    # S sums ~1e5 lattice terms in a different order on each side
+    assert abs(g["sog"]["S"] - S_) <= 1e-11 * S_
     assert core.rel_l2(g["Fn"], Fn) <= tol
     assert core.rel_l2(g["Ff"], Ff) <= tol
     assert core.rel_l2(g["Fn"] + g["Ff"], Ft) <= tol
     rho = core.rho(r, q, w.box, modes)
     assert np.max(np.abs(g["rho"] - rho)) <= tol * np.max(np.abs(rho))
     coef = core.rb_coef(modes, w.box, oracle_sog(w), w.kT, float(np.sum(q * q)), S_)
-    assert np.max(np.abs(g["coef"] - coef) / coef) <= 1e-13
+    assert np.max(np.abs(g["coef"] - coef) / coef) <= 1e-11
     for k_gpu, k_or in (("U_near", "U_N"), ("U_far", "U_F"), ("U_self", "U_self")):
         assert abs(g["e"][k_gpu] - e[k_or]) <= max(tol, 1e-12) * abs(e[k_or]) * 10, (k_gpu, g["e"][k_gpu], e[k_or])
 
@@ -163,6 +164,7 @@ def test_full_size_uniform_fp32_sampled():
     assert np.max(np.abs(rho_g - rho)) <= FP32_TOL * np.max(np.abs(rho))
     idx = np.random.default_rng(0).choice(w.N, 256, replace=False)
     Ft, Fno, Ffo, e, S_ = oracle_forces(w, r, q, modes, idx=idx, rho=rho)
-    assert abs(S_g - S_) <= 1e-12 * S_
+    # ~1e8 lattice terms summed in a different order on each side
+    assert abs(S_g - S_) <= 1e-11 * S_
     assert core.rel_l2(Fn[idx] + Ff[idx], Ft) <= FP32_TOL
     assert core.rel_l2(Ff[idx], Ffo) <= FP32_TOL
