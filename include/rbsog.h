@@ -175,6 +175,35 @@ const char *rbsog_profile_name(int32_t group);
  * the message is then available from rbsog_last_error(NULL). */
 int rbsog_build_sog(double lam, double r_c, double eps, int32_t mode, int32_t M1, int32_t M2, double *out6);
 
+/* Structure factor without device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code that runs
+ * inside a fixed memory budget owned by another allocator, or a latency-critical
+ * loop that must not pay for an allocation that can synchronise the device.
+ *
+ * Computes rho_l = sum_j q_j exp(i k_l . r_j), k_l = 2 pi (m_x/L_x, m_y/L_y, m_z/L_z),
+ * with the arithmetic of the FP32 build (2^32 fixed-point phases, FP32 sin/cos with
+ * compensated per-block sums, FP64 fixed-order reduction over blocks).
+ *   r_dev   device, [N][3] float64 positions (any real values; taken modulo the box)
+ *   q_dev   device, [N] float64 charges
+ *   box_host host, 3 box lengths > 0
+ *   m_dev   device, [P][3] int32 mode triples
+ *   rho_dev device, [P][2] float64 output (Re, Im)
+ *   stream  cudaStream_t the work is enqueued on; the call returns before it completes.
+ * It allocates nothing: its per-block partial sums live in one statically sized
+ * device array of 4 MiB (262144 double2 slots) that every GPU loading this library
+ * holds until the process exits.  The array needs G x S x P slots, G = min(152,
+ * ceil(N/64)) blocks and S = 1..8 particle subsets per block (S = 1 once P > 128), so
+ * P up to 1724 is always accepted (up to 4096 when G x P fits, i.e. small N); larger
+ * requests fail with RBSOG_EINVAL and a message.  The first call on a device looks the array's device address up with
+ * cudaGetSymbolAddress and caches it (with that device current); make that first
+ * call before any stream capture.  Every call shares the array, which keeps the last
+ * call's contents; each call writes every slot it later reads, so nothing needs
+ * clearing.  Calls whose work overlaps on the GPU (different streams, or other host
+ * threads) race on the array and must be serialised by the caller.  Errors are
+ * reported through rbsog_last_error(NULL). */
+int rbsog_rho_noalloc(const double *r_dev, const double *q_dev, int64_t N, const double *box_host,
+                      const int32_t *m_dev, int32_t P, double *rho_dev, void *stream);
+
 /* Message of the last failed call on ctx (or of the last failed rbsog_init when ctx
  * is NULL).  The pointer stays valid until the next call on the same context. */
 const char *rbsog_last_error(const rbsog_ctx *ctx);

@@ -65,6 +65,11 @@ struct rbsog_ctx {
 
 static std::string g_init_error;
 
+namespace rbsog {
+// message for rbsog_last_error(NULL) from calls that have no context
+void set_global_error(const std::string &msg) { g_init_error = msg; }
+}  // namespace rbsog
+
 namespace {
 
 const double kPi = 3.14159265358979323846;

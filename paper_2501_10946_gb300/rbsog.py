@@ -45,8 +45,8 @@ class RbsogError(RuntimeError):
 _lib = None
 EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
            "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog",
-           "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_last_error",
-           "rbsog_free"]
+           "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_rho_noalloc",
+           "rbsog_last_error", "rbsog_free"]
 RBSOG_NPROF = 10
 
 
@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True):
     L.rbsog_profile_read.argtypes = [vp, vp, vp]
     L.rbsog_profile_name.argtypes = [i32]
     L.rbsog_profile_name.restype = C.c_char_p
+    L.rbsog_rho_noalloc.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp]
     L.rbsog_last_error.argtypes = [vp]
     L.rbsog_last_error.restype = C.c_char_p
     L.rbsog_free.argtypes = [vp]
@@ -213,6 +214,14 @@ def rbsog_profile_read(ctx) -> dict:
 
 def rbsog_profile_name(group: int) -> str:
     return load().rbsog_profile_name(int(group)).decode()
+
+
+def rbsog_rho_noalloc(r_dev, q_dev, N: int, box, m_dev, P: int, rho_dev, stream=None):
+    """Structure factor of device arrays into rho_dev ([P][2] float64) without any device
+    allocation by the library (for callers that cannot allocate; see include/rbsog.h)."""
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    _check(None, load().rbsog_rho_noalloc(_ptr(r_dev), _ptr(q_dev), int(N), box.ctypes.data, _ptr(m_dev), int(P),
+                                          _ptr(rho_dev), _stream(stream)))
 
 
 def rbsog_last_error(ctx=None) -> str:
