@@ -14,6 +14,7 @@ constexpr int kMaxAttempts = 1 << 20;
 // error bits raised by kernels (device flag)
 constexpr int kErrCellOverflow = 1;
 constexpr int kErrSampler = 2;
+constexpr int kErrNearStage = 4;     // a bounded wait for staged near-field data gave up
 
 // Device counters that advance inside captured graphs.
 struct DevCounters {

@@ -62,13 +62,25 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
             const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
             U4 w0 = philox10(id, 0x40000000u, (uint32_t)step, (uint32_t)(step >> 32), k0, k1);
             U4 w1 = philox10(id, 0x40000001u, (uint32_t)step, (uint32_t)(step >> 32), k0, k1);
-            double u1 = u53_of(w0.x, w0.y), u2 = u53_of(w0.z, w0.w);
-            double rad = sqrt(-2.0 * log(1.0 - u1));
-            double s2, c2;
-            sincospi(2.0 * u2, &s2, &c2);
-            double u3 = u53_of(w1.x, w1.y), u4 = u53_of(w1.z, w1.w);
-            double rad3 = sqrt(-2.0 * log(1.0 - u3));
-            double xi[3] = {rad * c2, rad * s2, rad3 * cospi(2.0 * u4)};
+            double xi[3];
+            if (PREC == 1) {
+                // FP32 build: the same Box-Muller pairs from the 24 leading bits of the words
+                // (FP64 transcendentals would cost more than the rest of this kernel)
+                const float u1 = (float)(w0.x >> 8) * 5.9604645e-08f, u2 = (float)(w0.z >> 8) * 5.9604645e-08f;
+                const float u3 = (float)(w1.x >> 8) * 5.9604645e-08f, u4 = (float)(w1.z >> 8) * 5.9604645e-08f;
+                const float rad = sqrtf(-2.0f * logf(1.0f - u1)), rad3 = sqrtf(-2.0f * logf(1.0f - u3));
+                float s2, c2;
+                sincospif(2.0f * u2, &s2, &c2);
+                xi[0] = rad * c2; xi[1] = rad * s2; xi[2] = rad3 * cospif(2.0f * u4);
+            } else {
+                double u1 = u53_of(w0.x, w0.y), u2 = u53_of(w0.z, w0.w);
+                double rad = sqrt(-2.0 * log(1.0 - u1));
+                double s2, c2;
+                sincospi(2.0 * u2, &s2, &c2);
+                double u3 = u53_of(w1.x, w1.y), u4 = u53_of(w1.z, w1.w);
+                double rad3 = sqrt(-2.0 * log(1.0 - u3));
+                xi[0] = rad * c2; xi[1] = rad * s2; xi[2] = rad3 * cospi(2.0 * u4);
+            }
             const double sig = sqrt((1.0 - a.c1 * a.c1) * a.kT * invm);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {

@@ -1,8 +1,5 @@
-// Force kernels of one RBSOG step.
+// Far-field kernels of one RBSOG step (the near field is in k_near.cu).
 //
-//   k_near    near field, Eq. (55) first term with F_N1, F_N2 of Eqs. (56)-(57), and
-//             U_N of Eq. (50), over the 27 neighbour cells of each particle (minimum
-//             image by wrapping fixed-point differences).  FP32 build: compensated sums.
 //   k_rho     structure factor rho(k_l) = sum_j q_j exp(i k_l.r_j) (Sec. 2): per block,
 //             lane <-> mode, particles broadcast from shared memory; phases are exact
 //             integer products m.s modulo 2^32 (2^64), so sin/cos see [-pi, pi).
@@ -20,7 +17,6 @@ namespace rbsog {
 
 namespace {
 
-constexpr int kNearThreads = 128;
 constexpr int kRhoThreads = 256;
 constexpr int kRhoTile = 512;       // particles staged per tile (FP32: 8 KB, FP64: 16 KB)
 constexpr int kFarThreads = 256;
@@ -43,137 +39,6 @@ __device__ __forceinline__ T block_reduce_sum(T v, T *sh) {
     T out = sh[0];
     __syncthreads();
     return out;
-}
-
-// ------------------------------------------------------------------ near field
-template <int PREC>
-__global__ void __launch_bounds__(kNearThreads) k_near(NearArgs a) {
-    __shared__ double shU[kNearThreads];
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    double Uthread = 0.0;
-    // an overflowing cell (reported as RBSOG_EOVERFLOW) would make the pair loops quadratic
-    const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
-    if (p < a.N && overflow) {
-        for (int d = 0; d < 3; ++d) {
-            if (PREC == 1) ((float *)a.Fn)[(size_t)d * a.N + p] = 0.f;
-            else ((double *)a.Fn)[(size_t)d * a.N + p] = 0.0;
-        }
-    }
-    if (p < a.N && !overflow) {
-        const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
-        if (PREC == 1) {
-            const uint4 *rec = (const uint4 *)a.rec;
-            const uint4 ri = rec[p];
-            const float qi = __uint_as_float(ri.w);
-            const uint32_t si[3] = {ri.x, ri.y, ri.z};
-            int ci[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                ci[d] = (int)(((unsigned long long)si[d] * (unsigned long long)a.box.nc[d]) >> 32);
-            float Fs[3] = {0.f, 0.f, 0.f}, Fc[3] = {0.f, 0.f, 0.f}, Us = 0.f, Uc = 0.f;
-            const int zlo = nz >= 3 ? -1 : 0, zhi = nz >= 3 ? 1 : 0;
-            const int ylo = ny >= 3 ? -1 : 0, yhi = ny >= 3 ? 1 : 0;
-            const int xlo = nx >= 3 ? -1 : 0, xhi = nx >= 3 ? 1 : 0;
-            for (int dz = zlo; dz <= zhi; ++dz) {
-                const int cz = (ci[2] + dz + nz) % nz;
-                for (int dy = ylo; dy <= yhi; ++dy) {
-                    const int cy = (ci[1] + dy + ny) % ny;
-                    for (int dx = xlo; dx <= xhi; ++dx) {
-                        const int cx = (ci[0] + dx + nx) % nx;
-                        const int c = cx + nx * (cy + ny * cz);
-                        const uint32_t j0 = a.cell_start[c], j1 = a.cell_start[c + 1];
-                        for (uint32_t j = j0; j < j1; ++j) {
-                            if (j == p) continue;
-                            const uint4 rj = rec[j];
-                            const float d0 = (float)(int)(si[0] - rj.x) * a.box.L_2m32f[0];
-                            const float d1 = (float)(int)(si[1] - rj.y) * a.box.L_2m32f[1];
-                            const float d2 = (float)(int)(si[2] - rj.z) * a.box.L_2m32f[2];
-                            const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                            if (r2 < a.nc.rc2_f) {
-                                const float rinv = rsqrtf(r2);
-                                const float r = r2 * rinv;
-                                const float e1 = ex2_approx(-r * a.nc.inv_lam_log2e_f);
-                                float fsog = 0.f, fn2 = 0.f;
-                                for (int g = 0; g < a.nc.mtot; ++g) {
-                                    const float E = ex2_approx(-r2 * a.nc.bl2f[g]);
-                                    fsog = fmaf(a.nc.af[g], E, fsog);
-                                    fn2 = fmaf(a.nc.cf[g], E, fn2);
-                                }
-                                const float qq = qi * __uint_as_float(rj.w);
-                                const float fn1 = e1 * (1.f + r * a.nc.inv_lam_f) * (rinv * rinv * rinv);
-                                const float gsc = qq * (fn1 + fn2);
-                                kahan_add(Fs[0], Fc[0], gsc * d0);
-                                kahan_add(Fs[1], Fc[1], gsc * d1);
-                                kahan_add(Fs[2], Fc[2], gsc * d2);
-                                kahan_add(Us, Uc, 0.5f * qq * (e1 * rinv - fsog));
-                            }
-                        }
-                    }
-                }
-            }
-            float *Fn = (float *)a.Fn;
-            Fn[p] = Fs[0] - Fc[0];
-            Fn[a.N + p] = Fs[1] - Fc[1];
-            Fn[2 * (size_t)a.N + p] = Fs[2] - Fc[2];
-            Uthread = (double)Us - (double)Uc;
-        } else {
-            const Rec64 *rec = (const Rec64 *)a.rec;
-            const Rec64 ri = rec[p];
-            int ci[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d)
-                ci[d] = (int)(((ri.s[d] >> 32) * (unsigned long long)a.box.nc[d]) >> 32);
-            double F[3] = {0.0, 0.0, 0.0}, U = 0.0;
-            const int zlo = nz >= 3 ? -1 : 0, zhi = nz >= 3 ? 1 : 0;
-            const int ylo = ny >= 3 ? -1 : 0, yhi = ny >= 3 ? 1 : 0;
-            const int xlo = nx >= 3 ? -1 : 0, xhi = nx >= 3 ? 1 : 0;
-            for (int dz = zlo; dz <= zhi; ++dz) {
-                const int cz = (ci[2] + dz + nz) % nz;
-                for (int dy = ylo; dy <= yhi; ++dy) {
-                    const int cy = (ci[1] + dy + ny) % ny;
-                    for (int dx = xlo; dx <= xhi; ++dx) {
-                        const int cx = (ci[0] + dx + nx) % nx;
-                        const int c = cx + nx * (cy + ny * cz);
-                        const uint32_t j0 = a.cell_start[c], j1 = a.cell_start[c + 1];
-                        for (uint32_t j = j0; j < j1; ++j) {
-                            if (j == p) continue;
-                            const Rec64 rj = rec[j];
-                            double d[3];
-#pragma unroll
-                            for (int e = 0; e < 3; ++e)
-                                d[e] = (double)(long long)(ri.s[e] - rj.s[e]) * a.box.L_2m64[e];
-                            const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                            if (r2 < a.nc.rc2) {
-                                const double r = sqrt(r2);
-                                const double rinv = 1.0 / r;
-                                const double e1 = exp(-r * a.nc.inv_lam);
-                                double fsog = 0.0, fn2 = 0.0;
-                                for (int g = 0; g < a.nc.mtot; ++g) {
-                                    const double E = exp(-r2 * a.nc.b[g]);
-                                    fsog += a.nc.a[g] * E;
-                                    fn2 += a.nc.c[g] * E;
-                                }
-                                const double qq = ri.q * rj.q;
-                                const double fn1 = e1 * (1.0 + r * a.nc.inv_lam) * (rinv * rinv * rinv);
-                                const double gsc = qq * (fn1 + fn2);
-                                F[0] += gsc * d[0];
-                                F[1] += gsc * d[1];
-                                F[2] += gsc * d[2];
-                                U += 0.5 * qq * (e1 * rinv - fsog);
-                            }
-                        }
-                    }
-                }
-            }
-            double *Fn = (double *)a.Fn;
-            Fn[p] = F[0];
-            Fn[a.N + p] = F[1];
-            Fn[2 * (size_t)a.N + p] = F[2];
-            Uthread = U;
-        }
-    }
-    double tot = block_reduce_sum<double>(Uthread, shU);
-    if (threadIdx.x == 0) a.U_part[blockIdx.x] = tot;
 }
 
 // ------------------------------------------------------------------ structure factor
@@ -295,26 +160,39 @@ struct GTab64 {
     double re, im;
 };
 
+// Block b sums modes 32b .. 32b+31: warp w adds the partials of blocks w, w+8, ... in
+// order, then warp 0 adds the 8 warp sums in order (fixed, deterministic).  Writes rho,
+// the gather table and u_l = coef_l |rho_l|^2 / 2 (summed by k_energy).
 template <int PREC>
-__global__ void __launch_bounds__(1024) k_rho_final(RhoFinalArgs a, int ML) {
-    __shared__ double sh[1024];
-    double u = 0.0;
-    for (int l = threadIdx.x; l < a.P; l += blockDim.x) {
+__global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
+    __shared__ double2 sh[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int l = blockIdx.x * 32 + lane;
+    double re = 0.0, im = 0.0;
+    if (l < a.P) {
         const int pass_base = (l / (256 * ML)) * 256 * ML;
-        int left = a.P - pass_base;
-        int ngroups = (left + 32 * ML - 1) / (32 * ML);
-        if (ngroups > 8) ngroups = 8;
-        const int nsub = 8 / ngroups;
-        double re = 0.0, im = 0.0;
-        for (int b = 0; b < a.G; ++b)
+        int ngroups, nsub;
+        rho_split(a.P, pass_base, ML, ngroups, nsub);
+        for (int b = warp; b < a.G; b += 8)
             for (int s = 0; s < nsub; ++s) {
                 const double2 v = a.partial[((size_t)b * 8 + s) * a.P + l];
                 re += v.x;
                 im += v.y;
             }
+    }
+    sh[warp][lane] = make_double2(re, im);
+    __syncthreads();
+    if (warp == 0 && l < a.P) {
+        re = 0.0;
+        im = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            re += sh[w][lane].x;
+            im += sh[w][lane].y;
+        }
         a.rho[l] = make_double2(re, im);
         const double coef = a.coef[l];
-        u += 0.5 * coef * (re * re + im * im);
+        a.Ufar[l] = 0.5 * coef * (re * re + im * im);
         const int mx = a.m[3 * l], my = a.m[3 * l + 1], mz = a.m[3 * l + 2];
         const double kx = a.tpl[0] * mx, ky = a.tpl[1] * my, kz = a.tpl[2] * mz;
         if (PREC == 1) {
@@ -330,9 +208,7 @@ __global__ void __launch_bounds__(1024) k_rho_final(RhoFinalArgs a, int ML) {
             ((GTab64 *)a.gtab)[l] = t;
         }
     }
-    double tot = block_reduce_sum<double>(u, sh);
-    if (threadIdx.x == 0) {
-        *a.Ufar = tot;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctr->draw += 1ull;
         a.ctr->inject = 0;
     }
@@ -450,8 +326,11 @@ __global__ void __launch_bounds__(1024) k_energy(EnergyArgs a) {
     double U = block_reduce_sum<double>(u, sh);
     for (int i = threadIdx.x; i < a.nK; i += blockDim.x) k += a.K_part[i];
     double K = block_reduce_sum<double>(k, sh);
+    double uf = 0.0;
+    for (int i = threadIdx.x; i < a.nUfar; i += blockDim.x) uf += a.Ufar[i];
+    const double Ufs = block_reduce_sum<double>(uf, sh);
     if (threadIdx.x == 0) {
-        const double Uf = *a.Ufar + a.Ufar0;
+        const double Uf = Ufs + a.Ufar0;
         a.out[0] = U;
         a.out[1] = Uf;
         a.out[2] = a.Uself;
@@ -466,13 +345,6 @@ inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 
 int rho_ml(int P) { return P <= 256 ? 1 : (P <= 512 ? 2 : 4); }
 
 }  // namespace
-
-int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
-    unsigned nb = blocks_for(a.N, kNearThreads);
-    if (prec == 1) k_near<1><<<nb, kNearThreads, 0, st>>>(a);
-    else k_near<0><<<nb, kNearThreads, 0, st>>>(a);
-    return (int)nb;
-}
 
 int rho_blocks(int prec, uint32_t N, int P) {
     (void)prec; (void)P;
@@ -496,8 +368,9 @@ void launch_rho(int prec, const RhoArgs &a, cudaStream_t st) {
 }
 
 void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st) {
-    if (prec == 1) k_rho_final<1><<<1, 1024, 0, st>>>(a, rho_ml(a.P));
-    else k_rho_final<0><<<1, 1024, 0, st>>>(a, 1);
+    const int nb = (a.P + 31) / 32;
+    if (prec == 1) k_rho_final<1><<<nb, 256, 0, st>>>(a, rho_ml(a.P));
+    else k_rho_final<0><<<nb, 256, 0, st>>>(a, 1);
 }
 
 int launch_far(int prec, const FarArgs &a, cudaStream_t st) {

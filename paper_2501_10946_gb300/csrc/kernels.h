@@ -80,7 +80,7 @@ struct NearArgs {
     uint32_t N;
     void *Fn;                  // near force SoA [3][N] (float or double)
     double *U_part;            // per-block near energy
-    const DevCounters *ctr;    // skip the pair loops when the cell build overflowed
+    DevCounters *ctr;          // error bits: skip the pair loops when the cell build overflowed
 };
 int launch_near(int prec, const NearArgs &a, cudaStream_t st);   // returns #blocks (energy partials)
 struct RhoArgs {
@@ -101,7 +101,7 @@ struct RhoFinalArgs {
     double tpl[3];
     double2 *rho;              // [P]
     void *gtab;                // gather table: float (FP32) / double (FP64), [P] x {ckx,cky,ckz,Re,Im} + int m
-    double *Ufar;              // scalar: sum coef |rho|^2 / 2
+    double *Ufar;              // [P]: coef_l |rho_l|^2 / 2
     DevCounters *ctr;
 };
 void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st);
@@ -125,7 +125,7 @@ int launch_far(int prec, const FarArgs &a, cudaStream_t st);     // returns #blo
 struct EnergyArgs {
     const double *U_part; int nU;
     const double *K_part; int nK;
-    const double *Ufar;
+    const double *Ufar; int nUfar;   // per-mode U*_F terms
     double Ufar0;              // k = 0 term
     double Uself;
     double *out;               // [5]: U_near, U_far, U_self, K, total

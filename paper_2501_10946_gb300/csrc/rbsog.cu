@@ -11,6 +11,7 @@
 // and drift fused into "bin") and replays it.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -284,6 +285,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     { ProfScope ps(c, st, 8); c->nK = launch_far(prec, fa, st); }
     EnergyArgs ea{};
     ea.U_part = c->U_part; ea.nU = c->nU; ea.K_part = c->K_part; ea.nK = c->nK; ea.Ufar = c->Ufar;
+    ea.nUfar = c->p.P;
     ea.Ufar0 = c->Ufar0; ea.Uself = c->Uself; ea.out = c->energy; ea.ctr = c->ctr; ea.advance_step = advance;
     { ProfScope ps(c, st, 9); launch_energy(ea, st); }
     cudaError_t e = cudaGetLastError();
@@ -296,6 +298,7 @@ int check_device_errors(rbsog_ctx *c) {
     CK(cudaMemcpy(&h, c->ctr, sizeof h, cudaMemcpyDeviceToHost), "read device status");
     if (h.err & kErrCellOverflow) return fail(c, RBSOG_EOVERFLOW, "a cell holds more than 4096 particles");
     if (h.err & kErrSampler) return fail(c, RBSOG_ETIMEOUT, "k-sampler exceeded its attempt limit");
+    if (h.err & kErrNearStage) return fail(c, RBSOG_ETIMEOUT, "near-field staging wait exceeded its limit");
     return RBSOG_OK;
 }
 
@@ -449,8 +452,8 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         dalloc(c, &c->perm_src, n) || dalloc(c, &c->keys, n) || dalloc(c, &c->modes, 3 * (size_t)p.P) ||
         dalloc(c, &c->inject_m, 3 * (size_t)p.P) || dalloc(c, &c->coef, (size_t)p.P) ||
         dalloc(c, &c->partial, (size_t)c->G * 8 * p.P) || dalloc(c, &c->rho, (size_t)p.P) ||
-        dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, 1) ||
-        dalloc(c, &c->U_part, (n + 127) / 128 + 1) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
+        dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, (size_t)p.P) ||
+        dalloc(c, &c->U_part, std::max((n + 127) / 128, (size_t)bx.ncell) + 1) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
         dalloc(c, &c->energy, 8) || dalloc(c, &c->ctr, 1)) {
         g_init_error = "device allocation failed";
         return bail(RBSOG_ENOMEM);
