@@ -140,8 +140,9 @@ int rbsog_get_rho(rbsog_ctx *ctx, double *rho_host);
 /* The cell list of the last force evaluation: nc[3] cells per axis, cell_start
  * (n_c^3 + 1 entries) and perm (N entries, the caller's particle index at each
  * cell-sorted position; within a cell, ascending).  Host arrays; any may be NULL.
- * Cells: s_a = floor(frac(r_a/L_a) 2^32), c_a = floor(s_a n_a / 2^32), c = c_x +
- * n_x (c_y + n_y c_z), n_a = floor(L_a / r_c) when >= 3 else 1.  Synchronous. */
+ * Cells: s_a = floor(frac(r_a (1/L_a)) 2^32) with 1/L_a rounded to double,
+ * c_a = floor(s_a n_a / 2^32), c = c_x + n_x (c_y + n_y c_z), n_a = floor(L_a / r_c)
+ * when >= 3 else 1.  Synchronous. */
 int rbsog_get_cells(rbsog_ctx *ctx, int32_t *nc, uint32_t *cell_start, uint32_t *perm);
 
 /* The SOG decomposition in use (Eq. 37): h, t0, M1, M2, the C1 weight w of m = M2,

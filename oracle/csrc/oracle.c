@@ -93,10 +93,12 @@ double orc_calF(double k2, double kT, double V, double Q2, double lam) {
 
 /* ---- fixed-point coordinates and the cell list ----------------------- */
 
-/* Fractional coordinate of r in [0,1): u = r/L, f = u - floor(u); f == 1 (from
- * rounding of a tiny negative u) is the same point as f == 0. */
+/* Fractional coordinate of r in [0,1): u = r (1/L) with the reciprocal rounded to
+ * double, f = u - floor(u); f == 1 (from rounding of a tiny negative u) is the same
+ * point as f == 0. */
 static double frac01(double r, double L) {
-    double u = r / L;
+    double invL = 1.0 / L;
+    double u = r * invL;
     double f = u - floor(u);
     if (f >= 1.0) f = 0.0;
     return f;

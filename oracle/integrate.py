@@ -12,7 +12,7 @@ convergence theory (Sec. 4.4) without giving a scheme.  Readings used here:
   xi: standard normals from Philox4x32-10, key = seed, counter = (particle id,
   0x40000000 + j, step lo, step hi); j = 0 gives (xi_x, xi_y) by Box-Muller of its
   four words, j = 1 gives xi_z (cosine branch).
-  wrap(r) = r - L floor(r/L), then + L if negative, then - L if >= L.
+  wrap(r) = r - L floor(r (1/L)), then + L if negative, then - L if >= L.
 """
 from __future__ import annotations
 
@@ -25,7 +25,7 @@ from . import philox
 
 def wrap(r, L):
     L = np.asarray(L, dtype=np.float64)
-    w = r - L * np.floor(r / L)
+    w = r - L * np.floor(r * (1.0 / L))
     w = np.where(w < 0.0, w + L, w)
     return np.where(w >= L, w - L, w)
 

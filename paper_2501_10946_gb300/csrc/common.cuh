@@ -50,6 +50,7 @@ struct NearConsts {
 
 struct Box {
     double L[3];
+    double invL[3];       // 1/L rounded to double (fixed point and wrap multiply by it)
     int nc[3];
     int ncell;
     double cellscale_unused;

@@ -2,7 +2,7 @@
 //
 // Per step (Algorithm 2: integrate, then rebuild the neighbour structure of Eq. 55):
 //   k_bin          v += F dt/2m, drift (BAOAB: half drift, Ornstein-Uhlenbeck, half drift),
-//                  wrap into [0, L), fixed point s = floor(frac(r/L) 2^32) (2^64 in FP64),
+//                  wrap into [0, L), fixed point s = floor(frac(r (1/L)) 2^32) (2^64 in FP64),
 //                  cell c_a = floor(s_a n_a / 2^32), atomic count -> slot within the cell
 //   k_tile_sums    per 4096-cell tile population
 //   k_scan_tiles   exclusive scan -> cell_start; clears the counts for the next build
@@ -18,16 +18,17 @@ namespace rbsog {
 
 namespace {
 
-__device__ __forceinline__ double wrap_coord(double r, double L) {
-    // r - L floor(r/L), then into [0, L): IEEE operations without contraction
-    double w = __dsub_rn(r, __dmul_rn(L, floor(__ddiv_rn(r, L))));
+// FP64 division is slow on this part, so both use the double reciprocal 1/L:
+__device__ __forceinline__ double wrap_coord(double r, double L, double invL) {
+    // r - L floor(r (1/L)), then into [0, L): IEEE operations without contraction
+    double w = __dsub_rn(r, __dmul_rn(L, floor(__dmul_rn(r, invL))));
     if (w < 0.0) w = __dadd_rn(w, L);
     if (w >= L) w = __dsub_rn(w, L);
     return w;
 }
 
-__device__ __forceinline__ double frac01(double r, double L) {
-    double u = __ddiv_rn(r, L);
+__device__ __forceinline__ double frac01(double r, double invL) {
+    double u = __dmul_rn(r, invL);
     double f = __dsub_rn(u, floor(u));
     return f >= 1.0 ? 0.0 : f;
 }
@@ -81,7 +82,9 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
                 double rad3 = sqrt(-2.0 * log(1.0 - u3));
                 xi[0] = rad * c2; xi[1] = rad * s2; xi[2] = rad3 * cospi(2.0 * u4);
             }
-            const double sig = sqrt((1.0 - a.c1 * a.c1) * a.kT * invm);
+            // noise amplitude sqrt((1 - c1^2) kT / m); FP32 suffices for the FP32 build
+            const double sig = PREC == 1 ? (double)sqrtf((float)((1.0 - a.c1 * a.c1) * a.kT * invm))
+                                         : sqrt((1.0 - a.c1 * a.c1) * a.kT * invm);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 r[d] += 0.5 * a.dt * v[d];
@@ -93,8 +96,8 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
     uint32_t cc[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        r[d] = wrap_coord(r[d], a.box.L[d]);
-        double f = frac01(r[d], a.box.L[d]);
+        r[d] = wrap_coord(r[d], a.box.L[d], a.box.invL[d]);
+        double f = frac01(r[d], a.box.invL[d]);
         uint32_t s32;
         if (PREC == 1) {
             s32 = (uint32_t)__double2ull_rz(f * 4294967296.0);
@@ -249,9 +252,9 @@ __global__ void __launch_bounds__(256) k_set_state(const double *r, const double
                                                    const double *m_user, State rest, uint32_t N, Box box) {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    rest.rx[k] = wrap_coord(r[3 * (size_t)k], box.L[0]);
-    rest.ry[k] = wrap_coord(r[3 * (size_t)k + 1], box.L[1]);
-    rest.rz[k] = wrap_coord(r[3 * (size_t)k + 2], box.L[2]);
+    rest.rx[k] = wrap_coord(r[3 * (size_t)k], box.L[0], box.invL[0]);
+    rest.ry[k] = wrap_coord(r[3 * (size_t)k + 1], box.L[1], box.invL[1]);
+    rest.rz[k] = wrap_coord(r[3 * (size_t)k + 2], box.L[2], box.invL[2]);
     rest.vx[k] = v ? v[3 * (size_t)k] : 0.0;
     rest.vy[k] = v ? v[3 * (size_t)k + 1] : 0.0;
     rest.vz[k] = v ? v[3 * (size_t)k + 2] : 0.0;

@@ -4,7 +4,7 @@
 //             lane <-> mode, particles broadcast from shared memory; phases are exact
 //             integer products m.s modulo 2^32 (2^64), so sin/cos see [-pi, pi).
 //   k_rho_fin fixed-order grid reduction, U*_F of Eq. (60) and the gather table.
-//   k_far     F*_i = -q_i sum_l coef_l k_l Im(exp(-i k_l.r_i) rho_l) (Eq. 60), added to
+//   k_far32/64 F*_i = -q_i sum_l coef_l k_l Im(exp(-i k_l.r_i) rho_l) (Eq. 60), added to
 //             the near force, fused with the closing half kick v += F dt/(2m).
 //   k_energy  fixed-order reduction of the energy partials.
 #include <math_constants.h>
@@ -215,106 +215,137 @@ __global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
 }
 
 // ------------------------------------------------------------------ far gather + kick
+// Closing part of a step for one particle: total force, optional half kick, kinetic
+// energy, caller-order outputs.
 template <int PREC>
-__global__ void __launch_bounds__(kFarThreads) k_far(FarArgs a) {
+__device__ __forceinline__ double finish_particle(const FarArgs &a, uint32_t p, const double *Ff) {
+    const uint32_t N = a.N;
+    double Fn[3], Ft[3];
+    if (PREC == 1) {
+        const float *fn = (const float *)a.Fn;
+        Fn[0] = fn[p]; Fn[1] = fn[N + p]; Fn[2] = fn[2 * (size_t)N + p];
+    } else {
+        const double *fn = (const double *)a.Fn;
+        Fn[0] = fn[p]; Fn[1] = fn[N + p]; Fn[2] = fn[2 * (size_t)N + p];
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Ft[d] = Fn[d] + Ff[d];
+    if (PREC == 1) {
+        float *F = (float *)a.F;
+        F[p] = (float)Ft[0]; F[N + p] = (float)Ft[1]; F[2 * (size_t)N + p] = (float)Ft[2];
+    } else {
+        double *F = (double *)a.F;
+        F[p] = Ft[0]; F[N + p] = Ft[1]; F[2 * (size_t)N + p] = Ft[2];
+    }
+    double v[3] = {a.st.vx[p], a.st.vy[p], a.st.vz[p]};
+    const double invm = a.st.invm[p];
+    if (a.integrate) {
+        const double hk = 0.5 * a.dt * invm;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[d] += hk * Ft[d];
+        a.st.vx[p] = v[0]; a.st.vy[p] = v[1]; a.st.vz[p] = v[2];
+    }
+    const size_t u = 3 * (size_t)a.st.id[p];
+    if (a.F_user) { a.F_user[u] = Ft[0]; a.F_user[u + 1] = Ft[1]; a.F_user[u + 2] = Ft[2]; }
+    if (a.Fn_user) { a.Fn_user[u] = Fn[0]; a.Fn_user[u + 1] = Fn[1]; a.Fn_user[u + 2] = Fn[2]; }
+    if (a.Ff_user) { a.Ff_user[u] = Ff[0]; a.Ff_user[u + 1] = Ff[1]; a.Ff_user[u + 2] = Ff[2]; }
+    return 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm;
+}
+
+// FP32: two particles per thread (p and p + 256) share each mode's table entry.  The
+// gather sums over modes whose phases are unrelated, so rounding of the phase scaling is
+// incoherent here and the argument needs no half-turn reduction (unlike rho).
+__global__ void __launch_bounds__(kFarThreads) k_far32(FarArgs a) {
     __shared__ double shK[kFarThreads];
-    __shared__ __align__(16) unsigned char smem_raw[kFarTile * sizeof(GTab32)];
+    __shared__ __align__(16) GTab32 tab[kFarTile];
+    const uint32_t p0 = blockIdx.x * (2 * kFarThreads) + threadIdx.x;
+    const uint32_t p1 = p0 + kFarThreads;
+    const bool v0 = p0 < a.N, v1 = p1 < a.N;
+    const uint4 r0 = v0 ? ((const uint4 *)a.rec)[p0] : make_uint4(0, 0, 0, 0);
+    const uint4 r1 = v1 ? ((const uint4 *)a.rec)[p1] : make_uint4(0, 0, 0, 0);
+    float S0[3] = {0.f, 0.f, 0.f}, C0[3] = {0.f, 0.f, 0.f}, S1[3] = {0.f, 0.f, 0.f}, C1[3] = {0.f, 0.f, 0.f};
+    for (int base = 0; base < a.P; base += kFarTile) {
+        const int tn = min(kFarTile, a.P - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < tn; t += blockDim.x) tab[t] = ((const GTab32 *)a.gtab)[base + t];
+        __syncthreads();
+        for (int l0 = 0; l0 < tn; l0 += 32) {
+            const int l1 = min(tn, l0 + 32);
+            float A0[3] = {0.f, 0.f, 0.f}, A1[3] = {0.f, 0.f, 0.f};
+            for (int l = l0; l < l1; ++l) {
+                const GTab32 t = tab[l];
+                const float im = __int_as_float(t.m.w), re = t.f.w;
+                const uint32_t th0 = (uint32_t)t.m.x * r0.x + (uint32_t)t.m.y * r0.y + (uint32_t)t.m.z * r0.z;
+                const uint32_t th1 = (uint32_t)t.m.x * r1.x + (uint32_t)t.m.y * r1.y + (uint32_t)t.m.z * r1.z;
+                float s0, c0, s1, c1;
+                __sincosf((float)(int)th0 * kTwoPiOver2p32, &s0, &c0);
+                __sincosf((float)(int)th1 * kTwoPiOver2p32, &s1, &c1);
+                const float g0 = c0 * im - s0 * re, g1 = c1 * im - s1 * re;
+                A0[0] = fmaf(t.f.x, g0, A0[0]); A0[1] = fmaf(t.f.y, g0, A0[1]); A0[2] = fmaf(t.f.z, g0, A0[2]);
+                A1[0] = fmaf(t.f.x, g1, A1[0]); A1[1] = fmaf(t.f.y, g1, A1[1]); A1[2] = fmaf(t.f.z, g1, A1[2]);
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                kahan_add(S0[d], C0[d], A0[d]);
+                kahan_add(S1[d], C1[d], A1[d]);
+            }
+        }
+    }
+    double K = 0.0;
+    if (v0) {
+        double Ff[3];
+        const double q = (double)__uint_as_float(r0.w);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Ff[d] = -q * ((double)S0[d] - (double)C0[d]);
+        K += finish_particle<1>(a, p0, Ff);
+    }
+    if (v1) {
+        double Ff[3];
+        const double q = (double)__uint_as_float(r1.w);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Ff[d] = -q * ((double)S1[d] - (double)C1[d]);
+        K += finish_particle<1>(a, p1, Ff);
+    }
+    const double tot = block_reduce_sum<double>(K, shK);
+    if (threadIdx.x == 0) a.K_part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kFarThreads) k_far64(FarArgs a) {
+    __shared__ double shK[kFarThreads];
+    __shared__ __align__(16) GTab64 tab[kFarTile / 2];
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < a.N;
-    double Ff[3] = {0.0, 0.0, 0.0};
-    if (PREC == 1) {
-        GTab32 *tab = (GTab32 *)smem_raw;
-        const uint4 ri = valid ? ((const uint4 *)a.rec)[p] : make_uint4(0, 0, 0, 0);
-        float S[3] = {0.f, 0.f, 0.f}, C[3] = {0.f, 0.f, 0.f};
-        for (int base = 0; base < a.P; base += kFarTile) {
-            const int tn = min(kFarTile, a.P - base);
-            __syncthreads();
-            for (int t = threadIdx.x; t < tn; t += blockDim.x) tab[t] = ((const GTab32 *)a.gtab)[base + t];
-            __syncthreads();
-            for (int l0 = 0; l0 < tn; l0 += 32) {
-                const int l1 = min(tn, l0 + 32);
-                float acc[3] = {0.f, 0.f, 0.f};
-                for (int l = l0; l < l1; ++l) {
-                    const GTab32 t = tab[l];
-                    const uint32_t th = (uint32_t)t.m.x * ri.x + (uint32_t)t.m.y * ri.y + (uint32_t)t.m.z * ri.z;
-                    float sn, cs;
-                    const uint32_t sg = half_turn_sincos(th, sn, cs);
-                    const float gv = flip(cs * __int_as_float(t.m.w) - sn * t.f.w, sg);
-                    acc[0] = fmaf(t.f.x, gv, acc[0]);
-                    acc[1] = fmaf(t.f.y, gv, acc[1]);
-                    acc[2] = fmaf(t.f.z, gv, acc[2]);
-                }
-#pragma unroll
-                for (int d = 0; d < 3; ++d) kahan_add(S[d], C[d], acc[d]);
-            }
+    Rec64 ri;
+    if (valid) ri = ((const Rec64 *)a.rec)[p];
+    else { ri.s[0] = ri.s[1] = ri.s[2] = 0ull; ri.q = 0.0; }
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int base = 0; base < a.P; base += kFarTile / 2) {
+        const int tn = min(kFarTile / 2, a.P - base);
+        __syncthreads();
+        for (int t = threadIdx.x; t < tn; t += blockDim.x) tab[t] = ((const GTab64 *)a.gtab)[base + t];
+        __syncthreads();
+        for (int l = 0; l < tn; ++l) {
+            const GTab64 t = tab[l];
+            const unsigned long long th = (unsigned long long)(long long)t.m.x * ri.s[0] +
+                                          (unsigned long long)(long long)t.m.y * ri.s[1] +
+                                          (unsigned long long)(long long)t.m.z * ri.s[2];
+            const double f = (double)(long long)th * 5.421010862427522e-20;
+            double sn, cs;
+            sincospi(2.0 * f, &sn, &cs);
+            const double gv = cs * t.im - sn * t.re;
+            acc[0] += t.ck[0] * gv;
+            acc[1] += t.ck[1] * gv;
+            acc[2] += t.ck[2] * gv;
         }
-        const float qi = __uint_as_float(ri.w);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) Ff[d] = -(double)qi * ((double)S[d] - (double)C[d]);
-    } else {
-        GTab64 *tab = (GTab64 *)smem_raw;
-        const int tile = (int)(sizeof(smem_raw) / sizeof(GTab64));
-        Rec64 ri;
-        if (valid) ri = ((const Rec64 *)a.rec)[p];
-        else { ri.s[0] = ri.s[1] = ri.s[2] = 0ull; ri.q = 0.0; }
-        double acc[3] = {0.0, 0.0, 0.0};
-        for (int base = 0; base < a.P; base += tile) {
-            const int tn = min(tile, a.P - base);
-            __syncthreads();
-            for (int t = threadIdx.x; t < tn; t += blockDim.x) tab[t] = ((const GTab64 *)a.gtab)[base + t];
-            __syncthreads();
-            for (int l = 0; l < tn; ++l) {
-                const GTab64 t = tab[l];
-                const unsigned long long th = (unsigned long long)(long long)t.m.x * ri.s[0] +
-                                              (unsigned long long)(long long)t.m.y * ri.s[1] +
-                                              (unsigned long long)(long long)t.m.z * ri.s[2];
-                const double f = (double)(long long)th * 5.421010862427522e-20;
-                double sn, cs;
-                sincospi(2.0 * f, &sn, &cs);
-                const double gv = cs * t.im - sn * t.re;
-                acc[0] += t.ck[0] * gv;
-                acc[1] += t.ck[1] * gv;
-                acc[2] += t.ck[2] * gv;
-            }
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) Ff[d] = -ri.q * acc[d];
     }
     double K = 0.0;
     if (valid) {
-        const uint32_t N = a.N;
-        double Fn[3], Ft[3];
-        if (PREC == 1) {
-            const float *fn = (const float *)a.Fn;
-            Fn[0] = fn[p]; Fn[1] = fn[N + p]; Fn[2] = fn[2 * (size_t)N + p];
-        } else {
-            const double *fn = (const double *)a.Fn;
-            Fn[0] = fn[p]; Fn[1] = fn[N + p]; Fn[2] = fn[2 * (size_t)N + p];
-        }
+        double Ff[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) Ft[d] = Fn[d] + Ff[d];
-        if (PREC == 1) {
-            float *F = (float *)a.F;
-            F[p] = (float)Ft[0]; F[N + p] = (float)Ft[1]; F[2 * (size_t)N + p] = (float)Ft[2];
-        } else {
-            double *F = (double *)a.F;
-            F[p] = Ft[0]; F[N + p] = Ft[1]; F[2 * (size_t)N + p] = Ft[2];
-        }
-        double v[3] = {a.st.vx[p], a.st.vy[p], a.st.vz[p]};
-        const double invm = a.st.invm[p];
-        if (a.integrate) {
-            const double hk = 0.5 * a.dt * invm;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) v[d] += hk * Ft[d];
-            a.st.vx[p] = v[0]; a.st.vy[p] = v[1]; a.st.vz[p] = v[2];
-        }
-        K = 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm;
-        const size_t u = 3 * (size_t)a.st.id[p];
-        if (a.F_user) { a.F_user[u] = Ft[0]; a.F_user[u + 1] = Ft[1]; a.F_user[u + 2] = Ft[2]; }
-        if (a.Fn_user) { a.Fn_user[u] = Fn[0]; a.Fn_user[u + 1] = Fn[1]; a.Fn_user[u + 2] = Fn[2]; }
-        if (a.Ff_user) { a.Ff_user[u] = Ff[0]; a.Ff_user[u + 1] = Ff[1]; a.Ff_user[u + 2] = Ff[2]; }
+        for (int d = 0; d < 3; ++d) Ff[d] = -ri.q * acc[d];
+        K = finish_particle<0>(a, p, Ff);
     }
-    double tot = block_reduce_sum<double>(K, shK);
+    const double tot = block_reduce_sum<double>(K, shK);
     if (threadIdx.x == 0) a.K_part[blockIdx.x] = tot;
 }
 
@@ -374,9 +405,13 @@ void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st) {
 }
 
 int launch_far(int prec, const FarArgs &a, cudaStream_t st) {
-    unsigned nb = blocks_for(a.N, kFarThreads);
-    if (prec == 1) k_far<1><<<nb, kFarThreads, 0, st>>>(a);
-    else k_far<0><<<nb, kFarThreads, 0, st>>>(a);
+    if (prec == 1) {
+        const unsigned nb = blocks_for(a.N, 2 * kFarThreads);
+        k_far32<<<nb, kFarThreads, 0, st>>>(a);
+        return (int)nb;
+    }
+    const unsigned nb = blocks_for(a.N, kFarThreads);
+    k_far64<<<nb, kFarThreads, 0, st>>>(a);
     return (int)nb;
 }
 

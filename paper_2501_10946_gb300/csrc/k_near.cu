@@ -6,11 +6,13 @@
 // row is one (or, across the periodic seam, two) contiguous slices of the cell-sorted
 // 16-byte particle records, so the CTA stages the whole neighbourhood in shared memory
 // with TMA bulk copies completing on one mbarrier.  Each target particle then
-//   (1) filters its 27 cells with float coordinates relative to the tile (3 FADD per
-//       candidate, permissive by 1e-4 in r^2) into a short per-thread list, and
-//   (2) evaluates the pair force on the listed candidates from exact fixed-point
-//       differences, applying the exact test r^2 < r_c^2,
-// so the expensive pair arithmetic runs without the divergence of a fused loop.
+//   (1) tests its 27 cells with exact fixed-point differences (r^2 < r_c^2) and lists
+//       the hits by staging index, and
+//   (2) evaluates the pair force on the listed candidates,
+// with the list flushed at three points per target where the warp is converged (after
+// rows 2, 5 and 8), so the expensive pair arithmetic runs on whole warps instead of
+// diverging inside the candidate loop.  One 16-byte record per staged particle and a
+// 32-entry list keep enough CTAs resident to hide latency.
 // Otherwise (FP64 build, fewer than 3 cells on an axis, or a neighbourhood that does
 // not fit the staging buffer): one thread per particle reading candidates from global
 // memory.
@@ -25,8 +27,8 @@ namespace {
 
 constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
-constexpr int kRegionCap = 1536;       // staged particles per CTA (2 x 24 KB)
-constexpr int kListCap = 64;           // listed candidates per thread before a flush
+constexpr int kRegionCap = 1280;       // staged particles per CTA (20 KB)
+constexpr int kListCap = 32;           // listed candidates per thread between flushes
 constexpr int kMaxTileW = 64;
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -148,22 +150,18 @@ __device__ void near_one_f64(const NearArgs &a, uint32_t p, double *Fout, double
     Uout = U;
 }
 
-__device__ __forceinline__ double block_sum_128(double v, double *sh) {
+// Energy partials are per warp (4 per block, fixed order), so no block-wide barrier waits
+// for the slowest thread at the end of a kernel.
+constexpr int kWarpsPerBlock = 4;
+
+__device__ __forceinline__ void warp_partial(double v, double *U_part, unsigned blk) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
-    return t;
+    if ((threadIdx.x & 31) == 0) U_part[(size_t)blk * kWarpsPerBlock + (threadIdx.x >> 5)] = v;
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
-    __shared__ double sh[kGlobalThreads / 32];
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     double U = 0.0;
     if (p < a.N) {
@@ -180,21 +178,18 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
             Fn[p] = F[0]; Fn[a.N + p] = F[1]; Fn[2 * (size_t)a.N + p] = F[2];
         }
     }
-    const double tot = block_sum_128(U, sh);
-    if (threadIdx.x == 0) a.U_part[blockIdx.x] = tot;
+    warp_partial(U, a.U_part, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- tiled (TMA) FP32 path
 struct TileSmem {
-    uint4 srec[kRegionCap];                 // staged records, 16-byte aligned
-    float4 spos[kRegionCap];                // x, y, z relative to the tile origin, q
-    uint16_t list[kListCap][kTileThreads];  // per-thread candidate lists (smem indices)
+    uint4 stage[kRegionCap];                // staged records
+    uint16_t list[kListCap][kTileThreads];  // per-thread candidate lists (staging indices)
     int seg_off[9][kMaxTileW + 3];          // per row: offset of each region cell within the row
-    int row_base[10];                       // per row: offset of the row in srec
+    int row_base[10];                       // per row: offset of the row in the staging buffer
     uint32_t chunk_g[9][2];                 // per row: global start of up to two slices
     uint32_t chunk_n[9][2];                 // per row: particle count of each slice
     unsigned long long mbar;
-    double red[kTileThreads / 32];
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -202,12 +197,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 __device__ __forceinline__ void flush_list(const TileSmem &S, const NearConsts &nc, const Box &box, int cnt,
                                            uint4 ri, float qi, float *Fs, float *Fc, float &Us, float &Uc) {
     for (int k = 0; k < cnt; ++k) {
-        const uint4 rj = S.srec[S.list[k][threadIdx.x]];
+        const uint4 rj = S.stage[S.list[k][threadIdx.x]];
         const float d0 = (float)(int)(ri.x - rj.x) * box.L_2m32f[0];
         const float d1 = (float)(int)(ri.y - rj.y) * box.L_2m32f[1];
         const float d2 = (float)(int)(ri.z - rj.z) * box.L_2m32f[2];
-        const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-        if (r2 < nc.rc2_f) pair_f32(nc, qi * __uint_as_float(rj.w), d0, d1, d2, r2, Fs, Fc, Us, Uc);
+        pair_f32(nc, qi * __uint_as_float(rj.w), d0, d1, d2, d0 * d0 + d1 * d1 + d2 * d2, Fs, Fc, Us, Uc);
     }
 }
 
@@ -225,17 +219,26 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
     const uint32_t *cs = a.cell_start;
     const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
 
-    // per-row cell offsets and global slices (row r: dz = r/3 - 1, dy = r%3 - 1)
+    // cell populations of the 9 x wn region cells, loaded in parallel (row r: dz = r/3 - 1,
+    // dy = r%3 - 1), then per-row prefix sums and global slices
+    for (int e = tid; e < 9 * wn; e += kTileThreads) {
+        const int r = e / wn, i = e - r * wn;
+        const int yr = (cy + r % 3 - 1 + ny) % ny, zr = (cz + r / 3 - 1 + nz) % nz;
+        int x = x0 - 1 + i;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        const int c = x + nx * (yr + ny * zr);
+        S.seg_off[r][i + 1] = (int)(cs[c + 1] - cs[c]);
+    }
+    __syncthreads();
     if (tid < 9) {
         const int yr = (cy + tid % 3 - 1 + ny) % ny, zr = (cz + tid / 3 - 1 + nz) % nz;
         const int rowbase = nx * (yr + ny * zr);
         int off = 0;
-        for (int i = 0; i < wn; ++i) {
-            const int c = rowbase + (x0 - 1 + i + nx) % nx;
+        S.seg_off[tid][0] = 0;
+        for (int i = 1; i <= wn; ++i) {
+            off += S.seg_off[tid][i];
             S.seg_off[tid][i] = off;
-            off += (int)(cs[c + 1] - cs[c]);
         }
-        S.seg_off[tid][wn] = off;
         if (x0 >= 1 && x1 <= nx - 1) {           // one slice: cells x0-1 .. x1
             S.chunk_g[tid][0] = cs[rowbase + x0 - 1];
             S.chunk_n[tid][0] = cs[rowbase + x1 + 1] - cs[rowbase + x0 - 1];
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
                         if (n) {
                             asm volatile(
                                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-                                "[%3];" ::"r"(smem_u32(&S.srec[dst])),
+                                "[%3];" ::"r"(smem_u32(&S.stage[dst])),
                                 "l"(rec + S.chunk_g[r][h]), "r"(n * 16u), "r"(bar)
                                 : "memory");
                             dst += n;
@@ -320,24 +323,10 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
             }
         }
         if (ok) {
-            // float coordinates: unsigned fixed-point offsets from the lower corner of the
-            // region's first cell (x0-1, cy-1, cz-1).  The region is a run of consecutive cells
-            // that spans at most the whole periodic box, so every pair of neighbouring cells
-            // lies on the same side of this frame's seam (a frame centred on the tile would put
-            // its seam inside the region whenever W + 2 exceeds half the row).
-            const uint32_t o0 = (uint32_t)((((unsigned long long)((x0 - 1 + nx) % nx)) << 32) / (unsigned)nx);
-            const uint32_t o1 = (uint32_t)((((unsigned long long)((cy - 1 + ny) % ny)) << 32) / (unsigned)ny);
-            const uint32_t o2 = (uint32_t)((((unsigned long long)((cz - 1 + nz) % nz)) << 32) / (unsigned)nz);
-            for (int j = tid; j < region_n; j += kTileThreads) {
-                const uint4 r = S.srec[j];
-                S.spos[j] = make_float4((float)(r.x - o0) * a.box.L_2m32f[0], (float)(r.y - o1) * a.box.L_2m32f[1],
-                                        (float)(r.z - o2) * a.box.L_2m32f[2], __uint_as_float(r.w));
-            }
-            __syncthreads();
-            const float rc2_filter = a.nc.rc2_f * 1.0001f;
             const int t0 = S.row_base[4] + S.seg_off[4][1];
             const int t1 = S.row_base[4] + S.seg_off[4][wn - 1];
             float *Fn = (float *)a.Fn;
+            const float rc2 = a.nc.rc2_f;
             for (int j = t0 + tid; j < t1; j += kTileThreads) {
                 // region cell i (1 .. wn-2) holding target j: last i with seg_off[4][i] <= j - row_base[4]
                 const int jl = j - S.row_base[4];
@@ -348,27 +337,31 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
                     else hi = mid - 1;
                 }
                 const int i = lo;
-                const float4 pt = S.spos[j];
-                const uint4 ri = S.srec[j];
+                const uint4 ri = S.stage[j];
+                const float qi = __uint_as_float(ri.w);
                 float Fs[3] = {0.f, 0.f, 0.f}, Fc[3] = {0.f, 0.f, 0.f}, Us = 0.f, Uc = 0.f;
-                int cnt = 0;
-                for (int r = 0; r < 9; ++r) {
-                    const int k0 = S.row_base[r] + S.seg_off[r][i - 1];
-                    const int k1 = S.row_base[r] + S.seg_off[r][i + 2];
-                    for (int k = k0; k < k1; ++k) {
-                        const float4 pk = S.spos[k];
-                        const float dx = pt.x - pk.x, dy = pt.y - pk.y, dz = pt.z - pk.z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        if (r2 < rc2_filter && k != j) {
-                            S.list[cnt][tid] = (uint16_t)k;
-                            if (++cnt == kListCap) {
-                                flush_list(S, a.nc, a.box, cnt, ri, pt.w, Fs, Fc, Us, Uc);
-                                cnt = 0;
+                for (int r0 = 0; r0 < 9; r0 += 3) {
+                    int cnt = 0;
+                    for (int r = r0; r < r0 + 3; ++r) {
+                        const int rb = S.row_base[r];
+                        const int k0 = rb + S.seg_off[r][i - 1];
+                        const int k1 = rb + S.seg_off[r][i + 2];
+                        for (int k = k0; k < k1; ++k) {
+                            const uint4 rk = S.stage[k];
+                            const float d0 = (float)(int)(ri.x - rk.x) * a.box.L_2m32f[0];
+                            const float d1 = (float)(int)(ri.y - rk.y) * a.box.L_2m32f[1];
+                            const float d2 = (float)(int)(ri.z - rk.z) * a.box.L_2m32f[2];
+                            if (d0 * d0 + d1 * d1 + d2 * d2 < rc2 && k != j) {
+                                S.list[cnt][tid] = (uint16_t)k;
+                                if (++cnt == kListCap) {        // rare: more hits than the list holds
+                                    flush_list(S, a.nc, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
+                                    cnt = 0;
+                                }
                             }
                         }
                     }
+                    flush_list(S, a.nc, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
                 }
-                flush_list(S, a.nc, a.box, cnt, ri, pt.w, Fs, Fc, Us, Uc);
                 const uint32_t g = g_first + (uint32_t)(j - t0);
                 Fn[g] = Fs[0] - Fc[0];
                 Fn[a.N + g] = Fs[1] - Fc[1];
@@ -387,8 +380,7 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
             Ufall += U;
         }
     }
-    const double tot = block_sum_128((double)sumU + Ufall, S.red);
-    if (tid == 0) a.U_part[blockIdx.x] = tot;
+    warp_partial((double)sumU + Ufall, a.U_part, blockIdx.x);
 }
 
 inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
@@ -398,10 +390,11 @@ inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 
 int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
     if (prec == 1 && nx >= 3 && ny >= 3 && nz >= 3) {
-        // tile width: about 110 targets per CTA and about 1200 staged particles
+        // tile width: about 110 targets per CTA and about 1000 staged particles on average
+        // (the staging buffer holds 1280, so Poisson fluctuations rarely overflow it)
         const double occ = (double)a.N / (double)a.box.ncell;
         int Wt = (int)(110.0 / (occ > 1e-9 ? occ : 1e-9));
-        int Wcap = (int)(1200.0 / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
+        int Wcap = (int)(1000.0 / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
         if (Wt > Wcap) Wt = Wcap;
         if (Wt > kMaxTileW) Wt = kMaxTileW;
         if (Wt > nx - 2) Wt = nx - 2;
@@ -415,12 +408,12 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
         }
         const int nb = tiles_x * ny * nz;
         k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem), st>>>(a, W, tiles_x);
-        return nb;
+        return nb * kWarpsPerBlock;
     }
     const unsigned nb = blocks_for(a.N, kGlobalThreads);
     if (prec == 1) k_near_global<1><<<nb, kGlobalThreads, 0, st>>>(a);
     else k_near_global<0><<<nb, kGlobalThreads, 0, st>>>(a);
-    return (int)nb;
+    return (int)nb * kWarpsPerBlock;
 }
 
 }  // namespace rbsog

@@ -79,10 +79,10 @@ struct NearArgs {
     Box box;
     uint32_t N;
     void *Fn;                  // near force SoA [3][N] (float or double)
-    double *U_part;            // per-block near energy
+    double *U_part;            // near energy partials, one per warp
     DevCounters *ctr;          // error bits: skip the pair loops when the cell build overflowed
 };
-int launch_near(int prec, const NearArgs &a, cudaStream_t st);   // returns #blocks (energy partials)
+int launch_near(int prec, const NearArgs &a, cudaStream_t st);   // returns #energy partials (4 per block)
 struct RhoArgs {
     const void *rec;
     uint32_t N;

@@ -372,6 +372,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
     long long ncell = 1;
     for (int d = 0; d < 3; ++d) {
         bx.L[d] = p.box[d];
+        bx.invL[d] = 1.0 / p.box[d];
         int n = (int)std::floor(p.box[d] / p.r_c);
         bx.nc[d] = n >= 3 ? n : 1;
         ncell *= bx.nc[d];
@@ -453,7 +454,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         dalloc(c, &c->inject_m, 3 * (size_t)p.P) || dalloc(c, &c->coef, (size_t)p.P) ||
         dalloc(c, &c->partial, (size_t)c->G * 8 * p.P) || dalloc(c, &c->rho, (size_t)p.P) ||
         dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, (size_t)p.P) ||
-        dalloc(c, &c->U_part, std::max((n + 127) / 128, (size_t)bx.ncell) + 1) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
+        dalloc(c, &c->U_part, 4 * std::max((n + 127) / 128, (size_t)bx.ncell) + 4) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
         dalloc(c, &c->energy, 8) || dalloc(c, &c->ctr, 1)) {
         g_init_error = "device allocation failed";
         return bail(RBSOG_ENOMEM);
