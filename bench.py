@@ -32,7 +32,8 @@ from paper_2501_10946_gb300 import workloads as W  # noqa: E402
 
 METRIC = "RBSOG particle-steps/s at N=1e6"
 SMS = 152
-MUFU_PER_CLK_SM = 16            # sin/cos/ex2-class special-function results per clock per SM
+MUFU_PER_CLK_SM = 16            # sin/cos special-function results per clock per SM (measured 15.9)
+FP32_PER_CLK_SM = 128           # FP32 lanes per SM
 KERNELS_PER_STEP = 12
 # DRAM bytes per launch from the committed ncu capture of the current kernel (None: not captured)
 TRAFFIC = {}
@@ -173,27 +174,41 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
     return out
 
 
-def roofline(prof, w, steps_profiled, pk):
-    """Roofline of the dominant kernel group (rho or far: MUFU-bound sin/cos)."""
+def near_work(w, mtot):
+    """Algorithmic FP32 work of one near-field launch (27-cell candidates and in-range pairs)
+    for a decomposition of mtot Gaussians."""
+    nc = [max(int(math.floor(L / w.r_c)), 1) for L in w.box]
+    nc = [n if n >= 3 else 1 for n in nc]
+    ncell = nc[0] * nc[1] * nc[2]
+    dens = w.N / w.volume
+    candidates = w.N * 27.0 * w.N / ncell
+    pairs = w.N * (4.0 / 3.0) * math.pi * w.r_c ** 3 * dens
+    return 6.0 * candidates + (20.0 + 3.0 * mtot) * pairs
+
+
+def roofline(prof, w, steps_profiled, pk, mtot):
+    """Roofline of the dominant kernel group.  rho and far are bound by the special-function
+    unit (one sin and one cos per particle-mode pair); near by the FP32 pipe."""
     groups = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(groups, key=lambda k: groups[k][0])
     ms, n = groups[dom]
     avg_s = ms / n * 1e-3
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
-    peak = SMS * MUFU_PER_CLK_SM * sm_mhz * 1e6 / 1e9           # G MUFU results/s
     if dom in ("rho", "far"):
-        units = 2.0 * w.N * w.P                                   # one sin and one cos per (particle, mode)
+        units = 2.0 * w.N * w.P
+        peak = SMS * MUFU_PER_CLK_SM * sm_mhz * 1e6 / 1e9
+        basis = f"{SMS} SMs x {MUFU_PER_CLK_SM} MUFU/clk x {sm_mhz:.0f} MHz (sin+cos per particle-mode pair)"
     elif dom == "near":
-        lam = w.a_ws / w.kappa
-        pairs = w.N * (4.0 / 3.0) * math.pi * w.r_c ** 3 * w.N / w.volume
-        units = pairs * 6.0                                       # rsqrt, exp(-r/lambda) and ~4 exp per pair
+        units = near_work(w, mtot)
+        peak = SMS * FP32_PER_CLK_SM * sm_mhz * 1e6 / 1e9
+        basis = (f"{SMS} SMs x {FP32_PER_CLK_SM} FP32 lanes/clk x {sm_mhz:.0f} MHz (6 ops per 27-cell candidate, "
+                 f"20 + 3 M_tot per in-range pair)")
     else:
-        units = None
+        units, peak, basis = None, None, ""
     achieved = units / avg_s / 1e9 if units else None
     return {"kernel": dom, "bound": "alu", "unit": "Gop/s", "achieved": achieved, "peak": peak,
-            "frac": achieved / peak if achieved else None, "traffic": TRAFFIC.get(dom),
-            "peak_basis": f"{SMS} SMs x {MUFU_PER_CLK_SM} MUFU/clk x {sm_mhz:.0f} MHz",
-            "avg_launch_ms": avg_s * 1e3,
+            "frac": achieved / peak if achieved and peak else None, "traffic": TRAFFIC.get(dom),
+            "peak_basis": basis, "avg_launch_ms": avg_s * 1e3,
             "groups_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in groups.items()}}
 
 
@@ -284,7 +299,8 @@ def main():
             "config": {"workload": w.name, "N": w.N, "P": w.P, "Gamma": w.Gamma, "kappa": w.kappa,
                        "r_c_over_a": w.r_c / w.a_ws, "ensemble": w.ensemble, "integrator": "fp64",
                        "l2": "inputs larger than L2 (state + records > 129 MB)", "parallelism": f"replicas{ws}"}}
-    rf = roofline(res["profile"], w, 10, pk)
+    sog = R.rbsog_build_sog(w.a_ws / w.kappa, w.r_c, w.sog_eps)
+    rf = roofline(res["profile"], w, 10, pk, sog["M1"] + sog["M2"] + 1)
     rf["peak_source"] = pk_kind
     line["roofline"] = rf
     line["clocks"] = clocks.summary() if clocks else None

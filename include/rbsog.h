@@ -58,6 +58,7 @@ extern "C" {
 #define RBSOG_SOG_TABLE 2     /* sog_M1, sog_M2 given (e.g. a row of Table 1) */
 
 typedef struct rbsog_ctx rbsog_ctx;
+typedef struct rbsog_batch rbsog_batch;
 
 typedef struct rbsog_params {
     double box[3];          /* L_x, L_y, L_z (absolute lengths), each > 0 */
@@ -211,6 +212,67 @@ const char *rbsog_last_error(const rbsog_ctx *ctx);
 
 /* Release every device buffer and graph of ctx.  Synchronous.  NULL is a no-op. */
 void rbsog_free(rbsog_ctx *ctx);
+
+/* ---- Batches of independent systems ------------------------------------------------
+ * R systems, each a periodic Yukawa system with its own parameters (box, kappa, Gamma,
+ * r_c, P, seed, dt, ensemble), advanced together: every kernel of Algorithm 2's step is
+ * one launch over all systems and the step is replayed as one CUDA graph.  The systems'
+ * particles are concatenated in the caller's arrays: system r holds particles
+ * p_off[r] .. p_off[r+1]-1 (p_off[0] = 0, p_off[r+1] = p_off[r] + N[r]), and its P modes
+ * are entries m_off[r] .. m_off[r+1]-1 of the concatenated mode arrays.  Every system
+ * uses the FP32 path (precision must be RBSOG_FP32) and the same device.  The step and
+ * k-draw counters are shared, so system r draws the same modes and Langevin noise as a
+ * single context (rbsog_init) with params[r] after the same calls.  A device error in
+ * any system (cell overflow, sampler limit) fails the call for the whole batch. */
+
+/* Create a batch.  params: R parameter blocks; N: R particle counts (each >= 2, total
+ * < 2^31); q_host, m_host: host arrays of sum(N) charges and masses, copied.
+ * Synchronous.  On failure *out is NULL and rbsog_batch_last_error(NULL) holds the
+ * message (naming the first invalid system). */
+int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, const double *q_host,
+                     const double *m_host, rbsog_batch **out);
+
+/* Positions r and optional velocities v ([sum N][3] doubles, host or device) of all
+ * systems; as rbsog_set_state for each system.  Asynchronous on stream. */
+int rbsog_batch_set_state(rbsog_batch *b, const double *r, const double *v, void *stream);
+
+/* Positions and velocities ([sum N][3], caller order, host or device; either may be
+ * NULL) and the shared step counter.  Synchronous. */
+int rbsog_batch_get_state(rbsog_batch *b, double *r, double *v, uint64_t *step, void *stream);
+
+/* One force evaluation of every system: total forces ([sum N][3], caller order, host or
+ * device, may be NULL) and, if e is not NULL, R energy records.  Synchronous. */
+int rbsog_batch_forces(rbsog_batch *b, double *F, rbsog_energy *e, void *stream);
+
+/* Advance every system nsteps >= 0 steps (graph captured once on an internal stream,
+ * replayed on stream).  If e is not NULL, R energy records after the last step are
+ * written and the call is synchronous. */
+int rbsog_batch_step(rbsog_batch *b, int32_t nsteps, rbsog_energy *e, void *stream);
+
+/* Inject the next evaluation's modes for every system: sum(P) triples, host, not
+ * (0,0,0).  Synchronous. */
+int rbsog_batch_set_ksample(rbsog_batch *b, const int32_t *m_host);
+
+/* Modes (sum(P) triples) and coefficients (sum(P) doubles) of the last evaluation, host
+ * arrays, either may be NULL.  Synchronous. */
+int rbsog_batch_get_ksample(rbsog_batch *b, int32_t *m_host, double *coef_host);
+
+/* Layout: p_off and m_off (R + 1 entries each) and the structure-factor chunk (particles
+ * per block, R entries) of each system; any output may be NULL. */
+int rbsog_batch_layout(const rbsog_batch *b, int64_t *p_off, int64_t *m_off, int32_t *rho_chunk);
+
+/* Set the structure-factor chunk of each system (R entries, each >= 64 particles per
+ * block).  The chunk fixes the summation order of rho(k), so results are reproducible
+ * for a fixed chunk; it changes only the launch shape, not what is computed.  Drops the
+ * captured graph.  Synchronous. */
+int rbsog_batch_set_rho_chunk(rbsog_batch *b, const int32_t *rho_chunk);
+
+/* Message of the last failed call on b (or of the last failed rbsog_batch_init when b
+ * is NULL). */
+const char *rbsog_batch_last_error(const rbsog_batch *b);
+
+/* Release every device buffer and graph of b.  Synchronous.  NULL is a no-op. */
+void rbsog_batch_free(rbsog_batch *b);
 
 #ifdef __cplusplus
 }

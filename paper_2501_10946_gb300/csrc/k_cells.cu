@@ -34,10 +34,8 @@ __device__ __forceinline__ double frac01(double r, double invL) {
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(256) k_bin(BinArgs a) {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.N) return;
-    const uint32_t N = a.N;
+__device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
+    const uint32_t N = a.stride;
     double r[3] = {a.in.rx[k], a.in.ry[k], a.in.rz[k]};
     double v[3] = {a.in.vx[k], a.in.vy[k], a.in.vz[k]};
     const double invm = a.in.invm[k];
@@ -114,9 +112,33 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
     a.out.invm[k] = invm;
     a.out.q[k] = a.in.q[k];
     a.out.id[k] = id;
-    uint32_t c = cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);
+    uint32_t c = a.cell_base + cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);
     a.cell[k] = c;
     a.slot[k] = atomicAdd(&a.count[c], 1u);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_bin(BinArgs a) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < a.N) bin_body<PREC>(a, k);
+}
+
+// system of block b: the last r with items[r] <= b
+__device__ __forceinline__ int item_system(const uint32_t *items, int R, uint32_t b) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_bin_batch(const BinArgs *args, const uint32_t *items, int R) {
+    const int r = item_system(items, R, blockIdx.x);
+    const BinArgs &a = args[r];
+    const uint32_t k = (blockIdx.x - items[r]) * blockDim.x + threadIdx.x;
+    if (k < a.N) bin_body<1>(a, k);
 }
 
 __device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t *sh) {
@@ -248,10 +270,8 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_set_state(const double *r, const double *v, const double *q_user,
-                                                   const double *m_user, State rest, uint32_t N, Box box) {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
+__device__ __forceinline__ void set_state_body(const double *r, const double *v, const double *q_user,
+                                               const double *m_user, const State &rest, const Box &box, uint32_t k) {
     rest.rx[k] = wrap_coord(r[3 * (size_t)k], box.L[0], box.invL[0]);
     rest.ry[k] = wrap_coord(r[3 * (size_t)k + 1], box.L[1], box.invL[1]);
     rest.rz[k] = wrap_coord(r[3 * (size_t)k + 2], box.L[2], box.invL[2]);
@@ -263,17 +283,46 @@ __global__ void __launch_bounds__(256) k_set_state(const double *r, const double
     rest.id[k] = k;
 }
 
+__global__ void __launch_bounds__(256) k_set_state(const double *r, const double *v, const double *q_user,
+                                                   const double *m_user, State rest, uint32_t N, Box box) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) set_state_body(r, v, q_user, m_user, rest, box, k);
+}
+
+// Batched systems: the caller's arrays hold system r's particles at p_off .. p_off + N - 1.
+__global__ void __launch_bounds__(256) k_set_state_batch(const SysStateArgs *args, const uint32_t *items, int R,
+                                                         const double *r, const double *v) {
+    const int sys = item_system(items, R, blockIdx.x);
+    const SysStateArgs &a = args[sys];
+    const uint32_t k = (blockIdx.x - items[sys]) * blockDim.x + threadIdx.x;
+    if (k < a.N)
+        set_state_body(r + 3 * (size_t)a.p_off, v ? v + 3 * (size_t)a.p_off : nullptr, a.q_user, a.m_user, a.rest,
+                       a.box, k);
+}
+
 __global__ void k_reset_counters(DevCounters *ctr) {
     ctr->step = 0;
     ctr->err = 0;
 }
 
-__global__ void __launch_bounds__(256) k_get_state(State rest, uint32_t N, double *r_out, double *v_out) {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const size_t u = 3 * (size_t)rest.id[k];
+__device__ __forceinline__ void get_state_body(const State &rest, size_t base, uint32_t k, double *r_out,
+                                               double *v_out) {
+    const size_t u = 3 * (base + (size_t)rest.id[k]);
     if (r_out) { r_out[u] = rest.rx[k]; r_out[u + 1] = rest.ry[k]; r_out[u + 2] = rest.rz[k]; }
     if (v_out) { v_out[u] = rest.vx[k]; v_out[u + 1] = rest.vy[k]; v_out[u + 2] = rest.vz[k]; }
+}
+
+__global__ void __launch_bounds__(256) k_get_state(State rest, uint32_t N, double *r_out, double *v_out) {
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) get_state_body(rest, 0, k, r_out, v_out);
+}
+
+__global__ void __launch_bounds__(256) k_get_state_batch(const SysStateArgs *args, const uint32_t *items, int R,
+                                                         double *r_out, double *v_out) {
+    const int sys = item_system(items, R, blockIdx.x);
+    const SysStateArgs &a = args[sys];
+    const uint32_t k = (blockIdx.x - items[sys]) * blockDim.x + threadIdx.x;
+    if (k < a.N) get_state_body(a.rest, a.p_off, k, r_out, v_out);
 }
 
 inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
@@ -283,6 +332,10 @@ inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 
 void launch_bin(int prec, const BinArgs &a, cudaStream_t st) {
     if (prec == 1) k_bin<1><<<blocks_for(a.N, 256), 256, 0, st>>>(a);
     else k_bin<0><<<blocks_for(a.N, 256), 256, 0, st>>>(a);
+}
+
+void launch_bin_batch(const BinArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st) {
+    k_bin_batch<<<nblocks, 256, 0, st>>>(args, items, R);
 }
 
 void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int ncell, uint32_t N,
@@ -308,6 +361,19 @@ void launch_set_state(const double *r, const double *v, const double *q_user, co
                       uint32_t N, Box box, DevCounters *ctr, cudaStream_t st) {
     k_set_state<<<blocks_for(N, 256), 256, 0, st>>>(r, v, q_user, m_user, rest, N, box);
     k_reset_counters<<<1, 1, 0, st>>>(ctr);
+}
+
+uint32_t bin_batch_blocks(uint32_t N) { return blocks_for(N, 256); }
+
+void launch_set_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks,
+                            const double *r, const double *v, DevCounters *ctr, cudaStream_t st) {
+    k_set_state_batch<<<nblocks, 256, 0, st>>>(args, items, R, r, v);
+    k_reset_counters<<<1, 1, 0, st>>>(ctr);
+}
+
+void launch_get_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks, double *r_out,
+                            double *v_out, cudaStream_t st) {
+    k_get_state_batch<<<nblocks, 256, 0, st>>>(args, items, R, r_out, v_out);
 }
 
 void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st) {

@@ -52,10 +52,9 @@ __device__ __forceinline__ void rho_split(int P, int pass_base, int ML, int &ngr
 }
 
 template <int ML>
-__global__ void __launch_bounds__(kRhoThreads) k_rho32(RhoArgs a, int chunk) {
-    __shared__ uint4 sp[kRhoTile];
+__device__ __forceinline__ void rho32_body(const RhoArgs &a, int chunk, unsigned bx, unsigned by, uint4 *sp) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pass_base = blockIdx.y * 256 * ML;
+    const int pass_base = (int)by * 256 * ML;
     int ngroups, nsub;
     rho_split(a.P, pass_base, ML, ngroups, nsub);
     const int g = warp % ngroups, sub = warp / ngroups;
@@ -73,7 +72,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho32(RhoArgs a, int chunk) {
     float sre[ML], cre[ML], sim[ML], cim[ML];
 #pragma unroll
     for (int j = 0; j < ML; ++j) sre[j] = cre[j] = sim[j] = cim[j] = 0.f;
-    const uint32_t begin = (uint32_t)blockIdx.x * (uint32_t)chunk;
+    const uint32_t begin = (uint32_t)bx * (uint32_t)chunk;
     uint32_t end = begin + (uint32_t)chunk;
     if (end > a.N) end = a.N;
     const uint4 *rec = (const uint4 *)a.rec;
@@ -108,8 +107,35 @@ __global__ void __launch_bounds__(kRhoThreads) k_rho32(RhoArgs a, int chunk) {
 #pragma unroll
     for (int j = 0; j < ML; ++j)
         if (lidx[j] < a.P)
-            a.partial[((size_t)blockIdx.x * 8 + sub) * a.P + lidx[j]] =
+            a.partial[((size_t)bx * 8 + sub) * a.P + lidx[j]] =
                 make_double2((double)sre[j] - (double)cre[j], (double)sim[j] - (double)cim[j]);
+}
+
+template <int ML>
+__global__ void __launch_bounds__(kRhoThreads) k_rho32(RhoArgs a, int chunk) {
+    __shared__ uint4 sp[kRhoTile];
+    rho32_body<ML>(a, chunk, blockIdx.x, blockIdx.y, sp);
+}
+
+__device__ __forceinline__ int item_system(const uint32_t *items, int R, uint32_t b) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched systems: block -> (system, particle chunk, pass of 256 modes); a system has
+// G chunks x ceil(P/256) passes.
+__global__ void __launch_bounds__(kRhoThreads) k_rho_batch(const RhoArgs *args, const int *chunk,
+                                                           const uint32_t *items, int R) {
+    __shared__ uint4 sp[kRhoTile];
+    const int r = item_system(items, R, blockIdx.x);
+    const RhoArgs &a = args[r];
+    const unsigned local = blockIdx.x - items[r];
+    rho32_body<1>(a, chunk[r], local % (unsigned)a.G, local / (unsigned)a.G, sp);
 }
 
 __global__ void __launch_bounds__(kRhoThreads) k_rho64(RhoArgs a, int chunk) {
@@ -154,6 +180,7 @@ struct GTab32 {
     int4 m;      // m_x, m_y, m_z, Im(rho) as float bits
     float4 f;    // coef k_x, coef k_y, coef k_z, Re(rho)
 };
+static_assert(sizeof(GTab32) == kGTab32Bytes, "gather table entry size");
 struct GTab64 {
     int4 m;
     double ck[3];
@@ -164,10 +191,10 @@ struct GTab64 {
 // order, then warp 0 adds the 8 warp sums in order (fixed, deterministic).  Writes rho,
 // the gather table and u_l = coef_l |rho_l|^2 / 2 (summed by k_energy).
 template <int PREC>
-__global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
-    __shared__ double2 sh[8][32];
+__device__ __forceinline__ void rho_final_body(const RhoFinalArgs &a, int ML, unsigned bx, bool bump,
+                                               double2 (*sh)[32]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int l = blockIdx.x * 32 + lane;
+    const int l = (int)bx * 32 + lane;
     double re = 0.0, im = 0.0;
     if (l < a.P) {
         const int pass_base = (l / (256 * ML)) * 256 * ML;
@@ -208,10 +235,22 @@ __global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
             ((GTab64 *)a.gtab)[l] = t;
         }
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bump && threadIdx.x == 0) {
         a.ctr->draw += 1ull;
         a.ctr->inject = 0;
     }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
+    __shared__ double2 sh[8][32];
+    rho_final_body<PREC>(a, ML, blockIdx.x, blockIdx.x == 0, sh);
+}
+
+__global__ void __launch_bounds__(256) k_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int R) {
+    __shared__ double2 sh[8][32];
+    const int r = item_system(items, R, blockIdx.x);
+    rho_final_body<1>(args[r], 1, blockIdx.x - items[r], blockIdx.x == 0, sh);
 }
 
 // ------------------------------------------------------------------ far gather + kick
@@ -219,7 +258,7 @@ __global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
 // energy, caller-order outputs.
 template <int PREC>
 __device__ __forceinline__ double finish_particle(const FarArgs &a, uint32_t p, const double *Ff) {
-    const uint32_t N = a.N;
+    const uint32_t N = a.stride;
     double Fn[3], Ft[3];
     if (PREC == 1) {
         const float *fn = (const float *)a.Fn;
@@ -255,10 +294,8 @@ __device__ __forceinline__ double finish_particle(const FarArgs &a, uint32_t p, 
 // FP32: two particles per thread (p and p + 256) share each mode's table entry.  The
 // gather sums over modes whose phases are unrelated, so rounding of the phase scaling is
 // incoherent here and the argument needs no half-turn reduction (unlike rho).
-__global__ void __launch_bounds__(kFarThreads) k_far32(FarArgs a) {
-    __shared__ double shK[kFarThreads];
-    __shared__ __align__(16) GTab32 tab[kFarTile];
-    const uint32_t p0 = blockIdx.x * (2 * kFarThreads) + threadIdx.x;
+__device__ __forceinline__ void far32_body(const FarArgs &a, unsigned bx, GTab32 *tab, double *shK) {
+    const uint32_t p0 = bx * (2 * kFarThreads) + threadIdx.x;
     const uint32_t p1 = p0 + kFarThreads;
     const bool v0 = p0 < a.N, v1 = p1 < a.N;
     const uint4 r0 = v0 ? ((const uint4 *)a.rec)[p0] : make_uint4(0, 0, 0, 0);
@@ -307,7 +344,20 @@ __global__ void __launch_bounds__(kFarThreads) k_far32(FarArgs a) {
         K += finish_particle<1>(a, p1, Ff);
     }
     const double tot = block_reduce_sum<double>(K, shK);
-    if (threadIdx.x == 0) a.K_part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) a.K_part[bx] = tot;
+}
+
+__global__ void __launch_bounds__(kFarThreads) k_far32(FarArgs a) {
+    __shared__ double shK[kFarThreads];
+    __shared__ __align__(16) GTab32 tab[kFarTile];
+    far32_body(a, blockIdx.x, tab, shK);
+}
+
+__global__ void __launch_bounds__(kFarThreads) k_far_batch(const FarArgs *args, const uint32_t *items, int R) {
+    __shared__ double shK[kFarThreads];
+    __shared__ __align__(16) GTab32 tab[kFarTile];
+    const int r = item_system(items, R, blockIdx.x);
+    far32_body(args[r], blockIdx.x - items[r], tab, shK);
 }
 
 __global__ void __launch_bounds__(kFarThreads) k_far64(FarArgs a) {
@@ -349,8 +399,7 @@ __global__ void __launch_bounds__(kFarThreads) k_far64(FarArgs a) {
     if (threadIdx.x == 0) a.K_part[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(1024) k_energy(EnergyArgs a) {
-    __shared__ double sh[1024];
+__device__ __forceinline__ void energy_body(const EnergyArgs &a, double *sh) {
     double u = 0.0, k = 0.0;
     // fixed-order per-thread strides, then a fixed tree
     for (int i = threadIdx.x; i < a.nU; i += blockDim.x) u += a.U_part[i];
@@ -369,6 +418,16 @@ __global__ void __launch_bounds__(1024) k_energy(EnergyArgs a) {
         a.out[4] = U + Uf + a.Uself + K;
         if (a.advance_step) a.ctr->step += 1ull;
     }
+}
+
+__global__ void __launch_bounds__(1024) k_energy(EnergyArgs a) {
+    __shared__ double sh[1024];
+    energy_body(a, sh);
+}
+
+__global__ void __launch_bounds__(1024) k_energy_batch(const EnergyArgs *args) {
+    __shared__ double sh[1024];
+    energy_body(args[blockIdx.x], sh);
 }
 
 inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
@@ -416,5 +475,25 @@ int launch_far(int prec, const FarArgs &a, cudaStream_t st) {
 }
 
 void launch_energy(const EnergyArgs &a, cudaStream_t st) { k_energy<<<1, 1024, 0, st>>>(a); }
+
+uint32_t rho_batch_blocks(int G, int P) { return (uint32_t)G * (uint32_t)((P + 255) / 256); }
+uint32_t rho_final_batch_blocks(int P) { return (uint32_t)((P + 31) / 32); }
+uint32_t far_batch_blocks(uint32_t N) { return blocks_for(N, 2 * kFarThreads); }
+
+void launch_rho_batch(const RhoArgs *args, const int *chunk, const uint32_t *items, int R, uint32_t nblocks,
+                      cudaStream_t st) {
+    k_rho_batch<<<nblocks, kRhoThreads, 0, st>>>(args, chunk, items, R);
+}
+
+void launch_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int R, uint32_t nblocks,
+                            cudaStream_t st) {
+    k_rho_final_batch<<<nblocks, 256, 0, st>>>(args, items, R);
+}
+
+void launch_far_batch(const FarArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st) {
+    k_far_batch<<<nblocks, kFarThreads, 0, st>>>(args, items, R);
+}
+
+void launch_energy_batch(const EnergyArgs *args, int R, cudaStream_t st) { k_energy_batch<<<R, 1024, 0, st>>>(args); }
 
 }  // namespace rbsog

@@ -160,25 +160,33 @@ __device__ __forceinline__ void warp_partial(double v, double *U_part, unsigned 
     if ((threadIdx.x & 31) == 0) U_part[(size_t)blk * kWarpsPerBlock + (threadIdx.x >> 5)] = v;
 }
 
+// One block of the per-particle path: particles p0 + [0, 128) of this system (global
+// record indices p0 .. p0 + N - 1).
 template <int PREC>
-__global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
-    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void near_global_block(const NearArgs &a, uint32_t p0, unsigned blk) {
+    const uint32_t local = blk * blockDim.x + threadIdx.x;
     double U = 0.0;
-    if (p < a.N) {
+    if (local < a.N) {
+        const uint32_t p = p0 + local;
         const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
         if (PREC == 1) {
             float F[3] = {0.f, 0.f, 0.f};
             if (!overflow) near_one_f32(a, p, F, U);
             float *Fn = (float *)a.Fn;
-            Fn[p] = F[0]; Fn[a.N + p] = F[1]; Fn[2 * (size_t)a.N + p] = F[2];
+            Fn[p] = F[0]; Fn[a.stride + p] = F[1]; Fn[2 * (size_t)a.stride + p] = F[2];
         } else {
             double F[3] = {0.0, 0.0, 0.0};
             if (!overflow) near_one_f64(a, p, F, U);
             double *Fn = (double *)a.Fn;
-            Fn[p] = F[0]; Fn[a.N + p] = F[1]; Fn[2 * (size_t)a.N + p] = F[2];
+            Fn[p] = F[0]; Fn[a.stride + p] = F[1]; Fn[2 * (size_t)a.stride + p] = F[2];
         }
     }
-    warp_partial(U, a.U_part, blockIdx.x);
+    warp_partial(U, a.U_part, blk);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
+    near_global_block<PREC>(a, 0u, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- tiled (TMA) FP32 path
@@ -205,13 +213,11 @@ __device__ __forceinline__ void flush_list(const TileSmem &S, const NearConsts &
     }
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, int tiles_x) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileSmem &S = *reinterpret_cast<TileSmem *>(smem_raw);
+__device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk, TileSmem &S) {
     const int tid = threadIdx.x;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
-    const int tile = blockIdx.x % tiles_x;
-    const int rest = blockIdx.x / tiles_x;
+    const int tile = (int)(blk % (unsigned)tiles_x);
+    const int rest = (int)(blk / (unsigned)tiles_x);
     const int cy = rest % ny, cz = rest / ny;
     const int x0 = tile * W;
     const int x1 = min(x0 + W, nx);
@@ -364,8 +370,8 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
                 }
                 const uint32_t g = g_first + (uint32_t)(j - t0);
                 Fn[g] = Fs[0] - Fc[0];
-                Fn[a.N + g] = Fs[1] - Fc[1];
-                Fn[2 * (size_t)a.N + g] = Fs[2] - Fc[2];
+                Fn[a.stride + g] = Fs[1] - Fc[1];
+                Fn[2 * (size_t)a.stride + g] = Fs[2] - Fc[2];
                 sumU += Us - Uc;
             }
         }
@@ -376,44 +382,93 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
             float F[3] = {0.f, 0.f, 0.f};
             double U = 0.0;
             if (!overflow) near_one_f32(a, g, F, U);
-            Fn[g] = F[0]; Fn[a.N + g] = F[1]; Fn[2 * (size_t)a.N + g] = F[2];
+            Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
             Ufall += U;
         }
     }
-    warp_partial((double)sumU + Ufall, a.U_part, blockIdx.x);
+    warp_partial((double)sumU + Ufall, a.U_part, blk);
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, int tiles_x) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    near_tile_body(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem *>(smem_raw));
+}
+
+// Batched systems: block -> (system, local block); each system uses tiles or the
+// per-particle path as its geometry says.  geom.W doubles as the first global record
+// index of the system for the per-particle path.
+__global__ void __launch_bounds__(kTileThreads) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
+                                                            const uint32_t *items, int R) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid] <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const NearArgs &a = args[lo];
+    const NearBatchGeom g = geom[lo];
+    const unsigned blk = blockIdx.x - items[lo];
+    if (g.tiled) near_tile_body(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem *>(smem_raw));
+    else near_global_block<1>(a, (uint32_t)g.W, blk);
 }
 
 inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
-    const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
-    if (prec == 1 && nx >= 3 && ny >= 3 && nz >= 3) {
+void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks) {
+    const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
+    if (nx >= 3 && ny >= 3 && nz >= 3) {
         // tile width: about 110 targets per CTA and about 1000 staged particles on average
         // (the staging buffer holds 1280, so Poisson fluctuations rarely overflow it)
-        const double occ = (double)a.N / (double)a.box.ncell;
+        const double occ = (double)N / (double)box.ncell;
         int Wt = (int)(110.0 / (occ > 1e-9 ? occ : 1e-9));
         int Wcap = (int)(1000.0 / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
         if (Wt > Wcap) Wt = Wcap;
         if (Wt > kMaxTileW) Wt = kMaxTileW;
         if (Wt > nx - 2) Wt = nx - 2;
         if (Wt < 1) Wt = 1;
-        const int tiles_x = (nx + Wt - 1) / Wt;
-        const int W = (nx + tiles_x - 1) / tiles_x;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_near_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
-            attr_set = true;
-        }
-        const int nb = tiles_x * ny * nz;
-        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem), st>>>(a, W, tiles_x);
-        return nb * kWarpsPerBlock;
+        *tiles_x = (nx + Wt - 1) / Wt;
+        *W = (nx + *tiles_x - 1) / *tiles_x;
+        *tiled = 1;
+        *nblocks = (uint32_t)(*tiles_x) * (uint32_t)ny * (uint32_t)nz;
+    } else {
+        *tiled = 0;
+        *W = 0;
+        *tiles_x = 0;
+        *nblocks = blocks_for(N, kGlobalThreads);
     }
-    const unsigned nb = blocks_for(a.N, kGlobalThreads);
+}
+
+static void set_tile_smem_attr() {
+    static bool done = false;
+    if (!done) {
+        cudaFuncSetAttribute(k_near_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+        cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+        done = true;
+    }
+}
+
+int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
+    int tiled, W, tiles_x;
+    uint32_t nb;
+    near_geometry(a.box, a.N, &tiled, &W, &tiles_x, &nb);
+    if (prec == 1 && tiled) {
+        set_tile_smem_attr();
+        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem), st>>>(a, W, tiles_x);
+        return (int)nb * kWarpsPerBlock;
+    }
+    nb = blocks_for(a.N, kGlobalThreads);
     if (prec == 1) k_near_global<1><<<nb, kGlobalThreads, 0, st>>>(a);
     else k_near_global<0><<<nb, kGlobalThreads, 0, st>>>(a);
     return (int)nb * kWarpsPerBlock;
+}
+
+void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
+                       uint32_t nblocks, cudaStream_t st) {
+    set_tile_smem_attr();
+    k_near_batch<<<nblocks, kTileThreads, sizeof(TileSmem), st>>>(args, geom, items, R);
 }
 
 }  // namespace rbsog

@@ -25,9 +25,7 @@ __device__ __forceinline__ int alias_draw(U4 w, const double *prob, const int *a
     return (t < prob[i]) ? i : alias[i];
 }
 
-__global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= a.P) return;
+__device__ __forceinline__ void sample_body(const SampleArgs &a, int l) {
     int m[3];
     if (a.ctr->inject) {
         m[0] = a.inject_m[3 * l]; m[1] = a.inject_m[3 * l + 1]; m[2] = a.inject_m[3 * l + 2];
@@ -71,6 +69,23 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
     a.coef_out[l] = a.S / ((double)a.P * a.V * calF);
 }
 
+__global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < a.P) sample_body(a, l);
+}
+
+__global__ void __launch_bounds__(128) k_sample_batch(const SampleArgs *args, const uint32_t *items, int R) {
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid] <= blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const SampleArgs &a = args[lo];
+    const int l = (int)(blockIdx.x - items[lo]) * blockDim.x + threadIdx.x;
+    if (l < a.P) sample_body(a, l);
+}
+
 // S over the ball |k|^2 <= kmax2: block x = m_x slab; fixed-order reduction.
 __global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
     __shared__ double sh[256];
@@ -103,6 +118,12 @@ __global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
 
 void launch_sample(const SampleArgs &a, cudaStream_t st) {
     k_sample<<<(a.P + 127) / 128, 128, 0, st>>>(a);
+}
+
+uint32_t sample_batch_blocks(int P) { return (uint32_t)((P + 127) / 128); }
+
+void launch_sample_batch(const SampleArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st) {
+    k_sample_batch<<<nblocks, 128, 0, st>>>(args, items, R);
 }
 
 void launch_S(const SArgs &a, double *partials, cudaStream_t st) {

@@ -14,9 +14,11 @@ struct BinArgs {
     double dt, c1, kT;
     unsigned long long seed;
     DevCounters *ctr;
-    uint32_t N;
+    uint32_t N;               // particles of this system
+    uint32_t stride;          // SoA stride of F and s (N, or the batch total)
+    uint32_t cell_base;       // first global cell of this system (0 for a single system)
     Box box;
-    void *s;                  // fixed point [3][N]: uint32 (FP32) or uint64 (FP64)
+    void *s;                  // fixed point [3][stride]: uint32 (FP32) or uint64 (FP64)
     uint32_t *cell, *slot, *count;
 };
 void launch_bin(int prec, const BinArgs &a, cudaStream_t st);
@@ -77,8 +79,9 @@ struct NearArgs {
     const void *rec;
     const uint32_t *cell_start;
     Box box;
-    uint32_t N;
-    void *Fn;                  // near force SoA [3][N] (float or double)
+    uint32_t N;                // particles of this system
+    uint32_t stride;           // SoA stride of Fn (N, or the batch total)
+    void *Fn;                  // near force SoA [3][stride] (float or double), global particle index
     double *U_part;            // near energy partials, one per warp
     DevCounters *ctr;          // error bits: skip the pair loops when the cell build overflowed
 };
@@ -107,7 +110,8 @@ struct RhoFinalArgs {
 void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st);
 struct FarArgs {
     const void *rec;
-    uint32_t N;
+    uint32_t N;                // particles of this system
+    uint32_t stride;           // SoA stride of Fn and F
     int P;
     const void *gtab;
     const int *m;
@@ -133,5 +137,44 @@ struct EnergyArgs {
     int advance_step;
 };
 void launch_energy(const EnergyArgs &a, cudaStream_t st);
+
+// ---- batched systems: one launch per kernel over every system --------------------
+constexpr size_t kGTab32Bytes = 32;   // one FP32 gather-table entry (int4 + float4)
+// items[r] = first block of system r, items[R] = total blocks; argument arrays in device
+// memory hold each system's arguments with pointers already offset into the
+// concatenated buffers.
+void launch_bin_batch(const BinArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st);
+void launch_sample_batch(const SampleArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st);
+struct NearBatchGeom {
+    int tiled;                 // 1: shared-memory tiles, 0: per-particle global path
+    int W, tiles_x;
+};
+void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks);
+void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
+                       uint32_t nblocks, cudaStream_t st);
+void launch_rho_batch(const RhoArgs *args, const int *chunk, const uint32_t *items, int R, uint32_t nblocks,
+                      cudaStream_t st);
+void launch_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int R, uint32_t nblocks,
+                            cudaStream_t st);
+void launch_far_batch(const FarArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st);
+void launch_energy_batch(const EnergyArgs *args, int R, cudaStream_t st);
+// state of system r: rest buffer (offset), its charges and masses, first particle in the
+// caller's concatenated arrays
+struct SysStateArgs {
+    State rest;
+    const double *q_user, *m_user;
+    uint32_t N, p_off;
+    Box box;
+};
+void launch_set_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks,
+                            const double *r, const double *v, DevCounters *ctr, cudaStream_t st);
+void launch_get_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks, double *r_out,
+                            double *v_out, cudaStream_t st);
+// blocks one system takes in each batched kernel
+uint32_t bin_batch_blocks(uint32_t N);           // also set/get state
+uint32_t sample_batch_blocks(int P);
+uint32_t rho_batch_blocks(int G, int P);         // G particle chunks x ceil(P/256) mode passes
+uint32_t rho_final_batch_blocks(int P);
+uint32_t far_batch_blocks(uint32_t N);
 
 }  // namespace rbsog

@@ -22,6 +22,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "sog_host.h"
+#include "system.h"
 
 using namespace rbsog;
 
@@ -75,6 +76,202 @@ namespace {
 
 const double kPi = 3.14159265358979323846;
 
+
+// Vose's alias method, both work lists used as stacks filled in ascending index order.
+void vose(const std::vector<double> &w, std::vector<double> *prob, std::vector<int> *alias) {
+    const int n = (int)w.size();
+    double total = 0.0;
+    for (double x : w) total += x;
+    std::vector<double> sc(n);
+    for (int i = 0; i < n; ++i) sc[i] = (w[i] * n) / total;
+    prob->assign(n, 0.0);
+    alias->resize(n);
+    for (int i = 0; i < n; ++i) (*alias)[i] = i;
+    std::vector<int> small, large;
+    for (int i = 0; i < n; ++i) (sc[i] < 1.0 ? small : large).push_back(i);
+    while (!small.empty() && !large.empty()) {
+        int lo = small.back(); small.pop_back();
+        int g = large.back(); large.pop_back();
+        (*prob)[lo] = sc[lo];
+        (*alias)[lo] = g;
+        sc[g] = (sc[g] + sc[lo]) - 1.0;
+        (sc[g] < 1.0 ? small : large).push_back(g);
+    }
+    while (!large.empty()) { (*prob)[large.back()] = 1.0; large.pop_back(); }
+    while (!small.empty()) { (*prob)[small.back()] = 1.0; small.pop_back(); }
+}
+
+
+}  // namespace
+
+namespace rbsog {
+
+int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const double *m_host, HostSystem *hs,
+                 std::string *err) {
+    auto bad = [&](int code, const char *msg) {
+        *err = msg;
+        return code;
+    };
+    if (!q_host || !m_host) return bad(RBSOG_EINVAL, "q or m is NULL");
+    if (N < 2 || N > 0x7fffffffLL) return bad(RBSOG_EINVAL, "N must be in [2, 2^31)");
+    for (int d = 0; d < 3; ++d)
+        if (!(p.box[d] > 0)) return bad(RBSOG_EINVAL, "box lengths must be > 0");
+    if (!(p.kappa > 0)) return bad(RBSOG_EINVAL, "kappa must be > 0");
+    if (p.P < 1 || p.P > 4096) return bad(RBSOG_EINVAL, "P must be in [1, 4096]");
+    if (p.precision != RBSOG_FP64 && p.precision != RBSOG_FP32) return bad(RBSOG_EINVAL, "bad precision");
+    if (p.ensemble != RBSOG_NVE && p.ensemble != RBSOG_LANGEVIN) return bad(RBSOG_EINVAL, "bad ensemble");
+    if (p.sog_mode < 0 || p.sog_mode > 2) return bad(RBSOG_EINVAL, "bad sog_mode");
+    if (p.reserved != 0) return bad(RBSOG_EINVAL, "reserved must be 0");
+    const double Lmin = std::fmin(p.box[0], std::fmin(p.box[1], p.box[2]));
+    if (!(p.r_c > 0) || p.r_c > 0.5 * Lmin) return bad(RBSOG_EINVAL, "need 0 < r_c <= min(L)/2");
+    if (!(p.dt >= 0)) return bad(RBSOG_EINVAL, "dt must be >= 0");
+    for (int64_t i = 0; i < N; ++i)
+        if (!(m_host[i] > 0) || !std::isfinite(q_host[i])) return bad(RBSOG_EINVAL, "masses must be > 0");
+    HostSystem &h = *hs;
+    h.p = p;
+    h.N = (uint32_t)N;
+    h.V = (p.box[0] * p.box[1]) * p.box[2];
+    h.a_ws = p.a_ws > 0 ? p.a_ws : std::cbrt(3.0 * h.V / (4.0 * kPi * (double)N));
+    h.lam = h.a_ws / p.kappa;
+    h.kT = p.kT > 0 ? p.kT : 1.0 / (h.a_ws * p.Gamma);
+    if (!(h.kT > 0) || !std::isfinite(h.kT)) return bad(RBSOG_EINVAL, "k_B T must be > 0 (Gamma > 0 or kT > 0)");
+    if (!build_sog(h.lam, p.r_c, p.sog_eps, p.sog_mode, p.sog_M1, p.sog_M2, &h.sog, err)) return RBSOG_ENOCONV;
+    const int mt = h.sog.mtot();
+    if (mt > kMaxGauss) return bad(RBSOG_EUNSUPPORTED, "more than 40 Gaussians");
+    h.Q2 = 0.0;
+    h.qsum = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        h.Q2 += q_host[i] * q_host[i];
+        h.qsum += q_host[i];
+    }
+    if (!(h.Q2 > 0)) return bad(RBSOG_EINVAL, "all charges are zero");
+    // box and cells
+    Box &bx = h.box;
+    long long ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        bx.L[d] = p.box[d];
+        bx.invL[d] = 1.0 / p.box[d];
+        int n = (int)std::floor(p.box[d] / p.r_c);
+        bx.nc[d] = n >= 3 ? n : 1;
+        ncell *= bx.nc[d];
+        bx.L_2m32[d] = p.box[d] * 2.3283064365386963e-10;
+        bx.L_2m64[d] = p.box[d] * 5.421010862427522e-20;
+        bx.L_2m32f[d] = (float)bx.L_2m32[d];
+        bx.tpl[d] = 6.283185307179586 / p.box[d];
+    }
+    if (ncell > (1LL << 28)) return bad(RBSOG_EINVAL, "too many cells (box / r_c too large)");
+    bx.ncell = (int)ncell;
+    // SOG constants (Eqs. 37, 54, 56-57)
+    const double log2e = 1.4426950408889634;
+    NearConsts &nc = h.nconsts;
+    nc.mtot = mt;
+    nc.inv_lam = 1.0 / h.lam;
+    nc.rc2 = p.r_c * p.r_c;
+    nc.inv_lam_log2e_f = (float)(log2e / h.lam);
+    nc.inv_lam_f = (float)(1.0 / h.lam);
+    nc.rc2_f = (float)nc.rc2;
+    h.Fhat0 = 0.0;
+    h.sA.clear();
+    h.sb.clear();
+    double F0 = 0.0;
+    for (int i = 0; i < mt; ++i) {
+        const int m = -h.sog.M1 + i;
+        const double t = h.sog.t0 + m * h.sog.h;
+        const double w = (m == h.sog.M2) ? h.sog.w : 1.0;
+        const double b = std::exp(t);
+        const double f0 = sog_f(t, 0.0, h.lam);
+        const double a = h.sog.h * w * f0;
+        nc.a[i] = a;
+        nc.b[i] = b;
+        nc.c[i] = -2.0 * b * a;
+        nc.af[i] = (float)a;
+        nc.bl2f[i] = (float)(b * log2e);
+        nc.cf[i] = (float)(-2.0 * b * a);
+        const double A = h.sog.h * w * std::pow(kPi, 1.5) * f0 * std::exp(-1.5 * t);
+        h.sA.push_back(A);
+        h.sb.push_back(b);
+        h.Fhat0 += A;
+        F0 += a;
+    }
+    h.Uself = -0.5 * h.Q2 * F0;
+    h.Ufar0 = h.Fhat0 * h.qsum * h.qsum / (2.0 * h.V);
+    // sampling tables (Eq. 59): per-axis discrete Gaussians and the mixture over m
+    const double LN_1E18 = 41.44653167389282;
+    std::vector<double> mixw(mt);
+    h.ax_off.assign(3 * mt, 0);
+    h.ax_nmax.assign(3 * mt, 0);
+    h.ax_prob.clear();
+    h.ax_alias.clear();
+    for (int i = 0; i < mt; ++i) {
+        const double b = h.sb[i];
+        double prod = 1.0;
+        for (int a = 0; a < 3; ++a) {
+            const int nm = (int)std::ceil(std::sqrt(4.0 * b * LN_1E18) / bx.tpl[a]);
+            std::vector<double> g(2 * nm + 1);
+            double theta = 0.0;
+            for (int n = -nm; n <= nm; ++n) {
+                const double kk = bx.tpl[a] * n;
+                g[n + nm] = std::exp(-(kk * kk) / (4.0 * b));
+            }
+            for (double x : g) theta += x;
+            std::vector<double> pr;
+            std::vector<int> al;
+            vose(g, &pr, &al);
+            h.ax_off[3 * i + a] = (int)h.ax_prob.size();
+            h.ax_nmax[3 * i + a] = nm;
+            h.ax_prob.insert(h.ax_prob.end(), pr.begin(), pr.end());
+            h.ax_alias.insert(h.ax_alias.end(), al.begin(), al.end());
+            prod = prod * theta;
+        }
+        mixw[i] = h.sA[i] * prod;
+    }
+    vose(mixw, &h.mix_prob, &h.mix_alias);
+    return RBSOG_OK;
+}
+
+int system_S(HostSystem *hs, std::string *err) {
+    HostSystem &h = *hs;
+    SArgs a{};
+    a.mtot = h.sog.mtot();
+    double bmax = 0.0;
+    for (int i = 0; i < a.mtot; ++i) {
+        a.A[i] = h.sA[i];
+        a.inv4b[i] = 1.0 / (4.0 * h.sb[i]);
+        if (h.sb[i] > bmax) bmax = h.sb[i];
+    }
+    a.kmax2 = 4.0 * bmax * std::log(1e17);
+    for (int d = 0; d < 3; ++d) {
+        a.tpl[d] = h.box.tpl[d];
+        a.nmax[d] = (int)std::floor(std::sqrt(a.kmax2) / h.box.tpl[d]) + 1;
+    }
+    a.kTV = h.kT * h.V;
+    a.Q2 = h.Q2;
+    a.inv_lam2 = 1.0 / (h.lam * h.lam);
+    const int nb = 2 * a.nmax[0] + 1;
+    double *parts = nullptr;
+    cudaError_t e = cudaMalloc(&parts, nb * sizeof(double));
+    if (e != cudaSuccess) {
+        *err = std::string("CUDA error in alloc S: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? RBSOG_ENOMEM : RBSOG_ECUDA;
+    }
+    launch_S(a, parts, 0);
+    std::vector<double> hv(nb);
+    e = cudaMemcpy(hv.data(), parts, nb * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(parts);
+    if (e != cudaSuccess) {
+        *err = std::string("CUDA error in S kernel: ") + cudaGetErrorString(e);
+        return RBSOG_ECUDA;
+    }
+    double S = 0.0;
+    for (double x : hv) S += x;
+    h.S = S;
+    return RBSOG_OK;
+}
+
+}  // namespace rbsog
+
+namespace {
+
 int fail(rbsog_ctx *c, int code, const std::string &msg) {
     if (c) c->err = msg;
     else g_init_error = msg;
@@ -112,61 +309,10 @@ bool is_device_ptr(const void *ptr) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Vose's alias method, both work lists used as stacks filled in ascending index order.
-void vose(const std::vector<double> &w, std::vector<double> *prob, std::vector<int> *alias) {
-    const int n = (int)w.size();
-    double total = 0.0;
-    for (double x : w) total += x;
-    std::vector<double> sc(n);
-    for (int i = 0; i < n; ++i) sc[i] = (w[i] * n) / total;
-    prob->assign(n, 0.0);
-    alias->resize(n);
-    for (int i = 0; i < n; ++i) (*alias)[i] = i;
-    std::vector<int> small, large;
-    for (int i = 0; i < n; ++i) (sc[i] < 1.0 ? small : large).push_back(i);
-    while (!small.empty() && !large.empty()) {
-        int lo = small.back(); small.pop_back();
-        int g = large.back(); large.pop_back();
-        (*prob)[lo] = sc[lo];
-        (*alias)[lo] = g;
-        sc[g] = (sc[g] + sc[lo]) - 1.0;
-        (sc[g] < 1.0 ? small : large).push_back(g);
-    }
-    while (!large.empty()) { (*prob)[large.back()] = 1.0; large.pop_back(); }
-    while (!small.empty()) { (*prob)[small.back()] = 1.0; small.pop_back(); }
-}
-
-int build_sampler(rbsog_ctx *c) {
-    const double LN_1E18 = 41.44653167389282;
+int build_sampler(rbsog_ctx *c, const HostSystem &hs) {
     const int mt = c->sog.mtot();
-    std::vector<double> mixw(mt), axp;
-    std::vector<int> axa, off(3 * mt), nmax(3 * mt);
-    for (int i = 0; i < mt; ++i) {
-        const double b = c->sb[i];
-        double prod = 1.0;
-        for (int a = 0; a < 3; ++a) {
-            const int nm = (int)std::ceil(std::sqrt(4.0 * b * LN_1E18) / c->box.tpl[a]);
-            std::vector<double> g(2 * nm + 1);
-            double theta = 0.0;
-            for (int n = -nm; n <= nm; ++n) {
-                const double kk = c->box.tpl[a] * n;
-                g[n + nm] = std::exp(-(kk * kk) / (4.0 * b));
-            }
-            for (double x : g) theta += x;
-            std::vector<double> pr;
-            std::vector<int> al;
-            vose(g, &pr, &al);
-            off[3 * i + a] = (int)axp.size();
-            nmax[3 * i + a] = nm;
-            axp.insert(axp.end(), pr.begin(), pr.end());
-            axa.insert(axa.end(), al.begin(), al.end());
-            prod = prod * theta;
-        }
-        mixw[i] = c->sA[i] * prod;
-    }
-    std::vector<double> mp;
-    std::vector<int> ma;
-    vose(mixw, &mp, &ma);
+    const std::vector<double> &mp = hs.mix_prob, &axp = hs.ax_prob;
+    const std::vector<int> &ma = hs.mix_alias, &off = hs.ax_off, &nmax = hs.ax_nmax, &axa = hs.ax_alias;
     CK(dalloc(c, &c->mix_prob, mt), "alloc sampler");
     CK(dalloc(c, &c->mix_alias, mt), "alloc sampler");
     CK(dalloc(c, &c->ax_off, 3 * mt), "alloc sampler");
@@ -180,37 +326,6 @@ int build_sampler(rbsog_ctx *c) {
     CK(cudaMemcpy(c->ax_prob, axp.data(), axp.size() * sizeof(double), cudaMemcpyHostToDevice), "upload sampler");
     CK(cudaMemcpy(c->ax_alias, axa.data(), axa.size() * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
     c->tab = SamplerTables{mt, c->mix_prob, c->mix_alias, c->ax_off, c->ax_nmax, c->ax_prob, c->ax_alias};
-    return RBSOG_OK;
-}
-
-int compute_S(rbsog_ctx *c) {
-    SArgs a{};
-    a.mtot = c->sog.mtot();
-    double bmax = 0.0;
-    for (int i = 0; i < a.mtot; ++i) {
-        a.A[i] = c->sA[i];
-        a.inv4b[i] = 1.0 / (4.0 * c->sb[i]);
-        if (c->sb[i] > bmax) bmax = c->sb[i];
-    }
-    a.kmax2 = 4.0 * bmax * std::log(1e17);
-    for (int d = 0; d < 3; ++d) {
-        a.tpl[d] = c->box.tpl[d];
-        a.nmax[d] = (int)std::floor(std::sqrt(a.kmax2) / c->box.tpl[d]) + 1;
-    }
-    a.kTV = c->kT * c->V;
-    a.Q2 = c->Q2;
-    a.inv_lam2 = 1.0 / (c->lam * c->lam);
-    const int nb = 2 * a.nmax[0] + 1;
-    double *parts = nullptr;
-    CK(cudaMalloc(&parts, nb * sizeof(double)), "alloc S");
-    launch_S(a, parts, 0);
-    std::vector<double> h(nb);
-    cudaError_t e = cudaMemcpy(h.data(), parts, nb * sizeof(double), cudaMemcpyDeviceToHost);
-    cudaFree(parts);
-    CK(e, "S kernel");
-    double S = 0.0;
-    for (double x : h) S += x;
-    c->S = S;
     return RBSOG_OK;
 }
 
@@ -248,7 +363,8 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     BinArgs b{};
     b.in = c->rest; b.out = c->work; b.F = c->F; b.integrate = integrate;
     b.dt = c->p.dt; b.c1 = std::exp(-c->p.langevin_gamma * c->p.dt); b.kT = c->kT; b.seed = c->p.seed;
-    b.ctr = c->ctr; b.N = N; b.box = c->box; b.s = c->s; b.cell = c->cell; b.slot = c->slot; b.count = c->count;
+    b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.s = c->s; b.cell = c->cell;
+    b.slot = c->slot; b.count = c->count;
     { ProfScope ps(c, st, 0); launch_bin(prec, b, st); }
     { ProfScope ps(c, st, 1); launch_scan(c->count, c->tile_sums, c->cell_start, c->box.ncell, N, st); }
     {
@@ -266,7 +382,8 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
     { ProfScope ps(c, st, 4); launch_sample(sa, st); }
     NearArgs na{};
-    na.nc = c->nconsts; na.rec = c->rec; na.cell_start = c->cell_start; na.box = c->box; na.N = N; na.Fn = c->Fn;
+    na.nc = c->nconsts; na.rec = c->rec; na.cell_start = c->cell_start; na.box = c->box; na.N = N; na.stride = N;
+    na.Fn = c->Fn;
     na.U_part = c->U_part;
     na.ctr = c->ctr;
     { ProfScope ps(c, st, 5); c->nU = launch_near(prec, na, st); }
@@ -279,7 +396,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
     { ProfScope ps(c, st, 7); launch_rho_final(prec, rf, st); }
     FarArgs fa{};
-    fa.rec = c->rec; fa.N = N; fa.P = c->p.P; fa.gtab = c->gtab; fa.m = c->modes; fa.Fn = c->Fn; fa.F = c->F;
+    fa.rec = c->rec; fa.N = N; fa.stride = N; fa.P = c->p.P; fa.gtab = c->gtab; fa.m = c->modes; fa.Fn = c->Fn; fa.F = c->F;
     fa.st = c->rest; fa.integrate = integrate ? 1 : 0; fa.dt = c->p.dt; fa.K_part = c->K_part;
     fa.F_user = F_user; fa.Fn_user = Fn_user; fa.Ff_user = Ff_user;
     { ProfScope ps(c, st, 8); c->nK = launch_far(prec, fa, st); }
@@ -322,102 +439,20 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
     *out = nullptr;
     if (!params || !q_host || !m_host) return fail(nullptr, RBSOG_EINVAL, "params, q or m is NULL");
     const rbsog_params &p = *params;
-    if (N < 2 || N > 0x7fffffffLL) return fail(nullptr, RBSOG_EINVAL, "N must be in [2, 2^31)");
-    for (int d = 0; d < 3; ++d)
-        if (!(p.box[d] > 0)) return fail(nullptr, RBSOG_EINVAL, "box lengths must be > 0");
-    if (!(p.kappa > 0)) return fail(nullptr, RBSOG_EINVAL, "kappa must be > 0");
-    if (p.P < 1 || p.P > 4096) return fail(nullptr, RBSOG_EINVAL, "P must be in [1, 4096]");
-    if (p.precision != RBSOG_FP64 && p.precision != RBSOG_FP32) return fail(nullptr, RBSOG_EINVAL, "bad precision");
-    if (p.ensemble != RBSOG_NVE && p.ensemble != RBSOG_LANGEVIN) return fail(nullptr, RBSOG_EINVAL, "bad ensemble");
-    if (p.sog_mode < 0 || p.sog_mode > 2) return fail(nullptr, RBSOG_EINVAL, "bad sog_mode");
-    if (p.reserved != 0) return fail(nullptr, RBSOG_EINVAL, "reserved must be 0");
-    double Lmin = std::fmin(p.box[0], std::fmin(p.box[1], p.box[2]));
-    if (!(p.r_c > 0) || p.r_c > 0.5 * Lmin) return fail(nullptr, RBSOG_EINVAL, "need 0 < r_c <= min(L)/2");
-    if (!(p.dt >= 0)) return fail(nullptr, RBSOG_EINVAL, "dt must be >= 0");
-    for (int64_t i = 0; i < N; ++i)
-        if (!(m_host[i] > 0) || !std::isfinite(q_host[i])) return fail(nullptr, RBSOG_EINVAL, "masses must be > 0");
-
+    HostSystem hs;
+    {
+        std::string err;
+        const int code = setup_system(p, N, q_host, m_host, &hs, &err);
+        if (code != RBSOG_OK) return fail(nullptr, code, err);
+    }
     rbsog_ctx *c = new rbsog_ctx();
     c->p = p;
     c->N = (uint32_t)N;
     c->prec = p.precision;
-    c->V = (p.box[0] * p.box[1]) * p.box[2];
-    c->a_ws = p.a_ws > 0 ? p.a_ws : std::cbrt(3.0 * c->V / (4.0 * kPi * (double)N));
-    c->lam = c->a_ws / p.kappa;
-    c->kT = p.kT > 0 ? p.kT : 1.0 / (c->a_ws * p.Gamma);
-    if (!(c->kT > 0) || !std::isfinite(c->kT)) {
-        delete c;
-        return fail(nullptr, RBSOG_EINVAL, "k_B T must be > 0 (Gamma > 0 or kT > 0)");
-    }
-    std::string err;
-    if (!build_sog(c->lam, p.r_c, p.sog_eps, p.sog_mode, p.sog_M1, p.sog_M2, &c->sog, &err)) {
-        delete c;
-        return fail(nullptr, RBSOG_ENOCONV, err);
-    }
-    const int mt = c->sog.mtot();
-    if (mt > kMaxGauss) {
-        delete c;
-        return fail(nullptr, RBSOG_EUNSUPPORTED, "more than 40 Gaussians");
-    }
-    for (int64_t i = 0; i < N; ++i) {
-        c->Q2 += q_host[i] * q_host[i];
-        c->qsum += q_host[i];
-    }
-    if (!(c->Q2 > 0)) {
-        delete c;
-        return fail(nullptr, RBSOG_EINVAL, "all charges are zero");
-    }
-    // box and cells
-    Box &bx = c->box;
-    long long ncell = 1;
-    for (int d = 0; d < 3; ++d) {
-        bx.L[d] = p.box[d];
-        bx.invL[d] = 1.0 / p.box[d];
-        int n = (int)std::floor(p.box[d] / p.r_c);
-        bx.nc[d] = n >= 3 ? n : 1;
-        ncell *= bx.nc[d];
-        bx.L_2m32[d] = p.box[d] * 2.3283064365386963e-10;
-        bx.L_2m64[d] = p.box[d] * 5.421010862427522e-20;
-        bx.L_2m32f[d] = (float)bx.L_2m32[d];
-        bx.tpl[d] = 6.283185307179586 / p.box[d];
-    }
-    if (ncell > (1LL << 28)) {
-        delete c;
-        return fail(nullptr, RBSOG_EINVAL, "too many cells (box / r_c too large)");
-    }
-    bx.ncell = (int)ncell;
-    // SOG constants (Eqs. 37, 54, 56-57)
-    const double log2e = 1.4426950408889634;
-    NearConsts &nc = c->nconsts;
-    nc.mtot = mt;
-    nc.inv_lam = 1.0 / c->lam;
-    nc.rc2 = p.r_c * p.r_c;
-    nc.inv_lam_log2e_f = (float)(log2e / c->lam);
-    nc.inv_lam_f = (float)(1.0 / c->lam);
-    nc.rc2_f = (float)nc.rc2;
-    c->Fhat0 = 0.0;
-    double F0 = 0.0;
-    for (int i = 0; i < mt; ++i) {
-        const int m = -c->sog.M1 + i;
-        const double t = c->sog.t0 + m * c->sog.h;
-        const double w = (m == c->sog.M2) ? c->sog.w : 1.0;
-        const double b = std::exp(t);
-        const double f0 = sog_f(t, 0.0, c->lam);
-        const double a = c->sog.h * w * f0;
-        nc.a[i] = a;
-        nc.b[i] = b;
-        nc.c[i] = -2.0 * b * a;
-        nc.af[i] = (float)a;
-        nc.bl2f[i] = (float)(b * log2e);
-        nc.cf[i] = (float)(-2.0 * b * a);
-        const double A = c->sog.h * w * std::pow(kPi, 1.5) * f0 * std::exp(-1.5 * t);
-        c->sA.push_back(A);
-        c->sb.push_back(b);
-        c->Fhat0 += A;
-        F0 += a;
-    }
-    c->Uself = -0.5 * c->Q2 * F0;
-    c->Ufar0 = c->Fhat0 * c->qsum * c->qsum / (2.0 * c->V);
+    c->V = hs.V; c->a_ws = hs.a_ws; c->lam = hs.lam; c->kT = hs.kT; c->Q2 = hs.Q2; c->qsum = hs.qsum;
+    c->sog = hs.sog; c->box = hs.box; c->nconsts = hs.nconsts; c->sA = hs.sA; c->sb = hs.sb;
+    c->Fhat0 = hs.Fhat0; c->Uself = hs.Uself; c->Ufar0 = hs.Ufar0;
+    const Box &bx = c->box;
 
     // device
     int r = RBSOG_OK;
@@ -468,13 +503,17 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         g_init_error = "device initialisation failed";
         return bail(RBSOG_ECUDA);
     }
-    if ((r = build_sampler(c)) != RBSOG_OK) {
+    if ((r = build_sampler(c, hs)) != RBSOG_OK) {
         g_init_error = c->err;
         return bail(r);
     }
-    if ((r = compute_S(c)) != RBSOG_OK) {
-        g_init_error = c->err;
-        return bail(r);
+    {
+        std::string err;
+        if ((r = system_S(&hs, &err)) != RBSOG_OK) {
+            g_init_error = err;
+            return bail(r);
+        }
+        c->S = hs.S;
     }
     // a valid (zero) state so every call is defined before rbsog_set_state
     if (cudaMemset(c->stage_a, 0, n3 * sizeof(double)) != cudaSuccess) {

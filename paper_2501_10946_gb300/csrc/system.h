@@ -1,0 +1,35 @@
+// Host-side description of one simulated system (internal to the library): the SOG
+// decomposition, box and cell geometry, device constants and sampling tables, shared by
+// the single-system context and the batch of systems.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/rbsog.h"
+#include "common.cuh"
+#include "sog_host.h"
+
+namespace rbsog {
+
+struct HostSystem {
+    rbsog_params p{};
+    uint32_t N = 0;
+    double lam = 0, kT = 0, a_ws = 0, V = 0, Q2 = 0, qsum = 0, S = 0, Ufar0 = 0, Uself = 0, Fhat0 = 0;
+    SogDecomp sog;
+    Box box{};
+    NearConsts nconsts{};
+    std::vector<double> sA, sb;          // Fhat(k) = sum_m A_m exp(-k^2 / (4 b_m)), b_m = e^{t_m}
+    // sampling tables (alias tables of the Gaussian mixture and of each axis)
+    std::vector<double> mix_prob, ax_prob;
+    std::vector<int> mix_alias, ax_off, ax_nmax, ax_alias;
+};
+
+// Validate parameters and build everything host-side (no device work).  Returns an
+// RBSOG_* status and a message.
+int setup_system(const rbsog_params &p, int64_t N, const double *q, const double *m, HostSystem *hs,
+                 std::string *err);
+// S = sum_{k != 0} calF(k) Fhat(k) by a device lattice sum (synchronous).
+int system_S(HostSystem *hs, std::string *err);
+
+}  // namespace rbsog

@@ -46,7 +46,9 @@ _lib = None
 EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
            "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog",
            "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_rho_noalloc",
-           "rbsog_last_error", "rbsog_free"]
+           "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
+           "rbsog_batch_forces", "rbsog_batch_step", "rbsog_batch_set_ksample", "rbsog_batch_get_ksample",
+           "rbsog_batch_layout", "rbsog_batch_set_rho_chunk", "rbsog_batch_last_error", "rbsog_batch_free"]
 RBSOG_NPROF = 10
 
 
@@ -87,8 +89,22 @@ def load(build_if_missing: bool = True):
     L.rbsog_last_error.restype = C.c_char_p
     L.rbsog_free.argtypes = [vp]
     L.rbsog_free.restype = None
+    L.rbsog_batch_init.argtypes = [vp, i32, vp, vp, vp, C.POINTER(vp)]
+    L.rbsog_batch_set_state.argtypes = [vp, vp, vp, vp]
+    L.rbsog_batch_get_state.argtypes = [vp, vp, vp, C.POINTER(C.c_uint64), vp]
+    L.rbsog_batch_forces.argtypes = [vp, vp, vp, vp]
+    L.rbsog_batch_step.argtypes = [vp, i32, vp, vp]
+    L.rbsog_batch_set_ksample.argtypes = [vp, vp]
+    L.rbsog_batch_get_ksample.argtypes = [vp, vp, vp]
+    L.rbsog_batch_layout.argtypes = [vp, vp, vp, vp]
+    L.rbsog_batch_set_rho_chunk.argtypes = [vp, vp]
+    L.rbsog_batch_last_error.argtypes = [vp]
+    L.rbsog_batch_last_error.restype = C.c_char_p
+    L.rbsog_batch_free.argtypes = [vp]
+    L.rbsog_batch_free.restype = None
     for name in EXPORTS:
-        if name not in ("rbsog_profile_name", "rbsog_last_error", "rbsog_free"):
+        if name not in ("rbsog_profile_name", "rbsog_last_error", "rbsog_free", "rbsog_batch_last_error",
+                        "rbsog_batch_free"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -232,6 +248,89 @@ def rbsog_last_error(ctx=None) -> str:
 def rbsog_free(ctx):
     if ctx:
         load().rbsog_free(ctx)
+
+
+# ---- batches of independent systems ----------------------------------------------------
+
+def _bcheck(b, code):
+    if code != RBSOG_OK:
+        msg = load().rbsog_batch_last_error(b)
+        raise RbsogError(f"{STATUS.get(code, code)}: {msg.decode() if msg else ''}")
+
+
+def rbsog_batch_init(params, N, q, m):
+    """params: sequence of rbsog_params; N: particle counts; q, m: concatenated host arrays."""
+    R = len(params)
+    arr = (rbsog_params * R)(*params)
+    n = np.ascontiguousarray(N, dtype=np.int64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    out = C.c_void_p()
+    _bcheck(None, load().rbsog_batch_init(C.cast(arr, C.c_void_p), R, n.ctypes.data, q.ctypes.data,
+                                          m.ctypes.data, C.byref(out)))
+    return out.value
+
+
+def rbsog_batch_set_state(b, r, v=None, stream=None):
+    _bcheck(b, load().rbsog_batch_set_state(b, _ptr(r), _ptr(v), _stream(stream)))
+
+
+def rbsog_batch_get_state(b, r=None, v=None, stream=None) -> int:
+    step = C.c_uint64(0)
+    _bcheck(b, load().rbsog_batch_get_state(b, _ptr(r), _ptr(v), C.byref(step), _stream(stream)))
+    return step.value
+
+
+def _energies(e) -> list:
+    return [x.as_dict() for x in e]
+
+
+def rbsog_batch_forces(b, R: int, F=None, energy: bool = False, stream=None):
+    e = (rbsog_energy * R)()
+    _bcheck(b, load().rbsog_batch_forces(b, _ptr(F), C.cast(e, C.c_void_p) if energy else None, _stream(stream)))
+    return _energies(e) if energy else None
+
+
+def rbsog_batch_step(b, R: int, nsteps: int, energy: bool = False, stream=None):
+    e = (rbsog_energy * R)()
+    _bcheck(b, load().rbsog_batch_step(b, int(nsteps), C.cast(e, C.c_void_p) if energy else None,
+                                       _stream(stream)))
+    return _energies(e) if energy else None
+
+
+def rbsog_batch_set_ksample(b, m):
+    m = np.ascontiguousarray(m, dtype=np.int32).reshape(-1, 3)
+    _bcheck(b, load().rbsog_batch_set_ksample(b, m.ctypes.data))
+
+
+def rbsog_batch_get_ksample(b, Ptot: int):
+    m = np.zeros((Ptot, 3), dtype=np.int32)
+    coef = np.zeros(Ptot, dtype=np.float64)
+    _bcheck(b, load().rbsog_batch_get_ksample(b, m.ctypes.data, coef.ctypes.data))
+    return m, coef
+
+
+def rbsog_batch_layout(b, R: int):
+    p_off = np.zeros(R + 1, dtype=np.int64)
+    m_off = np.zeros(R + 1, dtype=np.int64)
+    chunk = np.zeros(R, dtype=np.int32)
+    _bcheck(b, load().rbsog_batch_layout(b, p_off.ctypes.data, m_off.ctypes.data, chunk.ctypes.data))
+    return p_off, m_off, chunk
+
+
+def rbsog_batch_set_rho_chunk(b, chunk):
+    chunk = np.ascontiguousarray(chunk, dtype=np.int32)
+    _bcheck(b, load().rbsog_batch_set_rho_chunk(b, chunk.ctypes.data))
+
+
+def rbsog_batch_last_error(b=None) -> str:
+    msg = load().rbsog_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def rbsog_batch_free(b):
+    if b:
+        load().rbsog_batch_free(b)
 
 
 def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int | None = None,

@@ -144,3 +144,21 @@ def small_system(N: int, L: float, seed: int, charge_mix: bool = False):
     r = rng.uniform(0.0, L, size=(N, 3))
     q = np.ones(N) if not charge_mix else rng.choice([-1.0, 1.0], size=N)
     return r, q
+
+
+def cfg_replicas(R: int = 256, seed: int = 401, steps: int = 500) -> list:
+    """Batched replica sweep: R independent YOCP systems at reduced density 1 (lengths in a),
+    N log-uniform in [500, 5e4], kappa uniform in [0.1, 3], Gamma log-uniform in [0.1, 200],
+    P in {64, 128, 256}, r_c = 3a, SOG tolerance 1e-6, dt = 0.01, NVE, FP32 forces."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(R):
+        N = int(round(math.exp(rng.uniform(math.log(500.0), math.log(5e4)))))
+        kappa = float(rng.uniform(0.1, 3.0))
+        Gamma = float(math.exp(rng.uniform(math.log(0.1), math.log(200.0))))
+        P = int(rng.choice([64, 128, 256]))
+        L = box_for_unit_a(N)
+        s = seed * 1000 + 4 * i
+        out.append(Workload(f"replica{i}_n{N}", N, (L, L, L), 1.0, kappa, Gamma, 3.0, 1e-6, P, 0.01, steps,
+                            "nve", 1.0, "uniform", s + 1, s + 2, s + 3))
+    return out

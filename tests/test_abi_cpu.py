@@ -122,3 +122,22 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(R._build, "LIB", str(tmp_path / "nope.so"))
     with pytest.raises(R.RbsogError):
         R.load(build_if_missing=False)
+
+
+def test_batch_rejects_fp64_and_names_the_bad_system():
+    """Host-side checks of rbsog_batch_init (no device call is reached)."""
+    w, p = base_params()
+    q, m = W.charges(w), W.masses(w)
+    with pytest.raises(R.RbsogError, match="EUNSUPPORTED"):
+        R.rbsog_batch_init([p], [w.N], q, m)
+    good = R.make_params(w, precision=R.RBSOG_FP32)
+    bad = R.make_params(w, precision=R.RBSOG_FP32)
+    bad.kappa = 0.0
+    with pytest.raises(R.RbsogError, match="EINVAL: system 1: kappa"):
+        R.rbsog_batch_init([good, bad], [w.N, w.N], np.concatenate([q, q]), np.concatenate([m, m]))
+    other_dev = R.make_params(w, precision=R.RBSOG_FP32, device=1)
+    with pytest.raises(R.RbsogError, match="same device"):
+        R.rbsog_batch_init([good, other_dev], [w.N, w.N], np.concatenate([q, q]), np.concatenate([m, m]))
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_batch_init([], [], q, m)
+    assert R.rbsog_batch_last_error(None)
