@@ -35,8 +35,9 @@ SMS = 152
 MUFU_PER_CLK_SM = 16            # sin/cos special-function results per clock per SM (measured 15.9)
 FP32_PER_CLK_SM = 128           # FP32 lanes per SM
 KERNELS_PER_STEP = 12
-# DRAM bytes per launch from the committed ncu capture of the current kernel (None: not captured)
-TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed
+# full-set ncu capture of the unchanged kernel at N = 1e6 (profiles/near_rho_far_yocp_uniform_n1e6.md)
+TRAFFIC = {"near": 16.645e6, "rho": 16.013e6, "far": 65.201e6}
 
 
 def peaks():
@@ -174,6 +175,69 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
     return out
 
 
+def batched_sweep(torch, R, steps, warmup, R_systems=256):
+    """Batched replica sweep: R_systems independent systems of uneven N in one graph per
+    step (autotuned shapes) against the same systems advanced one context at a time."""
+    ws = W.cfg_replicas(R_systems)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    params = [R.make_params(w, precision=R.RBSOG_FP32, device=dev.index) for w in ws]
+    r = torch.tensor(np.concatenate([W.positions(w) for w in ws]), device=dev, dtype=torch.float64)
+    v = torch.tensor(np.concatenate([W.velocities(w) for w in ws]), device=dev, dtype=torch.float64)
+    q = np.concatenate([W.charges(w) for w in ws])
+    m = np.concatenate([W.masses(w) for w in ws])
+    Ns = [w.N for w in ws]
+    Ntot = int(sum(Ns))
+    out = {"workload": f"yocp_replicas{R_systems}", "systems": R_systems, "N_total": Ntot, "N_min": min(Ns),
+           "N_max": max(Ns), "steps": steps, "warmup": warmup, "dtype": "f32"}
+    b = R.rbsog_batch_init(params, Ns, q, m)
+    try:
+        R.rbsog_batch_set_state(b, r, v, stream=stream)
+        near_t, rho_t = R.rbsog_batch_tune(b, 3, stream=stream)
+        out["shapes"] = {"near_target": near_t, "rho_target": rho_t}
+        R.rbsog_batch_step(b, R_systems, warmup, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R.rbsog_batch_step(b, R_systems, steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        out["value"] = Ntot * steps / (ms * 1e-3)
+        out["unit"] = "particle-steps/s"
+        out["ms_per_step"] = ms / steps
+        prof = R.rbsog_batch_profile(b, 3, stream=stream)
+        out["groups_ms_per_step"] = {k: round(t / 3, 4) for k, t in prof.items()}
+        out["gpu_launches_per_step"] = KERNELS_PER_STEP
+    finally:
+        R.rbsog_batch_free(b)
+    # the plain form: each system its own context, one after another
+    rh = r.cpu().numpy()
+    vh = v.cpu().numpy()
+    off = np.concatenate([[0], np.cumsum(Ns)])
+    tot_ms = 0.0
+    for i, w in enumerate(ws):
+        ctx = R.rbsog_init(params[i], w.N, W.charges(w), W.masses(w))
+        try:
+            R.rbsog_set_state(ctx, rh[off[i]:off[i + 1]], vh[off[i]:off[i + 1]], stream=stream)
+            R.rbsog_step(ctx, warmup, stream=stream)
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            R.rbsog_step(ctx, steps, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            tot_ms += e0.elapsed_time(e1)
+        finally:
+            R.rbsog_free(ctx)
+    out["plain"] = {"value": Ntot * steps / (tot_ms * 1e-3), "unit": "particle-steps/s",
+                    "ms_per_step": tot_ms / steps, "form": "one rbsog context per system, run one after another"}
+    out["speedup_vs_plain"] = out["value"] / out["plain"]["value"]
+    return out
+
+
 def near_work(w, mtot):
     """Algorithmic FP32 work of one near-field launch (27-cell candidates and in-range pairs)
     for a decomposition of mtot Gaussians."""
@@ -207,7 +271,7 @@ def roofline(prof, w, steps_profiled, pk, mtot):
         units, peak, basis = None, None, ""
     achieved = units / avg_s / 1e9 if units else None
     return {"kernel": dom, "bound": "alu", "unit": "Gop/s", "achieved": achieved, "peak": peak,
-            "frac": achieved / peak if achieved and peak else None, "traffic": TRAFFIC.get(dom),
+            "frac": achieved / peak if achieved and peak else None, "traffic": TRAFFIC.get(dom) if w.N == 1_000_000 else None,
             "peak_basis": basis, "avg_launch_ms": avg_s * 1e3,
             "groups_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in groups.items()}}
 
@@ -250,6 +314,7 @@ def main():
     ap.add_argument("--N", type=int, default=1_000_000)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     w = W.cfg_large(args.N)
@@ -309,6 +374,8 @@ def main():
     line["e2e"] = {"value": e2e_rate, "unit": "particle-steps/s", "h2d_bytes_per_step": res["e2e_h2d"],
                    "d2h_bytes_per_step": res["e2e_d2h"], "path": "rbsog_set_state(host) + rbsog_step(1) + "
                    "rbsog_get_state(host), pinned buffers"}
+    if not args.no_batch:
+        line["batched"] = batched_sweep(torch, R, args.steps, max(3, args.warmup))
     if not args.no_fp64:
         r64 = rbsog_replica(w, R.RBSOG_FP64, 3, 1, rank, torch, R, profile_steps=0, e2e_steps=0)
         line["fp64"] = {"value": w.N * 3 / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"] / 3, "steps": 3}

@@ -267,6 +267,28 @@ int rbsog_batch_layout(const rbsog_batch *b, int64_t *p_off, int64_t *m_off, int
  * captured graph.  Synchronous. */
 int rbsog_batch_set_rho_chunk(rbsog_batch *b, const int32_t *rho_chunk);
 
+/* Launch shapes of every system: near_target is the number of particles a near-field
+ * CTA aims at (the tile width in cells follows from each system's cell occupancy,
+ * capped by the shared-memory staging buffer; default 110), rho_target the particles
+ * per structure-factor block (each system's chunk is its N split evenly near that
+ * size; default 512).  The near-field shape changes only the order of the near-energy
+ * sum; the structure-factor shape the order of rho(k).  Drops the captured graph.
+ * Synchronous. */
+int rbsog_batch_set_shapes(rbsog_batch *b, double near_target, int32_t rho_target);
+
+/* Autotuner: times the near-field kernel and the structure-factor kernels (median of
+ * reps evaluations each) over a fixed set of candidate shapes on the current state,
+ * applies the fastest and returns it (either output may be NULL).  The step and draw
+ * counters are restored afterwards, so a batch tuned right after
+ * rbsog_batch_set_state follows the same trajectory as one given the same shapes
+ * with rbsog_batch_set_shapes.  Synchronous. */
+int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t *rho_target, void *stream);
+
+/* Advance nsteps >= 1 steps with eager launches and CUDA events around each kernel
+ * group (the groups of rbsog_profile_name); ms[RBSOG_NPROF] receives the summed
+ * milliseconds per group.  Synchronous. */
+int rbsog_batch_profile(rbsog_batch *b, int32_t nsteps, double *ms, void *stream);
+
 /* Message of the last failed call on b (or of the last failed rbsog_batch_init when b
  * is NULL). */
 const char *rbsog_batch_last_error(const rbsog_batch *b);

@@ -305,6 +305,14 @@ __global__ void k_reset_counters(DevCounters *ctr) {
     ctr->err = 0;
 }
 
+__global__ void k_reset_counters_n(DevCounters *ctr, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        ctr[i].step = 0;
+        ctr[i].err = 0;
+    }
+}
+
 __device__ __forceinline__ void get_state_body(const State &rest, size_t base, uint32_t k, double *r_out,
                                                double *v_out) {
     const size_t u = 3 * (base + (size_t)rest.id[k]);
@@ -366,9 +374,9 @@ void launch_set_state(const double *r, const double *v, const double *q_user, co
 uint32_t bin_batch_blocks(uint32_t N) { return blocks_for(N, 256); }
 
 void launch_set_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks,
-                            const double *r, const double *v, DevCounters *ctr, cudaStream_t st) {
+                            const double *r, const double *v, DevCounters *ctr, int nctr, cudaStream_t st) {
     k_set_state_batch<<<nblocks, 256, 0, st>>>(args, items, R, r, v);
-    k_reset_counters<<<1, 1, 0, st>>>(ctr);
+    k_reset_counters_n<<<(nctr + 255) / 256, 256, 0, st>>>(ctr, nctr);
 }
 
 void launch_get_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks, double *r_out,

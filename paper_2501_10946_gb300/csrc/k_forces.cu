@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
 __global__ void __launch_bounds__(256) k_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int R) {
     __shared__ double2 sh[8][32];
     const int r = item_system(items, R, blockIdx.x);
-    rho_final_body<1>(args[r], 1, blockIdx.x - items[r], blockIdx.x == 0, sh);
+    // each system advances its own draw counter (first block of the system)
+    rho_final_body<1>(args[r], 1, blockIdx.x - items[r], blockIdx.x == items[r], sh);
 }
 
 // ------------------------------------------------------------------ far gather + kick

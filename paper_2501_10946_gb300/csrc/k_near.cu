@@ -417,13 +417,14 @@ inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 
 
 }  // namespace
 
-void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks) {
+void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks, double target) {
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
     if (nx >= 3 && ny >= 3 && nz >= 3) {
-        // tile width: about 110 targets per CTA and about 1000 staged particles on average
-        // (the staging buffer holds 1280, so Poisson fluctuations rarely overflow it)
+        // tile width: about `target` (default 110) targets per CTA and about 1000 staged
+        // particles on average (the staging buffer holds 1280, so Poisson fluctuations
+        // rarely overflow it)
         const double occ = (double)N / (double)box.ncell;
-        int Wt = (int)(110.0 / (occ > 1e-9 ? occ : 1e-9));
+        int Wt = (int)(target / (occ > 1e-9 ? occ : 1e-9));
         int Wcap = (int)(1000.0 / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
         if (Wt > Wcap) Wt = Wcap;
         if (Wt > kMaxTileW) Wt = kMaxTileW;

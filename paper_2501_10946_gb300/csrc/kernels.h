@@ -149,7 +149,9 @@ struct NearBatchGeom {
     int tiled;                 // 1: shared-memory tiles, 0: per-particle global path
     int W, tiles_x;
 };
-void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks);
+// target: particles per CTA the tile width aims at (capped by the staging buffer)
+void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks,
+                   double target = 110.0);
 void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
                        uint32_t nblocks, cudaStream_t st);
 void launch_rho_batch(const RhoArgs *args, const int *chunk, const uint32_t *items, int R, uint32_t nblocks,
@@ -166,8 +168,9 @@ struct SysStateArgs {
     uint32_t N, p_off;
     Box box;
 };
+// also clears the step counter and error bits of ctr[0 .. nctr-1]
 void launch_set_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks,
-                            const double *r, const double *v, DevCounters *ctr, cudaStream_t st);
+                            const double *r, const double *v, DevCounters *ctr, int nctr, cudaStream_t st);
 void launch_get_state_batch(const SysStateArgs *args, const uint32_t *items, int R, uint32_t nblocks, double *r_out,
                             double *v_out, cudaStream_t st);
 // blocks one system takes in each batched kernel

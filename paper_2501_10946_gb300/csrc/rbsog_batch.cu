@@ -9,9 +9,9 @@
 // maps a block to (system, local block) through a prefix array of per-system block
 // counts and reads that system's arguments (pointers already offset) from a device
 // array, so the step is 12 launches whatever the number of systems, captured once as
-// a CUDA graph.  Each system keeps its own box, SOG decomposition, P, seed, time step
-// and ensemble; the step and draw counters are shared, so system r of a batch follows
-// the same Philox streams as a single context built with the same parameters.
+// a CUDA graph.  Each system keeps its own box, SOG decomposition, P, seed, time step,
+// ensemble and step/draw counters, so system r of a batch follows the same Philox
+// streams as a single context built with the same parameters.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,6 +36,8 @@ struct rbsog_batch {
     std::vector<HostSystem> sys;
     std::vector<uint32_t> p_off, c_off, m_off;         // R + 1 entries
     std::vector<int> rho_chunk;                        // particles per structure-factor block
+    double near_target = 110.0;                        // particles per near-field CTA the tiles aim at
+    size_t cap_part = 0, cap_upart = 0;                // allocated partial buffer entries
     // device buffers
     State rest{}, work{};
     double *q_user = nullptr, *m_user = nullptr, *stage_a = nullptr, *stage_b = nullptr;
@@ -51,7 +53,7 @@ struct rbsog_batch {
     unsigned char *gtab = nullptr;
     double *mix_prob = nullptr, *ax_prob = nullptr;
     int *mix_alias = nullptr, *ax_off = nullptr, *ax_nmax = nullptr, *ax_alias = nullptr;
-    DevCounters *ctr = nullptr;
+    DevCounters *ctr = nullptr;                        // [R + 1]: systems, then the cell-list status
     // per-system kernel arguments (device arrays) and block prefixes
     BinArgs *d_bin[2] = {nullptr, nullptr};            // [0] force evaluation only, [1] step
     FarArgs *d_far[2] = {nullptr, nullptr};
@@ -151,15 +153,33 @@ void partial_sizes(const rbsog_batch *b, size_t *part, size_t *upart, size_t *kp
         *part += (size_t)((h.N + c - 1) / c) * 8 * (size_t)h.p.P;
         int tiled, W, tiles_x;
         uint32_t nbn;
-        near_geometry(h.box, h.N, &tiled, &W, &tiles_x, &nbn);
+        near_geometry(h.box, h.N, &tiled, &W, &tiles_x, &nbn, b->near_target);
         *upart += 4 * (size_t)nbn;
         *kpart += far_batch_blocks(h.N);
     }
 }
 
+// Grow the partial buffers to the current shapes (old buffers stay allocated until free).
+int ensure_partials(rbsog_batch *b) {
+    size_t part, upart, kpart;
+    partial_sizes(b, &part, &upart, &kpart);
+    if (part > b->cap_part) {
+        BCK(balloc(b, &b->partial, part), "alloc partials");
+        b->cap_part = part;
+    }
+    if (upart + 4 > b->cap_upart) {
+        BCK(balloc(b, &b->U_part, upart + 4), "alloc partials");
+        b->cap_upart = upart + 4;
+    }
+    if (b->K_part == nullptr) BCK(balloc(b, &b->K_part, kpart + 1), "alloc partials");
+    return RBSOG_OK;
+}
+
 int check_errors(rbsog_batch *b) {
-    DevCounters h;
-    BCK(cudaMemcpy(&h, b->ctr, sizeof h, cudaMemcpyDeviceToHost), "read device status");
+    std::vector<DevCounters> hc(b->R + 1);
+    BCK(cudaMemcpy(hc.data(), b->ctr, hc.size() * sizeof(DevCounters), cudaMemcpyDeviceToHost), "read device status");
+    DevCounters h{};
+    for (const DevCounters &x : hc) h.err |= x.err;
     if (h.err & kErrCellOverflow) return bfail(b, RBSOG_EOVERFLOW, "a cell holds more than 4096 particles");
     if (h.err & kErrSampler) return bfail(b, RBSOG_ETIMEOUT, "k-sampler exceeded its attempt limit");
     if (h.err & kErrNearStage) return bfail(b, RBSOG_ETIMEOUT, "near-field staging wait exceeded its limit");
@@ -168,14 +188,15 @@ int check_errors(rbsog_batch *b) {
 
 int read_energies(rbsog_batch *b, rbsog_energy *e, cudaStream_t st) {
     std::vector<double> h(5 * (size_t)b->R);
-    DevCounters hc;
+    std::vector<DevCounters> hc(b->R);
     BCK(cudaMemcpyAsync(h.data(), b->energy, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read energy");
-    BCK(cudaMemcpyAsync(&hc, b->ctr, sizeof hc, cudaMemcpyDeviceToHost, st), "read counters");
+    BCK(cudaMemcpyAsync(hc.data(), b->ctr, hc.size() * sizeof(DevCounters), cudaMemcpyDeviceToHost, st),
+        "read counters");
     BCK(cudaStreamSynchronize(st), "synchronize");
     for (int r = 0; r < b->R; ++r) {
         const double *x = &h[5 * (size_t)r];
         e[r].U_near = x[0]; e[r].U_far = x[1]; e[r].U_self = x[2]; e[r].kinetic = x[3]; e[r].total = x[4];
-        e[r].step = hc.step;
+        e[r].step = hc[r].step;
     }
     return check_errors(b);
 }
@@ -218,7 +239,7 @@ int build_args(rbsog_batch *b) {
             a.c1 = std::exp(-p.langevin_gamma * p.dt);
             a.kT = h.kT;
             a.seed = p.seed;
-            a.ctr = b->ctr;
+            a.ctr = b->ctr + r;
             a.N = N;
             a.stride = b->Ntot;
             a.cell_base = b->c_off[r];
@@ -245,7 +266,7 @@ int build_args(rbsog_batch *b) {
             a.inv_lam2 = 1.0 / (h.lam * h.lam);
             a.S = h.S;
             a.V = h.V;
-            a.ctr = b->ctr;
+            a.ctr = b->ctr + r;
             a.inject_m = b->inject_m + 3 * mo;
             a.m_out = b->modes + 3 * mo;
             a.coef_out = b->coef + mo;
@@ -253,7 +274,7 @@ int build_args(rbsog_batch *b) {
         // near field: global records and forces, this system's cell range
         int tiled, W, tiles_x;
         uint32_t nbn;
-        near_geometry(h.box, N, &tiled, &W, &tiles_x, &nbn);
+        near_geometry(h.box, N, &tiled, &W, &tiles_x, &nbn, b->near_target);
         geom[r] = NearBatchGeom{tiled, tiled ? W : (int)po, tiles_x};
         {
             NearArgs &a = na[r];
@@ -265,7 +286,7 @@ int build_args(rbsog_batch *b) {
             a.stride = b->Ntot;
             a.Fn = b->Fn;
             a.U_part = b->U_part + u_off;
-            a.ctr = b->ctr;
+            a.ctr = b->ctr + b->R;   // cell-list status (overflow is detected by the global sort)
         }
         // structure factor and its reduction
         const int chunk = b->rho_chunk[r];
@@ -290,7 +311,7 @@ int build_args(rbsog_batch *b) {
             a.rho = b->rho + mo;
             a.gtab = b->gtab + kGTab32Bytes * mo;
             a.Ufar = b->Ufar + mo;
-            a.ctr = b->ctr;
+            a.ctr = b->ctr + r;
         }
         const uint32_t nbf = far_batch_blocks(N);
         for (int k = 0; k < 2; ++k) {
@@ -318,8 +339,8 @@ int build_args(rbsog_batch *b) {
             e.Ufar0 = h.Ufar0;
             e.Uself = h.Uself;
             e.out = b->energy + 5 * (size_t)r;
-            e.ctr = b->ctr;
-            e.advance_step = (k == 1 && r == 0) ? 1 : 0;
+            e.ctr = b->ctr + r;
+            e.advance_step = k;
         }
         ss[r] = SysStateArgs{offset_state(b->rest, po), b->q_user + po, b->m_user + po, N, (uint32_t)po, h.box};
         const uint32_t cnt[6] = {bin_batch_blocks(N), sample_batch_blocks(P), nbn, rho_batch_blocks(G, P),
@@ -357,23 +378,69 @@ int build_args(rbsog_batch *b) {
 
 const uint32_t *items_of(const rbsog_batch *b, int j) { return b->d_items + (size_t)j * (b->R + 1); }
 
-// One force evaluation (set 0) or one step (set 1) of every system.
-int enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far) {
+// One force evaluation (set 0) or one step (set 1) of every system.  With ev (11 events)
+// the kernel groups bin, scan, sort, gather, sample, near, rho, rho_final, far, energy
+// are bracketed by ev[g] and ev[g + 1].
+int enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far, cudaEvent_t *ev = nullptr) {
     const int R = b->R;
+    auto mark = [&](int g) {
+        if (ev) cudaEventRecord(ev[g], st);
+    };
+    mark(0);
     launch_bin_batch(b->d_bin[set], items_of(b, kItBin), R, b->nb[kItBin], st);
+    mark(1);
     launch_scan(b->count, b->tile_sums, b->cell_start, b->Ctot, b->Ntot, st);
-    launch_scatter_sort(b->cell, b->slot, b->cell_start, b->work.id, b->Ntot, b->Ctot, b->keys, b->perm_src, b->ctr,
-                        st);
+    mark(2);
+    launch_scatter_sort(b->cell, b->slot, b->cell_start, b->work.id, b->Ntot, b->Ctot, b->keys, b->perm_src,
+                        b->ctr + R, st);
+    mark(3);
     GatherArgs g{};
     g.in = b->work; g.out = b->rest; g.perm_src = b->perm_src; g.s = b->s; g.rec = b->rec; g.N = b->Ntot;
     launch_gather(RBSOG_FP32, g, st);
+    mark(4);
     launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
+    mark(5);
     launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
+    mark(6);
     launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], st);
+    mark(7);
     launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], st);
+    mark(8);
     launch_far_batch(far ? far : b->d_far[set], items_of(b, kItFar), R, b->nb[kItFar], st);
+    mark(9);
     launch_energy_batch(b->d_energy[set], R, st);
+    mark(10);
     BCK(cudaGetLastError(), "kernel launch");
+    return RBSOG_OK;
+}
+
+struct EventSet {
+    cudaEvent_t ev[11] = {};
+    bool ok = true;
+    EventSet() {
+        for (auto &e : ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    }
+    ~EventSet() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    float ms(int g0, int g1) const {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[g0], ev[g1]);
+        return t;
+    }
+};
+
+// Apply a near tile target and a structure-factor target to every system.
+int apply_shapes(rbsog_batch *b, double near_target, int rho_target) {
+    b->near_target = near_target;
+    for (int r = 0; r < b->R; ++r) b->rho_chunk[r] = chunk_for(b->sys[r].N, rho_target);
+    if (int c = ensure_partials(b)) return c;
+    if (int c = build_args(b)) return c;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
     return RBSOG_OK;
 }
 
@@ -444,7 +511,7 @@ int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, co
         balloc(b, &b->cell_start, (size_t)b->Ctot + 1) || balloc(b, &b->perm_src, n) || balloc(b, &b->keys, n) ||
         balloc(b, &b->modes, 3 * P) || balloc(b, &b->inject_m, 3 * P) || balloc(b, &b->coef, P) ||
         balloc(b, &b->rho, P) || balloc(b, &b->gtab, kGTab32Bytes * P) || balloc(b, &b->Ufar, P) ||
-        balloc(b, &b->energy, 5 * (size_t)R + 3) || balloc(b, &b->ctr, 1))
+        balloc(b, &b->energy, 5 * (size_t)R + 3) || balloc(b, &b->ctr, (size_t)R + 1))
         return bail(RBSOG_ENOMEM, "device allocation failed");
     // sampling tables, concatenated system by system
     std::vector<double> mp, axp;
@@ -463,7 +530,7 @@ int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, co
         cudaMemcpy(b->q_user, qv.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->m_user, mv.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->count, 0, sizeof(uint32_t) * (size_t)b->Ctot) != cudaSuccess ||
-        cudaMemset(b->ctr, 0, sizeof(DevCounters)) != cudaSuccess ||
+        cudaMemset(b->ctr, 0, sizeof(DevCounters) * ((size_t)R + 1)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(RBSOG_ECUDA, "device initialisation failed");
     for (int r = 0; r < R; ++r) {
@@ -471,17 +538,12 @@ int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, co
         const int code = system_S(&b->sys[r], &err);
         if (code != RBSOG_OK) return bail(code, err);
     }
-    {
-        size_t part, upart, kpart;
-        partial_sizes(b, &part, &upart, &kpart);
-        if (balloc(b, &b->partial, part) || balloc(b, &b->U_part, upart + 4) || balloc(b, &b->K_part, kpart + 1))
-            return bail(RBSOG_ENOMEM, "device allocation failed (partials)");
-    }
+    if (ensure_partials(b) != RBSOG_OK) return bail(RBSOG_ENOMEM, "device allocation failed (partials)");
     const int code = build_args(b);
     if (code != RBSOG_OK) return bail(code, "");
     // a valid (zero) state so every call is defined before rbsog_batch_set_state
     if (cudaMemset(b->stage_a, 0, n3 * sizeof(double)) != cudaSuccess) return bail(RBSOG_ECUDA, "device initialisation failed");
-    launch_set_state_batch(b->d_state, items_of(b, kItBin), R, b->nb[kItBin], b->stage_a, nullptr, b->ctr, 0);
+    launch_set_state_batch(b->d_state, items_of(b, kItBin), R, b->nb[kItBin], b->stage_a, nullptr, b->ctr, R + 1, 0);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(RBSOG_ECUDA, "device initialisation failed");
     *out = b;
     return RBSOG_OK;
@@ -500,7 +562,7 @@ int rbsog_batch_set_state(rbsog_batch *b, const double *r, const double *v, void
         BCK(cudaMemcpyAsync(b->stage_b, v, bytes, cudaMemcpyDefault, st), "copy v");
         vd = b->stage_b;
     }
-    launch_set_state_batch(b->d_state, items_of(b, kItBin), b->R, b->nb[kItBin], rd, vd, b->ctr, st);
+    launch_set_state_batch(b->d_state, items_of(b, kItBin), b->R, b->nb[kItBin], rd, vd, b->ctr, b->R + 1, st);
     BCK(cudaGetLastError(), "set_state");
     b->force_valid = false;
     return RBSOG_OK;
@@ -581,7 +643,8 @@ int rbsog_batch_set_ksample(rbsog_batch *b, const int32_t *m_host) {
     BCK(cudaDeviceSynchronize(), "synchronize");
     BCK(cudaMemcpy(b->inject_m, m_host, 3 * sizeof(int32_t) * (size_t)b->Ptot, cudaMemcpyHostToDevice), "copy modes");
     int one = 1;
-    BCK(cudaMemcpy(&b->ctr->inject, &one, sizeof(int), cudaMemcpyHostToDevice), "set inject flag");
+    for (int r = 0; r < b->R; ++r)
+        BCK(cudaMemcpy(&b->ctr[r].inject, &one, sizeof(int), cudaMemcpyHostToDevice), "set inject flag");
     return RBSOG_OK;
 }
 
@@ -610,11 +673,8 @@ int rbsog_batch_set_rho_chunk(rbsog_batch *b, const int32_t *rho_chunk) {
     for (int r = 0; r < b->R; ++r)
         if (rho_chunk[r] < 64) return bfail(b, RBSOG_EINVAL, "rho_chunk must be >= 64");
     BCK(cudaDeviceSynchronize(), "synchronize");
-    size_t part_old, part_new, u, k;
-    partial_sizes(b, &part_old, &u, &k);
     for (int r = 0; r < b->R; ++r) b->rho_chunk[r] = rho_chunk[r];
-    partial_sizes(b, &part_new, &u, &k);
-    if (part_new > part_old) BCK(balloc(b, &b->partial, part_new), "alloc partials");
+    if (int c = ensure_partials(b)) return c;
     int code = build_args(b);
     if (code != RBSOG_OK) return code;
     if (b->graph) {
@@ -622,6 +682,78 @@ int rbsog_batch_set_rho_chunk(rbsog_batch *b, const int32_t *rho_chunk) {
         b->graph = nullptr;
     }
     return RBSOG_OK;
+}
+
+int rbsog_batch_profile(rbsog_batch *b, int32_t nsteps, double *ms, void *stream) {
+    if (!b || !ms || nsteps < 1) return bfail(b, RBSOG_EINVAL, "batch or ms is NULL, or nsteps < 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    EventSet es;
+    if (!es.ok) return bfail(b, RBSOG_ECUDA, "event creation failed");
+    for (int g = 0; g < RBSOG_NPROF; ++g) ms[g] = 0.0;
+    if (!b->force_valid) {
+        if (int c = enqueue(b, st, 0, nullptr)) return c;
+        b->force_valid = true;
+    }
+    for (int i = 0; i < nsteps; ++i) {
+        if (int c = enqueue(b, st, 1, nullptr, es.ev)) return c;
+        BCK(cudaStreamSynchronize(st), "synchronize");
+        for (int g = 0; g < RBSOG_NPROF; ++g) ms[g] += es.ms(g, g + 1);
+    }
+    return check_errors(b);
+}
+
+int rbsog_batch_set_shapes(rbsog_batch *b, double near_target, int32_t rho_target) {
+    if (!b) return bfail(b, RBSOG_EINVAL, "batch is NULL");
+    if (!(near_target >= 8.0 && near_target <= 4096.0) || rho_target < 64)
+        return bfail(b, RBSOG_EINVAL, "need 8 <= near_target <= 4096 and rho_target >= 64");
+    BCK(cudaDeviceSynchronize(), "synchronize");
+    return apply_shapes(b, near_target, rho_target);
+}
+
+int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t *rho_target, void *stream) {
+    if (!b || reps < 1) return bfail(b, RBSOG_EINVAL, "batch is NULL or reps < 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    EventSet es;
+    if (!es.ok) return bfail(b, RBSOG_EINVAL, "event creation failed");
+    // the counters are restored afterwards, so the tuning evaluations leave no trace in
+    // the draws; the next step re-evaluates the forces
+    std::vector<DevCounters> saved(b->R + 1);
+    BCK(cudaStreamSynchronize(st), "synchronize");
+    BCK(cudaMemcpy(saved.data(), b->ctr, saved.size() * sizeof(DevCounters), cudaMemcpyDeviceToHost), "save counters");
+    const double near_c[] = {48.0, 80.0, 110.0, 160.0};
+    const int rho_c[] = {256, 512, 1024, 2048};
+    double best_near = b->near_target, best_near_ms = 1e30;
+    int best_rho = 512;
+    double best_rho_ms = 1e30;
+    int code = RBSOG_OK;
+    for (int ci = 0; ci < 4 && code == RBSOG_OK; ++ci) {
+        // near field and structure factor are independent: tune both from one sweep
+        if ((code = apply_shapes(b, near_c[ci], rho_c[ci])) != RBSOG_OK) break;
+        std::vector<double> tn, tr;
+        for (int i = 0; i <= reps && code == RBSOG_OK; ++i) {
+            if ((code = enqueue(b, st, 0, nullptr, es.ev)) != RBSOG_OK) break;
+            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                code = bcuda_fail(b, cudaGetLastError(), "synchronize");
+                break;
+            }
+            if (i == 0) continue;   // first run after a shape change: warm-up
+            tn.push_back(es.ms(5, 6));
+            tr.push_back(es.ms(6, 8));
+        }
+        if (code != RBSOG_OK) break;
+        std::sort(tn.begin(), tn.end());
+        std::sort(tr.begin(), tr.end());
+        if (tn[tn.size() / 2] < best_near_ms) { best_near_ms = tn[tn.size() / 2]; best_near = near_c[ci]; }
+        if (tr[tr.size() / 2] < best_rho_ms) { best_rho_ms = tr[tr.size() / 2]; best_rho = rho_c[ci]; }
+    }
+    if (code == RBSOG_OK) code = apply_shapes(b, best_near, best_rho);
+    cudaError_t e = cudaMemcpy(b->ctr, saved.data(), saved.size() * sizeof(DevCounters), cudaMemcpyHostToDevice);
+    b->force_valid = false;
+    if (code != RBSOG_OK) return code;
+    BCK(e, "restore counters");
+    if (near_target) *near_target = best_near;
+    if (rho_target) *rho_target = best_rho;
+    return check_errors(b);
 }
 
 const char *rbsog_batch_last_error(const rbsog_batch *b) { return b ? b->err.c_str() : g_batch_init_error.c_str(); }

@@ -48,7 +48,8 @@ EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_forces", "
            "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_rho_noalloc",
            "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
            "rbsog_batch_forces", "rbsog_batch_step", "rbsog_batch_set_ksample", "rbsog_batch_get_ksample",
-           "rbsog_batch_layout", "rbsog_batch_set_rho_chunk", "rbsog_batch_last_error", "rbsog_batch_free"]
+           "rbsog_batch_layout", "rbsog_batch_set_rho_chunk", "rbsog_batch_set_shapes", "rbsog_batch_tune",
+           "rbsog_batch_profile", "rbsog_batch_last_error", "rbsog_batch_free"]
 RBSOG_NPROF = 10
 
 
@@ -98,6 +99,9 @@ def load(build_if_missing: bool = True):
     L.rbsog_batch_get_ksample.argtypes = [vp, vp, vp]
     L.rbsog_batch_layout.argtypes = [vp, vp, vp, vp]
     L.rbsog_batch_set_rho_chunk.argtypes = [vp, vp]
+    L.rbsog_batch_set_shapes.argtypes = [vp, C.c_double, i32]
+    L.rbsog_batch_tune.argtypes = [vp, i32, dp, C.POINTER(i32), vp]
+    L.rbsog_batch_profile.argtypes = [vp, i32, vp, vp]
     L.rbsog_batch_last_error.argtypes = [vp]
     L.rbsog_batch_last_error.restype = C.c_char_p
     L.rbsog_batch_free.argtypes = [vp]
@@ -321,6 +325,23 @@ def rbsog_batch_layout(b, R: int):
 def rbsog_batch_set_rho_chunk(b, chunk):
     chunk = np.ascontiguousarray(chunk, dtype=np.int32)
     _bcheck(b, load().rbsog_batch_set_rho_chunk(b, chunk.ctypes.data))
+
+
+def rbsog_batch_set_shapes(b, near_target: float, rho_target: int):
+    _bcheck(b, load().rbsog_batch_set_shapes(b, float(near_target), int(rho_target)))
+
+
+def rbsog_batch_tune(b, reps: int = 3, stream=None):
+    nt = C.c_double(0.0)
+    rt = C.c_int32(0)
+    _bcheck(b, load().rbsog_batch_tune(b, int(reps), C.byref(nt), C.byref(rt), _stream(stream)))
+    return nt.value, rt.value
+
+
+def rbsog_batch_profile(b, nsteps: int, stream=None) -> dict:
+    ms = np.zeros(RBSOG_NPROF, dtype=np.float64)
+    _bcheck(b, load().rbsog_batch_profile(b, int(nsteps), ms.ctypes.data, _stream(stream)))
+    return {rbsog_profile_name(g): float(ms[g]) for g in range(RBSOG_NPROF)}
 
 
 def rbsog_batch_last_error(b=None) -> str:

@@ -196,3 +196,59 @@ def test_device_pointers_and_repeated_batches():
         out = torch.zeros((b.Ntot, 3), device="cuda", dtype=torch.float64)
         R.rbsog_batch_get_state(b.h, out)
         assert np.array_equal(out.cpu().numpy(), r)
+
+
+def test_tuner_leaves_no_trace_in_the_trajectory():
+    """A batch tuned right after set_state follows the trajectory of one given the tuned
+    shapes directly (the tuner restores the step and draw counters)."""
+    ws = systems()
+    r, v = state(ws)
+    with Batch(ws) as b:
+        R.rbsog_batch_set_state(b.h, r, v)
+        near_t, rho_t = R.rbsog_batch_tune(b.h, reps=2)
+        R.rbsog_batch_step(b.h, b.R, 3)
+        ra = np.zeros((b.Ntot, 3))
+        R.rbsog_batch_get_state(b.h, ra)
+        m_a, _ = R.rbsog_batch_get_ksample(b.h, b.Ptot)
+    assert near_t in (48.0, 80.0, 110.0, 160.0) and rho_t in (256, 512, 1024, 2048)
+    with Batch(ws) as b:
+        R.rbsog_batch_set_shapes(b.h, near_t, rho_t)
+        R.rbsog_batch_set_state(b.h, r, v)
+        R.rbsog_batch_step(b.h, b.R, 3)
+        rb = np.zeros((b.Ntot, 3))
+        R.rbsog_batch_get_state(b.h, rb)
+        m_b, _ = R.rbsog_batch_get_ksample(b.h, b.Ptot)
+    assert np.array_equal(m_a, m_b)
+    assert np.array_equal(ra, rb)
+
+
+def test_near_shape_changes_no_force():
+    """The near tile width changes which CTA handles a particle, not its pairs."""
+    ws = systems()
+    r, _ = state(ws)
+    modes = np.concatenate([modes_for(w, w.P, 400 + i) for i, w in enumerate(ws)])
+    Fs, Us = [], []
+    for near_t in (48.0, 160.0):
+        with Batch(ws) as b:
+            R.rbsog_batch_set_shapes(b.h, near_t, 512)
+            R.rbsog_batch_set_state(b.h, r)
+            R.rbsog_batch_set_ksample(b.h, modes)
+            F = np.zeros((b.Ntot, 3))
+            e = R.rbsog_batch_forces(b.h, b.R, F, energy=True)
+            Fs.append(F)
+            Us.append([x["U_near"] for x in e])
+    # same pairs in the same order per particle; a tile whose staged region overflows takes
+    # the per-particle path, which may round differently
+    assert core.rel_l2(Fs[0], Fs[1]) <= 1e-7
+    assert np.allclose(Us[0], Us[1], rtol=1e-6, atol=0)
+
+
+def test_batch_profile_reports_every_group():
+    ws = systems()
+    r, v = state(ws)
+    with Batch(ws) as b:
+        R.rbsog_batch_set_state(b.h, r, v)
+        prof = R.rbsog_batch_profile(b.h, 2)
+        assert set(prof) == {R.rbsog_profile_name(g) for g in range(R.RBSOG_NPROF)}
+        assert all(t > 0 for t in prof.values())
+        assert R.rbsog_batch_get_state(b.h) == 2
