@@ -238,6 +238,70 @@ def batched_sweep(torch, R, steps, warmup, R_systems=256):
     return out
 
 
+def percentile(x, q):
+    return float(np.percentile(np.asarray(x, dtype=np.float64), q))
+
+
+def served_stream(torch, R, n_jobs=64, rate=50.0):
+    """Served request stream through the job server (continuous batching) against the
+    plain form: the same jobs in arrival order, one rbsog context at a time."""
+    js = W.cfg_stream(n_jobs, rate)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    work = sum(w.N * n for w, n, _ in js)
+    out = {"workload": f"yocp_stream{n_jobs}", "jobs": n_jobs, "arrival_rate_per_s": rate,
+           "N_range": [min(w.N for w, _, _ in js), max(w.N for w, _, _ in js)],
+           "steps_range": [min(n for _, n, _ in js), max(n for _, n, _ in js)], "particle_steps": work}
+    inputs = [(R.make_params(w, precision=R.RBSOG_FP32, device=dev.index), W.charges(w), W.masses(w),
+               W.positions(w), W.velocities(w)) for w, _, _ in js]
+    cap = 6_000_000
+    cfg = R.make_server_config(cap, cap // 4, 64 * 256, 64, steps_per_round=32, device=dev.index)
+    s = R.rbsog_server_create(cfg)
+    try:
+        t0 = R.rbsog_server_clock(s) + 0.05
+        ids = [R.rbsog_server_submit(s, p, q, m, r, v, n, t0 + ta)
+               for (p, q, m, r, v), (_, n, ta) in zip(inputs, js)]
+        R.rbsog_server_run(s)
+        infos = [R.rbsog_server_job(s, i)[0] for i in ids]
+        stats = R.rbsog_server_stats(s)
+    finally:
+        R.rbsog_server_free(s)
+    failed = sum(1 for i in infos if i["status"] != R.RBSOG_JOB_DONE)
+    lat = [i["t_done"] - i["t_arrival"] for i in infos]
+    span = max(i["t_done"] for i in infos) - min(i["t_arrival"] for i in infos)
+    out["served"] = {"p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99), "makespan_s": span,
+                     "value": work / span, "unit": "particle-steps/s", "failed": failed,
+                     "rounds": stats["rounds"], "peak_resident_jobs": stats["peak_jobs"],
+                     "peak_resident_particles": stats["peak_particles"], "device_busy_s": stats["busy_s"],
+                     "admission_setup_s": stats["setup_s"],
+                     "form": "rbsog_server: continuous batching, 32-step rounds, up to 64 resident jobs"}
+    # plain: first come first served, one context per job (its own rbsog_init, which
+    # builds the same SOG, sampler tables and S the server builds at admission)
+    clock = 0.0
+    lat_p = []
+    first = js[0][2]
+    for (p, q, m, r, v), (w, n, ta) in zip(inputs, js):
+        start = max(clock, ta)
+        tb = time.perf_counter()
+        ctx = R.rbsog_init(p, w.N, q, m)
+        try:
+            R.rbsog_set_state(ctx, r, v)
+            R.rbsog_step(ctx, n)
+            rr = np.empty((w.N, 3))
+            vv = np.empty((w.N, 3))
+            R.rbsog_get_state(ctx, rr, vv)
+        finally:
+            R.rbsog_free(ctx)
+        clock = start + (time.perf_counter() - tb)
+        lat_p.append(clock - ta)
+    out["plain"] = {"p50_s": percentile(lat_p, 50), "p99_s": percentile(lat_p, 99), "makespan_s": clock - first,
+                    "value": work / (clock - first), "unit": "particle-steps/s",
+                    "form": "one rbsog context per job, first come first served (same arrival times)"}
+    out["p50_speedup_vs_plain"] = out["plain"]["p50_s"] / out["served"]["p50_s"]
+    out["p99_speedup_vs_plain"] = out["plain"]["p99_s"] / out["served"]["p99_s"]
+    out["throughput_vs_plain"] = out["served"]["value"] / out["plain"]["value"]
+    return out
+
+
 def near_work(w, mtot):
     """Algorithmic FP32 work of one near-field launch (27-cell candidates and in-range pairs)
     for a decomposition of mtot Gaussians."""
@@ -315,6 +379,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     w = W.cfg_large(args.N)
@@ -376,6 +441,8 @@ def main():
                    "rbsog_get_state(host), pinned buffers"}
     if not args.no_batch:
         line["batched"] = batched_sweep(torch, R, args.steps, max(3, args.warmup))
+    if not args.no_serve:
+        line["served"] = served_stream(torch, R)
     if not args.no_fp64:
         r64 = rbsog_replica(w, R.RBSOG_FP64, 3, 1, rank, torch, R, profile_steps=0, e2e_steps=0)
         line["fp64"] = {"value": w.N * 3 / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"] / 3, "steps": 3}

@@ -59,6 +59,7 @@ extern "C" {
 
 typedef struct rbsog_ctx rbsog_ctx;
 typedef struct rbsog_batch rbsog_batch;
+typedef struct rbsog_server rbsog_server;
 
 typedef struct rbsog_params {
     double box[3];          /* L_x, L_y, L_z (absolute lengths), each > 0 */
@@ -295,6 +296,88 @@ const char *rbsog_batch_last_error(const rbsog_batch *b);
 
 /* Release every device buffer and graph of b.  Synchronous.  NULL is a no-op. */
 void rbsog_batch_free(rbsog_batch *b);
+
+/* ---- Job server with continuous batching ---------------------------------------------
+ * MD jobs (each an independent FP32 system as in the batch functions, with its own step
+ * count) are submitted with an arrival time.  rbsog_server_run admits arrived jobs in
+ * arrival order as soon as the resident arenas have room for them (particles, cells,
+ * modes and job slots, fixed at creation; a job that does not fit yet waits and later
+ * arrivals may pass it), advances every resident job together in rounds of at most
+ * steps_per_round steps (every kernel of a step one launch over all resident jobs, the
+ * step a CUDA graph), and retires each job after its last step: its final state and
+ * energies are read back to the host and the remaining jobs are compacted.  A job's
+ * first pass evaluates its initial forces; a job draws the same modes and Langevin noise,
+ * and gives the same result bit for bit, alone and among any other jobs.  A device error
+ * of one job (cell overflow, sampler limit) fails that job only.  Times are seconds on
+ * the server's clock, which starts at rbsog_server_create.  The server runs on the
+ * calling thread; its functions must not be called concurrently. */
+
+#define RBSOG_JOB_QUEUED 0
+#define RBSOG_JOB_RESIDENT 1
+#define RBSOG_JOB_DONE 2
+#define RBSOG_JOB_FAILED 3
+
+typedef struct rbsog_server_config {
+    int64_t max_particles;   /* resident particles (sum of N), >= 2 */
+    int64_t max_cells;       /* resident cells (sum of the jobs' cell counts) */
+    int64_t max_modes;       /* resident modes (sum of P) */
+    double near_target;      /* near-field shape (see rbsog_batch_set_shapes); 0 selects 110 */
+    int32_t max_jobs;        /* resident jobs at once, 1 .. 65536 */
+    int32_t steps_per_round; /* steps between admission points, >= 1 */
+    int32_t rho_target;      /* structure-factor shape; 0 selects 512 */
+    int32_t device;          /* CUDA device ordinal */
+    int32_t reserved[2];     /* must be 0 */
+} rbsog_server_config;
+
+typedef struct rbsog_job_info {
+    int32_t status;          /* RBSOG_JOB_* */
+    int32_t error;           /* RBSOG_* status of a failed job */
+    int64_t N;
+    int32_t nsteps;
+    int32_t steps_done;
+    double t_arrival;        /* server clock, seconds */
+    double t_admit;          /* -1 until admitted */
+    double t_done;           /* -1 until done or failed */
+    uint64_t footprint_bytes; /* device memory the job occupied while resident */
+    rbsog_energy energy;     /* after the last step */
+} rbsog_job_info;
+
+/* Create a server: allocates the arenas on cfg->device.  On failure *out is NULL and
+ * rbsog_server_last_error(NULL) holds the message. */
+int rbsog_server_create(const rbsog_server_config *cfg, rbsog_server **out);
+
+/* Submit a job: params (precision RBSOG_FP32; device ignored), N particles, host arrays
+ * q[N], m[N], r[N][3] and optional v[N][3] (copied), nsteps >= 0 steps, and the arrival
+ * time on the server clock (t_arrival < 0: now).  The job becomes eligible for admission
+ * once the clock passes t_arrival.  *job_id receives its handle (0, 1, 2, ...).  Host
+ * only; invalid parameters are reported when the job is considered for admission (the
+ * job then fails). */
+int rbsog_server_submit(rbsog_server *s, const rbsog_params *params, int64_t N, const double *q, const double *m,
+                        const double *r, const double *v, int32_t nsteps, double t_arrival, int64_t *job_id);
+
+/* Run the admission / round / retirement loop until every submitted job is done or
+ * failed (t_until < 0), or until the server clock passes t_until.  Sleeps while nothing
+ * is resident and the next arrival is in the future.  Returns a non-zero status only for
+ * errors of the server itself (CUDA failures), not for failed jobs. */
+int rbsog_server_run(rbsog_server *s, double t_until);
+
+/* Status and timings of a job; for a done job also its final positions r_out[N][3] and
+ * velocities v_out[N][3] (host arrays, either may be NULL).  Returns the job's error for
+ * a failed job and RBSOG_EINVAL if a state is asked of a job that is not done. */
+int rbsog_server_job(rbsog_server *s, int64_t job_id, rbsog_job_info *info, double *r_out, double *v_out);
+
+/* Counters: rounds, admissions, retirements, seconds the device was busy with rounds,
+ * particle-steps of done jobs, peak resident particles, peak resident jobs, seconds of
+ * admission set-up (out8[8]). */
+int rbsog_server_stats(const rbsog_server *s, double *out8);
+
+/* The server clock (seconds since rbsog_server_create). */
+double rbsog_server_clock(const rbsog_server *s);
+
+const char *rbsog_server_last_error(const rbsog_server *s);
+
+/* Release the arenas.  Synchronous.  NULL is a no-op. */
+void rbsog_server_free(rbsog_server *s);
 
 #ifdef __cplusplus
 }

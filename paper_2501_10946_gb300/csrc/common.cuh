@@ -22,6 +22,8 @@ struct DevCounters {
     unsigned long long draw;    // k-set draws so far
     int inject;                 // 1: the next k-set comes from the injected buffer
     int err;                    // error bits
+    int fvalid;                 // 1: the forces of the current state have been evaluated
+    int pad;
 };
 
 // Per-particle record staged by the near and far kernels.

@@ -40,7 +40,9 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
     double v[3] = {a.in.vx[k], a.in.vy[k], a.in.vz[k]};
     const double invm = a.in.invm[k];
     const uint32_t id = a.in.id[k];
-    if (a.integrate) {
+    // a system whose forces were never evaluated (fvalid = 0) only rebuilds its cells
+    const int integrate = a.ctr->fvalid ? a.integrate : 0;
+    if (integrate) {
         double F[3];
         if (PREC == 1) {
             const float *Ff = (const float *)a.F;
@@ -52,7 +54,7 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
         const double hk = 0.5 * a.dt * invm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) v[d] += hk * F[d];
-        if (a.integrate == 1) {
+        if (integrate == 1) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) r[d] += a.dt * v[d];
         } else {
@@ -226,12 +228,15 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t *cell, const uin
 }
 
 __global__ void __launch_bounds__(256) k_sort_cells(const uint32_t *cell_start, int ncell, unsigned long long *keys,
-                                                    uint32_t *perm_src, DevCounters *ctr) {
+                                                    uint32_t *perm_src, DevCounters *ctr, const uint32_t *c_off,
+                                                    int R) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const uint32_t lo = cell_start[c], hi = cell_start[c + 1];
     if (hi - lo > (uint32_t)kMaxCellOcc) {
-        atomicOr(&ctr->err, kErrCellOverflow);
+        int r = 0;
+        if (c_off) r = item_system(c_off, R, (uint32_t)c);
+        atomicOr(&ctr[r].err, kErrCellOverflow);
     } else {
         for (uint32_t i = lo + 1; i < hi; ++i) {
             unsigned long long key = keys[i];
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
     uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= g.N) return;
     const uint32_t src = g.perm_src[p];
-    const uint32_t N = g.N;
+    const uint32_t N = g.stride;
     g.out.rx[p] = g.in.rx[src]; g.out.ry[p] = g.in.ry[src]; g.out.rz[p] = g.in.rz[src];
     g.out.vx[p] = g.in.vx[src]; g.out.vy[p] = g.in.vy[src]; g.out.vz[p] = g.in.vz[src];
     g.out.invm[p] = g.in.invm[src];
@@ -289,20 +294,37 @@ __global__ void __launch_bounds__(256) k_set_state(const double *r, const double
     if (k < N) set_state_body(r, v, q_user, m_user, rest, box, k);
 }
 
+// New positions and velocities for a particle already resident at position k of the rest
+// buffer: it keeps its place, charge and mass; caller index = its id.
+__device__ __forceinline__ void set_state_inplace(const double *r, const double *v, const State &rest, const Box &box,
+                                                  uint32_t k) {
+    const size_t i = 3 * (size_t)rest.id[k];
+    rest.rx[k] = wrap_coord(r[i], box.L[0], box.invL[0]);
+    rest.ry[k] = wrap_coord(r[i + 1], box.L[1], box.invL[1]);
+    rest.rz[k] = wrap_coord(r[i + 2], box.L[2], box.invL[2]);
+    rest.vx[k] = v ? v[i] : 0.0;
+    rest.vy[k] = v ? v[i + 1] : 0.0;
+    rest.vz[k] = v ? v[i + 2] : 0.0;
+}
+
 // Batched systems: the caller's arrays hold system r's particles at p_off .. p_off + N - 1.
+// With q_user/m_user the system is (re)initialised in caller order; without, its particles
+// keep their current places, charges and masses.
 __global__ void __launch_bounds__(256) k_set_state_batch(const SysStateArgs *args, const uint32_t *items, int R,
                                                          const double *r, const double *v) {
     const int sys = item_system(items, R, blockIdx.x);
     const SysStateArgs &a = args[sys];
     const uint32_t k = (blockIdx.x - items[sys]) * blockDim.x + threadIdx.x;
-    if (k < a.N)
-        set_state_body(r + 3 * (size_t)a.p_off, v ? v + 3 * (size_t)a.p_off : nullptr, a.q_user, a.m_user, a.rest,
-                       a.box, k);
+    if (k >= a.N) return;
+    const double *rr = r + 3 * (size_t)a.p_off, *vv = v ? v + 3 * (size_t)a.p_off : nullptr;
+    if (a.q_user) set_state_body(rr, vv, a.q_user, a.m_user, a.rest, a.box, k);
+    else set_state_inplace(rr, vv, a.rest, a.box, k);
 }
 
 __global__ void k_reset_counters(DevCounters *ctr) {
     ctr->step = 0;
     ctr->err = 0;
+    ctr->fvalid = 0;
 }
 
 __global__ void k_reset_counters_n(DevCounters *ctr, int n) {
@@ -310,7 +332,25 @@ __global__ void k_reset_counters_n(DevCounters *ctr, int n) {
     if (i < n) {
         ctr[i].step = 0;
         ctr[i].err = 0;
+        ctr[i].fvalid = 0;
     }
+}
+
+__global__ void __launch_bounds__(256) k_relayout(State from, State to, const float *F_from, float *F_to,
+                                                  uint32_t stride, const uint32_t *old_off, const uint32_t *new_off,
+                                                  int R, uint32_t Nnew) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Nnew) return;
+    const int r = item_system(new_off, R, p);
+    const uint32_t q = old_off[r] + (p - new_off[r]);
+    to.rx[p] = from.rx[q]; to.ry[p] = from.ry[q]; to.rz[p] = from.rz[q];
+    to.vx[p] = from.vx[q]; to.vy[p] = from.vy[q]; to.vz[p] = from.vz[q];
+    to.invm[p] = from.invm[q];
+    to.q[p] = from.q[q];
+    to.id[p] = from.id[q];
+    F_to[p] = F_from[q];
+    F_to[stride + p] = F_from[stride + q];
+    F_to[2 * (size_t)stride + p] = F_from[2 * (size_t)stride + q];
 }
 
 __device__ __forceinline__ void get_state_body(const State &rest, size_t base, uint32_t k, double *r_out,
@@ -355,9 +395,14 @@ void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int
 
 void launch_scatter_sort(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
                          uint32_t N, int ncell, unsigned long long *keys, uint32_t *perm_src, DevCounters *ctr,
-                         cudaStream_t st) {
+                         cudaStream_t st, const uint32_t *c_off, int R) {
     k_scatter<<<blocks_for(N, 256), 256, 0, st>>>(cell, slot, cell_start, id, N, keys);
-    k_sort_cells<<<blocks_for((uint32_t)ncell, 256), 256, 0, st>>>(cell_start, ncell, keys, perm_src, ctr);
+    k_sort_cells<<<blocks_for((uint32_t)ncell, 256), 256, 0, st>>>(cell_start, ncell, keys, perm_src, ctr, c_off, R);
+}
+
+void launch_relayout(State from, State to, const float *F_from, float *F_to, uint32_t stride,
+                     const uint32_t *old_off, const uint32_t *new_off, int R, uint32_t Nnew, cudaStream_t st) {
+    if (Nnew) k_relayout<<<blocks_for(Nnew, 256), 256, 0, st>>>(from, to, F_from, F_to, stride, old_off, new_off, R, Nnew);
 }
 
 void launch_gather(int prec, const GatherArgs &g, cudaStream_t st) {

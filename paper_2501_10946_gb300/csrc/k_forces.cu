@@ -279,7 +279,7 @@ __device__ __forceinline__ double finish_particle(const FarArgs &a, uint32_t p, 
     }
     double v[3] = {a.st.vx[p], a.st.vy[p], a.st.vz[p]};
     const double invm = a.st.invm[p];
-    if (a.integrate) {
+    if (a.integrate && a.ctr->fvalid) {
         const double hk = 0.5 * a.dt * invm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) v[d] += hk * Ft[d];
@@ -417,7 +417,9 @@ __device__ __forceinline__ void energy_body(const EnergyArgs &a, double *sh) {
         a.out[2] = a.Uself;
         a.out[3] = K;
         a.out[4] = U + Uf + a.Uself + K;
-        if (a.advance_step) a.ctr->step += 1ull;
+        // a pass that found the forces invalid only evaluated them
+        if (a.advance_step && a.ctr->fvalid) a.ctr->step += 1ull;
+        a.ctr->fvalid = 1;
     }
 }
 

@@ -24,16 +24,23 @@ struct BinArgs {
 void launch_bin(int prec, const BinArgs &a, cudaStream_t st);
 void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int ncell, uint32_t N,
                  cudaStream_t st);
+// A cell over the occupancy limit sets kErrCellOverflow in ctr[0], or, with c_off (R + 1
+// first cells of R systems), in the counter of the system that owns the cell.
 void launch_scatter_sort(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
                          uint32_t N, int ncell, unsigned long long *keys, uint32_t *perm_src, DevCounters *ctr,
-                         cudaStream_t st);
+                         cudaStream_t st, const uint32_t *c_off = nullptr, int R = 1);
+// Move R systems to a new particle layout: system r's particles old_off[r] + i (rest
+// state and forces F, SoA stride `stride`) go to new_off[r] + i of `to` and F_to.
+void launch_relayout(State from, State to, const float *F_from, float *F_to, uint32_t stride,
+                     const uint32_t *old_off, const uint32_t *new_off, int R, uint32_t Nnew, cudaStream_t st);
 struct GatherArgs {
     State in;                 // work buffer
     State out;                // rest buffer (new cell-sorted order)
     const uint32_t *perm_src;
-    const void *s;            // fixed point of the work order
+    const void *s;            // fixed point of the work order, SoA [3][stride]
     void *rec;                // uint4 (FP32) or Rec64 (FP64) records in the new order
     uint32_t N;
+    uint32_t stride;
 };
 void launch_gather(int prec, const GatherArgs &g, cudaStream_t st);
 void launch_set_state(const double *r, const double *v, const double *q_user, const double *m_user, State rest,
@@ -124,6 +131,7 @@ struct FarArgs {
     double *F_user;            // optional [N][3] total force in caller order
     double *Fn_user;           // optional near part
     double *Ff_user;           // optional far part
+    const DevCounters *ctr;    // integrate only once the forces of the state are valid
 };
 int launch_far(int prec, const FarArgs &a, cudaStream_t st);     // returns #blocks
 struct EnergyArgs {

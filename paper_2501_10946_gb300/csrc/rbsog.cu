@@ -373,7 +373,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
                             c->ctr, st);
     }
     GatherArgs g{};
-    g.in = c->work; g.out = c->rest; g.perm_src = c->perm_src; g.s = c->s; g.rec = c->rec; g.N = N;
+    g.in = c->work; g.out = c->rest; g.perm_src = c->perm_src; g.s = c->s; g.rec = c->rec; g.N = N; g.stride = N;
     { ProfScope ps(c, st, 3); launch_gather(prec, g, st); }
     SampleArgs sa{};
     sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
@@ -398,7 +398,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     FarArgs fa{};
     fa.rec = c->rec; fa.N = N; fa.stride = N; fa.P = c->p.P; fa.gtab = c->gtab; fa.m = c->modes; fa.Fn = c->Fn; fa.F = c->F;
     fa.st = c->rest; fa.integrate = integrate ? 1 : 0; fa.dt = c->p.dt; fa.K_part = c->K_part;
-    fa.F_user = F_user; fa.Fn_user = Fn_user; fa.Ff_user = Ff_user;
+    fa.F_user = F_user; fa.Fn_user = Fn_user; fa.Ff_user = Ff_user; fa.ctr = c->ctr;
     { ProfScope ps(c, st, 8); c->nK = launch_far(prec, fa, st); }
     EnergyArgs ea{};
     ea.U_part = c->U_part; ea.nU = c->nU; ea.K_part = c->K_part; ea.nK = c->nK; ea.Ufar = c->Ufar;

@@ -1,17 +1,6 @@
-// A batch of independent systems advanced together: every kernel of the step is one
-// launch over all systems (FP32 path).
-//
-// Layout: the systems' particles, cells and modes are concatenated system-major.  System
-// r owns particles p_off[r] .. p_off[r+1]-1 of every per-particle buffer, cells
-// c_off[r] .. c_off[r+1]-1 of the global cell list and modes m_off[r] .. m_off[r+1]-1.
-// The counting sort runs once over all cells; since the cells are ordered system-major,
-// the sorted order keeps every system in its own particle range.  Every other kernel
-// maps a block to (system, local block) through a prefix array of per-system block
-// counts and reads that system's arguments (pointers already offset) from a device
-// array, so the step is 12 launches whatever the number of systems, captured once as
-// a CUDA graph.  Each system keeps its own box, SOG decomposition, P, seed, time step,
-// ensemble and step/draw counters, so system r of a batch follows the same Philox
-// streams as a single context built with the same parameters.
+// Resident-set engine (the layout is described in engine.h) and the batch ABI: a fixed
+// set of systems advanced together, every kernel of the step one launch over all of
+// them, replayed from one CUDA graph per step.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,60 +9,9 @@
 #include <string>
 #include <vector>
 
-#include "../../include/rbsog.h"
-#include "common.cuh"
-#include "kernels.h"
-#include "system.h"
+#include "engine.h"
 
 using namespace rbsog;
-
-struct rbsog_batch {
-    int R = 0;
-    uint32_t Ntot = 0;
-    int Ctot = 0, Ptot = 0;
-    int device = 0;
-    std::string err;
-    std::vector<HostSystem> sys;
-    std::vector<uint32_t> p_off, c_off, m_off;         // R + 1 entries
-    std::vector<int> rho_chunk;                        // particles per structure-factor block
-    double near_target = 110.0;                        // particles per near-field CTA the tiles aim at
-    size_t cap_part = 0, cap_upart = 0;                // allocated partial buffer entries
-    // device buffers
-    State rest{}, work{};
-    double *q_user = nullptr, *m_user = nullptr, *stage_a = nullptr, *stage_b = nullptr;
-    float *F = nullptr, *Fn = nullptr;
-    uint32_t *s = nullptr;
-    uint4 *rec = nullptr;
-    uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr,
-             *perm_src = nullptr;
-    unsigned long long *keys = nullptr;
-    int *modes = nullptr, *inject_m = nullptr;
-    double *coef = nullptr, *Ufar = nullptr, *U_part = nullptr, *K_part = nullptr, *energy = nullptr;
-    double2 *partial = nullptr, *rho = nullptr;
-    unsigned char *gtab = nullptr;
-    double *mix_prob = nullptr, *ax_prob = nullptr;
-    int *mix_alias = nullptr, *ax_off = nullptr, *ax_nmax = nullptr, *ax_alias = nullptr;
-    DevCounters *ctr = nullptr;                        // [R + 1]: systems, then the cell-list status
-    // per-system kernel arguments (device arrays) and block prefixes
-    BinArgs *d_bin[2] = {nullptr, nullptr};            // [0] force evaluation only, [1] step
-    FarArgs *d_far[2] = {nullptr, nullptr};
-    FarArgs *d_far_user = nullptr;                     // force evaluation with caller outputs
-    EnergyArgs *d_energy[2] = {nullptr, nullptr};
-    SampleArgs *d_sample = nullptr;
-    NearArgs *d_near = nullptr;
-    NearBatchGeom *d_geom = nullptr;
-    RhoArgs *d_rho = nullptr;
-    int *d_chunk = nullptr;
-    RhoFinalArgs *d_rf = nullptr;
-    SysStateArgs *d_state = nullptr;
-    uint32_t *d_items = nullptr;                       // 6 prefix arrays of R + 1 entries
-    uint32_t nb[6] = {0, 0, 0, 0, 0, 0};               // total blocks: bin, sample, near, rho, rho_final, far
-    std::vector<FarArgs> h_far;                        // host copy of d_far[0]
-    std::vector<void *> allocs;
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    bool force_valid = false;
-};
 
 namespace {
 
@@ -81,21 +19,10 @@ enum { kItBin = 0, kItSample, kItNear, kItRho, kItRhoFinal, kItFar };
 
 std::string g_batch_init_error;
 
-int bfail(rbsog_batch *b, int code, const std::string &msg) {
-    if (b) b->err = msg;
-    else g_batch_init_error = msg;
-    return code;
-}
-
-int bcuda_fail(rbsog_batch *b, cudaError_t e, const char *where) {
-    return bfail(b, e == cudaErrorMemoryAllocation ? RBSOG_ENOMEM : RBSOG_ECUDA,
-                 std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e));
-}
-
-#define BCK(call, where)                                          \
-    do {                                                          \
-        cudaError_t e_ = (call);                                  \
-        if (e_ != cudaSuccess) return bcuda_fail(b, e_, where);   \
+#define BCK(call, where)                                                \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return engine_cuda_fail(b, e_, where);   \
     } while (0)
 
 template <typename T>
@@ -109,15 +36,26 @@ cudaError_t balloc(rbsog_batch *b, T **ptr, size_t count) {
     return e;
 }
 
-// Copy a host vector to a device array, allocating the array on first use (the size of
-// each array is fixed for the lifetime of the batch).
+// Replace a grow-only buffer by a larger one (the device is idle when this is called).
 template <typename T>
-cudaError_t upload(rbsog_batch *b, T **dst, const std::vector<T> &src) {
-    if (*dst == nullptr) {
-        cudaError_t e = balloc(b, dst, src.size());
-        if (e != cudaSuccess) return e;
+cudaError_t regrow(rbsog_batch *b, T **ptr, size_t *cap, size_t need) {
+    if (need <= *cap && *ptr) return cudaSuccess;
+    if (*ptr) {
+        auto it = std::find(b->allocs.begin(), b->allocs.end(), (void *)*ptr);
+        if (it != b->allocs.end()) b->allocs.erase(it);
+        cudaFree(*ptr);
+        *ptr = nullptr;
     }
-    return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    const size_t n = std::max<size_t>(need, 1) + need / 4;   // headroom against frequent regrowth
+    cudaError_t e = balloc(b, ptr, n);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+template <typename T>
+cudaError_t upload(T *dst, const std::vector<T> &src) {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
 bool dev_ptr(const void *ptr) {
@@ -144,82 +82,40 @@ int chunk_for(uint32_t N, int target) {
     return (int)((N + G - 1) / G);
 }
 
-// Sizes of the per-block partial buffers: structure factor (double2), near energy, kinetic energy.
-void partial_sizes(const rbsog_batch *b, size_t *part, size_t *upart, size_t *kpart) {
-    *part = *upart = *kpart = 0;
-    for (int r = 0; r < b->R; ++r) {
-        const HostSystem &h = b->sys[r];
-        const uint32_t c = (uint32_t)b->rho_chunk[r];
-        *part += (size_t)((h.N + c - 1) / c) * 8 * (size_t)h.p.P;
-        int tiled, W, tiles_x;
-        uint32_t nbn;
-        near_geometry(h.box, h.N, &tiled, &W, &tiles_x, &nbn, b->near_target);
-        *upart += 4 * (size_t)nbn;
-        *kpart += far_batch_blocks(h.N);
-    }
+struct SysShape {
+    int tiled, W, tiles_x;
+    uint32_t near_blocks;
+    int G;
+};
+
+SysShape shape_of(const HostSystem &h, double near_target, int chunk) {
+    SysShape s{};
+    near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target);
+    s.G = (int)((h.N + (uint32_t)chunk - 1) / (uint32_t)chunk);
+    return s;
 }
 
-// Grow the partial buffers to the current shapes (old buffers stay allocated until free).
-int ensure_partials(rbsog_batch *b) {
-    size_t part, upart, kpart;
-    partial_sizes(b, &part, &upart, &kpart);
-    if (part > b->cap_part) {
-        BCK(balloc(b, &b->partial, part), "alloc partials");
-        b->cap_part = part;
-    }
-    if (upart + 4 > b->cap_upart) {
-        BCK(balloc(b, &b->U_part, upart + 4), "alloc partials");
-        b->cap_upart = upart + 4;
-    }
-    if (b->K_part == nullptr) BCK(balloc(b, &b->K_part, kpart + 1), "alloc partials");
-    return RBSOG_OK;
-}
+const uint32_t *items_of(const rbsog_batch *b, int j) { return b->d_items + (size_t)j * (b->capR + 1); }
 
-int check_errors(rbsog_batch *b) {
-    std::vector<DevCounters> hc(b->R + 1);
-    BCK(cudaMemcpy(hc.data(), b->ctr, hc.size() * sizeof(DevCounters), cudaMemcpyDeviceToHost), "read device status");
-    DevCounters h{};
-    for (const DevCounters &x : hc) h.err |= x.err;
-    if (h.err & kErrCellOverflow) return bfail(b, RBSOG_EOVERFLOW, "a cell holds more than 4096 particles");
-    if (h.err & kErrSampler) return bfail(b, RBSOG_ETIMEOUT, "k-sampler exceeded its attempt limit");
-    if (h.err & kErrNearStage) return bfail(b, RBSOG_ETIMEOUT, "near-field staging wait exceeded its limit");
-    return RBSOG_OK;
-}
-
-int read_energies(rbsog_batch *b, rbsog_energy *e, cudaStream_t st) {
-    std::vector<double> h(5 * (size_t)b->R);
-    std::vector<DevCounters> hc(b->R);
-    BCK(cudaMemcpyAsync(h.data(), b->energy, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read energy");
-    BCK(cudaMemcpyAsync(hc.data(), b->ctr, hc.size() * sizeof(DevCounters), cudaMemcpyDeviceToHost, st),
-        "read counters");
-    BCK(cudaStreamSynchronize(st), "synchronize");
-    for (int r = 0; r < b->R; ++r) {
-        const double *x = &h[5 * (size_t)r];
-        e[r].U_near = x[0]; e[r].U_far = x[1]; e[r].U_self = x[2]; e[r].kinetic = x[3]; e[r].total = x[4];
-        e[r].step = hc[r].step;
-    }
-    return check_errors(b);
-}
-
-// Per-system argument arrays (device), rebuilt when the structure-factor chunking changes.
+// Per-system argument arrays and block prefixes for the current membership and shapes.
 int build_args(rbsog_batch *b) {
     const int R = b->R;
     std::vector<BinArgs> bin[2];
     std::vector<FarArgs> far[2];
     std::vector<EnergyArgs> en[2];
+    for (int k = 0; k < 2; ++k) {
+        bin[k].resize(R);
+        far[k].resize(R);
+        en[k].resize(R);
+    }
     std::vector<SampleArgs> sa(R);
     std::vector<NearArgs> na(R);
     std::vector<NearBatchGeom> geom(R);
     std::vector<RhoArgs> ra(R);
     std::vector<RhoFinalArgs> rf(R);
     std::vector<SysStateArgs> ss(R);
-    std::vector<uint32_t> items(6 * (size_t)(R + 1), 0u);
-    for (int k = 0; k < 2; ++k) {
-        bin[k].resize(R);
-        far[k].resize(R);
-        en[k].resize(R);
-    }
-    size_t part_off = 0, u_off = 0, k_off = 0, ax_base = 0;
+    std::vector<uint32_t> items(6 * (size_t)(b->capR + 1), 0u);
+    size_t part_off = 0, u_off = 0, k_off = 0, ax_base = 0, mix_base = 0;
     uint32_t it[6] = {0, 0, 0, 0, 0, 0};
     for (int r = 0; r < R; ++r) {
         const HostSystem &h = b->sys[r];
@@ -228,7 +124,8 @@ int build_args(rbsog_batch *b) {
         const uint32_t N = h.N;
         const int P = p.P;
         const int mode = p.ensemble == RBSOG_LANGEVIN ? 2 : 1;
-        // cell list + opening half of the integrator
+        DevCounters *ctr = b->ctr + r;
+        const SysShape sh = shape_of(h, b->near_target, b->rho_chunk[r]);
         for (int k = 0; k < 2; ++k) {
             BinArgs &a = bin[k][r];
             a.in = offset_state(b->rest, po);
@@ -239,9 +136,9 @@ int build_args(rbsog_batch *b) {
             a.c1 = std::exp(-p.langevin_gamma * p.dt);
             a.kT = h.kT;
             a.seed = p.seed;
-            a.ctr = b->ctr + r;
+            a.ctr = ctr;
             a.N = N;
-            a.stride = b->Ntot;
+            a.stride = b->capN;
             a.cell_base = b->c_off[r];
             a.box = h.box;
             a.s = b->s + po;
@@ -249,14 +146,12 @@ int build_args(rbsog_batch *b) {
             a.slot = b->slot + po;
             a.count = b->count;
         }
-        // sampler: this system's tables inside the concatenated ones
         {
             SampleArgs &a = sa[r];
             const int mt = h.sog.mtot();
-            size_t mix_base = 0;
-            for (int q = 0; q < r; ++q) mix_base += (size_t)b->sys[q].sog.mtot();
             a.tab = SamplerTables{mt, b->mix_prob + mix_base, b->mix_alias + mix_base, b->ax_off + 3 * mix_base,
                                   b->ax_nmax + 3 * mix_base, b->ax_prob + ax_base, b->ax_alias + ax_base};
+            mix_base += (size_t)mt;
             ax_base += h.ax_prob.size();
             a.P = P;
             a.seed = p.seed;
@@ -266,16 +161,13 @@ int build_args(rbsog_batch *b) {
             a.inv_lam2 = 1.0 / (h.lam * h.lam);
             a.S = h.S;
             a.V = h.V;
-            a.ctr = b->ctr + r;
+            a.ctr = ctr;
             a.inject_m = b->inject_m + 3 * mo;
             a.m_out = b->modes + 3 * mo;
             a.coef_out = b->coef + mo;
         }
-        // near field: global records and forces, this system's cell range
-        int tiled, W, tiles_x;
-        uint32_t nbn;
-        near_geometry(h.box, N, &tiled, &W, &tiles_x, &nbn, b->near_target);
-        geom[r] = NearBatchGeom{tiled, tiled ? W : (int)po, tiles_x};
+        // near field: global record and force indices, this system's cell range
+        geom[r] = NearBatchGeom{sh.tiled, sh.tiled ? sh.W : (int)po, sh.tiles_x};
         {
             NearArgs &a = na[r];
             a.nc = h.nconsts;
@@ -283,14 +175,11 @@ int build_args(rbsog_batch *b) {
             a.cell_start = b->cell_start + b->c_off[r];
             a.box = h.box;
             a.N = N;
-            a.stride = b->Ntot;
+            a.stride = b->capN;
             a.Fn = b->Fn;
             a.U_part = b->U_part + u_off;
-            a.ctr = b->ctr + b->R;   // cell-list status (overflow is detected by the global sort)
+            a.ctr = ctr;
         }
-        // structure factor and its reduction
-        const int chunk = b->rho_chunk[r];
-        const int G = (int)((N + (uint32_t)chunk - 1) / (uint32_t)chunk);
         {
             RhoArgs &a = ra[r];
             a.rec = b->rec + po;
@@ -298,12 +187,12 @@ int build_args(rbsog_batch *b) {
             a.m = b->modes + 3 * mo;
             a.P = P;
             a.partial = b->partial + part_off;
-            a.G = G;
+            a.G = sh.G;
         }
         {
             RhoFinalArgs &a = rf[r];
             a.partial = b->partial + part_off;
-            a.G = G;
+            a.G = sh.G;
             a.P = P;
             a.m = b->modes + 3 * mo;
             a.coef = b->coef + mo;
@@ -311,14 +200,14 @@ int build_args(rbsog_batch *b) {
             a.rho = b->rho + mo;
             a.gtab = b->gtab + kGTab32Bytes * mo;
             a.Ufar = b->Ufar + mo;
-            a.ctr = b->ctr + r;
+            a.ctr = ctr;
         }
         const uint32_t nbf = far_batch_blocks(N);
         for (int k = 0; k < 2; ++k) {
             FarArgs &a = far[k][r];
             a.rec = b->rec + po;
             a.N = N;
-            a.stride = b->Ntot;
+            a.stride = b->capN;
             a.P = P;
             a.gtab = b->gtab + kGTab32Bytes * mo;
             a.m = b->modes + 3 * mo;
@@ -329,9 +218,10 @@ int build_args(rbsog_batch *b) {
             a.dt = p.dt;
             a.K_part = b->K_part + k_off;
             a.F_user = a.Fn_user = a.Ff_user = nullptr;
+            a.ctr = ctr;
             EnergyArgs &e = en[k][r];
             e.U_part = b->U_part + u_off;
-            e.nU = 4 * (int)nbn;
+            e.nU = 4 * (int)sh.near_blocks;
             e.K_part = b->K_part + k_off;
             e.nK = (int)nbf;
             e.Ufar = b->Ufar + mo;
@@ -339,78 +229,69 @@ int build_args(rbsog_batch *b) {
             e.Ufar0 = h.Ufar0;
             e.Uself = h.Uself;
             e.out = b->energy + 5 * (size_t)r;
-            e.ctr = b->ctr + r;
+            e.ctr = ctr;
             e.advance_step = k;
         }
-        ss[r] = SysStateArgs{offset_state(b->rest, po), b->q_user + po, b->m_user + po, N, (uint32_t)po, h.box};
-        const uint32_t cnt[6] = {bin_batch_blocks(N), sample_batch_blocks(P), nbn, rho_batch_blocks(G, P),
-                                 rho_final_batch_blocks(P), nbf};
+        ss[r] = SysStateArgs{offset_state(b->rest, po), nullptr, nullptr, N, (uint32_t)po, h.box};
+        const uint32_t cnt[6] = {bin_batch_blocks(N), sample_batch_blocks(P), sh.near_blocks,
+                                 rho_batch_blocks(sh.G, P), rho_final_batch_blocks(P), nbf};
         for (int j = 0; j < 6; ++j) {
-            items[(size_t)j * (R + 1) + r] = it[j];
+            items[(size_t)j * (b->capR + 1) + r] = it[j];
             it[j] += cnt[j];
         }
-        part_off += (size_t)G * 8 * P;
-        u_off += 4 * (size_t)nbn;
+        part_off += (size_t)sh.G * 8 * P;
+        u_off += 4 * (size_t)sh.near_blocks;
         k_off += nbf;
     }
+    b->h_items.assign(R + 1, 0u);
     for (int j = 0; j < 6; ++j) {
-        items[(size_t)j * (R + 1) + R] = it[j];
+        items[(size_t)j * (b->capR + 1) + R] = it[j];
         b->nb[j] = it[j];
     }
-    BCK(upload(b, &b->d_bin[0], bin[0]), "upload arguments");
-    BCK(upload(b, &b->d_bin[1], bin[1]), "upload arguments");
-    BCK(upload(b, &b->d_far[0], far[0]), "upload arguments");
-    BCK(upload(b, &b->d_far[1], far[1]), "upload arguments");
-    BCK(upload(b, &b->d_far_user, far[0]), "upload arguments");
-    BCK(upload(b, &b->d_energy[0], en[0]), "upload arguments");
-    BCK(upload(b, &b->d_energy[1], en[1]), "upload arguments");
-    BCK(upload(b, &b->d_sample, sa), "upload arguments");
-    BCK(upload(b, &b->d_near, na), "upload arguments");
-    BCK(upload(b, &b->d_geom, geom), "upload arguments");
-    BCK(upload(b, &b->d_rho, ra), "upload arguments");
-    BCK(upload(b, &b->d_chunk, b->rho_chunk), "upload arguments");
-    BCK(upload(b, &b->d_rf, rf), "upload arguments");
-    BCK(upload(b, &b->d_state, ss), "upload arguments");
-    BCK(upload(b, &b->d_items, items), "upload arguments");
+    for (int r = 0; r <= R; ++r) b->h_items[r] = items[r];
+    BCK(upload(b->d_bin[0], bin[0]), "upload arguments");
+    BCK(upload(b->d_bin[1], bin[1]), "upload arguments");
+    BCK(upload(b->d_far[0], far[0]), "upload arguments");
+    BCK(upload(b->d_far[1], far[1]), "upload arguments");
+    BCK(upload(b->d_far_user, far[0]), "upload arguments");
+    BCK(upload(b->d_energy[0], en[0]), "upload arguments");
+    BCK(upload(b->d_energy[1], en[1]), "upload arguments");
+    BCK(upload(b->d_sample, sa), "upload arguments");
+    BCK(upload(b->d_near, na), "upload arguments");
+    BCK(upload(b->d_geom, geom), "upload arguments");
+    BCK(upload(b->d_rho, ra), "upload arguments");
+    BCK(upload(b->d_chunk, std::vector<int>(b->rho_chunk.begin(), b->rho_chunk.begin() + R)), "upload arguments");
+    BCK(upload(b->d_rf, rf), "upload arguments");
+    BCK(upload(b->d_state, ss), "upload arguments");
+    b->h_state = ss;
+    BCK(upload(b->d_items, items), "upload arguments");
+    BCK(upload(b->d_coff, std::vector<uint32_t>(b->c_off.begin(), b->c_off.end())), "upload arguments");
     b->h_far = far[0];
     return RBSOG_OK;
 }
 
-const uint32_t *items_of(const rbsog_batch *b, int j) { return b->d_items + (size_t)j * (b->R + 1); }
+int check_all(rbsog_batch *b) {
+    std::vector<DevCounters> c;
+    if (int code = engine_counters(b, &c)) return code;
+    for (int r = 0; r < b->R; ++r)
+        if (int code = engine_status(b, c, r)) return code;
+    return RBSOG_OK;
+}
 
-// One force evaluation (set 0) or one step (set 1) of every system.  With ev (11 events)
-// the kernel groups bin, scan, sort, gather, sample, near, rho, rho_final, far, energy
-// are bracketed by ev[g] and ev[g + 1].
-int enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far, cudaEvent_t *ev = nullptr) {
-    const int R = b->R;
-    auto mark = [&](int g) {
-        if (ev) cudaEventRecord(ev[g], st);
-    };
-    mark(0);
-    launch_bin_batch(b->d_bin[set], items_of(b, kItBin), R, b->nb[kItBin], st);
-    mark(1);
-    launch_scan(b->count, b->tile_sums, b->cell_start, b->Ctot, b->Ntot, st);
-    mark(2);
-    launch_scatter_sort(b->cell, b->slot, b->cell_start, b->work.id, b->Ntot, b->Ctot, b->keys, b->perm_src,
-                        b->ctr + R, st);
-    mark(3);
-    GatherArgs g{};
-    g.in = b->work; g.out = b->rest; g.perm_src = b->perm_src; g.s = b->s; g.rec = b->rec; g.N = b->Ntot;
-    launch_gather(RBSOG_FP32, g, st);
-    mark(4);
-    launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
-    mark(5);
-    launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
-    mark(6);
-    launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], st);
-    mark(7);
-    launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], st);
-    mark(8);
-    launch_far_batch(far ? far : b->d_far[set], items_of(b, kItFar), R, b->nb[kItFar], st);
-    mark(9);
-    launch_energy_batch(b->d_energy[set], R, st);
-    mark(10);
-    BCK(cudaGetLastError(), "kernel launch");
+int read_energies(rbsog_batch *b, rbsog_energy *e, cudaStream_t st) {
+    std::vector<double> h(5 * (size_t)b->R);
+    if (b->R) BCK(cudaMemcpyAsync(h.data(), b->energy, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+                  "read energy");
+    BCK(cudaStreamSynchronize(st), "synchronize");
+    std::vector<DevCounters> c;
+    if (int code = engine_counters(b, &c)) return code;
+    for (int r = 0; r < b->R; ++r) {
+        const double *x = &h[5 * (size_t)r];
+        e[r].U_near = x[0]; e[r].U_far = x[1]; e[r].U_self = x[2]; e[r].kinetic = x[3]; e[r].total = x[4];
+        e[r].step = c[r].step;
+    }
+    for (int r = 0; r < b->R; ++r)
+        if (int code = engine_status(b, c, r)) return code;
     return RBSOG_OK;
 }
 
@@ -434,85 +315,180 @@ struct EventSet {
 // Apply a near tile target and a structure-factor target to every system.
 int apply_shapes(rbsog_batch *b, double near_target, int rho_target) {
     b->near_target = near_target;
+    b->rho_target = rho_target;
     for (int r = 0; r < b->R; ++r) b->rho_chunk[r] = chunk_for(b->sys[r].N, rho_target);
-    if (int c = ensure_partials(b)) return c;
-    if (int c = build_args(b)) return c;
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
+    b->dirty = true;
+    return engine_commit(b);
+}
+
+// Items of the bin kernel restricted to systems first .. first+count-1 (relative block
+// numbers), uploaded to d_sub_items.
+int sub_items(rbsog_batch *b, int first, int count, uint32_t *nblocks, cudaStream_t st) {
+    std::vector<uint32_t> it(count + 1);
+    for (int k = 0; k <= count; ++k) it[k] = b->h_items[first + k] - b->h_items[first];
+    *nblocks = it[count];
+    BCK(cudaMemcpyAsync(b->d_sub_items, it.data(), it.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st),
+        "upload items");
+    // the host vector dies at return: wait for the copy
+    BCK(cudaStreamSynchronize(st), "synchronize");
     return RBSOG_OK;
 }
 
 }  // namespace
 
-extern "C" {
+namespace rbsog {
 
-int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, const double *q_host,
-                     const double *m_host, rbsog_batch **out) {
-    if (!out) return bfail(nullptr, RBSOG_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!params || !N || !q_host || !m_host) return bfail(nullptr, RBSOG_EINVAL, "params, N, q or m is NULL");
-    if (R < 1 || R > (1 << 20)) return bfail(nullptr, RBSOG_EINVAL, "R must be in [1, 2^20]");
-    std::vector<HostSystem> sys(R);
-    std::vector<uint32_t> p_off(R + 1, 0), c_off(R + 1, 0), m_off(R + 1, 0);
-    long long nt = 0, ct = 0, pt = 0;
-    for (int r = 0; r < R; ++r) {
-        if (params[r].precision != RBSOG_FP32)
-            return bfail(nullptr, RBSOG_EUNSUPPORTED, "batched systems run the FP32 path only");
-        if (params[r].device != params[0].device)
-            return bfail(nullptr, RBSOG_EINVAL, "every system of a batch uses the same device");
-        std::string err;
-        const int code = setup_system(params[r], N[r], q_host + nt, m_host + nt, &sys[r], &err);
-        if (code != RBSOG_OK) return bfail(nullptr, code, "system " + std::to_string(r) + ": " + err);
-        nt += N[r];
-        ct += sys[r].box.ncell;
-        pt += params[r].P;
-        if (nt >= 0x7fffffffLL || ct > (1LL << 28) || pt > (1LL << 26))
-            return bfail(nullptr, RBSOG_EINVAL, "batch too large (particles, cells or modes)");
-        p_off[r + 1] = (uint32_t)nt;
-        c_off[r + 1] = (uint32_t)ct;
-        m_off[r + 1] = (uint32_t)pt;
-    }
-    if (cudaSetDevice(params[0].device) != cudaSuccess) {
+int engine_fail(rbsog_batch *b, int code, const std::string &msg) {
+    if (b) b->err = msg;
+    else g_batch_init_error = msg;
+    return code;
+}
+
+int engine_cuda_fail(rbsog_batch *b, cudaError_t e, const char *where) {
+    return engine_fail(b, e == cudaErrorMemoryAllocation ? RBSOG_ENOMEM : RBSOG_ECUDA,
+                       std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e));
+}
+
+int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
+    if (caps.particles < 2 || caps.particles >= 0x7fffffffu || caps.cells < 1 || caps.cells > (1 << 28) ||
+        caps.modes < 1 || caps.modes > (1 << 26) || caps.systems < 1 || caps.systems > (1 << 20))
+        return engine_fail(b, RBSOG_EINVAL, "engine capacities out of range");
+    b->capN = caps.particles;
+    b->capC = caps.cells;
+    b->capP = caps.modes;
+    b->capR = caps.systems;
+    b->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
-        return bfail(nullptr, RBSOG_ECUDA, "cudaSetDevice failed (no usable CUDA device)");
+        return engine_fail(b, RBSOG_ECUDA, "cudaSetDevice failed (no usable CUDA device)");
     }
-    rbsog_batch *b = new rbsog_batch();
-    b->R = R;
-    b->Ntot = (uint32_t)nt;
-    b->Ctot = (int)ct;
-    b->Ptot = (int)pt;
-    b->device = params[0].device;
-    b->sys = std::move(sys);
-    b->p_off = p_off;
-    b->c_off = c_off;
-    b->m_off = m_off;
-    b->rho_chunk.resize(R);
-    for (int r = 0; r < R; ++r) b->rho_chunk[r] = chunk_for(b->sys[r].N, 512);
-    auto bail = [&](int code, const std::string &msg) {
-        g_batch_init_error = msg.empty() ? b->err : msg;
-        rbsog_batch_free(b);
-        return code;
-    };
-    const size_t n = b->Ntot, n3 = 3 * n;
+    const size_t n = b->capN, n3 = 3 * n, C = (size_t)b->capC, P = (size_t)b->capP, R = (size_t)b->capR;
     State *sts[2] = {&b->rest, &b->work};
     for (State *s : sts)
         if (balloc(b, &s->rx, n) || balloc(b, &s->ry, n) || balloc(b, &s->rz, n) || balloc(b, &s->vx, n) ||
             balloc(b, &s->vy, n) || balloc(b, &s->vz, n) || balloc(b, &s->invm, n) || balloc(b, &s->q, n) ||
             balloc(b, &s->id, n))
-            return bail(RBSOG_ENOMEM, "device allocation failed (state)");
-    const size_t ntiles = ((size_t)b->Ctot + kScanTile - 1) / kScanTile;
-    const size_t P = (size_t)b->Ptot;
-    if (balloc(b, &b->q_user, n) || balloc(b, &b->m_user, n) || balloc(b, &b->stage_a, n3) ||
-        balloc(b, &b->stage_b, n3) || balloc(b, &b->F, n3) || balloc(b, &b->Fn, n3) || balloc(b, &b->s, n3) ||
-        balloc(b, &b->rec, n) || balloc(b, &b->cell, n) || balloc(b, &b->slot, n) ||
-        balloc(b, &b->count, (size_t)b->Ctot) || balloc(b, &b->tile_sums, ntiles) ||
-        balloc(b, &b->cell_start, (size_t)b->Ctot + 1) || balloc(b, &b->perm_src, n) || balloc(b, &b->keys, n) ||
-        balloc(b, &b->modes, 3 * P) || balloc(b, &b->inject_m, 3 * P) || balloc(b, &b->coef, P) ||
-        balloc(b, &b->rho, P) || balloc(b, &b->gtab, kGTab32Bytes * P) || balloc(b, &b->Ufar, P) ||
-        balloc(b, &b->energy, 5 * (size_t)R + 3) || balloc(b, &b->ctr, (size_t)R + 1))
-        return bail(RBSOG_ENOMEM, "device allocation failed");
+            return engine_fail(b, RBSOG_ENOMEM, "device allocation failed (state)");
+    const size_t ntiles = (C + kScanTile - 1) / kScanTile;
+    if (balloc(b, &b->stage_a, n3) || balloc(b, &b->stage_b, n3) || balloc(b, &b->stage_qm, 2 * n) ||
+        balloc(b, &b->d_state_sub, R) || balloc(b, &b->F, n3) || balloc(b, &b->Fn, n3) ||
+        balloc(b, &b->s, n3) || balloc(b, &b->rec, n) || balloc(b, &b->cell, n) || balloc(b, &b->slot, n) ||
+        balloc(b, &b->count, C) || balloc(b, &b->tile_sums, ntiles) || balloc(b, &b->cell_start, C + 1) ||
+        balloc(b, &b->perm_src, n) || balloc(b, &b->keys, n) || balloc(b, &b->modes, 3 * P) ||
+        balloc(b, &b->inject_m, 3 * P) || balloc(b, &b->coef, P) || balloc(b, &b->rho, P) ||
+        balloc(b, &b->gtab, kGTab32Bytes * P) || balloc(b, &b->Ufar, P) || balloc(b, &b->energy, 5 * R) ||
+        balloc(b, &b->ctr, R) || balloc(b, &b->d_bin[0], R) || balloc(b, &b->d_bin[1], R) ||
+        balloc(b, &b->d_far[0], R) || balloc(b, &b->d_far[1], R) || balloc(b, &b->d_far_user, R) ||
+        balloc(b, &b->d_energy[0], R) || balloc(b, &b->d_energy[1], R) || balloc(b, &b->d_sample, R) ||
+        balloc(b, &b->d_near, R) || balloc(b, &b->d_geom, R) || balloc(b, &b->d_rho, R) ||
+        balloc(b, &b->d_chunk, R) || balloc(b, &b->d_rf, R) || balloc(b, &b->d_state, R) ||
+        balloc(b, &b->d_items, 6 * (R + 1)) || balloc(b, &b->d_coff, R + 1) || balloc(b, &b->d_off2, 2 * (R + 1)) ||
+        balloc(b, &b->d_sub_items, R + 1))
+        return engine_fail(b, RBSOG_ENOMEM, "device allocation failed");
+    if (cudaMemset(b->count, 0, sizeof(uint32_t) * C) != cudaSuccess ||
+        cudaMemset(b->ctr, 0, sizeof(DevCounters) * R) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return engine_fail(b, RBSOG_ECUDA, "device initialisation failed");
+    return RBSOG_OK;
+}
+
+void engine_release(rbsog_batch *b) {
+    cudaDeviceSynchronize();
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    b->cap_stream = nullptr;
+    for (void *p : b->allocs) cudaFree(p);
+    b->allocs.clear();
+}
+
+size_t engine_footprint(const rbsog_batch *b, const HostSystem &h) {
+    const SysShape sh = shape_of(h, b->near_target, chunk_for(h.N, b->rho_target));
+    const size_t per_particle = 2 * 9 * 8 - 2 * 4   // rest + work state (id is 4 bytes)
+                                + 2 * 3 * 8          // caller-order staging
+                                + 3 * 3 * 4          // F, Fn, fixed point
+                                + 16 + 3 * 4 + 8;    // record, cell/slot/perm, sort key
+    const size_t per_mode = 3 * 4 * 2 + 8 + 16 + kGTab32Bytes + 8;
+    return (size_t)h.N * per_particle + (size_t)h.box.ncell * 12 + (size_t)h.p.P * per_mode +
+           (size_t)sh.G * 8 * h.p.P * 16 + 4 * (size_t)sh.near_blocks * 8 + far_batch_blocks(h.N) * 8;
+}
+
+bool engine_fits(const rbsog_batch *b, const HostSystem &h) {
+    return b->R < b->capR && (uint64_t)b->Ntot + h.N <= b->capN && (int64_t)b->Ctot + h.box.ncell <= b->capC &&
+           (int64_t)b->Ptot + h.p.P <= b->capP;
+}
+
+int engine_append(rbsog_batch *b, HostSystem &&h) {
+    if (h.p.precision != RBSOG_FP32) return engine_fail(b, RBSOG_EUNSUPPORTED, "resident systems run the FP32 path");
+    if (!engine_fits(b, h)) return engine_fail(b, RBSOG_ENOMEM, "system does not fit the engine's capacity");
+    const uint32_t N = h.N;
+    const int cells = h.box.ncell, P = h.p.P;
+    b->rho_chunk.push_back(chunk_for(N, b->rho_target));
+    b->sys.push_back(std::move(h));
+    b->R += 1;
+    b->Ntot += N;
+    b->Ctot += cells;
+    b->Ptot += P;
+    b->p_off.push_back(b->Ntot);
+    b->c_off.push_back((uint32_t)b->Ctot);
+    b->m_off.push_back((uint32_t)b->Ptot);
+    b->dirty = true;
+    return RBSOG_OK;
+}
+
+int engine_retain(rbsog_batch *b, const std::vector<char> &keep, cudaStream_t st) {
+    std::vector<int> idx;
+    for (int r = 0; r < b->R; ++r)
+        if (keep[r]) idx.push_back(r);
+    if ((int)idx.size() == b->R) return RBSOG_OK;
+    const int Rn = (int)idx.size();
+    std::vector<uint32_t> old_off(Rn + 1, 0), new_off(Rn + 1, 0), c_new{0}, m_new{0};
+    std::vector<HostSystem> sys;
+    std::vector<int> chunk;
+    for (int k = 0; k < Rn; ++k) {
+        const int r = idx[k];
+        old_off[k] = b->p_off[r];
+        new_off[k + 1] = new_off[k] + b->sys[r].N;
+        c_new.push_back(c_new.back() + (uint32_t)b->sys[r].box.ncell);
+        m_new.push_back(m_new.back() + (uint32_t)b->sys[r].p.P);
+        chunk.push_back(b->rho_chunk[r]);
+    }
+    // counters move with their systems
+    std::vector<DevCounters> c;
+    if (int code = engine_counters(b, &c)) return code;
+    std::vector<DevCounters> cn(Rn);
+    for (int k = 0; k < Rn; ++k) cn[k] = c[idx[k]];
+    if (Rn) {
+        std::vector<uint32_t> offs(2 * (size_t)(Rn + 1));
+        std::copy(old_off.begin(), old_off.end(), offs.begin());
+        std::copy(new_off.begin(), new_off.end(), offs.begin() + Rn + 1);
+        BCK(cudaMemcpyAsync(b->d_off2, offs.data(), offs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st),
+            "upload relayout offsets");
+        launch_relayout(b->rest, b->work, b->F, b->Fn, b->capN, b->d_off2, b->d_off2 + Rn + 1, Rn, new_off[Rn], st);
+        BCK(cudaGetLastError(), "relayout");
+        BCK(cudaMemcpyAsync(b->ctr, cn.data(), Rn * sizeof(DevCounters), cudaMemcpyHostToDevice, st),
+            "move counters");
+        BCK(cudaStreamSynchronize(st), "synchronize");
+        std::swap(b->rest, b->work);
+        std::swap(b->F, b->Fn);
+    }
+    for (int k = 0; k < Rn; ++k) sys.push_back(std::move(b->sys[idx[k]]));
+    b->sys = std::move(sys);
+    b->rho_chunk = chunk;
+    b->R = Rn;
+    b->p_off = new_off;
+    b->c_off = c_new;
+    b->m_off = m_new;
+    b->Ntot = new_off[Rn];
+    b->Ctot = (int)c_new.back();
+    b->Ptot = (int)m_new.back();
+    b->dirty = true;
+    return RBSOG_OK;
+}
+
+int engine_commit(rbsog_batch *b) {
+    if (!b->dirty) return RBSOG_OK;
+    BCK(cudaDeviceSynchronize(), "synchronize");
     // sampling tables, concatenated system by system
     std::vector<double> mp, axp;
     std::vector<int> ma, off, nmax, axa;
@@ -524,33 +500,216 @@ int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, co
         axp.insert(axp.end(), h.ax_prob.begin(), h.ax_prob.end());
         axa.insert(axa.end(), h.ax_alias.begin(), h.ax_alias.end());
     }
-    std::vector<double> qv(q_host, q_host + n), mv(m_host, m_host + n);
-    if (upload(b, &b->mix_prob, mp) || upload(b, &b->mix_alias, ma) || upload(b, &b->ax_off, off) ||
-        upload(b, &b->ax_nmax, nmax) || upload(b, &b->ax_prob, axp) || upload(b, &b->ax_alias, axa) ||
-        cudaMemcpy(b->q_user, qv.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(b->m_user, mv.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->count, 0, sizeof(uint32_t) * (size_t)b->Ctot) != cudaSuccess ||
-        cudaMemset(b->ctr, 0, sizeof(DevCounters) * ((size_t)R + 1)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return bail(RBSOG_ECUDA, "device initialisation failed");
+    if (mp.size() > b->cap_mix || !b->mix_prob) {
+        size_t cm = 0, c1 = 0, c2 = 0, c3 = 0;
+        BCK(regrow(b, &b->mix_prob, &cm, mp.size()), "alloc sampler");
+        BCK(regrow(b, &b->mix_alias, &c1, mp.size()), "alloc sampler");
+        BCK(regrow(b, &b->ax_off, &c2, 3 * cm), "alloc sampler");
+        BCK(regrow(b, &b->ax_nmax, &c3, 3 * cm), "alloc sampler");
+        b->cap_mix = std::min(cm, c1);
+    }
+    if (axp.size() > b->cap_ax || !b->ax_prob) {
+        size_t ca = 0, c1 = 0;
+        BCK(regrow(b, &b->ax_prob, &ca, axp.size()), "alloc sampler");
+        BCK(regrow(b, &b->ax_alias, &c1, axp.size()), "alloc sampler");
+        b->cap_ax = std::min(ca, c1);
+    }
+    BCK(upload(b->mix_prob, mp), "upload sampler");
+    BCK(upload(b->mix_alias, ma), "upload sampler");
+    BCK(upload(b->ax_off, off), "upload sampler");
+    BCK(upload(b->ax_nmax, nmax), "upload sampler");
+    BCK(upload(b->ax_prob, axp), "upload sampler");
+    BCK(upload(b->ax_alias, axa), "upload sampler");
+    // per-block partial buffers at the current shapes
+    size_t part = 0, upart = 4, kpart = 1;
+    for (int r = 0; r < b->R; ++r) {
+        const HostSystem &h = b->sys[r];
+        const SysShape sh = shape_of(h, b->near_target, b->rho_chunk[r]);
+        part += (size_t)sh.G * 8 * (size_t)h.p.P;
+        upart += 4 * (size_t)sh.near_blocks;
+        kpart += far_batch_blocks(h.N);
+    }
+    BCK(regrow(b, &b->partial, &b->cap_part, part), "alloc partials");
+    BCK(regrow(b, &b->U_part, &b->cap_upart, upart), "alloc partials");
+    BCK(regrow(b, &b->K_part, &b->cap_kpart, kpart), "alloc partials");
+    if (int code = build_args(b)) return code;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    b->dirty = false;
+    return RBSOG_OK;
+}
+
+int engine_set_state(rbsog_batch *b, int first, int count, const double *r, const double *v, const double *q,
+                     const double *m, cudaStream_t st) {
+    if (first < 0 || count < 1 || first + count > b->R) return engine_fail(b, RBSOG_EINVAL, "bad system range");
+    if (int code = engine_commit(b)) return code;
+    uint32_t nbk = 0;
+    if (int code = sub_items(b, first, count, &nbk, st)) return code;
+    // arguments of the subset; caller charges and masses when initialising
+    std::vector<SysStateArgs> ss(b->h_state.begin() + first, b->h_state.begin() + first + count);
+    for (int k = 0; k < count; ++k) {
+        const size_t o = (size_t)b->p_off[first + k] - b->p_off[first];
+        ss[k].q_user = q ? q + o : nullptr;
+        ss[k].m_user = q ? m + o : nullptr;
+    }
+    BCK(cudaMemcpyAsync(b->d_state_sub, ss.data(), ss.size() * sizeof(SysStateArgs), cudaMemcpyHostToDevice, st),
+        "upload state arguments");
+    // the kernel offsets r and v by 3 p_off of each system; shift the base so that
+    // element 0 is the first particle of system `first` (pointer arithmetic only)
+    const size_t shift = 3 * (size_t)b->p_off[first];
+    launch_set_state_batch(b->d_state_sub, b->d_sub_items, count, nbk, r - shift, v ? v - shift : nullptr,
+                           b->ctr + first, count, st);
+    BCK(cudaGetLastError(), "set_state");
+    BCK(cudaStreamSynchronize(st), "synchronize");
+    return RBSOG_OK;
+}
+
+int engine_get_state(rbsog_batch *b, int first, int count, double *r, double *v, cudaStream_t st) {
+    if (first < 0 || count < 1 || first + count > b->R) return engine_fail(b, RBSOG_EINVAL, "bad system range");
+    if (int code = engine_commit(b)) return code;
+    uint32_t nbk = 0;
+    if (int code = sub_items(b, first, count, &nbk, st)) return code;
+    const size_t shift = 3 * (size_t)b->p_off[first];
+    launch_get_state_batch(b->d_state + first, b->d_sub_items, count, nbk, r ? r - shift : nullptr,
+                           v ? v - shift : nullptr, st);
+    BCK(cudaGetLastError(), "get_state");
+    return RBSOG_OK;
+}
+
+int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far, cudaEvent_t *ev) {
+    if (int code = engine_commit(b)) return code;
+    const int R = b->R;
+    if (R == 0) return RBSOG_OK;
+    auto mark = [&](int g) {
+        if (ev) cudaEventRecord(ev[g], st);
+    };
+    mark(0);
+    launch_bin_batch(b->d_bin[set], items_of(b, kItBin), R, b->nb[kItBin], st);
+    mark(1);
+    launch_scan(b->count, b->tile_sums, b->cell_start, b->Ctot, b->Ntot, st);
+    mark(2);
+    launch_scatter_sort(b->cell, b->slot, b->cell_start, b->work.id, b->Ntot, b->Ctot, b->keys, b->perm_src, b->ctr,
+                        st, b->d_coff, R);
+    mark(3);
+    GatherArgs g{};
+    g.in = b->work; g.out = b->rest; g.perm_src = b->perm_src; g.s = b->s; g.rec = b->rec;
+    g.N = b->Ntot; g.stride = b->capN;
+    launch_gather(RBSOG_FP32, g, st);
+    mark(4);
+    launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
+    mark(5);
+    launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
+    mark(6);
+    launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], st);
+    mark(7);
+    launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], st);
+    mark(8);
+    launch_far_batch(far ? far : b->d_far[set], items_of(b, kItFar), R, b->nb[kItFar], st);
+    mark(9);
+    launch_energy_batch(b->d_energy[set], R, st);
+    mark(10);
+    BCK(cudaGetLastError(), "kernel launch");
+    return RBSOG_OK;
+}
+
+int engine_launch_steps(rbsog_batch *b, int n, cudaStream_t st) {
+    if (int code = engine_commit(b)) return code;
+    if (n <= 0 || b->R == 0) return RBSOG_OK;
+    if (!b->graph) {
+        cudaGraph_t g;
+        BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int code = engine_enqueue(b, b->cap_stream, 1);
+        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+        if (code) return code;
+        BCK(e2, "end capture");
+        cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        BCK(e3, "graph instantiate");
+    }
+    for (int i = 0; i < n; ++i) BCK(cudaGraphLaunch(b->graph, st), "graph launch");
+    return RBSOG_OK;
+}
+
+int engine_counters(rbsog_batch *b, std::vector<DevCounters> *out) {
+    out->assign(b->capR, DevCounters{});
+    BCK(cudaMemcpy(out->data(), b->ctr, b->capR * sizeof(DevCounters), cudaMemcpyDeviceToHost), "read counters");
+    return RBSOG_OK;
+}
+
+int engine_status(rbsog_batch *b, const std::vector<DevCounters> &c, int r) {
+    const int e = c[r].err;
+    const std::string who = "system " + std::to_string(r) + ": ";
+    if (e & kErrCellOverflow) return engine_fail(b, RBSOG_EOVERFLOW, who + "a cell holds more than 4096 particles");
+    if (e & kErrSampler) return engine_fail(b, RBSOG_ETIMEOUT, who + "k-sampler exceeded its attempt limit");
+    if (e & kErrNearStage) return engine_fail(b, RBSOG_ETIMEOUT, who + "near-field staging wait exceeded its limit");
+    return RBSOG_OK;
+}
+
+}  // namespace rbsog
+
+extern "C" {
+
+int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, const double *q_host,
+                     const double *m_host, rbsog_batch **out) {
+    if (!out) return engine_fail(nullptr, RBSOG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!params || !N || !q_host || !m_host) return engine_fail(nullptr, RBSOG_EINVAL, "params, N, q or m is NULL");
+    if (R < 1 || R > (1 << 20)) return engine_fail(nullptr, RBSOG_EINVAL, "R must be in [1, 2^20]");
+    std::vector<HostSystem> sys(R);
+    long long nt = 0, ct = 0, pt = 0;
+    for (int r = 0; r < R; ++r) {
+        if (params[r].precision != RBSOG_FP32)
+            return engine_fail(nullptr, RBSOG_EUNSUPPORTED, "batched systems run the FP32 path only");
+        if (params[r].device != params[0].device)
+            return engine_fail(nullptr, RBSOG_EINVAL, "every system of a batch uses the same device");
+        std::string err;
+        const int code = setup_system(params[r], N[r], q_host + nt, m_host + nt, &sys[r], &err);
+        if (code != RBSOG_OK) return engine_fail(nullptr, code, "system " + std::to_string(r) + ": " + err);
+        nt += N[r];
+        ct += sys[r].box.ncell;
+        pt += params[r].P;
+        if (nt >= 0x7fffffffLL || ct > (1LL << 28) || pt > (1LL << 26))
+            return engine_fail(nullptr, RBSOG_EINVAL, "batch too large (particles, cells or modes)");
+    }
+    rbsog_batch *b = new rbsog_batch();
+    auto bail = [&](int code) {
+        g_batch_init_error = b->err;
+        rbsog_batch_free(b);
+        return code;
+    };
+    int code = engine_alloc(b, EngineCaps{(uint32_t)nt, (int)ct, (int)pt, R}, params[0].device);
+    if (code) return bail(code);
     for (int r = 0; r < R; ++r) {
         std::string err;
-        const int code = system_S(&b->sys[r], &err);
-        if (code != RBSOG_OK) return bail(code, err);
+        if ((code = system_S(&sys[r], &err)) != RBSOG_OK) {
+            b->err = err;
+            return bail(code);
+        }
+        if ((code = engine_append(b, std::move(sys[r]))) != RBSOG_OK) return bail(code);
     }
-    if (ensure_partials(b) != RBSOG_OK) return bail(RBSOG_ENOMEM, "device allocation failed (partials)");
-    const int code = build_args(b);
-    if (code != RBSOG_OK) return bail(code, "");
-    // a valid (zero) state so every call is defined before rbsog_batch_set_state
-    if (cudaMemset(b->stage_a, 0, n3 * sizeof(double)) != cudaSuccess) return bail(RBSOG_ECUDA, "device initialisation failed");
-    launch_set_state_batch(b->d_state, items_of(b, kItBin), R, b->nb[kItBin], b->stage_a, nullptr, b->ctr, R + 1, 0);
-    if (cudaDeviceSynchronize() != cudaSuccess) return bail(RBSOG_ECUDA, "device initialisation failed");
+    if ((code = engine_commit(b)) != RBSOG_OK) return bail(code);
+    // charges and masses into the rest state, positions zero: every call is defined
+    // before rbsog_batch_set_state
+    if (cudaMemcpy(b->stage_qm, q_host, nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->stage_qm + b->capN, m_host, nt * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->stage_a, 0, 3 * (size_t)nt * sizeof(double)) != cudaSuccess) {
+        b->err = "device initialisation failed";
+        return bail(RBSOG_ECUDA);
+    }
+    if ((code = engine_set_state(b, 0, R, b->stage_a, nullptr, b->stage_qm, b->stage_qm + b->capN, 0)) != RBSOG_OK)
+        return bail(code);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        b->err = "device initialisation failed";
+        return bail(RBSOG_ECUDA);
+    }
     *out = b;
     return RBSOG_OK;
 }
 
 int rbsog_batch_set_state(rbsog_batch *b, const double *r, const double *v, void *stream) {
-    if (!b || !r) return bfail(b, RBSOG_EINVAL, "batch or r is NULL");
+    if (!b || !r) return engine_fail(b, RBSOG_EINVAL, "batch or r is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = 3 * (size_t)b->Ntot * sizeof(double);
     const double *rd = r, *vd = v;
@@ -562,32 +721,32 @@ int rbsog_batch_set_state(rbsog_batch *b, const double *r, const double *v, void
         BCK(cudaMemcpyAsync(b->stage_b, v, bytes, cudaMemcpyDefault, st), "copy v");
         vd = b->stage_b;
     }
-    launch_set_state_batch(b->d_state, items_of(b, kItBin), b->R, b->nb[kItBin], rd, vd, b->ctr, b->R + 1, st);
-    BCK(cudaGetLastError(), "set_state");
+    if (int code = engine_set_state(b, 0, b->R, rd, vd, nullptr, nullptr, st)) return code;
     b->force_valid = false;
     return RBSOG_OK;
 }
 
 int rbsog_batch_get_state(rbsog_batch *b, double *r, double *v, uint64_t *step, void *stream) {
-    if (!b) return bfail(b, RBSOG_EINVAL, "batch is NULL");
+    if (!b) return engine_fail(b, RBSOG_EINVAL, "batch is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = 3 * (size_t)b->Ntot * sizeof(double);
     double *rd = r && dev_ptr(r) ? r : (r ? b->stage_a : nullptr);
     double *vd = v && dev_ptr(v) ? v : (v ? b->stage_b : nullptr);
-    launch_get_state_batch(b->d_state, items_of(b, kItBin), b->R, b->nb[kItBin], rd, vd, st);
-    BCK(cudaGetLastError(), "get_state");
+    if (rd || vd)
+        if (int code = engine_get_state(b, 0, b->R, rd, vd, st)) return code;
     if (r && rd != r) BCK(cudaMemcpyAsync(r, rd, bytes, cudaMemcpyDefault, st), "copy r out");
     if (v && vd != v) BCK(cudaMemcpyAsync(v, vd, bytes, cudaMemcpyDefault, st), "copy v out");
-    DevCounters hc;
-    BCK(cudaMemcpyAsync(&hc, b->ctr, sizeof hc, cudaMemcpyDeviceToHost, st), "read counters");
     BCK(cudaStreamSynchronize(st), "synchronize");
-    if (step) *step = hc.step;
-    return check_errors(b);
+    std::vector<DevCounters> c;
+    if (int code = engine_counters(b, &c)) return code;
+    if (step) *step = c[0].step;
+    return check_all(b);
 }
 
 int rbsog_batch_forces(rbsog_batch *b, double *F, rbsog_energy *e, void *stream) {
-    if (!b) return bfail(b, RBSOG_EINVAL, "batch is NULL");
+    if (!b) return engine_fail(b, RBSOG_EINVAL, "batch is NULL");
     cudaStream_t st = (cudaStream_t)stream;
+    if (int code = engine_commit(b)) return code;
     const FarArgs *far = nullptr;
     double *Fd = nullptr;
     if (F) {
@@ -600,46 +759,34 @@ int rbsog_batch_forces(rbsog_batch *b, double *F, rbsog_energy *e, void *stream)
         BCK(cudaStreamSynchronize(st), "synchronize");
         far = b->d_far_user;
     }
-    int code = enqueue(b, st, 0, far);
+    int code = engine_enqueue(b, st, 0, far);
     if (code) return code;
     b->force_valid = true;
     if (F && Fd != F)
         BCK(cudaMemcpyAsync(F, Fd, 3 * (size_t)b->Ntot * sizeof(double), cudaMemcpyDefault, st), "copy forces out");
     if (e) return read_energies(b, e, st);
     BCK(cudaStreamSynchronize(st), "synchronize");
-    return check_errors(b);
+    return check_all(b);
 }
 
 int rbsog_batch_step(rbsog_batch *b, int32_t nsteps, rbsog_energy *e, void *stream) {
-    if (!b) return bfail(b, RBSOG_EINVAL, "batch is NULL");
-    if (nsteps < 0) return bfail(b, RBSOG_EINVAL, "nsteps < 0");
+    if (!b) return engine_fail(b, RBSOG_EINVAL, "batch is NULL");
+    if (nsteps < 0) return engine_fail(b, RBSOG_EINVAL, "nsteps < 0");
     cudaStream_t st = (cudaStream_t)stream;
     if (!b->force_valid && nsteps > 0) {
-        int code = enqueue(b, st, 0, nullptr);
-        if (code) return code;
+        if (int code = engine_enqueue(b, st, 0)) return code;
         b->force_valid = true;
     }
-    if (nsteps > 0 && !b->graph) {
-        cudaGraph_t g;
-        BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        int code = enqueue(b, b->cap_stream, 1, nullptr);
-        cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
-        if (code) return code;
-        BCK(e2, "end capture");
-        cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
-        cudaGraphDestroy(g);
-        BCK(e3, "graph instantiate");
-    }
-    for (int i = 0; i < nsteps; ++i) BCK(cudaGraphLaunch(b->graph, st), "graph launch");
+    if (int code = engine_launch_steps(b, nsteps, st)) return code;
     if (e) return read_energies(b, e, st);
     return RBSOG_OK;
 }
 
 int rbsog_batch_set_ksample(rbsog_batch *b, const int32_t *m_host) {
-    if (!b || !m_host) return bfail(b, RBSOG_EINVAL, "batch or m is NULL");
+    if (!b || !m_host) return engine_fail(b, RBSOG_EINVAL, "batch or m is NULL");
     for (int l = 0; l < b->Ptot; ++l)
         if (m_host[3 * l] == 0 && m_host[3 * l + 1] == 0 && m_host[3 * l + 2] == 0)
-            return bfail(b, RBSOG_EINVAL, "mode (0,0,0) is not in the sampled support");
+            return engine_fail(b, RBSOG_EINVAL, "mode (0,0,0) is not in the sampled support");
     BCK(cudaDeviceSynchronize(), "synchronize");
     BCK(cudaMemcpy(b->inject_m, m_host, 3 * sizeof(int32_t) * (size_t)b->Ptot, cudaMemcpyHostToDevice), "copy modes");
     int one = 1;
@@ -649,17 +796,17 @@ int rbsog_batch_set_ksample(rbsog_batch *b, const int32_t *m_host) {
 }
 
 int rbsog_batch_get_ksample(rbsog_batch *b, int32_t *m_host, double *coef_host) {
-    if (!b) return bfail(b, RBSOG_EINVAL, "batch is NULL");
+    if (!b) return engine_fail(b, RBSOG_EINVAL, "batch is NULL");
     BCK(cudaDeviceSynchronize(), "synchronize");
     if (m_host)
         BCK(cudaMemcpy(m_host, b->modes, 3 * sizeof(int32_t) * (size_t)b->Ptot, cudaMemcpyDeviceToHost), "copy modes");
     if (coef_host)
         BCK(cudaMemcpy(coef_host, b->coef, sizeof(double) * (size_t)b->Ptot, cudaMemcpyDeviceToHost), "copy coef");
-    return check_errors(b);
+    return check_all(b);
 }
 
 int rbsog_batch_layout(const rbsog_batch *b, int64_t *p_off, int64_t *m_off, int32_t *rho_chunk) {
-    if (!b) return bfail(nullptr, RBSOG_EINVAL, "batch is NULL");
+    if (!b) return engine_fail(nullptr, RBSOG_EINVAL, "batch is NULL");
     for (int r = 0; r <= b->R; ++r) {
         if (p_off) p_off[r] = b->p_off[r];
         if (m_off) m_off[r] = b->m_off[r];
@@ -669,61 +816,53 @@ int rbsog_batch_layout(const rbsog_batch *b, int64_t *p_off, int64_t *m_off, int
 }
 
 int rbsog_batch_set_rho_chunk(rbsog_batch *b, const int32_t *rho_chunk) {
-    if (!b || !rho_chunk) return bfail(b, RBSOG_EINVAL, "batch or rho_chunk is NULL");
+    if (!b || !rho_chunk) return engine_fail(b, RBSOG_EINVAL, "batch or rho_chunk is NULL");
     for (int r = 0; r < b->R; ++r)
-        if (rho_chunk[r] < 64) return bfail(b, RBSOG_EINVAL, "rho_chunk must be >= 64");
-    BCK(cudaDeviceSynchronize(), "synchronize");
+        if (rho_chunk[r] < 64) return engine_fail(b, RBSOG_EINVAL, "rho_chunk must be >= 64");
     for (int r = 0; r < b->R; ++r) b->rho_chunk[r] = rho_chunk[r];
-    if (int c = ensure_partials(b)) return c;
-    int code = build_args(b);
-    if (code != RBSOG_OK) return code;
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
-    return RBSOG_OK;
+    b->dirty = true;
+    return engine_commit(b);
 }
 
 int rbsog_batch_profile(rbsog_batch *b, int32_t nsteps, double *ms, void *stream) {
-    if (!b || !ms || nsteps < 1) return bfail(b, RBSOG_EINVAL, "batch or ms is NULL, or nsteps < 1");
+    if (!b || !ms || nsteps < 1) return engine_fail(b, RBSOG_EINVAL, "batch or ms is NULL, or nsteps < 1");
     cudaStream_t st = (cudaStream_t)stream;
     EventSet es;
-    if (!es.ok) return bfail(b, RBSOG_ECUDA, "event creation failed");
+    if (!es.ok) return engine_fail(b, RBSOG_ECUDA, "event creation failed");
     for (int g = 0; g < RBSOG_NPROF; ++g) ms[g] = 0.0;
     if (!b->force_valid) {
-        if (int c = enqueue(b, st, 0, nullptr)) return c;
+        if (int c = engine_enqueue(b, st, 0)) return c;
         b->force_valid = true;
     }
     for (int i = 0; i < nsteps; ++i) {
-        if (int c = enqueue(b, st, 1, nullptr, es.ev)) return c;
+        if (int c = engine_enqueue(b, st, 1, nullptr, es.ev)) return c;
         BCK(cudaStreamSynchronize(st), "synchronize");
         for (int g = 0; g < RBSOG_NPROF; ++g) ms[g] += es.ms(g, g + 1);
     }
-    return check_errors(b);
+    return check_all(b);
 }
 
 int rbsog_batch_set_shapes(rbsog_batch *b, double near_target, int32_t rho_target) {
-    if (!b) return bfail(b, RBSOG_EINVAL, "batch is NULL");
+    if (!b) return engine_fail(b, RBSOG_EINVAL, "batch is NULL");
     if (!(near_target >= 8.0 && near_target <= 4096.0) || rho_target < 64)
-        return bfail(b, RBSOG_EINVAL, "need 8 <= near_target <= 4096 and rho_target >= 64");
-    BCK(cudaDeviceSynchronize(), "synchronize");
+        return engine_fail(b, RBSOG_EINVAL, "need 8 <= near_target <= 4096 and rho_target >= 64");
     return apply_shapes(b, near_target, rho_target);
 }
 
 int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t *rho_target, void *stream) {
-    if (!b || reps < 1) return bfail(b, RBSOG_EINVAL, "batch is NULL or reps < 1");
+    if (!b || reps < 1) return engine_fail(b, RBSOG_EINVAL, "batch is NULL or reps < 1");
     cudaStream_t st = (cudaStream_t)stream;
     EventSet es;
-    if (!es.ok) return bfail(b, RBSOG_EINVAL, "event creation failed");
+    if (!es.ok) return engine_fail(b, RBSOG_EINVAL, "event creation failed");
     // the counters are restored afterwards, so the tuning evaluations leave no trace in
     // the draws; the next step re-evaluates the forces
-    std::vector<DevCounters> saved(b->R + 1);
     BCK(cudaStreamSynchronize(st), "synchronize");
-    BCK(cudaMemcpy(saved.data(), b->ctr, saved.size() * sizeof(DevCounters), cudaMemcpyDeviceToHost), "save counters");
+    std::vector<DevCounters> saved;
+    if (int code = engine_counters(b, &saved)) return code;
     const double near_c[] = {48.0, 80.0, 110.0, 160.0};
     const int rho_c[] = {256, 512, 1024, 2048};
     double best_near = b->near_target, best_near_ms = 1e30;
-    int best_rho = 512;
+    int best_rho = b->rho_target;
     double best_rho_ms = 1e30;
     int code = RBSOG_OK;
     for (int ci = 0; ci < 4 && code == RBSOG_OK; ++ci) {
@@ -731,9 +870,10 @@ int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t 
         if ((code = apply_shapes(b, near_c[ci], rho_c[ci])) != RBSOG_OK) break;
         std::vector<double> tn, tr;
         for (int i = 0; i <= reps && code == RBSOG_OK; ++i) {
-            if ((code = enqueue(b, st, 0, nullptr, es.ev)) != RBSOG_OK) break;
-            if (cudaStreamSynchronize(st) != cudaSuccess) {
-                code = bcuda_fail(b, cudaGetLastError(), "synchronize");
+            if ((code = engine_enqueue(b, st, 0, nullptr, es.ev)) != RBSOG_OK) break;
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) {
+                code = engine_cuda_fail(b, e, "synchronize");
                 break;
             }
             if (i == 0) continue;   // first run after a shape change: warm-up
@@ -753,17 +893,14 @@ int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t 
     BCK(e, "restore counters");
     if (near_target) *near_target = best_near;
     if (rho_target) *rho_target = best_rho;
-    return check_errors(b);
+    return check_all(b);
 }
 
 const char *rbsog_batch_last_error(const rbsog_batch *b) { return b ? b->err.c_str() : g_batch_init_error.c_str(); }
 
 void rbsog_batch_free(rbsog_batch *b) {
     if (!b) return;
-    cudaDeviceSynchronize();
-    if (b->graph) cudaGraphExecDestroy(b->graph);
-    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    for (void *p : b->allocs) cudaFree(p);
+    engine_release(b);
     delete b;
 }
 

@@ -38,6 +38,26 @@ class rbsog_energy(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class rbsog_server_config(C.Structure):
+    _fields_ = [("max_particles", C.c_int64), ("max_cells", C.c_int64), ("max_modes", C.c_int64),
+                ("near_target", C.c_double), ("max_jobs", C.c_int32), ("steps_per_round", C.c_int32),
+                ("rho_target", C.c_int32), ("device", C.c_int32), ("reserved", C.c_int32 * 2)]
+
+
+class rbsog_job_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("error", C.c_int32), ("N", C.c_int64), ("nsteps", C.c_int32),
+                ("steps_done", C.c_int32), ("t_arrival", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("footprint_bytes", C.c_uint64), ("energy", rbsog_energy)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "energy"}
+        d["energy"] = self.energy.as_dict()
+        return d
+
+
+RBSOG_JOB_QUEUED, RBSOG_JOB_RESIDENT, RBSOG_JOB_DONE, RBSOG_JOB_FAILED = 0, 1, 2, 3
+
+
 class RbsogError(RuntimeError):
     pass
 
@@ -49,7 +69,9 @@ EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_forces", "
            "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
            "rbsog_batch_forces", "rbsog_batch_step", "rbsog_batch_set_ksample", "rbsog_batch_get_ksample",
            "rbsog_batch_layout", "rbsog_batch_set_rho_chunk", "rbsog_batch_set_shapes", "rbsog_batch_tune",
-           "rbsog_batch_profile", "rbsog_batch_last_error", "rbsog_batch_free"]
+           "rbsog_batch_profile", "rbsog_batch_last_error", "rbsog_batch_free", "rbsog_server_create",
+           "rbsog_server_submit", "rbsog_server_run", "rbsog_server_job", "rbsog_server_stats", "rbsog_server_clock",
+           "rbsog_server_last_error", "rbsog_server_free"]
 RBSOG_NPROF = 10
 
 
@@ -106,9 +128,21 @@ def load(build_if_missing: bool = True):
     L.rbsog_batch_last_error.restype = C.c_char_p
     L.rbsog_batch_free.argtypes = [vp]
     L.rbsog_batch_free.restype = None
+    L.rbsog_server_create.argtypes = [C.POINTER(rbsog_server_config), C.POINTER(vp)]
+    L.rbsog_server_submit.argtypes = [vp, C.POINTER(rbsog_params), i64, vp, vp, vp, vp, i32, C.c_double,
+                                      C.POINTER(i64)]
+    L.rbsog_server_run.argtypes = [vp, C.c_double]
+    L.rbsog_server_job.argtypes = [vp, i64, C.POINTER(rbsog_job_info), vp, vp]
+    L.rbsog_server_stats.argtypes = [vp, vp]
+    L.rbsog_server_clock.argtypes = [vp]
+    L.rbsog_server_clock.restype = C.c_double
+    L.rbsog_server_last_error.argtypes = [vp]
+    L.rbsog_server_last_error.restype = C.c_char_p
+    L.rbsog_server_free.argtypes = [vp]
+    L.rbsog_server_free.restype = None
     for name in EXPORTS:
         if name not in ("rbsog_profile_name", "rbsog_last_error", "rbsog_free", "rbsog_batch_last_error",
-                        "rbsog_batch_free"):
+                        "rbsog_batch_free", "rbsog_server_clock", "rbsog_server_last_error", "rbsog_server_free"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -352,6 +386,84 @@ def rbsog_batch_last_error(b=None) -> str:
 def rbsog_batch_free(b):
     if b:
         load().rbsog_batch_free(b)
+
+
+# ---- job server ------------------------------------------------------------------------
+
+def _scheck(s, code):
+    if code != RBSOG_OK:
+        msg = load().rbsog_server_last_error(s)
+        raise RbsogError(f"{STATUS.get(code, code)}: {msg.decode() if msg else ''}")
+
+
+def make_server_config(max_particles: int, max_cells: int, max_modes: int, max_jobs: int,
+                       steps_per_round: int = 32, near_target: float = 0.0, rho_target: int = 0,
+                       device: int = 0) -> rbsog_server_config:
+    c = rbsog_server_config()
+    c.max_particles, c.max_cells, c.max_modes = int(max_particles), int(max_cells), int(max_modes)
+    c.near_target, c.max_jobs, c.steps_per_round = float(near_target), int(max_jobs), int(steps_per_round)
+    c.rho_target, c.device = int(rho_target), int(device)
+    c.reserved[0] = c.reserved[1] = 0
+    return c
+
+
+def rbsog_server_create(cfg: rbsog_server_config):
+    out = C.c_void_p()
+    _scheck(None, load().rbsog_server_create(C.byref(cfg), C.byref(out)))
+    return out.value
+
+
+def rbsog_server_submit(s, params: rbsog_params, q, m, r, v=None, nsteps: int = 0, t_arrival: float = -1.0) -> int:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    v = None if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    jid = C.c_int64(-1)
+    _scheck(s, load().rbsog_server_submit(s, C.byref(params), int(q.shape[0]), q.ctypes.data, m.ctypes.data,
+                                          r.ctypes.data, None if v is None else v.ctypes.data, int(nsteps),
+                                          float(t_arrival), C.byref(jid)))
+    return jid.value
+
+
+def rbsog_server_run(s, t_until: float = -1.0):
+    _scheck(s, load().rbsog_server_run(s, float(t_until)))
+
+
+def rbsog_server_job(s, job_id: int, N: int | None = None, state: bool = False):
+    """(info dict, r, v); r and v only for a done job when state is True.  A failed job's
+    info is returned with its error code (no exception)."""
+    info = rbsog_job_info()
+    r = v = None
+    if state:
+        r = np.zeros((N, 3))
+        v = np.zeros((N, 3))
+    code = load().rbsog_server_job(s, int(job_id), C.byref(info), None if r is None else r.ctypes.data,
+                                   None if v is None else v.ctypes.data)
+    if code != RBSOG_OK and not (info.status == RBSOG_JOB_FAILED and code == info.error):
+        _scheck(s, code)
+    return info.as_dict(), r, v
+
+
+def rbsog_server_stats(s) -> dict:
+    out = np.zeros(8, dtype=np.float64)
+    _scheck(s, load().rbsog_server_stats(s, out.ctypes.data))
+    keys = ["rounds", "admissions", "retirements", "busy_s", "particle_steps", "peak_particles", "peak_jobs",
+            "setup_s"]
+    return dict(zip(keys, out.tolist()))
+
+
+def rbsog_server_clock(s) -> float:
+    return float(load().rbsog_server_clock(s))
+
+
+def rbsog_server_last_error(s=None) -> str:
+    msg = load().rbsog_server_last_error(s)
+    return msg.decode() if msg else ""
+
+
+def rbsog_server_free(s):
+    if s:
+        load().rbsog_server_free(s)
 
 
 def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int | None = None,

@@ -30,14 +30,14 @@ def test_library_exports_every_declared_function():
     assert sorted(R.EXPORTS) == names
 
 
-def test_struct_layouts_match_the_c_header(tmp_path):
-    """ctypes mirrors of rbsog_params / rbsog_energy against the C compiler's own layout."""
+@pytest.mark.parametrize("struct", [R.rbsog_params, R.rbsog_energy, R.rbsog_server_config, R.rbsog_job_info])
+def test_struct_layouts_match_the_c_header(tmp_path, struct):
+    """ctypes mirrors of the ABI structs against the C compiler's own layout."""
+    name = struct.__name__
     src = tmp_path / "layout.c"
-    fields_p = [f for f, _ in R.rbsog_params._fields_]
-    fields_e = [f for f, _ in R.rbsog_energy._fields_]
-    body = ['printf("%zu %zu\\n", sizeof(rbsog_params), sizeof(rbsog_energy));']
-    body += [f'printf("%zu\\n", offsetof(rbsog_params, {f}));' for f in fields_p]
-    body += [f'printf("%zu\\n", offsetof(rbsog_energy, {f}));' for f in fields_e]
+    fields = [f for f, _ in struct._fields_]
+    body = [f'printf("%zu\\n", sizeof({name}));']
+    body += [f'printf("%zu\\n", offsetof({name}, {f}));' for f in fields]
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "rbsog.h"\nint main(void){' +
                    "".join(body) + "return 0;}\n")
     exe = tmp_path / "layout"
@@ -45,10 +45,8 @@ def test_struct_layouts_match_the_c_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     vals = [int(x) for x in out]
-    assert vals[0] == C.sizeof(R.rbsog_params) and vals[1] == C.sizeof(R.rbsog_energy)
-    offs = vals[2:]
-    assert offs[:len(fields_p)] == [getattr(R.rbsog_params, f).offset for f in fields_p]
-    assert offs[len(fields_p):] == [getattr(R.rbsog_energy, f).offset for f in fields_e]
+    assert vals[0] == C.sizeof(struct)
+    assert vals[1:] == [getattr(struct, f).offset for f in fields]
 
 
 def base_params():
@@ -141,3 +139,15 @@ def test_batch_rejects_fp64_and_names_the_bad_system():
     with pytest.raises(R.RbsogError, match="EINVAL"):
         R.rbsog_batch_init([], [], q, m)
     assert R.rbsog_batch_last_error(None)
+
+
+def test_server_config_is_checked_on_the_host():
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_server_create(R.make_server_config(1, 10, 10, 1))
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_server_create(R.make_server_config(1000, 10, 10, 0))
+    cfg = R.make_server_config(1000, 10, 10, 1)
+    cfg.reserved[1] = 3
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_server_create(cfg)
+    assert "configuration" in R.rbsog_server_last_error(None)

@@ -1,0 +1,142 @@
+"""GPU job server (rbsog_server_*): continuous batching of MD jobs.  Each job's result is
+bit-identical alone and in a mix where jobs join while others are mid-run, agrees with a
+single context within the FP32 tolerance, waits for memory when the arenas are full, and
+fails alone when its own cells overflow."""
+import numpy as np
+import pytest
+
+from gpu_common import FP32_TOL, Ctx, require_gpu, workload
+from oracle import core
+from paper_2501_10946_gb300 import rbsog as R
+from paper_2501_10946_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    return require_gpu()
+
+
+def jobs():
+    """(workload, nsteps): uneven N, box shapes, screening, coupling, P and ensembles."""
+    return [
+        (workload(1500, 11.0, kappa=1.0, Gamma=2.0, P=96, seed=51, ensemble="langevin"), 50),
+        (workload(600, 8.0, kappa=2.5, Gamma=20.0, P=300, seed=53), 20),
+        (workload(800, 9.0, kappa=0.5, Gamma=1.0, P=128, seed=55, ensemble="langevin"), 37),
+        (workload(200, 4.0, kappa=1.0, Gamma=1.0, rc=1.9, P=64, seed=57), 10),
+        (workload(2500, None, kappa=1.5, Gamma=5.0, P=200, seed=59, box=(15.0, 12.0, 12.0)), 13),
+    ]
+
+
+def server(max_jobs=8, max_particles=20000, steps_per_round=8):
+    cfg = R.make_server_config(max_particles, max_particles, 4096, max_jobs, steps_per_round=steps_per_round)
+    return R.rbsog_server_create(cfg)
+
+
+def submit(s, w, nsteps, t=0.0, r=None):
+    p = R.make_params(w, precision=R.RBSOG_FP32)
+    r = W.positions(w) if r is None else r
+    return R.rbsog_server_submit(s, p, W.charges(w), W.masses(w), r, W.velocities(w), nsteps, t)
+
+
+def run_jobs(js, **kw):
+    s = server(**kw)
+    try:
+        ids = [submit(s, w, n) for w, n in js]
+        R.rbsog_server_run(s)
+        out = [R.rbsog_server_job(s, i, w.N, state=True) for i, (w, _) in zip(ids, js)]
+        stats = R.rbsog_server_stats(s)
+    finally:
+        R.rbsog_server_free(s)
+    return out, stats
+
+
+def test_each_job_is_the_same_alone_and_in_the_mix():
+    js = jobs()
+    # two job slots: jobs 3.. are admitted only as earlier ones retire, so they join
+    # while others are mid-run
+    mix, stats = run_jobs(js, max_jobs=2)
+    assert stats["admissions"] == len(js) and stats["retirements"] == len(js)
+    assert stats["peak_jobs"] == 2
+    infos = [m[0] for m in mix]
+    # at least one job was admitted while another was resident and mid-run
+    joined = [i for i in range(len(js)) for k in range(len(js))
+              if k != i and infos[k]["t_admit"] < infos[i]["t_admit"] < infos[k]["t_done"]]
+    assert joined
+    for i, (w, n) in enumerate(js):
+        alone, _ = run_jobs([(w, n)])
+        info_a, r_a, v_a = alone[0]
+        info_m, r_m, v_m = mix[i]
+        assert info_m["status"] == R.RBSOG_JOB_DONE and info_m["steps_done"] == n
+        assert info_m["energy"]["step"] == n
+        assert np.array_equal(r_a, r_m), i
+        assert np.array_equal(v_a, v_m), i
+        assert info_a["energy"]["total"] == info_m["energy"]["total"], i
+
+
+def test_served_job_follows_a_single_context():
+    w, n = jobs()[2]
+    out, _ = run_jobs([(w, n)])
+    info, r, v = out[0]
+    with Ctx(w, R.RBSOG_FP32) as c:
+        R.rbsog_set_state(c.h, W.positions(w), W.velocities(w))
+        e = R.rbsog_step(c.h, n, energy=True)
+        rs = np.zeros((w.N, 3))
+        vs = np.zeros((w.N, 3))
+        R.rbsog_get_state(c.h, rs, vs)
+    d = r - rs
+    L = np.asarray(w.box)
+    d -= L * np.round(d / L)
+    assert np.max(np.abs(d)) <= 1e-6 * np.max(L)
+    assert core.rel_l2(v, vs) <= FP32_TOL
+    assert info["energy"]["step"] == e["step"] == n
+
+
+def test_admission_waits_for_memory():
+    """Arenas for 2000 particles: a 1500- and an 800-particle job cannot be resident
+    together, so the second is admitted only after the first retires."""
+    js = [jobs()[0], jobs()[2]]
+    out, stats = run_jobs(js, max_particles=2000)
+    first, second = out[0][0], out[1][0]
+    assert first["status"] == second["status"] == R.RBSOG_JOB_DONE
+    assert second["t_admit"] >= first["t_done"]
+    assert stats["peak_jobs"] == 1
+    assert first["footprint_bytes"] > 1500 * 200
+
+
+def test_a_failing_job_fails_alone():
+    """A job whose particles all sit in one cell overflows the cell list: it fails with
+    EOVERFLOW and the job beside it completes unchanged."""
+    good, n_good = jobs()[0]
+    bad = workload(5000, 20.0, kappa=1.0, Gamma=1.0, P=64, seed=61)
+    s = server(max_particles=20000)
+    try:
+        i_bad = submit(s, bad, 5, r=np.full((bad.N, 3), 3.0))
+        i_good = submit(s, good, n_good)
+        R.rbsog_server_run(s)
+        info_bad, _, _ = R.rbsog_server_job(s, i_bad)
+        info_good, r_g, v_g = R.rbsog_server_job(s, i_good, good.N, state=True)
+    finally:
+        R.rbsog_server_free(s)
+    assert info_bad["status"] == R.RBSOG_JOB_FAILED and R.STATUS[info_bad["error"]] == "EOVERFLOW"
+    alone, _ = run_jobs([(good, n_good)])
+    assert info_good["status"] == R.RBSOG_JOB_DONE
+    assert np.array_equal(alone[0][1], r_g) and np.array_equal(alone[0][2], v_g)
+
+
+def test_arrivals_in_the_future_wait_and_stats_add_up():
+    js = jobs()[:3]
+    s = server()
+    try:
+        ids = [submit(s, w, n, t=0.05 * k) for k, (w, n) in enumerate(js)]
+        R.rbsog_server_run(s)
+        infos = [R.rbsog_server_job(s, i)[0] for i in ids]
+        stats = R.rbsog_server_stats(s)
+    finally:
+        R.rbsog_server_free(s)
+    for k, info in enumerate(infos):
+        assert info["status"] == R.RBSOG_JOB_DONE
+        assert info["t_admit"] >= info["t_arrival"] == pytest.approx(0.05 * k)
+        assert info["t_done"] >= info["t_admit"]
+    assert stats["particle_steps"] == sum(w.N * n for w, n in js)
