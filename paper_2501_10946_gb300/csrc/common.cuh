@@ -55,7 +55,7 @@ struct Box {
     double invL[3];       // 1/L rounded to double (fixed point and wrap multiply by it)
     int nc[3];
     int ncell;
-    double cellscale_unused;
+    double invL32[3];     // 2^32 / L (exact scaling of invL)
     double L_2m32[3];     // L / 2^32
     double L_2m64[3];     // L / 2^64
     float L_2m32f[3];

@@ -27,10 +27,25 @@ __device__ __forceinline__ double wrap_coord(double r, double L, double invL) {
     return w;
 }
 
-__device__ __forceinline__ double frac01(double r, double invL) {
-    double u = __dmul_rn(r, invL);
-    double f = __dsub_rn(u, floor(u));
-    return f >= 1.0 ? 0.0 : f;
+// wrap_coord for a position that left [0, L) by less than one box length, with the FP64
+// pipe (1/72 of the FP32 rate on this part) used only for the rare correction: the range
+// tests compare the IEEE bit patterns as integers (ordered like the values for w >= 0).
+// For r in [-L, 2L) the result equals wrap_coord(r) bit for bit; outside, wrap_coord.
+__device__ __forceinline__ double wrap_near(double r, double L, double invL) {
+    const long long bL = __double_as_longlong(L);
+    long long b = __double_as_longlong(r);
+    if (b >= 0 && b < bL) return r;                       // already in [0, L) (+0 included)
+    double w = r;
+    if (b < 0) {                                          // negative (or -0)
+        w = __dadd_rn(r, L);
+        if (__double_as_longlong(w) < 0) return wrap_coord(r, L, invL);   // below -L
+    }
+    b = __double_as_longlong(w);
+    if (b >= bL) {
+        w = __dsub_rn(w, L);
+        if (__double_as_longlong(w) >= bL) return wrap_coord(r, L, invL);  // 2L or beyond
+    }
+    return w;
 }
 
 template <int PREC>
@@ -83,7 +98,7 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
                 xi[0] = rad * c2; xi[1] = rad * s2; xi[2] = rad3 * cospi(2.0 * u4);
             }
             // noise amplitude sqrt((1 - c1^2) kT / m); FP32 suffices for the FP32 build
-            const double sig = PREC == 1 ? (double)sqrtf((float)((1.0 - a.c1 * a.c1) * a.kT * invm))
+            const double sig = PREC == 1 ? (double)sqrtf((float)(a.okT * invm))
                                          : sqrt((1.0 - a.c1 * a.c1) * a.kT * invm);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
@@ -96,14 +111,19 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
     uint32_t cc[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        r[d] = wrap_coord(r[d], a.box.L[d], a.box.invL[d]);
-        double f = frac01(r[d], a.box.invL[d]);
+        r[d] = wrap_near(r[d], a.box.L[d], a.box.invL[d]);
+        // r in [0, L): u = r (1/L) is in [0, 1], frac(u) = u except u = 1 (frac 0), and
+        // u 2^32 = r (2^32/L) exactly (a power-of-two scaling commutes with rounding), so
+        // s = floor(frac(r (1/L)) 2^32) takes one multiply and one conversion
         uint32_t s32;
         if (PREC == 1) {
-            s32 = (uint32_t)__double2ull_rz(f * 4294967296.0);
+            // u = 1 gives 2^32, whose low 32 bits are 0
+            s32 = (uint32_t)__double2ull_rz(__dmul_rn(r[d], a.box.invL32[d]));
             ((uint32_t *)a.s)[(size_t)d * N + k] = s32;
         } else {
-            unsigned long long s64 = __double2ull_rz(f * 18446744073709551616.0);
+            const double u = __dmul_rn(r[d], a.box.invL[d]);
+            const unsigned long long s64 =
+                __double_as_longlong(u) >= 0x3ff0000000000000LL ? 0ull : __double2ull_rz(u * 18446744073709551616.0);
             ((unsigned long long *)a.s)[(size_t)d * N + k] = s64;
             s32 = (uint32_t)(s64 >> 32);
         }

@@ -292,6 +292,32 @@ __device__ __forceinline__ double finish_particle(const FarArgs &a, uint32_t p, 
     return 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm;
 }
 
+// FP32 build: the total force is formed in FP32 (the Kahan far sum rounded once, plus the
+// FP32 near force); FP64 is kept for the velocity kick and the kinetic energy.
+__device__ __forceinline__ double finish_particle32(const FarArgs &a, uint32_t p, const float *Ff) {
+    const uint32_t N = a.stride;
+    const float *fn = (const float *)a.Fn;
+    const float Fn[3] = {fn[p], fn[N + p], fn[2 * (size_t)N + p]};
+    float Ft[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Ft[d] = Fn[d] + Ff[d];
+    float *F = (float *)a.F;
+    F[p] = Ft[0]; F[N + p] = Ft[1]; F[2 * (size_t)N + p] = Ft[2];
+    double v[3] = {a.st.vx[p], a.st.vy[p], a.st.vz[p]};
+    const double invm = a.st.invm[p];
+    if (a.integrate && a.ctr->fvalid) {
+        const double hk = 0.5 * a.dt * invm;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) v[d] += hk * (double)Ft[d];
+        a.st.vx[p] = v[0]; a.st.vy[p] = v[1]; a.st.vz[p] = v[2];
+    }
+    const size_t u = 3 * (size_t)a.st.id[p];
+    if (a.F_user) { a.F_user[u] = Ft[0]; a.F_user[u + 1] = Ft[1]; a.F_user[u + 2] = Ft[2]; }
+    if (a.Fn_user) { a.Fn_user[u] = Fn[0]; a.Fn_user[u + 1] = Fn[1]; a.Fn_user[u + 2] = Fn[2]; }
+    if (a.Ff_user) { a.Ff_user[u] = Ff[0]; a.Ff_user[u + 1] = Ff[1]; a.Ff_user[u + 2] = Ff[2]; }
+    return 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm;
+}
+
 // FP32: two particles per thread (p and p + 256) share each mode's table entry.  The
 // gather sums over modes whose phases are unrelated, so rounding of the phase scaling is
 // incoherent here and the argument needs no half-turn reduction (unlike rho).
@@ -331,18 +357,18 @@ __device__ __forceinline__ void far32_body(const FarArgs &a, unsigned bx, GTab32
     }
     double K = 0.0;
     if (v0) {
-        double Ff[3];
-        const double q = (double)__uint_as_float(r0.w);
+        float Ff[3];
+        const float q = __uint_as_float(r0.w);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) Ff[d] = -q * ((double)S0[d] - (double)C0[d]);
-        K += finish_particle<1>(a, p0, Ff);
+        for (int d = 0; d < 3; ++d) Ff[d] = -q * (S0[d] - C0[d]);
+        K += finish_particle32(a, p0, Ff);
     }
     if (v1) {
-        double Ff[3];
-        const double q = (double)__uint_as_float(r1.w);
+        float Ff[3];
+        const float q = __uint_as_float(r1.w);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) Ff[d] = -q * ((double)S1[d] - (double)C1[d]);
-        K += finish_particle<1>(a, p1, Ff);
+        for (int d = 0; d < 3; ++d) Ff[d] = -q * (S1[d] - C1[d]);
+        K += finish_particle32(a, p1, Ff);
     }
     const double tot = block_reduce_sum<double>(K, shK);
     if (threadIdx.x == 0) a.K_part[bx] = tot;

@@ -27,7 +27,6 @@ namespace {
 
 constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
-constexpr int kRegionCap = 1280;       // staged particles per CTA (20 KB)
 constexpr int kListCap = 32;           // listed candidates per thread between flushes
 constexpr int kMaxTileW = 64;
 
@@ -190,8 +189,11 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
 }
 
 // ---------------------------------------------------------------- tiled (TMA) FP32 path
+// CAP: staged particles per CTA (16 B each).  One large system stages 1280 (7 CTAs per
+// SM); batches of many systems stage 1024 (8 CTAs per SM), which measured faster there.
+template <int CAP>
 struct TileSmem {
-    uint4 stage[kRegionCap];                // staged records
+    uint4 stage[CAP];                       // staged records
     uint16_t list[kListCap][kTileThreads];  // per-thread candidate lists (staging indices)
     int seg_off[9][kMaxTileW + 3];          // per row: offset of each region cell within the row
     int row_base[10];                       // per row: offset of the row in the staging buffer
@@ -202,7 +204,8 @@ struct TileSmem {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void flush_list(const TileSmem &S, const NearConsts &nc, const Box &box, int cnt,
+template <int CAP>
+__device__ __forceinline__ void flush_list(const TileSmem<CAP> &S, const NearConsts &nc, const Box &box, int cnt,
                                            uint4 ri, float qi, float *Fs, float *Fc, float &Us, float &Uc) {
     for (int k = 0; k < cnt; ++k) {
         const uint4 rj = S.stage[S.list[k][threadIdx.x]];
@@ -213,7 +216,9 @@ __device__ __forceinline__ void flush_list(const TileSmem &S, const NearConsts &
     }
 }
 
-__device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk, TileSmem &S) {
+template <int CAP>
+__device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
+                                               TileSmem<CAP> &S) {
     const int tid = threadIdx.x;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
     const int tile = (int)(blk % (unsigned)tiles_x);
@@ -272,7 +277,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     }
     __syncthreads();
     const int region_n = S.row_base[9];
-    const bool staged = !overflow && region_n <= kRegionCap;
+    const bool staged = !overflow && region_n <= CAP;
     // center row (r = 4): targets are region cells 1 .. wn-2, contiguous in global memory
     const uint32_t g_first = cs[nx * (cy + ny * cz) + x0];
     const uint32_t g_end = cs[nx * (cy + ny * cz) + x1];
@@ -346,27 +351,46 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                 const uint4 ri = S.stage[j];
                 const float qi = __uint_as_float(ri.w);
                 float Fs[3] = {0.f, 0.f, 0.f}, Fc[3] = {0.f, 0.f, 0.f}, Us = 0.f, Uc = 0.f;
+                const float sx = a.box.L_2m32f[0], sy = a.box.L_2m32f[1], sz = a.box.L_2m32f[2];
                 for (int r0 = 0; r0 < 9; r0 += 3) {
+                    // filter: list the hits of three rows (the list keeps the first kListCap,
+                    // the count keeps going); the loop holds no pair arithmetic
                     int cnt = 0;
                     for (int r = r0; r < r0 + 3; ++r) {
                         const int rb = S.row_base[r];
                         const int k0 = rb + S.seg_off[r][i - 1];
                         const int k1 = rb + S.seg_off[r][i + 2];
+#pragma unroll 2
                         for (int k = k0; k < k1; ++k) {
                             const uint4 rk = S.stage[k];
-                            const float d0 = (float)(int)(ri.x - rk.x) * a.box.L_2m32f[0];
-                            const float d1 = (float)(int)(ri.y - rk.y) * a.box.L_2m32f[1];
-                            const float d2 = (float)(int)(ri.z - rk.z) * a.box.L_2m32f[2];
+                            const float d0 = (float)(int)(ri.x - rk.x) * sx;
+                            const float d1 = (float)(int)(ri.y - rk.y) * sy;
+                            const float d2 = (float)(int)(ri.z - rk.z) * sz;
                             if (d0 * d0 + d1 * d1 + d2 * d2 < rc2 && k != j) {
-                                S.list[cnt][tid] = (uint16_t)k;
-                                if (++cnt == kListCap) {        // rare: more hits than the list holds
-                                    flush_list(S, a.nc, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
-                                    cnt = 0;
-                                }
+                                if (cnt < kListCap) S.list[cnt][tid] = (uint16_t)k;
+                                ++cnt;
                             }
                         }
                     }
-                    flush_list(S, a.nc, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
+                    if (cnt <= kListCap) {
+                        flush_list(S, a.nc, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
+                    } else {
+                        // rare: more hits than the list holds; evaluate the three rows
+                        // directly, in the same candidate order
+                        for (int r = r0; r < r0 + 3; ++r) {
+                            const int rb = S.row_base[r];
+                            const int k1 = rb + S.seg_off[r][i + 2];
+                            for (int k = rb + S.seg_off[r][i - 1]; k < k1; ++k) {
+                                const uint4 rk = S.stage[k];
+                                const float d0 = (float)(int)(ri.x - rk.x) * sx;
+                                const float d1 = (float)(int)(ri.y - rk.y) * sy;
+                                const float d2 = (float)(int)(ri.z - rk.z) * sz;
+                                if (d0 * d0 + d1 * d1 + d2 * d2 < rc2 && k != j)
+                                    pair_f32(a.nc, qi * __uint_as_float(rk.w), d0, d1, d2,
+                                             d0 * d0 + d1 * d1 + d2 * d2, Fs, Fc, Us, Uc);
+                            }
+                        }
+                    }
                 }
                 const uint32_t g = g_first + (uint32_t)(j - t0);
                 Fn[g] = Fs[0] - Fc[0];
@@ -391,7 +415,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
 
 __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_tile_body(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem *>(smem_raw));
+    near_tile_body<kNearCapSingle>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle> *>(smem_raw));
 }
 
 // Batched systems: block -> (system, local block); each system uses tiles or the
@@ -409,7 +433,8 @@ __global__ void __launch_bounds__(kTileThreads) k_near_batch(const NearArgs *arg
     const NearArgs &a = args[lo];
     const NearBatchGeom g = geom[lo];
     const unsigned blk = blockIdx.x - items[lo];
-    if (g.tiled) near_tile_body(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem *>(smem_raw));
+    if (g.tiled)
+        near_tile_body<kNearCapBatch>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch> *>(smem_raw));
     else near_global_block<1>(a, (uint32_t)g.W, blk);
 }
 
@@ -417,7 +442,8 @@ inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 
 
 }  // namespace
 
-void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks, double target) {
+void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks, double target,
+                   int cap) {
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
     if (nx >= 3 && ny >= 3 && nz >= 3) {
         // tile width: about `target` (default 110) targets per CTA and about 1000 staged
@@ -425,7 +451,7 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
         // rarely overflow it)
         const double occ = (double)N / (double)box.ncell;
         int Wt = (int)(target / (occ > 1e-9 ? occ : 1e-9));
-        int Wcap = (int)(1000.0 / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
+        int Wcap = (int)(0.78 * cap / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
         if (Wt > Wcap) Wt = Wcap;
         if (Wt > kMaxTileW) Wt = kMaxTileW;
         if (Wt > nx - 2) Wt = nx - 2;
@@ -445,8 +471,10 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
 static void set_tile_smem_attr() {
     static bool done = false;
     if (!done) {
-        cudaFuncSetAttribute(k_near_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
-        cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem));
+        cudaFuncSetAttribute(k_near_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(TileSmem<kNearCapSingle>));
+        cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(TileSmem<kNearCapBatch>));
         done = true;
     }
 }
@@ -457,7 +485,7 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     near_geometry(a.box, a.N, &tiled, &W, &tiles_x, &nb);
     if (prec == 1 && tiled) {
         set_tile_smem_attr();
-        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem), st>>>(a, W, tiles_x);
+        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem<kNearCapSingle>), st>>>(a, W, tiles_x);
         return (int)nb * kWarpsPerBlock;
     }
     nb = blocks_for(a.N, kGlobalThreads);
@@ -469,7 +497,7 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
 void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
                        uint32_t nblocks, cudaStream_t st) {
     set_tile_smem_attr();
-    k_near_batch<<<nblocks, kTileThreads, sizeof(TileSmem), st>>>(args, geom, items, R);
+    k_near_batch<<<nblocks, kTileThreads, sizeof(TileSmem<kNearCapBatch>), st>>>(args, geom, items, R);
 }
 
 }  // namespace rbsog

@@ -12,6 +12,7 @@ struct BinArgs {
     const void *F;            // forces of the rest order, SoA [3][N]: float (FP32) or double (FP64)
     int integrate;            // 0 none, 1 velocity Verlet (kick + drift), 2 BAOAB (B A O A)
     double dt, c1, kT;
+    double okT;               // (1 - c1^2) k_B T: the FP32 build's noise variance per unit 1/m
     unsigned long long seed;
     DevCounters *ctr;
     uint32_t N;               // particles of this system
@@ -157,9 +158,12 @@ struct NearBatchGeom {
     int tiled;                 // 1: shared-memory tiles, 0: per-particle global path
     int W, tiles_x;
 };
-// target: particles per CTA the tile width aims at (capped by the staging buffer)
+// Staged particles per near-field CTA: one large system, and the batched kernel.
+constexpr int kNearCapSingle = 1280;
+constexpr int kNearCapBatch = 1024;
+// target: particles per CTA the tile width aims at (capped by the staging buffer `cap`)
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks,
-                   double target = 110.0);
+                   double target = 110.0, int cap = kNearCapSingle);
 void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
                        uint32_t nblocks, cudaStream_t st);
 void launch_rho_batch(const RhoArgs *args, const int *chunk, const uint32_t *items, int R, uint32_t nblocks,

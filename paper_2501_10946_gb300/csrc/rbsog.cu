@@ -151,6 +151,7 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
     for (int d = 0; d < 3; ++d) {
         bx.L[d] = p.box[d];
         bx.invL[d] = 1.0 / p.box[d];
+        bx.invL32[d] = bx.invL[d] * 4294967296.0;
         int n = (int)std::floor(p.box[d] / p.r_c);
         bx.nc[d] = n >= 3 ? n : 1;
         ncell *= bx.nc[d];
@@ -363,6 +364,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     BinArgs b{};
     b.in = c->rest; b.out = c->work; b.F = c->F; b.integrate = integrate;
     b.dt = c->p.dt; b.c1 = std::exp(-c->p.langevin_gamma * c->p.dt); b.kT = c->kT; b.seed = c->p.seed;
+    b.okT = (1.0 - b.c1 * b.c1) * b.kT;
     b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.s = c->s; b.cell = c->cell;
     b.slot = c->slot; b.count = c->count;
     { ProfScope ps(c, st, 0); launch_bin(prec, b, st); }

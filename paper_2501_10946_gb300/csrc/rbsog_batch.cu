@@ -90,7 +90,7 @@ struct SysShape {
 
 SysShape shape_of(const HostSystem &h, double near_target, int chunk) {
     SysShape s{};
-    near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target);
+    near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target, kNearCapBatch);
     s.G = (int)((h.N + (uint32_t)chunk - 1) / (uint32_t)chunk);
     return s;
 }
@@ -135,6 +135,7 @@ int build_args(rbsog_batch *b) {
             a.dt = p.dt;
             a.c1 = std::exp(-p.langevin_gamma * p.dt);
             a.kT = h.kT;
+            a.okT = (1.0 - a.c1 * a.c1) * a.kT;
             a.seed = p.seed;
             a.ctr = ctr;
             a.N = N;
