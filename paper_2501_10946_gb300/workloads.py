@@ -167,8 +167,8 @@ def cfg_replicas(R: int = 256, seed: int = 401, steps: int = 500) -> list:
 def cfg_stream(n_jobs: int = 64, rate: float = 50.0, seed: int = 501) -> list:
     """Served request stream: n_jobs YOCP jobs with Poisson arrivals (mean `rate` per s),
     N log-uniform in [1e3, 2e5], kappa uniform in [0.2, 3], Gamma log-uniform in
-    [0.5, 150], steps uniform in [100, 2000], P in {64, 128, 256}, r_c = 3a, reduced
-    density 1, NVE, FP32 forces.  Returns [(Workload, nsteps, t_arrival_s)]."""
+    [0.5, 150], steps uniform in [100, 2000], P = 128, r_c = 3a, reduced density 1, NVE,
+    FP32 forces.  Returns [(Workload, nsteps, t_arrival_s)]."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     t = 0.0
@@ -178,7 +178,7 @@ def cfg_stream(n_jobs: int = 64, rate: float = 50.0, seed: int = 501) -> list:
         kappa = float(rng.uniform(0.2, 3.0))
         Gamma = float(math.exp(rng.uniform(math.log(0.5), math.log(150.0))))
         nsteps = int(rng.integers(100, 2001))
-        P = int(rng.choice([64, 128, 256]))
+        P = 128
         L = box_for_unit_a(N)
         s = seed * 1000 + 4 * i
         w = Workload(f"job{i}_n{N}", N, (L, L, L), 1.0, kappa, Gamma, 3.0, 1e-6, P, 0.01, nsteps, "nve", 1.0,
