@@ -57,6 +57,15 @@ extern "C" {
 #define RBSOG_SOG_BOUND 1     /* ceilings of Eqs. (29)-(30) at the C0 root alpha_1 of Eq. (35) */
 #define RBSOG_SOG_TABLE 2     /* sog_M1, sog_M2 given (e.g. a row of Table 1) */
 
+/* Sampling measure P(k) = calF(k) Fhat(k) / S of Eq. (59), S = sum_{k != 0} calF Fhat, and
+ * coef_l = S / (P V calF(k_l)) (Eq. 60), for the three corrections compared in Sec. 5
+ * (Fig. 9).  Every choice gives an unbiased estimator; they differ in variance. */
+#define RBSOG_SAMPLING_ADAPTIVE 0   /* calF of Eq. (62) (Debye-Hueckel structure factor) */
+#define RBSOG_SAMPLING_UNIFORM 1    /* calF = 1: P(k) proportional to Fhat (as in RBE) */
+#define RBSOG_SAMPLING_K2 2         /* calF = k^2 (as in RBSOG for Coulomb systems) */
+#define RBSOG_SAMPLING_DEBYE 3      /* Eq. (62) with the Debye wavenumber of Gaussian units:
+                                       4 pi sum q^2 / (kT V) in place of sum q^2 / (kT V) */
+
 typedef struct rbsog_ctx rbsog_ctx;
 typedef struct rbsog_batch rbsog_batch;
 typedef struct rbsog_server rbsog_server;
@@ -79,7 +88,7 @@ typedef struct rbsog_params {
     int32_t sog_M1;         /* with RBSOG_SOG_TABLE: M1 of Eq. (37) */
     int32_t sog_M2;         /* with RBSOG_SOG_TABLE: M2 of Eq. (37) */
     int32_t device;         /* CUDA device ordinal */
-    int32_t reserved;       /* must be 0 */
+    int32_t sampling;       /* RBSOG_SAMPLING_*: correction calF of the sampling measure (Eq. 59) */
 } rbsog_params;
 
 typedef struct rbsog_energy {

@@ -46,7 +46,8 @@ def lib():
         L.orc_rho.argtypes = [i64, _dp, _dp, _dp, C.c_int, _i32p, _dp]
         L.orc_far_rb.argtypes = [i64, _dp, _dp, _dp, C.c_int, _i32p, _dp, _dp, i64, vp, _dp]
         L.orc_far_full.argtypes = [i64, _dp, _dp, _dp, _dp, d, _dp, C.POINTER(d)]
-        L.orc_S_sum.argtypes = [_dp, _dp, d, d, d]; L.orc_S_sum.restype = d
+        L.orc_S_sum.argtypes = [_dp, _dp, d, d, d, C.c_int]; L.orc_S_sum.restype = d
+        L.orc_measure.argtypes = [C.c_int, d, d, d, d, d]; L.orc_measure.restype = d
         L.orc_real_far.argtypes = [i64, _dp, _dp, _dp, _dp, C.c_int, _dp, C.POINTER(d)]
         L.orc_brute_yukawa.argtypes = [i64, _dp, _dp, _dp, d, d, _dp, C.POINTER(d)]
         L.orc_num_threads.restype = C.c_int
@@ -85,6 +86,15 @@ def fhat(sog: SOG, k2: float) -> float:
 
 def calF(k2: float, kT: float, V: float, Q2: float, lam: float) -> float:
     return lib().orc_calF(float(k2), float(kT), float(V), float(Q2), float(lam))
+
+
+# sampling measures of Eq. (59): adaptive calF of Eq. (62), calF = 1, calF = k^2, and Eq. (62)
+# with the Debye wavenumber of Gaussian units (4 pi sum q^2 / (kT V))
+ADAPTIVE, UNIFORM, K2, DEBYE = 0, 1, 2, 3
+
+
+def measure(kind: int, k2: float, kT: float, V: float, Q2: float, lam: float) -> float:
+    return lib().orc_measure(int(kind), float(k2), float(kT), float(V), float(Q2), float(lam))
 
 
 def kmax2_of(sog: SOG) -> float:
@@ -170,9 +180,10 @@ def far_full(r, q, L, sog: SOG, kmax2=None):
     return F, U.value
 
 
-def S_sum(L, sog: SOG, kT, Q2, kmax2=None):
+def S_sum(L, sog: SOG, kT, Q2, kmax2=None, kind: int = ADAPTIVE):
+    """S = sum_{k != 0} calF(k) Fhat(k) for the measure `kind` (Eq. 59)."""
     kmax2 = kmax2_of(sog) if kmax2 is None else float(kmax2)
-    return lib().orc_S_sum(_f64(L), sog.as_array(), float(kT), float(Q2), kmax2)
+    return lib().orc_S_sum(_f64(L), sog.as_array(), float(kT), float(Q2), kmax2, int(kind))
 
 
 def real_far(r, q, L, sog: SOG, nimg: int):
@@ -195,8 +206,9 @@ def self_energy(q, sog: SOG) -> float:
     return -0.5 * float(np.sum(q * q)) * sog_F(sog, 0.0)
 
 
-def rb_coef(m, L, sog: SOG, kT, Q2, S, P=None):
-    """coef_l = S / (P V calF(k_l)) for the modes m (Eq. 60 with P(k) of Eq. 59)."""
+def rb_coef(m, L, sog: SOG, kT, Q2, S, P=None, kind: int = ADAPTIVE):
+    """coef_l = S / (P V calF(k_l)) for the modes m (Eq. 60 with P(k) of Eq. 59), calF of
+    the measure `kind`."""
     m = np.asarray(m, dtype=np.float64).reshape(-1, 3)
     P = m.shape[0] if P is None else P
     V = (float(L[0]) * float(L[1])) * float(L[2])
@@ -204,7 +216,7 @@ def rb_coef(m, L, sog: SOG, kT, Q2, S, P=None):
     for l in range(m.shape[0]):
         k = [2.0 * math.pi * m[l, a] / float(L[a]) for a in range(3)]
         k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2]
-        out[l] = S / (P * V * calF(k2, kT, V, Q2, sog.lam))
+        out[l] = S / (P * V * measure(kind, k2, kT, V, Q2, sog.lam))
     return out
 
 
@@ -216,7 +228,7 @@ def rb_energy(rho_, coef, q, L, sog: SOG) -> float:
     return float(np.sum(0.5 * _f64(coef) * (rho_[:, 0] ** 2 + rho_[:, 1] ** 2))) + fhat(sog, 0.0) * qs * qs / (2.0 * V)
 
 
-def rb_forces(r, q, L, rc, sog: SOG, m, kT, S=None, near="cells", idx=None, rho_=None):
+def rb_forces(r, q, L, rc, sog: SOG, m, kT, S=None, near="cells", idx=None, rho_=None, kind: int = ADAPTIVE):
     """Total force (near + random-batch far) on the k-set m and the energy terms.
 
     Returns (F_total, F_near, F_far, energies) with energies = dict(U_N, U_F, U_self).
@@ -225,8 +237,8 @@ def rb_forces(r, q, L, rc, sog: SOG, m, kT, S=None, near="cells", idx=None, rho_
     q = _f64(q)
     Q2 = float(np.sum(q * q))
     if S is None:
-        S = S_sum(L, sog, kT, Q2)
-    coef = rb_coef(m, L, sog, kT, Q2, S)
+        S = S_sum(L, sog, kT, Q2, kind=kind)
+    coef = rb_coef(m, L, sog, kT, Q2, S, kind=kind)
     if rho_ is None:
         rho_ = rho(r, q, L, m)
     Ff = far_rb(r, q, L, m, coef, rho_, idx=idx)

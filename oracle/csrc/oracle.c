@@ -91,6 +91,21 @@ double orc_calF(double k2, double kT, double V, double Q2, double lam) {
     return kT * V / (kT * V / Q2 + epsinv_over_k2);
 }
 
+/* Correction calF(k) of the sampling measure P(k) = calF Fhat / S (Eq. 59) for the three
+ * choices compared in Sec. 5 (Fig. 9): 0 the adaptive Debye-Hueckel form of Eq. (62) as
+ * printed, 1 calF = 1 (the Gaussian itself, as in RBE), 2 calF = k^2 (as in Coulomb
+ * RBSOG); and 3 Eq. (62) with the Debye wavenumber of Gaussian units, 4 pi sum q^2 / (kT V)
+ * in place of sum q^2 / (kT V) (the Debye-Hueckel <|rho|^2> for Fhat ~ 4 pi/(k^2 + 1/lambda^2)). */
+double orc_measure(int measure, double k2, double kT, double V, double Q2, double lam) {
+    if (measure == 1) return 1.0;
+    if (measure == 2) return k2;
+    if (measure == 3) {
+        double epsinv_over_k2 = 1.0 / (k2 + 1.0 / (lam * lam));
+        return kT * V / (kT * V / Q2 + (4.0 * M_PI) * epsinv_over_k2);
+    }
+    return orc_calF(k2, kT, V, Q2, lam);
+}
+
 /* ---- fixed-point coordinates and the cell list ----------------------- */
 
 /* Fractional coordinate of r in [0,1): u = r (1/L) with the reciprocal rounded to
@@ -305,8 +320,8 @@ void orc_far_full(int64_t N, const double *r, const double *q, const double *L, 
 }
 
 /* Normalisation S = sum_{k != 0, |k|^2 <= kmax2} calF(k) Fhat(k) of the sampling
- * measure P(k) = calF Fhat / S (Eq. 59). */
-double orc_S_sum(const double *L, const double *sog, double kT, double Q2, double kmax2) {
+ * measure P(k) = calF Fhat / S (Eq. 59), calF of the chosen measure (orc_measure). */
+double orc_S_sum(const double *L, const double *sog, double kT, double Q2, double kmax2, int measure) {
     double V = L[0] * L[1] * L[2], lam = sog[5];
     int nmax[3];
     for (int a = 0; a < 3; ++a) nmax[a] = (int)floor(sqrt(kmax2) * L[a] / (2.0 * M_PI)) + 1;
@@ -320,7 +335,7 @@ double orc_S_sum(const double *L, const double *sog, double kT, double Q2, doubl
                 double kx = 2.0 * M_PI * mx / L[0], ky = 2.0 * M_PI * my / L[1], kz = 2.0 * M_PI * mz / L[2];
                 double k2 = kx * kx + ky * ky + kz * kz;
                 if (k2 > kmax2) continue;
-                Sx += orc_calF(k2, kT, V, Q2, lam) * orc_fhat(sog, k2);
+                Sx += orc_measure(measure, k2, kT, V, Q2, lam) * orc_fhat(sog, k2);
             }
         S += Sx;
     }

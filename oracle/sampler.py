@@ -1,4 +1,4 @@
-"""Exact i.i.d. draws of Fourier modes from the adaptive importance measure, FP64.
+"""Exact i.i.d. draws of Fourier modes from the importance measures of Eq. (59), FP64.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -19,6 +19,18 @@ paper's own sampler is Metropolis-Hastings, Sec. 4.3, while the variance lemma
   4. accept with probability calF(k) / sum_j q_j^2 (calF increases with |k| towards
      sum q^2), else start over.
 Accepted modes are distributed as P(k).
+
+DEBYE (Eq. 62 with the Debye wavenumber of Gaussian units, 4 pi sum q^2 / (k_B T V)) is the
+same procedure with sum q^2 replaced by 4 pi sum q^2 in the acceptance ratio of step 4:
+calF_D(k) = kT V / (kT V / sum q^2 + 4 pi / (k^2 + lambda^-2)) also rises to sum q^2.
+
+The other two corrections compared in Sec. 5 (Fig. 9) use the same machinery:
+  calF = 1:    steps 1-3 only (every nonzero draw is accepted);
+  calF = k^2:  k^2 Fhat(k) = sum_m A_m sum_a k_a^2 g_{m,a}(n_a) prod_{b != a} g_{m,b}(n_b) is a
+               mixture over (m, a) with weights A_m sigma_{m,a} prod_{b != a} theta_{m,b},
+               sigma_{m,a} = sum_n (2 pi n / L_a)^2 g_{m,a}(n); step 1 picks (m, a) (index
+               3 m + a), axis a is drawn from the k_a^2-weighted table (whose n = 0 entry has
+               weight 0, so k != 0) and the other axes from the plain tables; no rejection.
 
 Random numbers: Philox4x32-10, key = (seed lo, seed hi), counter = (slot l, 8*attempt + j,
 draw lo, draw hi) with j = 0 for the Gaussian index, j = 1, 2, 3 for the axes, j = 4 for
@@ -71,10 +83,15 @@ def vose_alias(weights):
     return np.asarray(prob, dtype=np.float64), np.asarray(alias, dtype=np.int64)
 
 
-class ModeSampler:
-    """Tables for drawing k from P(k) for one (SOG, box, k_B T, charges) state."""
+ADAPTIVE, UNIFORM, K2, DEBYE = 0, 1, 2, 3
 
-    def __init__(self, sog: SOG, L, kT: float, Q2: float):
+
+class ModeSampler:
+    """Tables for drawing k from P(k) for one (SOG, box, k_B T, charges) state and one
+    measure (ADAPTIVE: calF of Eq. 62; UNIFORM: calF = 1; K2: calF = k^2)."""
+
+    def __init__(self, sog: SOG, L, kT: float, Q2: float, kind: int = ADAPTIVE):
+        self.kind = int(kind)
         self.sog = sog
         self.L = [float(x) for x in L]
         self.kT = float(kT)
@@ -87,31 +104,51 @@ class ModeSampler:
         self.b = [math.exp(float(x)) for x in t]
         self.A = [sog.h * float(wt[i]) * math.pi ** 1.5 * float(f_tr(float(t[i]), 0.0, sog.lam))
                   * math.exp(-1.5 * float(t[i])) for i in range(len(t))]
-        self.axis = []       # per m: list of 3 (nmax, prob, alias)
+        self.axis = []       # per mixture component: list of 3 (nmax, prob, alias)
         mix = []
         for i, b in enumerate(self.b):
-            tabs = []
-            prod = 1.0
+            plain, sq = [], []
+            theta, sigma = [], []
             for a in range(3):
                 nmax = int(math.ceil(math.sqrt(4.0 * b * LN_1E18) / self.tpl[a]))
-                g = []
+                g, g2 = [], []
                 for n in range(-nmax, nmax + 1):
                     kk = self.tpl[a] * n
-                    g.append(math.exp(-(kk * kk) / (4.0 * b)))
-                theta = 0.0
+                    e = math.exp(-(kk * kk) / (4.0 * b))
+                    g.append(e)
+                    g2.append((kk * kk) * e)
+                th = 0.0
                 for x in g:
-                    theta += x
+                    th += x
+                sg = 0.0
+                for x in g2:
+                    sg += x
                 prob, alias = vose_alias(g)
-                tabs.append((nmax, prob, alias))
-                prod = prod * theta
-            self.axis.append(tabs)
-            mix.append(self.A[i] * prod)
+                plain.append((nmax, prob, alias))
+                theta.append(th)
+                if self.kind == K2:
+                    prob2, alias2 = vose_alias(g2)
+                    sq.append((nmax, prob2, alias2))
+                    sigma.append(sg)
+            if self.kind == K2:
+                for a in range(3):
+                    tabs = [sq[c] if c == a else plain[c] for c in range(3)]
+                    self.axis.append(tabs)
+                    w = self.A[i] * sigma[a]
+                    for c in range(3):
+                        if c != a:
+                            w = w * theta[c]
+                    mix.append(w)
+            else:
+                self.axis.append(plain)
+                mix.append(self.A[i] * ((theta[0] * theta[1]) * theta[2]))
         self.mix_prob, self.mix_alias = vose_alias(mix)
 
     def accept_ratio(self, k2):
-        """calF(k)/sum q^2 = kT V / (kT V + Q2/(k^2 + lambda^-2))."""
+        """calF(k)/sum q^2 = kT V / (kT V + Q2/(k^2 + lambda^-2)), with 4 pi Q2 for DEBYE."""
         A = self.kT * self.V
-        return A / (A + self.Q2 * (1.0 / (k2 + self.inv_lam2)))
+        Q2 = (4.0 * math.pi) * self.Q2 if self.kind == DEBYE else self.Q2
+        return A / (A + Q2 * (1.0 / (k2 + self.inv_lam2)))
 
     def k2_of(self, m):
         m = np.asarray(m, dtype=np.float64)
@@ -149,8 +186,11 @@ class ModeSampler:
                     wsel = [x[sel] for x in words[1 + a]]
                     n[sel, a] = self._alias_pick(wsel, prob, alias, 2 * nmax + 1) - nmax
             nonzero = np.any(n != 0, axis=1)
-            u = philox.u53(words[4][0], words[4][1])
-            ok = nonzero & (u < self.accept_ratio(self.k2_of(n)))
+            if self.kind in (ADAPTIVE, DEBYE):
+                u = philox.u53(words[4][0], words[4][1])
+                ok = nonzero & (u < self.accept_ratio(self.k2_of(n)))
+            else:
+                ok = nonzero
             out[todo[ok]] = n[ok]
             attempts[todo[ok]] = att + 1
             todo = todo[~ok]
@@ -159,6 +199,13 @@ class ModeSampler:
 
     # --- exact measure (for pins) ---
     def calF(self, k2):
+        k2 = np.asarray(k2, dtype=np.float64)
+        if self.kind == UNIFORM:
+            return np.ones_like(k2)
+        if self.kind == K2:
+            return k2
+        if self.kind == DEBYE:
+            return self.kT * self.V / (self.kT * self.V / self.Q2 + (4.0 * math.pi) / (k2 + self.inv_lam2))
         return self.kT * self.V / (self.kT * self.V / self.Q2 + 1.0 / (k2 + self.inv_lam2))
 
     def fhat(self, k2):

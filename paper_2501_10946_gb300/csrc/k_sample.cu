@@ -2,14 +2,21 @@
 // and the normalisation S = sum_{k != 0} calF(k) Fhat(k).
 //
 // Fhat is a sum of Gaussians (Eq. 54) that factorises per axis, so one attempt is:
-//   Gaussian index m      alias table, weights A_m prod_a theta_{m,a}
-//   n_a per axis          alias table of exp(-(2 pi n/L_a)^2 / (4 b_m)), |n| <= nmax_{m,a}
-//   reject n = 0; accept with probability calF(k)/sum q^2 (calF of Eq. 62 is
-//   increasing in |k| with supremum sum q^2)
+//   mixture component     alias table (for calF of Eq. 62 and calF = 1 the Gaussian m,
+//                         weights A_m prod_a theta_{m,a}; for calF = k^2 the pair (m, a)
+//                         of k^2 Fhat = sum_m sum_a k_a^2 (...), weights A_m sigma_{m,a}
+//                         prod_{b != a} theta_{m,b})
+//   n_a per axis          the component's alias tables over |n| <= nmax_{m,a}: the
+//                         discrete Gaussian exp(-(2 pi n/L_a)^2 / (4 b_m)), or on axis a of
+//                         a k^2 component that Gaussian times (2 pi n/L_a)^2
+//   reject n = 0; for calF of Eq. 62 accept with probability calF(k)/sum q^2 (increasing
+//   in |k| with supremum sum q^2); the other measures accept every nonzero draw
 // which yields i.i.d. draws from P(k).  Random words: Philox4x32-10, key = seed,
 // counter = (slot, 8 attempt + j, draw lo, draw hi): j = 0 Gaussian, 1..3 axes,
 // 4 acceptance.  An alias draw from words (x0..x3) takes index floor((x0 2^32 + x1)
 // n / 2^64) and keeps it when u53(x2, x3) < prob, else takes the alias.
+#include <math_constants.h>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "philox.cuh"
@@ -46,6 +53,11 @@ __device__ __forceinline__ void sample_body(const SampleArgs &a, int l) {
                                    a.tab.ax_alias + off, 2 * nm + 1) - nm;
             }
             if (n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+            if (a.measure == 1 || a.measure == 2) {   // calF = 1 or k^2: the mixture is P(k) itself
+                m[0] = n[0]; m[1] = n[1]; m[2] = n[2];
+                done = true;
+                break;
+            }
             U4 wa = philox10((uint32_t)l, cb + 4u, d0, d1, k0, k1);
             double u = u53_of(wa.x, wa.y);
             double kx = __dmul_rn(a.tpl[0], (double)n[0]);
@@ -53,7 +65,7 @@ __device__ __forceinline__ void sample_body(const SampleArgs &a, int l) {
             double kz = __dmul_rn(a.tpl[2], (double)n[2]);
             double k2 = __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
             double g2 = __ddiv_rn(1.0, __dadd_rn(k2, a.inv_lam2));
-            double ratio = __ddiv_rn(a.A, __dadd_rn(a.A, __dmul_rn(a.Q2, g2)));
+            double ratio = __ddiv_rn(a.A, __dadd_rn(a.A, __dmul_rn(a.Q2a, g2)));
             if (u < ratio) {
                 m[0] = n[0]; m[1] = n[1]; m[2] = n[2];
                 done = true;
@@ -65,7 +77,10 @@ __device__ __forceinline__ void sample_body(const SampleArgs &a, int l) {
     // coef = S / (P V calF(k)),  calF = kT V / (kT V / Q2 + 1/(k^2 + lambda^-2))   (Eqs. 60, 62)
     double kx = a.tpl[0] * m[0], ky = a.tpl[1] * m[1], kz = a.tpl[2] * m[2];
     double k2 = kx * kx + ky * ky + kz * kz;
-    double calF = a.A / (a.A / a.Q2 + 1.0 / (k2 + a.inv_lam2));
+    const double calF =
+        a.measure == 1 ? 1.0
+                       : (a.measure == 2 ? k2
+                                         : a.A / (a.A / a.Q2 + (a.measure == 3 ? 4.0 * CUDART_PI : 1.0) / (k2 + a.inv_lam2)));
     a.coef_out[l] = a.S / ((double)a.P * a.V * calF);
 }
 
@@ -102,7 +117,11 @@ __global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
         if (k2 > a.kmax2) continue;
         double fh = 0.0;
         for (int g = 0; g < a.mtot; ++g) fh += a.A[g] * exp(-k2 * a.inv4b[g]);
-        const double calF = a.kTV / (a.kTV / a.Q2 + 1.0 / (k2 + a.inv_lam2));
+        const double calF =
+            a.measure == 1 ? 1.0
+                           : (a.measure == 2 ? k2
+                                             : a.kTV / (a.kTV / a.Q2 + (a.measure == 3 ? 4.0 * CUDART_PI : 1.0) /
+                                                                           (k2 + a.inv_lam2)));
         acc += calF * fh;
     }
     sh[threadIdx.x] = acc;

@@ -49,8 +49,10 @@ void launch_set_state(const double *r, const double *v, const double *q_user, co
 void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st);
 
 // ---- sampler and normalisation (k_sample.cu) ----
+// A mixture of separable components: component c has weight mix and per-axis alias
+// tables (ax_off, ax_nmax) over |n| <= nmax.
 struct SamplerTables {
-    int mtot;
+    int mtot;                 // number of mixture components
     const double *mix_prob; const int *mix_alias;     // [mtot]
     const int *ax_off;        // [mtot*3] offset into ax_prob/ax_alias
     const int *ax_nmax;       // [mtot*3]
@@ -65,6 +67,8 @@ struct SampleArgs {
     double Q2;                // sum q^2
     double inv_lam2;
     double S, V;
+    int measure;              // RBSOG_SAMPLING_*: calF of Eq. (62), 1, k^2, Eq. (62) with 4 pi
+    double Q2a;               // sum q^2 in the acceptance ratio (4 pi sum q^2 for the Debye form)
     DevCounters *ctr;
     const int *inject_m;      // [P*3]
     int *m_out;               // [P*3]
@@ -78,6 +82,7 @@ struct SArgs {
     double kmax2;
     int nmax[3];
     double kTV, Q2, inv_lam2;
+    int measure;
 };
 void launch_S(const SArgs &a, double *partials, cudaStream_t st);   // partials[2*nmax[0]+1]
 

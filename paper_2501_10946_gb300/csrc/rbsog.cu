@@ -121,7 +121,7 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
     if (p.precision != RBSOG_FP64 && p.precision != RBSOG_FP32) return bad(RBSOG_EINVAL, "bad precision");
     if (p.ensemble != RBSOG_NVE && p.ensemble != RBSOG_LANGEVIN) return bad(RBSOG_EINVAL, "bad ensemble");
     if (p.sog_mode < 0 || p.sog_mode > 2) return bad(RBSOG_EINVAL, "bad sog_mode");
-    if (p.reserved != 0) return bad(RBSOG_EINVAL, "reserved must be 0");
+    if (p.sampling < 0 || p.sampling > 3) return bad(RBSOG_EINVAL, "bad sampling measure");
     const double Lmin = std::fmin(p.box[0], std::fmin(p.box[1], p.box[2]));
     if (!(p.r_c > 0) || p.r_c > 0.5 * Lmin) return bad(RBSOG_EINVAL, "need 0 < r_c <= min(L)/2");
     if (!(p.dt >= 0)) return bad(RBSOG_EINVAL, "dt must be >= 0");
@@ -196,35 +196,63 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
     }
     h.Uself = -0.5 * h.Q2 * F0;
     h.Ufar0 = h.Fhat0 * h.qsum * h.qsum / (2.0 * h.V);
-    // sampling tables (Eq. 59): per-axis discrete Gaussians and the mixture over m
+    // sampling tables (Eq. 59): the measure's mixture of separable components.  calF of
+    // Eq. (62) and calF = 1 draw from Fhat (component m: Gaussian m, plain per-axis tables;
+    // Eq. 62 adds a rejection step); calF = k^2 uses k^2 Fhat = sum_m sum_a k_a^2 (...):
+    // component 3m + a has a k_a^2-weighted table on axis a and plain tables elsewhere.
     const double LN_1E18 = 41.44653167389282;
-    std::vector<double> mixw(mt);
-    h.ax_off.assign(3 * mt, 0);
-    h.ax_nmax.assign(3 * mt, 0);
+    std::vector<double> mixw;
+    h.ax_off.clear();
+    h.ax_nmax.clear();
     h.ax_prob.clear();
     h.ax_alias.clear();
+    auto add_table = [&](const std::vector<double> &w, int *off) {
+        std::vector<double> pr;
+        std::vector<int> al;
+        vose(w, &pr, &al);
+        *off = (int)h.ax_prob.size();
+        h.ax_prob.insert(h.ax_prob.end(), pr.begin(), pr.end());
+        h.ax_alias.insert(h.ax_alias.end(), al.begin(), al.end());
+    };
     for (int i = 0; i < mt; ++i) {
         const double b = h.sb[i];
-        double prod = 1.0;
+        int off_plain[3], off_sq[3], nmax[3];
+        double theta[3], sigma[3];
         for (int a = 0; a < 3; ++a) {
             const int nm = (int)std::ceil(std::sqrt(4.0 * b * LN_1E18) / bx.tpl[a]);
-            std::vector<double> g(2 * nm + 1);
-            double theta = 0.0;
+            std::vector<double> g(2 * nm + 1), g2(2 * nm + 1);
             for (int n = -nm; n <= nm; ++n) {
                 const double kk = bx.tpl[a] * n;
-                g[n + nm] = std::exp(-(kk * kk) / (4.0 * b));
+                const double e = std::exp(-(kk * kk) / (4.0 * b));
+                g[n + nm] = e;
+                g2[n + nm] = (kk * kk) * e;
             }
-            for (double x : g) theta += x;
-            std::vector<double> pr;
-            std::vector<int> al;
-            vose(g, &pr, &al);
-            h.ax_off[3 * i + a] = (int)h.ax_prob.size();
-            h.ax_nmax[3 * i + a] = nm;
-            h.ax_prob.insert(h.ax_prob.end(), pr.begin(), pr.end());
-            h.ax_alias.insert(h.ax_alias.end(), al.begin(), al.end());
-            prod = prod * theta;
+            double th = 0.0, sg = 0.0;
+            for (double x : g) th += x;
+            for (double x : g2) sg += x;
+            nmax[a] = nm;
+            theta[a] = th;
+            sigma[a] = sg;
+            add_table(g, &off_plain[a]);
+            if (p.sampling == RBSOG_SAMPLING_K2) add_table(g2, &off_sq[a]);
         }
-        mixw[i] = h.sA[i] * prod;
+        if (p.sampling == RBSOG_SAMPLING_K2) {
+            for (int a = 0; a < 3; ++a) {
+                double w = h.sA[i] * sigma[a];
+                for (int c = 0; c < 3; ++c) {
+                    if (c != a) w = w * theta[c];
+                    h.ax_off.push_back(c == a ? off_sq[c] : off_plain[c]);
+                    h.ax_nmax.push_back(nmax[c]);
+                }
+                mixw.push_back(w);
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                h.ax_off.push_back(off_plain[c]);
+                h.ax_nmax.push_back(nmax[c]);
+            }
+            mixw.push_back(h.sA[i] * ((theta[0] * theta[1]) * theta[2]));
+        }
     }
     vose(mixw, &h.mix_prob, &h.mix_alias);
     return RBSOG_OK;
@@ -248,6 +276,7 @@ int system_S(HostSystem *hs, std::string *err) {
     a.kTV = h.kT * h.V;
     a.Q2 = h.Q2;
     a.inv_lam2 = 1.0 / (h.lam * h.lam);
+    a.measure = h.p.sampling;
     const int nb = 2 * a.nmax[0] + 1;
     double *parts = nullptr;
     cudaError_t e = cudaMalloc(&parts, nb * sizeof(double));
@@ -311,7 +340,7 @@ bool is_device_ptr(const void *ptr) {
 }
 
 int build_sampler(rbsog_ctx *c, const HostSystem &hs) {
-    const int mt = c->sog.mtot();
+    const int mt = (int)hs.mix_prob.size();   // mixture components
     const std::vector<double> &mp = hs.mix_prob, &axp = hs.ax_prob;
     const std::vector<int> &ma = hs.mix_alias, &off = hs.ax_off, &nmax = hs.ax_nmax, &axa = hs.ax_alias;
     CK(dalloc(c, &c->mix_prob, mt), "alloc sampler");
@@ -381,6 +410,8 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
     for (int d = 0; d < 3; ++d) sa.tpl[d] = c->box.tpl[d];
     sa.A = c->kT * c->V; sa.Q2 = c->Q2; sa.inv_lam2 = 1.0 / (c->lam * c->lam); sa.S = c->S; sa.V = c->V;
+    sa.measure = c->p.sampling;
+    sa.Q2a = c->p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * kPi) * c->Q2 : c->Q2;
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
     { ProfScope ps(c, st, 4); launch_sample(sa, st); }
     NearArgs na{};

@@ -149,7 +149,7 @@ int build_args(rbsog_batch *b) {
         }
         {
             SampleArgs &a = sa[r];
-            const int mt = h.sog.mtot();
+            const int mt = (int)h.mix_prob.size();   // mixture components
             a.tab = SamplerTables{mt, b->mix_prob + mix_base, b->mix_alias + mix_base, b->ax_off + 3 * mix_base,
                                   b->ax_nmax + 3 * mix_base, b->ax_prob + ax_base, b->ax_alias + ax_base};
             mix_base += (size_t)mt;
@@ -162,6 +162,8 @@ int build_args(rbsog_batch *b) {
             a.inv_lam2 = 1.0 / (h.lam * h.lam);
             a.S = h.S;
             a.V = h.V;
+            a.measure = h.p.sampling;
+            a.Q2a = h.p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * 3.14159265358979323846) * h.Q2 : h.Q2;
             a.ctr = ctr;
             a.inject_m = b->inject_m + 3 * mo;
             a.m_out = b->modes + 3 * mo;

@@ -18,6 +18,7 @@ RBSOG_OK = 0
 RBSOG_FP64, RBSOG_FP32 = 0, 1
 RBSOG_NVE, RBSOG_LANGEVIN = 0, 1
 RBSOG_SOG_MINIMAL, RBSOG_SOG_BOUND, RBSOG_SOG_TABLE = 0, 1, 2
+RBSOG_SAMPLING_ADAPTIVE, RBSOG_SAMPLING_UNIFORM, RBSOG_SAMPLING_K2, RBSOG_SAMPLING_DEBYE = 0, 1, 2, 3
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOCONV", 6: "EUNSUPPORTED",
           7: "EOVERFLOW"}
 
@@ -27,7 +28,7 @@ class rbsog_params(C.Structure):
                 ("kT", C.c_double), ("r_c", C.c_double), ("sog_eps", C.c_double), ("dt", C.c_double),
                 ("langevin_gamma", C.c_double), ("seed", C.c_uint64), ("P", C.c_int32),
                 ("precision", C.c_int32), ("ensemble", C.c_int32), ("sog_mode", C.c_int32),
-                ("sog_M1", C.c_int32), ("sog_M2", C.c_int32), ("device", C.c_int32), ("reserved", C.c_int32)]
+                ("sog_M1", C.c_int32), ("sog_M2", C.c_int32), ("device", C.c_int32), ("sampling", C.c_int32)]
 
 
 class rbsog_energy(C.Structure):
@@ -468,7 +469,8 @@ def rbsog_server_free(s):
 
 def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int | None = None,
                 sog_mode: int = RBSOG_SOG_MINIMAL, M1: int = 0, M2: int = 0, device: int = 0,
-                ensemble: int | None = None, dt: float | None = None) -> rbsog_params:
+                ensemble: int | None = None, dt: float | None = None,
+                sampling: int = RBSOG_SAMPLING_ADAPTIVE) -> rbsog_params:
     """rbsog_params from a workloads.Workload (plain field copy)."""
     p = rbsog_params()
     for d in range(3):
@@ -490,5 +492,5 @@ def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int 
     p.sog_mode = int(sog_mode)
     p.sog_M1, p.sog_M2 = int(M1), int(M2)
     p.device = int(device)
-    p.reserved = 0
+    p.sampling = int(sampling)
     return p

@@ -55,7 +55,8 @@ def base_params():
 
 
 @pytest.mark.parametrize("field,value", [("r_c", 6.0), ("P", 0), ("P", 5000), ("kappa", 0.0), ("precision", 7),
-                                         ("ensemble", 3), ("sog_mode", 9), ("reserved", 1), ("dt", -1.0)])
+                                         ("ensemble", 3), ("sog_mode", 9), ("sampling", 4), ("sampling", -1),
+                                         ("dt", -1.0)])
 def test_invalid_parameters_are_rejected_on_the_host(field, value):
     w, p = base_params()
     setattr(p, field, value)

@@ -45,31 +45,37 @@ def test_index_below_is_floor_of_u_times_n():
 
 
 class Fixture:
-    def __init__(self, mix, kT):
+    def __init__(self, mix, kT, kind=0):
+        self.kind = kind
         self.N, self.L = 8, [4.0, 4.0, 4.0]
         self.lam, self.rc = 0.6, 1.9
         self.r, self.q = W.small_system(self.N, 4.0, 21, charge_mix=mix)
         self.sog = S.build(self.lam, self.rc, 1e-5)
         self.kT = kT
         self.Q2 = float(np.sum(self.q ** 2))
-        self.ms = ModeSampler(self.sog, self.L, kT, self.Q2)
-        self.S = core.S_sum(self.L, self.sog, kT, self.Q2)
+        self.ms = ModeSampler(self.sog, self.L, kT, self.Q2, kind=kind)
+        self.S = core.S_sum(self.L, self.sog, kT, self.Q2, kind=kind)
         self.V = 64.0
         self.modes = self.ms.all_modes()
         k2 = self.ms.k2_of(self.modes)
-        self.p = np.array([core.calF(x, kT, self.V, self.Q2, self.lam) * core.fhat(self.sog, x) for x in k2]) / self.S
+        self.p = np.array([core.measure(kind, x, kT, self.V, self.Q2, self.lam) * core.fhat(self.sog, x)
+                           for x in k2]) / self.S
         # single-draw estimator X_i(k) (P = 1) through the oracle's own estimator functions
         self.X = np.zeros((len(self.modes), self.N, 3))
         self.Ue = np.zeros(len(self.modes))
         rho = core.rho(self.r, self.q, self.L, self.modes)
-        coef = core.rb_coef(self.modes, self.L, self.sog, kT, self.Q2, self.S, P=1)
+        coef = core.rb_coef(self.modes, self.L, self.sog, kT, self.Q2, self.S, P=1, kind=kind)
         for j in range(len(self.modes)):
             self.X[j] = core.far_rb(self.r, self.q, self.L, self.modes[j:j + 1], coef[j:j + 1], rho[j:j + 1])
             self.Ue[j] = 0.5 * coef[j] * (rho[j, 0] ** 2 + rho[j, 1] ** 2)
         self.index = {tuple(m): j for j, m in enumerate(self.modes)}
 
 
-@pytest.fixture(scope="module", params=[(False, 1.0), (True, 0.05), (False, 40.0)], ids=["ocp", "mix-cold", "hot"])
+@pytest.fixture(scope="module", params=[(False, 1.0, 0), (True, 0.05, 0), (False, 40.0, 0), (False, 1.0, 1),
+                                        (True, 0.05, 1), (False, 1.0, 2), (True, 0.05, 2), (False, 1.0, 3),
+                                        (True, 0.05, 3)],
+                ids=["ocp", "mix-cold", "hot", "ocp-F1", "mix-cold-F1", "ocp-k2", "mix-cold-k2", "ocp-debye",
+                     "mix-cold-debye"])
 def fx(request):
     return Fixture(*request.param)
 
@@ -92,12 +98,13 @@ def test_exact_mean_is_the_full_far_field(fx):
 
 
 def test_exact_variance_formula(fx):
-    """Eq. (66) with S = sum calF Fhat: E|X_i|^2 = (q_i^2 S / V^2) sum_k k^2 Fhat Im^2 / calF."""
+    """Eq. (66) with S = sum calF Fhat: E|X_i|^2 = (q_i^2 S / V^2) sum_k k^2 Fhat Im^2 / calF
+    (any measure)."""
     EX2 = np.tensordot(fx.p, np.sum(fx.X ** 2, axis=2), axes=1)
     rho = core.rho(fx.r, fx.q, fx.L, fx.modes)
     k = 2 * math.pi * fx.modes / 4.0
     k2 = np.sum(k * k, axis=1)
-    cal = np.array([core.calF(x, fx.kT, fx.V, fx.Q2, fx.lam) for x in k2])
+    cal = np.array([core.measure(fx.kind, x, fx.kT, fx.V, fx.Q2, fx.lam) for x in k2])
     fh = np.array([core.fhat(fx.sog, x) for x in k2])
     for i in range(fx.N):
         th = k @ fx.r[i]
@@ -153,3 +160,59 @@ def test_replay_is_deterministic():
     c, _ = f.ms.draw(7, 4, 64)
     assert np.array_equal(a, b) and not np.array_equal(a, c)
     assert np.all(np.any(a != 0, axis=1))
+
+
+def _image_sum(L, fn, rmax):
+    """sum over lattice vectors n L (n in Z^3, |n L| <= rmax) of fn(|n L|)."""
+    nm = [int(math.ceil(rmax / L[a])) for a in range(3)]
+    tot = 0.0
+    for i in range(-nm[0], nm[0] + 1):
+        for j in range(-nm[1], nm[1] + 1):
+            for k in range(-nm[2], nm[2] + 1):
+                d = math.sqrt((i * L[0]) ** 2 + (j * L[1]) ** 2 + (k * L[2]) ** 2)
+                if d <= rmax:
+                    tot += fn(d)
+    return tot
+
+
+@pytest.mark.parametrize("L", [(4.0, 4.0, 4.0), (3.0, 4.0, 5.5)])
+def test_S_of_the_other_measures_by_poisson_summation(L):
+    """The k-space normalisations against real space (Poisson summation of the Gaussian
+    sum F = sum_m a_m exp(-b_m r^2)): sum_k Fhat(k) = V sum_n F(|n L|) and
+    sum_k k^2 Fhat(k) = -V sum_n (Laplacian F)(|n L|), the k = 0 terms being Fhat(0) and 0."""
+    sog = S.build(0.6, 1.9, 1e-5)
+    V = L[0] * L[1] * L[2]
+    t = np.asarray(sog.t, dtype=np.float64)
+    b = np.exp(t)
+    a = np.array([sog.h * float(w) * float(S.f_tr(float(x), 0.0, sog.lam)) for x, w in zip(t, sog.weights)])
+    rmax = math.sqrt(45.0 / float(np.min(b)))
+
+    def F(r):
+        return float(np.sum(a * np.exp(-b * r * r)))
+
+    def lapF(r):
+        return float(np.sum(a * np.exp(-b * r * r) * (4.0 * b * b * r * r - 6.0 * b)))
+
+    # the Gaussian sum reproduces the library-independent kernel evaluation
+    assert abs(F(0.7) - core.sog_F(sog, 0.7)) <= 1e-13 * abs(F(0.7))
+    S1 = core.S_sum(L, sog, 1.0, 1.0, kind=core.UNIFORM)
+    S2 = core.S_sum(L, sog, 1.0, 1.0, kind=core.K2)
+    ref1 = V * _image_sum(L, F, rmax) - core.fhat(sog, 0.0)
+    ref2 = -V * _image_sum(L, lapF, rmax)
+    assert abs(S1 - ref1) <= 1e-11 * abs(ref1)
+    assert abs(S2 - ref2) <= 1e-11 * abs(ref2)
+
+
+def test_closed_form_fluctuations_match_the_single_draw_moments(fx):
+    """oracle.variance against the per-mode estimator table of the fixture:
+    F_fluc = (1/N) sum_i Var X_i / P and E_fluc = Var Y / P for every measure."""
+    from oracle import variance
+    P = 3
+    out = variance.fluctuations(fx.r, fx.q, fx.L, fx.sog, fx.kT, P, kinds=(fx.kind,))
+    mean = np.tensordot(fx.p, fx.X, axes=1)
+    var = np.tensordot(fx.p, np.sum(fx.X ** 2, axis=2), axes=1) - np.sum(mean ** 2, axis=1)
+    F_ref = float(np.mean(var)) / P
+    E_ref = (float(fx.p @ fx.Ue ** 2) - float(fx.p @ fx.Ue) ** 2) / P
+    F_fluc, E_fluc = out[fx.kind]
+    assert abs(F_fluc - F_ref) <= 1e-9 * F_ref
+    assert abs(E_fluc - E_ref) <= 1e-9 * E_ref
