@@ -200,12 +200,25 @@ __device__ __forceinline__ void rho_final_body(const RhoFinalArgs &a, int ML, un
         const int pass_base = (l / (256 * ML)) * 256 * ML;
         int ngroups, nsub;
         rho_split(a.P, pass_base, ML, ngroups, nsub);
-        for (int b = warp; b < a.G; b += 8)
-            for (int s = 0; s < nsub; ++s) {
-                const double2 v = a.partial[((size_t)b * 8 + s) * a.P + l];
-                re += v.x;
-                im += v.y;
+        // eight independent partial sums (blocks b0 + 8u of each stride of 64) keep eight
+        // loads in flight; combined in a fixed order
+        double r8[8], i8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) r8[u] = i8[u] = 0.0;
+        for (int b0 = warp; b0 < a.G; b0 += 64) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int b = b0 + 8 * u;
+                if (b < a.G)
+                    for (int s = 0; s < nsub; ++s) {
+                        const double2 v = a.partial[((size_t)b * 8 + s) * a.P + l];
+                        r8[u] += v.x;
+                        i8[u] += v.y;
+                    }
             }
+        }
+        re = ((r8[0] + r8[1]) + (r8[2] + r8[3])) + ((r8[4] + r8[5]) + (r8[6] + r8[7]));
+        im = ((i8[0] + i8[1]) + (i8[2] + i8[3])) + ((i8[4] + i8[5]) + (i8[6] + i8[7]));
     }
     sh[warp][lane] = make_double2(re, im);
     __syncthreads();
@@ -426,13 +439,27 @@ __global__ void __launch_bounds__(kFarThreads) k_far64(FarArgs a) {
     if (threadIdx.x == 0) a.K_part[blockIdx.x] = tot;
 }
 
+// Fixed-order strided sum of x[0 .. n-1] by this thread with eight independent partial
+// sums (eight loads in flight).
+__device__ __forceinline__ double strided_sum8(const double *x, int n) {
+    double s8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s8[u] = 0.0;
+    const int st = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < n; i0 += 8 * st) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = i0 + u * st;
+            if (i < n) s8[u] += x[i];
+        }
+    }
+    return ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+}
+
 __device__ __forceinline__ void energy_body(const EnergyArgs &a, double *sh) {
-    double u = 0.0, k = 0.0;
     // fixed-order per-thread strides, then a fixed tree
-    for (int i = threadIdx.x; i < a.nU; i += blockDim.x) u += a.U_part[i];
-    double U = block_reduce_sum<double>(u, sh);
-    for (int i = threadIdx.x; i < a.nK; i += blockDim.x) k += a.K_part[i];
-    double K = block_reduce_sum<double>(k, sh);
+    double U = block_reduce_sum<double>(strided_sum8(a.U_part, a.nU), sh);
+    double K = block_reduce_sum<double>(strided_sum8(a.K_part, a.nK), sh);
     double uf = 0.0;
     for (int i = threadIdx.x; i < a.nUfar; i += blockDim.x) uf += a.Ufar[i];
     const double Ufs = block_reduce_sum<double>(uf, sh);
@@ -449,9 +476,47 @@ __device__ __forceinline__ void energy_body(const EnergyArgs &a, double *sh) {
     }
 }
 
-__global__ void __launch_bounds__(1024) k_energy(EnergyArgs a) {
-    __shared__ double sh[1024];
-    energy_body(a, sh);
+// FP64 runs at 2 operations per clock per SM here, so one block summing ~5e4 partials
+// is FP64-bound; kEnergyBlocks blocks share the sums and the last one to arrive adds the
+// per-block results in block order (deterministic whichever block is last).
+__global__ void __launch_bounds__(256) k_energy(EnergyArgs a) {
+    __shared__ double sh[256];
+    __shared__ int last;
+    const int E = gridDim.x, b = blockIdx.x;
+    auto part = [&](const double *x, int n) {
+        const int lo = (int)((long long)n * b / E), hi = (int)((long long)n * (b + 1) / E);
+        return block_reduce_sum<double>(strided_sum8(x + lo, hi - lo), sh);
+    };
+    const double U = part(a.U_part, a.nU);
+    const double K = part(a.K_part, a.nK);
+    const double Uf = part(a.Ufar, a.nUfar);
+    if (threadIdx.x == 0) {
+        a.scratch[b] = U;
+        a.scratch[E + b] = K;
+        a.scratch[2 * E + b] = Uf;
+        __threadfence();
+        last = atomicAdd(a.done, 1u) == (unsigned)(E - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const volatile double *s = a.scratch;
+        double Us = 0.0, Ks = 0.0, Ufs = 0.0;
+        for (int i = 0; i < E; ++i) {
+            Us += s[i];
+            Ks += s[E + i];
+            Ufs += s[2 * E + i];
+        }
+        const double Ut = Ufs + a.Ufar0;
+        a.out[0] = Us;
+        a.out[1] = Ut;
+        a.out[2] = a.Uself;
+        a.out[3] = Ks;
+        a.out[4] = Us + Ut + a.Uself + Ks;
+        if (a.advance_step && a.ctr->fvalid) a.ctr->step += 1ull;
+        a.ctr->fvalid = 1;
+        *a.done = 0u;
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_energy_batch(const EnergyArgs *args) {
@@ -503,7 +568,7 @@ int launch_far(int prec, const FarArgs &a, cudaStream_t st) {
     return (int)nb;
 }
 
-void launch_energy(const EnergyArgs &a, cudaStream_t st) { k_energy<<<1, 1024, 0, st>>>(a); }
+void launch_energy(const EnergyArgs &a, cudaStream_t st) { k_energy<<<kEnergyBlocks, 256, 0, st>>>(a); }
 
 uint32_t rho_batch_blocks(int G, int P) { return (uint32_t)G * (uint32_t)((P + 255) / 256); }
 uint32_t rho_final_batch_blocks(int P) { return (uint32_t)((P + 31) / 32); }

@@ -32,8 +32,12 @@ __device__ __forceinline__ int alias_draw(U4 w, const double *prob, const int *a
     return (t < prob[i]) ? i : alias[i];
 }
 
-__device__ __forceinline__ void sample_body(const SampleArgs &a, int l) {
-    int m[3];
+// One slot l per warp: lane j tries attempt att0 + j, so 32 consecutive attempts run at
+// once and the slot takes the accepted attempt with the smallest index, exactly the draw
+// a sequential loop over attempts returns (the random words depend only on the counter).
+__device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
+    const int lane = threadIdx.x & 31;
+    int m[3] = {1, 0, 0};
     if (a.ctr->inject) {
         m[0] = a.inject_m[3 * l]; m[1] = a.inject_m[3 * l + 1]; m[2] = a.inject_m[3 * l + 2];
     } else {
@@ -41,10 +45,10 @@ __device__ __forceinline__ void sample_body(const SampleArgs &a, int l) {
         const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
         const uint32_t d0 = (uint32_t)d, d1 = (uint32_t)(d >> 32);
         bool done = false;
-        m[0] = 1; m[1] = 0; m[2] = 0;
-        for (int att = 0; att < kMaxAttempts && !done; ++att) {
-            const uint32_t cb = 8u * (uint32_t)att;
-            int g = alias_draw(philox10((uint32_t)l, cb, d0, d1, k0, k1), a.tab.mix_prob, a.tab.mix_alias, a.tab.mtot);
+        for (int att0 = 0; att0 < kMaxAttempts && !done; att0 += 32) {
+            const uint32_t cb = 8u * (uint32_t)(att0 + lane);
+            const int g = alias_draw(philox10((uint32_t)l, cb, d0, d1, k0, k1), a.tab.mix_prob, a.tab.mix_alias,
+                                     a.tab.mtot);
             int n[3];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
@@ -52,41 +56,47 @@ __device__ __forceinline__ void sample_body(const SampleArgs &a, int l) {
                 n[ax] = alias_draw(philox10((uint32_t)l, cb + 1u + ax, d0, d1, k0, k1), a.tab.ax_prob + off,
                                    a.tab.ax_alias + off, 2 * nm + 1) - nm;
             }
-            if (n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
-            if (a.measure == 1 || a.measure == 2) {   // calF = 1 or k^2: the mixture is P(k) itself
-                m[0] = n[0]; m[1] = n[1]; m[2] = n[2];
-                done = true;
-                break;
+            bool ok = !(n[0] == 0 && n[1] == 0 && n[2] == 0);
+            if (ok && (a.measure == 0 || a.measure == 3)) {
+                U4 wa = philox10((uint32_t)l, cb + 4u, d0, d1, k0, k1);
+                double u = u53_of(wa.x, wa.y);
+                double kx = __dmul_rn(a.tpl[0], (double)n[0]);
+                double ky = __dmul_rn(a.tpl[1], (double)n[1]);
+                double kz = __dmul_rn(a.tpl[2], (double)n[2]);
+                double k2 = __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
+                double g2 = __ddiv_rn(1.0, __dadd_rn(k2, a.inv_lam2));
+                double ratio = __ddiv_rn(a.A, __dadd_rn(a.A, __dmul_rn(a.Q2a, g2)));
+                ok = u < ratio;
             }
-            U4 wa = philox10((uint32_t)l, cb + 4u, d0, d1, k0, k1);
-            double u = u53_of(wa.x, wa.y);
-            double kx = __dmul_rn(a.tpl[0], (double)n[0]);
-            double ky = __dmul_rn(a.tpl[1], (double)n[1]);
-            double kz = __dmul_rn(a.tpl[2], (double)n[2]);
-            double k2 = __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
-            double g2 = __ddiv_rn(1.0, __dadd_rn(k2, a.inv_lam2));
-            double ratio = __ddiv_rn(a.A, __dadd_rn(a.A, __dmul_rn(a.Q2a, g2)));
-            if (u < ratio) {
-                m[0] = n[0]; m[1] = n[1]; m[2] = n[2];
+            const unsigned acc = __ballot_sync(0xffffffffu, ok);
+            if (acc) {
+                const int src = __ffs(acc) - 1;
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) m[ax] = __shfl_sync(0xffffffffu, n[ax], src);
                 done = true;
             }
         }
-        if (!done) atomicOr(&a.ctr->err, kErrSampler);
+        if (!done && lane == 0) atomicOr(&a.ctr->err, kErrSampler);
     }
-    a.m_out[3 * l] = m[0]; a.m_out[3 * l + 1] = m[1]; a.m_out[3 * l + 2] = m[2];
-    // coef = S / (P V calF(k)),  calF = kT V / (kT V / Q2 + 1/(k^2 + lambda^-2))   (Eqs. 60, 62)
-    double kx = a.tpl[0] * m[0], ky = a.tpl[1] * m[1], kz = a.tpl[2] * m[2];
-    double k2 = kx * kx + ky * ky + kz * kz;
-    const double calF =
-        a.measure == 1 ? 1.0
-                       : (a.measure == 2 ? k2
-                                         : a.A / (a.A / a.Q2 + (a.measure == 3 ? 4.0 * CUDART_PI : 1.0) / (k2 + a.inv_lam2)));
-    a.coef_out[l] = a.S / ((double)a.P * a.V * calF);
+    if (lane == 0) {
+        a.m_out[3 * l] = m[0]; a.m_out[3 * l + 1] = m[1]; a.m_out[3 * l + 2] = m[2];
+        // coef = S / (P V calF(k)) (Eqs. 60, 62), calF of the measure
+        double kx = a.tpl[0] * m[0], ky = a.tpl[1] * m[1], kz = a.tpl[2] * m[2];
+        double k2 = kx * kx + ky * ky + kz * kz;
+        const double calF =
+            a.measure == 1 ? 1.0
+                           : (a.measure == 2 ? k2
+                                             : a.A / (a.A / a.Q2 + (a.measure == 3 ? 4.0 * CUDART_PI : 1.0) /
+                                                                       (k2 + a.inv_lam2)));
+        a.coef_out[l] = a.S / ((double)a.P * a.V * calF);
+    }
 }
 
+constexpr int kSampleWarps = 4;   // slots per 128-thread block
+
 __global__ void __launch_bounds__(128) k_sample(SampleArgs a) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l < a.P) sample_body(a, l);
+    const int l = blockIdx.x * kSampleWarps + (threadIdx.x >> 5);
+    if (l < a.P) sample_warp(a, l);
 }
 
 __global__ void __launch_bounds__(128) k_sample_batch(const SampleArgs *args, const uint32_t *items, int R) {
@@ -97,8 +107,8 @@ __global__ void __launch_bounds__(128) k_sample_batch(const SampleArgs *args, co
         else hi = mid - 1;
     }
     const SampleArgs &a = args[lo];
-    const int l = (int)(blockIdx.x - items[lo]) * blockDim.x + threadIdx.x;
-    if (l < a.P) sample_body(a, l);
+    const int l = (int)(blockIdx.x - items[lo]) * kSampleWarps + (threadIdx.x >> 5);
+    if (l < a.P) sample_warp(a, l);
 }
 
 // S over the ball |k|^2 <= kmax2: block x = m_x slab; fixed-order reduction.
@@ -136,10 +146,10 @@ __global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
 }  // namespace
 
 void launch_sample(const SampleArgs &a, cudaStream_t st) {
-    k_sample<<<(a.P + 127) / 128, 128, 0, st>>>(a);
+    k_sample<<<(a.P + kSampleWarps - 1) / kSampleWarps, 128, 0, st>>>(a);
 }
 
-uint32_t sample_batch_blocks(int P) { return (uint32_t)((P + 127) / 128); }
+uint32_t sample_batch_blocks(int P) { return (uint32_t)((P + kSampleWarps - 1) / kSampleWarps); }
 
 void launch_sample_batch(const SampleArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st) {
     k_sample_batch<<<nblocks, 128, 0, st>>>(args, items, R);

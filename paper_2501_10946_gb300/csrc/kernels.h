@@ -149,7 +149,11 @@ struct EnergyArgs {
     double *out;               // [5]: U_near, U_far, U_self, K, total
     DevCounters *ctr;
     int advance_step;
+    double *scratch;           // [3 kEnergyBlocks] per-block sums (single system)
+    unsigned int *done;        // arrival counter of the blocks (0 between launches)
 };
+constexpr int kEnergyBlocks = 32;
+// Single system: kEnergyBlocks blocks, the last to finish adds their sums in a fixed order.
 void launch_energy(const EnergyArgs &a, cudaStream_t st);
 
 // ---- batched systems: one launch per kernel over every system --------------------

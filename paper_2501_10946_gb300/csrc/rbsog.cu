@@ -50,7 +50,8 @@ struct rbsog_ctx {
     double *coef = nullptr;
     double2 *partial = nullptr, *rho = nullptr;
     void *gtab = nullptr;
-    double *Ufar = nullptr, *U_part = nullptr, *K_part = nullptr, *energy = nullptr;
+    double *Ufar = nullptr, *U_part = nullptr, *K_part = nullptr, *energy = nullptr, *escratch = nullptr;
+    unsigned int *edone = nullptr;
     int G = 0, nU = 0, nK = 0;
     DevCounters *ctr = nullptr;
     std::vector<void *> allocs;
@@ -437,6 +438,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     ea.U_part = c->U_part; ea.nU = c->nU; ea.K_part = c->K_part; ea.nK = c->nK; ea.Ufar = c->Ufar;
     ea.nUfar = c->p.P;
     ea.Ufar0 = c->Ufar0; ea.Uself = c->Uself; ea.out = c->energy; ea.ctr = c->ctr; ea.advance_step = advance;
+    ea.scratch = c->escratch; ea.done = c->edone;
     { ProfScope ps(c, st, 9); launch_energy(ea, st); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
@@ -523,13 +525,15 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         dalloc(c, &c->partial, (size_t)c->G * 8 * p.P) || dalloc(c, &c->rho, (size_t)p.P) ||
         dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, (size_t)p.P) ||
         dalloc(c, &c->U_part, 4 * std::max((n + 127) / 128, (size_t)bx.ncell) + 4) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
-        dalloc(c, &c->energy, 8) || dalloc(c, &c->ctr, 1)) {
+        dalloc(c, &c->energy, 8) || dalloc(c, &c->escratch, 3 * (size_t)kEnergyBlocks) || dalloc(c, &c->edone, 1) ||
+        dalloc(c, &c->ctr, 1)) {
         g_init_error = "device allocation failed";
         return bail(RBSOG_ENOMEM);
     }
     c->F = Fb; c->Fn = Fnb; c->s = sb; c->rec = recb;
     if (cudaMemset(c->count, 0, sizeof(uint32_t) * bx.ncell) != cudaSuccess ||
         cudaMemset(c->ctr, 0, sizeof(DevCounters)) != cudaSuccess ||
+        cudaMemset(c->edone, 0, sizeof(unsigned int)) != cudaSuccess ||
         cudaMemcpy(c->q_user, q_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->m_user, m_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -17,10 +17,10 @@ def gpu():
     return require_gpu()
 
 
-def gpu_trajectory(w, prec, r0, v0, nsteps):
+def gpu_trajectory(w, prec, r0, v0, nsteps, q=None, m=None):
     """Positions, velocities and the k-set of every force evaluation, one step at a time."""
     ks, rs, vs, es = [], [], [], []
-    with Ctx(w, prec) as c:
+    with Ctx(w, prec, q=q, m=m) as c:
         R.rbsog_set_state(c.h, r0, v0)
         R.rbsog_forces(c.h)
         ks.append(R.rbsog_get_ksample(c.h, c.P)[0])
@@ -35,9 +35,9 @@ def gpu_trajectory(w, prec, r0, v0, nsteps):
     return ks, rs, vs, es
 
 
-def oracle_trajectory(w, r0, v0, ks, nsteps):
-    q = W.charges(w)
-    m = W.masses(w)
+def oracle_trajectory(w, r0, v0, ks, nsteps, q=None, m=None):
+    q = W.charges(w) if q is None else q
+    m = W.masses(w) if m is None else m
     sog = oracle_sog(w)
     S_ = core.S_sum(w.box, sog, w.kT, float(np.sum(q * q)))
     state = {"i": 0}
@@ -75,6 +75,27 @@ def test_trajectory_parity(prec, ensemble):
     n = 5
     ks, rg, vg, _ = gpu_trajectory(w, prec, r0, v0, n)
     ro, vo = oracle_trajectory(w, r0, v0, ks, n)
+    tol = 1e-11 if prec == R.RBSOG_FP64 else 2e-5
+    for s in range(n):
+        dr = box_diff(rg[s], ro[s], w.box)
+        assert np.max(np.abs(dr)) <= tol * w.box[0], (s, np.max(np.abs(dr)))
+        assert core.rel_l2(vg[s], vo[s]) <= tol * 10, s
+
+
+@pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32], ids=["fp64", "fp32"])
+def test_two_species_trajectory_parity(prec):
+    """A two-species plasma (like the D-alpha mixture of Sec. 5: charges 1 and 2, masses 2
+    and 4, half of each), BAOAB: the per-particle charges enter the forces and the
+    adaptive measure through sum q^2, the masses the kick and the noise amplitude."""
+    w = workload(600, 8.0, kappa=1.0, Gamma=1.0, P=64, seed=43, dt=0.002, ensemble="langevin")
+    alpha = np.arange(w.N) % 2 == 1
+    q = np.where(alpha, 2.0, 1.0)
+    m = np.where(alpha, 4.0, 2.0)
+    r0 = W.positions(w)
+    v0 = W.velocities(w) / np.sqrt(m)[:, None]
+    n = 5
+    ks, rg, vg, _ = gpu_trajectory(w, prec, r0, v0, n, q=q, m=m)
+    ro, vo = oracle_trajectory(w, r0, v0, ks, n, q=q, m=m)
     tol = 1e-11 if prec == R.RBSOG_FP64 else 2e-5
     for s in range(n):
         dr = box_diff(rg[s], ro[s], w.box)
