@@ -17,7 +17,8 @@ paper's own sampler is Metropolis-Hastings, Sec. 4.3, while the variance lemma
      (alias table over |n_a| <= nmax_{m,a}, where g < 1e-18 beyond);
   3. if n = 0, start the attempt over;
   4. accept with probability calF(k) / sum_j q_j^2 (calF increases with |k| towards
-     sum q^2), else start over.
+     sum q^2), else start over; the test u < kT V / (kT V + Q2/t), t = k^2 + lambda^-2, is
+     evaluated as u (kT V t + Q2) < kT V t.
 Accepted modes are distributed as P(k).
 
 DEBYE (Eq. 62 with the Debye wavenumber of Gaussian units, 4 pi sum q^2 / (k_B T V)) is the
@@ -150,6 +151,14 @@ class ModeSampler:
         Q2 = (4.0 * math.pi) * self.Q2 if self.kind == DEBYE else self.Q2
         return A / (A + Q2 * (1.0 / (k2 + self.inv_lam2)))
 
+    def accepts(self, u, k2):
+        """Step 4, u < calF(k)/sum q^2 = A / (A + Q2/t) with A = kT V, t = k^2 + lambda^-2,
+        evaluated without division as u (A t + Q2) < A t (IEEE double operations)."""
+        A = self.kT * self.V
+        Q2 = (4.0 * math.pi) * self.Q2 if self.kind == DEBYE else self.Q2
+        At = A * (k2 + self.inv_lam2)
+        return u * (At + Q2) < At
+
     def k2_of(self, m):
         m = np.asarray(m, dtype=np.float64)
         kx = self.tpl[0] * m[..., 0]
@@ -188,7 +197,7 @@ class ModeSampler:
             nonzero = np.any(n != 0, axis=1)
             if self.kind in (ADAPTIVE, DEBYE):
                 u = philox.u53(words[4][0], words[4][1])
-                ok = nonzero & (u < self.accept_ratio(self.k2_of(n)))
+                ok = nonzero & self.accepts(u, self.k2_of(n))
             else:
                 ok = nonzero
             out[todo[ok]] = n[ok]

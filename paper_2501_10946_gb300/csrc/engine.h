@@ -62,7 +62,7 @@ struct rbsog_batch {
     double2 *partial = nullptr;
     double *U_part = nullptr, *K_part = nullptr;
     size_t cap_part = 0, cap_upart = 0, cap_kpart = 0;
-    double *mix_prob = nullptr, *ax_prob = nullptr;
+    unsigned long long *mix_thr = nullptr, *ax_thr = nullptr;   // alias keep thresholds
     int *mix_alias = nullptr, *ax_off = nullptr, *ax_nmax = nullptr, *ax_alias = nullptr;
     size_t cap_mix = 0, cap_ax = 0;
     // per-system arguments (device arrays of capR entries) and block prefixes

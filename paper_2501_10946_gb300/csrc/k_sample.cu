@@ -25,11 +25,13 @@ namespace rbsog {
 
 namespace {
 
-__device__ __forceinline__ int alias_draw(U4 w, const double *prob, const int *alias, int n) {
+// keep index i when u53(z, w) < prob_i, i.e. when its 53-bit integer is below the
+// precomputed threshold ceil(prob_i 2^53)
+__device__ __forceinline__ int alias_draw(U4 w, const unsigned long long *thr, const int *alias, int n) {
     unsigned long long u = ((unsigned long long)w.x << 32) | (unsigned long long)w.y;
     int i = (int)__umul64hi(u, (unsigned long long)n);
-    double t = u53_of(w.z, w.w);
-    return (t < prob[i]) ? i : alias[i];
+    const unsigned long long U = ((unsigned long long)(w.z >> 11) << 32) | (unsigned long long)w.w;
+    return (U < thr[i]) ? i : alias[i];
 }
 
 // One slot l per warp: lane j tries attempt att0 + j, so 32 consecutive attempts run at
@@ -47,13 +49,13 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
         bool done = false;
         for (int att0 = 0; att0 < kMaxAttempts && !done; att0 += 32) {
             const uint32_t cb = 8u * (uint32_t)(att0 + lane);
-            const int g = alias_draw(philox10((uint32_t)l, cb, d0, d1, k0, k1), a.tab.mix_prob, a.tab.mix_alias,
+            const int g = alias_draw(philox10((uint32_t)l, cb, d0, d1, k0, k1), a.tab.mix_thr, a.tab.mix_alias,
                                      a.tab.mtot);
             int n[3];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 const int off = a.tab.ax_off[3 * g + ax], nm = a.tab.ax_nmax[3 * g + ax];
-                n[ax] = alias_draw(philox10((uint32_t)l, cb + 1u + ax, d0, d1, k0, k1), a.tab.ax_prob + off,
+                n[ax] = alias_draw(philox10((uint32_t)l, cb + 1u + ax, d0, d1, k0, k1), a.tab.ax_thr + off,
                                    a.tab.ax_alias + off, 2 * nm + 1) - nm;
             }
             bool ok = !(n[0] == 0 && n[1] == 0 && n[2] == 0);
@@ -64,9 +66,10 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
                 double ky = __dmul_rn(a.tpl[1], (double)n[1]);
                 double kz = __dmul_rn(a.tpl[2], (double)n[2]);
                 double k2 = __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
-                double g2 = __ddiv_rn(1.0, __dadd_rn(k2, a.inv_lam2));
-                double ratio = __ddiv_rn(a.A, __dadd_rn(a.A, __dmul_rn(a.Q2a, g2)));
-                ok = u < ratio;
+                // u < A / (A + Q2/t), t = k^2 + lambda^-2, evaluated without division as
+                // u (A t + Q2) < A t
+                const double At = __dmul_rn(a.A, __dadd_rn(k2, a.inv_lam2));
+                ok = __dmul_rn(u, __dadd_rn(At, a.Q2a)) < At;
             }
             const unsigned acc = __ballot_sync(0xffffffffu, ok);
             if (acc) {

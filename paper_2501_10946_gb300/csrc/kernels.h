@@ -53,10 +53,10 @@ void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cuda
 // tables (ax_off, ax_nmax) over |n| <= nmax.
 struct SamplerTables {
     int mtot;                 // number of mixture components
-    const double *mix_prob; const int *mix_alias;     // [mtot]
+    const unsigned long long *mix_thr; const int *mix_alias;     // [mtot] keep thresholds, aliases
     const int *ax_off;        // [mtot*3] offset into ax_prob/ax_alias
     const int *ax_nmax;       // [mtot*3]
-    const double *ax_prob; const int *ax_alias;
+    const unsigned long long *ax_thr; const int *ax_alias;
 };
 struct SampleArgs {
     SamplerTables tab;

@@ -44,7 +44,7 @@ struct rbsog_ctx {
     uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr,
              *perm_src = nullptr;
     unsigned long long *keys = nullptr;
-    double *mix_prob = nullptr, *ax_prob = nullptr;
+    unsigned long long *mix_thr = nullptr, *ax_thr = nullptr;
     int *mix_alias = nullptr, *ax_off = nullptr, *ax_nmax = nullptr, *ax_alias = nullptr;
     int *modes = nullptr, *inject_m = nullptr;
     double *coef = nullptr;
@@ -342,21 +342,22 @@ bool is_device_ptr(const void *ptr) {
 
 int build_sampler(rbsog_ctx *c, const HostSystem &hs) {
     const int mt = (int)hs.mix_prob.size();   // mixture components
-    const std::vector<double> &mp = hs.mix_prob, &axp = hs.ax_prob;
+    const std::vector<unsigned long long> mp = alias_thresholds(hs.mix_prob), axp = alias_thresholds(hs.ax_prob);
     const std::vector<int> &ma = hs.mix_alias, &off = hs.ax_off, &nmax = hs.ax_nmax, &axa = hs.ax_alias;
-    CK(dalloc(c, &c->mix_prob, mt), "alloc sampler");
+    CK(dalloc(c, &c->mix_thr, mt), "alloc sampler");
     CK(dalloc(c, &c->mix_alias, mt), "alloc sampler");
     CK(dalloc(c, &c->ax_off, 3 * mt), "alloc sampler");
     CK(dalloc(c, &c->ax_nmax, 3 * mt), "alloc sampler");
-    CK(dalloc(c, &c->ax_prob, axp.size()), "alloc sampler");
+    CK(dalloc(c, &c->ax_thr, axp.size()), "alloc sampler");
     CK(dalloc(c, &c->ax_alias, axa.size()), "alloc sampler");
-    CK(cudaMemcpy(c->mix_prob, mp.data(), mt * sizeof(double), cudaMemcpyHostToDevice), "upload sampler");
+    CK(cudaMemcpy(c->mix_thr, mp.data(), mt * sizeof(unsigned long long), cudaMemcpyHostToDevice), "upload sampler");
     CK(cudaMemcpy(c->mix_alias, ma.data(), mt * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
     CK(cudaMemcpy(c->ax_off, off.data(), 3 * mt * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
     CK(cudaMemcpy(c->ax_nmax, nmax.data(), 3 * mt * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
-    CK(cudaMemcpy(c->ax_prob, axp.data(), axp.size() * sizeof(double), cudaMemcpyHostToDevice), "upload sampler");
+    CK(cudaMemcpy(c->ax_thr, axp.data(), axp.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice),
+       "upload sampler");
     CK(cudaMemcpy(c->ax_alias, axa.data(), axa.size() * sizeof(int), cudaMemcpyHostToDevice), "upload sampler");
-    c->tab = SamplerTables{mt, c->mix_prob, c->mix_alias, c->ax_off, c->ax_nmax, c->ax_prob, c->ax_alias};
+    c->tab = SamplerTables{mt, c->mix_thr, c->mix_alias, c->ax_off, c->ax_nmax, c->ax_thr, c->ax_alias};
     return RBSOG_OK;
 }
 

@@ -150,8 +150,8 @@ int build_args(rbsog_batch *b) {
         {
             SampleArgs &a = sa[r];
             const int mt = (int)h.mix_prob.size();   // mixture components
-            a.tab = SamplerTables{mt, b->mix_prob + mix_base, b->mix_alias + mix_base, b->ax_off + 3 * mix_base,
-                                  b->ax_nmax + 3 * mix_base, b->ax_prob + ax_base, b->ax_alias + ax_base};
+            a.tab = SamplerTables{mt, b->mix_thr + mix_base, b->mix_alias + mix_base, b->ax_off + 3 * mix_base,
+                                  b->ax_nmax + 3 * mix_base, b->ax_thr + ax_base, b->ax_alias + ax_base};
             mix_base += (size_t)mt;
             ax_base += h.ax_prob.size();
             a.P = P;
@@ -493,35 +493,36 @@ int engine_commit(rbsog_batch *b) {
     if (!b->dirty) return RBSOG_OK;
     BCK(cudaDeviceSynchronize(), "synchronize");
     // sampling tables, concatenated system by system
-    std::vector<double> mp, axp;
+    std::vector<unsigned long long> mp, axp;
     std::vector<int> ma, off, nmax, axa;
     for (const HostSystem &h : b->sys) {
-        mp.insert(mp.end(), h.mix_prob.begin(), h.mix_prob.end());
+        const std::vector<unsigned long long> mt = alias_thresholds(h.mix_prob), at = alias_thresholds(h.ax_prob);
+        mp.insert(mp.end(), mt.begin(), mt.end());
         ma.insert(ma.end(), h.mix_alias.begin(), h.mix_alias.end());
         off.insert(off.end(), h.ax_off.begin(), h.ax_off.end());
         nmax.insert(nmax.end(), h.ax_nmax.begin(), h.ax_nmax.end());
-        axp.insert(axp.end(), h.ax_prob.begin(), h.ax_prob.end());
+        axp.insert(axp.end(), at.begin(), at.end());
         axa.insert(axa.end(), h.ax_alias.begin(), h.ax_alias.end());
     }
-    if (mp.size() > b->cap_mix || !b->mix_prob) {
+    if (mp.size() > b->cap_mix || !b->mix_thr) {
         size_t cm = 0, c1 = 0, c2 = 0, c3 = 0;
-        BCK(regrow(b, &b->mix_prob, &cm, mp.size()), "alloc sampler");
+        BCK(regrow(b, &b->mix_thr, &cm, mp.size()), "alloc sampler");
         BCK(regrow(b, &b->mix_alias, &c1, mp.size()), "alloc sampler");
         BCK(regrow(b, &b->ax_off, &c2, 3 * cm), "alloc sampler");
         BCK(regrow(b, &b->ax_nmax, &c3, 3 * cm), "alloc sampler");
         b->cap_mix = std::min(cm, c1);
     }
-    if (axp.size() > b->cap_ax || !b->ax_prob) {
+    if (axp.size() > b->cap_ax || !b->ax_thr) {
         size_t ca = 0, c1 = 0;
-        BCK(regrow(b, &b->ax_prob, &ca, axp.size()), "alloc sampler");
+        BCK(regrow(b, &b->ax_thr, &ca, axp.size()), "alloc sampler");
         BCK(regrow(b, &b->ax_alias, &c1, axp.size()), "alloc sampler");
         b->cap_ax = std::min(ca, c1);
     }
-    BCK(upload(b->mix_prob, mp), "upload sampler");
+    BCK(upload(b->mix_thr, mp), "upload sampler");
     BCK(upload(b->mix_alias, ma), "upload sampler");
     BCK(upload(b->ax_off, off), "upload sampler");
     BCK(upload(b->ax_nmax, nmax), "upload sampler");
-    BCK(upload(b->ax_prob, axp), "upload sampler");
+    BCK(upload(b->ax_thr, axp), "upload sampler");
     BCK(upload(b->ax_alias, axa), "upload sampler");
     // per-block partial buffers at the current shapes
     size_t part = 0, upart = 4, kpart = 1;

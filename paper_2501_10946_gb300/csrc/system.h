@@ -3,6 +3,7 @@
 // the single-system context and the batch of systems.
 #pragma once
 
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -27,6 +28,15 @@ struct HostSystem {
 
 // Validate parameters and build everything host-side (no device work).  Returns an
 // RBSOG_* status and a message.
+// Alias "keep" thresholds in integer form: for the 53-bit integer U of a uniform draw
+// u = U 2^-53, u < prob exactly when U < ceil(prob 2^53), so the device decides with an
+// integer compare (no FP64 operation) and the same outcome.
+inline std::vector<unsigned long long> alias_thresholds(const std::vector<double> &prob) {
+    std::vector<unsigned long long> t(prob.size());
+    for (size_t i = 0; i < prob.size(); ++i) t[i] = (unsigned long long)std::ceil(prob[i] * 9007199254740992.0);
+    return t;
+}
+
 int setup_system(const rbsog_params &p, int64_t N, const double *q, const double *m, HostSystem *hs,
                  std::string *err);
 // S = sum_{k != 0} calF(k) Fhat(k) by a device lattice sum (synchronous).
