@@ -38,7 +38,7 @@ KERNELS_PER_STEP = 12
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed
 # full-set ncu capture at N = 1e6 of kernels unchanged since (profiles/near_rho_far_yocp_uniform_n1e6.md);
 # a kernel changed after its capture has no entry
-TRAFFIC = {"rho": 16.013e6}
+TRAFFIC = {"near": 16.649e6, "rho": 16.013e6, "far": 65.430e6}
 
 
 def peaks():
@@ -452,7 +452,8 @@ def main():
     e2e_rate = w.N * res["e2e_steps"] / res["e2e_s"]
     line["e2e"] = {"value": e2e_rate, "unit": "particle-steps/s", "h2d_bytes_per_step": res["e2e_h2d"],
                    "d2h_bytes_per_step": res["e2e_d2h"], "path": "rbsog_set_state(host) + rbsog_step(1) + "
-                   "rbsog_get_state(host), pinned buffers"}
+                   "rbsog_get_state(host), pinned buffers; an uploaded state has no forces yet, so each "
+                   "step also evaluates the forces of the uploaded positions (two force evaluations)"}
     if not args.no_batch:
         line["batched"] = batched_sweep(torch, R, args.steps, max(3, args.warmup))
     if not args.no_serve:
