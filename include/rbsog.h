@@ -360,7 +360,8 @@ int rbsog_server_create(const rbsog_server_config *cfg, rbsog_server **out);
  * time on the server clock (t_arrival < 0: now).  The job becomes eligible for admission
  * once the clock passes t_arrival.  *job_id receives its handle (0, 1, 2, ...).  Host
  * only; invalid parameters are reported when the job is considered for admission (the
- * job then fails). */
+ * job then fails), as is a job larger than the arenas (RBSOG_ENOMEM, once nothing else
+ * is resident). */
 int rbsog_server_submit(rbsog_server *s, const rbsog_params *params, int64_t N, const double *q, const double *m,
                         const double *r, const double *v, int32_t nsteps, double t_arrival, int64_t *job_id);
 

@@ -249,7 +249,7 @@ int rbsog_server_create(const rbsog_server_config *cfg, rbsog_server **out) {
 int rbsog_server_submit(rbsog_server *s, const rbsog_params *p, int64_t N, const double *q, const double *m,
                         const double *r, const double *v, int32_t nsteps, double t_arrival, int64_t *job_id) {
     if (!s || !p || !q || !m || !r) return sfail(s, RBSOG_EINVAL, "server, params, q, m or r is NULL");
-    if (N < 2 || N > s->cfg.max_particles) return sfail(s, RBSOG_EINVAL, "N must be in [2, max_particles]");
+    if (N < 2 || N >= 0x7fffffffLL) return sfail(s, RBSOG_EINVAL, "N must be in [2, 2^31)");
     if (nsteps < 0) return sfail(s, RBSOG_EINVAL, "nsteps < 0");
     Job j;
     j.id = (int64_t)s->jobs.size();

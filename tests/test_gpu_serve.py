@@ -140,3 +140,34 @@ def test_arrivals_in_the_future_wait_and_stats_add_up():
         assert info["t_admit"] >= info["t_arrival"] == pytest.approx(0.05 * k)
         assert info["t_done"] >= info["t_admit"]
     assert stats["particle_steps"] == sum(w.N * n for w, n in js)
+
+
+def test_edge_jobs_are_handled_and_do_not_block_the_queue():
+    """Zero steps (only the initial evaluation), two particles, a job larger than the
+    arenas and a job with invalid parameters, mixed with a normal job: the impossible ones
+    fail at admission, the rest complete."""
+    normal, n_normal = jobs()[2]
+    s = server(max_particles=5000)
+    try:
+        ids = {}
+        ids["zero"] = submit(s, normal, 0)
+        two = workload(2, 4.0, rc=1.9, P=8, seed=71)
+        ids["two"] = submit(s, two, 7)
+        big = workload(6000, 18.0, P=64, seed=73)
+        ids["big"] = submit(s, big, 3)
+        bad = R.make_params(normal, precision=R.RBSOG_FP32)
+        bad.kappa = -1.0
+        ids["bad"] = R.rbsog_server_submit(s, bad, W.charges(normal), W.masses(normal), W.positions(normal), None, 5)
+        ids["normal"] = submit(s, normal, n_normal)
+        R.rbsog_server_run(s)
+        info = {k: R.rbsog_server_job(s, v)[0] for k, v in ids.items()}
+        _, r0, v0 = R.rbsog_server_job(s, ids["zero"], normal.N, state=True)
+    finally:
+        R.rbsog_server_free(s)
+    assert info["zero"]["status"] == R.RBSOG_JOB_DONE and info["zero"]["steps_done"] == 0
+    assert np.array_equal(r0, W.positions(normal))         # no step taken
+    assert info["zero"]["energy"]["step"] == 0 and np.isfinite(info["zero"]["energy"]["total"])
+    assert info["two"]["status"] == R.RBSOG_JOB_DONE and info["two"]["steps_done"] == 7
+    assert info["big"]["status"] == R.RBSOG_JOB_FAILED and R.STATUS[info["big"]["error"]] == "ENOMEM"
+    assert info["bad"]["status"] == R.RBSOG_JOB_FAILED and R.STATUS[info["bad"]["error"]] == "EINVAL"
+    assert info["normal"]["status"] == R.RBSOG_JOB_DONE and info["normal"]["steps_done"] == n_normal
