@@ -10,8 +10,8 @@ Reduced OCP units (Sec. 5.1 of the paper defines Gamma~ = Q^2/(a k_B T) and
 kappa = a/lambda): every particle has charge Q = 1 and mass 1, a is the
 Wigner-Seitz radius a = (3/(4 pi n))^(1/3) with n = N/V, and lengths given
 "in units of a" are multiplied by a here.  The paper prints a = (4 pi n)^(-1/3),
-which lacks the factor 3 of the Wigner-Seitz radius; the Wigner-Seitz reading
-is used (reading R-1).
+which lacks the factor 3 of the Wigner-Seitz radius; the Wigner-Seitz radius is
+used here.
 """
 from __future__ import annotations
 
