@@ -28,7 +28,7 @@ namespace {
 constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
 constexpr int kListCap = 32;           // listed candidates per thread between flushes
-constexpr int kMaxTileW = 64;
+constexpr int kMaxTileW = 48;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -36,8 +36,19 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// FP32 pair constants of one system, copied to shared memory by each tiled CTA (a batch
+// reads its systems' arguments from global memory, and the pair loop reads them per
+// Gaussian).
+struct NearF {
+    int mtot;
+    float inv_lam_log2e_f, inv_lam_f, rc2_f;
+    float af[kMaxGauss], bl2f[kMaxGauss], cf[kMaxGauss];
+};
+
 // One FP32 pair: accumulate q_i q_j [F_N1 + F_N2](r) (r_i - r_j) and U_N/2 (compensated).
-__device__ __forceinline__ void pair_f32(const NearConsts &nc, float qq, float d0, float d1, float d2, float r2,
+// C is NearConsts or NearF (the same float fields).
+template <class C>
+__device__ __forceinline__ void pair_f32(const C &nc, float qq, float d0, float d1, float d2, float r2,
                                          float *Fs, float *Fc, float &Us, float &Uc) {
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
@@ -195,6 +206,7 @@ template <int CAP>
 struct TileSmem {
     uint4 stage[CAP];                       // staged records
     uint16_t list[kListCap][kTileThreads];  // per-thread candidate lists (staging indices)
+    NearF nf;                               // the system's FP32 pair constants
     int seg_off[9][kMaxTileW + 3];          // per row: offset of each region cell within the row
     int row_base[10];                       // per row: offset of the row in the staging buffer
     uint32_t chunk_g[9][2];                 // per row: global start of up to two slices
@@ -205,7 +217,7 @@ struct TileSmem {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <int CAP>
-__device__ __forceinline__ void flush_list(const TileSmem<CAP> &S, const NearConsts &nc, const Box &box, int cnt,
+__device__ __forceinline__ void flush_list(const TileSmem<CAP> &S, const NearF &nc, const Box &box, int cnt,
                                            uint4 ri, float qi, float *Fs, float *Fc, float &Us, float &Uc) {
     for (int k = 0; k < cnt; ++k) {
         const uint4 rj = S.stage[S.list[k][threadIdx.x]];
@@ -239,6 +251,17 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
         const int c = x + nx * (yr + ny * zr);
         S.seg_off[r][i + 1] = (int)(cs[c + 1] - cs[c]);
+    }
+    if (tid == 0) {
+        S.nf.mtot = a.nc.mtot;
+        S.nf.inv_lam_log2e_f = a.nc.inv_lam_log2e_f;
+        S.nf.inv_lam_f = a.nc.inv_lam_f;
+        S.nf.rc2_f = a.nc.rc2_f;
+    }
+    for (int g = tid; g < a.nc.mtot; g += kTileThreads) {
+        S.nf.af[g] = a.nc.af[g];
+        S.nf.bl2f[g] = a.nc.bl2f[g];
+        S.nf.cf[g] = a.nc.cf[g];
     }
     __syncthreads();
     if (tid < 9) {
@@ -373,7 +396,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                         }
                     }
                     if (cnt <= kListCap) {
-                        flush_list(S, a.nc, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
+                        flush_list(S, S.nf, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
                     } else {
                         // rare: more hits than the list holds; evaluate the three rows
                         // directly, in the same candidate order
@@ -386,7 +409,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                                 const float d1 = (float)(int)(ri.y - rk.y) * sy;
                                 const float d2 = (float)(int)(ri.z - rk.z) * sz;
                                 if (d0 * d0 + d1 * d1 + d2 * d2 < rc2 && k != j)
-                                    pair_f32(a.nc, qi * __uint_as_float(rk.w), d0, d1, d2,
+                                    pair_f32(S.nf, qi * __uint_as_float(rk.w), d0, d1, d2,
                                              d0 * d0 + d1 * d1 + d2 * d2, Fs, Fc, Us, Uc);
                             }
                         }
