@@ -5,14 +5,21 @@
 // in one (y, z) row.  Their 27-cell neighbourhood is 9 rows of W + 2 cells, and each such
 // row is one (or, across the periodic seam, two) contiguous slices of the cell-sorted
 // 16-byte particle records, so the CTA stages the whole neighbourhood in shared memory
-// with TMA bulk copies completing on one mbarrier.  Each target particle then
-//   (1) tests its 27 cells with exact fixed-point differences (r^2 < r_c^2) and lists
-//       the hits by staging index, and
-//   (2) evaluates the pair force on the listed candidates,
-// with the list flushed at three points per target where the warp is converged (after
-// rows 2, 5 and 8), so the expensive pair arithmetic runs on whole warps instead of
-// diverging inside the candidate loop.  One 16-byte record per staged particle and a
-// 32-entry list keep enough CTAs resident to hide latency.
+// with TMA bulk copies completing on one mbarrier; while they fly it writes, for each
+// of its target cells, the list of staging indices of that cell's 27-cell candidates.
+// A warp owns 32 consecutive targets (about five cells) and works in two phases:
+//   (1) filter, cell by cell: the lanes hold the cell's candidates (32 per slot) as FP32
+//       offsets from the cell centre, and the warp tests each target of the cell against
+//       all of them at once (packed FP32x2 arithmetic), keeping one ballot mask per slot.
+//       Loop counts are the same on every lane, and a candidate is converted once per
+//       cell, not once per target.  The FP32 offsets are a slightly generous pre-filter:
+//       every pair that the exact test accepts passes it;
+//   (2) pairs: each lane walks its own target's masks in candidate order, recomputes the
+//       separation exactly from the fixed-point coordinates, applies the exact r < r_c
+//       test and accumulates the pair force (compensated FP32 sums).  The pairs and their
+//       order are those of a plain loop over the 27 cells, so the result does not depend
+//       on the pre-filter.
+// Neighbourhoods larger than 8 slots (256 candidates) run in several such rounds.
 // Otherwise (FP64 build, fewer than 3 cells on an axis, or a neighbourhood that does
 // not fit the staging buffer): one thread per particle reading candidates from global
 // memory.
@@ -27,13 +34,38 @@ namespace {
 
 constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
-constexpr int kListCap = 32;           // listed candidates per thread between flushes
+constexpr int kSlots = 8;              // candidate slots (32 candidates each) per filter round
 constexpr int kMaxTileW = 48;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Packed FP32x2 arithmetic (two lanes of one 64-bit register), round to nearest.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 // FP32 pair constants of one system, copied to shared memory by each tiled CTA (a batch
@@ -44,6 +76,24 @@ struct NearF {
     float inv_lam_log2e_f, inv_lam_f, rc2_f;
     float af[kMaxGauss], bl2f[kMaxGauss], cf[kMaxGauss];
 };
+
+// The two terms of one FP32 pair before accumulation: gsc = q_i q_j [F_N1 + F_N2](r) and
+// uh = q_i q_j [Y - F](r) / 2.
+template <class C>
+__device__ __forceinline__ void pair_terms(const C &nc, float qq, float r2, float &gsc, float &uh) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float e1 = ex2_approx(-r * nc.inv_lam_log2e_f);
+    float fsog = 0.f, fn2 = 0.f;
+    for (int g = 0; g < nc.mtot; ++g) {
+        const float E = ex2_approx(-r2 * nc.bl2f[g]);
+        fsog = fmaf(nc.af[g], E, fsog);
+        fn2 = fmaf(nc.cf[g], E, fn2);
+    }
+    const float fn1 = e1 * (1.f + r * nc.inv_lam_f) * (rinv * rinv * rinv);
+    gsc = qq * (fn1 + fn2);
+    uh = 0.5f * qq * (e1 * rinv - fsog);
+}
 
 // One FP32 pair: accumulate q_i q_j [F_N1 + F_N2](r) (r_i - r_j) and U_N/2 (compensated).
 // C is NearConsts or NearF (the same float fields).
@@ -200,12 +250,14 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
 }
 
 // ---------------------------------------------------------------- tiled (TMA) FP32 path
-// CAP: staged particles per CTA (16 B each).  One large system stages 1280 (7 CTAs per
-// SM); batches of many systems stage 1024 (8 CTAs per SM), which measured faster there.
+// CAP: staged particles per CTA (16 B each).  One large system stages 1280; batches of
+// many systems stage 1024.
 template <int CAP>
 struct TileSmem {
     uint4 stage[CAP];                       // staged records
-    uint16_t list[kListCap][kTileThreads];  // per-thread candidate lists (staging indices)
+    uint32_t mask[kSlots][kTileThreads];    // per target (column = owning thread): hit bits of a round
+    uint16_t flat[3 * CAP];                 // per target cell: staging indices of its 27-cell candidates
+    int fb[kMaxTileW + 2];                  // target cell i: candidates flat[fb[i] .. fb[i+1])
     NearF nf;                               // the system's FP32 pair constants
     int seg_off[9][kMaxTileW + 3];          // per row: offset of each region cell within the row
     int row_base[10];                       // per row: offset of the row in the staging buffer
@@ -216,22 +268,25 @@ struct TileSmem {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Region cell (1 .. wn-2) of the centre row holding staged target jl (offset within row 4):
+// the last i with seg_off[4][i] <= jl.
 template <int CAP>
-__device__ __forceinline__ void flush_list(const TileSmem<CAP> &S, const NearF &nc, const Box &box, int cnt,
-                                           uint4 ri, float qi, float *Fs, float *Fc, float &Us, float &Uc) {
-    for (int k = 0; k < cnt; ++k) {
-        const uint4 rj = S.stage[S.list[k][threadIdx.x]];
-        const float d0 = (float)(int)(ri.x - rj.x) * box.L_2m32f[0];
-        const float d1 = (float)(int)(ri.y - rj.y) * box.L_2m32f[1];
-        const float d2 = (float)(int)(ri.z - rj.z) * box.L_2m32f[2];
-        pair_f32(nc, qi * __uint_as_float(rj.w), d0, d1, d2, d0 * d0 + d1 * d1 + d2 * d2, Fs, Fc, Us, Uc);
+__device__ __forceinline__ int region_cell(const TileSmem<CAP> &S, int wn, int jl) {
+    int lo = 1, hi = wn - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (S.seg_off[4][mid] <= jl) lo = mid;
+        else hi = mid - 1;
     }
+    return lo;
 }
 
 template <int CAP>
 __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
                                                TileSmem<CAP> &S) {
     const int tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const unsigned full = 0xffffffffu;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
     const int tile = (int)(blk % (unsigned)tiles_x);
     const int rest = (int)(blk / (unsigned)tiles_x);
@@ -239,11 +294,12 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     const int x0 = tile * W;
     const int x1 = min(x0 + W, nx);
     const int wn = x1 - x0 + 2;                  // region cells per row: x0-1 .. x1
+    const int ntc = wn - 2;                      // target cells: region cells 1 .. wn-2
     const uint32_t *cs = a.cell_start;
     const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
 
     // cell populations of the 9 x wn region cells, loaded in parallel (row r: dz = r/3 - 1,
-    // dy = r%3 - 1), then per-row prefix sums and global slices
+    // dy = r%3 - 1)
     for (int e = tid; e < 9 * wn; e += kTileThreads) {
         const int r = e / wn, i = e - r * wn;
         const int yr = (cy + r % 3 - 1 + ny) % ny, zr = (cz + r / 3 - 1 + nz) % nz;
@@ -264,6 +320,8 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         S.nf.cf[g] = a.nc.cf[g];
     }
     __syncthreads();
+    // per-row prefix sums and the global slices of each row (a short serial loop per row
+    // measured faster here than warp-wide scans)
     if (tid < 9) {
         const int yr = (cy + tid % 3 - 1 + ny) % ny, zr = (cz + tid / 3 - 1 + nz) % nz;
         const int rowbase = nx * (yr + ny * zr);
@@ -311,13 +369,12 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         bool ok = true;
         if (region_n > 0) {
             const uint32_t bar = smem_u32(&S.mbar);
-            if (tid == 0) {
+            if (tid == 0) {                              // start the bulk copies of the region
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
                 asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                             "r"((uint32_t)region_n * 16u)
-                             : "memory");
+                             "r"((uint32_t)region_n * 16u) : "memory");
                 const uint4 *rec = (const uint4 *)a.rec;
                 for (int r = 0; r < 9; ++r) {
                     uint32_t dst = (uint32_t)S.row_base[r];
@@ -327,15 +384,44 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             asm volatile(
                                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
                                 "[%3];" ::"r"(smem_u32(&S.stage[dst])),
-                                "l"(rec + S.chunk_g[r][h]), "r"(n * 16u), "r"(bar)
-                                : "memory");
+                                "l"(rec + S.chunk_g[r][h]), "r"(n * 16u), "r"(bar) : "memory");
                             dst += n;
                         }
                     }
                 }
             }
+            // offsets of the target cells' candidate lists: fb[i] = sum of the 27-cell counts
+            // of target cells 1 .. i-1.  A staged particle is a candidate of at most 3 target
+            // cells, so all lists together fit 3 CAP entries.  (The barriers below also make
+            // thread 0's mbarrier initialisation visible before any thread polls it.)
+            if (tid < ntc) {
+                const int i = tid + 1;
+                int tot = 0;
+                for (int r = 0; r < 9; ++r) tot += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
+                S.fb[i + 1] = tot;
+            }
             __syncthreads();
-            // bounded wait for the staged bytes (phase 0); the outcome is made block-uniform
+            if (tid == 0) {
+                int b = 0;
+                S.fb[1] = 0;
+                for (int i = 1; i <= ntc; ++i) {
+                    b += S.fb[i + 1];
+                    S.fb[i + 1] = b;
+                }
+            }
+            __syncthreads();
+            // while the copies fly: the candidate list of each target cell i, rows 0..8 in
+            // order, each row's cells i-1 .. i+1 in staging order
+            for (int e = tid; e < 9 * ntc; e += kTileThreads) {
+                const int i = e / 9 + 1, r = e - (e / 9) * 9;
+                int pos = S.fb[i];
+                for (int q = 0; q < r; ++q) pos += S.seg_off[q][i + 2] - S.seg_off[q][i - 1];
+                const int a0 = S.seg_off[r][i - 1], n = S.seg_off[r][i + 2] - a0;
+                const int st = S.row_base[r] + a0;
+                for (int l = 0; l < n; ++l) S.flat[pos + l] = (uint16_t)(st + l);
+            }
+            // bounded wait for the staged bytes (phase 0); the outcome is made block-uniform,
+            // and the block barrier also publishes the candidate lists
             uint32_t done = 0;
             for (int it = 0; it < (1 << 22) && !done; ++it) {
                 asm volatile(
@@ -357,69 +443,187 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             }
         }
         if (ok) {
-            const int t0 = S.row_base[4] + S.seg_off[4][1];
-            const int t1 = S.row_base[4] + S.seg_off[4][wn - 1];
+            const int rb4 = S.row_base[4];
+            const int t0 = rb4 + S.seg_off[4][1];
+            const int t1 = rb4 + S.seg_off[4][wn - 1];
             float *Fn = (float *)a.Fn;
             const float rc2 = a.nc.rc2_f;
-            for (int j = t0 + tid; j < t1; j += kTileThreads) {
-                // region cell i (1 .. wn-2) holding target j: last i with seg_off[4][i] <= j - row_base[4]
-                const int jl = j - S.row_base[4];
-                int lo = 1, hi = wn - 2;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (S.seg_off[4][mid] <= jl) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int i = lo;
-                const uint4 ri = S.stage[j];
+            // Pre-filter threshold.  An FP32 offset from the cell centre is within 1.8e-7 c of
+            // the exact one (|offset| <= 1.5 c, two roundings), so the pre-filter's r^2 is
+            // within 1.5e-6 r_c^2 of the exact r^2 near the cutoff (c < 4/3 r_c because
+            // n_c = floor(L / r_c) >= 3); a margin of 1e-5 keeps every pair that the exact
+            // test accepts.
+            const float rcf2 = rc2 * 1.00001f;
+            const float sx = a.box.L_2m32f[0], sy = a.box.L_2m32f[1], sz = a.box.L_2m32f[2];
+            // fixed-point centre of the target row (y, z) and cell width along x; any point
+            // near the centre serves, only offsets up to 1.5 cells matter
+            const float cwx = 4294967296.f / (float)nx;
+            const uint32_t oy = __float2uint_rz(((float)cy + 0.5f) * (4294967296.f / (float)ny));
+            const uint32_t oz = __float2uint_rz(((float)cz + 0.5f) * (4294967296.f / (float)nz));
+            for (int wlo = t0 + 32 * wid; wlo < t1; wlo += kTileThreads) {
+                const int whi = min(wlo + 32, t1);
+                const int j = wlo + lane;
+                const bool has = j < whi;
+                const int i_lo = region_cell(S, wn, wlo - rb4);
+                const int i_hi = region_cell(S, wn, whi - 1 - rb4);
+                const int i_own = has ? region_cell(S, wn, j - rb4) : i_hi;
+                const uint4 ri = S.stage[has ? j : wlo];
                 const float qi = __uint_as_float(ri.w);
                 float Fs[3] = {0.f, 0.f, 0.f}, Fc[3] = {0.f, 0.f, 0.f}, Us = 0.f, Uc = 0.f;
-                const float sx = a.box.L_2m32f[0], sy = a.box.L_2m32f[1], sz = a.box.L_2m32f[2];
-                for (int r0 = 0; r0 < 9; r0 += 3) {
-                    // filter: list the hits of three rows (the list keeps the first kListCap,
-                    // the count keeps going); the loop holds no pair arithmetic
-                    int cnt = 0;
-                    for (int r = r0; r < r0 + 3; ++r) {
-                        const int rb = S.row_base[r];
-                        const int k0 = rb + S.seg_off[r][i - 1];
-                        const int k1 = rb + S.seg_off[r][i + 2];
-#pragma unroll 2
-                        for (int k = k0; k < k1; ++k) {
-                            const uint4 rk = S.stage[k];
-                            const float d0 = (float)(int)(ri.x - rk.x) * sx;
-                            const float d1 = (float)(int)(ri.y - rk.y) * sy;
-                            const float d2 = (float)(int)(ri.z - rk.z) * sz;
-                            if (d0 * d0 + d1 * d1 + d2 * d2 < rc2 && k != j) {
-                                if (cnt < kListCap) S.list[cnt][tid] = (uint16_t)k;
-                                ++cnt;
+                int own_cb = 0, own_total = 0;
+                for (int base = 0;; base += 32 * kSlots) {
+                    bool more = false;
+                    // (1) filter, cell by cell: the lanes hold the cell's candidates, the warp
+                    // tests each target of the cell against all of them
+                    for (int i = i_lo; i <= i_hi; ++i) {
+                        const int ta = max(wlo, rb4 + S.seg_off[4][i]);
+                        const int tb = min(whi, rb4 + S.seg_off[4][i + 1]);
+                        if (ta >= tb) continue;
+                        const int cb = S.fb[i], total = S.fb[i + 1] - cb;
+                        if (i == i_own) {
+                            own_cb = cb;
+                            own_total = total;
+                        }
+                        if (total <= base) continue;
+                        more = more || total > base + 32 * kSlots;
+                        const int nsl = min(kSlots, (total - base + 31) >> 5);
+                        const uint32_t ox = __float2uint_rz(((float)(x0 - 1 + i) + 0.5f) * cwx);
+                        float X[kSlots], Y[kSlots], Z[kSlots];
+#pragma unroll
+                        for (int s = 0; s < kSlots; ++s) {
+                            X[s] = 3e30f;
+                            Y[s] = 0.f;
+                            Z[s] = 0.f;
+                            const int f = base + 32 * s + lane;
+                            if (s < nsl && f < total) {
+                                const uint4 rk = S.stage[S.flat[cb + f]];
+                                X[s] = (float)(int)(rk.x - ox) * sx;
+                                Y[s] = (float)(int)(rk.y - oy) * sy;
+                                Z[s] = (float)(int)(rk.z - oz) * sz;
+                            }
+                        }
+                        unsigned long long X2[kSlots / 2], Y2[kSlots / 2], Z2[kSlots / 2];
+#pragma unroll
+                        for (int h = 0; h < kSlots / 2; ++h) {
+                            X2[h] = pk2(X[2 * h], X[2 * h + 1]);
+                            Y2[h] = pk2(Y[2 * h], Y[2 * h + 1]);
+                            Z2[h] = pk2(Z[2 * h], Z[2 * h + 1]);
+                        }
+                        int t = ta;
+                        for (; t + 1 < tb; t += 2) {
+                            const uint4 pa = S.stage[t], pb = S.stage[t + 1];
+                            const float xa = (float)(int)(pa.x - ox) * sx, ya = (float)(int)(pa.y - oy) * sy,
+                                        za = (float)(int)(pa.z - oz) * sz;
+                            const float xb = (float)(int)(pb.x - ox) * sx, yb = (float)(int)(pb.y - oy) * sy,
+                                        zb = (float)(int)(pb.z - oz) * sz;
+                            const unsigned long long xa2 = pk2(xa, xa), ya2 = pk2(ya, ya), za2 = pk2(za, za);
+                            const unsigned long long xb2 = pk2(xb, xb), yb2 = pk2(yb, yb), zb2 = pk2(zb, zb);
+                            const int col = 32 * wid + (t - wlo);
+#pragma unroll
+                            for (int h = 0; h < kSlots / 2; ++h) {
+                                if (2 * h < nsl) {
+                                    const unsigned long long dxa = sub2(xa2, X2[h]), dya = sub2(ya2, Y2[h]), dza = sub2(za2, Z2[h]);
+                                    const unsigned long long dxb = sub2(xb2, X2[h]), dyb = sub2(yb2, Y2[h]), dzb = sub2(zb2, Z2[h]);
+                                    const unsigned long long r2a = fma2(dza, dza, fma2(dya, dya, mul2(dxa, dxa)));
+                                    const unsigned long long r2b = fma2(dzb, dzb, fma2(dyb, dyb, mul2(dxb, dxb)));
+                                    float a0, a1, b0, b1;
+                                    upk2(r2a, a0, a1);
+                                    upk2(r2b, b0, b1);
+                                    const uint32_t ma0 = __ballot_sync(full, a0 < rcf2);
+                                    const uint32_t mb0 = __ballot_sync(full, b0 < rcf2);
+                                    if (lane == 0) {
+                                        S.mask[2 * h][col] = ma0;
+                                        S.mask[2 * h][col + 1] = mb0;
+                                    }
+                                    if (2 * h + 1 < nsl) {
+                                        const uint32_t ma1 = __ballot_sync(full, a1 < rcf2);
+                                        const uint32_t mb1 = __ballot_sync(full, b1 < rcf2);
+                                        if (lane == 0) {
+                                            S.mask[2 * h + 1][col] = ma1;
+                                            S.mask[2 * h + 1][col + 1] = mb1;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                        if (t < tb) {
+                            const uint4 rt = S.stage[t];
+                            const float xt = (float)(int)(rt.x - ox) * sx;
+                            const float yt = (float)(int)(rt.y - oy) * sy;
+                            const float zt = (float)(int)(rt.z - oz) * sz;
+                            const unsigned long long xt2 = pk2(xt, xt), yt2 = pk2(yt, yt), zt2 = pk2(zt, zt);
+                            const int col = 32 * wid + (t - wlo);
+#pragma unroll
+                            for (int h = 0; h < kSlots / 2; ++h) {
+                                if (2 * h < nsl) {
+                                    const unsigned long long dx = sub2(xt2, X2[h]), dy = sub2(yt2, Y2[h]), dz = sub2(zt2, Z2[h]);
+                                    const unsigned long long r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                                    float ra, rb;
+                                    upk2(r2, ra, rb);
+                                    const uint32_t ma = __ballot_sync(full, ra < rcf2);
+                                    if (lane == 0) S.mask[2 * h][col] = ma;
+                                    if (2 * h + 1 < nsl) {
+                                        const uint32_t mb = __ballot_sync(full, rb < rcf2);
+                                        if (lane == 0) S.mask[2 * h + 1][col] = mb;
+                                    }
+                                }
                             }
                         }
                     }
-                    if (cnt <= kListCap) {
-                        flush_list(S, S.nf, a.box, cnt, ri, qi, Fs, Fc, Us, Uc);
-                    } else {
-                        // rare: more hits than the list holds; evaluate the three rows
-                        // directly, in the same candidate order
-                        for (int r = r0; r < r0 + 3; ++r) {
-                            const int rb = S.row_base[r];
-                            const int k1 = rb + S.seg_off[r][i + 2];
-                            for (int k = rb + S.seg_off[r][i - 1]; k < k1; ++k) {
-                                const uint4 rk = S.stage[k];
-                                const float d0 = (float)(int)(ri.x - rk.x) * sx;
-                                const float d1 = (float)(int)(ri.y - rk.y) * sy;
-                                const float d2 = (float)(int)(ri.z - rk.z) * sz;
-                                if (d0 * d0 + d1 * d1 + d2 * d2 < rc2 && k != j)
-                                    pair_f32(S.nf, qi * __uint_as_float(rk.w), d0, d1, d2,
-                                             d0 * d0 + d1 * d1 + d2 * d2, Fs, Fc, Us, Uc);
+                    __syncwarp();
+                    // (2) pairs of the own target in candidate order (rows 0..8, staging
+                    // order), two per pass: exact separation and exact r < r_c test
+                    if (has) {
+                        const int nsl = min(kSlots, max(0, (own_total - base + 31) >> 5));
+                        uint32_t m = 0;
+                        int s = -1;
+                        while (true) {
+                            int kA = -1, kB = -1;
+                            while (m == 0 && ++s < nsl) m = S.mask[s][tid];
+                            if (m != 0) {
+                                kA = S.flat[own_cb + base + 32 * s + (__ffs(m) - 1)];
+                                m &= m - 1;
+                            }
+                            while (m == 0 && ++s < nsl) m = S.mask[s][tid];
+                            if (m != 0) {
+                                kB = S.flat[own_cb + base + 32 * s + (__ffs(m) - 1)];
+                                m &= m - 1;
+                            }
+                            if (kA < 0) break;
+                            const uint4 pa = S.stage[kA], pb = S.stage[kB < 0 ? kA : kB];
+                            const float a0 = (float)(int)(ri.x - pa.x) * sx, a1 = (float)(int)(ri.y - pa.y) * sy,
+                                        a2 = (float)(int)(ri.z - pa.z) * sz;
+                            const float b0 = (float)(int)(ri.x - pb.x) * sx, b1 = (float)(int)(ri.y - pb.y) * sy,
+                                        b2 = (float)(int)(ri.z - pb.z) * sz;
+                            const float r2a = a0 * a0 + a1 * a1 + a2 * a2, r2b = b0 * b0 + b1 * b1 + b2 * b2;
+                            const bool va = kA != j && r2a < rc2, vb = kB >= 0 && kB != j && r2b < rc2;
+                            float ga, ua, gb, ub;
+                            pair_terms(S.nf, qi * __uint_as_float(pa.w), va ? r2a : rc2, ga, ua);
+                            pair_terms(S.nf, qi * __uint_as_float(pb.w), vb ? r2b : rc2, gb, ub);
+                            if (va) {
+                                kahan_add(Fs[0], Fc[0], ga * a0);
+                                kahan_add(Fs[1], Fc[1], ga * a1);
+                                kahan_add(Fs[2], Fc[2], ga * a2);
+                                kahan_add(Us, Uc, ua);
+                            }
+                            if (vb) {
+                                kahan_add(Fs[0], Fc[0], gb * b0);
+                                kahan_add(Fs[1], Fc[1], gb * b1);
+                                kahan_add(Fs[2], Fc[2], gb * b2);
+                                kahan_add(Us, Uc, ub);
                             }
                         }
                     }
+                    __syncwarp();
+                    if (!more) break;
                 }
-                const uint32_t g = g_first + (uint32_t)(j - t0);
-                Fn[g] = Fs[0] - Fc[0];
-                Fn[a.stride + g] = Fs[1] - Fc[1];
-                Fn[2 * (size_t)a.stride + g] = Fs[2] - Fc[2];
-                sumU += Us - Uc;
+                if (has) {
+                    const uint32_t g = g_first + (uint32_t)(j - t0);
+                    Fn[g] = Fs[0] - Fc[0];
+                    Fn[a.stride + g] = Fs[1] - Fc[1];
+                    Fn[2 * (size_t)a.stride + g] = Fs[2] - Fc[2];
+                    sumU += Us - Uc;
+                }
             }
         }
     } else {
@@ -436,7 +640,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     warp_partial((double)sumU + Ufall, a.U_part, blk);
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, int tiles_x) {
+__global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     near_tile_body<kNearCapSingle>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle> *>(smem_raw));
 }
@@ -444,7 +648,7 @@ __global__ void __launch_bounds__(kTileThreads) k_near_tiled(NearArgs a, int W, 
 // Batched systems: block -> (system, local block); each system uses tiles or the
 // per-particle path as its geometry says.  geom.W doubles as the first global record
 // index of the system for the per-particle path.
-__global__ void __launch_bounds__(kTileThreads) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
+__global__ void __launch_bounds__(kTileThreads, 6) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
                                                             const uint32_t *items, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int lo = 0, hi = R - 1;
