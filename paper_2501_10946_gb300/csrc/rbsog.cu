@@ -56,6 +56,9 @@ struct rbsog_ctx {
     DevCounters *ctr = nullptr;
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
+    // the structure factor runs beside the near field on this stream inside a step
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool force_valid = false;
     SamplerTables tab{};
@@ -416,20 +419,40 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     sa.Q2a = c->p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * kPi) * c->Q2 : c->Q2;
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
     { ProfScope ps(c, st, 4); launch_sample(sa, st); }
+    // The structure factor (rho, rho_final: special-function unit) and the near field
+    // (integer and FMA pipes) are independent: outside profiling, rho runs on a side stream
+    // so that the two share the SMs; far waits for both.  Profiling keeps one stream so
+    // every group's events time that group alone.
+    const bool fork = !c->prof;
+    cudaStream_t sr = st;
+    if (fork) {
+        if (cudaEventRecord(c->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "fork the structure-factor stream");
+        sr = c->side_stream;
+    }
+    RhoArgs ra{};
+    ra.rec = c->rec; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
+    RhoFinalArgs rf{};
+    rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
+    for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
+    rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
+    if (fork) {
+        launch_rho(prec, ra, sr);
+        launch_rho_final(prec, rf, sr);
+    }
     NearArgs na{};
     na.nc = c->nconsts; na.rec = c->rec; na.cell_start = c->cell_start; na.box = c->box; na.N = N; na.stride = N;
     na.Fn = c->Fn;
     na.U_part = c->U_part;
     na.ctr = c->ctr;
     { ProfScope ps(c, st, 5); c->nU = launch_near(prec, na, st); }
-    RhoArgs ra{};
-    ra.rec = c->rec; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
-    { ProfScope ps(c, st, 6); launch_rho(prec, ra, st); }
-    RhoFinalArgs rf{};
-    rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
-    for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
-    rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
-    { ProfScope ps(c, st, 7); launch_rho_final(prec, rf, st); }
+    if (fork) {
+        if (cudaEventRecord(c->ev_join, sr) != cudaSuccess || cudaStreamWaitEvent(st, c->ev_join, 0) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "join the structure-factor stream");
+    } else {
+        { ProfScope ps(c, st, 6); launch_rho(prec, ra, st); }
+        { ProfScope ps(c, st, 7); launch_rho_final(prec, rf, st); }
+    }
     FarArgs fa{};
     fa.rec = c->rec; fa.N = N; fa.stride = N; fa.P = c->p.P; fa.gtab = c->gtab; fa.m = c->modes; fa.Fn = c->Fn; fa.F = c->F;
     fa.st = c->rest; fa.integrate = integrate ? 1 : 0; fa.dt = c->p.dt; fa.K_part = c->K_part;
@@ -537,7 +560,10 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         cudaMemset(c->edone, 0, sizeof(unsigned int)) != cudaSuccess ||
         cudaMemcpy(c->q_user, q_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->m_user, m_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         g_init_error = "device initialisation failed";
         return bail(RBSOG_ECUDA);
     }
@@ -767,6 +793,9 @@ void rbsog_free(rbsog_ctx *c) {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (void *p : c->allocs) cudaFree(p);
     delete c;
 }
