@@ -88,6 +88,8 @@ struct rbsog_batch {
     std::vector<rbsog::FarArgs> h_far;                   // host copy of d_far[0]
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side_stream = nullptr;                  // structure factor beside the near field
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
 };
 

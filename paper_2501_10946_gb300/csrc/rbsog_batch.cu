@@ -390,7 +390,10 @@ int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
         return engine_fail(b, RBSOG_ENOMEM, "device allocation failed");
     if (cudaMemset(b->count, 0, sizeof(uint32_t) * C) != cudaSuccess ||
         cudaMemset(b->ctr, 0, sizeof(DevCounters) * R) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return engine_fail(b, RBSOG_ECUDA, "device initialisation failed");
     return RBSOG_OK;
 }
@@ -401,6 +404,11 @@ void engine_release(rbsog_batch *b) {
     b->graph = nullptr;
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     b->cap_stream = nullptr;
+    if (b->side_stream) cudaStreamDestroy(b->side_stream);
+    b->side_stream = nullptr;
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    b->ev_fork = b->ev_join = nullptr;
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
 }
@@ -604,11 +612,23 @@ int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far,
     mark(4);
     launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
     mark(5);
-    launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
-    mark(6);
-    launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], st);
-    mark(7);
-    launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], st);
+    if (!ev) {
+        // the structure factor beside the near field (disjoint outputs); far waits for both
+        BCK(cudaEventRecord(b->ev_fork, st), "fork the structure-factor stream");
+        BCK(cudaStreamWaitEvent(b->side_stream, b->ev_fork, 0), "fork the structure-factor stream");
+        launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], b->side_stream);
+        launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], b->side_stream);
+        launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
+        BCK(cudaEventRecord(b->ev_join, b->side_stream), "join the structure-factor stream");
+        BCK(cudaStreamWaitEvent(st, b->ev_join, 0), "join the structure-factor stream");
+    } else {
+        // profiling: one stream, so each group's events time that group alone
+        launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
+        mark(6);
+        launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], st);
+        mark(7);
+        launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], st);
+    }
     mark(8);
     launch_far_batch(far ? far : b->d_far[set], items_of(b, kItFar), R, b->nb[kItFar], st);
     mark(9);
