@@ -80,7 +80,8 @@ typedef struct rbsog_params {
     double sog_eps;         /* SOG tolerance eps of Algorithm 1, in (0, 0.1] */
     double dt;              /* time step */
     double langevin_gamma;  /* Langevin friction (1/time), used with RBSOG_LANGEVIN */
-    uint64_t seed;          /* Philox key for the k-sampler and the Langevin noise */
+    uint64_t seed;          /* Philox key for the k-sampler and the Langevin noise; both are
+                               counted by force evaluations, which rbsog_set_state does not reset */
     int32_t P;              /* random-batch size, 1 <= P <= 4096 */
     int32_t precision;      /* RBSOG_FP64 | RBSOG_FP32 */
     int32_t ensemble;       /* RBSOG_NVE | RBSOG_LANGEVIN */

@@ -73,11 +73,13 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) r[d] += a.dt * v[d];
         } else {
-            // B A O A of BAOAB; noise: Philox key = seed, counter = (id, 0x40000000 + j, step)
-            const unsigned long long step = a.ctr->step;
+            // B A O A of BAOAB; noise: Philox key = seed, counter = (id, 0x40000000 + j, n),
+            // n = force evaluations (k-draws) so far.  Setting a state does not reset n, so a
+            // loop that uploads the state before every step still draws fresh noise.
+            const unsigned long long n = a.ctr->draw;
             const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-            U4 w0 = philox10(id, 0x40000000u, (uint32_t)step, (uint32_t)(step >> 32), k0, k1);
-            U4 w1 = philox10(id, 0x40000001u, (uint32_t)step, (uint32_t)(step >> 32), k0, k1);
+            U4 w0 = philox10(id, 0x40000000u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
+            U4 w1 = philox10(id, 0x40000001u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
             double xi[3];
             if (PREC == 1) {
                 // FP32 build: the same Box-Muller pairs from the 24 leading bits of the words

@@ -52,7 +52,8 @@ def oracle_trajectory(w, r0, v0, ks, nsteps, q=None, m=None):
     rs, vs = [], []
     for n in range(nsteps):
         if w.ensemble == "langevin":
-            r, v, F = integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n, force)
+            # the GPU keys step n's noise by the force evaluations before it: n + 1
+            r, v, F = integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n + 1, force)
         else:
             r, v, F = integrate.vv_step(r, v, F, m, w.box, w.dt, force)
         rs.append(r)
@@ -132,3 +133,24 @@ def test_energy_components_after_steps_match_oracle():
     assert abs(e["U_far"] - eo["U_F"]) <= 1e-11 * abs(eo["U_F"])
     assert abs(e["kinetic"] - integrate.kinetic(v, W.masses(w))) <= 1e-12 * e["kinetic"]
     assert e["step"] == 3
+
+
+def test_each_upload_draws_fresh_langevin_noise():
+    """A host loop that uploads the state before every step (set_state, step, get_state)
+    must not reuse the Langevin noise: the same state uploaded twice and stepped once
+    gives velocities that differ by about sqrt(2) times the noise amplitude c2 sigma,
+    far more than the random far force makes them differ."""
+    w = workload(500, 8.0, kappa=1.0, Gamma=1.0, P=64, seed=47, dt=0.002, ensemble="langevin")
+    r0, v0 = W.positions(w), W.velocities(w)
+    vs = []
+    with Ctx(w, R.RBSOG_FP32) as c:
+        for _ in range(2):
+            R.rbsog_set_state(c.h, r0, v0)
+            R.rbsog_step(c.h, 1)
+            v = np.zeros((w.N, 3))
+            R.rbsog_get_state(c.h, None, v)
+            vs.append(v)
+    c1 = np.exp(-w.langevin_gamma * w.dt)
+    c2 = np.sqrt((1.0 - c1 * c1) * w.kT)          # unit masses
+    rms = float(np.sqrt(np.mean((vs[0] - vs[1]) ** 2)))
+    assert 0.8 * np.sqrt(2.0) * c2 <= rms <= 1.2 * np.sqrt(2.0) * c2, (rms, c2)
