@@ -57,6 +57,11 @@ __device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigne
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
     unsigned long long r;
     asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
@@ -70,29 +75,50 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 
 // FP32 pair constants of one system, copied to shared memory by each tiled CTA (a batch
 // reads its systems' arguments from global memory, and the pair loop reads them per
-// Gaussian).
+// Gaussian).  Each constant is stored twice in one 64-bit word, for packed arithmetic on
+// two pairs at once.
 struct NearF {
     int mtot;
-    float inv_lam_log2e_f, inv_lam_f, rc2_f;
-    float af[kMaxGauss], bl2f[kMaxGauss], cf[kMaxGauss];
+    unsigned long long nl2;                 // -log2(e)/lambda
+    unsigned long long il2;                 // 1/lambda
+    unsigned long long nb[kMaxGauss];       // -b_m log2(e)
+    unsigned long long af[kMaxGauss];       // a_m
+    unsigned long long cf[kMaxGauss];       // c_m
 };
 
-// The two terms of one FP32 pair before accumulation: gsc = q_i q_j [F_N1 + F_N2](r) and
-// uh = q_i q_j [Y - F](r) / 2.
-template <class C>
-__device__ __forceinline__ void pair_terms(const C &nc, float qq, float r2, float &gsc, float &uh) {
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float e1 = ex2_approx(-r * nc.inv_lam_log2e_f);
-    float fsog = 0.f, fn2 = 0.f;
+__device__ __forceinline__ unsigned long long dup2(float a) { return pk2(a, a); }
+
+// Compensated sum of two lanes at once (the steps of kahan_add on each lane).
+__device__ __forceinline__ void kahan2(unsigned long long &s, unsigned long long &c, unsigned long long x) {
+    const unsigned long long y = sub2(x, c);
+    const unsigned long long t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+}
+
+// The two terms of two FP32 pairs (one per lane) before accumulation:
+// gsc = q_i q_j [F_N1 + F_N2](r) and uh = q_i q_j [Y - F](r) / 2.
+__device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long qq, unsigned long long r2,
+                                            unsigned long long &gsc, unsigned long long &uh) {
+    float r2a, r2b;
+    upk2(r2, r2a, r2b);
+    const unsigned long long rinv = pk2(rsqrtf(r2a), rsqrtf(r2b));
+    const unsigned long long r = mul2(r2, rinv);
+    float xa, xb;
+    upk2(mul2(r, nc.nl2), xa, xb);
+    const unsigned long long e1 = pk2(ex2_approx(xa), ex2_approx(xb));
+    unsigned long long fsog = 0ull, fn2 = 0ull;
     for (int g = 0; g < nc.mtot; ++g) {
-        const float E = ex2_approx(-r2 * nc.bl2f[g]);
-        fsog = fmaf(nc.af[g], E, fsog);
-        fn2 = fmaf(nc.cf[g], E, fn2);
+        float ya, yb;
+        upk2(mul2(r2, nc.nb[g]), ya, yb);
+        const unsigned long long E = pk2(ex2_approx(ya), ex2_approx(yb));
+        fsog = fma2(nc.af[g], E, fsog);
+        fn2 = fma2(nc.cf[g], E, fn2);
     }
-    const float fn1 = e1 * (1.f + r * nc.inv_lam_f) * (rinv * rinv * rinv);
-    gsc = qq * (fn1 + fn2);
-    uh = 0.5f * qq * (e1 * rinv - fsog);
+    const unsigned long long rinv3 = mul2(mul2(rinv, rinv), rinv);
+    const unsigned long long fn1 = mul2(mul2(e1, fma2(r, nc.il2, dup2(1.f))), rinv3);
+    gsc = mul2(qq, add2(fn1, fn2));
+    uh = mul2(mul2(dup2(0.5f), qq), fma2(e1, rinv, fsog ^ 0x8000000080000000ull));
 }
 
 // One FP32 pair: accumulate q_i q_j [F_N1 + F_N2](r) (r_i - r_j) and U_N/2 (compensated).
@@ -310,14 +336,13 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     }
     if (tid == 0) {
         S.nf.mtot = a.nc.mtot;
-        S.nf.inv_lam_log2e_f = a.nc.inv_lam_log2e_f;
-        S.nf.inv_lam_f = a.nc.inv_lam_f;
-        S.nf.rc2_f = a.nc.rc2_f;
+        S.nf.nl2 = dup2(-a.nc.inv_lam_log2e_f);
+        S.nf.il2 = dup2(a.nc.inv_lam_f);
     }
     for (int g = tid; g < a.nc.mtot; g += kTileThreads) {
-        S.nf.af[g] = a.nc.af[g];
-        S.nf.bl2f[g] = a.nc.bl2f[g];
-        S.nf.cf[g] = a.nc.cf[g];
+        S.nf.nb[g] = dup2(-a.nc.bl2f[g]);
+        S.nf.af[g] = dup2(a.nc.af[g]);
+        S.nf.cf[g] = dup2(a.nc.cf[g]);
     }
     __syncthreads();
     // per-row prefix sums and the global slices of each row (a short serial loop per row
@@ -469,7 +494,8 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                 const int i_own = has ? region_cell(S, wn, j - rb4) : i_hi;
                 const uint4 ri = S.stage[has ? j : wlo];
                 const float qi = __uint_as_float(ri.w);
-                float Fs[3] = {0.f, 0.f, 0.f}, Fc[3] = {0.f, 0.f, 0.f}, Us = 0.f, Uc = 0.f;
+                // compensated sums, packed: (F_x, F_y) and (F_z, U)
+                unsigned long long Fxy = 0ull, Cxy = 0ull, Fzu = 0ull, Czu = 0ull;
                 int own_cb = 0, own_total = 0;
                 for (int base = 0;; base += 32 * kSlots) {
                     bool more = false;
@@ -597,20 +623,19 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                                         b2 = (float)(int)(ri.z - pb.z) * sz;
                             const float r2a = a0 * a0 + a1 * a1 + a2 * a2, r2b = b0 * b0 + b1 * b1 + b2 * b2;
                             const bool va = kA != j && r2a < rc2, vb = kB >= 0 && kB != j && r2b < rc2;
-                            float ga, ua, gb, ub;
-                            pair_terms(S.nf, qi * __uint_as_float(pa.w), va ? r2a : rc2, ga, ua);
-                            pair_terms(S.nf, qi * __uint_as_float(pb.w), vb ? r2b : rc2, gb, ub);
+                            unsigned long long g2, u2;
+                            pair_terms2(S.nf, pk2(qi * __uint_as_float(pa.w), qi * __uint_as_float(pb.w)),
+                                        pk2(va ? r2a : rc2, vb ? r2b : rc2), g2, u2);
+                            float ga, gb, ua, ub;
+                            upk2(g2, ga, gb);
+                            upk2(u2, ua, ub);
                             if (va) {
-                                kahan_add(Fs[0], Fc[0], ga * a0);
-                                kahan_add(Fs[1], Fc[1], ga * a1);
-                                kahan_add(Fs[2], Fc[2], ga * a2);
-                                kahan_add(Us, Uc, ua);
+                                kahan2(Fxy, Cxy, pk2(ga * a0, ga * a1));
+                                kahan2(Fzu, Czu, pk2(ga * a2, ua));
                             }
                             if (vb) {
-                                kahan_add(Fs[0], Fc[0], gb * b0);
-                                kahan_add(Fs[1], Fc[1], gb * b1);
-                                kahan_add(Fs[2], Fc[2], gb * b2);
-                                kahan_add(Us, Uc, ub);
+                                kahan2(Fxy, Cxy, pk2(gb * b0, gb * b1));
+                                kahan2(Fzu, Czu, pk2(gb * b2, ub));
                             }
                         }
                     }
@@ -618,11 +643,16 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                     if (!more) break;
                 }
                 if (has) {
+                    float fx, fy, fz, us, cx, cy, cz_, uc;
+                    upk2(Fxy, fx, fy);
+                    upk2(Cxy, cx, cy);
+                    upk2(Fzu, fz, us);
+                    upk2(Czu, cz_, uc);
                     const uint32_t g = g_first + (uint32_t)(j - t0);
-                    Fn[g] = Fs[0] - Fc[0];
-                    Fn[a.stride + g] = Fs[1] - Fc[1];
-                    Fn[2 * (size_t)a.stride + g] = Fs[2] - Fc[2];
-                    sumU += Us - Uc;
+                    Fn[g] = fx - cx;
+                    Fn[a.stride + g] = fy - cy;
+                    Fn[2 * (size_t)a.stride + g] = fz - cz_;
+                    sumU += us - uc;
                 }
             }
         }
