@@ -28,6 +28,25 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T block_reduce_sum(T v, T *sh) {
     sh[threadIdx.x] = v;
@@ -85,16 +104,45 @@ __device__ __forceinline__ void rho32_body(const RhoArgs &a, int chunk, unsigned
         float tre[ML], tim[ML];
 #pragma unroll
         for (int j = 0; j < ML; ++j) tre[j] = tim[j] = 0.f;
-        for (int i = sub; i < tn; i += nsub) {
-            const uint4 r = sp[i];
-            const float q = __uint_as_float(r.w);
-#pragma unroll
-            for (int j = 0; j < ML; ++j) {
-                const uint32_t th = (uint32_t)mm[j][0] * r.x + (uint32_t)mm[j][1] * r.y + (uint32_t)mm[j][2] * r.z;
+        if constexpr (ML == 1) {
+            for (int i = sub; i < tn; i += nsub) {
+                const uint4 r = sp[i];
+                const float q = __uint_as_float(r.w);
+                const uint32_t th = (uint32_t)mm[0][0] * r.x + (uint32_t)mm[0][1] * r.y + (uint32_t)mm[0][2] * r.z;
                 float sn, cs;
                 const float qs = flip(q, half_turn_sincos(th, sn, cs));
-                tre[j] = fmaf(qs, cs, tre[j]);
-                tim[j] = fmaf(qs, sn, tim[j]);
+                tre[0] = fmaf(qs, cs, tre[0]);
+                tim[0] = fmaf(qs, sn, tim[0]);
+            }
+        } else {
+            // two modes per packed FP32x2 operation
+            unsigned long long re2[ML / 2], im2[ML / 2];
+#pragma unroll
+            for (int h = 0; h < ML / 2; ++h) re2[h] = im2[h] = 0ull;
+            const unsigned long long K2 = pk2(kTwoPiOver2p32, kTwoPiOver2p32);
+            for (int i = sub; i < tn; i += nsub) {
+                const uint4 r = sp[i];
+                const float q = __uint_as_float(r.w);
+#pragma unroll
+                for (int h = 0; h < ML / 2; ++h) {
+                    const int j0 = 2 * h, j1 = 2 * h + 1;
+                    const uint32_t t0 = (uint32_t)mm[j0][0] * r.x + (uint32_t)mm[j0][1] * r.y + (uint32_t)mm[j0][2] * r.z;
+                    const uint32_t t1 = (uint32_t)mm[j1][0] * r.x + (uint32_t)mm[j1][1] * r.y + (uint32_t)mm[j1][2] * r.z;
+                    const uint32_t g0 = (t0 ^ (t0 << 1)) & 0x80000000u, g1 = (t1 ^ (t1 << 1)) & 0x80000000u;
+                    float x0, x1;
+                    upk2(mul2(pk2((float)(int)(t0 ^ g0), (float)(int)(t1 ^ g1)), K2), x0, x1);
+                    float s0, c0, s1, c1;
+                    __sincosf(x0, &s0, &c0);
+                    __sincosf(x1, &s1, &c1);
+                    const unsigned long long qs = pk2(flip(q, g0), flip(q, g1));
+                    re2[h] = fma2(qs, pk2(c0, c1), re2[h]);
+                    im2[h] = fma2(qs, pk2(s0, s1), im2[h]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < ML / 2; ++h) {
+                upk2(re2[h], tre[2 * h], tre[2 * h + 1]);
+                upk2(im2[h], tim[2 * h], tim[2 * h + 1]);
             }
         }
 #pragma unroll
@@ -346,25 +394,32 @@ __device__ __forceinline__ void far32_body(const FarArgs &a, unsigned bx, GTab32
         __syncthreads();
         for (int t = threadIdx.x; t < tn; t += blockDim.x) tab[t] = ((const GTab32 *)a.gtab)[base + t];
         __syncthreads();
+        const unsigned long long K2 = pk2(kTwoPiOver2p32, kTwoPiOver2p32);
         for (int l0 = 0; l0 < tn; l0 += 32) {
             const int l1 = min(tn, l0 + 32);
-            float A0[3] = {0.f, 0.f, 0.f}, A1[3] = {0.f, 0.f, 0.f};
+            // the two particles of the thread share each packed FP32x2 operation
+            unsigned long long A[3] = {0ull, 0ull, 0ull};
             for (int l = l0; l < l1; ++l) {
                 const GTab32 t = tab[l];
                 const float im = __int_as_float(t.m.w), re = t.f.w;
                 const uint32_t th0 = (uint32_t)t.m.x * r0.x + (uint32_t)t.m.y * r0.y + (uint32_t)t.m.z * r0.z;
                 const uint32_t th1 = (uint32_t)t.m.x * r1.x + (uint32_t)t.m.y * r1.y + (uint32_t)t.m.z * r1.z;
+                float x0, x1;
+                upk2(mul2(pk2((float)(int)th0, (float)(int)th1), K2), x0, x1);
                 float s0, c0, s1, c1;
-                __sincosf((float)(int)th0 * kTwoPiOver2p32, &s0, &c0);
-                __sincosf((float)(int)th1 * kTwoPiOver2p32, &s1, &c1);
-                const float g0 = c0 * im - s0 * re, g1 = c1 * im - s1 * re;
-                A0[0] = fmaf(t.f.x, g0, A0[0]); A0[1] = fmaf(t.f.y, g0, A0[1]); A0[2] = fmaf(t.f.z, g0, A0[2]);
-                A1[0] = fmaf(t.f.x, g1, A1[0]); A1[1] = fmaf(t.f.y, g1, A1[1]); A1[2] = fmaf(t.f.z, g1, A1[2]);
+                __sincosf(x0, &s0, &c0);
+                __sincosf(x1, &s1, &c1);
+                const unsigned long long g = fma2(pk2(c0, c1), pk2(im, im), mul2(pk2(s0, s1), pk2(-re, -re)));
+                A[0] = fma2(pk2(t.f.x, t.f.x), g, A[0]);
+                A[1] = fma2(pk2(t.f.y, t.f.y), g, A[1]);
+                A[2] = fma2(pk2(t.f.z, t.f.z), g, A[2]);
             }
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                kahan_add(S0[d], C0[d], A0[d]);
-                kahan_add(S1[d], C1[d], A1[d]);
+                float a0, a1;
+                upk2(A[d], a0, a1);
+                kahan_add(S0[d], C0[d], a0);
+                kahan_add(S1[d], C1[d], a1);
             }
         }
     }
@@ -387,7 +442,8 @@ __device__ __forceinline__ void far32_body(const FarArgs &a, unsigned bx, GTab32
     if (threadIdx.x == 0) a.K_part[bx] = tot;
 }
 
-__global__ void __launch_bounds__(kFarThreads) k_far32(FarArgs a) {
+// 5 blocks per SM (51 registers) measured faster than 4 with more registers
+__global__ void __launch_bounds__(kFarThreads, 5) k_far32(FarArgs a) {
     __shared__ double shK[kFarThreads];
     __shared__ __align__(16) GTab32 tab[kFarTile];
     far32_body(a, blockIdx.x, tab, shK);
