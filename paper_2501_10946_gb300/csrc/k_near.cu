@@ -480,6 +480,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             // test accepts.
             const float rcf2 = rc2 * 1.00001f;
             const float sx = a.box.L_2m32f[0], sy = a.box.L_2m32f[1], sz = a.box.L_2m32f[2];
+            const unsigned long long sx2 = dup2(sx), sy2 = dup2(sy), sz2 = dup2(sz);
             // fixed-point centre of the target row (y, z) and cell width along x; any point
             // near the centre serves, only offsets up to 1.5 cells matter
             const float cwx = 4294967296.f / (float)nx;
@@ -617,11 +618,14 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             }
                             if (kA < 0) break;
                             const uint4 pa = S.stage[kA], pb = S.stage[kB < 0 ? kA : kB];
-                            const float a0 = (float)(int)(ri.x - pa.x) * sx, a1 = (float)(int)(ri.y - pa.y) * sy,
-                                        a2 = (float)(int)(ri.z - pa.z) * sz;
-                            const float b0 = (float)(int)(ri.x - pb.x) * sx, b1 = (float)(int)(ri.y - pb.y) * sy,
-                                        b2 = (float)(int)(ri.z - pb.z) * sz;
-                            const float r2a = a0 * a0 + a1 * a1 + a2 * a2, r2b = b0 * b0 + b1 * b1 + b2 * b2;
+                            const unsigned long long d0 = mul2(pk2((float)(int)(ri.x - pa.x), (float)(int)(ri.x - pb.x)), sx2);
+                            const unsigned long long d1 = mul2(pk2((float)(int)(ri.y - pa.y), (float)(int)(ri.y - pb.y)), sy2);
+                            const unsigned long long d2 = mul2(pk2((float)(int)(ri.z - pa.z), (float)(int)(ri.z - pb.z)), sz2);
+                            float a0, b0, a1, b1, a2, b2, r2a, r2b;
+                            upk2(d0, a0, b0);
+                            upk2(d1, a1, b1);
+                            upk2(d2, a2, b2);
+                            upk2(fma2(d2, d2, fma2(d1, d1, mul2(d0, d0))), r2a, r2b);
                             const bool va = kA != j && r2a < rc2, vb = kB >= 0 && kB != j && r2b < rc2;
                             unsigned long long g2, u2;
                             pair_terms2(S.nf, pk2(qi * __uint_as_float(pa.w), qi * __uint_as_float(pb.w)),
