@@ -15,6 +15,8 @@ Contents, each restating the paper:
   philox.py     Philox4x32-10 (Salmon et al. 2011)
   sampler.py    exact i.i.d. draws from P(k) of Eq. (59)
   integrate.py  velocity Verlet and BAOAB Langevin (Algorithm 2, integration step)
+  egs.py        the EGS screening of Sec. 1 as two Yukawa kernels, and its envelope
+                random-batch estimator, composed from the above by linearity
 
 Every function is pinned by a not-gpu test to something other than itself (printed
 table values, closed forms, brute-force sums, exact moments, published test vectors).
