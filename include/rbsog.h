@@ -90,6 +90,13 @@ typedef struct rbsog_params {
     int32_t sog_M2;         /* with RBSOG_SOG_TABLE: M2 of Eq. (37) */
     int32_t device;         /* CUDA device ordinal */
     int32_t sampling;       /* RBSOG_SAMPLING_*: correction calF of the sampling measure (Eq. 59) */
+    double egs_nu;          /* 0: the Yukawa kernel.  0 < egs_nu <= 0.96: the gradient-corrected
+                               screening eps(k) = 1 + (lambda k)^-2 (1 + egs_nu lambda^2 k^2/4)^-1
+                               of Sec. 1, split by partial fractions into two Yukawa kernels
+                               B Y_{lambda_B} + A Y_{lambda_A} (A + B = 1, A < 0), each with its
+                               own SOG decomposition at r_c and sog_eps (sog_mode MINIMAL or
+                               BOUND); the modes are drawn from the envelope of the far
+                               field's transform and coef carries Fhat / Fhat_env */
 } rbsog_params;
 
 typedef struct rbsog_energy {
@@ -158,8 +165,9 @@ int rbsog_get_rho(rbsog_ctx *ctx, double *rho_host);
 int rbsog_get_cells(rbsog_ctx *ctx, int32_t *nc, uint32_t *cell_start, uint32_t *perm);
 
 /* The SOG decomposition in use (Eq. 37): h, t0, M1, M2, the C1 weight w of m = M2,
- * lambda, and the sampling normalisation S = sum_{k != 0} calF(k) Fhat(k).  Host
- * pointers, any may be NULL. */
+ * lambda, and the sampling normalisation S = sum_{k != 0} calF(k) Fhat(k).  With the EGS
+ * screening (egs_nu > 0) the decomposition is that of its first Yukawa term, lambda_B,
+ * and S is the envelope's.  Host pointers, any may be NULL. */
 int rbsog_get_sog(rbsog_ctx *ctx, double *h, double *t0, int32_t *M1, int32_t *M2, double *w, double *lam,
                   double *S);
 

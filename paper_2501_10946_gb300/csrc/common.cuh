@@ -39,15 +39,32 @@ struct __align__(16) Rec64 {
 //   F(r)    = sum_m a_m E_m,                    a_m = h w_m f(t_m, 0)
 //   F_N2(r) = sum_m c_m E_m,                    c_m = -2 b_m a_m
 //   F_N1(r) = exp(-r/lambda)(1 + r/lambda)/r^3
+// The Yukawa part is sum_i y_i exp(-r/lambda_i)/r over one term (y_1 = 1, the Yukawa
+// kernel) or two (the EGS screening, y_1 > 0 > y_2); F_N1 and Y carry the same weights,
+// and the Gaussians a_m, c_m already include their term's weight.
 struct NearConsts {
     int mtot;
-    double inv_lam;
+    double inv_lam;                    // 1/lambda_1
     double rc2;
     double a[kMaxGauss], b[kMaxGauss], c[kMaxGauss];
-    float inv_lam_log2e_f;             // log2(e)/lambda
+    float inv_lam_log2e_f;             // log2(e)/lambda_1
     float inv_lam_f;
     float rc2_f;
     float af[kMaxGauss], bl2f[kMaxGauss], cf[kMaxGauss];   // bl2f = b_m log2(e)
+    double y1;                         // weight of the first term (1 for the Yukawa kernel)
+    float ly1_f;                       // log2(y1): the FP32 path folds the weight into exp
+    int two;                           // 1: a second Yukawa term
+    double y2, inv_lam2;               // its weight and 1/lambda_2
+    float ly2_f, sgn2_f;               // log2|y2| and the sign of y2
+    float inv_lam2_log2e_f, inv_lam2_f;
+};
+
+// Yukawa terms of the interaction in Fourier space: 4 pi psi(k), psi(k) = sum_i c_i /
+// (k^2 + lambda_i^-2); one term of weight 1 (Yukawa kernel) or two (EGS screening).
+struct Yterms {
+    int n;
+    double c[2];
+    double inv_lam2[2];
 };
 
 struct Box {

@@ -79,8 +79,11 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 // two pairs at once.
 struct NearF {
     int mtot;
+    int two;                                // a second Yukawa term (EGS screening)
     unsigned long long nl2;                 // -log2(e)/lambda
     unsigned long long il2;                 // 1/lambda
+    unsigned long long ly1;                 // log2 of the first term's weight
+    unsigned long long nl2b, il2b, ly2, sg2;   // second term: -log2(e)/lambda_2, 1/lambda_2, log2|y2|, sign
     unsigned long long nb[kMaxGauss];       // -b_m log2(e)
     unsigned long long af[kMaxGauss];       // a_m
     unsigned long long cf[kMaxGauss];       // c_m
@@ -116,9 +119,21 @@ __device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long 
         fn2 = fma2(nc.cf[g], E, fn2);
     }
     const unsigned long long rinv3 = mul2(mul2(rinv, rinv), rinv);
-    const unsigned long long fn1 = mul2(mul2(e1, fma2(r, nc.il2, dup2(1.f))), rinv3);
-    gsc = mul2(qq, add2(fn1, fn2));
-    uh = mul2(mul2(dup2(0.5f), qq), fma2(e1, rinv, fsog ^ 0x8000000080000000ull));
+    if (!nc.two) {
+        const unsigned long long fn1 = mul2(mul2(e1, fma2(r, nc.il2, dup2(1.f))), rinv3);
+        gsc = mul2(qq, add2(fn1, fn2));
+        uh = mul2(mul2(dup2(0.5f), qq), fma2(e1, rinv, fsog ^ 0x8000000080000000ull));
+    } else {
+        // two Yukawa terms (EGS): weights folded into the exponents, the second's sign apart
+        upk2(fma2(r, nc.nl2, nc.ly1), xa, xb);
+        const unsigned long long ew = pk2(ex2_approx(xa), ex2_approx(xb));
+        upk2(fma2(r, nc.nl2b, nc.ly2), xa, xb);
+        const unsigned long long e2 = mul2(pk2(ex2_approx(xa), ex2_approx(xb)), nc.sg2);
+        const unsigned long long fn1 = fma2(mul2(e2, fma2(r, nc.il2b, dup2(1.f))), rinv3,
+                                            mul2(mul2(ew, fma2(r, nc.il2, dup2(1.f))), rinv3));
+        gsc = mul2(qq, add2(fn1, fn2));
+        uh = mul2(mul2(dup2(0.5f), qq), fma2(ew, rinv, fma2(e2, rinv, fsog ^ 0x8000000080000000ull)));
+    }
 }
 
 // One FP32 pair: accumulate q_i q_j [F_N1 + F_N2](r) (r_i - r_j) and U_N/2 (compensated).
@@ -135,12 +150,25 @@ __device__ __forceinline__ void pair_f32(const C &nc, float qq, float d0, float 
         fsog = fmaf(nc.af[g], E, fsog);
         fn2 = fmaf(nc.cf[g], E, fn2);
     }
-    const float fn1 = e1 * (1.f + r * nc.inv_lam_f) * (rinv * rinv * rinv);
-    const float gsc = qq * (fn1 + fn2);
-    kahan_add(Fs[0], Fc[0], gsc * d0);
-    kahan_add(Fs[1], Fc[1], gsc * d1);
-    kahan_add(Fs[2], Fc[2], gsc * d2);
-    kahan_add(Us, Uc, 0.5f * qq * (e1 * rinv - fsog));
+    if (!nc.two) {
+        const float fn1 = e1 * (1.f + r * nc.inv_lam_f) * (rinv * rinv * rinv);
+        const float gsc = qq * (fn1 + fn2);
+        kahan_add(Fs[0], Fc[0], gsc * d0);
+        kahan_add(Fs[1], Fc[1], gsc * d1);
+        kahan_add(Fs[2], Fc[2], gsc * d2);
+        kahan_add(Us, Uc, 0.5f * qq * (e1 * rinv - fsog));
+    } else {
+        // two Yukawa terms (EGS): weights folded into the exponents, the second's sign apart
+        const float ew = ex2_approx(fmaf(-r, nc.inv_lam_log2e_f, nc.ly1_f));
+        const float e2 = nc.sgn2_f * ex2_approx(fmaf(-r, nc.inv_lam2_log2e_f, nc.ly2_f));
+        const float rinv3 = rinv * rinv * rinv;
+        const float fn1 = fmaf(e2 * (1.f + r * nc.inv_lam2_f), rinv3, ew * (1.f + r * nc.inv_lam_f) * rinv3);
+        const float gsc = qq * (fn1 + fn2);
+        kahan_add(Fs[0], Fc[0], gsc * d0);
+        kahan_add(Fs[1], Fc[1], gsc * d1);
+        kahan_add(Fs[2], Fc[2], gsc * d2);
+        kahan_add(Us, Uc, 0.5f * qq * fmaf(ew, rinv, fmaf(e2, rinv, -fsog)));
+    }
 }
 
 // Per-particle near field from global memory (FP32 records).
@@ -220,12 +248,19 @@ __device__ void near_one_f64(const NearArgs &a, uint32_t p, double *Fout, double
                             fn2 += a.nc.c[g] * E;
                         }
                         const double qq = ri.q * rj.q;
-                        const double fn1 = e1 * (1.0 + r * a.nc.inv_lam) * (rinv * rinv * rinv);
+                        double fn1 = e1 * (1.0 + r * a.nc.inv_lam) * (rinv * rinv * rinv);
+                        double yk = e1 * rinv;
+                        if (a.nc.two) {
+                            // two Yukawa terms (EGS) with weights y1, y2
+                            const double e2 = a.nc.y2 * exp(-r * a.nc.inv_lam2);
+                            fn1 = a.nc.y1 * fn1 + e2 * (1.0 + r * a.nc.inv_lam2) * (rinv * rinv * rinv);
+                            yk = a.nc.y1 * yk + e2 * rinv;
+                        }
                         const double gsc = qq * (fn1 + fn2);
                         F[0] += gsc * d[0];
                         F[1] += gsc * d[1];
                         F[2] += gsc * d[2];
-                        U += 0.5 * qq * (e1 * rinv - fsog);
+                        U += 0.5 * qq * (yk - fsog);
                     }
                 }
             }
@@ -336,8 +371,14 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     }
     if (tid == 0) {
         S.nf.mtot = a.nc.mtot;
+        S.nf.two = a.nc.two;
         S.nf.nl2 = dup2(-a.nc.inv_lam_log2e_f);
         S.nf.il2 = dup2(a.nc.inv_lam_f);
+        S.nf.ly1 = dup2(a.nc.ly1_f);
+        S.nf.nl2b = dup2(-a.nc.inv_lam2_log2e_f);
+        S.nf.il2b = dup2(a.nc.inv_lam2_f);
+        S.nf.ly2 = dup2(a.nc.ly2_f);
+        S.nf.sg2 = dup2(a.nc.sgn2_f);
     }
     for (int g = tid; g < a.nc.mtot; g += kTileThreads) {
         S.nf.nb[g] = dup2(-a.nc.bl2f[g]);

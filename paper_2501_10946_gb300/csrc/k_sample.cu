@@ -10,7 +10,10 @@
 //                         discrete Gaussian exp(-(2 pi n/L_a)^2 / (4 b_m)), or on axis a of
 //                         a k^2 component that Gaussian times (2 pi n/L_a)^2
 //   reject n = 0; for calF of Eq. 62 accept with probability calF(k)/sum q^2 (increasing
-//   in |k| with supremum sum q^2); the other measures accept every nonzero draw
+//   in |k| with supremum sum q^2); the other measures accept every nonzero draw.
+// For the EGS screening the mixture weights are |A_m| (the envelope of a transform that
+// may change sign), psi(k) of Eq. 62 is that of its two Yukawa terms, and coef carries
+// Fhat(k)/Fhat_env(k).
 // which yields i.i.d. draws from P(k).  Random words: Philox4x32-10, key = seed,
 // counter = (slot, 8 attempt + j, draw lo, draw hi): j = 0 Gaussian, 1..3 axes,
 // 4 acceptance.  An alias draw from words (x0..x3) takes index floor((x0 2^32 + x1)
@@ -24,6 +27,23 @@
 namespace rbsog {
 
 namespace {
+
+// psi(k) = sum_i c_i / (k^2 + lambda_i^-2) of the kernel's Yukawa terms
+__device__ __forceinline__ double psi_of(const Yterms &y, double k2) {
+    double p = y.c[0] / (k2 + y.inv_lam2[0]);
+    if (y.n > 1) p += y.c[1] / (k2 + y.inv_lam2[1]);
+    return p;
+}
+
+// calF of the measure (Eq. 62 and its variants) at k^2; A = k_B T V.  One Yukawa term of
+// weight 1 keeps the form s / (k^2 + lambda^-2).
+__device__ __forceinline__ double calF_of(int measure, double k2, double A, double Q2, const Yterms &y) {
+    if (measure == 1) return 1.0;
+    if (measure == 2) return k2;
+    const double s = measure == 3 ? 4.0 * CUDART_PI : 1.0;
+    const double t = y.n == 1 ? s / (k2 + y.inv_lam2[0]) : s * psi_of(y, k2);
+    return A / (A / Q2 + t);
+}
 
 // keep index i when u53(z, w) < prob_i, i.e. when its 53-bit integer is below the
 // precomputed threshold ceil(prob_i 2^53)
@@ -66,9 +86,10 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
                 double ky = __dmul_rn(a.tpl[1], (double)n[1]);
                 double kz = __dmul_rn(a.tpl[2], (double)n[2]);
                 double k2 = __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
-                // u < A / (A + Q2/t), t = k^2 + lambda^-2, evaluated without division as
-                // u (A t + Q2) < A t
-                const double At = __dmul_rn(a.A, __dadd_rn(k2, a.inv_lam2));
+                // u < A / (A + Q2 psi), evaluated without division as u (A t + Q2) < A t
+                // with t = 1/psi = k^2 + lambda^-2 for one Yukawa term
+                const double At = a.y.n == 1 ? __dmul_rn(a.A, __dadd_rn(k2, a.y.inv_lam2[0]))
+                                             : __ddiv_rn(a.A, psi_of(a.y, k2));
                 ok = __dmul_rn(u, __dadd_rn(At, a.Q2a)) < At;
             }
             const unsigned acc = __ballot_sync(0xffffffffu, ok);
@@ -83,15 +104,22 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
     }
     if (lane == 0) {
         a.m_out[3 * l] = m[0]; a.m_out[3 * l + 1] = m[1]; a.m_out[3 * l + 2] = m[2];
-        // coef = S / (P V calF(k)) (Eqs. 60, 62), calF of the measure
+        // coef = S / (P V calF(k)) (Eqs. 60, 62), calF of the measure; with a far-field
+        // transform that may change sign, times Fhat(k) / Fhat_env(k) (draws from the envelope)
         double kx = a.tpl[0] * m[0], ky = a.tpl[1] * m[1], kz = a.tpl[2] * m[2];
         double k2 = kx * kx + ky * ky + kz * kz;
-        const double calF =
-            a.measure == 1 ? 1.0
-                           : (a.measure == 2 ? k2
-                                             : a.A / (a.A / a.Q2 + (a.measure == 3 ? 4.0 * CUDART_PI : 1.0) /
-                                                                       (k2 + a.inv_lam2)));
-        a.coef_out[l] = a.S / ((double)a.P * a.V * calF);
+        const double calF = calF_of(a.measure, k2, a.A, a.Q2, a.y);
+        double coef = a.S / ((double)a.P * a.V * calF);
+        if (a.nfh > 0) {
+            double fh = 0.0, fe = 0.0;
+            for (int g = 0; g < a.nfh; ++g) {
+                const double e = a.fA[g] * exp(-k2 * a.finv4b[g]);
+                fh += e;
+                fe += fabs(e);
+            }
+            coef = coef * (fh / fe);
+        }
+        a.coef_out[l] = coef;
     }
 }
 
@@ -130,12 +158,7 @@ __global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
         if (k2 > a.kmax2) continue;
         double fh = 0.0;
         for (int g = 0; g < a.mtot; ++g) fh += a.A[g] * exp(-k2 * a.inv4b[g]);
-        const double calF =
-            a.measure == 1 ? 1.0
-                           : (a.measure == 2 ? k2
-                                             : a.kTV / (a.kTV / a.Q2 + (a.measure == 3 ? 4.0 * CUDART_PI : 1.0) /
-                                                                           (k2 + a.inv_lam2)));
-        acc += calF * fh;
+        acc += calF_of(a.measure, k2, a.kTV, a.Q2, a.y) * fh;
     }
     sh[threadIdx.x] = acc;
     __syncthreads();

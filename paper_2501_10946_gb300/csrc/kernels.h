@@ -65,8 +65,12 @@ struct SampleArgs {
     double tpl[3];            // 2 pi / L
     double A;                 // k_B T V
     double Q2;                // sum q^2
-    double inv_lam2;
+    Yterms y;                 // psi(k) of the adaptive correction (Eq. 62 with the kernel's transform)
     double S, V;
+    // signed far-field transform when it may change sign (EGS): the modes come from the
+    // envelope sum |fA_m| exp(-k^2 finv4b_m) and coef carries Fhat / Fhat_env; nfh = 0 otherwise
+    int nfh;
+    double fA[kMaxGauss], finv4b[kMaxGauss];
     int measure;              // RBSOG_SAMPLING_*: calF of Eq. (62), 1, k^2, Eq. (62) with 4 pi
     double Q2a;               // sum q^2 in the acceptance ratio (4 pi sum q^2 for the Debye form)
     DevCounters *ctr;
@@ -81,7 +85,8 @@ struct SArgs {
     double tpl[3];
     double kmax2;
     int nmax[3];
-    double kTV, Q2, inv_lam2;
+    double kTV, Q2;
+    Yterms y;
     int measure;
 };
 void launch_S(const SArgs &a, double *partials, cudaStream_t st);   // partials[2*nmax[0]+1]

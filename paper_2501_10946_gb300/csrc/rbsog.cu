@@ -35,7 +35,8 @@ struct rbsog_ctx {
     double lam = 0, kT = 0, a_ws = 0, V = 0, Q2 = 0, qsum = 0, S = 0, Ufar0 = 0, Uself = 0, Fhat0 = 0;
     Box box{};
     NearConsts nconsts{};
-    std::vector<double> sA, sb;   // Fhat coefficients A_m and b_m = e^{t_m}
+    std::vector<double> sA, sb;   // Fhat coefficients A_m (signed, with the term weights) and b_m
+    Yterms y{};                   // the kernel's Yukawa terms
     // device buffers
     State rest{}, work{};
     double *q_user = nullptr, *m_user = nullptr;
@@ -139,9 +140,40 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
     h.lam = h.a_ws / p.kappa;
     h.kT = p.kT > 0 ? p.kT : 1.0 / (h.a_ws * p.Gamma);
     if (!(h.kT > 0) || !std::isfinite(h.kT)) return bad(RBSOG_EINVAL, "k_B T must be > 0 (Gamma > 0 or kT > 0)");
-    if (!build_sog(h.lam, p.r_c, p.sog_eps, p.sog_mode, p.sog_M1, p.sog_M2, &h.sog, err)) return RBSOG_ENOCONV;
-    const int mt = h.sog.mtot();
+    // Yukawa terms: the kernel itself, or the two of the EGS screening (Sec. 1), whose
+    // transform 4 pi / (k^2 eps(k)) splits by partial fractions as 4 pi [B / (k^2 + beta) +
+    // A / (k^2 + alpha)], alpha, beta = 2 (1 +- s) / (nu lambda^2), s = sqrt(1 - nu),
+    // B = (1 + s) / (2 s), A = -(1 - s) / (2 s); each term has its own SOG decomposition
+    const double nu = p.egs_nu;
+    if (!(nu >= 0.0 && nu <= 0.96)) return bad(RBSOG_EINVAL, "egs_nu must be in [0, 0.96]");
+    if (nu > 0.0 && p.sog_mode == RBSOG_SOG_TABLE)
+        return bad(RBSOG_EINVAL, "the EGS screening takes sog_mode MINIMAL or BOUND");
+    int nterms = 1;
+    double yc[2] = {1.0, 0.0}, ylam[2] = {h.lam, h.lam};
+    if (nu > 0.0) {
+        const double s = std::sqrt(1.0 - nu);
+        const double beta = 2.0 * (1.0 - s) / (nu * h.lam * h.lam);
+        const double alpha = 2.0 * (1.0 + s) / (nu * h.lam * h.lam);
+        yc[0] = (1.0 + s) / (2.0 * s);
+        ylam[0] = 1.0 / std::sqrt(beta);
+        yc[1] = -(1.0 - s) / (2.0 * s);
+        ylam[1] = 1.0 / std::sqrt(alpha);
+        nterms = 2;
+    }
+    SogDecomp sogs[2];
+    int mt = 0;
+    for (int k = 0; k < nterms; ++k) {
+        if (!build_sog(ylam[k], p.r_c, p.sog_eps, p.sog_mode, p.sog_M1, p.sog_M2, &sogs[k], err))
+            return RBSOG_ENOCONV;
+        mt += sogs[k].mtot();
+    }
+    h.sog = sogs[0];
     if (mt > kMaxGauss) return bad(RBSOG_EUNSUPPORTED, "more than 40 Gaussians");
+    h.y.n = nterms;
+    for (int k = 0; k < 2; ++k) {
+        h.y.c[k] = yc[k];
+        h.y.inv_lam2[k] = 1.0 / (ylam[k] * ylam[k]);
+    }
     h.Q2 = 0.0;
     h.qsum = 0.0;
     for (int64_t i = 0; i < N; ++i) {
@@ -170,33 +202,45 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
     const double log2e = 1.4426950408889634;
     NearConsts &nc = h.nconsts;
     nc.mtot = mt;
-    nc.inv_lam = 1.0 / h.lam;
+    nc.inv_lam = 1.0 / ylam[0];
     nc.rc2 = p.r_c * p.r_c;
-    nc.inv_lam_log2e_f = (float)(log2e / h.lam);
-    nc.inv_lam_f = (float)(1.0 / h.lam);
+    nc.inv_lam_log2e_f = (float)(log2e / ylam[0]);
+    nc.inv_lam_f = (float)(1.0 / ylam[0]);
     nc.rc2_f = (float)nc.rc2;
+    nc.y1 = yc[0];
+    nc.ly1_f = (float)std::log2(yc[0]);
+    nc.two = nterms > 1 ? 1 : 0;
+    nc.y2 = yc[1];
+    nc.inv_lam2 = 1.0 / ylam[1];
+    nc.ly2_f = nterms > 1 ? (float)std::log2(std::fabs(yc[1])) : 0.f;
+    nc.sgn2_f = yc[1] < 0.0 ? -1.f : 1.f;
+    nc.inv_lam2_log2e_f = (float)(log2e / ylam[1]);
+    nc.inv_lam2_f = (float)(1.0 / ylam[1]);
     h.Fhat0 = 0.0;
     h.sA.clear();
     h.sb.clear();
     double F0 = 0.0;
-    for (int i = 0; i < mt; ++i) {
-        const int m = -h.sog.M1 + i;
-        const double t = h.sog.t0 + m * h.sog.h;
-        const double w = (m == h.sog.M2) ? h.sog.w : 1.0;
-        const double b = std::exp(t);
-        const double f0 = sog_f(t, 0.0, h.lam);
-        const double a = h.sog.h * w * f0;
-        nc.a[i] = a;
-        nc.b[i] = b;
-        nc.c[i] = -2.0 * b * a;
-        nc.af[i] = (float)a;
-        nc.bl2f[i] = (float)(b * log2e);
-        nc.cf[i] = (float)(-2.0 * b * a);
-        const double A = h.sog.h * w * std::pow(kPi, 1.5) * f0 * std::exp(-1.5 * t);
-        h.sA.push_back(A);
-        h.sb.push_back(b);
-        h.Fhat0 += A;
-        F0 += a;
+    int gi = 0;
+    for (int k = 0; k < nterms; ++k) {
+        const SogDecomp &sg = sogs[k];
+        for (int m = -sg.M1; m <= sg.M2; ++m, ++gi) {
+            const double t = sg.t0 + m * sg.h;
+            const double w = (m == sg.M2) ? sg.w : 1.0;
+            const double b = std::exp(t);
+            const double f0 = sog_f(t, 0.0, ylam[k]);
+            const double a = yc[k] * (sg.h * w * f0);     // the term's weight times Eq. (37)'s
+            nc.a[gi] = a;
+            nc.b[gi] = b;
+            nc.c[gi] = -2.0 * b * a;
+            nc.af[gi] = (float)a;
+            nc.bl2f[gi] = (float)(b * log2e);
+            nc.cf[gi] = (float)(-2.0 * b * a);
+            const double A = yc[k] * (sg.h * w * std::pow(kPi, 1.5) * f0 * std::exp(-1.5 * t));
+            h.sA.push_back(A);
+            h.sb.push_back(b);
+            h.Fhat0 += A;
+            F0 += a;
+        }
     }
     h.Uself = -0.5 * h.Q2 * F0;
     h.Ufar0 = h.Fhat0 * h.qsum * h.qsum / (2.0 * h.V);
@@ -242,7 +286,7 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
         }
         if (p.sampling == RBSOG_SAMPLING_K2) {
             for (int a = 0; a < 3; ++a) {
-                double w = h.sA[i] * sigma[a];
+                double w = std::fabs(h.sA[i]) * sigma[a];
                 for (int c = 0; c < 3; ++c) {
                     if (c != a) w = w * theta[c];
                     h.ax_off.push_back(c == a ? off_sq[c] : off_plain[c]);
@@ -255,7 +299,7 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
                 h.ax_off.push_back(off_plain[c]);
                 h.ax_nmax.push_back(nmax[c]);
             }
-            mixw.push_back(h.sA[i] * ((theta[0] * theta[1]) * theta[2]));
+            mixw.push_back(std::fabs(h.sA[i]) * ((theta[0] * theta[1]) * theta[2]));
         }
     }
     vose(mixw, &h.mix_prob, &h.mix_alias);
@@ -265,10 +309,10 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
 int system_S(HostSystem *hs, std::string *err) {
     HostSystem &h = *hs;
     SArgs a{};
-    a.mtot = h.sog.mtot();
+    a.mtot = (int)h.sA.size();
     double bmax = 0.0;
     for (int i = 0; i < a.mtot; ++i) {
-        a.A[i] = h.sA[i];
+        a.A[i] = std::fabs(h.sA[i]);     // the envelope of the far field's transform
         a.inv4b[i] = 1.0 / (4.0 * h.sb[i]);
         if (h.sb[i] > bmax) bmax = h.sb[i];
     }
@@ -279,7 +323,7 @@ int system_S(HostSystem *hs, std::string *err) {
     }
     a.kTV = h.kT * h.V;
     a.Q2 = h.Q2;
-    a.inv_lam2 = 1.0 / (h.lam * h.lam);
+    a.y = h.y;
     a.measure = h.p.sampling;
     const int nb = 2 * a.nmax[0] + 1;
     double *parts = nullptr;
@@ -414,7 +458,8 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     SampleArgs sa{};
     sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
     for (int d = 0; d < 3; ++d) sa.tpl[d] = c->box.tpl[d];
-    sa.A = c->kT * c->V; sa.Q2 = c->Q2; sa.inv_lam2 = 1.0 / (c->lam * c->lam); sa.S = c->S; sa.V = c->V;
+    sa.A = c->kT * c->V; sa.Q2 = c->Q2; sa.y = c->y; sa.S = c->S; sa.V = c->V;
+    fill_signed_fhat(c->y, c->sA, c->sb, &sa);
     sa.measure = c->p.sampling;
     sa.Q2a = c->p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * kPi) * c->Q2 : c->Q2;
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
@@ -509,7 +554,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
     c->N = (uint32_t)N;
     c->prec = p.precision;
     c->V = hs.V; c->a_ws = hs.a_ws; c->lam = hs.lam; c->kT = hs.kT; c->Q2 = hs.Q2; c->qsum = hs.qsum;
-    c->sog = hs.sog; c->box = hs.box; c->nconsts = hs.nconsts; c->sA = hs.sA; c->sb = hs.sb;
+    c->sog = hs.sog; c->box = hs.box; c->nconsts = hs.nconsts; c->sA = hs.sA; c->sb = hs.sb; c->y = hs.y;
     c->Fhat0 = hs.Fhat0; c->Uself = hs.Uself; c->Ufar0 = hs.Ufar0;
     const Box &bx = c->box;
 
@@ -737,7 +782,7 @@ int rbsog_get_sog(rbsog_ctx *c, double *h, double *t0, int32_t *M1, int32_t *M2,
     if (M1) *M1 = c->sog.M1;
     if (M2) *M2 = c->sog.M2;
     if (w) *w = c->sog.w;
-    if (lam) *lam = c->lam;
+    if (lam) *lam = c->sog.lam;
     if (S) *S = c->S;
     return RBSOG_OK;
 }

@@ -159,7 +159,8 @@ int build_args(rbsog_batch *b) {
             for (int d = 0; d < 3; ++d) a.tpl[d] = h.box.tpl[d];
             a.A = h.kT * h.V;
             a.Q2 = h.Q2;
-            a.inv_lam2 = 1.0 / (h.lam * h.lam);
+            a.y = h.y;
+            fill_signed_fhat(h.y, h.sA, h.sb, &a);
             a.S = h.S;
             a.V = h.V;
             a.measure = h.p.sampling;

@@ -20,6 +20,7 @@ struct HostSystem {
     SogDecomp sog;
     Box box{};
     NearConsts nconsts{};
+    Yterms y{};                          // the kernel's Yukawa terms (one, or two for EGS)
     std::vector<double> sA, sb;          // Fhat(k) = sum_m A_m exp(-k^2 / (4 b_m)), b_m = e^{t_m}
     // sampling tables (alias tables of the Gaussian mixture and of each axis)
     std::vector<double> mix_prob, ax_prob;
@@ -39,6 +40,18 @@ inline std::vector<unsigned long long> alias_thresholds(const std::vector<double
 
 int setup_system(const rbsog_params &p, int64_t N, const double *q, const double *m, HostSystem *hs,
                  std::string *err);
+
+// The sampler's signed far-field transform: with two Yukawa terms (EGS) Fhat may change
+// sign, so coef carries Fhat / Fhat_env; with one term it is positive and nfh = 0.
+template <class Args>
+inline void fill_signed_fhat(const Yterms &y, const std::vector<double> &sA, const std::vector<double> &sb,
+                             Args *a) {
+    a->nfh = y.n > 1 ? (int)sA.size() : 0;
+    for (int i = 0; i < a->nfh; ++i) {
+        a->fA[i] = sA[i];
+        a->finv4b[i] = 1.0 / (4.0 * sb[i]);
+    }
+}
 // S = sum_{k != 0} calF(k) Fhat(k) by a device lattice sum (synchronous).
 int system_S(HostSystem *hs, std::string *err);
 

@@ -28,7 +28,8 @@ class rbsog_params(C.Structure):
                 ("kT", C.c_double), ("r_c", C.c_double), ("sog_eps", C.c_double), ("dt", C.c_double),
                 ("langevin_gamma", C.c_double), ("seed", C.c_uint64), ("P", C.c_int32),
                 ("precision", C.c_int32), ("ensemble", C.c_int32), ("sog_mode", C.c_int32),
-                ("sog_M1", C.c_int32), ("sog_M2", C.c_int32), ("device", C.c_int32), ("sampling", C.c_int32)]
+                ("sog_M1", C.c_int32), ("sog_M2", C.c_int32), ("device", C.c_int32), ("sampling", C.c_int32),
+                ("egs_nu", C.c_double)]
 
 
 class rbsog_energy(C.Structure):
@@ -470,7 +471,7 @@ def rbsog_server_free(s):
 def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int | None = None,
                 sog_mode: int = RBSOG_SOG_MINIMAL, M1: int = 0, M2: int = 0, device: int = 0,
                 ensemble: int | None = None, dt: float | None = None,
-                sampling: int = RBSOG_SAMPLING_ADAPTIVE) -> rbsog_params:
+                sampling: int = RBSOG_SAMPLING_ADAPTIVE, egs_nu: float = 0.0) -> rbsog_params:
     """rbsog_params from a workloads.Workload (plain field copy)."""
     p = rbsog_params()
     for d in range(3):
@@ -493,4 +494,5 @@ def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int 
     p.sog_M1, p.sog_M2 = int(M1), int(M2)
     p.device = int(device)
     p.sampling = int(sampling)
+    p.egs_nu = float(egs_nu)
     return p

@@ -56,13 +56,23 @@ def base_params():
 
 @pytest.mark.parametrize("field,value", [("r_c", 6.0), ("P", 0), ("P", 5000), ("kappa", 0.0), ("precision", 7),
                                          ("ensemble", 3), ("sog_mode", 9), ("sampling", 4), ("sampling", -1),
-                                         ("dt", -1.0)])
+                                         ("dt", -1.0), ("egs_nu", -0.1), ("egs_nu", 0.97)])
 def test_invalid_parameters_are_rejected_on_the_host(field, value):
     w, p = base_params()
     setattr(p, field, value)
     with pytest.raises(R.RbsogError, match="EINVAL"):
         R.rbsog_init(p, w.N, W.charges(w), W.masses(w))
     assert R.rbsog_last_error(None)
+
+
+def test_egs_screening_rejects_a_table_of_one_kernel():
+    """The EGS screening builds one SOG per Yukawa term, so a given (M1, M2) is refused."""
+    w, p = base_params()
+    p.egs_nu = 0.5
+    p.sog_mode = R.RBSOG_SOG_TABLE
+    p.sog_M1, p.sog_M2 = 4, 0
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_init(p, w.N, W.charges(w), W.masses(w))
 
 
 def test_invalid_sizes_are_rejected():
