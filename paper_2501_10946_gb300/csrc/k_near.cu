@@ -723,7 +723,9 @@ __global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int 
 // Batched systems: block -> (system, local block); each system uses tiles or the
 // per-particle path as its geometry says.  geom.W doubles as the first global record
 // index of the system for the per-particle path.
-__global__ void __launch_bounds__(kTileThreads, 6) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
+// 7 blocks per SM (the batch's staging buffer leaves room for 7; a small register spill)
+// measured faster than 6 on the 256-system sweep
+__global__ void __launch_bounds__(kTileThreads, 7) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
                                                             const uint32_t *items, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int lo = 0, hi = R - 1;
