@@ -48,6 +48,24 @@ def test_egs_forces_and_energies_match_the_oracle(prec, tol, kind):
         assert abs(eg[key] - ref) <= 10 * tol * abs(ref), key
 
 
+@pytest.mark.parametrize("prec,tol", [(R.RBSOG_FP64, FP64_TOL), (R.RBSOG_FP32, FP32_TOL)], ids=["fp64", "fp32"])
+def test_egs_small_box_per_particle_path(prec, tol):
+    """Fewer than 3 cells per axis: the per-particle near path with both Yukawa terms."""
+    w = workload(200, 4.0, kappa=1.0, Gamma=1.0, rc=1.9, P=64, seed=91)
+    r, q = W.positions(w), W.charges(w)
+    modes = modes_for(w, w.P, 92)
+    e = oracle_egs(w, nu=0.8)
+    with Ctx(w, prec, egs_nu=0.8) as c:
+        assert R.rbsog_get_cells(c.h, w.N)[0].tolist() == [1, 1, 1]
+        R.rbsog_set_state(c.h, r)
+        R.rbsog_set_ksample(c.h, modes)
+        F = np.zeros((w.N, 3))
+        eg = R.rbsog_forces(c.h, F, energy=True)
+    Ft, _, _, eo, _ = egs.rb_forces(r, q, w.box, e, modes, w.kT, cells=False)
+    assert core.rel_l2(F, Ft) <= tol
+    assert abs(eg["U_near"] - eo["U_N"]) <= 10 * tol * abs(eo["U_N"])
+
+
 def test_egs_sampled_coefficients_match_the_oracle():
     """Modes drawn by the GPU sampler from the envelope: their coefficients are the oracle's
     S_env Fhat / (P V calF Fhat_env), including modes where Fhat < 0."""
