@@ -38,7 +38,7 @@ struct rbsog_batch {
     std::vector<rbsog::HostSystem> sys;
     std::vector<uint32_t> p_off{0}, c_off{0}, m_off{0};   // R + 1 entries
     std::vector<int> rho_chunk;                          // particles per structure-factor block
-    double near_target = 110.0;                          // particles per near-field CTA
+    double near_target = 96.0;                           // particles per near-field CTA
     int rho_target = 512;
     bool dirty = true;                                   // arguments need rebuilding
     bool force_valid = false;                            // batch API: forces of the state evaluated

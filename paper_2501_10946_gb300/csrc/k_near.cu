@@ -35,7 +35,6 @@ namespace {
 constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
 constexpr int kSlots = 8;              // candidate slots (32 candidates each) per filter round
-constexpr int kMaxTileW = 48;
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -271,17 +270,19 @@ __device__ void near_one_f64(const NearArgs &a, uint32_t p, double *Fout, double
     Uout = U;
 }
 
-// Energy partials are per warp (4 per block, fixed order), so no block-wide barrier waits
-// for the slowest thread at the end of a kernel.
+// Energy partials are per warp (blockDim.x / 32 per block, fixed order), so no block-wide
+// barrier waits for the slowest thread at the end of a kernel.  The single-system kernels
+// run 128 threads per block.
 constexpr int kWarpsPerBlock = 4;
+static_assert(kGlobalThreads == 32 * kWarpsPerBlock && kTileThreads == kGlobalThreads, "single-system block size");
 
 __device__ __forceinline__ void warp_partial(double v, double *U_part, unsigned blk) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) U_part[(size_t)blk * kWarpsPerBlock + (threadIdx.x >> 5)] = v;
+    if ((threadIdx.x & 31) == 0) U_part[(size_t)blk * (blockDim.x >> 5) + (threadIdx.x >> 5)] = v;
 }
 
-// One block of the per-particle path: particles p0 + [0, 128) of this system (global
+// One block of the per-particle path: particles p0 + [0, blockDim.x) of this system (global
 // record indices p0 .. p0 + N - 1).
 template <int PREC>
 __device__ __forceinline__ void near_global_block(const NearArgs &a, uint32_t p0, unsigned blk) {
@@ -311,16 +312,16 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
 }
 
 // ---------------------------------------------------------------- tiled (TMA) FP32 path
-// CAP: staged particles per CTA (16 B each).  One large system stages 1280; batches of
-// many systems stage 1024.
-template <int CAP>
+// CAP: staged particles per CTA (16 B each); NT: threads per CTA.  One large system
+// stages 1280 with 128 threads; batches of many (mostly small) systems stage 1024 with 96.
+template <int CAP, int NT, int MW>
 struct TileSmem {
     uint4 stage[CAP];                       // staged records
-    uint32_t mask[kSlots][kTileThreads];    // per target (column = owning thread): hit bits of a round
+    uint32_t mask[kSlots][NT];    // per target (column = owning thread): hit bits of a round
     uint16_t flat[3 * CAP];                 // per target cell: staging indices of its 27-cell candidates
-    int fb[kMaxTileW + 2];                  // target cell i: candidates flat[fb[i] .. fb[i+1])
+    int fb[MW + 2];                         // target cell i: candidates flat[fb[i] .. fb[i+1])
     NearF nf;                               // the system's FP32 pair constants
-    int seg_off[9][kMaxTileW + 3];          // per row: offset of each region cell within the row
+    int seg_off[9][MW + 3];                 // per row: offset of each region cell within the row
     int row_base[10];                       // per row: offset of the row in the staging buffer
     uint32_t chunk_g[9][2];                 // per row: global start of up to two slices
     uint32_t chunk_n[9][2];                 // per row: particle count of each slice
@@ -331,8 +332,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 
 // Region cell (1 .. wn-2) of the centre row holding staged target jl (offset within row 4):
 // the last i with seg_off[4][i] <= jl.
-template <int CAP>
-__device__ __forceinline__ int region_cell(const TileSmem<CAP> &S, int wn, int jl) {
+template <int CAP, int NT, int MW>
+__device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW> &S, int wn, int jl) {
     int lo = 1, hi = wn - 2;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -342,9 +343,9 @@ __device__ __forceinline__ int region_cell(const TileSmem<CAP> &S, int wn, int j
     return lo;
 }
 
-template <int CAP>
+template <int CAP, int NT, int MW>
 __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
-                                               TileSmem<CAP> &S) {
+                                               TileSmem<CAP, NT, MW> &S) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
     const unsigned full = 0xffffffffu;
@@ -361,7 +362,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
 
     // cell populations of the 9 x wn region cells, loaded in parallel (row r: dz = r/3 - 1,
     // dy = r%3 - 1)
-    for (int e = tid; e < 9 * wn; e += kTileThreads) {
+    for (int e = tid; e < 9 * wn; e += NT) {
         const int r = e / wn, i = e - r * wn;
         const int yr = (cy + r % 3 - 1 + ny) % ny, zr = (cz + r / 3 - 1 + nz) % nz;
         int x = x0 - 1 + i;
@@ -380,7 +381,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         S.nf.ly2 = dup2(a.nc.ly2_f);
         S.nf.sg2 = dup2(a.nc.sgn2_f);
     }
-    for (int g = tid; g < a.nc.mtot; g += kTileThreads) {
+    for (int g = tid; g < a.nc.mtot; g += NT) {
         S.nf.nb[g] = dup2(-a.nc.bl2f[g]);
         S.nf.af[g] = dup2(a.nc.af[g]);
         S.nf.cf[g] = dup2(a.nc.cf[g]);
@@ -478,7 +479,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             __syncthreads();
             // while the copies fly: the candidate list of each target cell i, rows 0..8 in
             // order, each row's cells i-1 .. i+1 in staging order
-            for (int e = tid; e < 9 * ntc; e += kTileThreads) {
+            for (int e = tid; e < 9 * ntc; e += NT) {
                 const int i = e / 9 + 1, r = e - (e / 9) * 9;
                 int pos = S.fb[i];
                 for (int q = 0; q < r; ++q) pos += S.seg_off[q][i + 2] - S.seg_off[q][i - 1];
@@ -527,7 +528,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             const float cwx = 4294967296.f / (float)nx;
             const uint32_t oy = __float2uint_rz(((float)cy + 0.5f) * (4294967296.f / (float)ny));
             const uint32_t oz = __float2uint_rz(((float)cz + 0.5f) * (4294967296.f / (float)nz));
-            for (int wlo = t0 + 32 * wid; wlo < t1; wlo += kTileThreads) {
+            for (int wlo = t0 + 32 * wid; wlo < t1; wlo += NT) {
                 const int whi = min(wlo + 32, t1);
                 const int j = wlo + lane;
                 const bool has = j < whi;
@@ -704,7 +705,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     } else {
         // neighbourhood larger than the staging buffer (or an overflowing cell): global path
         float *Fn = (float *)a.Fn;
-        for (uint32_t g = g_first + tid; g < g_end; g += kTileThreads) {
+        for (uint32_t g = g_first + tid; g < g_end; g += NT) {
             float F[3] = {0.f, 0.f, 0.f};
             double U = 0.0;
             if (!overflow) near_one_f32(a, g, F, U);
@@ -717,15 +718,16 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
 
 __global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_tile_body<kNearCapSingle>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle> *>(smem_raw));
+    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle> *>(smem_raw));
 }
 
 // Batched systems: block -> (system, local block); each system uses tiles or the
 // per-particle path as its geometry says.  geom.W doubles as the first global record
 // index of the system for the per-particle path.
-// 7 blocks per SM (the batch's staging buffer leaves room for 7; a small register spill)
-// measured faster than 6 on the 256-system sweep
-__global__ void __launch_bounds__(kTileThreads, 7) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
+// Small systems make tiles of few targets (a 1024-particle buffer holds tiles of about
+// 60 to 100), so the batch runs three-warp CTAs: each warp has targets of its own, where
+// four-warp CTAs left one or two idle.  7 CTAs per SM, with a small register spill.
+__global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
                                                             const uint32_t *items, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int lo = 0, hi = R - 1;
@@ -738,7 +740,7 @@ __global__ void __launch_bounds__(kTileThreads, 7) k_near_batch(const NearArgs *
     const NearBatchGeom g = geom[lo];
     const unsigned blk = blockIdx.x - items[lo];
     if (g.tiled)
-        near_tile_body<kNearCapBatch>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch> *>(smem_raw));
+        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch> *>(smem_raw));
     else near_global_block<1>(a, (uint32_t)g.W, blk);
 }
 
@@ -747,7 +749,7 @@ inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 
 }  // namespace
 
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks, double target,
-                   int cap) {
+                   int cap, int threads, int max_w) {
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
     if (nx >= 3 && ny >= 3 && nz >= 3) {
         // tile width: about `target` (default 110) targets per CTA and about 1000 staged
@@ -757,7 +759,7 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
         int Wt = (int)(target / (occ > 1e-9 ? occ : 1e-9));
         int Wcap = (int)(0.78 * cap / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
         if (Wt > Wcap) Wt = Wcap;
-        if (Wt > kMaxTileW) Wt = kMaxTileW;
+        if (Wt > max_w) Wt = max_w;
         if (Wt > nx - 2) Wt = nx - 2;
         if (Wt < 1) Wt = 1;
         *tiles_x = (nx + Wt - 1) / Wt;
@@ -768,7 +770,7 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
         *tiled = 0;
         *W = 0;
         *tiles_x = 0;
-        *nblocks = blocks_for(N, kGlobalThreads);
+        *nblocks = blocks_for(N, (unsigned)threads);
     }
 }
 
@@ -776,9 +778,9 @@ static void set_tile_smem_attr() {
     static bool done = false;
     if (!done) {
         cudaFuncSetAttribute(k_near_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(TileSmem<kNearCapSingle>));
+                             (int)sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle>));
         cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(TileSmem<kNearCapBatch>));
+                             (int)sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch>));
         done = true;
     }
 }
@@ -789,7 +791,7 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     near_geometry(a.box, a.N, &tiled, &W, &tiles_x, &nb);
     if (prec == 1 && tiled) {
         set_tile_smem_attr();
-        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem<kNearCapSingle>), st>>>(a, W, tiles_x);
+        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle>), st>>>(a, W, tiles_x);
         return (int)nb * kWarpsPerBlock;
     }
     nb = blocks_for(a.N, kGlobalThreads);
@@ -801,7 +803,7 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
 void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
                        uint32_t nblocks, cudaStream_t st) {
     set_tile_smem_attr();
-    k_near_batch<<<nblocks, kTileThreads, sizeof(TileSmem<kNearCapBatch>), st>>>(args, geom, items, R);
+    k_near_batch<<<nblocks, kNearBatchThreads, sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch>), st>>>(args, geom, items, R);
 }
 
 }  // namespace rbsog

@@ -174,10 +174,18 @@ struct NearBatchGeom {
 };
 // Staged particles per near-field CTA: one large system, and the batched kernel.
 constexpr int kNearCapSingle = 1280;
+constexpr int kNearMaxWSingle = 48;      // widest tile in cells
 constexpr int kNearCapBatch = 1024;
-// target: particles per CTA the tile width aims at (capped by the staging buffer `cap`)
+constexpr int kNearBatchThreads = 96;     // threads per CTA of the batched near kernel
+constexpr int kNearBatchMinBlocks = 7;    // its CTAs per SM (the staging buffer fits 7)
+constexpr int kNearBatchWarps = kNearBatchThreads / 32;   // energy partials per CTA
+constexpr int kNearMaxWBatch = 16;
+// target: particles per CTA the tile width aims at (capped by the staging buffer `cap`);
+// threads: threads per CTA of the per-particle path (boxes under 3 cells per axis);
+// max_w: widest tile in cells
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks,
-                   double target = 110.0, int cap = kNearCapSingle);
+                   double target = 110.0, int cap = kNearCapSingle, int threads = 128,
+                   int max_w = kNearMaxWSingle);
 void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
                        uint32_t nblocks, cudaStream_t st);
 void launch_rho_batch(const RhoArgs *args, const int *chunk, const uint32_t *items, int R, uint32_t nblocks,

@@ -90,7 +90,8 @@ struct SysShape {
 
 SysShape shape_of(const HostSystem &h, double near_target, int chunk) {
     SysShape s{};
-    near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target, kNearCapBatch);
+    near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target, kNearCapBatch,
+                  kNearBatchThreads, kNearMaxWBatch);
     s.G = (int)((h.N + (uint32_t)chunk - 1) / (uint32_t)chunk);
     return s;
 }
@@ -225,7 +226,7 @@ int build_args(rbsog_batch *b) {
             a.ctr = ctr;
             EnergyArgs &e = en[k][r];
             e.U_part = b->U_part + u_off;
-            e.nU = 4 * (int)sh.near_blocks;
+            e.nU = kNearBatchWarps * (int)sh.near_blocks;
             e.K_part = b->K_part + k_off;
             e.nK = (int)nbf;
             e.Ufar = b->Ufar + mo;
@@ -244,7 +245,7 @@ int build_args(rbsog_batch *b) {
             it[j] += cnt[j];
         }
         part_off += (size_t)sh.G * 8 * P;
-        u_off += 4 * (size_t)sh.near_blocks;
+        u_off += kNearBatchWarps * (size_t)sh.near_blocks;
         k_off += nbf;
     }
     b->h_items.assign(R + 1, 0u);
@@ -422,7 +423,7 @@ size_t engine_footprint(const rbsog_batch *b, const HostSystem &h) {
                                 + 16 + 3 * 4 + 8;    // record, cell/slot/perm, sort key
     const size_t per_mode = 3 * 4 * 2 + 8 + 16 + kGTab32Bytes + 8;
     return (size_t)h.N * per_particle + (size_t)h.box.ncell * 12 + (size_t)h.p.P * per_mode +
-           (size_t)sh.G * 8 * h.p.P * 16 + 4 * (size_t)sh.near_blocks * 8 + far_batch_blocks(h.N) * 8;
+           (size_t)sh.G * 8 * h.p.P * 16 + kNearBatchWarps * (size_t)sh.near_blocks * 8 + far_batch_blocks(h.N) * 8;
 }
 
 bool engine_fits(const rbsog_batch *b, const HostSystem &h) {
@@ -539,7 +540,7 @@ int engine_commit(rbsog_batch *b) {
         const HostSystem &h = b->sys[r];
         const SysShape sh = shape_of(h, b->near_target, b->rho_chunk[r]);
         part += (size_t)sh.G * 8 * (size_t)h.p.P;
-        upart += 4 * (size_t)sh.near_blocks;
+        upart += kNearBatchWarps * (size_t)sh.near_blocks;
         kpart += far_batch_blocks(h.N);
     }
     BCK(regrow(b, &b->partial, &b->cap_part, part), "alloc partials");
@@ -884,7 +885,7 @@ int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t 
     BCK(cudaStreamSynchronize(st), "synchronize");
     std::vector<DevCounters> saved;
     if (int code = engine_counters(b, &saved)) return code;
-    const double near_c[] = {48.0, 80.0, 110.0, 160.0};
+    const double near_c[] = {48.0, 64.0, 96.0, 128.0};
     const int rho_c[] = {256, 512, 1024, 2048};
     double best_near = b->near_target, best_near_ms = 1e30;
     int best_rho = b->rho_target;
