@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int 
 // index of the system for the per-particle path.
 // Small systems make tiles of few targets (a 1024-particle buffer holds tiles of about
 // 60 to 100), so the batch runs three-warp CTAs: each warp has targets of its own, where
-// four-warp CTAs left one or two idle.  7 CTAs per SM, with a small register spill.
+// four-warp CTAs left one or two idle.  8 CTAs per SM (80 registers, a small spill).
 __global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
                                                             const uint32_t *items, int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -177,7 +177,7 @@ constexpr int kNearCapSingle = 1280;
 constexpr int kNearMaxWSingle = 48;      // widest tile in cells
 constexpr int kNearCapBatch = 1024;
 constexpr int kNearBatchThreads = 96;     // threads per CTA of the batched near kernel
-constexpr int kNearBatchMinBlocks = 7;    // its CTAs per SM (the staging buffer fits 7)
+constexpr int kNearBatchMinBlocks = 7;    // launch bound: CTAs per SM (80 registers; 8 fit)
 constexpr int kNearBatchWarps = kNearBatchThreads / 32;   // energy partials per CTA
 constexpr int kNearMaxWBatch = 16;
 // target: particles per CTA the tile width aims at (capped by the staging buffer `cap`);
