@@ -48,6 +48,63 @@ __device__ __forceinline__ double wrap_near(double r, double L, double invL) {
     return w;
 }
 
+// IEEE 754 conversions on the integer pipe.  On this part the FP64 unit (1/64 of the FP32
+// rate) also executes the float <-> double and double -> integer conversion
+// instructions, so the FP32 build's integrator, which would otherwise spend most of its
+// time there, assembles the results from the fields of the formats instead.  Each
+// function returns exactly what the conversion instruction returns; the rare operands
+// outside the handled range (subnormal, infinite, NaN) take the instruction itself.
+
+// float -> double (exact): sign, exponent rebiased from 127 to 1023, fraction widened.
+__device__ __forceinline__ double f2d_int(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 0xffu;
+    if (e - 1u < 254u) {                                     // normal
+        const uint32_t hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b >> 3) & 0xfffffu);
+        return __hiloint2double((int)hi, (int)(b << 29));
+    }
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)b, 0);   // +-0
+    return (double)x;
+}
+
+// double -> float, round to nearest even: keep 23 of the 52 fraction bits and round on
+// the 29 dropped ones; a carry out of the fraction moves into the exponent, which is the
+// correctly rounded result (up to the largest finite float and beyond it to infinity).
+__device__ __forceinline__ float d2f_int(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t E = (hi >> 20) & 0x7ffu;
+    if (E - 897u < 254u) {                                   // a normal float before rounding
+        const uint32_t mant = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t rest = lo & 0x1fffffffu;
+        uint32_t v = ((E - 896u) << 23) | mant;
+        v += (rest > 0x10000000u || (rest == 0x10000000u && (mant & 1u))) ? 1u : 0u;
+        return __uint_as_float((hi & 0x80000000u) | v);
+    }
+    if ((hi & 0x7fffffffu) == 0u && lo == 0u) return __uint_as_float(hi);   // +-0
+    return __double2float_rn(x);
+}
+
+// The low 32 bits of the truncation of x in [0, 2^33) (what the 64-bit unsigned
+// round-toward-zero conversion gives there): 1.f x 2^e shifted down by 52 - e.
+__device__ __forceinline__ uint32_t trunc_lo32(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t E = hi >> 20;                            // sign bit included: x >= 0 here
+    if (E < 1023u) return 0u;                                // [0, 1), +0
+    if (E > 1055u) return (uint32_t)__double2ull_rz(x);      // 2^33 and above, inf, NaN, x < 0
+    const unsigned long long m = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+    return (uint32_t)(m >> (52u - (E - 1023u)));
+}
+
+// Langevin noise words of particle `id`: Philox key = seed, counter = (id, 0x40000000 + j, n),
+// n = force evaluations (k-draws) so far.  Setting a state does not reset n, so a loop
+// that uploads the state before every step still draws fresh noise.
+__device__ __forceinline__ void noise_words(const BinArgs &a, uint32_t id, U4 &w0, U4 &w1) {
+    const unsigned long long n = a.ctr->draw;
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    w0 = philox10(id, 0x40000000u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
+    w1 = philox10(id, 0x40000001u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
+}
+
 template <int PREC>
 __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
     const uint32_t N = a.stride;
@@ -57,15 +114,47 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
     const uint32_t id = a.in.id[k];
     // a system whose forces were never evaluated (fvalid = 0) only rebuilds its cells
     const int integrate = a.ctr->fvalid ? a.integrate : 0;
-    if (integrate) {
-        double F[3];
-        if (PREC == 1) {
-            const float *Ff = (const float *)a.F;
-            F[0] = Ff[k]; F[1] = Ff[N + k]; F[2] = Ff[2 * (size_t)N + k];
+    if (PREC == 1 && integrate) {
+        // FP32 build: kick, drift increments and the O step in FP32 (the forces carry FP32
+        // errors already); the positions add those increments in FP64.
+        const float *Ff = (const float *)a.F;
+        const float im = d2f_int(invm);
+        float vf[3] = {d2f_int(v[0]), d2f_int(v[1]), d2f_int(v[2])};
+        const float hk = a.hdt_f * im;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) vf[d] = fmaf(hk, Ff[(size_t)d * N + k], vf[d]);
+        float dr[3];
+        if (integrate == 1) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) dr[d] = a.dt_f * vf[d];
         } else {
-            const double *Fd = (const double *)a.F;
-            F[0] = Fd[k]; F[1] = Fd[N + k]; F[2] = Fd[2 * (size_t)N + k];
+            // B A O A of BAOAB; Box-Muller pairs from the 24 leading bits of the noise words
+            // (FP64 transcendentals would cost more than the rest of this kernel)
+            U4 w0, w1;
+            noise_words(a, id, w0, w1);
+            const float u1 = (float)(w0.x >> 8) * 5.9604645e-08f, u2 = (float)(w0.z >> 8) * 5.9604645e-08f;
+            const float u3 = (float)(w1.x >> 8) * 5.9604645e-08f, u4 = (float)(w1.z >> 8) * 5.9604645e-08f;
+            const float rad = sqrtf(-2.0f * logf(1.0f - u1)), rad3 = sqrtf(-2.0f * logf(1.0f - u3));
+            float s2, c2;
+            sincospif(2.0f * u2, &s2, &c2);
+            const float xi[3] = {rad * c2, rad * s2, rad3 * cospif(2.0f * u4)};
+            const float sig = sqrtf(a.okT_f * im);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const float d1 = a.hdt_f * vf[d];
+                vf[d] = fmaf(a.c1_f, vf[d], sig * xi[d]);
+                dr[d] = fmaf(a.hdt_f, vf[d], d1);
+            }
         }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            r[d] = __dadd_rn(r[d], f2d_int(dr[d]));
+            v[d] = f2d_int(vf[d]);
+        }
+    } else if (integrate) {
+        // FP64 build
+        const double *Fd = (const double *)a.F;
+        const double F[3] = {Fd[k], Fd[N + k], Fd[2 * (size_t)N + k]};
         const double hk = 0.5 * a.dt * invm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) v[d] += hk * F[d];
@@ -73,35 +162,19 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) r[d] += a.dt * v[d];
         } else {
-            // B A O A of BAOAB; noise: Philox key = seed, counter = (id, 0x40000000 + j, n),
-            // n = force evaluations (k-draws) so far.  Setting a state does not reset n, so a
-            // loop that uploads the state before every step still draws fresh noise.
-            const unsigned long long n = a.ctr->draw;
-            const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-            U4 w0 = philox10(id, 0x40000000u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
-            U4 w1 = philox10(id, 0x40000001u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
+            // B A O A of BAOAB
+            U4 w0, w1;
+            noise_words(a, id, w0, w1);
             double xi[3];
-            if (PREC == 1) {
-                // FP32 build: the same Box-Muller pairs from the 24 leading bits of the words
-                // (FP64 transcendentals would cost more than the rest of this kernel)
-                const float u1 = (float)(w0.x >> 8) * 5.9604645e-08f, u2 = (float)(w0.z >> 8) * 5.9604645e-08f;
-                const float u3 = (float)(w1.x >> 8) * 5.9604645e-08f, u4 = (float)(w1.z >> 8) * 5.9604645e-08f;
-                const float rad = sqrtf(-2.0f * logf(1.0f - u1)), rad3 = sqrtf(-2.0f * logf(1.0f - u3));
-                float s2, c2;
-                sincospif(2.0f * u2, &s2, &c2);
-                xi[0] = rad * c2; xi[1] = rad * s2; xi[2] = rad3 * cospif(2.0f * u4);
-            } else {
-                double u1 = u53_of(w0.x, w0.y), u2 = u53_of(w0.z, w0.w);
-                double rad = sqrt(-2.0 * log(1.0 - u1));
-                double s2, c2;
-                sincospi(2.0 * u2, &s2, &c2);
-                double u3 = u53_of(w1.x, w1.y), u4 = u53_of(w1.z, w1.w);
-                double rad3 = sqrt(-2.0 * log(1.0 - u3));
-                xi[0] = rad * c2; xi[1] = rad * s2; xi[2] = rad3 * cospi(2.0 * u4);
-            }
-            // noise amplitude sqrt((1 - c1^2) kT / m); FP32 suffices for the FP32 build
-            const double sig = PREC == 1 ? (double)sqrtf((float)(a.okT * invm))
-                                         : sqrt((1.0 - a.c1 * a.c1) * a.kT * invm);
+            double u1 = u53_of(w0.x, w0.y), u2 = u53_of(w0.z, w0.w);
+            double rad = sqrt(-2.0 * log(1.0 - u1));
+            double s2, c2;
+            sincospi(2.0 * u2, &s2, &c2);
+            double u3 = u53_of(w1.x, w1.y), u4 = u53_of(w1.z, w1.w);
+            double rad3 = sqrt(-2.0 * log(1.0 - u3));
+            xi[0] = rad * c2; xi[1] = rad * s2; xi[2] = rad3 * cospi(2.0 * u4);
+            // noise amplitude sqrt((1 - c1^2) kT / m)
+            const double sig = sqrt((1.0 - a.c1 * a.c1) * a.kT * invm);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 r[d] += 0.5 * a.dt * v[d];
@@ -120,7 +193,7 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
         uint32_t s32;
         if (PREC == 1) {
             // u = 1 gives 2^32, whose low 32 bits are 0
-            s32 = (uint32_t)__double2ull_rz(__dmul_rn(r[d], a.box.invL32[d]));
+            s32 = trunc_lo32(__dmul_rn(r[d], a.box.invL32[d]));
             ((uint32_t *)a.s)[(size_t)d * N + k] = s32;
         } else {
             const double u = __dmul_rn(r[d], a.box.invL[d]);

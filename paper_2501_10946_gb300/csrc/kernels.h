@@ -13,6 +13,7 @@ struct BinArgs {
     int integrate;            // 0 none, 1 velocity Verlet (kick + drift), 2 BAOAB (B A O A)
     double dt, c1, kT;
     double okT;               // (1 - c1^2) k_B T: the FP32 build's noise variance per unit 1/m
+    float dt_f, hdt_f, c1_f, okT_f;   // dt, dt/2, c1, okT rounded to FP32 (set_bin_floats)
     unsigned long long seed;
     DevCounters *ctr;
     uint32_t N;               // particles of this system
@@ -22,6 +23,13 @@ struct BinArgs {
     void *s;                  // fixed point [3][stride]: uint32 (FP32) or uint64 (FP64)
     uint32_t *cell, *slot, *count;
 };
+// Fills the FP32 copies of dt, dt/2, c1 and okT from the doubles.
+inline void set_bin_floats(BinArgs &a) {
+    a.dt_f = (float)a.dt;
+    a.hdt_f = (float)(0.5 * a.dt);
+    a.c1_f = (float)a.c1;
+    a.okT_f = (float)a.okT;
+}
 void launch_bin(int prec, const BinArgs &a, cudaStream_t st);
 void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int ncell, uint32_t N,
                  cudaStream_t st);

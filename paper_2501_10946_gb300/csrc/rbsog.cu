@@ -443,6 +443,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     b.in = c->rest; b.out = c->work; b.F = c->F; b.integrate = integrate;
     b.dt = c->p.dt; b.c1 = std::exp(-c->p.langevin_gamma * c->p.dt); b.kT = c->kT; b.seed = c->p.seed;
     b.okT = (1.0 - b.c1 * b.c1) * b.kT;
+    set_bin_floats(b);
     b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.s = c->s; b.cell = c->cell;
     b.slot = c->slot; b.count = c->count;
     { ProfScope ps(c, st, 0); launch_bin(prec, b, st); }

@@ -137,6 +137,7 @@ int build_args(rbsog_batch *b) {
             a.c1 = std::exp(-p.langevin_gamma * p.dt);
             a.kT = h.kT;
             a.okT = (1.0 - a.c1 * a.c1) * a.kT;
+            set_bin_floats(a);
             a.seed = p.seed;
             a.ctr = ctr;
             a.N = N;
