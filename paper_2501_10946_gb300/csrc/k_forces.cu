@@ -532,20 +532,45 @@ __device__ __forceinline__ void energy_body(const EnergyArgs &a, double *sh) {
     }
 }
 
+// Sum over the warps of a 256-thread block of three values at once, in a fixed order
+// (shuffle tree in each warp, then warp 0 over the 8 warp sums); one barrier.
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double (*sh)[3]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) { sh[w][0] = a; sh[w][1] = b; sh[w][2] = c; }
+    __syncthreads();
+    if (w == 0) {
+        a = lane < 8 ? sh[lane][0] : 0.0;
+        b = lane < 8 ? sh[lane][1] : 0.0;
+        c = lane < 8 ? sh[lane][2] : 0.0;
+#pragma unroll
+        for (int o = 4; o; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+    }
+}
+
 // FP64 runs at 2 operations per clock per SM here, so one block summing ~5e4 partials
-// is FP64-bound; kEnergyBlocks blocks share the sums and the last one to arrive adds the
-// per-block results in block order (deterministic whichever block is last).
+// is FP64-bound; kEnergyBlocks (<= 32) blocks share the sums and the last one to arrive
+// combines the per-block results with a fixed shuffle tree over the block index
+// (deterministic whichever block is last).
 __global__ void __launch_bounds__(256) k_energy(EnergyArgs a) {
-    __shared__ double sh[256];
+    __shared__ double sh[8][3];
     __shared__ int last;
     const int E = gridDim.x, b = blockIdx.x;
     auto part = [&](const double *x, int n) {
         const int lo = (int)((long long)n * b / E), hi = (int)((long long)n * (b + 1) / E);
-        return block_reduce_sum<double>(strided_sum8(x + lo, hi - lo), sh);
+        return strided_sum8(x + lo, hi - lo);
     };
-    const double U = part(a.U_part, a.nU);
-    const double K = part(a.K_part, a.nK);
-    const double Uf = part(a.Ufar, a.nUfar);
+    double U = part(a.U_part, a.nU), K = part(a.K_part, a.nK), Uf = part(a.Ufar, a.nUfar);
+    block_sum3(U, K, Uf, sh);
     if (threadIdx.x == 0) {
         a.scratch[b] = U;
         a.scratch[E + b] = K;
@@ -554,24 +579,28 @@ __global__ void __launch_bounds__(256) k_energy(EnergyArgs a) {
         last = atomicAdd(a.done, 1u) == (unsigned)(E - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last && threadIdx.x < 32) {
         __threadfence();
         const volatile double *s = a.scratch;
-        double Us = 0.0, Ks = 0.0, Ufs = 0.0;
-        for (int i = 0; i < E; ++i) {
-            Us += s[i];
-            Ks += s[E + i];
-            Ufs += s[2 * E + i];
+        const int i = threadIdx.x;
+        double Us = i < E ? s[i] : 0.0, Ks = i < E ? s[E + i] : 0.0, Ufs = i < E ? s[2 * E + i] : 0.0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            Us += __shfl_xor_sync(0xffffffffu, Us, o);
+            Ks += __shfl_xor_sync(0xffffffffu, Ks, o);
+            Ufs += __shfl_xor_sync(0xffffffffu, Ufs, o);
         }
-        const double Ut = Ufs + a.Ufar0;
-        a.out[0] = Us;
-        a.out[1] = Ut;
-        a.out[2] = a.Uself;
-        a.out[3] = Ks;
-        a.out[4] = Us + Ut + a.Uself + Ks;
-        if (a.advance_step && a.ctr->fvalid) a.ctr->step += 1ull;
-        a.ctr->fvalid = 1;
-        *a.done = 0u;
+        if (i == 0) {
+            const double Ut = Ufs + a.Ufar0;
+            a.out[0] = Us;
+            a.out[1] = Ut;
+            a.out[2] = a.Uself;
+            a.out[3] = Ks;
+            a.out[4] = Us + Ut + a.Uself + Ks;
+            if (a.advance_step && a.ctr->fvalid) a.ctr->step += 1ull;
+            a.ctr->fvalid = 1;
+            *a.done = 0u;
+        }
     }
 }
 
@@ -624,6 +653,7 @@ int launch_far(int prec, const FarArgs &a, cudaStream_t st) {
     return (int)nb;
 }
 
+static_assert(kEnergyBlocks <= 32, "k_energy combines the block sums in one warp");
 void launch_energy(const EnergyArgs &a, cudaStream_t st) { k_energy<<<kEnergyBlocks, 256, 0, st>>>(a); }
 
 uint32_t rho_batch_blocks(int G, int P) { return (uint32_t)G * (uint32_t)((P + 255) / 256); }

@@ -36,6 +36,13 @@ constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
 constexpr int kSlots = 8;              // candidate slots (32 candidates each) per filter round
 
+// rsqrt and ex2 with subnormals flushed: a pair's r^2 and the exponents are never
+// subnormal, and the flushing forms skip the subnormal handling of the plain ones
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -104,7 +111,7 @@ __device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long 
                                             unsigned long long &gsc, unsigned long long &uh) {
     float r2a, r2b;
     upk2(r2, r2a, r2b);
-    const unsigned long long rinv = pk2(rsqrtf(r2a), rsqrtf(r2b));
+    const unsigned long long rinv = pk2(rsqrt_ftz(r2a), rsqrt_ftz(r2b));
     const unsigned long long r = mul2(r2, rinv);
     float xa, xb;
     upk2(mul2(r, nc.nl2), xa, xb);
@@ -140,7 +147,7 @@ __device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long 
 template <class C>
 __device__ __forceinline__ void pair_f32(const C &nc, float qq, float d0, float d1, float d2, float r2,
                                          float *Fs, float *Fc, float &Us, float &Uc) {
-    const float rinv = rsqrtf(r2);
+    const float rinv = rsqrt_ftz(r2);
     const float r = r2 * rinv;
     const float e1 = ex2_approx(-r * nc.inv_lam_log2e_f);
     float fsog = 0.f, fn2 = 0.f;
