@@ -34,7 +34,7 @@ METRIC = "RBSOG particle-steps/s at N=1e6"
 SMS = 152
 MUFU_PER_CLK_SM = 16            # sin/cos special-function results per clock per SM (measured 15.9)
 FP32_PER_CLK_SM = 128           # FP32 lanes per SM
-KERNELS_PER_STEP = 12
+KERNELS_PER_STEP = 11
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed
 # full-set ncu capture at N = 1e6 of kernels unchanged since (profiles/near_rho_far_yocp_uniform_n1e6.md);
 # a kernel changed after its capture has no entry

@@ -50,8 +50,7 @@ struct rbsog_batch {
     float *F = nullptr, *Fn = nullptr;                   // SoA [3][capN]
     uint32_t *s = nullptr;                               // SoA [3][capN]
     uint4 *rec = nullptr;
-    uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr,
-             *perm_src = nullptr;
+    uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr;
     unsigned long long *keys = nullptr;
     int *modes = nullptr, *inject_m = nullptr;
     double *coef = nullptr, *Ufar = nullptr, *energy = nullptr;

@@ -7,9 +7,9 @@
 //   k_tile_sums    per 4096-cell tile population
 //   k_scan_tiles   exclusive scan -> cell_start; clears the counts for the next build
 //   k_scatter      key = (particle id, previous position) at cell_start + slot
-//   k_sort_cells   each cell's keys ascending by particle id (the order the atomics
-//                  produced is discarded, so the result is deterministic)
-//   k_gather       state and 16/32-byte particle records into the new cell order
+//   k_gather       each key's rank among its cell's keys (by particle id) gives its place:
+//                  the order the atomics produced is discarded, so the result is
+//                  deterministic; state and 16/32-byte particle records move there
 #include "common.cuh"
 #include "kernels.h"
 #include "philox.cuh"
@@ -322,35 +322,28 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t *cell, const uin
     keys[cell_start[cell[k]] + slot[k]] = ((unsigned long long)id[k] << 32) | (unsigned long long)k;
 }
 
-__global__ void __launch_bounds__(256) k_sort_cells(const uint32_t *cell_start, int ncell, unsigned long long *keys,
-                                                    uint32_t *perm_src, DevCounters *ctr, const uint32_t *c_off,
-                                                    int R) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const uint32_t lo = cell_start[c], hi = cell_start[c + 1];
-    if (hi - lo > (uint32_t)kMaxCellOcc) {
-        int r = 0;
-        if (c_off) r = item_system(c_off, R, (uint32_t)c);
-        atomicOr(&ctr[r].err, kErrCellOverflow);
-    } else {
-        for (uint32_t i = lo + 1; i < hi; ++i) {
-            unsigned long long key = keys[i];
-            uint32_t j = i;
-            while (j > lo && keys[j - 1] > key) {
-                keys[j] = keys[j - 1];
-                --j;
-            }
-            keys[j] = key;
-        }
-    }
-    for (uint32_t i = lo; i < hi; ++i) perm_src[i] = (uint32_t)keys[i];
-}
-
+// Thread i takes the key at scattered position i of its cell [lo, hi) and moves particle
+// src = low word of the key to lo + (number of the cell's keys below it).  Ids are unique,
+// so the ranks of a cell are a permutation of 0 .. n-1: particles in ascending id order,
+// as a stable sort by id would leave them.  A cell above kMaxCellOcc keeps the scatter
+// order and sets kErrCellOverflow (in the counter of the system that owns the cell when
+// c_off is given).
 template <int PREC>
 __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
-    uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= g.N) return;
-    const uint32_t src = g.perm_src[p];
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const unsigned long long key = g.keys[i];
+    const uint32_t src = (uint32_t)key;
+    const uint32_t c = g.cell[src];
+    const uint32_t lo = g.cell_start[c], hi = g.cell_start[c + 1];
+    uint32_t p = i;
+    if (hi - lo <= (uint32_t)kMaxCellOcc) {
+        p = lo;
+        for (uint32_t j = lo; j < hi; ++j) p += g.keys[j] < key ? 1u : 0u;
+    } else if (i == lo) {
+        const int r = g.c_off ? item_system(g.c_off, g.R, c) : 0;
+        atomicOr(&g.ctr[r].err, kErrCellOverflow);
+    }
     const uint32_t N = g.stride;
     g.out.rx[p] = g.in.rx[src]; g.out.ry[p] = g.in.ry[src]; g.out.rz[p] = g.in.rz[src];
     g.out.vx[p] = g.in.vx[src]; g.out.vy[p] = g.in.vy[src]; g.out.vz[p] = g.in.vz[src];
@@ -488,11 +481,9 @@ void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int
     k_scan_tiles<<<tiles, 1024, 0, st>>>(count, ncell, tile_sums, cell_start, N);
 }
 
-void launch_scatter_sort(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
-                         uint32_t N, int ncell, unsigned long long *keys, uint32_t *perm_src, DevCounters *ctr,
-                         cudaStream_t st, const uint32_t *c_off, int R) {
+void launch_scatter(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
+                    uint32_t N, unsigned long long *keys, cudaStream_t st) {
     k_scatter<<<blocks_for(N, 256), 256, 0, st>>>(cell, slot, cell_start, id, N, keys);
-    k_sort_cells<<<blocks_for((uint32_t)ncell, 256), 256, 0, st>>>(cell_start, ncell, keys, perm_src, ctr, c_off, R);
 }
 
 void launch_relayout(State from, State to, const float *F_from, float *F_to, uint32_t stride,

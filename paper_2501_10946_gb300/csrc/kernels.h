@@ -33,19 +33,26 @@ inline void set_bin_floats(BinArgs &a) {
 void launch_bin(int prec, const BinArgs &a, cudaStream_t st);
 void launch_scan(uint32_t *count, uint32_t *tile_sums, uint32_t *cell_start, int ncell, uint32_t N,
                  cudaStream_t st);
-// A cell over the occupancy limit sets kErrCellOverflow in ctr[0], or, with c_off (R + 1
-// first cells of R systems), in the counter of the system that owns the cell.
-void launch_scatter_sort(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
-                         uint32_t N, int ncell, unsigned long long *keys, uint32_t *perm_src, DevCounters *ctr,
-                         cudaStream_t st, const uint32_t *c_off = nullptr, int R = 1);
+// keys[cell_start[cell[k]] + slot[k]] = (id[k] << 32) | k: each cell's keys, in the order
+// the atomics gave the slots
+void launch_scatter(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start, const uint32_t *id,
+                    uint32_t N, unsigned long long *keys, cudaStream_t st);
 // Move R systems to a new particle layout: system r's particles old_off[r] + i (rest
 // state and forces F, SoA stride `stride`) go to new_off[r] + i of `to` and F_to.
 void launch_relayout(State from, State to, const float *F_from, float *F_to, uint32_t stride,
                      const uint32_t *old_off, const uint32_t *new_off, int R, uint32_t Nnew, cudaStream_t st);
+// The cell of each key orders it by particle id (rank among the cell's keys); a cell over
+// the occupancy limit sets kErrCellOverflow in ctr[0], or, with c_off (R + 1 first cells
+// of R systems), in the counter of the system that owns the cell.
 struct GatherArgs {
     State in;                 // work buffer
     State out;                // rest buffer (new cell-sorted order)
-    const uint32_t *perm_src;
+    const unsigned long long *keys;   // launch_scatter's output
+    const uint32_t *cell;     // cell of each work-order particle
+    const uint32_t *cell_start;
+    DevCounters *ctr;
+    const uint32_t *c_off;    // nullptr for one system
+    int R;
     const void *s;            // fixed point of the work order, SoA [3][stride]
     void *rec;                // uint4 (FP32) or Rec64 (FP64) records in the new order
     uint32_t N;

@@ -42,8 +42,7 @@ struct rbsog_ctx {
     double *q_user = nullptr, *m_user = nullptr;
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;
     void *F = nullptr, *Fn = nullptr, *s = nullptr, *rec = nullptr;
-    uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr,
-             *perm_src = nullptr;
+    uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr;
     unsigned long long *keys = nullptr;
     unsigned long long *mix_thr = nullptr, *ax_thr = nullptr;
     int *mix_alias = nullptr, *ax_off = nullptr, *ax_nmax = nullptr, *ax_alias = nullptr;
@@ -450,11 +449,11 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     { ProfScope ps(c, st, 1); launch_scan(c->count, c->tile_sums, c->cell_start, c->box.ncell, N, st); }
     {
         ProfScope ps(c, st, 2);
-        launch_scatter_sort(c->cell, c->slot, c->cell_start, c->work.id, N, c->box.ncell, c->keys, c->perm_src,
-                            c->ctr, st);
+        launch_scatter(c->cell, c->slot, c->cell_start, c->work.id, N, c->keys, st);
     }
     GatherArgs g{};
-    g.in = c->work; g.out = c->rest; g.perm_src = c->perm_src; g.s = c->s; g.rec = c->rec; g.N = N; g.stride = N;
+    g.in = c->work; g.out = c->rest; g.keys = c->keys; g.cell = c->cell; g.cell_start = c->cell_start; g.ctr = c->ctr;
+    g.c_off = nullptr; g.R = 1; g.s = c->s; g.rec = c->rec; g.N = N; g.stride = N;
     { ProfScope ps(c, st, 3); launch_gather(prec, g, st); }
     SampleArgs sa{};
     sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
@@ -590,7 +589,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         dalloc(c, &Fnb, n3 * real) || dalloc(c, &sb, n3 * real) || dalloc(c, &recb, n * 4 * real) ||
         dalloc(c, &c->cell, n) || dalloc(c, &c->slot, n) || dalloc(c, &c->count, (size_t)bx.ncell) ||
         dalloc(c, &c->tile_sums, (size_t)ntiles) || dalloc(c, &c->cell_start, (size_t)bx.ncell + 1) ||
-        dalloc(c, &c->perm_src, n) || dalloc(c, &c->keys, n) || dalloc(c, &c->modes, 3 * (size_t)p.P) ||
+        dalloc(c, &c->keys, n) || dalloc(c, &c->modes, 3 * (size_t)p.P) ||
         dalloc(c, &c->inject_m, 3 * (size_t)p.P) || dalloc(c, &c->coef, (size_t)p.P) ||
         dalloc(c, &c->partial, (size_t)c->G * 8 * p.P) || dalloc(c, &c->rho, (size_t)p.P) ||
         dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, (size_t)p.P) ||

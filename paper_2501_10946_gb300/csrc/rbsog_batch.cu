@@ -380,7 +380,7 @@ int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
         balloc(b, &b->d_state_sub, R) || balloc(b, &b->F, n3) || balloc(b, &b->Fn, n3) ||
         balloc(b, &b->s, n3) || balloc(b, &b->rec, n) || balloc(b, &b->cell, n) || balloc(b, &b->slot, n) ||
         balloc(b, &b->count, C) || balloc(b, &b->tile_sums, ntiles) || balloc(b, &b->cell_start, C + 1) ||
-        balloc(b, &b->perm_src, n) || balloc(b, &b->keys, n) || balloc(b, &b->modes, 3 * P) ||
+        balloc(b, &b->keys, n) || balloc(b, &b->modes, 3 * P) ||
         balloc(b, &b->inject_m, 3 * P) || balloc(b, &b->coef, P) || balloc(b, &b->rho, P) ||
         balloc(b, &b->gtab, kGTab32Bytes * P) || balloc(b, &b->Ufar, P) || balloc(b, &b->energy, 5 * R) ||
         balloc(b, &b->ctr, R) || balloc(b, &b->d_bin[0], R) || balloc(b, &b->d_bin[1], R) ||
@@ -421,7 +421,7 @@ size_t engine_footprint(const rbsog_batch *b, const HostSystem &h) {
     const size_t per_particle = 2 * 9 * 8 - 2 * 4   // rest + work state (id is 4 bytes)
                                 + 2 * 3 * 8          // caller-order staging
                                 + 3 * 3 * 4          // F, Fn, fixed point
-                                + 16 + 3 * 4 + 8;    // record, cell/slot/perm, sort key
+                                + 16 + 2 * 4 + 8;    // record, cell/slot, sort key
     const size_t per_mode = 3 * 4 * 2 + 8 + 16 + kGTab32Bytes + 8;
     return (size_t)h.N * per_particle + (size_t)h.box.ncell * 12 + (size_t)h.p.P * per_mode +
            (size_t)sh.G * 8 * h.p.P * 16 + kNearBatchWarps * (size_t)sh.near_blocks * 8 + far_batch_blocks(h.N) * 8;
@@ -605,11 +605,11 @@ int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far,
     mark(1);
     launch_scan(b->count, b->tile_sums, b->cell_start, b->Ctot, b->Ntot, st);
     mark(2);
-    launch_scatter_sort(b->cell, b->slot, b->cell_start, b->work.id, b->Ntot, b->Ctot, b->keys, b->perm_src, b->ctr,
-                        st, b->d_coff, R);
+    launch_scatter(b->cell, b->slot, b->cell_start, b->work.id, b->Ntot, b->keys, st);
     mark(3);
     GatherArgs g{};
-    g.in = b->work; g.out = b->rest; g.perm_src = b->perm_src; g.s = b->s; g.rec = b->rec;
+    g.in = b->work; g.out = b->rest; g.keys = b->keys; g.cell = b->cell; g.cell_start = b->cell_start; g.ctr = b->ctr;
+    g.c_off = b->d_coff; g.R = R; g.s = b->s; g.rec = b->rec;
     g.N = b->Ntot; g.stride = b->capN;
     launch_gather(RBSOG_FP32, g, st);
     mark(4);
