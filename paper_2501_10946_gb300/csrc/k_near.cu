@@ -83,7 +83,7 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 // reads its systems' arguments from global memory, and the pair loop reads them per
 // Gaussian).  Each constant is stored twice in one 64-bit word, for packed arithmetic on
 // two pairs at once.
-struct NearF {
+struct alignas(16) NearF {
     int mtot;
     int two;                                // a second Yukawa term (EGS screening)
     unsigned long long nl2;                 // -log2(e)/lambda
@@ -117,7 +117,23 @@ __device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long 
     upk2(mul2(r, nc.nl2), xa, xb);
     const unsigned long long e1 = pk2(ex2_approx(xa), ex2_approx(xb));
     unsigned long long fsog = 0ull, fn2 = 0ull;
-    for (int g = 0; g < nc.mtot; ++g) {
+    // two Gaussians per iteration (16-byte loads of adjacent constants), same order of sums
+    int g = 0;
+    for (; g + 1 < nc.mtot; g += 2) {
+        const ulonglong2 nb = *reinterpret_cast<const ulonglong2 *>(&nc.nb[g]);
+        const ulonglong2 af = *reinterpret_cast<const ulonglong2 *>(&nc.af[g]);
+        const ulonglong2 cf = *reinterpret_cast<const ulonglong2 *>(&nc.cf[g]);
+        float ya, yb, za, zb;
+        upk2(mul2(r2, nb.x), ya, yb);
+        upk2(mul2(r2, nb.y), za, zb);
+        const unsigned long long E0 = pk2(ex2_approx(ya), ex2_approx(yb));
+        const unsigned long long E1 = pk2(ex2_approx(za), ex2_approx(zb));
+        fsog = fma2(af.x, E0, fsog);
+        fn2 = fma2(cf.x, E0, fn2);
+        fsog = fma2(af.y, E1, fsog);
+        fn2 = fma2(cf.y, E1, fn2);
+    }
+    if (g < nc.mtot) {
         float ya, yb;
         upk2(mul2(r2, nc.nb[g]), ya, yb);
         const unsigned long long E = pk2(ex2_approx(ya), ex2_approx(yb));
