@@ -366,7 +366,9 @@ __device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW> &S, int w
     return lo;
 }
 
-template <int CAP, int NT, int MW>
+// DOT selects the form of the pre-filter test (see the threshold below): the expanded
+// one takes fewer instructions, the direct one fewer registers.
+template <int CAP, int NT, int MW, bool DOT>
 __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
                                                TileSmem<CAP, NT, MW> &S) {
     const int tid = threadIdx.x;
@@ -538,12 +540,15 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             const int t1 = rb4 + S.seg_off[4][wn - 1];
             float *Fn = (float *)a.Fn;
             const float rc2 = a.nc.rc2_f;
-            // Pre-filter threshold.  An FP32 offset from the cell centre is within 1.8e-7 c of
-            // the exact one (|offset| <= 1.5 c, two roundings), so the pre-filter's r^2 is
-            // within 1.5e-6 r_c^2 of the exact r^2 near the cutoff (c < 4/3 r_c because
-            // n_c = floor(L / r_c) >= 3); a margin of 1e-5 keeps every pair that the exact
-            // test accepts.
-            const float rcf2 = rc2 * 1.00001f;
+            // Pre-filter threshold thr = r_c^2 (1 + 4e-5).  An FP32 offset from the cell
+            // centre is within 1.8e-7 c of the exact one (|offset| <= 1.5 c per axis, two
+            // roundings; c < 4/3 r_c because n_c = floor(L / r_c) >= 3).  Either form of the
+            // test then decides within 3.3e-6 r_c^2 of the exact comparison, roundings of the
+            // expanded form included, so every pair that the exact test accepts passes:
+            //   direct:   |t - c|^2 < thr
+            //   expanded: t.c - |c|^2/2 > (|t|^2 - thr)/2, with |c|^2/2 once per candidate
+            //             and the right side once per target: 3 FMAs per test instead of 6.
+            const float rcf2 = rc2 * 1.00004f;
             const float sx = a.box.L_2m32f[0], sy = a.box.L_2m32f[1], sz = a.box.L_2m32f[2];
             const unsigned long long sx2 = dup2(sx), sy2 = dup2(sy), sz2 = dup2(sz);
             // fixed-point centre of the target row (y, z) and cell width along x; any point
@@ -580,27 +585,32 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                         more = more || total > base + 32 * kSlots;
                         const int nsl = min(kSlots, (total - base + 31) >> 5);
                         const uint32_t ox = __float2uint_rz(((float)(x0 - 1 + i) + 0.5f) * cwx);
-                        float X[kSlots], Y[kSlots], Z[kSlots];
+                        // no candidate: far away (direct form) or never above the bound (expanded)
+                        float X[kSlots], Y[kSlots], Z[kSlots], H[kSlots];
 #pragma unroll
                         for (int s = 0; s < kSlots; ++s) {
-                            X[s] = 3e30f;
+                            X[s] = DOT ? 0.f : 3e30f;
                             Y[s] = 0.f;
                             Z[s] = 0.f;
+                            H[s] = -3e38f;
                             const int f = base + 32 * s + lane;
                             if (s < nsl && f < total) {
                                 const uint4 rk = S.stage[S.flat[cb + f]];
                                 X[s] = (float)(int)(rk.x - ox) * sx;
                                 Y[s] = (float)(int)(rk.y - oy) * sy;
                                 Z[s] = (float)(int)(rk.z - oz) * sz;
+                                if (DOT) H[s] = -0.5f * fmaf(X[s], X[s], fmaf(Y[s], Y[s], Z[s] * Z[s]));
                             }
                         }
-                        unsigned long long X2[kSlots / 2], Y2[kSlots / 2], Z2[kSlots / 2];
+                        unsigned long long X2[kSlots / 2], Y2[kSlots / 2], Z2[kSlots / 2], H2[kSlots / 2];
 #pragma unroll
                         for (int h = 0; h < kSlots / 2; ++h) {
                             X2[h] = pk2(X[2 * h], X[2 * h + 1]);
                             Y2[h] = pk2(Y[2 * h], Y[2 * h + 1]);
                             Z2[h] = pk2(Z[2 * h], Z[2 * h + 1]);
+                            if (DOT) H2[h] = pk2(H[2 * h], H[2 * h + 1]);
                         }
+
                         int t = ta;
                         for (; t + 1 < tb; t += 2) {
                             const uint4 pa = S.stage[t], pb = S.stage[t + 1];
@@ -610,26 +620,32 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                                         zb = (float)(int)(pb.z - oz) * sz;
                             const unsigned long long xa2 = pk2(xa, xa), ya2 = pk2(ya, ya), za2 = pk2(za, za);
                             const unsigned long long xb2 = pk2(xb, xb), yb2 = pk2(yb, yb), zb2 = pk2(zb, zb);
+                            // expanded: accept t.c - |c|^2/2 > k; direct: accept |t - c|^2 < k
+                            const float ka = DOT ? 0.5f * (fmaf(xa, xa, fmaf(ya, ya, za * za)) - rcf2) : rcf2;
+                            const float kb = DOT ? 0.5f * (fmaf(xb, xb, fmaf(yb, yb, zb * zb)) - rcf2) : rcf2;
                             const int col = 32 * wid + (t - wlo);
 #pragma unroll
                             for (int h = 0; h < kSlots / 2; ++h) {
                                 if (2 * h < nsl) {
-                                    const unsigned long long dxa = sub2(xa2, X2[h]), dya = sub2(ya2, Y2[h]), dza = sub2(za2, Z2[h]);
-                                    const unsigned long long dxb = sub2(xb2, X2[h]), dyb = sub2(yb2, Y2[h]), dzb = sub2(zb2, Z2[h]);
-                                    const unsigned long long r2a = fma2(dza, dza, fma2(dya, dya, mul2(dxa, dxa)));
-                                    const unsigned long long r2b = fma2(dzb, dzb, fma2(dyb, dyb, mul2(dxb, dxb)));
                                     float a0, a1, b0, b1;
-                                    upk2(r2a, a0, a1);
-                                    upk2(r2b, b0, b1);
-                                    const uint32_t ma0 = __ballot_sync(full, a0 < rcf2);
-                                    const uint32_t mb0 = __ballot_sync(full, b0 < rcf2);
+                                    if constexpr (DOT) {
+                                        upk2(fma2(xa2, X2[h], fma2(ya2, Y2[h], fma2(za2, Z2[h], H2[h]))), a0, a1);
+                                        upk2(fma2(xb2, X2[h], fma2(yb2, Y2[h], fma2(zb2, Z2[h], H2[h]))), b0, b1);
+                                    } else {
+                                        const unsigned long long dxa = sub2(xa2, X2[h]), dya = sub2(ya2, Y2[h]), dza = sub2(za2, Z2[h]);
+                                        const unsigned long long dxb = sub2(xb2, X2[h]), dyb = sub2(yb2, Y2[h]), dzb = sub2(zb2, Z2[h]);
+                                        upk2(fma2(dza, dza, fma2(dya, dya, mul2(dxa, dxa))), a0, a1);
+                                        upk2(fma2(dzb, dzb, fma2(dyb, dyb, mul2(dxb, dxb))), b0, b1);
+                                    }
+                                    const uint32_t ma0 = __ballot_sync(full, DOT ? a0 > ka : a0 < ka);
+                                    const uint32_t mb0 = __ballot_sync(full, DOT ? b0 > kb : b0 < kb);
                                     if (lane == 0) {
                                         S.mask[2 * h][col] = ma0;
                                         S.mask[2 * h][col + 1] = mb0;
                                     }
                                     if (2 * h + 1 < nsl) {
-                                        const uint32_t ma1 = __ballot_sync(full, a1 < rcf2);
-                                        const uint32_t mb1 = __ballot_sync(full, b1 < rcf2);
+                                        const uint32_t ma1 = __ballot_sync(full, DOT ? a1 > ka : a1 < ka);
+                                        const uint32_t mb1 = __ballot_sync(full, DOT ? b1 > kb : b1 < kb);
                                         if (lane == 0) {
                                             S.mask[2 * h + 1][col] = ma1;
                                             S.mask[2 * h + 1][col + 1] = mb1;
@@ -644,18 +660,22 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             const float yt = (float)(int)(rt.y - oy) * sy;
                             const float zt = (float)(int)(rt.z - oz) * sz;
                             const unsigned long long xt2 = pk2(xt, xt), yt2 = pk2(yt, yt), zt2 = pk2(zt, zt);
+                            const float kt = DOT ? 0.5f * (fmaf(xt, xt, fmaf(yt, yt, zt * zt)) - rcf2) : rcf2;
                             const int col = 32 * wid + (t - wlo);
 #pragma unroll
                             for (int h = 0; h < kSlots / 2; ++h) {
                                 if (2 * h < nsl) {
-                                    const unsigned long long dx = sub2(xt2, X2[h]), dy = sub2(yt2, Y2[h]), dz = sub2(zt2, Z2[h]);
-                                    const unsigned long long r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
                                     float ra, rb;
-                                    upk2(r2, ra, rb);
-                                    const uint32_t ma = __ballot_sync(full, ra < rcf2);
+                                    if constexpr (DOT) {
+                                        upk2(fma2(xt2, X2[h], fma2(yt2, Y2[h], fma2(zt2, Z2[h], H2[h]))), ra, rb);
+                                    } else {
+                                        const unsigned long long dx = sub2(xt2, X2[h]), dy = sub2(yt2, Y2[h]), dz = sub2(zt2, Z2[h]);
+                                        upk2(fma2(dz, dz, fma2(dy, dy, mul2(dx, dx))), ra, rb);
+                                    }
+                                    const uint32_t ma = __ballot_sync(full, DOT ? ra > kt : ra < kt);
                                     if (lane == 0) S.mask[2 * h][col] = ma;
                                     if (2 * h + 1 < nsl) {
-                                        const uint32_t mb = __ballot_sync(full, rb < rcf2);
+                                        const uint32_t mb = __ballot_sync(full, DOT ? rb > kt : rb < kt);
                                         if (lane == 0) S.mask[2 * h + 1][col] = mb;
                                     }
                                 }
@@ -741,7 +761,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
 
 __global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle> *>(smem_raw));
+    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle> *>(smem_raw));
 }
 
 // Batched systems: block -> (system, local block); each system uses tiles or the
@@ -763,7 +783,7 @@ __global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near
     const NearBatchGeom g = geom[lo];
     const unsigned blk = blockIdx.x - items[lo];
     if (g.tiled)
-        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch> *>(smem_raw));
+        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, false>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch> *>(smem_raw));
     else near_global_block<1>(a, (uint32_t)g.W, blk);
 }
 
