@@ -48,7 +48,7 @@ struct rbsog_batch {
     double *stage_a = nullptr, *stage_b = nullptr;       // [3 capN] caller-order staging
     double *stage_qm = nullptr;                          // [2 capN]: charges, then masses (admission)
     float *F = nullptr, *Fn = nullptr;                   // SoA [3][capN]
-    uint32_t *s = nullptr;                               // SoA [3][capN]
+    uint4 *rec_w = nullptr;                              // records in the work order [capN]
     uint4 *rec = nullptr;
     uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr;
     unsigned long long *keys = nullptr;

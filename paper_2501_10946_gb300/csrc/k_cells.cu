@@ -184,6 +184,8 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
         }
     }
     uint32_t cc[3];
+    uint32_t s32v[3];
+    unsigned long long s64v[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         r[d] = wrap_near(r[d], a.box.L[d], a.box.invL[d]);
@@ -194,12 +196,12 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
         if (PREC == 1) {
             // u = 1 gives 2^32, whose low 32 bits are 0
             s32 = trunc_lo32(__dmul_rn(r[d], a.box.invL32[d]));
-            ((uint32_t *)a.s)[(size_t)d * N + k] = s32;
+            s32v[d] = s32;
         } else {
             const double u = __dmul_rn(r[d], a.box.invL[d]);
             const unsigned long long s64 =
                 __double_as_longlong(u) >= 0x3ff0000000000000LL ? 0ull : __double2ull_rz(u * 18446744073709551616.0);
-            ((unsigned long long *)a.s)[(size_t)d * N + k] = s64;
+            s64v[d] = s64;
             s32 = (uint32_t)(s64 >> 32);
         }
         cc[d] = (uint32_t)(((unsigned long long)s32 * (unsigned long long)a.box.nc[d]) >> 32);
@@ -207,7 +209,18 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
     a.out.rx[k] = r[0]; a.out.ry[k] = r[1]; a.out.rz[k] = r[2];
     a.out.vx[k] = v[0]; a.out.vy[k] = v[1]; a.out.vz[k] = v[2];
     a.out.invm[k] = invm;
-    a.out.q[k] = a.in.q[k];
+    const double q = a.in.q[k];
+    a.out.q[k] = q;
+    // the particle record of this order: the structure factor reads it here, the gather
+    // moves it into the cell order
+    if (PREC == 1) {
+        ((uint4 *)a.rec_w)[k] = make_uint4(s32v[0], s32v[1], s32v[2], __float_as_uint(d2f_int(q)));
+    } else {
+        Rec64 rw;
+        rw.s[0] = s64v[0]; rw.s[1] = s64v[1]; rw.s[2] = s64v[2];
+        rw.q = q;
+        ((Rec64 *)a.rec_w)[k] = rw;
+    }
     a.out.id[k] = id;
     uint32_t c = a.cell_base + cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);
     a.cell[k] = c;
@@ -344,23 +357,13 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
         const int r = g.c_off ? item_system(g.c_off, g.R, c) : 0;
         atomicOr(&g.ctr[r].err, kErrCellOverflow);
     }
-    const uint32_t N = g.stride;
     g.out.rx[p] = g.in.rx[src]; g.out.ry[p] = g.in.ry[src]; g.out.rz[p] = g.in.rz[src];
     g.out.vx[p] = g.in.vx[src]; g.out.vy[p] = g.in.vy[src]; g.out.vz[p] = g.in.vz[src];
     g.out.invm[p] = g.in.invm[src];
-    const double q = g.in.q[src];
-    g.out.q[p] = q;
+    g.out.q[p] = g.in.q[src];
     g.out.id[p] = g.in.id[src];
-    if (PREC == 1) {
-        const uint32_t *s = (const uint32_t *)g.s;
-        ((uint4 *)g.rec)[p] = make_uint4(s[src], s[N + src], s[2 * (size_t)N + src], __float_as_uint((float)q));
-    } else {
-        const unsigned long long *s = (const unsigned long long *)g.s;
-        Rec64 r;
-        r.s[0] = s[src]; r.s[1] = s[N + src]; r.s[2] = s[2 * (size_t)N + src];
-        r.q = q;
-        ((Rec64 *)g.rec)[p] = r;
-    }
+    if (PREC == 1) ((uint4 *)g.rec)[p] = ((const uint4 *)g.rec_w)[src];
+    else ((Rec64 *)g.rec)[p] = ((const Rec64 *)g.rec_w)[src];
 }
 
 __device__ __forceinline__ void set_state_body(const double *r, const double *v, const double *q_user,

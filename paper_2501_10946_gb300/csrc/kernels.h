@@ -17,10 +17,10 @@ struct BinArgs {
     unsigned long long seed;
     DevCounters *ctr;
     uint32_t N;               // particles of this system
-    uint32_t stride;          // SoA stride of F and s (N, or the batch total)
+    uint32_t stride;          // SoA stride of F (N, or the batch total)
     uint32_t cell_base;       // first global cell of this system (0 for a single system)
     Box box;
-    void *s;                  // fixed point [3][stride]: uint32 (FP32) or uint64 (FP64)
+    void *rec_w;              // particle records in this (work) order: uint4 (FP32) or Rec64 (FP64)
     uint32_t *cell, *slot, *count;
 };
 // Fills the FP32 copies of dt, dt/2, c1 and okT from the doubles.
@@ -53,10 +53,9 @@ struct GatherArgs {
     DevCounters *ctr;
     const uint32_t *c_off;    // nullptr for one system
     int R;
-    const void *s;            // fixed point of the work order, SoA [3][stride]
+    const void *rec_w;        // records of the work order (k_bin's)
     void *rec;                // uint4 (FP32) or Rec64 (FP64) records in the new order
     uint32_t N;
-    uint32_t stride;
 };
 void launch_gather(int prec, const GatherArgs &g, cudaStream_t st);
 void launch_set_state(const double *r, const double *v, const double *q_user, const double *m_user, State rest,

@@ -41,7 +41,7 @@ struct rbsog_ctx {
     State rest{}, work{};
     double *q_user = nullptr, *m_user = nullptr;
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;
-    void *F = nullptr, *Fn = nullptr, *s = nullptr, *rec = nullptr;
+    void *F = nullptr, *Fn = nullptr, *rec_w = nullptr, *rec = nullptr;   // records: work order, cell order
     uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr;
     unsigned long long *keys = nullptr;
     unsigned long long *mix_thr = nullptr, *ax_thr = nullptr;
@@ -58,7 +58,7 @@ struct rbsog_ctx {
     cudaStream_t cap_stream = nullptr;
     // the structure factor runs beside the near field on this stream inside a step
     cudaStream_t side_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_bin = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool force_valid = false;
     SamplerTables tab{};
@@ -443,18 +443,8 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     b.dt = c->p.dt; b.c1 = std::exp(-c->p.langevin_gamma * c->p.dt); b.kT = c->kT; b.seed = c->p.seed;
     b.okT = (1.0 - b.c1 * b.c1) * b.kT;
     set_bin_floats(b);
-    b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.s = c->s; b.cell = c->cell;
+    b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.rec_w = c->rec_w; b.cell = c->cell;
     b.slot = c->slot; b.count = c->count;
-    { ProfScope ps(c, st, 0); launch_bin(prec, b, st); }
-    { ProfScope ps(c, st, 1); launch_scan(c->count, c->tile_sums, c->cell_start, c->box.ncell, N, st); }
-    {
-        ProfScope ps(c, st, 2);
-        launch_scatter(c->cell, c->slot, c->cell_start, c->work.id, N, c->keys, st);
-    }
-    GatherArgs g{};
-    g.in = c->work; g.out = c->rest; g.keys = c->keys; g.cell = c->cell; g.cell_start = c->cell_start; g.ctr = c->ctr;
-    g.c_off = nullptr; g.R = 1; g.s = c->s; g.rec = c->rec; g.N = N; g.stride = N;
-    { ProfScope ps(c, st, 3); launch_gather(prec, g, st); }
     SampleArgs sa{};
     sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
     for (int d = 0; d < 3; ++d) sa.tpl[d] = c->box.tpl[d];
@@ -463,28 +453,43 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     sa.measure = c->p.sampling;
     sa.Q2a = c->p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * kPi) * c->Q2 : c->Q2;
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
-    { ProfScope ps(c, st, 4); launch_sample(sa, st); }
-    // The structure factor (rho, rho_final: special-function unit) and the near field
-    // (integer and FMA pipes) are independent: outside profiling, rho runs on a side stream
-    // so that the two share the SMs; far waits for both.  Profiling keeps one stream so
-    // every group's events time that group alone.
+    RhoArgs ra{};
+    ra.rec = c->rec_w; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
+    RhoFinalArgs rf{};
+    rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
+    for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
+    rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
+    // The structure factor needs the particle records in any order and the k-sample, not
+    // the cell list: outside profiling the sample runs on a side stream from the start of
+    // the step, and rho and rho_final follow there as soon as k_bin has written the
+    // records, beside the rest of the cell list and the near field (special-function unit
+    // against integer, memory and FMA work); far waits for both streams.  Profiling keeps
+    // one stream so every group's events time that group alone.
     const bool fork = !c->prof;
     cudaStream_t sr = st;
     if (fork) {
         if (cudaEventRecord(c->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0) != cudaSuccess)
             return cuda_fail(c, cudaGetLastError(), "fork the structure-factor stream");
         sr = c->side_stream;
+        launch_sample(sa, sr);
     }
-    RhoArgs ra{};
-    ra.rec = c->rec; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
-    RhoFinalArgs rf{};
-    rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
-    for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
-    rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
+    { ProfScope ps(c, st, 0); launch_bin(prec, b, st); }
     if (fork) {
+        if (cudaEventRecord(c->ev_bin, st) != cudaSuccess || cudaStreamWaitEvent(sr, c->ev_bin, 0) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "hand the records to the structure-factor stream");
         launch_rho(prec, ra, sr);
         launch_rho_final(prec, rf, sr);
     }
+    { ProfScope ps(c, st, 1); launch_scan(c->count, c->tile_sums, c->cell_start, c->box.ncell, N, st); }
+    {
+        ProfScope ps(c, st, 2);
+        launch_scatter(c->cell, c->slot, c->cell_start, c->work.id, N, c->keys, st);
+    }
+    GatherArgs g{};
+    g.in = c->work; g.out = c->rest; g.keys = c->keys; g.cell = c->cell; g.cell_start = c->cell_start; g.ctr = c->ctr;
+    g.c_off = nullptr; g.R = 1; g.rec_w = c->rec_w; g.rec = c->rec; g.N = N;
+    { ProfScope ps(c, st, 3); launch_gather(prec, g, st); }
+    if (!fork) { ProfScope ps(c, st, 4); launch_sample(sa, st); }
     NearArgs na{};
     na.nc = c->nconsts; na.rec = c->rec; na.cell_start = c->cell_start; na.box = c->box; na.N = N; na.stride = N;
     na.Fn = c->Fn;
@@ -580,13 +585,13 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
             return bail(RBSOG_ENOMEM);
         }
     }
-    unsigned char *Fb = nullptr, *Fnb = nullptr, *sb = nullptr, *recb = nullptr;
+    unsigned char *Fb = nullptr, *Fnb = nullptr, *recwb = nullptr, *recb = nullptr;
     const int ntiles = (bx.ncell + kScanTile - 1) / kScanTile;
     c->G = rho_blocks(c->prec, c->N, p.P);
     const size_t gtab_bytes = (size_t)p.P * 64;
     if (dalloc(c, &c->q_user, n) || dalloc(c, &c->m_user, n) || dalloc(c, &c->stage_a, n3) ||
         dalloc(c, &c->stage_b, n3) || dalloc(c, &c->stage_c, n3) || dalloc(c, &Fb, n3 * real) ||
-        dalloc(c, &Fnb, n3 * real) || dalloc(c, &sb, n3 * real) || dalloc(c, &recb, n * 4 * real) ||
+        dalloc(c, &Fnb, n3 * real) || dalloc(c, &recwb, n * 4 * real) || dalloc(c, &recb, n * 4 * real) ||
         dalloc(c, &c->cell, n) || dalloc(c, &c->slot, n) || dalloc(c, &c->count, (size_t)bx.ncell) ||
         dalloc(c, &c->tile_sums, (size_t)ntiles) || dalloc(c, &c->cell_start, (size_t)bx.ncell + 1) ||
         dalloc(c, &c->keys, n) || dalloc(c, &c->modes, 3 * (size_t)p.P) ||
@@ -599,7 +604,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         g_init_error = "device allocation failed";
         return bail(RBSOG_ENOMEM);
     }
-    c->F = Fb; c->Fn = Fnb; c->s = sb; c->rec = recb;
+    c->F = Fb; c->Fn = Fnb; c->rec_w = recwb; c->rec = recb;
     if (cudaMemset(c->count, 0, sizeof(uint32_t) * bx.ncell) != cudaSuccess ||
         cudaMemset(c->ctr, 0, sizeof(DevCounters)) != cudaSuccess ||
         cudaMemset(c->edone, 0, sizeof(unsigned int)) != cudaSuccess ||
@@ -608,6 +613,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_bin, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         g_init_error = "device initialisation failed";
         return bail(RBSOG_ECUDA);
@@ -840,6 +846,7 @@ void rbsog_free(rbsog_ctx *c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_bin) cudaEventDestroy(c->ev_bin);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (void *p : c->allocs) cudaFree(p);
     delete c;

@@ -144,7 +144,7 @@ int build_args(rbsog_batch *b) {
             a.stride = b->capN;
             a.cell_base = b->c_off[r];
             a.box = h.box;
-            a.s = b->s + po;
+            a.rec_w = b->rec_w + po;
             a.cell = b->cell + po;
             a.slot = b->slot + po;
             a.count = b->count;
@@ -378,7 +378,7 @@ int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
     const size_t ntiles = (C + kScanTile - 1) / kScanTile;
     if (balloc(b, &b->stage_a, n3) || balloc(b, &b->stage_b, n3) || balloc(b, &b->stage_qm, 2 * n) ||
         balloc(b, &b->d_state_sub, R) || balloc(b, &b->F, n3) || balloc(b, &b->Fn, n3) ||
-        balloc(b, &b->s, n3) || balloc(b, &b->rec, n) || balloc(b, &b->cell, n) || balloc(b, &b->slot, n) ||
+        balloc(b, &b->rec_w, n) || balloc(b, &b->rec, n) || balloc(b, &b->cell, n) || balloc(b, &b->slot, n) ||
         balloc(b, &b->count, C) || balloc(b, &b->tile_sums, ntiles) || balloc(b, &b->cell_start, C + 1) ||
         balloc(b, &b->keys, n) || balloc(b, &b->modes, 3 * P) ||
         balloc(b, &b->inject_m, 3 * P) || balloc(b, &b->coef, P) || balloc(b, &b->rho, P) ||
@@ -420,7 +420,7 @@ size_t engine_footprint(const rbsog_batch *b, const HostSystem &h) {
     const SysShape sh = shape_of(h, b->near_target, chunk_for(h.N, b->rho_target));
     const size_t per_particle = 2 * 9 * 8 - 2 * 4   // rest + work state (id is 4 bytes)
                                 + 2 * 3 * 8          // caller-order staging
-                                + 3 * 3 * 4          // F, Fn, fixed point
+                                + 2 * 3 * 4 + 16     // F, Fn, work-order record
                                 + 16 + 2 * 4 + 8;    // record, cell/slot, sort key
     const size_t per_mode = 3 * 4 * 2 + 8 + 16 + kGTab32Bytes + 8;
     return (size_t)h.N * per_particle + (size_t)h.box.ncell * 12 + (size_t)h.p.P * per_mode +
@@ -609,8 +609,8 @@ int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far,
     mark(3);
     GatherArgs g{};
     g.in = b->work; g.out = b->rest; g.keys = b->keys; g.cell = b->cell; g.cell_start = b->cell_start; g.ctr = b->ctr;
-    g.c_off = b->d_coff; g.R = R; g.s = b->s; g.rec = b->rec;
-    g.N = b->Ntot; g.stride = b->capN;
+    g.c_off = b->d_coff; g.R = R; g.rec_w = b->rec_w; g.rec = b->rec;
+    g.N = b->Ntot;
     launch_gather(RBSOG_FP32, g, st);
     mark(4);
     launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
