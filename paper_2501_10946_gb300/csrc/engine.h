@@ -49,6 +49,7 @@ struct rbsog_batch {
     double *stage_qm = nullptr;                          // [2 capN]: charges, then masses (admission)
     float *F = nullptr, *Fn = nullptr;                   // SoA [3][capN]
     uint4 *rec_w = nullptr;                              // records in the work order [capN]
+    uint4 *rec_id = nullptr;                             // records at system offset + particle id [capN]
     uint4 *rec = nullptr;
     uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr;
     unsigned long long *keys = nullptr;
@@ -88,7 +89,7 @@ struct rbsog_batch {
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side_stream = nullptr;                  // structure factor beside the near field
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_bin = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
 };
 

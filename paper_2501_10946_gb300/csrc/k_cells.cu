@@ -211,15 +211,19 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
     a.out.invm[k] = invm;
     const double q = a.in.q[k];
     a.out.q[k] = q;
-    // the particle record of this order: the structure factor reads it here, the gather
-    // moves it into the cell order
+    // the particle record, at this position for the gather (which moves it into the cell
+    // order) and at the particle's id for the structure factor: the order of the rho sums
+    // then depends on the state alone, not on how the particles were stored before
     if (PREC == 1) {
-        ((uint4 *)a.rec_w)[k] = make_uint4(s32v[0], s32v[1], s32v[2], __float_as_uint(d2f_int(q)));
+        const uint4 rw = make_uint4(s32v[0], s32v[1], s32v[2], __float_as_uint(d2f_int(q)));
+        ((uint4 *)a.rec_w)[k] = rw;
+        ((uint4 *)a.rec_id)[id] = rw;
     } else {
         Rec64 rw;
         rw.s[0] = s64v[0]; rw.s[1] = s64v[1]; rw.s[2] = s64v[2];
         rw.q = q;
         ((Rec64 *)a.rec_w)[k] = rw;
+        ((Rec64 *)a.rec_id)[id] = rw;
     }
     a.out.id[k] = id;
     uint32_t c = a.cell_base + cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);

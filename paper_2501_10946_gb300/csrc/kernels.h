@@ -21,6 +21,7 @@ struct BinArgs {
     uint32_t cell_base;       // first global cell of this system (0 for a single system)
     Box box;
     void *rec_w;              // particle records in this (work) order: uint4 (FP32) or Rec64 (FP64)
+    void *rec_id;             // the same records at their particle ids (an order the storage does not change)
     uint32_t *cell, *slot, *count;
 };
 // Fills the FP32 copies of dt, dt/2, c1 and okT from the doubles.

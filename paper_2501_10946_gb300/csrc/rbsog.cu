@@ -41,7 +41,7 @@ struct rbsog_ctx {
     State rest{}, work{};
     double *q_user = nullptr, *m_user = nullptr;
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;
-    void *F = nullptr, *Fn = nullptr, *rec_w = nullptr, *rec = nullptr;   // records: work order, cell order
+    void *F = nullptr, *Fn = nullptr, *rec_w = nullptr, *rec_id = nullptr, *rec = nullptr;   // records: work, id, cell order
     uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr;
     unsigned long long *keys = nullptr;
     unsigned long long *mix_thr = nullptr, *ax_thr = nullptr;
@@ -443,7 +443,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     b.dt = c->p.dt; b.c1 = std::exp(-c->p.langevin_gamma * c->p.dt); b.kT = c->kT; b.seed = c->p.seed;
     b.okT = (1.0 - b.c1 * b.c1) * b.kT;
     set_bin_floats(b);
-    b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.rec_w = c->rec_w; b.cell = c->cell;
+    b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.rec_w = c->rec_w; b.rec_id = c->rec_id; b.cell = c->cell;
     b.slot = c->slot; b.count = c->count;
     SampleArgs sa{};
     sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
@@ -454,12 +454,12 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     sa.Q2a = c->p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * kPi) * c->Q2 : c->Q2;
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
     RhoArgs ra{};
-    ra.rec = c->rec_w; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
+    ra.rec = c->rec_id; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
     RhoFinalArgs rf{};
     rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
     for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
     rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
-    // The structure factor needs the particle records in any order and the k-sample, not
+    // The structure factor needs the particle records (in id order) and the k-sample, not
     // the cell list: outside profiling the sample runs on a side stream from the start of
     // the step, and rho and rho_final follow there as soon as k_bin has written the
     // records, beside the rest of the cell list and the near field (special-function unit
@@ -585,13 +585,13 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
             return bail(RBSOG_ENOMEM);
         }
     }
-    unsigned char *Fb = nullptr, *Fnb = nullptr, *recwb = nullptr, *recb = nullptr;
+    unsigned char *Fb = nullptr, *Fnb = nullptr, *recwb = nullptr, *recib = nullptr, *recb = nullptr;
     const int ntiles = (bx.ncell + kScanTile - 1) / kScanTile;
     c->G = rho_blocks(c->prec, c->N, p.P);
     const size_t gtab_bytes = (size_t)p.P * 64;
     if (dalloc(c, &c->q_user, n) || dalloc(c, &c->m_user, n) || dalloc(c, &c->stage_a, n3) ||
         dalloc(c, &c->stage_b, n3) || dalloc(c, &c->stage_c, n3) || dalloc(c, &Fb, n3 * real) ||
-        dalloc(c, &Fnb, n3 * real) || dalloc(c, &recwb, n * 4 * real) || dalloc(c, &recb, n * 4 * real) ||
+        dalloc(c, &Fnb, n3 * real) || dalloc(c, &recwb, n * 4 * real) || dalloc(c, &recib, n * 4 * real) || dalloc(c, &recb, n * 4 * real) ||
         dalloc(c, &c->cell, n) || dalloc(c, &c->slot, n) || dalloc(c, &c->count, (size_t)bx.ncell) ||
         dalloc(c, &c->tile_sums, (size_t)ntiles) || dalloc(c, &c->cell_start, (size_t)bx.ncell + 1) ||
         dalloc(c, &c->keys, n) || dalloc(c, &c->modes, 3 * (size_t)p.P) ||
@@ -604,7 +604,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         g_init_error = "device allocation failed";
         return bail(RBSOG_ENOMEM);
     }
-    c->F = Fb; c->Fn = Fnb; c->rec_w = recwb; c->rec = recb;
+    c->F = Fb; c->Fn = Fnb; c->rec_w = recwb; c->rec_id = recib; c->rec = recb;
     if (cudaMemset(c->count, 0, sizeof(uint32_t) * bx.ncell) != cudaSuccess ||
         cudaMemset(c->ctr, 0, sizeof(DevCounters)) != cudaSuccess ||
         cudaMemset(c->edone, 0, sizeof(unsigned int)) != cudaSuccess ||

@@ -145,6 +145,7 @@ int build_args(rbsog_batch *b) {
             a.cell_base = b->c_off[r];
             a.box = h.box;
             a.rec_w = b->rec_w + po;
+            a.rec_id = b->rec_id + po;
             a.cell = b->cell + po;
             a.slot = b->slot + po;
             a.count = b->count;
@@ -188,7 +189,7 @@ int build_args(rbsog_batch *b) {
         }
         {
             RhoArgs &a = ra[r];
-            a.rec = b->rec + po;
+            a.rec = b->rec_id + po;    // id order: no cell list needed
             a.N = N;
             a.m = b->modes + 3 * mo;
             a.P = P;
@@ -378,7 +379,7 @@ int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
     const size_t ntiles = (C + kScanTile - 1) / kScanTile;
     if (balloc(b, &b->stage_a, n3) || balloc(b, &b->stage_b, n3) || balloc(b, &b->stage_qm, 2 * n) ||
         balloc(b, &b->d_state_sub, R) || balloc(b, &b->F, n3) || balloc(b, &b->Fn, n3) ||
-        balloc(b, &b->rec_w, n) || balloc(b, &b->rec, n) || balloc(b, &b->cell, n) || balloc(b, &b->slot, n) ||
+        balloc(b, &b->rec_w, n) || balloc(b, &b->rec_id, n) || balloc(b, &b->rec, n) || balloc(b, &b->cell, n) || balloc(b, &b->slot, n) ||
         balloc(b, &b->count, C) || balloc(b, &b->tile_sums, ntiles) || balloc(b, &b->cell_start, C + 1) ||
         balloc(b, &b->keys, n) || balloc(b, &b->modes, 3 * P) ||
         balloc(b, &b->inject_m, 3 * P) || balloc(b, &b->coef, P) || balloc(b, &b->rho, P) ||
@@ -396,6 +397,7 @@ int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
         cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_bin, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return engine_fail(b, RBSOG_ECUDA, "device initialisation failed");
     return RBSOG_OK;
@@ -410,8 +412,9 @@ void engine_release(rbsog_batch *b) {
     if (b->side_stream) cudaStreamDestroy(b->side_stream);
     b->side_stream = nullptr;
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_bin) cudaEventDestroy(b->ev_bin);
     if (b->ev_join) cudaEventDestroy(b->ev_join);
-    b->ev_fork = b->ev_join = nullptr;
+    b->ev_fork = b->ev_bin = b->ev_join = nullptr;
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
 }
@@ -420,7 +423,7 @@ size_t engine_footprint(const rbsog_batch *b, const HostSystem &h) {
     const SysShape sh = shape_of(h, b->near_target, chunk_for(h.N, b->rho_target));
     const size_t per_particle = 2 * 9 * 8 - 2 * 4   // rest + work state (id is 4 bytes)
                                 + 2 * 3 * 8          // caller-order staging
-                                + 2 * 3 * 4 + 16     // F, Fn, work-order record
+                                + 2 * 3 * 4 + 2 * 16 // F, Fn, work-order and id-order records
                                 + 16 + 2 * 4 + 8;    // record, cell/slot, sort key
     const size_t per_mode = 3 * 4 * 2 + 8 + 16 + kGTab32Bytes + 8;
     return (size_t)h.N * per_particle + (size_t)h.box.ncell * 12 + (size_t)h.p.P * per_mode +
@@ -600,9 +603,27 @@ int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far,
     auto mark = [&](int g) {
         if (ev) cudaEventRecord(ev[g], st);
     };
+    // Outside profiling (ev == nullptr) the k-sample runs on a side stream from the start
+    // of the step, and the structure factor follows there as soon as binning has written
+    // the work-order records, beside the rest of the cell list and the near field; far
+    // waits for both streams.  Profiling keeps one stream, so each group's events time that
+    // group alone.
+    const bool fork = !ev;
+    cudaStream_t sr = fork ? b->side_stream : st;
+    if (fork) {
+        BCK(cudaEventRecord(b->ev_fork, st), "fork the structure-factor stream");
+        BCK(cudaStreamWaitEvent(sr, b->ev_fork, 0), "fork the structure-factor stream");
+        launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], sr);
+    }
     mark(0);
     launch_bin_batch(b->d_bin[set], items_of(b, kItBin), R, b->nb[kItBin], st);
     mark(1);
+    if (fork) {
+        BCK(cudaEventRecord(b->ev_bin, st), "hand the records to the structure-factor stream");
+        BCK(cudaStreamWaitEvent(sr, b->ev_bin, 0), "hand the records to the structure-factor stream");
+        launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], sr);
+        launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], sr);
+    }
     launch_scan(b->count, b->tile_sums, b->cell_start, b->Ctot, b->Ntot, st);
     mark(2);
     launch_scatter(b->cell, b->slot, b->cell_start, b->work.id, b->Ntot, b->keys, st);
@@ -613,21 +634,14 @@ int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far,
     g.N = b->Ntot;
     launch_gather(RBSOG_FP32, g, st);
     mark(4);
-    launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
+    if (!fork) launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
     mark(5);
-    if (!ev) {
-        // the structure factor beside the near field (disjoint outputs); far waits for both
-        BCK(cudaEventRecord(b->ev_fork, st), "fork the structure-factor stream");
-        BCK(cudaStreamWaitEvent(b->side_stream, b->ev_fork, 0), "fork the structure-factor stream");
-        launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], b->side_stream);
-        launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], b->side_stream);
-        launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
-        BCK(cudaEventRecord(b->ev_join, b->side_stream), "join the structure-factor stream");
+    launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
+    mark(6);
+    if (fork) {
+        BCK(cudaEventRecord(b->ev_join, sr), "join the structure-factor stream");
         BCK(cudaStreamWaitEvent(st, b->ev_join, 0), "join the structure-factor stream");
     } else {
-        // profiling: one stream, so each group's events time that group alone
-        launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
-        mark(6);
         launch_rho_batch(b->d_rho, b->d_chunk, items_of(b, kItRho), R, b->nb[kItRho], st);
         mark(7);
         launch_rho_final_batch(b->d_rf, items_of(b, kItRhoFinal), R, b->nb[kItRhoFinal], st);
