@@ -150,27 +150,32 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
             torch.cuda.synchronize(dev)
             out["profile"] = R.rbsog_profile_read(ctx)
             R.rbsog_profile(ctx, False)
-        # end to end through the C ABI with pinned host buffers
+        # end to end through the C ABI with pinned host buffers: every step uploads the
+        # integrator state (r, v and the forces at r), takes one step and reads the new
+        # state back into the same buffers, which the next step uploads
         if e2e_steps:
             hr = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
             hv = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
-            hr.copy_(r.cpu())
-            hv.copy_(v.cpu())
-            ho = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
-            R.rbsog_set_state(ctx, hr, hv, stream=stream)
-            R.rbsog_step(ctx, 1, stream=stream)
-            R.rbsog_get_state(ctx, ho, None, stream=stream)
+            hF = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
+            R.rbsog_get_state(ctx, hr, hv, stream=stream)
+            R.rbsog_get_forces(ctx, hF, stream=stream)
+
+            def e2e_step():
+                R.rbsog_set_state_forces(ctx, hr, hv, hF, stream=stream)
+                R.rbsog_step(ctx, 1, stream=stream)
+                R.rbsog_get_state(ctx, hr, hv, stream=stream)
+                R.rbsog_get_forces(ctx, hF, stream=stream)
+
+            e2e_step()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             for _ in range(e2e_steps):
-                R.rbsog_set_state(ctx, hr, hv, stream=stream)
-                R.rbsog_step(ctx, 1, stream=stream)
-                R.rbsog_get_state(ctx, ho, None, stream=stream)
+                e2e_step()
             torch.cuda.synchronize(dev)
             out["e2e_s"] = time.perf_counter() - t0
             out["e2e_steps"] = e2e_steps
-            out["e2e_h2d"] = 2 * w.N * 3 * 8
-            out["e2e_d2h"] = w.N * 3 * 8
+            out["e2e_h2d"] = 3 * w.N * 3 * 8
+            out["e2e_d2h"] = 3 * w.N * 3 * 8
     finally:
         R.rbsog_free(ctx)
     return out
@@ -451,9 +456,9 @@ def main():
     line["gpu_launches"] = KERNELS_PER_STEP * args.steps
     e2e_rate = w.N * res["e2e_steps"] / res["e2e_s"]
     line["e2e"] = {"value": e2e_rate, "unit": "particle-steps/s", "h2d_bytes_per_step": res["e2e_h2d"],
-                   "d2h_bytes_per_step": res["e2e_d2h"], "path": "rbsog_set_state(host) + rbsog_step(1) + "
-                   "rbsog_get_state(host), pinned buffers; an uploaded state has no forces yet, so each "
-                   "step also evaluates the forces of the uploaded positions (two force evaluations)"}
+                   "d2h_bytes_per_step": res["e2e_d2h"], "path": "rbsog_set_state_forces(host r, v, F) + "
+                   "rbsog_step(1) + rbsog_get_state(host r, v) + rbsog_get_forces(host F), pinned buffers, "
+                   "each step's outputs the next step's inputs (one force evaluation per step)"}
     if not args.no_batch:
         line["batched"] = batched_sweep(torch, R, args.steps, max(3, args.warmup))
     if not args.no_serve:

@@ -128,6 +128,21 @@ int rbsog_set_state(rbsog_ctx *ctx, const double *r, const double *v, void *stre
  * to *step (host; may be NULL).  Synchronous. */
 int rbsog_get_state(rbsog_ctx *ctx, double *r, double *v, uint64_t *step, void *stream);
 
+/* As rbsog_set_state, together with the forces F at that state ([N][3] in the caller's
+ * order, host or device; NULL = rbsog_set_state), for instance those that
+ * rbsog_get_forces returned after a step.  The next rbsog_step then integrates with
+ * them (the first kick of Algorithm 2) instead of evaluating forces first, so a loop
+ * that uploads r, v and F and reads them back after each step follows the same
+ * trajectory, bit for bit, as steps that stay on the device.  The FP32 build keeps F
+ * in FP32 (an F that it returned comes back exactly).  Enqueued on stream. */
+int rbsog_set_state_forces(rbsog_ctx *ctx, const double *r, const double *v, const double *F, void *stream);
+
+/* The forces at the current state (those of the last force evaluation: Eq. 55, with the
+ * far part of that evaluation's draw) into F ([N][3] in the caller's order, host or
+ * device).  RBSOG_EINVAL when no force has been evaluated or uploaded since the last
+ * rbsog_set_state.  Synchronous. */
+int rbsog_get_forces(rbsog_ctx *ctx, double *F, void *stream);
+
 /* Forces at the current positions (Eq. 55 with the far part estimated by Eq. 60)
  * from one fresh draw of P modes (or the set injected by rbsog_set_ksample) into
  * F ([N][3], host or device; NULL = keep internal only).  If e is not NULL the

@@ -455,6 +455,34 @@ __device__ __forceinline__ void get_state_body(const State &rest, size_t base, u
     if (v_out) { v_out[u] = rest.vx[k]; v_out[u + 1] = rest.vy[k]; v_out[u + 2] = rest.vz[k]; }
 }
 
+// Forces at an uploaded state: caller order [N][3] doubles into the SoA force buffer of
+// the rest order, which is the caller order right after a state upload; marks the forces
+// valid (after the counter reset of the upload, on the same stream).
+template <int PREC>
+__global__ void __launch_bounds__(256) k_set_forces(const double *F_in, void *F, uint32_t N, DevCounters *ctr) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double f = F_in[3 * (size_t)k + d];
+            if (PREC == 1) ((float *)F)[(size_t)d * N + k] = d2f_int(f);
+            else ((double *)F)[(size_t)d * N + k] = f;
+        }
+    }
+    if (k == 0) ctr->fvalid = 1;
+}
+
+// The forces of the rest order into the caller's order [N][3].
+template <int PREC>
+__global__ void __launch_bounds__(256) k_get_forces(State rest, const void *F, uint32_t N, double *F_out) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const size_t u = 3 * (size_t)rest.id[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        F_out[u + d] = PREC == 1 ? f2d_int(((const float *)F)[(size_t)d * N + k]) : ((const double *)F)[(size_t)d * N + k];
+}
+
 __global__ void __launch_bounds__(256) k_get_state(State rest, uint32_t N, double *r_out, double *v_out) {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < N) get_state_body(rest, 0, k, r_out, v_out);
@@ -524,6 +552,17 @@ void launch_get_state_batch(const SysStateArgs *args, const uint32_t *items, int
 
 void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st) {
     k_get_state<<<blocks_for(N, 256), 256, 0, st>>>(rest, N, r_out, v_out);
+}
+
+void launch_set_forces(int prec, const double *F_in, void *F, uint32_t N, DevCounters *ctr, cudaStream_t st) {
+    const unsigned nb = blocks_for(N > 0 ? N : 1, 256);
+    if (prec == 1) k_set_forces<1><<<nb, 256, 0, st>>>(F_in, F, N, ctr);
+    else k_set_forces<0><<<nb, 256, 0, st>>>(F_in, F, N, ctr);
+}
+
+void launch_get_forces(int prec, State rest, const void *F, uint32_t N, double *F_out, cudaStream_t st) {
+    if (prec == 1) k_get_forces<1><<<blocks_for(N, 256), 256, 0, st>>>(rest, F, N, F_out);
+    else k_get_forces<0><<<blocks_for(N, 256), 256, 0, st>>>(rest, F, N, F_out);
 }
 
 }  // namespace rbsog

@@ -62,6 +62,11 @@ void launch_gather(int prec, const GatherArgs &g, cudaStream_t st);
 void launch_set_state(const double *r, const double *v, const double *q_user, const double *m_user, State rest,
                       uint32_t N, Box box, DevCounters *ctr, cudaStream_t st);
 void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st);
+// F_in ([N][3] doubles, caller order = the rest order after a state upload) into the SoA
+// force buffer F of the build's precision; sets ctr->fvalid
+void launch_set_forces(int prec, const double *F_in, void *F, uint32_t N, DevCounters *ctr, cudaStream_t st);
+// the SoA forces of the rest order into F_out ([N][3] doubles, caller order)
+void launch_get_forces(int prec, State rest, const void *F, uint32_t N, double *F_out, cudaStream_t st);
 
 // ---- sampler and normalisation (k_sample.cu) ----
 // A mixture of separable components: component c has weight mix and per-axis alias

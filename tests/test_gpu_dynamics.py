@@ -118,6 +118,57 @@ def test_graph_replay_is_deterministic():
     assert outs[0][2] == 7
 
 
+@pytest.mark.parametrize("ensemble", ["nve", "langevin"])
+@pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32], ids=["fp64", "fp32"])
+def test_host_round_trip_with_forces_follows_the_device_trajectory(prec, ensemble):
+    """Reading r, v and F back after every step and uploading them with
+    rbsog_set_state_forces gives the device-resident trajectory bit for bit: one force
+    evaluation per step, the same draws, and forces that do not depend on the particle
+    layout the upload resets."""
+    w = workload(700, 8.5, kappa=1.0, Gamma=1.0, P=48, seed=47, dt=0.002, ensemble=ensemble)
+    r0, v0 = W.positions(w), W.velocities(w)
+    n = 4
+    dev = []
+    with Ctx(w, prec) as c:
+        R.rbsog_set_state(c.h, r0, v0)
+        for _ in range(n):
+            R.rbsog_step(c.h, 1)
+            r, v = np.zeros((w.N, 3)), np.zeros((w.N, 3))
+            R.rbsog_get_state(c.h, r, v)
+            dev.append((r, v))
+    with Ctx(w, prec) as c:
+        R.rbsog_set_state(c.h, r0, v0)
+        F = np.zeros((w.N, 3))
+        with pytest.raises(R.RbsogError):
+            R.rbsog_get_forces(c.h, F)              # no forces at an uploaded state yet
+        R.rbsog_forces(c.h)
+        R.rbsog_get_forces(c.h, F)
+        r, v = r0.copy(), v0.copy()
+        for s in range(n):
+            R.rbsog_set_state_forces(c.h, r, v, F)
+            R.rbsog_step(c.h, 1)
+            R.rbsog_get_state(c.h, r, v)
+            R.rbsog_get_forces(c.h, F)
+            assert np.array_equal(r, dev[s][0]), s
+            assert np.array_equal(v, dev[s][1]), s
+
+
+def test_set_state_forces_without_forces_is_set_state():
+    w = workload(500, 8.0, P=32, seed=49)
+    outs = []
+    for with_forces in (False, True):
+        with Ctx(w, R.RBSOG_FP32) as c:
+            if with_forces:
+                R.rbsog_set_state_forces(c.h, W.positions(w), W.velocities(w), None)
+            else:
+                R.rbsog_set_state(c.h, W.positions(w), W.velocities(w))
+            R.rbsog_step(c.h, 2)
+            r = np.zeros((w.N, 3))
+            R.rbsog_get_state(c.h, r)
+            outs.append(r)
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_energy_components_after_steps_match_oracle():
     """After steps, the GPU energies at the final state equal the oracle's on the GPU's k-set."""
     w = W.cfg_small_fp64()
