@@ -16,9 +16,10 @@
 //       every pair that the exact test accepts passes it;
 //   (2) pairs: each lane walks its own target's masks in candidate order, recomputes the
 //       separation exactly from the fixed-point coordinates, applies the exact r < r_c
-//       test and accumulates the pair force (compensated FP32 sums).  The pairs and their
-//       order are those of a plain loop over the 27 cells, so the result does not depend
-//       on the pre-filter.
+//       test and accumulates the pair forces: the two of a pass added in FP32, then one
+//       compensated FP32 add.  The pairs are those of a plain loop over the 27 cells, in
+//       its order; which two share a pass follows the pre-filter's hits, so the
+//       pre-filter changes the rounding of the sums, never the set of pairs.
 // Neighbourhoods larger than 8 slots (256 candidates) run in several such rounds.
 // Otherwise (FP64 build, fewer than 3 cells on an axis, or a neighbourhood that does
 // not fit the staging buffer): one thread per particle reading candidates from global
@@ -718,14 +719,11 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             float ga, gb, ua, ub;
                             upk2(g2, ga, gb);
                             upk2(u2, ua, ub);
-                            if (va) {
-                                kahan2(Fxy, Cxy, pk2(ga * a0, ga * a1));
-                                kahan2(Fzu, Czu, pk2(ga * a2, ua));
-                            }
-                            if (vb) {
-                                kahan2(Fxy, Cxy, pk2(gb * b0, gb * b1));
-                                kahan2(Fzu, Czu, pk2(gb * b2, ub));
-                            }
+                            // the pass's two contributions added in FP32, then one compensated add
+                            ga = va ? ga : 0.f; ua = va ? ua : 0.f;
+                            gb = vb ? gb : 0.f; ub = vb ? ub : 0.f;
+                            kahan2(Fxy, Cxy, fma2(dup2(ga), pk2(a0, a1), mul2(dup2(gb), pk2(b0, b1))));
+                            kahan2(Fzu, Czu, fma2(pk2(ga, 1.f), pk2(a2, ua), mul2(pk2(gb, 1.f), pk2(b2, ub))));
                         }
                     }
                     __syncwarp();
