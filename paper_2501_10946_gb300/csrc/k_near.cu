@@ -92,7 +92,7 @@ struct alignas(16) NearF {
     unsigned long long ly1;                 // log2 of the first term's weight
     unsigned long long nl2b, il2b, ly2, sg2;   // second term: -log2(e)/lambda_2, 1/lambda_2, log2|y2|, sign
     unsigned long long nb[kMaxGauss];       // -b_m log2(e)
-    unsigned long long af[kMaxGauss];       // a_m
+    unsigned long long naf[kMaxGauss];      // -a_m (the energy's SOG sum is accumulated negated)
     unsigned long long cf[kMaxGauss];       // c_m
 };
 
@@ -107,7 +107,7 @@ __device__ __forceinline__ void kahan2(unsigned long long &s, unsigned long long
 }
 
 // The two terms of two FP32 pairs (one per lane) before accumulation:
-// gsc = q_i q_j [F_N1 + F_N2](r) and uh = q_i q_j [Y - F](r) / 2.
+// gsc = q_i q_j [F_N1 + F_N2](r) and uh = q_i q_j [Y - F](r) (the caller halves the sum).
 __device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long qq, unsigned long long r2,
                                             unsigned long long &gsc, unsigned long long &uh) {
     float r2a, r2b;
@@ -117,35 +117,35 @@ __device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long 
     float xa, xb;
     upk2(mul2(r, nc.nl2), xa, xb);
     const unsigned long long e1 = pk2(ex2_approx(xa), ex2_approx(xb));
-    unsigned long long fsog = 0ull, fn2 = 0ull;
+    unsigned long long nsog = 0ull, fn2 = 0ull;   // nsog = -F(r) of the SOG
     // two Gaussians per iteration (16-byte loads of adjacent constants), same order of sums
     int g = 0;
     for (; g + 1 < nc.mtot; g += 2) {
         const ulonglong2 nb = *reinterpret_cast<const ulonglong2 *>(&nc.nb[g]);
-        const ulonglong2 af = *reinterpret_cast<const ulonglong2 *>(&nc.af[g]);
+        const ulonglong2 af = *reinterpret_cast<const ulonglong2 *>(&nc.naf[g]);
         const ulonglong2 cf = *reinterpret_cast<const ulonglong2 *>(&nc.cf[g]);
         float ya, yb, za, zb;
         upk2(mul2(r2, nb.x), ya, yb);
         upk2(mul2(r2, nb.y), za, zb);
         const unsigned long long E0 = pk2(ex2_approx(ya), ex2_approx(yb));
         const unsigned long long E1 = pk2(ex2_approx(za), ex2_approx(zb));
-        fsog = fma2(af.x, E0, fsog);
+        nsog = fma2(af.x, E0, nsog);
         fn2 = fma2(cf.x, E0, fn2);
-        fsog = fma2(af.y, E1, fsog);
+        nsog = fma2(af.y, E1, nsog);
         fn2 = fma2(cf.y, E1, fn2);
     }
     if (g < nc.mtot) {
         float ya, yb;
         upk2(mul2(r2, nc.nb[g]), ya, yb);
         const unsigned long long E = pk2(ex2_approx(ya), ex2_approx(yb));
-        fsog = fma2(nc.af[g], E, fsog);
+        nsog = fma2(nc.naf[g], E, nsog);
         fn2 = fma2(nc.cf[g], E, fn2);
     }
     const unsigned long long rinv3 = mul2(mul2(rinv, rinv), rinv);
     if (!nc.two) {
         const unsigned long long fn1 = mul2(mul2(e1, fma2(r, nc.il2, dup2(1.f))), rinv3);
         gsc = mul2(qq, add2(fn1, fn2));
-        uh = mul2(mul2(dup2(0.5f), qq), fma2(e1, rinv, fsog ^ 0x8000000080000000ull));
+        uh = mul2(qq, fma2(e1, rinv, nsog));
     } else {
         // two Yukawa terms (EGS): weights folded into the exponents, the second's sign apart
         upk2(fma2(r, nc.nl2, nc.ly1), xa, xb);
@@ -155,12 +155,12 @@ __device__ __forceinline__ void pair_terms2(const NearF &nc, unsigned long long 
         const unsigned long long fn1 = fma2(mul2(e2, fma2(r, nc.il2b, dup2(1.f))), rinv3,
                                             mul2(mul2(ew, fma2(r, nc.il2, dup2(1.f))), rinv3));
         gsc = mul2(qq, add2(fn1, fn2));
-        uh = mul2(mul2(dup2(0.5f), qq), fma2(ew, rinv, fma2(e2, rinv, fsog ^ 0x8000000080000000ull)));
+        uh = mul2(qq, fma2(ew, rinv, fma2(e2, rinv, nsog)));
     }
 }
 
 // One FP32 pair: accumulate q_i q_j [F_N1 + F_N2](r) (r_i - r_j) and U_N/2 (compensated).
-// C is NearConsts or NearF (the same float fields).
+// C is NearConsts (the per-particle path).
 template <class C>
 __device__ __forceinline__ void pair_f32(const C &nc, float qq, float d0, float d1, float d2, float r2,
                                          float *Fs, float *Fc, float &Us, float &Uc) {
@@ -409,7 +409,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     }
     for (int g = tid; g < a.nc.mtot; g += NT) {
         S.nf.nb[g] = dup2(-a.nc.bl2f[g]);
-        S.nf.af[g] = dup2(a.nc.af[g]);
+        S.nf.naf[g] = dup2(-a.nc.af[g]);
         S.nf.cf[g] = dup2(a.nc.cf[g]);
     }
     __syncthreads();
@@ -739,7 +739,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                     Fn[g] = fx - cx;
                     Fn[a.stride + g] = fy - cy;
                     Fn[2 * (size_t)a.stride + g] = fz - cz_;
-                    sumU += us - uc;
+                    sumU += 0.5f * (us - uc);        // each pair counted from both ends
                 }
             }
         }
