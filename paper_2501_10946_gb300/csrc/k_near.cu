@@ -338,7 +338,8 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
 // ---------------------------------------------------------------- tiled (TMA) FP32 path
 // CAP: staged particles per CTA (16 B each); NT: threads per CTA.  One large system
 // stages 1280 with 128 threads; batches of many (mostly small) systems stage 1024 with 96.
-template <int CAP, int NT, int MW>
+// FR: tiles may span a whole row of cells (a third staging slice per row)
+template <int CAP, int NT, int MW, bool FR>
 struct TileSmem {
     uint4 stage[CAP];                       // staged records
     uint32_t mask[kSlots][NT];    // per target (column = owning thread): hit bits of a round
@@ -347,8 +348,8 @@ struct TileSmem {
     NearF nf;                               // the system's FP32 pair constants
     int seg_off[9][MW + 3];                 // per row: offset of each region cell within the row
     int row_base[10];                       // per row: offset of the row in the staging buffer
-    uint32_t chunk_g[9][2];                 // per row: global start of up to two slices
-    uint32_t chunk_n[9][2];                 // per row: particle count of each slice
+    uint32_t chunk_g[9][FR ? 3 : 2];        // per row: global start of up to two (three) slices
+    uint32_t chunk_n[9][FR ? 3 : 2];        // per row: particle count of each slice
     unsigned long long mbar;
 };
 
@@ -356,8 +357,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 
 // Region cell (1 .. wn-2) of the centre row holding staged target jl (offset within row 4):
 // the last i with seg_off[4][i] <= jl.
-template <int CAP, int NT, int MW>
-__device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW> &S, int wn, int jl) {
+template <int CAP, int NT, int MW, bool FR>
+__device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW, FR> &S, int wn, int jl) {
     int lo = 1, hi = wn - 2;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -369,9 +370,9 @@ __device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW> &S, int w
 
 // DOT selects the form of the pre-filter test (see the threshold below): the expanded
 // one takes fewer instructions, the direct one fewer registers.
-template <int CAP, int NT, int MW, bool DOT>
+template <int CAP, int NT, int MW, bool DOT, bool FR>
 __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
-                                               TileSmem<CAP, NT, MW> &S) {
+                                               TileSmem<CAP, NT, MW, FR> &S) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, wid = tid >> 5;
     const unsigned full = 0xffffffffu;
@@ -424,10 +425,20 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             off += S.seg_off[tid][i];
             S.seg_off[tid][i] = off;
         }
+        if constexpr (FR) { S.chunk_g[tid][2] = 0; S.chunk_n[tid][2] = 0; }
         if (x0 >= 1 && x1 <= nx - 1) {           // one slice: cells x0-1 .. x1
             S.chunk_g[tid][0] = cs[rowbase + x0 - 1];
             S.chunk_n[tid][0] = cs[rowbase + x1 + 1] - cs[rowbase + x0 - 1];
             S.chunk_g[tid][1] = 0; S.chunk_n[tid][1] = 0;
+        } else if (FR && x0 == 0 && x1 == nx) {  // the whole row: cell nx-1, cells 0 .. nx-1, cell 0
+            S.chunk_g[tid][0] = cs[rowbase + nx - 1];
+            S.chunk_n[tid][0] = cs[rowbase + nx] - cs[rowbase + nx - 1];
+            S.chunk_g[tid][1] = cs[rowbase];
+            S.chunk_n[tid][1] = cs[rowbase + nx] - cs[rowbase];
+            if constexpr (FR) {
+                S.chunk_g[tid][2] = cs[rowbase];
+                S.chunk_n[tid][2] = cs[rowbase + 1] - cs[rowbase];
+            }
         } else if (x0 == 0) {                    // cell nx-1, then cells 0 .. x1
             S.chunk_g[tid][0] = cs[rowbase + nx - 1];
             S.chunk_n[tid][0] = cs[rowbase + nx] - cs[rowbase + nx - 1];
@@ -471,7 +482,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                 const uint4 *rec = (const uint4 *)a.rec;
                 for (int r = 0; r < 9; ++r) {
                     uint32_t dst = (uint32_t)S.row_base[r];
-                    for (int h = 0; h < 2; ++h) {
+                    for (int h = 0; h < (FR ? 3 : 2); ++h) {
                         const uint32_t n = S.chunk_n[r][h];
                         if (n) {
                             asm volatile(
@@ -759,7 +770,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
 
 __global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle> *>(smem_raw));
+    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true, false>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false> *>(smem_raw));
 }
 
 // Batched systems: block -> (system, local block); each system uses tiles or the
@@ -781,7 +792,7 @@ __global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near
     const NearBatchGeom g = geom[lo];
     const unsigned blk = blockIdx.x - items[lo];
     if (g.tiled)
-        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, false>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch> *>(smem_raw));
+        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, false, true>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true> *>(smem_raw));
     else near_global_block<1>(a, (uint32_t)g.W, blk);
 }
 
@@ -790,7 +801,7 @@ inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 
 }  // namespace
 
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks, double target,
-                   int cap, int threads, int max_w) {
+                   int cap, int threads, int max_w, bool full_rows) {
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
     if (nx >= 3 && ny >= 3 && nz >= 3) {
         // tile width: about `target` (default 110) targets per CTA and about 1000 staged
@@ -801,7 +812,11 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
         int Wcap = (int)(0.78 * cap / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
         if (Wt > Wcap) Wt = Wcap;
         if (Wt > max_w) Wt = max_w;
-        if (Wt > nx - 2) Wt = nx - 2;
+        // A tile of the whole row (W = nx) stages cells nx-1 and 0 twice, as its two halo
+        // cells; every target cell still sees three distinct cells per row (nx >= 3).  It
+        // fills the CTAs of small boxes in a batch; one small system alone keeps tiles of at
+        // most nx - 2 cells, whose larger number of CTAs it needs.
+        if (Wt > (full_rows ? nx : nx - 2)) Wt = full_rows ? nx : nx - 2;
         if (Wt < 1) Wt = 1;
         *tiles_x = (nx + Wt - 1) / Wt;
         *W = (nx + *tiles_x - 1) / *tiles_x;
@@ -819,9 +834,9 @@ static void set_tile_smem_attr() {
     static bool done = false;
     if (!done) {
         cudaFuncSetAttribute(k_near_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle>));
+                             (int)sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false>));
         cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch>));
+                             (int)sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true>));
         done = true;
     }
 }
@@ -832,7 +847,7 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     near_geometry(a.box, a.N, &tiled, &W, &tiles_x, &nb);
     if (prec == 1 && tiled) {
         set_tile_smem_attr();
-        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle>), st>>>(a, W, tiles_x);
+        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false>), st>>>(a, W, tiles_x);
         return (int)nb * kWarpsPerBlock;
     }
     nb = blocks_for(a.N, kGlobalThreads);
@@ -844,7 +859,7 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
 void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
                        uint32_t nblocks, cudaStream_t st) {
     set_tile_smem_attr();
-    k_near_batch<<<nblocks, kNearBatchThreads, sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch>), st>>>(args, geom, items, R);
+    k_near_batch<<<nblocks, kNearBatchThreads, sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true>), st>>>(args, geom, items, R);
 }
 
 }  // namespace rbsog

@@ -202,10 +202,10 @@ constexpr int kNearBatchWarps = kNearBatchThreads / 32;   // energy partials per
 constexpr int kNearMaxWBatch = 16;
 // target: particles per CTA the tile width aims at (capped by the staging buffer `cap`);
 // threads: threads per CTA of the per-particle path (boxes under 3 cells per axis);
-// max_w: widest tile in cells
+// max_w: widest tile in cells; full_rows: tiles may span a whole row of cells
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks,
                    double target = 110.0, int cap = kNearCapSingle, int threads = 128,
-                   int max_w = kNearMaxWSingle);
+                   int max_w = kNearMaxWSingle, bool full_rows = false);
 void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
                        uint32_t nblocks, cudaStream_t st);
 void launch_rho_batch(const RhoArgs *args, const int *chunk, const uint32_t *items, int R, uint32_t nblocks,

@@ -91,7 +91,7 @@ struct SysShape {
 SysShape shape_of(const HostSystem &h, double near_target, int chunk) {
     SysShape s{};
     near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target, kNearCapBatch,
-                  kNearBatchThreads, kNearMaxWBatch);
+                  kNearBatchThreads, kNearMaxWBatch, true);
     s.G = (int)((h.N + (uint32_t)chunk - 1) / (uint32_t)chunk);
     return s;
 }
