@@ -65,6 +65,16 @@ def test_invalid_parameters_are_rejected_on_the_host(field, value):
     assert R.rbsog_last_error(None)
 
 
+def test_state_entry_points_reject_a_null_context():
+    """The state and force entry points check their context and pointers on the host."""
+    F = np.zeros((4, 3))
+    calls = [lambda: R.rbsog_set_state(None, F, F), lambda: R.rbsog_set_state_forces(None, F, F, F),
+             lambda: R.rbsog_get_state(None, F, F), lambda: R.rbsog_get_forces(None, F)]
+    for call in calls:
+        with pytest.raises(R.RbsogError, match="EINVAL"):
+            call()
+
+
 def test_egs_screening_rejects_a_table_of_one_kernel():
     """The EGS screening builds one SOG per Yukawa term, so a given (M1, M2) is refused."""
     w, p = base_params()

@@ -153,6 +153,19 @@ def test_host_round_trip_with_forces_follows_the_device_trajectory(prec, ensembl
             assert np.array_equal(v, dev[s][1]), s
 
 
+@pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32], ids=["fp64", "fp32"])
+def test_get_forces_returns_the_last_evaluation(prec):
+    """rbsog_get_forces gives, in the caller's order, the forces that rbsog_forces returned."""
+    w = workload(600, 8.0, P=32, seed=51)
+    with Ctx(w, prec) as c:
+        R.rbsog_set_state(c.h, W.positions(w), W.velocities(w))
+        F = np.zeros((w.N, 3))
+        R.rbsog_forces(c.h, F)
+        G = np.zeros((w.N, 3))
+        R.rbsog_get_forces(c.h, G)
+        assert np.array_equal(F, G)
+
+
 def test_set_state_forces_without_forces_is_set_state():
     w = workload(500, 8.0, P=32, seed=49)
     outs = []
