@@ -48,7 +48,9 @@ extern "C" {
 /* precision */
 #define RBSOG_FP64 0          /* every force and phase in FP64 (parity build) */
 #define RBSOG_FP32 1          /* FP32 pair and phase arithmetic with compensated sums;
-                                 FP64 positions, velocities, integration and energies */
+                                 positions and velocities stored in FP64, the positions
+                                 accumulating FP32 kick and drift increments; energies
+                                 reduced in FP64 */
 /* ensemble */
 #define RBSOG_NVE 0           /* velocity Verlet */
 #define RBSOG_LANGEVIN 1      /* BAOAB Langevin, friction langevin_gamma, target k_B T */
