@@ -599,11 +599,17 @@ __global__ void __launch_bounds__(256) k_energy(EnergyArgs a) {
             a.out[2] = a.Uself;
             a.out[3] = Ks;
             a.out[4] = Us + Ut + a.Uself + Ks;
-            if (a.advance_step && a.ctr->fvalid) a.ctr->step += 1ull;
-            a.ctr->fvalid = 1;
             *a.done = 0u;
         }
     }
+}
+
+// Close of one force evaluation of a single system: the forces are now valid, and a
+// step that integrated counts (a pass that found the forces invalid only evaluated
+// them).  The energy reduction (k_energy) runs only when the energies are read.
+__global__ void k_close_eval(DevCounters *ctr, int advance_step) {
+    if (advance_step && ctr->fvalid) ctr->step += 1ull;
+    ctr->fvalid = 1;
 }
 
 __global__ void __launch_bounds__(1024) k_energy_batch(const EnergyArgs *args) {
@@ -660,6 +666,8 @@ int launch_far(int prec, const FarArgs &a, cudaStream_t st) {
     k_far64<<<nb, kFarThreads, 0, st>>>(a);
     return (int)nb;
 }
+
+void launch_close_eval(DevCounters *ctr, int advance_step, cudaStream_t st) { k_close_eval<<<1, 1, 0, st>>>(ctr, advance_step); }
 
 static_assert(kEnergyBlocks <= 32, "k_energy combines the block sums in one warp");
 void launch_energy(const EnergyArgs &a, cudaStream_t st) { k_energy<<<kEnergyBlocks, 256, 0, st>>>(a); }

@@ -178,8 +178,12 @@ struct EnergyArgs {
     unsigned int *done;        // arrival counter of the blocks (0 between launches)
 };
 constexpr int kEnergyBlocks = 32;
-// Single system: kEnergyBlocks blocks, the last to finish adds their sums in a fixed order.
+// Single system: kEnergyBlocks blocks, the last to finish adds their sums in a fixed order
+// (the partials of the last force evaluation; launched when the energies are read).
 void launch_energy(const EnergyArgs &a, cudaStream_t st);
+// End of a single system's force evaluation: fvalid = 1, step += 1 when advance_step and
+// the forces were valid before.
+void launch_close_eval(DevCounters *ctr, int advance_step, cudaStream_t st);
 
 // ---- batched systems: one launch per kernel over every system --------------------
 constexpr size_t kGTab32Bytes = 32;   // one FP32 gather-table entry (int4 + float4)

@@ -508,12 +508,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     fa.st = c->rest; fa.integrate = integrate ? 1 : 0; fa.dt = c->p.dt; fa.K_part = c->K_part;
     fa.F_user = F_user; fa.Fn_user = Fn_user; fa.Ff_user = Ff_user; fa.ctr = c->ctr;
     { ProfScope ps(c, st, 8); c->nK = launch_far(prec, fa, st); }
-    EnergyArgs ea{};
-    ea.U_part = c->U_part; ea.nU = c->nU; ea.K_part = c->K_part; ea.nK = c->nK; ea.Ufar = c->Ufar;
-    ea.nUfar = c->p.P;
-    ea.Ufar0 = c->Ufar0; ea.Uself = c->Uself; ea.out = c->energy; ea.ctr = c->ctr; ea.advance_step = advance;
-    ea.scratch = c->escratch; ea.done = c->edone;
-    { ProfScope ps(c, st, 9); launch_energy(ea, st); }
+    { ProfScope ps(c, st, 9); launch_close_eval(c->ctr, advance, st); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
     return RBSOG_OK;
@@ -528,7 +523,16 @@ int check_device_errors(rbsog_ctx *c) {
     return RBSOG_OK;
 }
 
+// The energies of the last force evaluation: its near, kinetic and per-mode partials
+// reduced in a fixed order (k_energy), then read back.  Synchronous.
 int read_energy(rbsog_ctx *c, rbsog_energy *e, cudaStream_t st) {
+    EnergyArgs ea{};
+    ea.U_part = c->U_part; ea.nU = c->nU; ea.K_part = c->K_part; ea.nK = c->nK; ea.Ufar = c->Ufar;
+    ea.nUfar = c->p.P;
+    ea.Ufar0 = c->Ufar0; ea.Uself = c->Uself; ea.out = c->energy; ea.ctr = c->ctr;
+    ea.scratch = c->escratch; ea.done = c->edone;
+    launch_energy(ea, st);
+    CK(cudaGetLastError(), "energy reduction");
     double h[5];
     CK(cudaMemcpyAsync(h, c->energy, sizeof h, cudaMemcpyDeviceToHost, st), "read energy");
     DevCounters hc;
