@@ -106,6 +106,8 @@ void engine_release(rbsog_batch *b);
 // Bytes of device memory a system takes in the arenas (particles, cells, modes and
 // per-block partials at the engine's shapes).
 size_t engine_footprint(const rbsog_batch *b, const HostSystem &h);
+// each system's energies of its last force evaluation into energy[5 R]; enqueued on st
+int engine_reduce_energies(rbsog_batch *b, cudaStream_t st);
 // True if the system fits the remaining capacity.
 bool engine_fits(const rbsog_batch *b, const HostSystem &h);
 // Append a system (host bookkeeping only; its state is set with engine_set_state).

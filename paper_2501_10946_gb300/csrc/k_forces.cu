@@ -528,9 +528,6 @@ __device__ __forceinline__ void energy_body(const EnergyArgs &a, double *sh) {
         a.out[2] = a.Uself;
         a.out[3] = K;
         a.out[4] = U + Uf + a.Uself + K;
-        // a pass that found the forces invalid only evaluated them
-        if (a.advance_step && a.ctr->fvalid) a.ctr->step += 1ull;
-        a.ctr->fvalid = 1;
     }
 }
 
@@ -612,6 +609,14 @@ __global__ void k_close_eval(DevCounters *ctr, int advance_step) {
     ctr->fvalid = 1;
 }
 
+// The same for the R systems of a batch (their counters are contiguous).
+__global__ void __launch_bounds__(256) k_close_eval_batch(DevCounters *ctr, int R, int advance_step) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    if (advance_step && ctr[r].fvalid) ctr[r].step += 1ull;
+    ctr[r].fvalid = 1;
+}
+
 __global__ void __launch_bounds__(1024) k_energy_batch(const EnergyArgs *args) {
     __shared__ double sh[1024];
     energy_body(args[blockIdx.x], sh);
@@ -668,6 +673,9 @@ int launch_far(int prec, const FarArgs &a, cudaStream_t st) {
 }
 
 void launch_close_eval(DevCounters *ctr, int advance_step, cudaStream_t st) { k_close_eval<<<1, 1, 0, st>>>(ctr, advance_step); }
+void launch_close_eval_batch(DevCounters *ctr, int R, int advance_step, cudaStream_t st) {
+    k_close_eval_batch<<<(R + 255) / 256, 256, 0, st>>>(ctr, R, advance_step);
+}
 
 static_assert(kEnergyBlocks <= 32, "k_energy combines the block sums in one warp");
 void launch_energy(const EnergyArgs &a, cudaStream_t st) { k_energy<<<kEnergyBlocks, 256, 0, st>>>(a); }

@@ -173,7 +173,6 @@ struct EnergyArgs {
     double Uself;
     double *out;               // [5]: U_near, U_far, U_self, K, total
     DevCounters *ctr;
-    int advance_step;
     double *scratch;           // [3 kEnergyBlocks] per-block sums (single system)
     unsigned int *done;        // arrival counter of the blocks (0 between launches)
 };
@@ -184,6 +183,7 @@ void launch_energy(const EnergyArgs &a, cudaStream_t st);
 // End of a single system's force evaluation: fvalid = 1, step += 1 when advance_step and
 // the forces were valid before.
 void launch_close_eval(DevCounters *ctr, int advance_step, cudaStream_t st);
+void launch_close_eval_batch(DevCounters *ctr, int R, int advance_step, cudaStream_t st);
 
 // ---- batched systems: one launch per kernel over every system --------------------
 constexpr size_t kGTab32Bytes = 32;   // one FP32 gather-table entry (int4 + float4)

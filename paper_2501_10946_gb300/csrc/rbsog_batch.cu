@@ -237,7 +237,6 @@ int build_args(rbsog_batch *b) {
             e.Uself = h.Uself;
             e.out = b->energy + 5 * (size_t)r;
             e.ctr = ctr;
-            e.advance_step = k;
         }
         ss[r] = SysStateArgs{offset_state(b->rest, po), nullptr, nullptr, N, (uint32_t)po, h.box};
         const uint32_t cnt[6] = {bin_batch_blocks(N), sample_batch_blocks(P), sh.near_blocks,
@@ -286,6 +285,7 @@ int check_all(rbsog_batch *b) {
 }
 
 int read_energies(rbsog_batch *b, rbsog_energy *e, cudaStream_t st) {
+    if (int code = engine_reduce_energies(b, st)) return code;
     std::vector<double> h(5 * (size_t)b->R);
     if (b->R) BCK(cudaMemcpyAsync(h.data(), b->energy, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
                   "read energy");
@@ -417,6 +417,14 @@ void engine_release(rbsog_batch *b) {
     b->ev_fork = b->ev_bin = b->ev_join = nullptr;
     for (void *p : b->allocs) cudaFree(p);
     b->allocs.clear();
+}
+
+// Each system's energies from the partials of its last force evaluation (fixed order),
+// into b->energy.  Enqueued on st.
+int engine_reduce_energies(rbsog_batch *b, cudaStream_t st) {
+    if (b->R) launch_energy_batch(b->d_energy[0], b->R, st);
+    BCK(cudaGetLastError(), "energy reduction");
+    return RBSOG_OK;
 }
 
 size_t engine_footprint(const rbsog_batch *b, const HostSystem &h) {
@@ -649,7 +657,7 @@ int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far,
     mark(8);
     launch_far_batch(far ? far : b->d_far[set], items_of(b, kItFar), R, b->nb[kItFar], st);
     mark(9);
-    launch_energy_batch(b->d_energy[set], R, st);
+    launch_close_eval_batch(b->ctr, R, set, st);   // the energies are reduced when read
     mark(10);
     BCK(cudaGetLastError(), "kernel launch");
     return RBSOG_OK;

@@ -78,8 +78,11 @@ int retire(rbsog_server *s, const std::vector<DevCounters> &ctr) {
     rbsog_batch *b = &s->eng;
     std::vector<char> keep(b->R, 1);
     std::vector<double> e5(5 * (size_t)b->R);
-    if (b->R)
+    if (b->R) {
+        if (int c = engine_reduce_energies(b, s->st)) return sfail(s, c, b->err);
+        SCK(cudaStreamSynchronize(s->st), "energy reduction");
         SCK(cudaMemcpy(e5.data(), b->energy, e5.size() * sizeof(double), cudaMemcpyDeviceToHost), "read energy");
+    }
     for (int r = 0; r < b->R; ++r) {
         Job &j = s->jobs[s->resident[r]];
         const int code = engine_status(b, ctr, r);
