@@ -446,7 +446,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "N": w.N, "P": w.P, "Gamma": w.Gamma, "kappa": w.kappa,
-                       "r_c_over_a": w.r_c / w.a_ws, "ensemble": w.ensemble, "integrator": "fp64",
+                       "r_c_over_a": w.r_c / w.a_ws, "ensemble": w.ensemble, "integrator": "fp32 increments, fp64 state",
                        "l2": "inputs larger than L2 (state + records > 129 MB)", "parallelism": f"replicas{ws}"}}
     sog = R.rbsog_build_sog(w.a_ws / w.kappa, w.r_c, w.sog_eps)
     rf = roofline(res["profile"], w, 10, pk, sog["M1"] + sog["M2"] + 1)
