@@ -152,19 +152,24 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
             R.rbsog_profile(ctx, False)
         # end to end through the C ABI with pinned host buffers: every step uploads the
         # integrator state (r, v and the forces at r), takes one step and reads the new
-        # state back into the same buffers, which the next step uploads
+        # state back into the same buffers, which the next step uploads.  The FP32 build
+        # moves its forces as FP32 (the values it computes), r and v as FP64.
         if e2e_steps:
+            f32 = precision == R.RBSOG_FP32
+            fdt = torch.float32 if f32 else torch.float64
+            set_sf = R.rbsog_set_state_forces_f32 if f32 else R.rbsog_set_state_forces
+            get_f = R.rbsog_get_forces_f32 if f32 else R.rbsog_get_forces
             hr = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
             hv = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
-            hF = torch.empty((w.N, 3), dtype=torch.float64, pin_memory=True)
+            hF = torch.empty((w.N, 3), dtype=fdt, pin_memory=True)
             R.rbsog_get_state(ctx, hr, hv, stream=stream)
-            R.rbsog_get_forces(ctx, hF, stream=stream)
+            get_f(ctx, hF, stream=stream)
 
             def e2e_step():
-                R.rbsog_set_state_forces(ctx, hr, hv, hF, stream=stream)
+                set_sf(ctx, hr, hv, hF, stream=stream)
                 R.rbsog_step(ctx, 1, stream=stream)
                 R.rbsog_get_state(ctx, hr, hv, stream=stream)
-                R.rbsog_get_forces(ctx, hF, stream=stream)
+                get_f(ctx, hF, stream=stream)
 
             e2e_step()
             torch.cuda.synchronize(dev)
@@ -174,8 +179,12 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
             torch.cuda.synchronize(dev)
             out["e2e_s"] = time.perf_counter() - t0
             out["e2e_steps"] = e2e_steps
-            out["e2e_h2d"] = 3 * w.N * 3 * 8
-            out["e2e_d2h"] = 3 * w.N * 3 * 8
+            nbytes = hr.numel() * hr.element_size() + hv.numel() * hv.element_size() + hF.numel() * hF.element_size()
+            out["e2e_h2d"] = nbytes
+            out["e2e_d2h"] = nbytes
+            out["e2e_path"] = (f"{set_sf.__name__}(host r, v FP64; F {'FP32' if f32 else 'FP64'}) + rbsog_step(1) + "
+                               f"rbsog_get_state(host r, v) + {get_f.__name__}(host F), pinned buffers, each step's "
+                               "outputs the next step's inputs (one force evaluation per step)")
     finally:
         R.rbsog_free(ctx)
     return out
@@ -456,9 +465,7 @@ def main():
     line["gpu_launches"] = KERNELS_PER_STEP * args.steps
     e2e_rate = w.N * res["e2e_steps"] / res["e2e_s"]
     line["e2e"] = {"value": e2e_rate, "unit": "particle-steps/s", "h2d_bytes_per_step": res["e2e_h2d"],
-                   "d2h_bytes_per_step": res["e2e_d2h"], "path": "rbsog_set_state_forces(host r, v, F) + "
-                   "rbsog_step(1) + rbsog_get_state(host r, v) + rbsog_get_forces(host F), pinned buffers, "
-                   "each step's outputs the next step's inputs (one force evaluation per step)"}
+                   "d2h_bytes_per_step": res["e2e_d2h"], "path": res["e2e_path"]}
     if not args.no_batch:
         line["batched"] = batched_sweep(torch, R, args.steps, max(3, args.warmup))
     if not args.no_serve:

@@ -145,6 +145,16 @@ int rbsog_set_state_forces(rbsog_ctx *ctx, const double *r, const double *v, con
  * rbsog_set_state.  Synchronous. */
 int rbsog_get_forces(rbsog_ctx *ctx, double *F, void *stream);
 
+/* FP32 forms of the two calls above, for precision RBSOG_FP32 only (RBSOG_EINVAL for the
+ * FP64 build, or for ctx NULL).  That build computes and keeps the forces in FP32, so
+ * F ([N][3] floats, caller's order, host or device) carries the same values in half the
+ * bytes: a loop through the host that moves F this way follows the same trajectory, bit
+ * for bit, as one that moves it in FP64.  rbsog_set_state_forces_f32 with F NULL is
+ * rbsog_set_state; it is enqueued on stream.  rbsog_get_forces_f32 fails as
+ * rbsog_get_forces does and is synchronous. */
+int rbsog_set_state_forces_f32(rbsog_ctx *ctx, const double *r, const double *v, const float *F, void *stream);
+int rbsog_get_forces_f32(rbsog_ctx *ctx, float *F, void *stream);
+
 /* Forces at the current positions (Eq. 55 with the far part estimated by Eq. 60)
  * from one fresh draw of P modes (or the set injected by rbsog_set_ksample) into
  * F ([N][3], host or device; NULL = keep internal only).  If e is not NULL the

@@ -483,6 +483,24 @@ __global__ void __launch_bounds__(256) k_get_forces(State rest, const void *F, u
         F_out[u + d] = PREC == 1 ? f2d_int(((const float *)F)[(size_t)d * N + k]) : ((const double *)F)[(size_t)d * N + k];
 }
 
+// FP32 forms for the FP32 build, whose forces are FP32 values: no conversion either way.
+__global__ void __launch_bounds__(256) k_set_forces_f32(const float *F_in, float *F, uint32_t N, DevCounters *ctr) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) F[(size_t)d * N + k] = F_in[3 * (size_t)k + d];
+    }
+    if (k == 0) ctr->fvalid = 1;
+}
+
+__global__ void __launch_bounds__(256) k_get_forces_f32(State rest, const float *F, uint32_t N, float *F_out) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const size_t u = 3 * (size_t)rest.id[k];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) F_out[u + d] = F[(size_t)d * N + k];
+}
+
 __global__ void __launch_bounds__(256) k_get_state(State rest, uint32_t N, double *r_out, double *v_out) {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < N) get_state_body(rest, 0, k, r_out, v_out);
@@ -558,6 +576,14 @@ void launch_set_forces(int prec, const double *F_in, void *F, uint32_t N, DevCou
     const unsigned nb = blocks_for(N > 0 ? N : 1, 256);
     if (prec == 1) k_set_forces<1><<<nb, 256, 0, st>>>(F_in, F, N, ctr);
     else k_set_forces<0><<<nb, 256, 0, st>>>(F_in, F, N, ctr);
+}
+
+void launch_set_forces_f32(const float *F_in, float *F, uint32_t N, DevCounters *ctr, cudaStream_t st) {
+    k_set_forces_f32<<<blocks_for(N > 0 ? N : 1, 256), 256, 0, st>>>(F_in, F, N, ctr);
+}
+
+void launch_get_forces_f32(State rest, const float *F, uint32_t N, float *F_out, cudaStream_t st) {
+    k_get_forces_f32<<<blocks_for(N, 256), 256, 0, st>>>(rest, F, N, F_out);
 }
 
 void launch_get_forces(int prec, State rest, const void *F, uint32_t N, double *F_out, cudaStream_t st) {

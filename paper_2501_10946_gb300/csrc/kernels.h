@@ -67,6 +67,8 @@ void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cuda
 void launch_set_forces(int prec, const double *F_in, void *F, uint32_t N, DevCounters *ctr, cudaStream_t st);
 // the SoA forces of the rest order into F_out ([N][3] doubles, caller order)
 void launch_get_forces(int prec, State rest, const void *F, uint32_t N, double *F_out, cudaStream_t st);
+void launch_set_forces_f32(const float *F_in, float *F, uint32_t N, DevCounters *ctr, cudaStream_t st);
+void launch_get_forces_f32(State rest, const float *F, uint32_t N, float *F_out, cudaStream_t st);
 
 // ---- sampler and normalisation (k_sample.cu) ----
 // A mixture of separable components: component c has weight mix and per-axis alias

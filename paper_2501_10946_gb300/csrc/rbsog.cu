@@ -694,6 +694,36 @@ int rbsog_get_forces(rbsog_ctx *c, double *F, void *stream) {
     return check_device_errors(c);
 }
 
+int rbsog_set_state_forces_f32(rbsog_ctx *c, const double *r, const double *v, const float *F, void *stream) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    if (c->prec != RBSOG_FP32) return fail(c, RBSOG_EINVAL, "FP32 forces need precision RBSOG_FP32");
+    if (int code = rbsog_set_state(c, r, v, stream)) return code;
+    if (!F) return RBSOG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *Fd = F;
+    if (!is_device_ptr(F)) {
+        CK(cudaMemcpyAsync(c->stage_c, F, 3 * (size_t)c->N * sizeof(float), cudaMemcpyDefault, st), "copy F");
+        Fd = (const float *)c->stage_c;
+    }
+    launch_set_forces_f32(Fd, (float *)c->F, c->N, c->ctr, st);
+    CK(cudaGetLastError(), "set forces");
+    c->force_valid = true;
+    return RBSOG_OK;
+}
+
+int rbsog_get_forces_f32(rbsog_ctx *c, float *F, void *stream) {
+    if (!c || !F) return fail(c, RBSOG_EINVAL, "ctx or F is NULL");
+    if (c->prec != RBSOG_FP32) return fail(c, RBSOG_EINVAL, "FP32 forces need precision RBSOG_FP32");
+    if (!c->force_valid) return fail(c, RBSOG_EINVAL, "no forces at the current state yet");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *Fd = is_device_ptr(F) ? F : (float *)c->stage_c;
+    launch_get_forces_f32(c->rest, (const float *)c->F, c->N, Fd, st);
+    CK(cudaGetLastError(), "get forces");
+    if (Fd != F) CK(cudaMemcpyAsync(F, Fd, 3 * (size_t)c->N * sizeof(float), cudaMemcpyDefault, st), "copy F out");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    return check_device_errors(c);
+}
+
 int rbsog_get_state(rbsog_ctx *c, double *r, double *v, uint64_t *step, void *stream) {
     if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
     cudaStream_t st = (cudaStream_t)stream;

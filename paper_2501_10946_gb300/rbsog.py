@@ -65,7 +65,7 @@ class RbsogError(RuntimeError):
 
 
 _lib = None
-EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_set_state_forces", "rbsog_get_forces", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
+EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_set_state_forces", "rbsog_get_forces", "rbsog_set_state_forces_f32", "rbsog_get_forces_f32", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
            "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog",
            "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_rho_noalloc",
            "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
     L.rbsog_get_state.argtypes = [vp, vp, vp, C.POINTER(C.c_uint64), vp]
     L.rbsog_set_state_forces.argtypes = [vp, vp, vp, vp, vp]
     L.rbsog_get_forces.argtypes = [vp, vp, vp]
+    L.rbsog_set_state_forces_f32.argtypes = [vp, vp, vp, vp, vp]
+    L.rbsog_get_forces_f32.argtypes = [vp, vp, vp]
     L.rbsog_forces.argtypes = [vp, vp, C.POINTER(rbsog_energy), vp]
     L.rbsog_forces_split.argtypes = [vp, vp, vp, C.POINTER(rbsog_energy), vp]
     L.rbsog_step.argtypes = [vp, i32, C.POINTER(rbsog_energy), vp]
@@ -203,6 +205,16 @@ def rbsog_set_state_forces(ctx, r, v=None, F=None, stream=None):
 
 def rbsog_get_forces(ctx, F, stream=None):
     _check(ctx, load().rbsog_get_forces(ctx, _ptr(F), _stream(stream)))
+
+
+def rbsog_set_state_forces_f32(ctx, r, v=None, F=None, stream=None):
+    """F: [N][3] float32 (FP32 build only)."""
+    _check(ctx, load().rbsog_set_state_forces_f32(ctx, _ptr(r), _ptr(v), _ptr(F), _stream(stream)))
+
+
+def rbsog_get_forces_f32(ctx, F, stream=None):
+    """F: [N][3] float32 (FP32 build only)."""
+    _check(ctx, load().rbsog_get_forces_f32(ctx, _ptr(F), _stream(stream)))
 
 
 def rbsog_forces(ctx, F=None, energy: bool = False, stream=None):

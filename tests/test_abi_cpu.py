@@ -69,7 +69,9 @@ def test_state_entry_points_reject_a_null_context():
     """The state and force entry points check their context and pointers on the host."""
     F = np.zeros((4, 3))
     calls = [lambda: R.rbsog_set_state(None, F, F), lambda: R.rbsog_set_state_forces(None, F, F, F),
-             lambda: R.rbsog_get_state(None, F, F), lambda: R.rbsog_get_forces(None, F)]
+             lambda: R.rbsog_get_state(None, F, F), lambda: R.rbsog_get_forces(None, F),
+             lambda: R.rbsog_set_state_forces_f32(None, F, F, F.astype(np.float32)),
+             lambda: R.rbsog_get_forces_f32(None, F.astype(np.float32))]
     for call in calls:
         with pytest.raises(R.RbsogError, match="EINVAL"):
             call()

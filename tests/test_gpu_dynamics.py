@@ -153,6 +153,54 @@ def test_host_round_trip_with_forces_follows_the_device_trajectory(prec, ensembl
             assert np.array_equal(v, dev[s][1]), s
 
 
+@pytest.mark.parametrize("ensemble", ["nve", "langevin"])
+def test_fp32_forces_round_trip_follows_the_device_trajectory(ensemble):
+    """The FP32 build's forces are FP32 values: rbsog_get_forces_f32 returns exactly what
+    rbsog_get_forces does, and a host loop that moves F as FP32 follows the
+    device-resident trajectory bit for bit."""
+    w = workload(700, 8.5, kappa=1.0, Gamma=1.0, P=48, seed=53, dt=0.002, ensemble=ensemble)
+    r0, v0 = W.positions(w), W.velocities(w)
+    n = 4
+    dev = []
+    with Ctx(w, R.RBSOG_FP32) as c:
+        R.rbsog_set_state(c.h, r0, v0)
+        for _ in range(n):
+            R.rbsog_step(c.h, 1)
+            r, v = np.zeros((w.N, 3)), np.zeros((w.N, 3))
+            R.rbsog_get_state(c.h, r, v)
+            dev.append((r, v))
+    with Ctx(w, R.RBSOG_FP32) as c:
+        R.rbsog_set_state(c.h, r0, v0)
+        F = np.zeros((w.N, 3), dtype=np.float32)
+        with pytest.raises(R.RbsogError):
+            R.rbsog_get_forces_f32(c.h, F)          # no forces at an uploaded state yet
+        R.rbsog_forces(c.h)
+        R.rbsog_get_forces_f32(c.h, F)
+        F64 = np.zeros((w.N, 3))
+        R.rbsog_get_forces(c.h, F64)
+        assert np.array_equal(F.astype(np.float64), F64)
+        r, v = r0.copy(), v0.copy()
+        for s in range(n):
+            R.rbsog_set_state_forces_f32(c.h, r, v, F)
+            R.rbsog_step(c.h, 1)
+            R.rbsog_get_state(c.h, r, v)
+            R.rbsog_get_forces_f32(c.h, F)
+            assert np.array_equal(r, dev[s][0]), s
+            assert np.array_equal(v, dev[s][1]), s
+
+
+def test_fp32_force_calls_refuse_the_fp64_build():
+    w = workload(300, 6.5, P=16, seed=55)
+    F = np.zeros((w.N, 3), dtype=np.float32)
+    with Ctx(w, R.RBSOG_FP64) as c:
+        R.rbsog_set_state(c.h, W.positions(w), W.velocities(w))
+        R.rbsog_forces(c.h)
+        for call in (lambda: R.rbsog_get_forces_f32(c.h, F),
+                     lambda: R.rbsog_set_state_forces_f32(c.h, W.positions(w), W.velocities(w), F)):
+            with pytest.raises(R.RbsogError, match="EINVAL"):
+                call()
+
+
 @pytest.mark.parametrize("prec", [R.RBSOG_FP64, R.RBSOG_FP32], ids=["fp64", "fp32"])
 def test_get_forces_returns_the_last_evaluation(prec):
     """rbsog_get_forces gives, in the caller's order, the forces that rbsog_forces returned."""
