@@ -151,7 +151,9 @@ int rbsog_get_forces(rbsog_ctx *ctx, double *F, void *stream);
  * bytes: a loop through the host that moves F this way follows the same trajectory, bit
  * for bit, as one that moves it in FP64.  rbsog_set_state_forces_f32 with F NULL is
  * rbsog_set_state; it is enqueued on stream.  rbsog_get_forces_f32 fails as
- * rbsog_get_forces does and is synchronous. */
+ * rbsog_get_forces does and is synchronous.  F is taken in the caller's particle order:
+ * the state upload in the same call resets the internal order to the caller's, and the
+ * forces are stored in that order before the next step sorts particles into cells. */
 int rbsog_set_state_forces_f32(rbsog_ctx *ctx, const double *r, const double *v, const float *F, void *stream);
 int rbsog_get_forces_f32(rbsog_ctx *ctx, float *F, void *stream);
 
@@ -168,7 +170,9 @@ int rbsog_forces_split(rbsog_ctx *ctx, double *F_near, double *F_far, rbsog_ener
 /* Advance nsteps >= 0 steps of Algorithm 2 (sample, far force, near force,
  * integrate).  The step sequence is captured once as a CUDA graph (on an internal
  * stream) and replayed on `stream`.  If e is not NULL the energies after the last step are written to *e
- * and the call is synchronous. */
+ * and the call is synchronous.  The energies are those of the last force evaluation, so
+ * with nsteps = 0 right after rbsog_set_state or rbsog_set_state_forces(_f32) (no
+ * evaluation at the uploaded state yet) an energy request fails with RBSOG_EINVAL. */
 int rbsog_step(rbsog_ctx *ctx, int32_t nsteps, rbsog_energy *e, void *stream);
 
 /* Inject the next force evaluation's modes: m_host is P triples (m_x, m_y, m_z) of
@@ -202,7 +206,9 @@ int rbsog_get_sog(rbsog_ctx *ctx, double *h, double *t0, int32_t *M1, int32_t *M
  * kernels eagerly (no graph) and record CUDA events on the launching stream around
  * each of the RBSOG_NPROF groups named by rbsog_profile_name: bin (integrator first
  * half + cell binning), scan, sort (scatter + per-cell sort), gather, sample, near,
- * rho, rho_final, far (gather of Eq. 60 + closing half kick), energy.  enable = 0
+ * rho, rho_final, far (gather of Eq. 60 + closing half kick), close (the one-thread
+ * kernel that ends an evaluation: step counter and forces-valid flag; the energy
+ * reduction itself runs only when energies are read).  enable = 0
  * restores graph replay.  Either call discards collected timings.  Synchronous. */
 #define RBSOG_NPROF 10
 int rbsog_profile(rbsog_ctx *ctx, int32_t enable);
@@ -292,7 +298,9 @@ int rbsog_batch_forces(rbsog_batch *b, double *F, rbsog_energy *e, void *stream)
 
 /* Advance every system nsteps >= 0 steps (graph captured once on an internal stream,
  * replayed on stream).  If e is not NULL, R energy records after the last step are
- * written and the call is synchronous. */
+ * written and the call is synchronous; with nsteps = 0 right after
+ * rbsog_batch_set_state (no evaluation at the uploaded state yet) that fails with
+ * RBSOG_EINVAL. */
 int rbsog_batch_step(rbsog_batch *b, int32_t nsteps, rbsog_energy *e, void *stream);
 
 /* Inject the next evaluation's modes for every system: sum(P) triples, host, not

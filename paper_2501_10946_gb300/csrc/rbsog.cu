@@ -61,6 +61,7 @@ struct rbsog_ctx {
     cudaEvent_t ev_fork = nullptr, ev_bin = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
     bool force_valid = false;
+    bool energy_valid = false;     // the energy partials belong to the current state
     SamplerTables tab{};
     // profiling: events around each kernel group of eager force evaluations
     bool prof = false;
@@ -408,7 +409,7 @@ int build_sampler(rbsog_ctx *c, const HostSystem &hs) {
 }
 
 const char *kProfNames[RBSOG_NPROF] = {"bin", "scan", "sort", "gather", "sample", "near", "rho", "rho_final",
-                                       "far", "energy"};
+                                       "far", "close"};
 
 // Record a profiling boundary on st (no-op unless profiling); returns the event index.
 size_t prof_mark(rbsog_ctx *c, cudaStream_t st) {
@@ -511,6 +512,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     { ProfScope ps(c, st, 9); launch_close_eval(c->ctr, advance, st); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    c->energy_valid = true;
     return RBSOG_OK;
 }
 
@@ -526,6 +528,8 @@ int check_device_errors(rbsog_ctx *c) {
 // The energies of the last force evaluation: its near, kinetic and per-mode partials
 // reduced in a fixed order (k_energy), then read back.  Synchronous.
 int read_energy(rbsog_ctx *c, rbsog_energy *e, cudaStream_t st) {
+    if (!c->energy_valid)
+        return fail(c, RBSOG_EINVAL, "no force evaluation since the last state upload: no energies to read");
     EnergyArgs ea{};
     ea.U_part = c->U_part; ea.nU = c->nU; ea.K_part = c->K_part; ea.nK = c->nK; ea.Ufar = c->Ufar;
     ea.nUfar = c->p.P;
@@ -664,6 +668,7 @@ int rbsog_set_state(rbsog_ctx *c, const double *r, const double *v, void *stream
     launch_set_state(rd, vd, c->q_user, c->m_user, c->rest, c->N, c->box, c->ctr, st);
     CK(cudaGetLastError(), "set_state");
     c->force_valid = false;
+    c->energy_valid = false;
     return RBSOG_OK;
 }
 

@@ -827,6 +827,8 @@ int rbsog_batch_step(rbsog_batch *b, int32_t nsteps, rbsog_energy *e, void *stre
         b->force_valid = true;
     }
     if (int code = engine_launch_steps(b, nsteps, st)) return code;
+    if (e && !b->force_valid)
+        return engine_fail(b, RBSOG_EINVAL, "no force evaluation since the last state upload: no energies to read");
     if (e) return read_energies(b, e, st);
     return RBSOG_OK;
 }

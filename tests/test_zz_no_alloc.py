@@ -15,7 +15,8 @@ from paper_2501_10946_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("N,L,P", [(20000, 27.0, 200), (3000, 14.0, 700), (500, 8.0, 40)])
+# (12000, 1724): 152 blocks x 1724 modes = 262048 of the 262144 slots, four modes per lane
+@pytest.mark.parametrize("N,L,P", [(20000, 27.0, 200), (3000, 14.0, 700), (500, 8.0, 40), (12000, 24.0, 1724)])
 def test_rho_noalloc_matches_the_context_structure_factor(N, L, P):
     torch = require_gpu()
     w = workload(N, L, P=P, seed=N)
@@ -40,9 +41,10 @@ def test_rho_noalloc_matches_the_context_structure_factor(N, L, P):
         assert np.max(np.abs(got - ref)) <= FP32_TOL * scale, (call, np.max(np.abs(got - ref)) / scale)
 
 
-def test_rho_noalloc_rejects_requests_beyond_its_scratch():
+@pytest.mark.parametrize("N,P", [(20000, 4096), (12000, 1725)])
+def test_rho_noalloc_rejects_requests_beyond_its_scratch(N, P):
+    """P = 1725 at 152 blocks needs 262200 slots, one mode more than the array holds."""
     torch = require_gpu()
-    N, P = 20000, 4096
     rd = torch.zeros((N, 3), device="cuda", dtype=torch.float64)
     qd = torch.ones(N, device="cuda", dtype=torch.float64)
     md = torch.ones((P, 3), device="cuda", dtype=torch.int32)
