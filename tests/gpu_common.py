@@ -12,6 +12,48 @@ from paper_2501_10946_gb300 import workloads as W
 
 FP64_TOL = 1e-12
 FP32_TOL = 1e-5
+# Floor of the per-particle relative force error, as a fraction of the RMS force: a
+# particle whose force nearly cancels has no meaningful relative error of its own.
+PP_FLOOR = 1e-2
+
+
+def force_errors(got, ref):
+    """The force-error metrics of the parity tests: the relative L2 error over all
+    particles, sqrt(sum |dF|^2 / sum |F|^2), and the largest per-particle relative error
+    max_i |dF_i| / (|F_i| + PP_FLOOR rms|F|)."""
+    got = np.asarray(got, dtype=np.float64).reshape(-1, 3)
+    ref = np.asarray(ref, dtype=np.float64).reshape(-1, 3)
+    d = np.linalg.norm(got - ref, axis=1)
+    n = np.linalg.norm(ref, axis=1)
+    rms = float(np.sqrt(np.mean(n * n))) if n.size else 0.0
+    rel = core.rel_l2(got, ref)
+    pp = float(np.max(d / (n + PP_FLOOR * rms))) if rms > 0 else float(np.max(d, initial=0.0))
+    return rel, pp
+
+
+def check_forces(got, ref, tol, what=""):
+    """Relative L2 and per-particle relative error (with the floor above) both <= tol."""
+    rel, pp = force_errors(got, ref)
+    assert rel <= tol and pp <= tol, (what, {"rel_l2": rel, "per_particle_max": pp, "tol": tol})
+    return rel, pp
+
+
+def check_rho(got, ref, q, tol, what="rho"):
+    """Every mode: |rho_gpu - rho_ref| <= tol (|rho_ref| + sqrt(sum q^2)); sqrt(sum q^2) is
+    the size of rho for uncorrelated phases, the scale of a rounding error that grows
+    like a random walk over the particles."""
+    got = np.asarray(got, dtype=np.float64).reshape(-1, 2)
+    ref = np.asarray(ref, dtype=np.float64).reshape(-1, 2)
+    scale = np.hypot(ref[:, 0], ref[:, 1]) + float(np.sqrt(np.sum(np.asarray(q, dtype=np.float64) ** 2)))
+    err = float(np.max(np.hypot(got[:, 0] - ref[:, 0], got[:, 1] - ref[:, 1]) / scale))
+    assert err <= tol, (what, err, tol)
+    return err
+
+
+def check_energy(got, ref, tol, what=""):
+    err = abs(got - ref) / abs(ref)
+    assert err <= tol, (what, got, ref, err, tol)
+    return err
 
 
 def require_gpu():

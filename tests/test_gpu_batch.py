@@ -5,7 +5,7 @@ passes), ensemble, and near-field path (one box too small for the tiled kernel).
 import numpy as np
 import pytest
 
-from gpu_common import FP32_TOL, Ctx, modes_for, oracle_forces, require_gpu, workload
+from gpu_common import FP32_TOL, Ctx, check_energy, check_forces, modes_for, oracle_forces, require_gpu, workload
 from oracle import core
 from paper_2501_10946_gb300 import rbsog as R
 from paper_2501_10946_gb300 import workloads as W
@@ -93,8 +93,9 @@ def test_batch_forces_match_single_contexts_and_the_oracle():
         assert core.rel_l2(Fi, Fs) <= FP32_TOL, i
         assert abs(e[i]["U_far"] - es["U_far"]) <= FP32_TOL * abs(es["U_far"]), i
         Ft, _, _, eo, _ = oracle_forces(w, ri, W.charges(w), modes[i])
-        assert core.rel_l2(Fi, Ft) <= FP32_TOL, i
-        assert abs(e[i]["U_near"] - eo["U_N"]) <= 10 * FP32_TOL * abs(eo["U_N"]), i
+        check_forces(Fi, Ft, FP32_TOL, ("system", i))
+        check_energy(e[i]["U_near"], eo["U_N"], FP32_TOL, ("U_near", i))
+        check_energy(e[i]["U_far"], eo["U_F"], FP32_TOL, ("U_far", i))
 
 
 def test_batch_draws_the_modes_of_single_contexts():

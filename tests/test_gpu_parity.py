@@ -1,12 +1,15 @@
 """GPU parity through the C ABI: every step of the force path against the FP64 oracle on
-the same seeded inputs and the same injected k-set.  FP64 build: relative L2 <= 1e-12;
-FP32 build: <= 1e-5; cell lists bit-exact."""
+the same seeded inputs and the same injected k-set.  FP64 build: 1e-12; FP32 build: 1e-5,
+applied to the relative L2 error of the forces, to every particle's relative force error
+(with a floor of 1e-2 of the RMS force), to every mode of rho (relative to |rho_l| +
+sqrt(sum q^2)) and to each energy; cell lists bit-exact."""
 import math
 
 import numpy as np
 import pytest
 
-from gpu_common import FP32_TOL, FP64_TOL, Ctx, modes_for, oracle_forces, oracle_sog, require_gpu, workload
+from gpu_common import (FP32_TOL, FP64_TOL, Ctx, check_energy, check_forces, check_rho, modes_for, oracle_forces,
+                        oracle_sog, require_gpu, workload)
 from oracle import core
 from paper_2501_10946_gb300 import rbsog as R
 from paper_2501_10946_gb300 import workloads as W
@@ -48,15 +51,15 @@ def test_small_workload_parity(prec):
     tol = TOL[prec]
     # S sums ~1e5 lattice terms in a different order on each side
     assert abs(g["sog"]["S"] - S_) <= 1e-11 * S_
-    assert core.rel_l2(g["Fn"], Fn) <= tol
-    assert core.rel_l2(g["Ff"], Ff) <= tol
-    assert core.rel_l2(g["Fn"] + g["Ff"], Ft) <= tol
+    check_forces(g["Fn"], Fn, tol, "near")
+    check_forces(g["Ff"], Ff, tol, "far")
+    check_forces(g["Fn"] + g["Ff"], Ft, tol, "total")
     rho = core.rho(r, q, w.box, modes)
-    assert np.max(np.abs(g["rho"] - rho)) <= tol * np.max(np.abs(rho))
+    check_rho(g["rho"], rho, q, tol)
     coef = core.rb_coef(modes, w.box, oracle_sog(w), w.kT, float(np.sum(q * q)), S_)
     assert np.max(np.abs(g["coef"] - coef) / coef) <= 1e-11
     for k_gpu, k_or in (("U_near", "U_N"), ("U_far", "U_F"), ("U_self", "U_self")):
-        assert abs(g["e"][k_gpu] - e[k_or]) <= max(tol, 1e-12) * abs(e[k_or]) * 10, (k_gpu, g["e"][k_gpu], e[k_or])
+        check_energy(g["e"][k_gpu], e[k_or], tol, k_gpu)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -105,10 +108,14 @@ def test_edge_cases(prec, case):
     g = run_forces(w, prec, r, modes, q=q)
     Ft, Fn, Ff, e, S_ = oracle_forces(w, r, qq, modes, near="images" if case == "one_cell" else "cells")
     tol = TOL[prec]
-    assert core.rel_l2(g["Fn"] + g["Ff"], Ft) <= tol
-    assert core.rel_l2(g["Ff"], Ff) <= tol
+    check_forces(g["Fn"] + g["Ff"], Ft, tol, "total")
+    check_forces(g["Ff"], Ff, tol, "far")
     if np.any(Fn != 0):
-        assert core.rel_l2(g["Fn"], Fn) <= tol
+        check_forces(g["Fn"], Fn, tol, "near")
+    check_rho(g["rho"], core.rho(r, qq, w.box, modes), qq, tol)
+    for k_gpu, k_or in (("U_near", "U_N"), ("U_far", "U_F")):
+        if e[k_or] != 0:
+            check_energy(g["e"][k_gpu], e[k_or], tol, k_gpu)
 
 
 @pytest.mark.parametrize("nc", [3, 4, 5, 6, 7, 9, 12])
@@ -122,7 +129,7 @@ def test_near_field_all_tile_geometries(nc):
     g = run_forces(w, R.RBSOG_FP32, r, modes_for(w, w.P, 1))
     assert list(g["cells"][0]) == [nc] * 3
     Ft, Fn, Ff, e, S_ = oracle_forces(w, r, W.charges(w), modes_for(w, w.P, 1))
-    assert core.rel_l2(g["Fn"], Fn) <= FP32_TOL
+    check_forces(g["Fn"], Fn, FP32_TOL, "near")
     # a missing or extra pair shows up as an error of the order of that pair's force; FP32
     # rounding stays orders of magnitude below 1e-3 of the force scale
     rms = float(np.sqrt(np.mean(np.sum(Fn * Fn, axis=1))))
@@ -161,12 +168,28 @@ def test_scaled_strong_coupling_bcc(prec):
     modes = modes_for(w, w.P, 5)
     g = run_forces(w, prec, r, modes)
     Ft, Fn, Ff, e, S_ = oracle_forces(w, r, W.charges(w), modes)
-    assert core.rel_l2(g["Fn"] + g["Ff"], Ft) <= TOL[prec]
+    check_forces(g["Fn"] + g["Ff"], Ft, TOL[prec], "total")
+    check_forces(g["Fn"], Fn, TOL[prec], "near")
+    check_energy(g["e"]["U_near"], e["U_N"], TOL[prec], "U_near")
+
+
+def cell_rows(r, box, r_c, rows):
+    """Particles of whole rows of the cell list: (c_y, c_z) fixed, every c_x."""
+    nc = core.n_cells(box, r_c)
+    cell_of, _, _ = core.cell_list(r, box, nc)
+    cy = (cell_of // nc[0]) % nc[1]
+    cz = cell_of // (nc[0] * nc[1])
+    sel = np.zeros(len(r), dtype=bool)
+    for y, z in rows:
+        sel |= (cy == y) & (cz == z)
+    return np.nonzero(sel)[0]
 
 
 def test_full_size_uniform_fp32_sampled():
     """N=1e6 uniform, Gamma=0.1, kappa=2, r_c=3a, P=500 in the FP32 build: rho over all
-    particles and the total force on 256 sampled particles against the oracle."""
+    particles (every mode), and the total, near and far forces on three whole rows of the
+    cell list (one through the periodic corner, one through the middle, one on a face)
+    plus 256 sampled particles against the oracle."""
     w = W.cfg_large()
     r = W.positions(w)
     q = W.charges(w)
@@ -180,10 +203,14 @@ def test_full_size_uniform_fp32_sampled():
         rho_g = R.rbsog_get_rho(c.h, c.P)
         S_g = R.rbsog_get_sog(c.h)["S"]
     rho = core.rho(r, q, w.box, modes)
-    assert np.max(np.abs(rho_g - rho)) <= FP32_TOL * np.max(np.abs(rho))
-    idx = np.random.default_rng(0).choice(w.N, 256, replace=False)
+    check_rho(rho_g, rho, q, FP32_TOL)
+    nc = int(core.n_cells(w.box, w.r_c)[1])
+    rows = cell_rows(r, w.box, w.r_c, [(0, 0), (nc // 2, nc // 2), (nc - 1, nc // 3)])
+    assert len(rows) > 900
+    idx = np.unique(np.concatenate([rows, np.random.default_rng(0).choice(w.N, 256, replace=False)]))
     Ft, Fno, Ffo, e, S_ = oracle_forces(w, r, q, modes, idx=idx, rho=rho)
     # ~1e8 lattice terms summed in a different order on each side
     assert abs(S_g - S_) <= 1e-11 * S_
-    assert core.rel_l2(Fn[idx] + Ff[idx], Ft) <= FP32_TOL
-    assert core.rel_l2(Ff[idx], Ffo) <= FP32_TOL
+    check_forces(Fn[idx] + Ff[idx], Ft, FP32_TOL, "total")
+    check_forces(Fn[idx], Fno, FP32_TOL, "near")
+    check_forces(Ff[idx], Ffo, FP32_TOL, "far")
