@@ -1,12 +1,13 @@
 """GPU job server (rbsog_server_*): continuous batching of MD jobs.  Each job's result is
-bit-identical alone and in a mix where jobs join while others are mid-run, agrees with a
-single context within the FP32 tolerance, waits for memory when the arenas are full, and
-fails alone when its own cells overflow."""
+bit-identical alone and in a mix where jobs join while others are mid-run, agrees with the
+FP64 oracle's trajectory of that job and with a single context within the FP32 tolerance,
+waits for memory when the arenas are full, and fails alone when its own cells overflow."""
 import numpy as np
 import pytest
 
-from gpu_common import FP32_TOL, Ctx, require_gpu, workload
-from oracle import core
+from gpu_common import FP32_TOL, Ctx, oracle_sog, require_gpu, workload
+from oracle import core, integrate
+from oracle.sampler import ModeSampler
 from paper_2501_10946_gb300 import rbsog as R
 from paper_2501_10946_gb300 import workloads as W
 
@@ -73,6 +74,64 @@ def test_each_job_is_the_same_alone_and_in_the_mix():
         assert np.array_equal(r_a, r_m), i
         assert np.array_equal(v_a, v_m), i
         assert info_a["energy"]["total"] == info_m["energy"]["total"], i
+
+
+def oracle_job(w, nsteps):
+    """The oracle's run of one job (Algorithm 2): evaluation d uses the oracle sampler's
+    draw d from the job's seed, the integrator is the oracle's velocity Verlet or BAOAB
+    (step n keyed by the n + 1 evaluations before it).  Returns the final positions,
+    velocities and the energy terms of the last evaluation."""
+    r0, v0, q, m = W.positions(w), W.velocities(w), W.charges(w), W.masses(w)
+    sog = oracle_sog(w)
+    Q2 = float(np.sum(q * q))
+    S_ = core.S_sum(w.box, sog, w.kT, Q2)
+    ms = ModeSampler(sog, w.box, w.kT, Q2)
+    near = "cells" if min(core.n_cells(w.box, w.r_c)) >= 3 else "images"
+    st = {"d": 0, "e": None}
+
+    def force(x):
+        ks, _ = ms.draw(w.seed_k, st["d"], w.P)
+        st["d"] += 1
+        Ft, _, _, e = core.rb_forces(x, q, w.box, w.r_c, sog, ks, w.kT, S=S_, near=near)
+        st["e"] = e
+        return Ft
+
+    r, v = integrate.wrap(r0, w.box), v0.copy()
+    F = force(r)
+    for n in range(nsteps):
+        if w.ensemble == "langevin":
+            r, v, F = integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n + 1, force)
+        else:
+            r, v, F = integrate.vv_step(r, v, F, m, w.box, w.dt, force)
+    e = dict(st["e"])
+    e["kinetic"] = integrate.kinetic(v, m)
+    return r, v, e
+
+
+def test_served_jobs_match_the_oracle():
+    """Three jobs of different N, kappa, Gamma, P and ensemble, with two job slots and
+    two-step rounds, so the third is admitted while the others are mid-run: each job's
+    final positions, velocities and energies against the oracle's run of that job alone."""
+    js = [
+        (workload(1200, 10.5, kappa=1.2, Gamma=3.0, P=96, seed=151, dt=0.004, ensemble="langevin"), 5),
+        (workload(700, 8.5, kappa=2.2, Gamma=30.0, P=160, seed=153, dt=0.004), 3),
+        (workload(900, 9.5, kappa=0.6, Gamma=0.8, P=64, seed=155, dt=0.004), 4),
+    ]
+    out, stats = run_jobs(js, max_jobs=2, steps_per_round=2)
+    infos = [o[0] for o in out]
+    assert any(infos[k]["t_admit"] < infos[2]["t_admit"] < infos[k]["t_done"] for k in (0, 1))
+    for i, (w, n) in enumerate(js):
+        info, r, v = out[i]
+        assert info["status"] == R.RBSOG_JOB_DONE and info["steps_done"] == n
+        ro, vo, eo = oracle_job(w, n)
+        d = r - ro
+        L = np.asarray(w.box)
+        d -= L * np.round(d / L)
+        assert np.max(np.abs(d)) <= FP32_TOL * np.max(L), (i, np.max(np.abs(d)))
+        assert core.rel_l2(v, vo) <= FP32_TOL, (i, core.rel_l2(v, vo))
+        for k_gpu, k_or in (("U_near", "U_N"), ("U_far", "U_F"), ("U_self", "U_self"), ("kinetic", "kinetic")):
+            err = abs(info["energy"][k_gpu] - eo[k_or]) / abs(eo[k_or])
+            assert err <= FP32_TOL, (i, k_gpu, info["energy"][k_gpu], eo[k_or])
 
 
 def test_served_job_follows_a_single_context():
