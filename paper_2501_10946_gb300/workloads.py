@@ -44,6 +44,7 @@ class Workload:
     seed_k: int
     bcc_cells: int = 0
     bcc_sigma: float = 0.0   # displacement std in units of a
+    min_sep: float = 0.0     # uniform placement: minimum pair separation in units of a (0: none)
 
     @property
     def volume(self) -> float:
@@ -100,7 +101,10 @@ def positions(w: Workload) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(w.seed_pos))
     L = np.asarray(w.box, dtype=np.float64)
     if w.placement == "uniform":
-        return rng.uniform(0.0, 1.0, size=(w.N, 3)) * L
+        r = rng.uniform(0.0, 1.0, size=(w.N, 3)) * L
+        if w.min_sep > 0.0:
+            r = _separate(r, L, w.min_sep * w.a_ws, rng)
+        return r
     if w.placement == "bcc":
         nc = w.bcc_cells
         g = np.arange(nc, dtype=np.float64)
@@ -110,6 +114,26 @@ def positions(w: Workload) -> np.ndarray:
         lat = lat + rng.normal(0.0, w.bcc_sigma * w.a_ws, size=lat.shape)
         return np.mod(lat, L)
     raise ValueError(w.placement)
+
+
+def _separate(r: np.ndarray, L: np.ndarray, dmin: float, rng) -> np.ndarray:
+    """Uniform positions with no pair (minimum image) closer than dmin: every pair closer
+    than dmin gives up its higher-indexed particle, which is drawn again uniformly, until
+    no such pair is left.  At the densities used here (hard-sphere packing fraction below
+    2%) a few rounds suffice."""
+    from scipy.spatial import cKDTree
+    r = np.mod(r, L)
+    pairs = cKDTree(r, boxsize=L).query_pairs(dmin, output_type="ndarray")
+    for _ in range(200):
+        if len(pairs) == 0:
+            return r
+        redo = np.unique(np.max(pairs, axis=1))
+        r[redo] = np.mod(rng.uniform(0.0, 1.0, size=(len(redo), 3)) * L, L)
+        # only pairs with a redrawn particle can be new
+        near = cKDTree(r, boxsize=L).query_ball_point(r[redo], dmin)
+        pairs = np.asarray([(min(i, j), max(i, j)) for i, js in zip(redo.tolist(), near) for j in js if j != i],
+                           dtype=np.int64).reshape(-1, 2)
+    raise RuntimeError("minimum-separation placement did not converge")
 
 
 def velocities(w: Workload) -> np.ndarray:
@@ -149,7 +173,8 @@ def small_system(N: int, L: float, seed: int, charge_mix: bool = False):
 def cfg_replicas(R: int = 256, seed: int = 401, steps: int = 500) -> list:
     """Batched replica sweep: R independent YOCP systems at reduced density 1 (lengths in a),
     N log-uniform in [500, 5e4], kappa uniform in [0.1, 3], Gamma log-uniform in [0.1, 200],
-    P in {64, 128, 256}, r_c = 3a, SOG tolerance 1e-6, dt = 0.01, NVE, FP32 forces."""
+    P in {64, 128, 256}, r_c = 3a, SOG tolerance 1e-6, dt = 0.01, NVE, FP32 forces; uniform
+    positions with a minimum separation of 0.5a."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for i in range(R):
@@ -160,7 +185,7 @@ def cfg_replicas(R: int = 256, seed: int = 401, steps: int = 500) -> list:
         L = box_for_unit_a(N)
         s = seed * 1000 + 4 * i
         out.append(Workload(f"replica{i}_n{N}", N, (L, L, L), 1.0, kappa, Gamma, 3.0, 1e-6, P, 0.01, steps,
-                            "nve", 1.0, "uniform", s + 1, s + 2, s + 3))
+                            "nve", 1.0, "uniform", s + 1, s + 2, s + 3, min_sep=0.5))
     return out
 
 
@@ -168,7 +193,8 @@ def cfg_stream(n_jobs: int = 64, rate: float = 50.0, seed: int = 501) -> list:
     """Served request stream: n_jobs YOCP jobs with Poisson arrivals (mean `rate` per s),
     N log-uniform in [1e3, 2e5], kappa uniform in [0.2, 3], Gamma log-uniform in
     [0.5, 150], steps uniform in [100, 2000], P = 128, r_c = 3a, reduced density 1, NVE,
-    FP32 forces.  Returns [(Workload, nsteps, t_arrival_s)]."""
+    FP32 forces, uniform positions with a minimum separation of 0.5a.  Returns
+    [(Workload, nsteps, t_arrival_s)]."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     t = 0.0
@@ -182,6 +208,6 @@ def cfg_stream(n_jobs: int = 64, rate: float = 50.0, seed: int = 501) -> list:
         L = box_for_unit_a(N)
         s = seed * 1000 + 4 * i
         w = Workload(f"job{i}_n{N}", N, (L, L, L), 1.0, kappa, Gamma, 3.0, 1e-6, P, 0.01, nsteps, "nve", 1.0,
-                     "uniform", s + 1, s + 2, s + 3)
+                     "uniform", s + 1, s + 2, s + 3, min_sep=0.5)
         out.append((w, nsteps, t))
     return out
