@@ -32,13 +32,33 @@ from paper_2501_10946_gb300 import workloads as W  # noqa: E402
 
 METRIC = "RBSOG particle-steps/s at N=1e6"
 SMS = 152
-MUFU_PER_CLK_SM = 16            # sin/cos special-function results per clock per SM (measured 15.9)
+MUFU_PER_CLK_SM = 16            # sin/cos and rsqrt special-function results per clock per SM (measured 15.9)
+EX2_PER_CLK_SM = 32             # ex2 results per clock per SM (measured)
 FP32_PER_CLK_SM = 128           # FP32 lanes per SM
+NEAR_FP32_OPS_PER_PAIR = 25     # separation, r^2, Yukawa and Gaussian terms, force accumulation
 KERNELS_PER_STEP = 11
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the committed
-# full-set ncu capture at N = 1e6 of kernels unchanged since (profiles/near_rho_far_yocp_uniform_n1e6.md);
-# a kernel changed after its capture has no entry
-TRAFFIC = {"near": 16.665e6, "rho": 16.015e6, "far": 65.532e6}
+# DRAM bytes per launch of each kernel group from an ncu capture, with the SHA-256 of the
+# kernel's source file at capture time: a kernel whose source has changed since gets no
+# traffic figure.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_yocp_uniform_n1e6.txt")
+CSRC = os.path.join(ROOT, "paper_2501_10946_gb300", "csrc")
+
+
+def traffic_table():
+    """{group: bytes per launch} for the groups whose source is unchanged since capture."""
+    import hashlib
+    out = {}
+    if not os.path.exists(TRAFFIC_FILE):
+        return out
+    for line in open(TRAFFIC_FILE):
+        parts = line.split()
+        if len(parts) < 4 or line.startswith("#"):
+            continue
+        group, src, sha, nbytes = parts[:4]
+        path = os.path.join(CSRC, src)
+        if os.path.exists(path) and hashlib.sha256(open(path, "rb").read()).hexdigest() == sha:
+            out[group] = float(nbytes)
+    return out
 
 
 def peaks():
@@ -257,7 +277,7 @@ def percentile(x, q):
     return float(np.percentile(np.asarray(x, dtype=np.float64), q))
 
 
-def served_stream(torch, R, n_jobs=64, rate=50.0):
+def served_stream(torch, R, n_jobs=64, rate=50.0, plain=True):
     """Served request stream through the job server (continuous batching) against the
     plain form: the same jobs in arrival order, one rbsog context at a time."""
     js = W.cfg_stream(n_jobs, rate)
@@ -289,6 +309,8 @@ def served_stream(torch, R, n_jobs=64, rate=50.0):
                      "peak_resident_particles": stats["peak_particles"], "device_busy_s": stats["busy_s"],
                      "admission_setup_s": stats["setup_s"],
                      "form": "rbsog_server: continuous batching, 32-step rounds, up to 64 resident jobs"}
+    if not plain:
+        return out
     # plain: first come first served, one context per job (its own rbsog_init, which
     # builds the same SOG, sampler tables and S the server builds at admission)
     clock = 0.0
@@ -317,42 +339,60 @@ def served_stream(torch, R, n_jobs=64, rate=50.0):
     return out
 
 
-def near_work(w, mtot):
-    """Algorithmic FP32 work of one near-field launch (27-cell candidates and in-range pairs)
-    for a decomposition of mtot Gaussians."""
+def near_pairs(w):
+    """In-range pairs of one near-field launch, counted from both ends as the kernel
+    evaluates them: N (4 pi / 3) r_c^3 n."""
+    dens = w.N / w.volume
+    return w.N * (4.0 / 3.0) * math.pi * w.r_c ** 3 * dens
+
+
+def near_candidates(w):
+    """27-cell candidates of one launch: N x 27 x mean cell occupancy."""
     nc = [max(int(math.floor(L / w.r_c)), 1) for L in w.box]
     nc = [n if n >= 3 else 1 for n in nc]
-    ncell = nc[0] * nc[1] * nc[2]
-    dens = w.N / w.volume
-    candidates = w.N * 27.0 * w.N / ncell
-    pairs = w.N * (4.0 / 3.0) * math.pi * w.r_c ** 3 * dens
-    return 6.0 * candidates + (20.0 + 3.0 * mtot) * pairs
+    return w.N * 27.0 * w.N / (nc[0] * nc[1] * nc[2])
 
 
-def roofline(prof, w, steps_profiled, pk, mtot):
+def roofline(prof, w, pk, mtot):
     """Roofline of the dominant kernel group.  rho and far are bound by the special-function
-    unit (one sin and one cos per particle-mode pair); near by the FP32 pipe."""
+    unit (one sin and one cos per particle-mode pair).  near is counted on the method's own
+    work: the in-range pairs, each with 25 FP32 operations on the FP32 pipe and one rsqrt
+    plus 1 + M_tot ex2 on the special-function unit; the cell-list candidate tests are
+    reported apart, as overhead."""
     groups = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(groups, key=lambda k: groups[k][0])
     ms, n = groups[dom]
     avg_s = ms / n * 1e-3
     sm_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    clk = sm_mhz * 1e6
+    extra = {}
     if dom in ("rho", "far"):
         units = 2.0 * w.N * w.P
-        peak = SMS * MUFU_PER_CLK_SM * sm_mhz * 1e6 / 1e9
+        peak = SMS * MUFU_PER_CLK_SM * clk / 1e9
         basis = f"{SMS} SMs x {MUFU_PER_CLK_SM} MUFU/clk x {sm_mhz:.0f} MHz (sin+cos per particle-mode pair)"
     elif dom == "near":
-        units = near_work(w, mtot)
-        peak = SMS * FP32_PER_CLK_SM * sm_mhz * 1e6 / 1e9
-        basis = (f"{SMS} SMs x {FP32_PER_CLK_SM} FP32 lanes/clk x {sm_mhz:.0f} MHz (6 ops per 27-cell candidate, "
-                 f"20 + 3 M_tot per in-range pair)")
+        pairs = near_pairs(w)
+        units = NEAR_FP32_OPS_PER_PAIR * pairs
+        peak = SMS * FP32_PER_CLK_SM * clk / 1e9
+        basis = (f"{SMS} SMs x {FP32_PER_CLK_SM} FP32 lanes/clk x {sm_mhz:.0f} MHz; work = "
+                 f"{pairs / w.N:.1f} in-range pairs per particle x {NEAR_FP32_OPS_PER_PAIR} FP32 ops")
+        xu_s = pairs * (1.0 / MUFU_PER_CLK_SM + (1.0 + mtot) / EX2_PER_CLK_SM) / (SMS * clk)
+        extra["xu"] = {"frac": xu_s / avg_s, "basis": f"1 rsqrt at {MUFU_PER_CLK_SM}/clk/SM + {1 + mtot} ex2 at "
+                                                      f"{EX2_PER_CLK_SM}/clk/SM per in-range pair"}
+        cand = near_candidates(w)
+        extra["overhead"] = {"candidates_per_particle": cand / w.N, "pairs_per_particle": pairs / w.N,
+                             "filter_ops_per_candidate": 6,
+                             "frac_with_filter_ops": (units + 6.0 * cand) / avg_s / 1e9 / peak}
     else:
         units, peak, basis = None, None, ""
     achieved = units / avg_s / 1e9 if units else None
-    return {"kernel": dom, "bound": "alu", "unit": "Gop/s", "achieved": achieved, "peak": peak,
-            "frac": achieved / peak if achieved and peak else None, "traffic": TRAFFIC.get(dom) if w.N == 1_000_000 else None,
-            "peak_basis": basis, "avg_launch_ms": avg_s * 1e3,
-            "groups_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in groups.items()}}
+    traffic = traffic_table().get(dom) if w.N == 1_000_000 else None
+    out = {"kernel": dom, "bound": "alu", "unit": "Gop/s", "achieved": achieved, "peak": peak,
+           "frac": achieved / peak if achieved and peak else None, "traffic": traffic,
+           "peak_basis": basis, "avg_launch_ms": avg_s * 1e3,
+           "groups_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in groups.items()}}
+    out.update(extra)
+    return out
 
 
 def oracle_step_time(w, steps: int = 1, warmup: int = 0):
@@ -378,16 +418,45 @@ def oracle_step_time(w, steps: int = 1, warmup: int = 0):
         Ft, _, _, _ = core.rb_forces(x, q, w.box, w.r_c, sog, kset, w.kT, S=S_)
         return Ft
 
+    def step(r, v, F, n):
+        if w.ensemble == "langevin":
+            return integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n, force)
+        return integrate.vv_step(r, v, F, m, w.box, w.dt, force)
+
     F = force(r)
     n = 0
     for _ in range(warmup):
-        r, v, F = integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n, force)
+        r, v, F = step(r, v, F, n)
         n += 1
     t0 = time.perf_counter()
     for _ in range(steps):
-        r, v, F = integrate.baoab_step(r, v, F, m, w.box, w.dt, w.langevin_gamma, w.kT, w.seed_k, n, force)
+        r, v, F = step(r, v, F, n)
         n += 1
     return time.perf_counter() - t0, core.num_threads()
+
+
+def cpu_baseline(w):
+    """The FP64 oracle as it stands on this host's cores: 3 steps of the workload after one
+    warm-up step on every core; one step of the same state point at N = 1e5 on one core;
+    and the full 10-step N = 1000 FP64 workload (velocity Verlet) on every core."""
+    from oracle import core
+    secs, thr = oracle_step_time(w, 3, 1)
+    out = {"value": 3 * w.N / secs, "unit": "particle-steps/s", "cores": thr, "kind": "oracle",
+           "sample": f"3 FP64 oracle steps (after 1 warm-up step) of the N={w.N} workload, OpenMP on {thr} threads"}
+    w1 = W.scaled(w, min(100_000, w.N), name=w.name)
+    core.set_threads(1)
+    try:
+        s1, _ = oracle_step_time(w1, 1, 0)
+    finally:
+        core.set_threads(thr)
+    out["single_core"] = {"value": w1.N / s1, "unit": "particle-steps/s", "cores": 1,
+                          "sample": f"1 FP64 oracle step of the same state point at N={w1.N}"}
+    ws = W.cfg_small_fp64()
+    s2, _ = oracle_step_time(ws, ws.steps, 0)
+    out["small_full_run"] = {"value": ws.N * ws.steps / s2, "unit": "particle-steps/s", "cores": thr,
+                             "workload": ws.name, "steps": ws.steps,
+                             "sample": f"the whole {ws.steps}-step N={ws.N} FP64 velocity-Verlet run"}
+    return out
 
 
 # the reference arm's bounded sample: the same state point with 1e5 particles (the
@@ -406,6 +475,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=64,
+                    help="jobs of the served stream (the full stream of the served workload is 2000)")
+    ap.add_argument("--no-serve-plain", action="store_true",
+                    help="skip the one-context-per-job comparison of the served stream")
     args = ap.parse_args()
     ws, rank, local = dist_info()
     w = W.cfg_large(args.N)
@@ -458,7 +531,7 @@ def main():
                        "r_c_over_a": w.r_c / w.a_ws, "ensemble": w.ensemble, "integrator": "fp32 increments, fp64 state",
                        "l2": "inputs larger than L2 (state + records > 129 MB)", "parallelism": f"replicas{ws}"}}
     sog = R.rbsog_build_sog(w.a_ws / w.kappa, w.r_c, w.sog_eps)
-    rf = roofline(res["profile"], w, 10, pk, sog["M1"] + sog["M2"] + 1)
+    rf = roofline(res["profile"], w, pk, sog["M1"] + sog["M2"] + 1)
     rf["peak_source"] = pk_kind
     line["roofline"] = rf
     line["clocks"] = clocks.summary() if clocks else None
@@ -469,14 +542,12 @@ def main():
     if not args.no_batch:
         line["batched"] = batched_sweep(torch, R, args.steps, max(3, args.warmup))
     if not args.no_serve:
-        line["served"] = served_stream(torch, R)
+        line["served"] = served_stream(torch, R, n_jobs=args.serve_jobs, plain=not args.no_serve_plain)
     if not args.no_fp64:
         r64 = rbsog_replica(w, R.RBSOG_FP64, 3, 1, rank, torch, R, profile_steps=0, e2e_steps=0)
         line["fp64"] = {"value": w.N * 3 / (r64["ms"] * 1e-3), "ms_per_step": r64["ms"] / 3, "steps": 3}
     if not args.no_cpu:
-        secs, thr = oracle_step_time(w, 1)
-        line["cpu_baseline"] = {"value": w.N / secs, "unit": "particle-steps/s", "cores": thr, "kind": "oracle",
-                                "sample": f"1 full step of the N={w.N} workload (FP64 oracle, OpenMP)"}
+        line["cpu_baseline"] = cpu_baseline(w)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -51,6 +51,8 @@ def lib():
         L.orc_real_far.argtypes = [i64, _dp, _dp, _dp, _dp, C.c_int, _dp, C.POINTER(d)]
         L.orc_brute_yukawa.argtypes = [i64, _dp, _dp, _dp, d, d, _dp, C.POINTER(d)]
         L.orc_num_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = None
         _lib = L
     return _lib
 
@@ -69,6 +71,11 @@ def _idx(idx):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Thread count of the C core's parallel loops (used by timing legs)."""
+    lib().orc_set_threads(int(n))
 
 
 # ---- scalar kernel pieces (C) ----

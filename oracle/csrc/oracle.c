@@ -409,3 +409,14 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Thread count of the parallel loops above (timing legs only; results do not depend on it
+ * beyond the order of the reductions). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
