@@ -231,3 +231,103 @@ class ModeSampler:
         m = m[np.any(m != 0, axis=1)]
         m = m[self.k2_of(m) <= kmax2]
         return m.astype(np.int64)
+
+
+MH_TAG = 0x80000000          # top bit of the fourth counter word: the chains' own stream
+MH_T_BITS = 29               # proposal index t enters as (8 (t mod 2^29) + j, t >> 29)
+
+
+class MHChains:
+    """P independent Metropolis-Hastings chains on Z^3 \\ {0} whose stationary measure is
+    P(k) of Eq. (59): the sampler Sec. 4.3 names for drawing the batch.
+
+    The paper names the method only.  Reading used here: an independence sampler whose
+    proposal Q is the exact draw of steps 1-2 of ModeSampler (the Gaussian mixture of Fhat,
+    or of k^2 Fhat for calF = k^2) and whose acceptance probability is
+        alpha(k -> k') = min(1, a(k') / a(k)),   a(k) = P(k) / Q(k) (up to a constant),
+    so a(k) = calF(k) / sum q^2 for the adaptive measures and a = 1 otherwise (every move
+    is accepted and the chain is i.i.d.).  A proposal k' = 0 is rejected (the chain stays).
+    With A = kT V, t = k^2 + lambda^-2 and At = A t, the test u < a(k')/a(k) is evaluated
+    without division as (u At)(At' + Q2) < At' (At + Q2) in IEEE double operations.
+
+    Chain l's proposal number t (counted from its start, never reset) uses the Philox words
+    counter = (l, 8 (t mod 2^29) + j, t >> 29, 2^31), key = seed: j = 0 mixture, j = 1..3
+    axes, j = 4 the uniform u.  At its first evaluation a chain takes its first nonzero
+    proposal as its state and then makes `burnin` more proposals; every later evaluation
+    makes `sweeps` proposals.  The evaluation's batch is the P chain states."""
+
+    def __init__(self, sampler: "ModeSampler", P: int, sweeps: int = 1, burnin: int = 64):
+        self.s = sampler
+        self.P = int(P)
+        self.sweeps = int(sweeps)
+        self.burnin = int(burnin)
+        self.m = np.zeros((self.P, 3), dtype=np.int64)
+        self.t = np.zeros(self.P, dtype=np.int64)
+        self.started = False
+        self.accepted = 0
+        self.proposed = 0
+
+    def _words(self, seed: int, slots, t):
+        k0 = np.uint64(seed & 0xFFFFFFFF)
+        k1 = np.uint64((seed >> 32) & 0xFFFFFFFF)
+        slots = np.asarray(slots, dtype=np.uint64)
+        t = np.asarray(t, dtype=np.uint64)
+        lo = t & np.uint64((1 << MH_T_BITS) - 1)
+        hi = t >> np.uint64(MH_T_BITS)
+        return [philox.philox4x32_10(slots, np.uint64(8) * lo + np.uint64(j), hi, np.uint64(MH_TAG), k0, k1)
+                for j in range(5)]
+
+    def _propose(self, seed: int, slots):
+        """Proposal n ([len(slots), 3]) and u of each chain's next proposal."""
+        s = self.s
+        words = self._words(seed, slots, self.t[slots])
+        mi = s._alias_pick(words[0], s.mix_prob, s.mix_alias, len(s.mix_prob))
+        n = np.zeros((len(slots), 3), dtype=np.int64)
+        for a in range(3):
+            for g in np.unique(mi):
+                sel = mi == g
+                nmax, prob, alias = s.axis[g][a]
+                wsel = [x[sel] for x in words[1 + a]]
+                n[sel, a] = s._alias_pick(wsel, prob, alias, 2 * nmax + 1) - nmax
+        self.t[slots] += 1
+        return n, philox.u53(words[4][0], words[4][1])
+
+    def accepts(self, u, k2_cur, k2_new):
+        """u < a(k')/a(k) as (u At)(At' + Q2) < At' (At + Q2)."""
+        s = self.s
+        if s.kind not in (ADAPTIVE, DEBYE):
+            return np.ones(np.shape(u), dtype=bool)
+        A = s.kT * s.V
+        Q2 = (4.0 * math.pi) * s.Q2 if s.kind == DEBYE else s.Q2
+        At = A * (k2_cur + s.inv_lam2)
+        Atn = A * (k2_new + s.inv_lam2)
+        return (u * At) * (Atn + Q2) < Atn * (At + Q2)
+
+    def _sweep(self, seed: int):
+        slots = np.arange(self.P)
+        n, u = self._propose(seed, slots)
+        ok = np.any(n != 0, axis=1) & self.accepts(u, self.s.k2_of(self.m), self.s.k2_of(n))
+        self.m[ok] = n[ok]
+        self.accepted += int(np.sum(ok))
+        self.proposed += self.P
+
+    def draw(self, seed: int):
+        """The P modes (int32 [P, 3]) of the next force evaluation."""
+        if not self.started:
+            todo = np.arange(self.P)
+            tries = 0
+            while todo.size:
+                if tries >= MAX_ATTEMPTS:
+                    raise RuntimeError("MH chain start exceeded the attempt limit")
+                n, _ = self._propose(seed, todo)
+                nz = np.any(n != 0, axis=1)
+                self.m[todo[nz]] = n[nz]
+                todo = todo[~nz]
+                tries += 1
+            self.started = True
+            for _ in range(self.burnin):
+                self._sweep(seed)
+        else:
+            for _ in range(self.sweeps):
+                self._sweep(seed)
+        return self.m.astype(np.int32)
