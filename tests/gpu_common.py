@@ -12,9 +12,11 @@ from paper_2501_10946_gb300 import workloads as W
 
 FP64_TOL = 1e-12
 FP32_TOL = 1e-5
-# Floor of the per-particle relative force error, as a fraction of the RMS force: a
-# particle whose force nearly cancels has no meaningful relative error of its own.
-PP_FLOOR = 1e-2
+# Floor of the per-particle relative force error, as a fraction of the RMS force.  A
+# particle's force is a sum of pair terms (and of mode terms); where they nearly cancel,
+# as on a bcc lattice, the rounding error scales with the terms, not with their small
+# total, so the relative error of such a particle says nothing about the arithmetic.
+PP_FLOOR = 0.1
 
 
 def force_errors(got, ref):

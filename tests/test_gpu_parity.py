@@ -1,7 +1,7 @@
 """GPU parity through the C ABI: every step of the force path against the FP64 oracle on
 the same seeded inputs and the same injected k-set.  FP64 build: 1e-12; FP32 build: 1e-5,
 applied to the relative L2 error of the forces, to every particle's relative force error
-(with a floor of 1e-2 of the RMS force), to every mode of rho (relative to |rho_l| +
+(with a floor of 0.1 of the RMS force), to every mode of rho (relative to |rho_l| +
 sqrt(sum q^2)) and to each energy; cell lists bit-exact."""
 import math
 
