@@ -68,6 +68,26 @@ extern "C" {
 #define RBSOG_SAMPLING_DEBYE 3      /* Eq. (62) with the Debye wavenumber of Gaussian units:
                                        4 pi sum q^2 / (kT V) in place of sum q^2 / (kT V) */
 
+/* How the P modes of a force evaluation are drawn from P(k) (Eq. 59). */
+#define RBSOG_SAMPLER_IID 0         /* exact independent draws (rejection from the Gaussian
+                                       mixture of Fhat); every evaluation's batch is fresh */
+#define RBSOG_SAMPLER_MH 1          /* the Metropolis-Hastings method Sec. 4.3 names: P
+                                       independent chains, one per batch slot, each an
+                                       independence sampler whose proposal is the mixture
+                                       draw and whose acceptance is min(1, a(k')/a(k)),
+                                       a = calF / sum q^2 (a = 1 for calF = 1 and k^2); the
+                                       batch is the chain states, correlated from one
+                                       evaluation to the next */
+
+/* Temperature of the adaptive correction calF of Eq. (62). */
+#define RBSOG_KT_TARGET 0           /* the target k_B T (Gamma or kT) */
+#define RBSOG_KT_INSTANT 1          /* the instantaneous kinetic temperature, computed on the
+                                       device at every force evaluation (Sec. 4.3, NVT): k_B T =
+                                       2 K / (3 N), K the kinetic energy of the velocities the
+                                       step has when the forces are evaluated (after the
+                                       opening kick and drift, before the closing kick); S of
+                                       Eq. (59) is re-summed at that temperature */
+
 typedef struct rbsog_ctx rbsog_ctx;
 typedef struct rbsog_batch rbsog_batch;
 typedef struct rbsog_server rbsog_server;
@@ -99,6 +119,13 @@ typedef struct rbsog_params {
                                own SOG decomposition at r_c and sog_eps (sog_mode MINIMAL or
                                BOUND); the modes are drawn from the envelope of the far
                                field's transform and coef carries Fhat / Fhat_env */
+    int32_t sampler;        /* RBSOG_SAMPLER_IID | RBSOG_SAMPLER_MH (the latter: Yukawa kernel,
+                               single contexts only) */
+    int32_t mh_sweeps;      /* MH: proposals per chain at each force evaluation; 0 selects 1 */
+    int32_t mh_burnin;      /* MH: proposals per chain after its start, at the first force
+                               evaluation; 0 selects 64, negative selects none */
+    int32_t temperature;    /* RBSOG_KT_TARGET | RBSOG_KT_INSTANT (single contexts only; a no-op
+                               for calF = 1 and calF = k^2, which do not depend on T) */
 } rbsog_params;
 
 typedef struct rbsog_energy {
@@ -201,6 +228,12 @@ int rbsog_get_cells(rbsog_ctx *ctx, int32_t *nc, uint32_t *cell_start, uint32_t 
  * and S is the envelope's.  Host pointers, any may be NULL. */
 int rbsog_get_sog(rbsog_ctx *ctx, double *h, double *t0, int32_t *M1, int32_t *M2, double *w, double *lam,
                   double *S);
+
+/* The k_B T and the normalisation S = sum_{k != 0} calF(k) Fhat(k) of the last force
+ * evaluation (host pointers, either may be NULL): with RBSOG_KT_INSTANT the instantaneous
+ * temperature and the S re-summed at it, else the target k_B T and the S of
+ * rbsog_get_sog.  Synchronous. */
+int rbsog_get_temperature(rbsog_ctx *ctx, double *kT, double *S);
 
 /* Kernel-group timing.  With enable != 0, rbsog_step and rbsog_forces launch their
  * kernels eagerly (no graph) and record CUDA events on the launching stream around

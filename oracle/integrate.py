@@ -13,6 +13,9 @@ convergence theory (Sec. 4.4) without giving a scheme.  Readings used here:
   0x40000000 + j, step lo, step hi); j = 0 gives (xi_x, xi_y) by Box-Muller of its
   four words, j = 1 gives xi_z (cosine branch).
   wrap(r) = r - L floor(r (1/L)), then + L if negative, then - L if >= L.
+With the instantaneous temperature of Sec. 4.3 (NVT), the force evaluation also takes the
+velocities it sees (after B A O A, or after the half kick of velocity Verlet), whose
+kinetic temperature 2K/(3N) enters calF of Eq. (62).
 """
 from __future__ import annotations
 
@@ -43,17 +46,23 @@ def langevin_noise(seed: int, step: int, ids) -> np.ndarray:
     return np.stack([x, y, z], axis=1)
 
 
-def vv_step(r, v, F, mass, L, dt, force_fn):
-    """One velocity-Verlet step; force_fn(r) -> F.  Returns (r, v, F)."""
+def vv_step(r, v, F, mass, L, dt, force_fn, with_v=False):
+    """One velocity-Verlet step; force_fn(r) -> F, or force_fn(r, v) with the half-kicked
+    velocities when with_v.  Returns (r, v, F)."""
     hm = (0.5 * dt / np.asarray(mass, dtype=np.float64))[:, None]
     v = v + hm * F
     r = wrap(r + dt * v, L)
-    F = force_fn(r)
+    F = force_fn(r, v) if with_v else force_fn(r)
     v = v + hm * F
     return r, v, F
 
 
-def baoab_step(r, v, F, mass, L, dt, gamma, kT, seed, step, force_fn, ids=None):
+def kinetic_temperature(v, mass) -> float:
+    """Instantaneous k_B T = 2 K / (3 N) (three degrees of freedom per particle)."""
+    return 2.0 * kinetic(v, mass) / (3.0 * np.asarray(v).shape[0])
+
+
+def baoab_step(r, v, F, mass, L, dt, gamma, kT, seed, step, force_fn, ids=None, with_v=False):
     mass = np.asarray(mass, dtype=np.float64)
     ids = np.arange(r.shape[0]) if ids is None else ids
     hm = (0.5 * dt / mass)[:, None]
@@ -63,7 +72,7 @@ def baoab_step(r, v, F, mass, L, dt, gamma, kT, seed, step, force_fn, ids=None):
     r = r + (0.5 * dt) * v
     v = c1 * v + c2 * langevin_noise(seed, step, ids)
     r = wrap(r + (0.5 * dt) * v, L)
-    F = force_fn(r)
+    F = force_fn(r, v) if with_v else force_fn(r)
     v = v + hm * F
     return r, v, F
 

@@ -105,8 +105,10 @@ __device__ __forceinline__ void noise_words(const BinArgs &a, uint32_t id, U4 &w
     w1 = philox10(id, 0x40000001u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
 }
 
+// Returns the particle's kinetic energy m |v|^2 / 2 after the update when a.K_part is set
+// (else 0).
 template <int PREC>
-__device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
+__device__ __forceinline__ double bin_body(const BinArgs &a, uint32_t k) {
     const uint32_t N = a.stride;
     double r[3] = {a.in.rx[k], a.in.ry[k], a.in.rz[k]};
     double v[3] = {a.in.vx[k], a.in.vy[k], a.in.vz[k]};
@@ -229,12 +231,27 @@ __device__ __forceinline__ void bin_body(const BinArgs &a, uint32_t k) {
     uint32_t c = a.cell_base + cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);
     a.cell[k] = c;
     a.slot[k] = atomicAdd(&a.count[c], 1u);
+    return a.K_part ? 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm : 0.0;
 }
 
 template <int PREC>
 __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < a.N) bin_body<PREC>(a, k);
+    double ke = 0.0;
+    if (k < a.N) ke = bin_body<PREC>(a, k);
+    if (a.K_part) {
+        // per-block kinetic energy in a fixed order (warp shuffles, then the 8 warp sums)
+        __shared__ double wsum[8];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ke += __shfl_xor_sync(0xffffffffu, ke, o);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = ke;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += wsum[w];
+            a.K_part[blockIdx.x] = t;
+        }
+    }
 }
 
 // system of block b: the last r with items[r] <= b

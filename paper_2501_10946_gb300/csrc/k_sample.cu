@@ -54,11 +54,46 @@ __device__ __forceinline__ int alias_draw(U4 w, const unsigned long long *thr, c
     return (U < thr[i]) ? i : alias[i];
 }
 
+// coef = S / (P V calF(k)) (Eqs. 60, 62), calF of the measure at A = k_B T V; with a
+// far-field transform that may change sign, times Fhat(k) / Fhat_env(k) (draws from the
+// envelope)
+__device__ __forceinline__ double mode_coef(const SampleArgs &a, const int m[3], double A, double S) {
+    double kx = a.tpl[0] * m[0], ky = a.tpl[1] * m[1], kz = a.tpl[2] * m[2];
+    double k2 = kx * kx + ky * ky + kz * kz;
+    const double calF = calF_of(a.measure, k2, A, a.Q2, a.y);
+    double coef = S / ((double)a.P * a.V * calF);
+    if (a.nfh > 0) {
+        double fh = 0.0, fe = 0.0;
+        for (int g = 0; g < a.nfh; ++g) {
+            const double e = a.fA[g] * exp(-k2 * a.finv4b[g]);
+            fh += e;
+            fe += fabs(e);
+        }
+        coef = coef * (fh / fe);
+    }
+    return coef;
+}
+
+// |k|^2 of mode n in IEEE operations without contraction: (kx^2 + ky^2) + kz^2
+__device__ __forceinline__ double k2_rn(const SampleArgs &a, const int n[3]) {
+    const double kx = __dmul_rn(a.tpl[0], (double)n[0]);
+    const double ky = __dmul_rn(a.tpl[1], (double)n[1]);
+    const double kz = __dmul_rn(a.tpl[2], (double)n[2]);
+    return __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
+}
+
+// A t of the acceptance tests: A (k^2 + lambda^-2) for one Yukawa term, A / psi(k) otherwise
+__device__ __forceinline__ double At_of(const SampleArgs &a, double A, double k2) {
+    return a.y.n == 1 ? __dmul_rn(A, __dadd_rn(k2, a.y.inv_lam2[0])) : __ddiv_rn(A, psi_of(a.y, k2));
+}
+
 // One slot l per warp: lane j tries attempt att0 + j, so 32 consecutive attempts run at
 // once and the slot takes the accepted attempt with the smallest index, exactly the draw
 // a sequential loop over attempts returns (the random words depend only on the counter).
 __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
     const int lane = threadIdx.x & 31;
+    const double A = a.temp ? a.temp[0] : a.A;
+    const double S = a.temp ? a.temp[1] : a.S;
     int m[3] = {1, 0, 0};
     if (a.ctr->inject) {
         m[0] = a.inject_m[3 * l]; m[1] = a.inject_m[3 * l + 1]; m[2] = a.inject_m[3 * l + 2];
@@ -82,14 +117,9 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
             if (ok && (a.measure == 0 || a.measure == 3)) {
                 U4 wa = philox10((uint32_t)l, cb + 4u, d0, d1, k0, k1);
                 double u = u53_of(wa.x, wa.y);
-                double kx = __dmul_rn(a.tpl[0], (double)n[0]);
-                double ky = __dmul_rn(a.tpl[1], (double)n[1]);
-                double kz = __dmul_rn(a.tpl[2], (double)n[2]);
-                double k2 = __dadd_rn(__dadd_rn(__dmul_rn(kx, kx), __dmul_rn(ky, ky)), __dmul_rn(kz, kz));
                 // u < A / (A + Q2 psi), evaluated without division as u (A t + Q2) < A t
                 // with t = 1/psi = k^2 + lambda^-2 for one Yukawa term
-                const double At = a.y.n == 1 ? __dmul_rn(a.A, __dadd_rn(k2, a.y.inv_lam2[0]))
-                                             : __ddiv_rn(a.A, psi_of(a.y, k2));
+                const double At = At_of(a, A, k2_rn(a, n));
                 ok = __dmul_rn(u, __dadd_rn(At, a.Q2a)) < At;
             }
             const unsigned acc = __ballot_sync(0xffffffffu, ok);
@@ -104,22 +134,135 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
     }
     if (lane == 0) {
         a.m_out[3 * l] = m[0]; a.m_out[3 * l + 1] = m[1]; a.m_out[3 * l + 2] = m[2];
-        // coef = S / (P V calF(k)) (Eqs. 60, 62), calF of the measure; with a far-field
-        // transform that may change sign, times Fhat(k) / Fhat_env(k) (draws from the envelope)
-        double kx = a.tpl[0] * m[0], ky = a.tpl[1] * m[1], kz = a.tpl[2] * m[2];
-        double k2 = kx * kx + ky * ky + kz * kz;
-        const double calF = calF_of(a.measure, k2, a.A, a.Q2, a.y);
-        double coef = a.S / ((double)a.P * a.V * calF);
-        if (a.nfh > 0) {
-            double fh = 0.0, fe = 0.0;
-            for (int g = 0; g < a.nfh; ++g) {
-                const double e = a.fA[g] * exp(-k2 * a.finv4b[g]);
-                fh += e;
-                fe += fabs(e);
+        a.coef_out[l] = mode_coef(a, m, A, S);
+    }
+}
+
+// Metropolis-Hastings chains (RBSOG_SAMPLER_MH), one thread per chain l.  The proposal is
+// the mixture draw of the i.i.d. sampler (component and per-axis alias tables) with Philox
+// counter (l, 8 (t mod 2^29) + j, t >> 29, 2^31), t the chain's proposal index, key = seed:
+// j = 0 component, 1..3 axes, 4 the uniform u.  A proposal n = 0 is rejected; otherwise n
+// replaces the state m when (u At_m)(At_n + Q2) < At_n (At_m + Q2), i.e. u < a(n)/a(m) with
+// a = calF / sum q^2 (for calF = 1 and k^2, a = 1 and every nonzero proposal is taken).  A
+// chain with t = 0 starts at its first nonzero proposal and makes `burnin` more; later
+// evaluations make `sweeps`.  The batch of the evaluation is the P chain states.
+__device__ __forceinline__ void mh_propose(const SampleArgs &a, int l, unsigned long long &t, int n[3], double &u) {
+    const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+    const uint32_t c1 = 8u * (uint32_t)(t & ((1ull << 29) - 1ull));
+    const uint32_t c2 = (uint32_t)(t >> 29);
+    const int g = alias_draw(philox10((uint32_t)l, c1, c2, 0x80000000u, k0, k1), a.tab.mix_thr, a.tab.mix_alias,
+                             a.tab.mtot);
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const int off = a.tab.ax_off[3 * g + ax], nm = a.tab.ax_nmax[3 * g + ax];
+        n[ax] = alias_draw(philox10((uint32_t)l, c1 + 1u + ax, c2, 0x80000000u, k0, k1), a.tab.ax_thr + off,
+                           a.tab.ax_alias + off, 2 * nm + 1) - nm;
+    }
+    const U4 wa = philox10((uint32_t)l, c1 + 4u, c2, 0x80000000u, k0, k1);
+    u = u53_of(wa.x, wa.y);
+    t += 1ull;
+}
+
+__global__ void __launch_bounds__(128) k_sample_mh(SampleArgs a, MHChainArgs c) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.P) return;
+    const double A = a.temp ? a.temp[0] : a.A;
+    const double S = a.temp ? a.temp[1] : a.S;
+    int m[3];
+    if (a.ctr->inject) {
+        m[0] = a.inject_m[3 * l]; m[1] = a.inject_m[3 * l + 1]; m[2] = a.inject_m[3 * l + 2];
+    } else {
+        const bool adaptive = a.measure == 0 || a.measure == 3;
+        unsigned long long t = c.t[l];
+        int cur[3] = {c.m[3 * l], c.m[3 * l + 1], c.m[3 * l + 2]};
+        int nprop = c.sweeps;
+        if (t == 0ull) {
+            bool found = false;
+            for (int tries = 0; tries < kMaxAttempts && !found; ++tries) {
+                int n[3];
+                double u;
+                mh_propose(a, l, t, n, u);
+                if (!(n[0] == 0 && n[1] == 0 && n[2] == 0)) {
+                    cur[0] = n[0]; cur[1] = n[1]; cur[2] = n[2];
+                    found = true;
+                }
             }
-            coef = coef * (fh / fe);
+            if (!found) {
+                atomicOr(&a.ctr->err, kErrSampler);
+                cur[0] = 1; cur[1] = 0; cur[2] = 0;
+            }
+            nprop = c.burnin;
         }
-        a.coef_out[l] = coef;
+        double At_cur = adaptive ? At_of(a, A, k2_rn(a, cur)) : 0.0;
+        for (int s = 0; s < nprop; ++s) {
+            int n[3];
+            double u;
+            mh_propose(a, l, t, n, u);
+            if (n[0] == 0 && n[1] == 0 && n[2] == 0) continue;
+            bool ok = true;
+            double At_new = 0.0;
+            if (adaptive) {
+                At_new = At_of(a, A, k2_rn(a, n));
+                ok = __dmul_rn(__dmul_rn(u, At_cur), __dadd_rn(At_new, a.Q2a)) <
+                     __dmul_rn(At_new, __dadd_rn(At_cur, a.Q2a));
+            }
+            if (ok) {
+                cur[0] = n[0]; cur[1] = n[1]; cur[2] = n[2];
+                At_cur = At_new;
+            }
+        }
+        c.t[l] = t;
+        c.m[3 * l] = cur[0]; c.m[3 * l + 1] = cur[1]; c.m[3 * l + 2] = cur[2];
+        m[0] = cur[0]; m[1] = cur[1]; m[2] = cur[2];
+    }
+    a.m_out[3 * l] = m[0]; a.m_out[3 * l + 1] = m[1]; a.m_out[3 * l + 2] = m[2];
+    a.coef_out[l] = mode_coef(a, m, A, S);
+}
+
+// Instantaneous temperature and the normalisation S at it (RBSOG_KT_INSTANT).  Every block
+// sums the kinetic-energy partials in the same fixed order (so all agree on k_B T), then its
+// share of the table; the last block to arrive adds the block sums in block order.
+__device__ __forceinline__ double block_sum_256(double v, double *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    __syncthreads();
+    return t;     // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_temperature(TempArgs a) {
+    __shared__ double sh[8];
+    __shared__ double kTV_sh;
+    double k = 0.0;
+    for (int i = threadIdx.x; i < a.nK; i += blockDim.x) k += a.K_part[i];
+    k = block_sum_256(k, sh);
+    if (threadIdx.x == 0) kTV_sh = (a.two_3N * k) * a.V;
+    __syncthreads();
+    const double A = kTV_sh;
+    double s = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += gridDim.x * blockDim.x)
+        s += calF_of(a.measure, a.k2[j], A, a.Q2, a.y) * a.W[j];
+    s = block_sum_256(s, sh);
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        a.part[blockIdx.x] = s;
+        __threadfence();
+        last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double S = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) S += ((volatile double *)a.part)[b];
+        a.out[0] = A;
+        a.out[1] = S;
+        a.out[2] = A / a.V;
+        *a.done = 0u;
     }
 }
 
@@ -173,6 +316,14 @@ __global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
 
 void launch_sample(const SampleArgs &a, cudaStream_t st) {
     k_sample<<<(a.P + kSampleWarps - 1) / kSampleWarps, 128, 0, st>>>(a);
+}
+
+void launch_sample_mh(const SampleArgs &a, const MHChainArgs &c, cudaStream_t st) {
+    k_sample_mh<<<(a.P + 127) / 128, 128, 0, st>>>(a, c);
+}
+
+void launch_temperature(const TempArgs &a, cudaStream_t st) {
+    k_temperature<<<kTempBlocks, 256, 0, st>>>(a);
 }
 
 uint32_t sample_batch_blocks(int P) { return (uint32_t)((P + kSampleWarps - 1) / kSampleWarps); }

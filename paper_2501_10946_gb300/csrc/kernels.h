@@ -23,6 +23,8 @@ struct BinArgs {
     void *rec_w;              // particle records in this (work) order: uint4 (FP32) or Rec64 (FP64)
     void *rec_id;             // the same records at their particle ids (an order the storage does not change)
     uint32_t *cell, *slot, *count;
+    double *K_part;           // nullptr, or per-block kinetic energy of the velocities this
+                              // kernel leaves (the instantaneous temperature of calF)
 };
 // Fills the FP32 copies of dt, dt/2, c1 and okT from the doubles.
 inline void set_bin_floats(BinArgs &a) {
@@ -99,8 +101,36 @@ struct SampleArgs {
     const int *inject_m;      // [P*3]
     int *m_out;               // [P*3]
     double *coef_out;         // [P]
+    const double *temp;       // nullptr, or {k_B T V, S} of this evaluation at the instantaneous
+                              // temperature (launch_temperature), which replace A and S
 };
 void launch_sample(const SampleArgs &a, cudaStream_t st);
+// Metropolis-Hastings chains (one per batch slot): state m and proposals made t (t = 0: the
+// chain has not started)
+struct MHChainArgs {
+    int *m;                   // [P*3]
+    unsigned long long *t;    // [P]
+    int sweeps, burnin;
+};
+void launch_sample_mh(const SampleArgs &a, const MHChainArgs &c, cudaStream_t st);
+// Instantaneous temperature and S at it: k_B T = 2 K / (3 N) from the kinetic-energy
+// partials of k_bin, S(T) = sum_j calF(k2_j; T) W_j over the distinct |k|^2 of the mode
+// support (W_j: multiplicity times Fhat_env at k2_j).  out = {k_B T V, S, k_B T}.
+struct TempArgs {
+    const double *K_part;
+    int nK;
+    double two_3N;            // 2 / (3 N)
+    double V, Q2;
+    Yterms y;
+    int measure;
+    const double *k2, *W;
+    int n;
+    double *part;             // [kTempBlocks]
+    unsigned int *done;       // arrival counter (0 between launches)
+    double *out;              // [3]
+};
+constexpr int kTempBlocks = 64;
+void launch_temperature(const TempArgs &a, cudaStream_t st);
 struct SArgs {
     int mtot;
     double A[kMaxGauss], inv4b[kMaxGauss];   // Fhat(k) = sum_m A_m exp(-k^2 inv4b_m)

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/rbsog.h"
@@ -63,6 +64,16 @@ struct rbsog_ctx {
     bool force_valid = false;
     bool energy_valid = false;     // the energy partials belong to the current state
     SamplerTables tab{};
+    // Metropolis-Hastings chains (RBSOG_SAMPLER_MH)
+    bool mh = false;
+    int *mh_m = nullptr;
+    unsigned long long *mh_t = nullptr;
+    // instantaneous temperature (RBSOG_KT_INSTANT): kinetic-energy partials of k_bin, the
+    // distinct |k|^2 of the mode support with their weights, and {k_B T V, S, k_B T}
+    bool instT = false;
+    double *Kb_part = nullptr, *shell_k2 = nullptr, *shell_W = nullptr, *temp_part = nullptr, *temp_out = nullptr;
+    unsigned int *temp_done = nullptr;
+    int nshell = 0;
     // profiling: events around each kernel group of eager force evaluations
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -346,6 +357,76 @@ int system_S(HostSystem *hs, std::string *err) {
     return RBSOG_OK;
 }
 
+// The distinct |k|^2 of the mode support (k != 0, |k|^2 <= kmax2 of system_S) with weights
+// W = (number of modes) x Fhat_env(k), so that S(T) = sum_j calF(k2_j; T) W_j.  Axes of equal
+// length are grouped, and a mode's key is the sum of m_a^2 over each group (one integer
+// |m|^2 for a cubic box), so modes related by sign changes and by permutations of equal
+// axes share one entry.  Sorted by k2.
+int shell_table(const HostSystem &h, std::vector<double> *k2out, std::vector<double> *Wout, std::string *err) {
+    double bmax = 0.0;
+    for (double b : h.sb) bmax = std::max(bmax, b);
+    const double kmax2 = 4.0 * bmax * std::log(1e17);
+    int grp[3] = {0, 0, 0}, ng = 1;
+    const double *L = h.box.L;
+    grp[1] = (L[1] == L[0]) ? 0 : ng++;
+    grp[2] = (L[2] == L[0]) ? 0 : ((L[2] == L[1]) ? grp[1] : ng++);
+    double tpl2[3];
+    int nmax[3];
+    for (int d = 0; d < 3; ++d) {
+        tpl2[grp[d]] = h.box.tpl[d] * h.box.tpl[d];
+        nmax[d] = (int)std::floor(std::sqrt(kmax2) / h.box.tpl[d]) + 1;
+    }
+    const unsigned long long B = (unsigned long long)3 * (unsigned long long)nmax[0] * nmax[0] +
+                                 3ull * nmax[1] * nmax[1] + 3ull * nmax[2] * nmax[2] + 1ull;
+    if ((double)B * (double)B * (double)B > 1.8e19) {
+        *err = "instantaneous temperature: the mode support is too large for the |k|^2 table";
+        return RBSOG_EUNSUPPORTED;
+    }
+    std::unordered_map<unsigned long long, double> cnt;
+    for (int mx = 0; mx <= nmax[0]; ++mx) {
+        const double kx = h.box.tpl[0] * mx;
+        for (int my = 0; my <= nmax[1]; ++my) {
+            const double ky = h.box.tpl[1] * my;
+            for (int mz = 0; mz <= nmax[2]; ++mz) {
+                if (mx == 0 && my == 0 && mz == 0) continue;
+                const double kz = h.box.tpl[2] * mz;
+                if (kx * kx + ky * ky + kz * kz > kmax2) break;
+                unsigned long long key[3] = {0, 0, 0};
+                key[grp[0]] += (unsigned long long)mx * mx;
+                key[grp[1]] += (unsigned long long)my * my;
+                key[grp[2]] += (unsigned long long)mz * mz;
+                const double mult = (mx ? 2.0 : 1.0) * (my ? 2.0 : 1.0) * (mz ? 2.0 : 1.0);
+                cnt[key[0] + B * (key[1] + B * key[2])] += mult;
+            }
+            if (cnt.size() > (1u << 22)) {
+                *err = "instantaneous temperature: more than 2^22 distinct |k|^2 (box too large or too anisotropic)";
+                return RBSOG_EUNSUPPORTED;
+            }
+        }
+    }
+    std::vector<std::pair<double, double>> ent;
+    ent.reserve(cnt.size());
+    for (const auto &kv : cnt) {
+        unsigned long long k = kv.first;
+        double k2 = 0.0;
+        for (int g = 0; g < ng; ++g) {
+            k2 += tpl2[g] * (double)(k % B);
+            k /= B;
+        }
+        double fe = 0.0;
+        for (size_t i = 0; i < h.sA.size(); ++i) fe += std::fabs(h.sA[i]) * std::exp(-k2 / (4.0 * h.sb[i]));
+        ent.push_back({k2, kv.second * fe});
+    }
+    std::sort(ent.begin(), ent.end());
+    k2out->resize(ent.size());
+    Wout->resize(ent.size());
+    for (size_t j = 0; j < ent.size(); ++j) {
+        (*k2out)[j] = ent[j].first;
+        (*Wout)[j] = ent[j].second;
+    }
+    return RBSOG_OK;
+}
+
 }  // namespace rbsog
 
 namespace {
@@ -446,6 +527,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     set_bin_floats(b);
     b.ctr = c->ctr; b.N = N; b.stride = N; b.cell_base = 0; b.box = c->box; b.rec_w = c->rec_w; b.rec_id = c->rec_id; b.cell = c->cell;
     b.slot = c->slot; b.count = c->count;
+    b.K_part = c->instT ? c->Kb_part : nullptr;
     SampleArgs sa{};
     sa.tab = c->tab; sa.P = c->p.P; sa.seed = c->p.seed;
     for (int d = 0; d < 3; ++d) sa.tpl[d] = c->box.tpl[d];
@@ -454,6 +536,23 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     sa.measure = c->p.sampling;
     sa.Q2a = c->p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * kPi) * c->Q2 : c->Q2;
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
+    sa.temp = c->instT ? c->temp_out : nullptr;
+    TempArgs ta{};
+    ta.K_part = c->Kb_part; ta.nK = (int)((N + 255) / 256); ta.two_3N = 2.0 / (3.0 * (double)N);
+    ta.V = c->V; ta.Q2 = c->Q2; ta.y = c->y; ta.measure = c->p.sampling;
+    ta.k2 = c->shell_k2; ta.W = c->shell_W; ta.n = c->nshell;
+    ta.part = c->temp_part; ta.done = c->temp_done; ta.out = c->temp_out;
+    MHChainArgs mc{};
+    mc.m = c->mh_m; mc.t = c->mh_t;
+    mc.sweeps = c->p.mh_sweeps > 0 ? c->p.mh_sweeps : 1;
+    mc.burnin = c->p.mh_burnin == 0 ? 64 : (c->p.mh_burnin < 0 ? 0 : c->p.mh_burnin);
+    // the k-sample: temperature first when calF takes the instantaneous one (it needs the
+    // kinetic energy k_bin leaves), then the i.i.d. draw or the chains
+    auto sample = [&](cudaStream_t s2) {
+        if (c->instT) launch_temperature(ta, s2);
+        if (c->mh) launch_sample_mh(sa, mc, s2);
+        else launch_sample(sa, s2);
+    };
     RhoArgs ra{};
     ra.rec = c->rec_id; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
     RhoFinalArgs rf{};
@@ -472,12 +571,13 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
         if (cudaEventRecord(c->ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0) != cudaSuccess)
             return cuda_fail(c, cudaGetLastError(), "fork the structure-factor stream");
         sr = c->side_stream;
-        launch_sample(sa, sr);
+        if (!c->instT) sample(sr);
     }
     { ProfScope ps(c, st, 0); launch_bin(prec, b, st); }
     if (fork) {
         if (cudaEventRecord(c->ev_bin, st) != cudaSuccess || cudaStreamWaitEvent(sr, c->ev_bin, 0) != cudaSuccess)
             return cuda_fail(c, cudaGetLastError(), "hand the records to the structure-factor stream");
+        if (c->instT) sample(sr);
         launch_rho(prec, ra, sr);
         launch_rho_final(prec, rf, sr);
     }
@@ -490,7 +590,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     g.in = c->work; g.out = c->rest; g.keys = c->keys; g.cell = c->cell; g.cell_start = c->cell_start; g.ctr = c->ctr;
     g.c_off = nullptr; g.R = 1; g.rec_w = c->rec_w; g.rec = c->rec; g.N = N;
     { ProfScope ps(c, st, 3); launch_gather(prec, g, st); }
-    if (!fork) { ProfScope ps(c, st, 4); launch_sample(sa, st); }
+    if (!fork) { ProfScope ps(c, st, 4); sample(st); }
     NearArgs na{};
     na.nc = c->nconsts; na.rec = c->rec; na.cell_start = c->cell_start; na.box = c->box; na.N = N; na.stride = N;
     na.Fn = c->Fn;
@@ -562,8 +662,26 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         const int code = setup_system(p, N, q_host, m_host, &hs, &err);
         if (code != RBSOG_OK) return fail(nullptr, code, err);
     }
+    if (p.sampler != RBSOG_SAMPLER_IID && p.sampler != RBSOG_SAMPLER_MH)
+        return fail(nullptr, RBSOG_EINVAL, "bad sampler");
+    if (p.temperature != RBSOG_KT_TARGET && p.temperature != RBSOG_KT_INSTANT)
+        return fail(nullptr, RBSOG_EINVAL, "bad temperature source");
+    if (p.sampler == RBSOG_SAMPLER_MH && hs.y.n != 1)
+        return fail(nullptr, RBSOG_EUNSUPPORTED, "the Metropolis-Hastings sampler takes the Yukawa kernel (egs_nu = 0)");
+    if (p.mh_sweeps < 0) return fail(nullptr, RBSOG_EINVAL, "mh_sweeps must be >= 0");
+    std::vector<double> shell_k2, shell_W;
+    const bool instT = p.temperature == RBSOG_KT_INSTANT &&
+                       (p.sampling == RBSOG_SAMPLING_ADAPTIVE || p.sampling == RBSOG_SAMPLING_DEBYE);
+    if (instT) {
+        std::string err;
+        const int code = shell_table(hs, &shell_k2, &shell_W, &err);
+        if (code != RBSOG_OK) return fail(nullptr, code, err);
+    }
     rbsog_ctx *c = new rbsog_ctx();
     c->p = p;
+    c->mh = p.sampler == RBSOG_SAMPLER_MH;
+    c->instT = instT;
+    c->nshell = (int)shell_k2.size();
     c->N = (uint32_t)N;
     c->prec = p.precision;
     c->V = hs.V; c->a_ws = hs.a_ws; c->lam = hs.lam; c->kT = hs.kT; c->Q2 = hs.Q2; c->qsum = hs.qsum;
@@ -613,6 +731,25 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         return bail(RBSOG_ENOMEM);
     }
     c->F = Fb; c->Fn = Fnb; c->rec_w = recwb; c->rec_id = recib; c->rec = recb;
+    if (c->mh) {
+        if (dalloc(c, &c->mh_m, 3 * (size_t)p.P) || dalloc(c, &c->mh_t, (size_t)p.P) ||
+            cudaMemset(c->mh_m, 0, 3 * sizeof(int) * (size_t)p.P) != cudaSuccess ||
+            cudaMemset(c->mh_t, 0, sizeof(unsigned long long) * (size_t)p.P) != cudaSuccess) {
+            g_init_error = "device allocation failed (sampler chains)";
+            return bail(RBSOG_ENOMEM);
+        }
+    }
+    if (c->instT) {
+        const size_t ns = shell_k2.size();
+        if (dalloc(c, &c->Kb_part, (n + 255) / 256) || dalloc(c, &c->shell_k2, ns) || dalloc(c, &c->shell_W, ns) ||
+            dalloc(c, &c->temp_part, (size_t)kTempBlocks) || dalloc(c, &c->temp_out, 3) ||
+            dalloc(c, &c->temp_done, 1) || cudaMemset(c->temp_done, 0, sizeof(unsigned int)) != cudaSuccess ||
+            cudaMemcpy(c->shell_k2, shell_k2.data(), ns * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c->shell_W, shell_W.data(), ns * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            g_init_error = "device allocation failed (temperature table)";
+            return bail(RBSOG_ENOMEM);
+        }
+    }
     if (cudaMemset(c->count, 0, sizeof(uint32_t) * bx.ncell) != cudaSuccess ||
         cudaMemset(c->ctr, 0, sizeof(DevCounters)) != cudaSuccess ||
         cudaMemset(c->edone, 0, sizeof(unsigned int)) != cudaSuccess ||
@@ -637,6 +774,14 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
             return bail(r);
         }
         c->S = hs.S;
+    }
+    if (c->instT) {
+        // until the first evaluation: the target temperature
+        const double t0[3] = {c->kT * c->V, c->S, c->kT};
+        if (cudaMemcpy(c->temp_out, t0, sizeof t0, cudaMemcpyHostToDevice) != cudaSuccess) {
+            g_init_error = "device initialisation failed";
+            return bail(RBSOG_ECUDA);
+        }
     }
     // a valid (zero) state so every call is defined before rbsog_set_state
     if (cudaMemset(c->stage_a, 0, n3 * sizeof(double)) != cudaSuccess) {
@@ -845,6 +990,18 @@ int rbsog_get_cells(rbsog_ctx *c, int32_t *nc, uint32_t *cell_start, uint32_t *p
            "copy cell_start");
     if (perm) CK(cudaMemcpy(perm, c->rest.id, sizeof(uint32_t) * c->N, cudaMemcpyDeviceToHost), "copy perm");
     return check_device_errors(c);
+}
+
+int rbsog_get_temperature(rbsog_ctx *c, double *kT, double *S) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    double v[3] = {c->kT * c->V, c->S, c->kT};
+    if (c->instT) {
+        CK(cudaDeviceSynchronize(), "synchronize");
+        CK(cudaMemcpy(v, c->temp_out, sizeof v, cudaMemcpyDeviceToHost), "copy temperature");
+    }
+    if (kT) *kT = v[2];
+    if (S) *S = v[1];
+    return RBSOG_OK;
 }
 
 int rbsog_get_sog(rbsog_ctx *c, double *h, double *t0, int32_t *M1, int32_t *M2, double *w, double *lam, double *S) {

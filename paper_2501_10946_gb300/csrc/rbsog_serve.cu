@@ -137,6 +137,10 @@ int admit(rbsog_server *s) {
             code = RBSOG_EUNSUPPORTED;
             err = "served jobs run the FP32 path";
         }
+        if (code == RBSOG_OK && (hs.p.sampler != RBSOG_SAMPLER_IID || hs.p.temperature != RBSOG_KT_TARGET)) {
+            code = RBSOG_EUNSUPPORTED;
+            err = "served jobs draw i.i.d. modes at the target temperature";
+        }
         if (code == RBSOG_OK && !engine_fits(b, hs) && b->R == 0) {
             code = RBSOG_ENOMEM;
             err = "job larger than the server's arenas";

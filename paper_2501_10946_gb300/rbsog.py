@@ -19,6 +19,8 @@ RBSOG_FP64, RBSOG_FP32 = 0, 1
 RBSOG_NVE, RBSOG_LANGEVIN = 0, 1
 RBSOG_SOG_MINIMAL, RBSOG_SOG_BOUND, RBSOG_SOG_TABLE = 0, 1, 2
 RBSOG_SAMPLING_ADAPTIVE, RBSOG_SAMPLING_UNIFORM, RBSOG_SAMPLING_K2, RBSOG_SAMPLING_DEBYE = 0, 1, 2, 3
+RBSOG_SAMPLER_IID, RBSOG_SAMPLER_MH = 0, 1
+RBSOG_KT_TARGET, RBSOG_KT_INSTANT = 0, 1
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENOCONV", 6: "EUNSUPPORTED",
           7: "EOVERFLOW"}
 
@@ -29,7 +31,8 @@ class rbsog_params(C.Structure):
                 ("langevin_gamma", C.c_double), ("seed", C.c_uint64), ("P", C.c_int32),
                 ("precision", C.c_int32), ("ensemble", C.c_int32), ("sog_mode", C.c_int32),
                 ("sog_M1", C.c_int32), ("sog_M2", C.c_int32), ("device", C.c_int32), ("sampling", C.c_int32),
-                ("egs_nu", C.c_double)]
+                ("egs_nu", C.c_double), ("sampler", C.c_int32), ("mh_sweeps", C.c_int32), ("mh_burnin", C.c_int32),
+                ("temperature", C.c_int32)]
 
 
 class rbsog_energy(C.Structure):
@@ -66,7 +69,7 @@ class RbsogError(RuntimeError):
 
 _lib = None
 EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_set_state_forces", "rbsog_get_forces", "rbsog_set_state_forces_f32", "rbsog_get_forces_f32", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
-           "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog",
+           "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog", "rbsog_get_temperature",
            "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_rho_noalloc",
            "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
            "rbsog_batch_forces", "rbsog_batch_step", "rbsog_batch_set_ksample", "rbsog_batch_get_ksample",
@@ -108,6 +111,7 @@ def load(build_if_missing: bool = True):
     L.rbsog_get_rho.argtypes = [vp, vp]
     L.rbsog_get_cells.argtypes = [vp, vp, vp, vp]
     L.rbsog_get_sog.argtypes = [vp, dp, dp, C.POINTER(i32), C.POINTER(i32), dp, dp, dp]
+    L.rbsog_get_temperature.argtypes = [vp, dp, dp]
     L.rbsog_build_sog.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, i32, vp]
     L.rbsog_profile.argtypes = [vp, i32]
     L.rbsog_profile_read.argtypes = [vp, vp, vp]
@@ -269,6 +273,13 @@ def rbsog_get_sog(ctx) -> dict:
     _check(ctx, load().rbsog_get_sog(ctx, C.byref(h), C.byref(t0), C.byref(M1), C.byref(M2), C.byref(w),
                                      C.byref(lam), C.byref(S)))
     return dict(h=h.value, t0=t0.value, M1=M1.value, M2=M2.value, w=w.value, lam=lam.value, S=S.value)
+
+
+def rbsog_get_temperature(ctx) -> tuple:
+    """(k_B T, S) of the last force evaluation."""
+    kT, S = C.c_double(), C.c_double()
+    _check(ctx, load().rbsog_get_temperature(ctx, C.byref(kT), C.byref(S)))
+    return kT.value, S.value
 
 
 def rbsog_build_sog(lam: float, r_c: float, eps: float, mode: int = RBSOG_SOG_MINIMAL, M1: int = 0,
@@ -493,7 +504,8 @@ def rbsog_server_free(s):
 def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int | None = None,
                 sog_mode: int = RBSOG_SOG_MINIMAL, M1: int = 0, M2: int = 0, device: int = 0,
                 ensemble: int | None = None, dt: float | None = None,
-                sampling: int = RBSOG_SAMPLING_ADAPTIVE, egs_nu: float = 0.0) -> rbsog_params:
+                sampling: int = RBSOG_SAMPLING_ADAPTIVE, egs_nu: float = 0.0, sampler: int = RBSOG_SAMPLER_IID,
+                mh_sweeps: int = 0, mh_burnin: int = 0, temperature: int = RBSOG_KT_TARGET) -> rbsog_params:
     """rbsog_params from a workloads.Workload (plain field copy)."""
     p = rbsog_params()
     for d in range(3):
@@ -517,4 +529,8 @@ def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int 
     p.device = int(device)
     p.sampling = int(sampling)
     p.egs_nu = float(egs_nu)
+    p.sampler = int(sampler)
+    p.mh_sweeps = int(mh_sweeps)
+    p.mh_burnin = int(mh_burnin)
+    p.temperature = int(temperature)
     return p

@@ -5,6 +5,11 @@ Langevin runs at each coupling; for every configuration the oracle gives the exa
 fluctuations E_fluc and F_fluc of the corrections calF (Eq. 62 as printed, 1, k^2, and Eq. 62
 with the Debye wavenumber of Gaussian units) in closed form,
 and the GPU's own estimator with each correction is checked against them by Monte Carlo.
+Two variants of the adaptive correction from Sec. 4.3 join the table: the paper's
+Metropolis-Hastings sampler (same marginal law, so the same per-evaluation fluctuation,
+checked by Monte Carlo, but correlated from one evaluation to the next: the lag-1
+correlation of the force error is printed for it and for i.i.d. draws) and calF at the
+instantaneous kinetic temperature of each configuration.
 The averaged table is printed, normalised per coupling by its smallest entry as in Fig. 9."""
 import json
 import math
@@ -13,7 +18,7 @@ import numpy as np
 import pytest
 
 from gpu_common import Ctx, oracle_sog, require_gpu
-from oracle import variance
+from oracle import integrate, variance
 from paper_2501_10946_gb300 import rbsog as R
 from paper_2501_10946_gb300 import workloads as W
 
@@ -37,11 +42,13 @@ def system(gamma_star, seed):
 
 def test_fluctuations_of_the_three_measures():
     table = {}
+    lag1 = {}
     for gi, gs in enumerate((0.01, 1.0, 100.0)):
         w = system(gs, 600 + 10 * gi)
         sog = oracle_sog(w)
         q = W.charges(w)
         acc = {k: np.zeros(2) for k in KINDS}
+        acc_T = np.zeros(2)
         snaps = []
         with Ctx(w, R.RBSOG_FP32) as c:
             R.rbsog_set_state(c.h, W.positions(w), W.velocities(w))
@@ -49,31 +56,50 @@ def test_fluctuations_of_the_three_measures():
             for _ in range(4):
                 R.rbsog_step(c.h, 500)
                 r = np.zeros((w.N, 3))
-                R.rbsog_get_state(c.h, r)
-                snaps.append(r)
-        for si, r in enumerate(snaps):
+                v = np.zeros((w.N, 3))
+                R.rbsog_get_state(c.h, r, v)
+                snaps.append((r, v))
+        for si, (r, v) in enumerate(snaps):
             fl, Fex = variance.fluctuations(r, q, w.box, sog, w.kT, w.P, with_force=True)
             for k in KINDS:
                 acc[k] += np.asarray(fl[k]) / len(snaps)
+            kT_inst = integrate.kinetic_temperature(v, W.masses(w))
+            acc_T += np.asarray(variance.fluctuations(r, q, w.box, sog, kT_inst, w.P, kinds=(0,))[0]) / len(snaps)
             if si == 0:
                 # the GPU estimator of each measure against the closed form: 256 draws
-                for k in KINDS:
-                    with Ctx(w, R.RBSOG_FP32, sampling=k) as c:
+                for k in list(KINDS) + ["mh"]:
+                    kw = dict(sampling=0, sampler=R.RBSOG_SAMPLER_MH) if k == "mh" else dict(sampling=k)
+                    with Ctx(w, R.RBSOG_FP32, **kw) as c:
                         R.rbsog_set_state(c.h, r)
-                        dev = []
+                        errs = []
                         for _ in range(256):
                             Ff = np.zeros((w.N, 3))
                             R.rbsog_forces_split(c.h, None, Ff)
-                            dev.append(float(np.mean(np.sum((Ff - Fex) ** 2, axis=1))))
-                    mc, exact = float(np.mean(dev)), fl[k][0]
-                    assert abs(mc - exact) <= 0.3 * exact, (gs, KINDS[k], mc, exact)
+                            errs.append((Ff - Fex).ravel())
+                    errs = np.asarray(errs)
+                    dev = np.sum(errs * errs, axis=1) / w.N
+                    mc, exact = float(np.mean(dev)), fl[0 if k == "mh" else k][0]
+                    assert abs(mc - exact) <= 0.3 * exact, (gs, k, mc, exact)
+                    lag1[(gs, k)] = float(np.mean(np.sum(errs[1:] * errs[:-1], axis=1)) / np.mean(dev * w.N))
+                    if k == "mh":
+                        mh_mc = [mc, fl[0][1]]
         table[gs] = {KINDS[k]: acc[k].tolist() for k in KINDS}
+        table[gs]["adaptive-MH"] = [acc[0][0] * mh_mc[0] / fl[0][0], acc[0][1]]
+        table[gs]["adaptive-Tinst"] = acc_T.tolist()
     norm = {}
     for gs, row in table.items():
-        fmin = min(v[0] for v in row.values())
-        emin = min(v[1] for v in row.values())
+        # normalised by the best of the four corrections of Fig. 9
+        fmin = min(row[name][0] for name in KINDS.values())
+        emin = min(row[name][1] for name in KINDS.values())
         norm[gs] = {name: [v[0] / fmin, v[1] / emin] for name, v in row.items()}
-    print(json.dumps({"F_fluc_E_fluc": table, "normalised": norm}))
+    print(json.dumps({"F_fluc_E_fluc": table, "normalised": norm,
+                      "lag1_force_error": {f"{g}/{KINDS.get(k, k)}": x for (g, k), x in lag1.items()}}))
+    # the chains' draws are correlated where they reject (strong coupling), i.i.d. draws not
+    assert lag1[(100.0, "mh")] > lag1[(100.0, 0)] + 0.1, lag1
+    assert abs(lag1[(100.0, 0)]) < 0.2, lag1
+    # at equilibrium the instantaneous temperature stays near the target: same fluctuations
+    for g in table:
+        assert abs(table[g]["adaptive-Tinst"][0] / table[g]["adaptive"][0] - 1.0) < 0.2, table[g]
     lo, hi = table[0.01], table[100.0]
     adaptive = ("adaptive", "adaptive-4pi")
     # weak coupling: almost no correlation, the adaptive corrections are essentially calF = 1,
@@ -87,6 +113,7 @@ def test_fluctuations_of_the_three_measures():
     # over the whole range the adaptive corrections are the robust choice: their worst
     # normalised fluctuation stays well below the worst of either fixed correction
     worst = {name: max(max(norm[g][name]) for g in norm) for name in KINDS.values()}
+    assert all(abs(norm[g]["adaptive-MH"][0] / norm[g]["adaptive"][0] - 1.0) < 0.3 for g in norm), norm
     for name in adaptive:
         assert worst[name] < 0.6 * min(worst["calF=1"], worst["calF=k^2"]), worst
     # with the Debye wavenumber of Gaussian units the adaptive correction is within 2% of
