@@ -12,7 +12,9 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librbsog.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["rbsog.cu", "rbsog_batch.cu", "rbsog_serve.cu", "k_cells.cu", "k_sample.cu", "k_near.cu", "k_forces.cu", "k_noalloc.cu", "sog_host.cpp"]
+# k_all.cu compiles the step's kernel files (k_cells, k_sample, k_near, k_forces) and the
+# persistent batched step as one translation unit
+SOURCES = ["rbsog.cu", "rbsog_batch.cu", "rbsog_serve.cu", "k_all.cu", "k_noalloc.cu", "sog_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code keeps IEEE semantics (no FMA contraction): the SOG root of Eq. 36 is computed
 # with the same operation order as any other FP64 implementation of it

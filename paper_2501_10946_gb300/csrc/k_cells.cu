@@ -11,6 +11,7 @@
 //                  the order the atomics produced is discarded, so the result is
 //                  deterministic; state and 16/32-byte particle records move there
 #include "common.cuh"
+#include "devutil.cuh"
 #include "kernels.h"
 #include "philox.cuh"
 
@@ -254,16 +255,6 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
     }
 }
 
-// system of block b: the last r with items[r] <= b
-__device__ __forceinline__ int item_system(const uint32_t *items, int R, uint32_t b) {
-    int lo = 0, hi = R - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (items[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 __global__ void __launch_bounds__(256) k_bin_batch(const BinArgs *args, const uint32_t *items, int R) {
     const int r = item_system(items, R, blockIdx.x);
@@ -531,7 +522,6 @@ __global__ void __launch_bounds__(256) k_get_state_batch(const SysStateArgs *arg
     if (k < a.N) get_state_body(a.rest, a.p_off, k, r_out, v_out);
 }
 
-inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 

@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "devmath.cuh"
+#include "devutil.cuh"
 #include "kernels.h"
 
 namespace rbsog {
@@ -21,31 +22,6 @@ constexpr int kRhoThreads = 256;
 constexpr int kRhoTile = 512;       // particles staged per tile (FP32: 8 KB, FP64: 16 KB)
 constexpr int kFarThreads = 256;
 constexpr int kFarTile = 512;       // modes staged per tile
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ unsigned long long pk2(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(unsigned long long v, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 
 template <typename T>
 __device__ __forceinline__ T block_reduce_sum(T v, T *sh) {
@@ -167,15 +143,6 @@ __global__ void __launch_bounds__(kRhoThreads, 4) k_rho32(RhoArgs a, int chunk) 
     rho32_body<ML>(a, chunk, blockIdx.x, blockIdx.y, sp);
 }
 
-__device__ __forceinline__ int item_system(const uint32_t *items, int R, uint32_t b) {
-    int lo = 0, hi = R - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (items[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 // Batched systems: block -> (system, particle chunk, pass of 256 modes); a system has
 // G chunks x ceil(P/256) passes.
@@ -622,7 +589,6 @@ __global__ void __launch_bounds__(1024) k_energy_batch(const EnergyArgs *args) {
     energy_body(args[blockIdx.x], sh);
 }
 
-inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
 // modes per lane: four above 256 modes, so that a particle's load and the loop overhead
 // serve four phases.  With fewer mode groups per block the warps split the particles into

@@ -28,6 +28,7 @@
 
 #include "common.cuh"
 #include "devmath.cuh"
+#include "devutil.cuh"
 #include "kernels.h"
 
 namespace rbsog {
@@ -36,49 +37,6 @@ namespace {
 constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
 constexpr int kSlots = 8;              // candidate slots (32 candidates each) per filter round
-
-// rsqrt and ex2 with subnormals flushed: a pair's r^2 and the exponents are never
-// subnormal, and the flushing forms skip the subnormal handling of the plain ones
-__device__ __forceinline__ float rsqrt_ftz(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Packed FP32x2 arithmetic (two lanes of one 64-bit register), round to nearest.
-__device__ __forceinline__ unsigned long long pk2(float a, float b) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(unsigned long long v, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
 
 // FP32 pair constants of one system, copied to shared memory by each tiled CTA (a batch
 // reads its systems' arguments from global memory, and the pair loop reads them per
@@ -795,8 +753,6 @@ __global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near
         near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, false, true>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true> *>(smem_raw));
     else near_global_block<1>(a, (uint32_t)g.W, blk);
 }
-
-inline unsigned blocks_for(uint32_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
