@@ -376,6 +376,25 @@ int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t 
  * milliseconds per group.  Synchronous. */
 int rbsog_batch_profile(rbsog_batch *b, int32_t nsteps, double *ms, void *stream);
 
+/* The form of a step: enable = 0 replays the batched kernels (one launch per kernel over
+ * all systems, 11 per step) from a CUDA graph; enable != 0 runs the whole step (or force
+ * evaluation) as one persistent cooperative launch, captured in the graph the same way.
+ * Its CTAs are all resident and walk the step's phases, meeting at grid barriers between
+ * dependent phases; the near-field tiles and the structure-factor blocks of every system
+ * form work lists that CTAs take items from as they finish.  Forces and trajectories are
+ * bit-identical in both forms (the same per-block arithmetic); the near energies differ
+ * in rounding (another grouping of the per-warp partial sums).  Energies of evaluations
+ * before a switch cannot be read after it (RBSOG_EINVAL until the next evaluation).
+ * rbsog_batch_profile and rbsog_batch_tune time the graph form's kernels.  Every
+ * grid-barrier wait is bounded (rbsog_batch_set_wait_limit): a wait that gives up makes
+ * the next synchronous call return RBSOG_ETIMEOUT (the pass that timed out is not valid).
+ * RBSOG_EUNSUPPORTED if the device has no cooperative launch.  Synchronous. */
+int rbsog_batch_set_persistent(rbsog_batch *b, int32_t enable);
+
+/* Polls of one grid-barrier wait of the persistent step before it gives up (>= 1; default
+ * 2e7, about a second or more).  Synchronous. */
+int rbsog_batch_set_wait_limit(rbsog_batch *b, int64_t polls);
+
 /* Message of the last failed call on b (or of the last failed rbsog_batch_init when b
  * is NULL). */
 const char *rbsog_batch_last_error(const rbsog_batch *b);

@@ -91,6 +91,12 @@ struct rbsog_batch {
     cudaStream_t side_stream = nullptr;                  // structure factor beside the near field
     cudaEvent_t ev_fork = nullptr, ev_bin = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
+    // persistent step: one cooperative launch per pass (near-field tiles of 128 threads)
+    bool persistent = false;
+    bool energies_stale = false;                         // partials written in the other layout
+    int pgrid = 0;                                       // CTAs of the cooperative grid
+    rbsog::GridBar *bar = nullptr;
+    long long wait_limit = 20000000;                     // polls of a grid-barrier wait
 };
 
 namespace rbsog {

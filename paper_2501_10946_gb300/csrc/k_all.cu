@@ -4,3 +4,4 @@
 #include "k_sample.cu"
 #include "k_near.cu"
 #include "k_forces.cu"
+#include "k_persist.cuh"

@@ -339,12 +339,82 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t *count, int ncell,
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) cell_start[ncell] = N;
 }
 
+__device__ __forceinline__ void scatter_one(const uint32_t *cell, const uint32_t *slot, const uint32_t *cell_start,
+                                            const uint32_t *id, unsigned long long *keys, uint32_t k) {
+    keys[cell_start[cell[k]] + slot[k]] = ((unsigned long long)id[k] << 32) | (unsigned long long)k;
+}
+
+// The two scan passes for a block of 256 threads (the persistent batched step): tile t
+// of kScanTile cells, 16 cells per thread.  Same results as k_tile_sums / k_scan_tiles.
+constexpr int kScanPer256 = kScanTile / 256;
+
+__device__ __forceinline__ uint32_t block_sum_256u(uint32_t v, uint32_t *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    return t;
+}
+
+__device__ __forceinline__ void tile_sum_256(const uint32_t *count, int ncell, uint32_t *tile_sums, int tile,
+                                             uint32_t *sh) {
+    const int base = tile * kScanTile + threadIdx.x * kScanPer256;
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer256; ++j)
+        if (base + j < ncell) s += count[base + j];
+    s = block_sum_256u(s, sh);
+    if (threadIdx.x == 0) tile_sums[tile] = s;
+}
+
+__device__ __forceinline__ void scan_tile_256(uint32_t *count, int ncell, const uint32_t *tile_sums,
+                                              uint32_t *cell_start, uint32_t N, int tile, int ntiles, uint32_t *sh) {
+    uint32_t pre = 0;
+    for (int b = threadIdx.x; b < tile; b += 256) pre += tile_sums[b];
+    pre = block_sum_256u(pre, sh);
+    const int base = tile * kScanTile + threadIdx.x * kScanPer256;
+    uint32_t c[kScanPer256];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPer256; ++j) {
+        c[j] = (base + j < ncell) ? count[base + j] : 0u;
+        tot += c[j];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[8 + wid] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < wid; ++w) wpre += sh[8 + w];
+    uint32_t run = pre + wpre + inc - tot;
+#pragma unroll
+    for (int j = 0; j < kScanPer256; ++j) {
+        if (base + j < ncell) {
+            cell_start[base + j] = run;
+            count[base + j] = 0u;
+        }
+        run += c[j];
+    }
+    if (tile == ntiles - 1 && threadIdx.x == 0) cell_start[ncell] = N;
+}
+
 __global__ void __launch_bounds__(256) k_scatter(const uint32_t *cell, const uint32_t *slot,
                                                  const uint32_t *cell_start, const uint32_t *id, uint32_t N,
                                                  unsigned long long *keys) {
     uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
-    keys[cell_start[cell[k]] + slot[k]] = ((unsigned long long)id[k] << 32) | (unsigned long long)k;
+    scatter_one(cell, slot, cell_start, id, keys, k);
 }
 
 // Thread i takes the key at scattered position i of its cell [lo, hi) and moves particle
@@ -354,9 +424,7 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t *cell, const uin
 // order and sets kErrCellOverflow (in the counter of the system that owns the cell when
 // c_off is given).
 template <int PREC>
-__global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
+__device__ __forceinline__ void gather_one(const GatherArgs &g, uint32_t i) {
     const unsigned long long key = g.keys[i];
     const uint32_t src = (uint32_t)key;
     const uint32_t c = g.cell[src];
@@ -376,6 +444,12 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
     g.out.id[p] = g.in.id[src];
     if (PREC == 1) ((uint4 *)g.rec)[p] = ((const uint4 *)g.rec_w)[src];
     else ((Rec64 *)g.rec)[p] = ((const Rec64 *)g.rec_w)[src];
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) k_gather(GatherArgs g) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < g.N) gather_one<PREC>(g, i);
 }
 
 __device__ __forceinline__ void set_state_body(const double *r, const double *v, const double *q_user,

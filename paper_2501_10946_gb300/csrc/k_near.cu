@@ -258,17 +258,37 @@ __device__ void near_one_f64(const NearArgs &a, uint32_t p, double *Fout, double
 constexpr int kWarpsPerBlock = 4;
 static_assert(kGlobalThreads == 32 * kWarpsPerBlock && kTileThreads == kGlobalThreads, "single-system block size");
 
-__device__ __forceinline__ void warp_partial(double v, double *U_part, unsigned blk) {
+// tid: thread index within the group of nt threads that handles block blk
+__device__ __forceinline__ void warp_partial(double v, double *U_part, unsigned blk, int tid, int nt) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) U_part[(size_t)blk * (blockDim.x >> 5) + (threadIdx.x >> 5)] = v;
+    if ((tid & 31) == 0) U_part[(size_t)blk * (unsigned)(nt >> 5) + (unsigned)(tid >> 5)] = v;
+}
+
+// Barriers of a group of NT threads: the whole CTA (barrier 0 with NT = blockDim.x), or a
+// part of a larger CTA with its own barrier BAR (the persistent batched step runs two
+// near-field tiles per CTA side by side).
+template <int NT, int BAR>
+__device__ __forceinline__ void group_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
+}
+template <int NT, int BAR>
+__device__ __forceinline__ int group_sync_and(int pred) {
+    int r;
+    asm volatile(
+        "{ .reg .pred a, b; setp.ne.s32 a, %1, 0; bar.red.and.pred b, %2, %3, a; selp.s32 %0, 1, 0, b; }"
+        : "=r"(r)
+        : "r"(pred), "n"(BAR), "n"(NT)
+        : "memory");
+    return r;
 }
 
 // One block of the per-particle path: particles p0 + [0, blockDim.x) of this system (global
 // record indices p0 .. p0 + N - 1).
 template <int PREC>
-__device__ __forceinline__ void near_global_block(const NearArgs &a, uint32_t p0, unsigned blk) {
-    const uint32_t local = blk * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void near_global_block(const NearArgs &a, uint32_t p0, unsigned blk,
+                                                  int tid = (int)threadIdx.x, int nt = (int)blockDim.x) {
+    const uint32_t local = blk * (unsigned)nt + (unsigned)tid;
     double U = 0.0;
     if (local < a.N) {
         const uint32_t p = p0 + local;
@@ -285,7 +305,7 @@ __device__ __forceinline__ void near_global_block(const NearArgs &a, uint32_t p0
             Fn[p] = F[0]; Fn[a.stride + p] = F[1]; Fn[2 * (size_t)a.stride + p] = F[2];
         }
     }
-    warp_partial(U, a.U_part, blk);
+    warp_partial(U, a.U_part, blk, tid, nt);
 }
 
 template <int PREC>
@@ -328,10 +348,10 @@ __device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW, FR> &S, i
 
 // DOT selects the form of the pre-filter test (see the threshold below): the expanded
 // one takes fewer instructions, the direct one fewer registers.
-template <int CAP, int NT, int MW, bool DOT, bool FR>
+// The tile is handled by NT threads (tid 0 .. NT-1) synchronised by barrier BAR.
+template <int CAP, int NT, int MW, bool DOT, bool FR, int BAR = 0>
 __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
-                                               TileSmem<CAP, NT, MW, FR> &S) {
-    const int tid = threadIdx.x;
+                                               TileSmem<CAP, NT, MW, FR> &S, int tid) {
     const int lane = tid & 31, wid = tid >> 5;
     const unsigned full = 0xffffffffu;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
@@ -371,7 +391,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         S.nf.naf[g] = dup2(-a.nc.af[g]);
         S.nf.cf[g] = dup2(a.nc.cf[g]);
     }
-    __syncthreads();
+    group_sync<NT, BAR>();
     // per-row prefix sums and the global slices of each row (a short serial loop per row
     // measured faster here than warp-wide scans)
     if (tid < 9) {
@@ -409,7 +429,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             S.chunk_n[tid][1] = cs[rowbase + 1] - cs[rowbase];
         }
     }
-    __syncthreads();
+    group_sync<NT, BAR>();
     if (tid == 0) {
         int b = 0;
         for (int r = 0; r < 9; ++r) {
@@ -418,7 +438,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         }
         S.row_base[9] = b;
     }
-    __syncthreads();
+    group_sync<NT, BAR>();
     const int region_n = S.row_base[9];
     const bool staged = !overflow && region_n <= CAP;
     // center row (r = 4): targets are region cells 1 .. wn-2, contiguous in global memory
@@ -462,7 +482,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                 for (int r = 0; r < 9; ++r) tot += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
                 S.fb[i + 1] = tot;
             }
-            __syncthreads();
+            group_sync<NT, BAR>();
             if (tid == 0) {
                 int b = 0;
                 S.fb[1] = 0;
@@ -471,7 +491,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                     S.fb[i + 1] = b;
                 }
             }
-            __syncthreads();
+            group_sync<NT, BAR>();
             // while the copies fly: the candidate list of each target cell i, rows 0..8 in
             // order, each row's cells i-1 .. i+1 in staging order
             for (int e = tid; e < 9 * ntc; e += NT) {
@@ -492,7 +512,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                     : "r"(bar)
                     : "memory");
             }
-            ok = __syncthreads_and((int)done) != 0;
+            ok = group_sync_and<NT, BAR>((int)done) != 0;
             if (!ok) {
                 if (tid == 0) atomicOr(&a.ctr->err, kErrNearStage);
                 // let the copies in flight land before the CTA exits (again bounded)
@@ -723,12 +743,18 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             Ufall += U;
         }
     }
-    warp_partial((double)sumU + Ufall, a.U_part, blk);
+    if (staged && region_n > 0) {
+        // the tile's mbarrier is done with (a CTA of the persistent step reuses its shared
+        // memory for the next tile, which initialises it again)
+        group_sync<NT, BAR>();
+        if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
+    }
+    warp_partial((double)sumU + Ufall, a.U_part, blk, tid, NT);
 }
 
 __global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true, false>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false> *>(smem_raw));
+    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true, false>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false> *>(smem_raw), (int)threadIdx.x);
 }
 
 // Batched systems: block -> (system, local block); each system uses tiles or the
@@ -750,7 +776,7 @@ __global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near
     const NearBatchGeom g = geom[lo];
     const unsigned blk = blockIdx.x - items[lo];
     if (g.tiled)
-        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, false, true>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true> *>(smem_raw));
+        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, false, true>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true> *>(smem_raw), (int)threadIdx.x);
     else near_global_block<1>(a, (uint32_t)g.W, blk);
 }
 

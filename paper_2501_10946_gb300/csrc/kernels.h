@@ -250,6 +250,36 @@ void launch_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int
                             cudaStream_t st);
 void launch_far_batch(const FarArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st);
 void launch_energy_batch(const EnergyArgs *args, int R, cudaStream_t st);
+
+// ---- persistent batched step (k_persist.cuh): one cooperative launch per pass ----
+// Grid-barrier state and the work counters of the near-field / structure-factor phase.
+// count, q_near, q_rho return to 0 after a completed launch; status is sticky (1: a
+// barrier wait gave up) until the host clears it.
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int q_near, q_rho;
+    int status;
+    int pad[3];
+};
+constexpr int kPersistNearThreadsHost = 128;   // threads of one near-field tile in the persistent step
+struct PersistArgs {
+    const BinArgs *bin; const uint32_t *it_bin; uint32_t nb_bin;
+    const SampleArgs *sample; const uint32_t *it_sample; uint32_t nb_sample;   // 4-slot sample blocks
+    uint32_t *count, *tile_sums, *cell_start; int ncell, ntiles; uint32_t N;
+    const uint32_t *cell, *slot, *id; unsigned long long *keys;
+    GatherArgs gather;
+    const NearArgs *near; const NearBatchGeom *geom; const uint32_t *it_near; uint32_t nb_near;
+    const RhoArgs *rho; const int *chunk; const uint32_t *it_rho; uint32_t nb_rho;
+    const RhoFinalArgs *rf; const uint32_t *it_rf; uint32_t nb_rf;
+    const FarArgs *far; const uint32_t *it_far; uint32_t nb_far;
+    DevCounters *ctr; int R; int advance;
+    GridBar *bar; long long wait_limit;   // polls of a barrier wait before it gives up
+};
+size_t persist_smem_bytes();
+// CTAs of the cooperative grid on `device` (all resident); returns a cudaError_t value
+int persist_grid(int device, int *grid);
+cudaError_t launch_step_persist(const PersistArgs &a, int grid, cudaStream_t st);
 // state of system r: rest buffer (offset), its charges and masses, first particle in the
 // caller's concatenated arrays
 struct SysStateArgs {

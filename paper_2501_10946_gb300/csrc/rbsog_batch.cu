@@ -88,10 +88,14 @@ struct SysShape {
     int G;
 };
 
-SysShape shape_of(const HostSystem &h, double near_target, int chunk) {
+// Threads of one near-field block: the batched kernel's CTA, or half a CTA of the
+// persistent step.
+int near_threads(const rbsog_batch *b) { return b->persistent ? kPersistNearThreadsHost : kNearBatchThreads; }
+
+SysShape shape_of(const HostSystem &h, double near_target, int chunk, int nthreads) {
     SysShape s{};
     near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target, kNearCapBatch,
-                  kNearBatchThreads, kNearMaxWBatch, true);
+                  nthreads, kNearMaxWBatch, true);
     s.G = (int)((h.N + (uint32_t)chunk - 1) / (uint32_t)chunk);
     return s;
 }
@@ -126,7 +130,7 @@ int build_args(rbsog_batch *b) {
         const int P = p.P;
         const int mode = p.ensemble == RBSOG_LANGEVIN ? 2 : 1;
         DevCounters *ctr = b->ctr + r;
-        const SysShape sh = shape_of(h, b->near_target, b->rho_chunk[r]);
+        const SysShape sh = shape_of(h, b->near_target, b->rho_chunk[r], near_threads(b));
         for (int k = 0; k < 2; ++k) {
             BinArgs &a = bin[k][r];
             a.in = offset_state(b->rest, po);
@@ -228,7 +232,7 @@ int build_args(rbsog_batch *b) {
             a.ctr = ctr;
             EnergyArgs &e = en[k][r];
             e.U_part = b->U_part + u_off;
-            e.nU = kNearBatchWarps * (int)sh.near_blocks;
+            e.nU = near_threads(b) / 32 * (int)sh.near_blocks;
             e.K_part = b->K_part + k_off;
             e.nK = (int)nbf;
             e.Ufar = b->Ufar + mo;
@@ -246,7 +250,7 @@ int build_args(rbsog_batch *b) {
             it[j] += cnt[j];
         }
         part_off += (size_t)sh.G * 8 * P;
-        u_off += kNearBatchWarps * (size_t)sh.near_blocks;
+        u_off += (size_t)(near_threads(b) / 32) * sh.near_blocks;
         k_off += nbf;
     }
     b->h_items.assign(R + 1, 0u);
@@ -276,7 +280,48 @@ int build_args(rbsog_batch *b) {
     return RBSOG_OK;
 }
 
+// Switch between the graph of batched kernels and the persistent step; the arguments are
+// rebuilt for the form's near-field block size (energy partials written before the switch
+// are no longer readable).
+int set_form(rbsog_batch *b, bool persistent) {
+    if (b->persistent == persistent) return RBSOG_OK;
+    BCK(cudaDeviceSynchronize(), "synchronize");
+    b->persistent = persistent;
+    b->dirty = true;
+    b->energies_stale = true;
+    return engine_commit(b);
+}
+
+// Per-kernel timing (profiling, tuning) runs the graph form's kernels one by one.
+struct GraphFormScope {
+    rbsog_batch *b;
+    bool was;
+    int code = RBSOG_OK;
+    explicit GraphFormScope(rbsog_batch *b_) : b(b_), was(b_->persistent) {
+        if (was) code = set_form(b, false);
+    }
+    ~GraphFormScope() {
+        if (was) set_form(b, true);
+    }
+};
+
+// A persistent step whose barrier wait gave up: report it and clear the barrier state
+// (the state of that pass is not valid).
+int check_barrier(rbsog_batch *b) {
+    GridBar h{};
+    BCK(cudaMemcpy(&h, b->bar, sizeof h, cudaMemcpyDeviceToHost), "read barrier state");
+    if (h.status) {
+        // the pass stopped between phases: barrier state, work counters and the cell counts
+        // (incremented by binning, cleared by the scan) start again from zero
+        BCK(cudaMemset(b->bar, 0, sizeof(GridBar)), "reset barrier state");
+        if (b->Ctot) BCK(cudaMemset(b->count, 0, sizeof(uint32_t) * (size_t)b->Ctot), "reset cell counts");
+        return engine_fail(b, RBSOG_ETIMEOUT, "a grid-barrier wait of the persistent step exceeded its limit");
+    }
+    return RBSOG_OK;
+}
+
 int check_all(rbsog_batch *b) {
+    if (int code = check_barrier(b)) return code;
     std::vector<DevCounters> c;
     if (int code = engine_counters(b, &c)) return code;
     for (int r = 0; r < b->R; ++r)
@@ -285,6 +330,9 @@ int check_all(rbsog_batch *b) {
 }
 
 int read_energies(rbsog_batch *b, rbsog_energy *e, cudaStream_t st) {
+    if (b->energies_stale)
+        return engine_fail(b, RBSOG_EINVAL, "the form changed since the last force evaluation: no energies to read");
+    if (int code = check_barrier(b)) return code;
     if (int code = engine_reduce_energies(b, st)) return code;
     std::vector<double> h(5 * (size_t)b->R);
     if (b->R) BCK(cudaMemcpyAsync(h.data(), b->energy, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
@@ -390,9 +438,10 @@ int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
         balloc(b, &b->d_near, R) || balloc(b, &b->d_geom, R) || balloc(b, &b->d_rho, R) ||
         balloc(b, &b->d_chunk, R) || balloc(b, &b->d_rf, R) || balloc(b, &b->d_state, R) ||
         balloc(b, &b->d_items, 6 * (R + 1)) || balloc(b, &b->d_coff, R + 1) || balloc(b, &b->d_off2, 2 * (R + 1)) ||
-        balloc(b, &b->d_sub_items, R + 1))
+        balloc(b, &b->d_sub_items, R + 1) || balloc(b, &b->bar, 1))
         return engine_fail(b, RBSOG_ENOMEM, "device allocation failed");
     if (cudaMemset(b->count, 0, sizeof(uint32_t) * C) != cudaSuccess ||
+        cudaMemset(b->bar, 0, sizeof(GridBar)) != cudaSuccess ||
         cudaMemset(b->ctr, 0, sizeof(DevCounters) * R) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -428,14 +477,14 @@ int engine_reduce_energies(rbsog_batch *b, cudaStream_t st) {
 }
 
 size_t engine_footprint(const rbsog_batch *b, const HostSystem &h) {
-    const SysShape sh = shape_of(h, b->near_target, chunk_for(h.N, b->rho_target));
+    const SysShape sh = shape_of(h, b->near_target, chunk_for(h.N, b->rho_target), near_threads(b));
     const size_t per_particle = 2 * 9 * 8 - 2 * 4   // rest + work state (id is 4 bytes)
                                 + 2 * 3 * 8          // caller-order staging
                                 + 2 * 3 * 4 + 2 * 16 // F, Fn, work-order and id-order records
                                 + 16 + 2 * 4 + 8;    // record, cell/slot, sort key
     const size_t per_mode = 3 * 4 * 2 + 8 + 16 + kGTab32Bytes + 8;
     return (size_t)h.N * per_particle + (size_t)h.box.ncell * 12 + (size_t)h.p.P * per_mode +
-           (size_t)sh.G * 8 * h.p.P * 16 + kNearBatchWarps * (size_t)sh.near_blocks * 8 + far_batch_blocks(h.N) * 8;
+           (size_t)sh.G * 8 * h.p.P * 16 + (size_t)(near_threads(b) / 32) * sh.near_blocks * 8 + far_batch_blocks(h.N) * 8;
 }
 
 bool engine_fits(const rbsog_batch *b, const HostSystem &h) {
@@ -550,9 +599,9 @@ int engine_commit(rbsog_batch *b) {
     size_t part = 0, upart = 4, kpart = 1;
     for (int r = 0; r < b->R; ++r) {
         const HostSystem &h = b->sys[r];
-        const SysShape sh = shape_of(h, b->near_target, b->rho_chunk[r]);
+        const SysShape sh = shape_of(h, b->near_target, b->rho_chunk[r], near_threads(b));
         part += (size_t)sh.G * 8 * (size_t)h.p.P;
-        upart += kNearBatchWarps * (size_t)sh.near_blocks;
+        upart += (size_t)(near_threads(b) / 32) * sh.near_blocks;
         kpart += far_batch_blocks(h.N);
     }
     BCK(regrow(b, &b->partial, &b->cap_part, part), "alloc partials");
@@ -604,10 +653,42 @@ int engine_get_state(rbsog_batch *b, int first, int count, double *r, double *v,
     return RBSOG_OK;
 }
 
+// The persistent form of one pass: every phase in one cooperative launch.
+int enqueue_persistent(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far) {
+    if (!b->pgrid) {
+        int grid = 0;
+        const int e = persist_grid(b->device, &grid);
+        if (e) return engine_cuda_fail(b, (cudaError_t)e, "persistent grid size");
+        b->pgrid = grid;
+    }
+    const int R = b->R;
+    PersistArgs a{};
+    a.bin = b->d_bin[set]; a.it_bin = items_of(b, kItBin); a.nb_bin = b->nb[kItBin];
+    a.sample = b->d_sample; a.it_sample = items_of(b, kItSample); a.nb_sample = b->nb[kItSample];
+    a.count = b->count; a.tile_sums = b->tile_sums; a.cell_start = b->cell_start; a.ncell = b->Ctot;
+    a.ntiles = (b->Ctot + kScanTile - 1) / kScanTile; a.N = b->Ntot;
+    a.cell = b->cell; a.slot = b->slot; a.id = b->work.id; a.keys = b->keys;
+    GatherArgs &g = a.gather;
+    g.in = b->work; g.out = b->rest; g.keys = b->keys; g.cell = b->cell; g.cell_start = b->cell_start; g.ctr = b->ctr;
+    g.c_off = b->d_coff; g.R = R; g.rec_w = b->rec_w; g.rec = b->rec; g.N = b->Ntot;
+    a.near = b->d_near; a.geom = b->d_geom; a.it_near = items_of(b, kItNear); a.nb_near = b->nb[kItNear];
+    a.rho = b->d_rho; a.chunk = b->d_chunk; a.it_rho = items_of(b, kItRho); a.nb_rho = b->nb[kItRho];
+    a.rf = b->d_rf; a.it_rf = items_of(b, kItRhoFinal); a.nb_rf = b->nb[kItRhoFinal];
+    a.far = far ? far : b->d_far[set]; a.it_far = items_of(b, kItFar); a.nb_far = b->nb[kItFar];
+    a.ctr = b->ctr; a.R = R; a.advance = set;
+    a.bar = b->bar; a.wait_limit = b->wait_limit;
+    BCK(launch_step_persist(a, b->pgrid, st), "persistent step launch");
+    b->energies_stale = false;
+    return RBSOG_OK;
+}
+
 int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far, cudaEvent_t *ev) {
     if (int code = engine_commit(b)) return code;
     const int R = b->R;
     if (R == 0) return RBSOG_OK;
+    if (b->persistent && !ev) return enqueue_persistent(b, st, set, far);
+    if (b->persistent) return engine_fail(b, RBSOG_EINVAL, "per-kernel timing needs the graph form");
+    b->energies_stale = false;
     auto mark = [&](int g) {
         if (ev) cudaEventRecord(ev[g], st);
     };
@@ -880,6 +961,8 @@ int rbsog_batch_set_rho_chunk(rbsog_batch *b, const int32_t *rho_chunk) {
 
 int rbsog_batch_profile(rbsog_batch *b, int32_t nsteps, double *ms, void *stream) {
     if (!b || !ms || nsteps < 1) return engine_fail(b, RBSOG_EINVAL, "batch or ms is NULL, or nsteps < 1");
+    GraphFormScope form(b);
+    if (form.code) return form.code;
     cudaStream_t st = (cudaStream_t)stream;
     EventSet es;
     if (!es.ok) return engine_fail(b, RBSOG_ECUDA, "event creation failed");
@@ -896,6 +979,27 @@ int rbsog_batch_profile(rbsog_batch *b, int32_t nsteps, double *ms, void *stream
     return check_all(b);
 }
 
+int rbsog_batch_set_persistent(rbsog_batch *b, int32_t enable) {
+    if (!b) return engine_fail(b, RBSOG_EINVAL, "batch is NULL");
+    if (enable) {
+        int coop = 0;
+        BCK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device), "device attribute");
+        if (!coop) return engine_fail(b, RBSOG_EUNSUPPORTED, "the device has no cooperative launch");
+    }
+    return set_form(b, enable != 0);
+}
+
+int rbsog_batch_set_wait_limit(rbsog_batch *b, int64_t polls) {
+    if (!b || polls < 1) return engine_fail(b, RBSOG_EINVAL, "batch is NULL or polls < 1");
+    BCK(cudaDeviceSynchronize(), "synchronize");
+    b->wait_limit = polls;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return RBSOG_OK;
+}
+
 int rbsog_batch_set_shapes(rbsog_batch *b, double near_target, int32_t rho_target) {
     if (!b) return engine_fail(b, RBSOG_EINVAL, "batch is NULL");
     if (!(near_target >= 8.0 && near_target <= 4096.0) || rho_target < 64)
@@ -905,6 +1009,8 @@ int rbsog_batch_set_shapes(rbsog_batch *b, double near_target, int32_t rho_targe
 
 int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t *rho_target, void *stream) {
     if (!b || reps < 1) return engine_fail(b, RBSOG_EINVAL, "batch is NULL or reps < 1");
+    GraphFormScope form(b);
+    if (form.code) return form.code;
     cudaStream_t st = (cudaStream_t)stream;
     EventSet es;
     if (!es.ok) return engine_fail(b, RBSOG_EINVAL, "event creation failed");

@@ -74,7 +74,7 @@ EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_set_state_
            "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
            "rbsog_batch_forces", "rbsog_batch_step", "rbsog_batch_set_ksample", "rbsog_batch_get_ksample",
            "rbsog_batch_layout", "rbsog_batch_set_rho_chunk", "rbsog_batch_set_shapes", "rbsog_batch_tune",
-           "rbsog_batch_profile", "rbsog_batch_last_error", "rbsog_batch_free", "rbsog_server_create",
+           "rbsog_batch_profile", "rbsog_batch_set_persistent", "rbsog_batch_set_wait_limit", "rbsog_batch_last_error", "rbsog_batch_free", "rbsog_server_create",
            "rbsog_server_submit", "rbsog_server_run", "rbsog_server_job", "rbsog_server_stats", "rbsog_server_clock",
            "rbsog_server_last_error", "rbsog_server_free"]
 RBSOG_NPROF = 10
@@ -134,6 +134,8 @@ def load(build_if_missing: bool = True):
     L.rbsog_batch_set_shapes.argtypes = [vp, C.c_double, i32]
     L.rbsog_batch_tune.argtypes = [vp, i32, dp, C.POINTER(i32), vp]
     L.rbsog_batch_profile.argtypes = [vp, i32, vp, vp]
+    L.rbsog_batch_set_persistent.argtypes = [vp, i32]
+    L.rbsog_batch_set_wait_limit.argtypes = [vp, i64]
     L.rbsog_batch_last_error.argtypes = [vp]
     L.rbsog_batch_last_error.restype = C.c_char_p
     L.rbsog_batch_free.argtypes = [vp]
@@ -405,6 +407,14 @@ def rbsog_batch_tune(b, reps: int = 3, stream=None):
     rt = C.c_int32(0)
     _bcheck(b, load().rbsog_batch_tune(b, int(reps), C.byref(nt), C.byref(rt), _stream(stream)))
     return nt.value, rt.value
+
+
+def rbsog_batch_set_persistent(b, enable: bool = True):
+    _bcheck(b, load().rbsog_batch_set_persistent(b, 1 if enable else 0))
+
+
+def rbsog_batch_set_wait_limit(b, polls: int):
+    _bcheck(b, load().rbsog_batch_set_wait_limit(b, int(polls)))
 
 
 def rbsog_batch_profile(b, nsteps: int, stream=None) -> dict:
