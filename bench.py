@@ -245,6 +245,19 @@ def batched_sweep(torch, R, steps, warmup, R_systems=256):
         prof = R.rbsog_batch_profile(b, 3, stream=stream)
         out["groups_ms_per_step"] = {k: round(t / 3, 4) for k, t in prof.items()}
         out["gpu_launches_per_step"] = KERNELS_PER_STEP
+        # the persistent form: the whole step as one cooperative launch (graph-captured)
+        R.rbsog_batch_set_persistent(b, True)
+        R.rbsog_batch_step(b, R_systems, warmup, stream=stream)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        R.rbsog_batch_step(b, R_systems, steps, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        R.rbsog_batch_get_state(b, stream=stream)          # reports a barrier wait that ran out
+        pms = e0.elapsed_time(e1)
+        out["persistent"] = {"value": Ntot * steps / (pms * 1e-3), "unit": "particle-steps/s",
+                             "ms_per_step": pms / steps, "gpu_launches_per_step": 1,
+                             "form": "one persistent cooperative launch per step, CUDA-graph replay"}
     finally:
         R.rbsog_batch_free(b)
     # the plain form: each system its own context, one after another
