@@ -210,6 +210,57 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
     return out
 
 
+def sharded_evaluations(w, steps, warmup, rank, ws, torch, R):
+    """Domain-decomposed force evaluations of the workload: rank k owns slab k of ws slabs
+    along x (with its halo of width r_c), and every evaluation is rbsog_forces_partial, an
+    all-reduce of the 2P values of rho (NCCL across ranks), and rbsog_forces_complete.  No
+    integration and no particle migration: the decomposition stays that of the initial
+    state.  Returns the max-over-ranks milliseconds of `steps` evaluations."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    r, q, m = W.positions(w), W.charges(w), W.masses(w)
+    idx, n_owned = R.rbsog_slab_split(r, w.box, 0, ws, rank, w.r_c)
+    p = R.make_params(w, precision=R.RBSOG_FP32, device=dev.index, q2_total=float(np.sum(q * q)),
+                      qsum_total=float(np.sum(q)))
+    ctx = R.rbsog_init(p, len(idx), q[idx], m[idx])
+    try:
+        R.rbsog_set_owned(ctx, n_owned)
+        R.rbsog_set_state(ctx, torch.tensor(r[idx], device=dev, dtype=torch.float64), stream=stream)
+        rho = torch.zeros((w.P, 2), device=dev, dtype=torch.float64)
+        F = torch.zeros((len(idx), 3), device=dev, dtype=torch.float64)
+
+        def evaluate():
+            R.rbsog_forces_partial(ctx, rho, stream=stream)
+            if ws > 1:
+                torch.distributed.all_reduce(rho)
+            R.rbsog_forces_complete(ctx, rho, F, stream=stream)
+
+        for _ in range(warmup):
+            evaluate()
+        if torch.distributed.is_initialized():
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            evaluate()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+    finally:
+        R.rbsog_free(ctx)
+    return {"value": w.N * steps / (ms * 1e-3), "unit": "particle-evaluations/s", "ms_per_evaluation": ms / steps,
+            "ranks": ws, "owned_on_rank0": n_owned, "halo_on_rank0": len(idx) - n_owned,
+            "form": "slabs along x, halo r_c; rbsog_forces_partial + all-reduce of rho (2P doubles) + "
+                    "rbsog_forces_complete; no integration or migration",
+            "measured_ranks": ws}
+
+
 def batched_sweep(torch, R, steps, warmup, R_systems=256):
     """Batched replica sweep: R_systems independent systems of uneven N in one graph per
     step (autotuned shapes) against the same systems advanced one context at a time."""
@@ -490,6 +541,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=64,
                     help="jobs of the served stream (the full stream of the served workload is 2000)")
+    ap.add_argument("--shard", action="store_true",
+                    help="also time domain-decomposed force evaluations (one slab per rank)")
     ap.add_argument("--no-serve-plain", action="store_true",
                     help="skip the one-context-per-job comparison of the served stream")
     args = ap.parse_args()
@@ -526,6 +579,7 @@ def main():
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     res = rbsog_replica(w, R.RBSOG_FP32, args.steps, args.warmup, rank, torch, R, clocks=clocks,
                         profile_steps=10 if rank == 0 else 0, e2e_steps=5 if rank == 0 else 0)
+    sharded = sharded_evaluations(w, args.steps, max(3, args.warmup), rank, ws, torch, R) if args.shard else None
     ms = res["ms"]
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
@@ -549,6 +603,8 @@ def main():
     line["roofline"] = rf
     line["clocks"] = clocks.summary() if clocks else None
     line["gpu_launches"] = KERNELS_PER_STEP * args.steps
+    if sharded is not None:
+        line["sharded"] = sharded
     e2e_rate = w.N * res["e2e_steps"] / res["e2e_s"]
     line["e2e"] = {"value": e2e_rate, "unit": "particle-steps/s", "h2d_bytes_per_step": res["e2e_h2d"],
                    "d2h_bytes_per_step": res["e2e_d2h"], "path": res["e2e_path"]}

@@ -126,6 +126,10 @@ typedef struct rbsog_params {
                                evaluation; 0 selects 64, negative selects none */
     int32_t temperature;    /* RBSOG_KT_TARGET | RBSOG_KT_INSTANT (single contexts only; a no-op
                                for calF = 1 and calF = k^2, which do not depend on T) */
+    double q2_total;        /* > 0: sum q^2 of the whole system when the context holds one
+                               domain of it (rbsog_set_owned); enters calF of Eq. (62), S and
+                               the coefficients.  0: the context's own charges */
+    double qsum_total;      /* with q2_total > 0: sum q of the whole system (the k = 0 term) */
 } rbsog_params;
 
 typedef struct rbsog_energy {
@@ -290,6 +294,49 @@ int rbsog_build_sog(double lam, double r_c, double eps, int32_t mode, int32_t M1
  * reported through rbsog_last_error(NULL). */
 int rbsog_rho_noalloc(const double *r_dev, const double *q_dev, int64_t N, const double *box_host,
                       const int32_t *m_dev, int32_t P, double *rho_dev, void *stream);
+
+/* ---- Domain decomposition (Sec. 4.3: local structure factors, a global reduction of
+ * rho, a broadcast) ----------------------------------------------------------------------
+ * A context can hold one domain of a larger system: its particles are the domain's own
+ * ("owned") particles followed by halo copies of the particles of neighbouring domains
+ * within the cutoff.  The halo particles take part in the near field of the owned ones
+ * and nothing else.  Every domain's context uses the whole system's box, seed and
+ * parameters, with q2_total / qsum_total of the whole system, so all domains draw the same
+ * modes with the same coefficients.  One force evaluation is then:
+ *   rbsog_forces_partial   every domain: cell list and near field of its particles, the
+ *                          k-sample, and rho over its owned particles -> partial rho;
+ *   (caller)               sum the partial rho over the domains (an all-reduce of 2P
+ *                          doubles: MPI, NCCL, gloo, or a host sum);
+ *   rbsog_forces_complete  every domain: the far force of Eq. (60) from the summed rho,
+ *                          plus the near force, for its particles; the rows of the owned
+ *                          particles are the whole system's forces on them.
+ * The energies of such an evaluation are not available (RBSOG_EINVAL from an energy read).
+ * rbsog_slab_split computes a domain's particle list for slabs along one axis. */
+
+/* The first n_owned particles (1 <= n_owned <= N) are the context's own; only they enter
+ * rho(k) (in every evaluation).  Default N.  Synchronous. */
+int rbsog_set_owned(rbsog_ctx *ctx, int64_t n_owned);
+
+/* First half of a domain's force evaluation (see above): writes the partial rho over the
+ * owned particles as P (Re, Im) pairs to rho_partial (host or device).  One fresh draw of
+ * modes (or the injected set).  Synchronous. */
+int rbsog_forces_partial(rbsog_ctx *ctx, double *rho_partial, void *stream);
+
+/* Second half: rho (P (Re, Im) pairs, host or device) is the sum of every domain's partial
+ * rho; writes the total forces of all the context's particles to F ([N][3], caller order,
+ * host or device; may be NULL), valid for the owned ones.  The forces are kept as those
+ * of the current state (rbsog_get_forces).  RBSOG_EINVAL unless rbsog_forces_partial came
+ * first.  Synchronous. */
+int rbsog_forces_complete(rbsog_ctx *ctx, const double *rho, double *F, void *stream);
+
+/* Host only: the particle list of slab `slab` of `nslabs` equal slabs along `axis` (0..2)
+ * of the periodic box: idx_out[0 .. *n_owned) are the particles whose wrapped coordinate
+ * lies in the slab (ascending index), idx_out[*n_owned .. *n_local) those of other slabs
+ * within `halo` of it (periodic distance along the axis; ascending index).  idx_out has
+ * room for N entries.  Requires halo <= L / 2 (the near field's minimum image then finds
+ * every pair across the slab's faces once).  RBSOG_EINVAL on bad arguments. */
+int rbsog_slab_split(int64_t N, const double *r_host, const double *box, int32_t axis, int32_t nslabs,
+                     int32_t slab, double halo, int64_t *idx_out, int64_t *n_owned, int64_t *n_local);
 
 /* Message of the last failed call on ctx (or of the last failed rbsog_init when ctx
  * is NULL).  The pointer stays valid until the next call on the same context. */

@@ -274,7 +274,7 @@ __device__ __forceinline__ void rho_final_body(const RhoFinalArgs &a, int ML, un
 template <int PREC>
 __global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
     __shared__ double2 sh[8][32];
-    rho_final_body<PREC>(a, ML, blockIdx.x, blockIdx.x == 0, sh);
+    rho_final_body<PREC>(a, ML, blockIdx.x, blockIdx.x == 0 && !a.keep_draw, sh);
 }
 
 __global__ void __launch_bounds__(256) k_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int R) {

@@ -176,6 +176,7 @@ struct RhoFinalArgs {
     void *gtab;                // gather table: float (FP32) / double (FP64), [P] x {ckx,cky,ckz,Re,Im} + int m
     double *Ufar;              // [P]: coef_l |rho_l|^2 / 2
     DevCounters *ctr;
+    int keep_draw;             // 1: the draw counter is not advanced (a reduced rho set from outside)
 };
 void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st);
 struct FarArgs {

@@ -63,6 +63,8 @@ struct rbsog_ctx {
     cudaGraphExec_t graph = nullptr;
     bool force_valid = false;
     bool energy_valid = false;     // the energy partials belong to the current state
+    uint32_t n_owned = 0;          // particles 0 .. n_owned-1 enter rho (domain decomposition)
+    bool partial_done = false;     // rbsog_forces_partial ran; rbsog_forces_complete may follow
     SamplerTables tab{};
     // Metropolis-Hastings chains (RBSOG_SAMPLER_MH)
     bool mh = false;
@@ -192,6 +194,14 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
         h.qsum += q_host[i];
     }
     if (!(h.Q2 > 0)) return bad(RBSOG_EINVAL, "all charges are zero");
+    // the context's own sum for the self energy; the whole system's for calF, S and the
+    // k = 0 term when the context holds one domain of it
+    const double Q2_own = h.Q2;
+    if (!(p.q2_total >= 0.0)) return bad(RBSOG_EINVAL, "q2_total must be >= 0");
+    if (p.q2_total > 0.0) {
+        h.Q2 = p.q2_total;
+        h.qsum = p.qsum_total;
+    }
     // box and cells
     Box &bx = h.box;
     long long ncell = 1;
@@ -253,7 +263,7 @@ int setup_system(const rbsog_params &p, int64_t N, const double *q_host, const d
             F0 += a;
         }
     }
-    h.Uself = -0.5 * h.Q2 * F0;
+    h.Uself = -0.5 * Q2_own * F0;
     h.Ufar0 = h.Fhat0 * h.qsum * h.qsum / (2.0 * h.V);
     // sampling tables (Eq. 59): the measure's mixture of separable components.  calF of
     // Eq. (62) and calF = 1 draw from Fhat (component m: Gaussian m, plain per-axis tables;
@@ -516,8 +526,9 @@ struct ProfScope {
 };
 
 // Enqueue one force evaluation (and, with integrate != 0, one full step).
+// part = 1: stop after the structure factor (the first half of a domain's evaluation)
 int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double *Fn_user, double *Ff_user,
-            int advance) {
+            int advance, int part = 0) {
     const int prec = c->prec;
     const uint32_t N = c->N;
     BinArgs b{};
@@ -554,7 +565,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
         else launch_sample(sa, s2);
     };
     RhoArgs ra{};
-    ra.rec = c->rec_id; ra.N = N; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
+    ra.rec = c->rec_id; ra.N = c->n_owned; ra.m = c->modes; ra.P = c->p.P; ra.partial = c->partial; ra.G = c->G;
     RhoFinalArgs rf{};
     rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
     for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
@@ -603,6 +614,11 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     } else {
         { ProfScope ps(c, st, 6); launch_rho(prec, ra, st); }
         { ProfScope ps(c, st, 7); launch_rho_final(prec, rf, st); }
+    }
+    if (part) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+        return RBSOG_OK;
     }
     FarArgs fa{};
     fa.rec = c->rec; fa.N = N; fa.stride = N; fa.P = c->p.P; fa.gtab = c->gtab; fa.m = c->modes; fa.Fn = c->Fn; fa.F = c->F;
@@ -680,6 +696,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
     rbsog_ctx *c = new rbsog_ctx();
     c->p = p;
     c->mh = p.sampler == RBSOG_SAMPLER_MH;
+    c->n_owned = (uint32_t)N;
     c->instT = instT;
     c->nshell = (int)shell_k2.size();
     c->N = (uint32_t)N;
@@ -814,6 +831,7 @@ int rbsog_set_state(rbsog_ctx *c, const double *r, const double *v, void *stream
     CK(cudaGetLastError(), "set_state");
     c->force_valid = false;
     c->energy_valid = false;
+    c->partial_done = false;
     return RBSOG_OK;
 }
 
@@ -950,6 +968,96 @@ int rbsog_step(rbsog_ctx *c, int32_t nsteps, rbsog_energy *e, void *stream) {
     }
     for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->graph, st), "graph launch");
     if (e) return read_energy(c, e, st);
+    return RBSOG_OK;
+}
+
+int rbsog_set_owned(rbsog_ctx *c, int64_t n_owned) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    if (n_owned < 1 || n_owned > (int64_t)c->N) return fail(c, RBSOG_EINVAL, "n_owned must be in [1, N]");
+    CK(cudaDeviceSynchronize(), "synchronize");
+    c->n_owned = (uint32_t)n_owned;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return RBSOG_OK;
+}
+
+int rbsog_forces_partial(rbsog_ctx *c, double *rho_partial, void *stream) {
+    if (!c || !rho_partial) return fail(c, RBSOG_EINVAL, "ctx or rho_partial is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int r = enqueue(c, st, 0, nullptr, nullptr, nullptr, 0, 1)) return r;
+    CK(cudaMemcpyAsync(rho_partial, c->rho, sizeof(double2) * (size_t)c->p.P, cudaMemcpyDefault, st), "copy rho");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    c->partial_done = true;
+    c->energy_valid = false;
+    return check_device_errors(c);
+}
+
+int rbsog_forces_complete(rbsog_ctx *c, const double *rho, double *F, void *stream) {
+    if (!c || !rho) return fail(c, RBSOG_EINVAL, "ctx or rho is NULL");
+    if (!c->partial_done) return fail(c, RBSOG_EINVAL, "rbsog_forces_partial must come first");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int prec = c->prec;
+    const size_t P = (size_t)c->p.P;
+    // the summed rho as the only nonzero per-block partial: the fixed-order reduction of
+    // rho_final then returns it exactly and builds the gather table and the U*_F terms
+    CK(cudaMemsetAsync(c->partial, 0, sizeof(double2) * (size_t)c->G * 8 * P, st), "clear partials");
+    CK(cudaMemcpyAsync(c->partial, rho, sizeof(double2) * P, cudaMemcpyDefault, st), "copy rho");
+    RhoFinalArgs rf{};
+    rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
+    for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
+    rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr; rf.keep_draw = 1;
+    launch_rho_final(prec, rf, st);
+    const size_t bytes = 3 * (size_t)c->N * sizeof(double);
+    double *Fd = nullptr;
+    if (F) Fd = is_device_ptr(F) ? F : c->stage_a;
+    FarArgs fa{};
+    fa.rec = c->rec; fa.N = c->N; fa.stride = c->N; fa.P = c->p.P; fa.gtab = c->gtab; fa.m = c->modes; fa.Fn = c->Fn;
+    fa.F = c->F; fa.st = c->rest; fa.integrate = 0; fa.dt = c->p.dt; fa.K_part = c->K_part;
+    fa.F_user = Fd; fa.ctr = c->ctr;
+    c->nK = launch_far(prec, fa, st);
+    launch_close_eval(c->ctr, 0, st);
+    CK(cudaGetLastError(), "kernel launch");
+    if (F && Fd != F) CK(cudaMemcpyAsync(F, Fd, bytes, cudaMemcpyDefault, st), "copy forces out");
+    CK(cudaStreamSynchronize(st), "synchronize");
+    c->partial_done = false;
+    c->force_valid = true;
+    c->energy_valid = false;
+    return check_device_errors(c);
+}
+
+int rbsog_slab_split(int64_t N, const double *r, const double *box, int32_t axis, int32_t nslabs, int32_t slab,
+                     double halo, int64_t *idx_out, int64_t *n_owned, int64_t *n_local) {
+    if (N < 1 || !r || !box || !idx_out || !n_owned || !n_local) return fail(nullptr, RBSOG_EINVAL, "bad argument");
+    if (axis < 0 || axis > 2 || nslabs < 1 || slab < 0 || slab >= nslabs || !(box[axis] > 0) || !(halo >= 0))
+        return fail(nullptr, RBSOG_EINVAL, "bad axis, slab count, slab or halo");
+    const double L = box[axis], w = L / nslabs;
+    if (!(halo <= 0.5 * L)) return fail(nullptr, RBSOG_EINVAL, "halo must be at most half the box");
+    const double lo = slab * w, hi = (slab + 1) * w;
+    auto wrap = [&](double x) {
+        double y = x - L * std::floor(x / L);
+        return (y >= L) ? y - L : y;
+    };
+    // slab of a wrapped coordinate: floor(x / w), clamped for the rounding at the top
+    auto slab_of = [&](double x) {
+        int k = (int)std::floor(wrap(x) / w);
+        return k < 0 ? 0 : (k >= nslabs ? nslabs - 1 : k);
+    };
+    int64_t no = 0;
+    for (int64_t i = 0; i < N; ++i)
+        if (slab_of(r[3 * i + axis]) == slab) idx_out[no++] = i;
+    int64_t nl = no;
+    if (nslabs > 1)
+        for (int64_t i = 0; i < N; ++i) {
+            const double x = wrap(r[3 * i + axis]);
+            if (slab_of(r[3 * i + axis]) == slab) continue;
+            // periodic distance from x to the slab interval [lo, hi)
+            const double d_lo = std::fmod(lo - x + 2.0 * L, L), d_hi = std::fmod(x - hi + 2.0 * L, L);
+            if (std::fmin(d_lo, d_hi) < halo) idx_out[nl++] = i;
+        }
+    *n_owned = no;
+    *n_local = nl;
     return RBSOG_OK;
 }
 

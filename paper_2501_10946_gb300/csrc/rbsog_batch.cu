@@ -792,6 +792,8 @@ int rbsog_batch_init(const rbsog_params *params, int32_t R, const int64_t *N, co
     for (int r = 0; r < R; ++r) {
         if (params[r].precision != RBSOG_FP32)
             return engine_fail(nullptr, RBSOG_EUNSUPPORTED, "batched systems run the FP32 path only");
+        if (params[r].q2_total != 0.0)
+            return engine_fail(nullptr, RBSOG_EUNSUPPORTED, "batched systems are whole systems (q2_total = 0)");
         if (params[r].sampler != RBSOG_SAMPLER_IID || params[r].temperature != RBSOG_KT_TARGET)
             return engine_fail(nullptr, RBSOG_EUNSUPPORTED,
                                "batched systems draw i.i.d. modes at the target temperature");

@@ -137,7 +137,8 @@ int admit(rbsog_server *s) {
             code = RBSOG_EUNSUPPORTED;
             err = "served jobs run the FP32 path";
         }
-        if (code == RBSOG_OK && (hs.p.sampler != RBSOG_SAMPLER_IID || hs.p.temperature != RBSOG_KT_TARGET)) {
+        if (code == RBSOG_OK && (hs.p.sampler != RBSOG_SAMPLER_IID || hs.p.temperature != RBSOG_KT_TARGET ||
+                                 hs.p.q2_total != 0.0)) {
             code = RBSOG_EUNSUPPORTED;
             err = "served jobs draw i.i.d. modes at the target temperature";
         }

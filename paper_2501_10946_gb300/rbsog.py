@@ -32,7 +32,7 @@ class rbsog_params(C.Structure):
                 ("precision", C.c_int32), ("ensemble", C.c_int32), ("sog_mode", C.c_int32),
                 ("sog_M1", C.c_int32), ("sog_M2", C.c_int32), ("device", C.c_int32), ("sampling", C.c_int32),
                 ("egs_nu", C.c_double), ("sampler", C.c_int32), ("mh_sweeps", C.c_int32), ("mh_burnin", C.c_int32),
-                ("temperature", C.c_int32)]
+                ("temperature", C.c_int32), ("q2_total", C.c_double), ("qsum_total", C.c_double)]
 
 
 class rbsog_energy(C.Structure):
@@ -69,7 +69,7 @@ class RbsogError(RuntimeError):
 
 _lib = None
 EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_set_state_forces", "rbsog_get_forces", "rbsog_set_state_forces_f32", "rbsog_get_forces_f32", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
-           "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog", "rbsog_get_temperature",
+           "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog", "rbsog_get_temperature", "rbsog_set_owned", "rbsog_forces_partial", "rbsog_forces_complete", "rbsog_slab_split",
            "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_rho_noalloc",
            "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
            "rbsog_batch_forces", "rbsog_batch_step", "rbsog_batch_set_ksample", "rbsog_batch_get_ksample",
@@ -112,6 +112,10 @@ def load(build_if_missing: bool = True):
     L.rbsog_get_cells.argtypes = [vp, vp, vp, vp]
     L.rbsog_get_sog.argtypes = [vp, dp, dp, C.POINTER(i32), C.POINTER(i32), dp, dp, dp]
     L.rbsog_get_temperature.argtypes = [vp, dp, dp]
+    L.rbsog_set_owned.argtypes = [vp, i64]
+    L.rbsog_forces_partial.argtypes = [vp, vp, vp]
+    L.rbsog_forces_complete.argtypes = [vp, vp, vp, vp]
+    L.rbsog_slab_split.argtypes = [i64, vp, vp, i32, i32, i32, C.c_double, vp, C.POINTER(i64), C.POINTER(i64)]
     L.rbsog_build_sog.argtypes = [C.c_double, C.c_double, C.c_double, i32, i32, i32, vp]
     L.rbsog_profile.argtypes = [vp, i32]
     L.rbsog_profile_read.argtypes = [vp, vp, vp]
@@ -282,6 +286,33 @@ def rbsog_get_temperature(ctx) -> tuple:
     kT, S = C.c_double(), C.c_double()
     _check(ctx, load().rbsog_get_temperature(ctx, C.byref(kT), C.byref(S)))
     return kT.value, S.value
+
+
+def rbsog_set_owned(ctx, n_owned: int):
+    _check(ctx, load().rbsog_set_owned(ctx, int(n_owned)))
+
+
+def rbsog_forces_partial(ctx, rho_out, stream=None):
+    """Partial rho over the owned particles into rho_out ([P][2], host numpy or device tensor)."""
+    _check(ctx, load().rbsog_forces_partial(ctx, _ptr(rho_out), _stream(stream)))
+
+
+def rbsog_forces_complete(ctx, rho, F=None, stream=None):
+    """Far force from the summed rho ([P][2], host or device) plus the near force into F."""
+    if isinstance(rho, np.ndarray):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+    _check(ctx, load().rbsog_forces_complete(ctx, _ptr(rho), _ptr(F), _stream(stream)))
+
+
+def rbsog_slab_split(r, box, axis: int, nslabs: int, slab: int, halo: float):
+    """(idx, n_owned): the slab's owned particles, then its halo copies (host arrays)."""
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    idx = np.zeros(r.shape[0], dtype=np.int64)
+    no, nl = C.c_int64(), C.c_int64()
+    _check(None, load().rbsog_slab_split(r.shape[0], r.ctypes.data, box.ctypes.data, int(axis), int(nslabs),
+                                         int(slab), float(halo), idx.ctypes.data, C.byref(no), C.byref(nl)))
+    return idx[:nl.value].copy(), int(no.value)
 
 
 def rbsog_build_sog(lam: float, r_c: float, eps: float, mode: int = RBSOG_SOG_MINIMAL, M1: int = 0,
@@ -515,7 +546,8 @@ def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int 
                 sog_mode: int = RBSOG_SOG_MINIMAL, M1: int = 0, M2: int = 0, device: int = 0,
                 ensemble: int | None = None, dt: float | None = None,
                 sampling: int = RBSOG_SAMPLING_ADAPTIVE, egs_nu: float = 0.0, sampler: int = RBSOG_SAMPLER_IID,
-                mh_sweeps: int = 0, mh_burnin: int = 0, temperature: int = RBSOG_KT_TARGET) -> rbsog_params:
+                mh_sweeps: int = 0, mh_burnin: int = 0, temperature: int = RBSOG_KT_TARGET, q2_total: float = 0.0,
+                qsum_total: float = 0.0) -> rbsog_params:
     """rbsog_params from a workloads.Workload (plain field copy)."""
     p = rbsog_params()
     for d in range(3):
@@ -543,4 +575,6 @@ def make_params(w, precision: int = RBSOG_FP32, P: int | None = None, seed: int 
     p.mh_sweeps = int(mh_sweeps)
     p.mh_burnin = int(mh_burnin)
     p.temperature = int(temperature)
+    p.q2_total = float(q2_total)
+    p.qsum_total = float(qsum_total)
     return p

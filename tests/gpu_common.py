@@ -71,7 +71,8 @@ class Ctx:
         self.m = W.masses(w) if m is None else np.asarray(m, dtype=np.float64)
         self.params = R.make_params(w, precision=precision, **kw)
         self.P = self.params.P
-        self.h = R.rbsog_init(self.params, w.N, self.q, self.m)
+        # N of the context: the charges given (a domain of the workload), else the workload's
+        self.h = R.rbsog_init(self.params, len(self.q), self.q, self.m)
 
     def close(self):
         R.rbsog_free(self.h)

@@ -174,3 +174,31 @@ def test_server_config_is_checked_on_the_host():
     with pytest.raises(R.RbsogError, match="EINVAL"):
         R.rbsog_server_create(cfg)
     assert "configuration" in R.rbsog_server_last_error(None)
+
+
+def test_slab_split_owns_every_particle_once_and_finds_the_halo():
+    """rbsog_slab_split (host only): the slabs' owned lists partition the particles; each
+    slab's halo is exactly the particles of other slabs whose periodic distance to the slab
+    along the axis is below the halo width."""
+    from paper_2501_10946_gb300 import rbsog as R
+    rng = np.random.default_rng(3)
+    L = np.array([12.0, 9.0, 10.0])
+    r = rng.uniform(-5.0, 20.0, size=(2000, 3))          # not wrapped: the split wraps
+    for axis, nslabs, halo in ((0, 2, 2.5), (1, 3, 1.2), (2, 4, 2.0), (0, 1, 3.0)):
+        w = L[axis] / nslabs
+        x = np.mod(r[:, axis], L[axis])
+        seen = np.zeros(len(r), dtype=int)
+        for slab in range(nslabs):
+            idx, n_owned = R.rbsog_slab_split(r, L, axis, nslabs, slab, halo)
+            own, hal = idx[:n_owned], idx[n_owned:]
+            assert np.all(np.diff(own) > 0) and np.all(np.diff(hal) > 0)
+            seen[own] += 1
+            lo, hi = slab * w, (slab + 1) * w
+            inside = np.minimum(np.floor(x / w), nslabs - 1) == slab
+            assert np.array_equal(np.sort(own), np.nonzero(inside)[0])
+            d = np.minimum(np.mod(lo - x, L[axis]), np.mod(x - hi, L[axis]))
+            expect = np.nonzero(~inside & (d < halo))[0] if nslabs > 1 else np.array([], dtype=int)
+            assert np.array_equal(hal, expect), (axis, nslabs, slab)
+        assert np.all(seen == 1)
+    with pytest.raises(R.RbsogError, match="EINVAL"):
+        R.rbsog_slab_split(r, L, 0, 2, 2, 1.0)
