@@ -191,6 +191,34 @@ __device__ void near_one_f32(const NearArgs &a, uint32_t p, float *Fout, double 
     Uout = (double)Us - (double)Uc;
 }
 
+// One FP64 pair inside r_c: adds q_i q_j [F_N1 + F_N2](r) (r_i - r_j) to F and
+// q_i q_j [Y - F](r) / 2 to U (the per-particle and the tiled FP64 paths share it).
+__device__ __forceinline__ void pair_f64(const NearConsts &nc, double qq, const double d[3], double r2, double F[3],
+                                         double &U) {
+    const double r = sqrt(r2);
+    const double rinv = 1.0 / r;
+    const double e1 = exp(-r * nc.inv_lam);
+    double fsog = 0.0, fn2 = 0.0;
+    for (int g = 0; g < nc.mtot; ++g) {
+        const double E = exp(-r2 * nc.b[g]);
+        fsog += nc.a[g] * E;
+        fn2 += nc.c[g] * E;
+    }
+    double fn1 = e1 * (1.0 + r * nc.inv_lam) * (rinv * rinv * rinv);
+    double yk = e1 * rinv;
+    if (nc.two) {
+        // two Yukawa terms (EGS) with weights y1, y2
+        const double e2 = nc.y2 * exp(-r * nc.inv_lam2);
+        fn1 = nc.y1 * fn1 + e2 * (1.0 + r * nc.inv_lam2) * (rinv * rinv * rinv);
+        yk = nc.y1 * yk + e2 * rinv;
+    }
+    const double gsc = qq * (fn1 + fn2);
+    F[0] += gsc * d[0];
+    F[1] += gsc * d[1];
+    F[2] += gsc * d[2];
+    U += 0.5 * qq * (yk - fsog);
+}
+
 // Per-particle near field from global memory (FP64 records, 2^64 fixed point).
 __device__ void near_one_f64(const NearArgs &a, uint32_t p, double *Fout, double &Uout) {
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
@@ -218,31 +246,7 @@ __device__ void near_one_f64(const NearArgs &a, uint32_t p, double *Fout, double
 #pragma unroll
                     for (int e = 0; e < 3; ++e) d[e] = (double)(long long)(ri.s[e] - rj.s[e]) * a.box.L_2m64[e];
                     const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (r2 < a.nc.rc2) {
-                        const double r = sqrt(r2);
-                        const double rinv = 1.0 / r;
-                        const double e1 = exp(-r * a.nc.inv_lam);
-                        double fsog = 0.0, fn2 = 0.0;
-                        for (int g = 0; g < a.nc.mtot; ++g) {
-                            const double E = exp(-r2 * a.nc.b[g]);
-                            fsog += a.nc.a[g] * E;
-                            fn2 += a.nc.c[g] * E;
-                        }
-                        const double qq = ri.q * rj.q;
-                        double fn1 = e1 * (1.0 + r * a.nc.inv_lam) * (rinv * rinv * rinv);
-                        double yk = e1 * rinv;
-                        if (a.nc.two) {
-                            // two Yukawa terms (EGS) with weights y1, y2
-                            const double e2 = a.nc.y2 * exp(-r * a.nc.inv_lam2);
-                            fn1 = a.nc.y1 * fn1 + e2 * (1.0 + r * a.nc.inv_lam2) * (rinv * rinv * rinv);
-                            yk = a.nc.y1 * yk + e2 * rinv;
-                        }
-                        const double gsc = qq * (fn1 + fn2);
-                        F[0] += gsc * d[0];
-                        F[1] += gsc * d[1];
-                        F[2] += gsc * d[2];
-                        U += 0.5 * qq * (yk - fsog);
-                    }
+                    if (r2 < a.nc.rc2) pair_f64(a.nc, ri.q * rj.q, d, r2, F, U);
                 }
             }
         }
@@ -317,9 +321,28 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
 // CAP: staged particles per CTA (16 B each); NT: threads per CTA.  One large system
 // stages 1280 with 128 threads; batches of many (mostly small) systems stage 1024 with 96.
 // FR: tiles may span a whole row of cells (a third staging slice per row)
-template <int CAP, int NT, int MW, bool FR>
+// F64: the FP64 build's 32-byte records (u64 coordinates), else the FP32 build's 16-byte ones.
+template <bool F64>
+struct TileRec;
+template <>
+struct TileRec<false> {
+    using T = uint4;
+    // the high 32 bits of the fixed-point coordinates (the pre-filter's input)
+    __device__ static __forceinline__ uint32_t x(const uint4 &r) { return r.x; }
+    __device__ static __forceinline__ uint32_t y(const uint4 &r) { return r.y; }
+    __device__ static __forceinline__ uint32_t z(const uint4 &r) { return r.z; }
+};
+template <>
+struct TileRec<true> {
+    using T = Rec64;
+    __device__ static __forceinline__ uint32_t x(const Rec64 &r) { return (uint32_t)(r.s[0] >> 32); }
+    __device__ static __forceinline__ uint32_t y(const Rec64 &r) { return (uint32_t)(r.s[1] >> 32); }
+    __device__ static __forceinline__ uint32_t z(const Rec64 &r) { return (uint32_t)(r.s[2] >> 32); }
+};
+
+template <int CAP, int NT, int MW, bool FR, bool F64 = false>
 struct TileSmem {
-    uint4 stage[CAP];                       // staged records
+    typename TileRec<F64>::T stage[CAP];    // staged records
     uint32_t mask[kSlots][NT];    // per target (column = owning thread): hit bits of a round
     uint16_t flat[3 * CAP];                 // per target cell: staging indices of its 27-cell candidates
     int fb[MW + 2];                         // target cell i: candidates flat[fb[i] .. fb[i+1])
@@ -335,8 +358,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 
 // Region cell (1 .. wn-2) of the centre row holding staged target jl (offset within row 4):
 // the last i with seg_off[4][i] <= jl.
-template <int CAP, int NT, int MW, bool FR>
-__device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW, FR> &S, int wn, int jl) {
+template <class TS>
+__device__ __forceinline__ int region_cell(const TS &S, int wn, int jl) {
     int lo = 1, hi = wn - 2;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -349,9 +372,12 @@ __device__ __forceinline__ int region_cell(const TileSmem<CAP, NT, MW, FR> &S, i
 // DOT selects the form of the pre-filter test (see the threshold below): the expanded
 // one takes fewer instructions, the direct one fewer registers.
 // The tile is handled by NT threads (tid 0 .. NT-1) synchronised by barrier BAR.
-template <int CAP, int NT, int MW, bool DOT, bool FR, int BAR = 0>
+template <int CAP, int NT, int MW, bool DOT, bool FR, int BAR = 0, bool F64 = false>
 __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
-                                               TileSmem<CAP, NT, MW, FR> &S, int tid) {
+                                               TileSmem<CAP, NT, MW, FR, F64> &S, int tid) {
+    using RecT = typename TileRec<F64>::T;
+    using RO = TileRec<F64>;
+    constexpr uint32_t kRecBytes = (uint32_t)sizeof(RecT);
     const int lane = tid & 31, wid = tid >> 5;
     const unsigned full = 0xffffffffu;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
@@ -446,6 +472,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     const uint32_t g_end = cs[nx * (cy + ny * cz) + x1];
 
     float sumU = 0.f;
+    double sumUd = 0.0;            // FP64 build
     double Ufall = 0.0;
     if (staged) {
         bool ok = true;
@@ -456,8 +483,8 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                 asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                             "r"((uint32_t)region_n * 16u) : "memory");
-                const uint4 *rec = (const uint4 *)a.rec;
+                             "r"((uint32_t)region_n * kRecBytes) : "memory");
+                const RecT *rec = (const RecT *)a.rec;
                 for (int r = 0; r < 9; ++r) {
                     uint32_t dst = (uint32_t)S.row_base[r];
                     for (int h = 0; h < (FR ? 3 : 2); ++h) {
@@ -466,7 +493,7 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             asm volatile(
                                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
                                 "[%3];" ::"r"(smem_u32(&S.stage[dst])),
-                                "l"(rec + S.chunk_g[r][h]), "r"(n * 16u), "r"(bar) : "memory");
+                                "l"(rec + S.chunk_g[r][h]), "r"(n * kRecBytes), "r"(bar) : "memory");
                             dst += n;
                         }
                     }
@@ -553,10 +580,13 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                 const int i_lo = region_cell(S, wn, wlo - rb4);
                 const int i_hi = region_cell(S, wn, whi - 1 - rb4);
                 const int i_own = has ? region_cell(S, wn, j - rb4) : i_hi;
-                const uint4 ri = S.stage[has ? j : wlo];
-                const float qi = __uint_as_float(ri.w);
-                // compensated sums, packed: (F_x, F_y) and (F_z, U)
+                const RecT ri = S.stage[has ? j : wlo];
+                float qi = 0.f;
+                if constexpr (!F64) qi = __uint_as_float(ri.w);
+                // FP32: compensated sums, packed: (F_x, F_y) and (F_z, U); FP64: plain sums in
+                // candidate order (the order of the per-particle path)
                 unsigned long long Fxy = 0ull, Cxy = 0ull, Fzu = 0ull, Czu = 0ull;
+                double Fd[3] = {0.0, 0.0, 0.0}, Ud = 0.0;
                 int own_cb = 0, own_total = 0;
                 for (int base = 0;; base += 32 * kSlots) {
                     bool more = false;
@@ -585,10 +615,10 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             H[s] = -3e38f;
                             const int f = base + 32 * s + lane;
                             if (s < nsl && f < total) {
-                                const uint4 rk = S.stage[S.flat[cb + f]];
-                                X[s] = (float)(int)(rk.x - ox) * sx;
-                                Y[s] = (float)(int)(rk.y - oy) * sy;
-                                Z[s] = (float)(int)(rk.z - oz) * sz;
+                                const RecT rk = S.stage[S.flat[cb + f]];
+                                X[s] = (float)(int)(RO::x(rk) - ox) * sx;
+                                Y[s] = (float)(int)(RO::y(rk) - oy) * sy;
+                                Z[s] = (float)(int)(RO::z(rk) - oz) * sz;
                                 if (DOT) H[s] = -0.5f * fmaf(X[s], X[s], fmaf(Y[s], Y[s], Z[s] * Z[s]));
                             }
                         }
@@ -603,11 +633,11 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
 
                         int t = ta;
                         for (; t + 1 < tb; t += 2) {
-                            const uint4 pa = S.stage[t], pb = S.stage[t + 1];
-                            const float xa = (float)(int)(pa.x - ox) * sx, ya = (float)(int)(pa.y - oy) * sy,
-                                        za = (float)(int)(pa.z - oz) * sz;
-                            const float xb = (float)(int)(pb.x - ox) * sx, yb = (float)(int)(pb.y - oy) * sy,
-                                        zb = (float)(int)(pb.z - oz) * sz;
+                            const RecT pa = S.stage[t], pb = S.stage[t + 1];
+                            const float xa = (float)(int)(RO::x(pa) - ox) * sx, ya = (float)(int)(RO::y(pa) - oy) * sy,
+                                        za = (float)(int)(RO::z(pa) - oz) * sz;
+                            const float xb = (float)(int)(RO::x(pb) - ox) * sx, yb = (float)(int)(RO::y(pb) - oy) * sy,
+                                        zb = (float)(int)(RO::z(pb) - oz) * sz;
                             const unsigned long long xa2 = pk2(xa, xa), ya2 = pk2(ya, ya), za2 = pk2(za, za);
                             const unsigned long long xb2 = pk2(xb, xb), yb2 = pk2(yb, yb), zb2 = pk2(zb, zb);
                             // expanded: accept t.c - |c|^2/2 > k; direct: accept |t - c|^2 < k
@@ -645,10 +675,10 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             }
                         }
                         if (t < tb) {
-                            const uint4 rt = S.stage[t];
-                            const float xt = (float)(int)(rt.x - ox) * sx;
-                            const float yt = (float)(int)(rt.y - oy) * sy;
-                            const float zt = (float)(int)(rt.z - oz) * sz;
+                            const RecT rt = S.stage[t];
+                            const float xt = (float)(int)(RO::x(rt) - ox) * sx;
+                            const float yt = (float)(int)(RO::y(rt) - oy) * sy;
+                            const float zt = (float)(int)(RO::z(rt) - oz) * sz;
                             const unsigned long long xt2 = pk2(xt, xt), yt2 = pk2(yt, yt), zt2 = pk2(zt, zt);
                             const float kt = DOT ? 0.5f * (fmaf(xt, xt, fmaf(yt, yt, zt * zt)) - rcf2) : rcf2;
                             const int col = 32 * wid + (t - wlo);
@@ -675,7 +705,27 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                     __syncwarp();
                     // (2) pairs of the own target in candidate order (rows 0..8, staging
                     // order), two per pass: exact separation and exact r < r_c test
-                    if (has) {
+                    if constexpr (F64) {
+                        // FP64: one pair at a time, the separation from the 2^64 fixed point
+                        if (has) {
+                            const int nsl = min(kSlots, max(0, (own_total - base + 31) >> 5));
+                            for (int s2 = 0; s2 < nsl; ++s2) {
+                                uint32_t m = S.mask[s2][tid];
+                                while (m != 0) {
+                                    const int k = S.flat[own_cb + base + 32 * s2 + (__ffs(m) - 1)];
+                                    m &= m - 1;
+                                    if (k == j) continue;
+                                    const Rec64 &rk = S.stage[k];
+                                    double d[3];
+#pragma unroll
+                                    for (int e = 0; e < 3; ++e)
+                                        d[e] = (double)(long long)(ri.s[e] - rk.s[e]) * a.box.L_2m64[e];
+                                    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                                    if (r2 < a.nc.rc2) pair_f64(a.nc, ri.q * rk.q, d, r2, Fd, Ud);
+                                }
+                            }
+                        }
+                    } else if (has) {
                         const int nsl = min(kSlots, max(0, (own_total - base + 31) >> 5));
                         uint32_t m = 0;
                         int s = -1;
@@ -719,27 +769,42 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                     if (!more) break;
                 }
                 if (has) {
-                    float fx, fy, fz, us, cx, cy, cz_, uc;
-                    upk2(Fxy, fx, fy);
-                    upk2(Cxy, cx, cy);
-                    upk2(Fzu, fz, us);
-                    upk2(Czu, cz_, uc);
                     const uint32_t g = g_first + (uint32_t)(j - t0);
-                    Fn[g] = fx - cx;
-                    Fn[a.stride + g] = fy - cy;
-                    Fn[2 * (size_t)a.stride + g] = fz - cz_;
-                    sumU += 0.5f * (us - uc);        // each pair counted from both ends
+                    if constexpr (F64) {
+                        double *Fn64 = (double *)a.Fn;
+                        Fn64[g] = Fd[0];
+                        Fn64[a.stride + g] = Fd[1];
+                        Fn64[2 * (size_t)a.stride + g] = Fd[2];
+                        sumUd += Ud;
+                    } else {
+                        float fx, fy, fz, us, cx, cy, cz_, uc;
+                        upk2(Fxy, fx, fy);
+                        upk2(Cxy, cx, cy);
+                        upk2(Fzu, fz, us);
+                        upk2(Czu, cz_, uc);
+                        Fn[g] = fx - cx;
+                        Fn[a.stride + g] = fy - cy;
+                        Fn[2 * (size_t)a.stride + g] = fz - cz_;
+                        sumU += 0.5f * (us - uc);        // each pair counted from both ends
+                    }
                 }
             }
         }
     } else {
         // neighbourhood larger than the staging buffer (or an overflowing cell): global path
-        float *Fn = (float *)a.Fn;
         for (uint32_t g = g_first + tid; g < g_end; g += NT) {
-            float F[3] = {0.f, 0.f, 0.f};
             double U = 0.0;
-            if (!overflow) near_one_f32(a, g, F, U);
-            Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
+            if constexpr (F64) {
+                double F[3] = {0.0, 0.0, 0.0};
+                if (!overflow) near_one_f64(a, g, F, U);
+                double *Fn = (double *)a.Fn;
+                Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
+            } else {
+                float F[3] = {0.f, 0.f, 0.f};
+                if (!overflow) near_one_f32(a, g, F, U);
+                float *Fn = (float *)a.Fn;
+                Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
+            }
             Ufall += U;
         }
     }
@@ -749,12 +814,23 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         group_sync<NT, BAR>();
         if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
     }
-    warp_partial((double)sumU + Ufall, a.U_part, blk, tid, NT);
+    if constexpr (F64) warp_partial(sumUd + Ufall, a.U_part, blk, tid, NT);
+    else warp_partial((double)sumU + Ufall, a.U_part, blk, tid, NT);
 }
 
 __global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true, false>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false> *>(smem_raw), (int)threadIdx.x);
+}
+
+// FP64 build: the same tiles with the 32-byte records (the staging buffer holds 1280 of
+// them, 40 KB); the pre-filter takes the high 32 bits of the coordinates, the pairs the full
+// 2^64 fixed point and FP64 arithmetic.
+using TileSmem64 = TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false, true>;
+__global__ void __launch_bounds__(kTileThreads, 4) k_near_tiled64(NearArgs a, int W, int tiles_x) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, false, false, 0, true>(
+        a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem64 *>(smem_raw), (int)threadIdx.x);
 }
 
 // Batched systems: block -> (system, local block); each system uses tiles or the
@@ -819,6 +895,7 @@ static void set_tile_smem_attr() {
                              (int)sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false>));
         cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true>));
+        cudaFuncSetAttribute(k_near_tiled64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem64));
         done = true;
     }
 }
@@ -830,6 +907,11 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     if (prec == 1 && tiled) {
         set_tile_smem_attr();
         k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false>), st>>>(a, W, tiles_x);
+        return (int)nb * kWarpsPerBlock;
+    }
+    if (prec == 0 && tiled) {
+        set_tile_smem_attr();
+        k_near_tiled64<<<nb, kTileThreads, sizeof(TileSmem64), st>>>(a, W, tiles_x);
         return (int)nb * kWarpsPerBlock;
     }
     nb = blocks_for(a.N, kGlobalThreads);
