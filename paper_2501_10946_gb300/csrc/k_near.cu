@@ -808,11 +808,13 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             Ufall += U;
         }
     }
-    if (staged && region_n > 0) {
-        // the tile's mbarrier is done with (a CTA of the persistent step reuses its shared
-        // memory for the next tile, which initialises it again)
-        group_sync<NT, BAR>();
-        if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
+    if constexpr (BAR != 0) {
+        // a group of the persistent step reuses its shared memory for its next tile, which
+        // initialises the mbarrier again: invalidate it once every thread is done with it
+        if (staged && region_n > 0) {
+            group_sync<NT, BAR>();
+            if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
+        }
     }
     if constexpr (F64) warp_partial(sumUd + Ufall, a.U_part, blk, tid, NT);
     else warp_partial((double)sumU + Ufall, a.U_part, blk, tid, NT);
