@@ -1,30 +1,25 @@
 // Near field of the RBSOG force step: Eq. (55) first term with F_N1 and F_N2 of
 // Eqs. (56)-(57), and U_N of Eq. (50), over the particles within r_c (minimum image).
 //
-// FP32 build, cells >= 3 per axis: k_near_tiled.  One CTA owns a run of W cells along x
-// in one (y, z) row.  Their 27-cell neighbourhood is 9 rows of W + 2 cells, and each such
-// row is one (or, across the periodic seam, two) contiguous slices of the cell-sorted
-// 16-byte particle records, so the CTA stages the whole neighbourhood in shared memory
-// with TMA bulk copies completing on one mbarrier; while they fly it writes, for each
-// of its target cells, the list of staging indices of that cell's 27-cell candidates.
-// A warp owns 32 consecutive targets (about five cells) and works in two phases:
-//   (1) filter, cell by cell: the lanes hold the cell's candidates (32 per slot) as FP32
-//       offsets from the cell centre, and the warp tests each target of the cell against
-//       all of them at once (packed FP32x2 arithmetic), keeping one ballot mask per slot.
-//       Loop counts are the same on every lane, and a candidate is converted once per
-//       cell, not once per target.  The FP32 offsets are a slightly generous pre-filter:
-//       every pair that the exact test accepts passes it;
-//   (2) pairs: each lane walks its own target's masks in candidate order, recomputes the
-//       separation exactly from the fixed-point coordinates, applies the exact r < r_c
-//       test and accumulates the pair forces: the two of a pass added in FP32, then one
-//       compensated FP32 add.  The pairs are those of a plain loop over the 27 cells, in
-//       its order; which two share a pass follows the pre-filter's hits, so the
-//       pre-filter changes the rounding of the sums, never the set of pairs.
-// Neighbourhoods larger than 8 slots (256 candidates) run in several such rounds.
-// Otherwise (FP64 build, fewer than 3 cells on an axis, or a neighbourhood that does
-// not fit the staging buffer): one thread per particle reading candidates from global
-// memory.
+// Two shared-memory tilings of the cell list (cells >= 3 per axis), both staging the
+// 27-cell neighbourhood of their target cells with TMA bulk copies completing on one
+// mbarrier, pre-filtering candidates in FP32 with ballot masks, and evaluating the exact
+// pairs two per pass in packed FP32x2 (FP64 in the FP64 build):
+//   * row tiles (near_tile_body): a run of W cells in one (y, z) row, its 9 neighbour rows
+//     staged; the batched kernels, the persistent step and the FP64 build use them;
+//   * bricks (near_brick_body, k_near_bricks): a run of W cells in each of by x bz rows,
+//     (by + 2)(bz + 2) neighbour rows staged, about 4 staged particles per target instead
+//     of 10, which leaves room for precomputed FP32 offsets; one large FP32 system uses
+//     them.  The layout of each is described above its body.
+// In both, the pairs of a target are those of a plain loop over the 27 cells in its order;
+// which two share a pass follows the pre-filter's hits, so the pre-filter changes the
+// rounding of the sums, never the set of pairs.
+// Otherwise (fewer than 3 cells on an axis, or a neighbourhood that does not fit the
+// buffers): one thread per particle reading candidates from global memory.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "devmath.cuh"
@@ -317,11 +312,24 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
     near_global_block<PREC>(a, 0u, blockIdx.x);
 }
 
-// ---------------------------------------------------------------- tiled (TMA) FP32 path
-// CAP: staged particles per CTA (16 B each); NT: threads per CTA.  One large system
-// stages 1280 with 128 threads; batches of many (mostly small) systems stage 1024 with 96.
-// FR: tiles may span a whole row of cells (a third staging slice per row)
-// F64: the FP64 build's 32-byte records (u64 coordinates), else the FP32 build's 16-byte ones.
+// ---------------------------------------------------------------- row tiles
+// One CTA owns a run of W cells along x in one (y, z) row.  Their 27-cell neighbourhood is
+// 9 rows of W + 2 cells, each row one (or, across the periodic seam, two) contiguous slices
+// of the cell-sorted particle records, staged with TMA bulk copies; while they fly the CTA
+// writes, for each of its target cells, the list of staging indices of that cell's 27-cell
+// candidates.  A warp owns 32 consecutive targets (about five cells), in two phases:
+//   (1) filter, cell by cell: the lanes hold the cell's candidates (32 per slot) as FP32
+//       offsets from the cell centre, and the warp tests each target of the cell against
+//       all of them at once (packed FP32x2 arithmetic), keeping one ballot mask per slot;
+//   (2) pairs: each lane walks its own target's masks in candidate order, recomputes the
+//       separation exactly from the fixed-point coordinates, applies the exact r < r_c
+//       test and accumulates the pair forces: the two of a pass added in FP32, then one
+//       compensated FP32 add (FP64 build: plain FP64 sums, one pair at a time).
+// Neighbourhoods larger than 8 slots (256 candidates) run in several such rounds.
+// CAP: staged particles per CTA; NT: threads per CTA (batches of many, mostly small,
+// systems stage 1024 with 96).  FR: tiles may span a whole row of cells (a third staging
+// slice per row).  F64: the FP64 build's 32-byte records (u64 coordinates), else the FP32
+// build's 16-byte ones.
 template <bool F64>
 struct TileRec;
 template <>
@@ -342,7 +350,9 @@ struct TileRec<true> {
 
 template <int CAP, int NT, int MW, bool FR, bool F64 = false>
 struct TileSmem {
-    typename TileRec<F64>::T stage[CAP];    // staged records
+    using Rec = typename TileRec<F64>::T;
+    static constexpr bool kFR = FR;
+    Rec stage[CAP];                         // staged records
     uint32_t mask[kSlots][NT];    // per target (column = owning thread): hit bits of a round
     uint16_t flat[3 * CAP];                 // per target cell: staging indices of its 27-cell candidates
     int fb[MW + 2];                         // target cell i: candidates flat[fb[i] .. fb[i+1])
@@ -369,17 +379,27 @@ __device__ __forceinline__ int region_cell(const TS &S, int wn, int jl) {
     return lo;
 }
 
-// DOT selects the form of the pre-filter test (see the threshold below): the expanded
-// one takes fewer instructions, the direct one fewer registers.
-// The tile is handled by NT threads (tid 0 .. NT-1) synchronised by barrier BAR.
-template <int CAP, int NT, int MW, bool DOT, bool FR, int BAR = 0, bool F64 = false>
-__device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
-                                               TileSmem<CAP, NT, MW, FR, F64> &S, int tid) {
-    using RecT = typename TileRec<F64>::T;
-    using RO = TileRec<F64>;
+// One tile's geometry and the outcome of its staging.
+struct TileCtx {
+    int x0, x1, wn, ntc, cy, cz;
+    uint32_t g_first, g_end;                // the tile's targets in global record order
+    int region_n;                           // staged particles
+    bool overflow;                          // the cell build overflowed: no pairs at all
+    bool staged;                            // the neighbourhood fits the staging buffer
+    bool ok;                                // staged, and the copies landed
+};
+
+// Prologue of a tile (NT threads tid 0 .. NT-1, barrier BAR): cell populations of the
+// 9 x wn region, the row slices, the bulk copies of the region into S.stage, the system's
+// pair constants, and per target cell the list of its 27-cell candidates (staging index
+// << FSH, rows 0..8 in order, each row's cells i-1 .. i+1 in staging order) in S.flat.
+template <int NT, int BAR, int FSH, class TS>
+__device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tiles_x, unsigned blk, TS &S,
+                                              int tid) {
+    using RecT = typename TS::Rec;
+    constexpr bool FR = TS::kFR;
     constexpr uint32_t kRecBytes = (uint32_t)sizeof(RecT);
-    const int lane = tid & 31, wid = tid >> 5;
-    const unsigned full = 0xffffffffu;
+    TileCtx c;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
     const int tile = (int)(blk % (unsigned)tiles_x);
     const int rest = (int)(blk / (unsigned)tiles_x);
@@ -388,8 +408,9 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     const int x1 = min(x0 + W, nx);
     const int wn = x1 - x0 + 2;                  // region cells per row: x0-1 .. x1
     const int ntc = wn - 2;                      // target cells: region cells 1 .. wn-2
+    c.x0 = x0; c.x1 = x1; c.wn = wn; c.ntc = ntc; c.cy = cy; c.cz = cz;
     const uint32_t *cs = a.cell_start;
-    const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
+    c.overflow = (a.ctr->err & kErrCellOverflow) != 0;
 
     // cell populations of the 9 x wn region cells, loaded in parallel (row r: dz = r/3 - 1,
     // dy = r%3 - 1)
@@ -398,8 +419,8 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
         const int yr = (cy + r % 3 - 1 + ny) % ny, zr = (cz + r / 3 - 1 + nz) % nz;
         int x = x0 - 1 + i;
         x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-        const int c = x + nx * (yr + ny * zr);
-        S.seg_off[r][i + 1] = (int)(cs[c + 1] - cs[c]);
+        const int cc = x + nx * (yr + ny * zr);
+        S.seg_off[r][i + 1] = (int)(cs[cc + 1] - cs[cc]);
     }
     if (tid == 0) {
         S.nf.mtot = a.nc.mtot;
@@ -466,91 +487,144 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     }
     group_sync<NT, BAR>();
     const int region_n = S.row_base[9];
-    const bool staged = !overflow && region_n <= CAP;
+    c.region_n = region_n;
+    c.staged = !c.overflow && region_n <= (int)(sizeof(S.stage) / sizeof(RecT));
     // center row (r = 4): targets are region cells 1 .. wn-2, contiguous in global memory
-    const uint32_t g_first = cs[nx * (cy + ny * cz) + x0];
-    const uint32_t g_end = cs[nx * (cy + ny * cz) + x1];
+    c.g_first = cs[nx * (cy + ny * cz) + x0];
+    c.g_end = cs[nx * (cy + ny * cz) + x1];
+    c.ok = c.staged;
+    if (!c.staged || region_n == 0) return c;
 
+    const uint32_t bar = smem_u32(&S.mbar);
+    if (tid == 0) {                              // start the bulk copies of the region
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"((uint32_t)region_n * kRecBytes) : "memory");
+        const RecT *rec = (const RecT *)a.rec;
+        for (int r = 0; r < 9; ++r) {
+            uint32_t dst = (uint32_t)S.row_base[r];
+            for (int h = 0; h < (FR ? 3 : 2); ++h) {
+                const uint32_t n = S.chunk_n[r][h];
+                if (n) {
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+                        "[%3];" ::"r"(smem_u32(&S.stage[dst])),
+                        "l"(rec + S.chunk_g[r][h]), "r"(n * kRecBytes), "r"(bar) : "memory");
+                    dst += n;
+                }
+            }
+        }
+    }
+    // offsets of the target cells' candidate lists: fb[i] = sum of the 27-cell counts
+    // of target cells 1 .. i-1.  A staged particle is a candidate of at most 3 target
+    // cells, so all lists together fit 3 CAP entries.  (The barriers below also make
+    // thread 0's mbarrier initialisation visible before any thread polls it.)
+    if (tid < ntc) {
+        const int i = tid + 1;
+        int tot = 0;
+        for (int r = 0; r < 9; ++r) tot += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
+        S.fb[i + 1] = tot;
+    }
+    group_sync<NT, BAR>();
+    if (tid == 0) {
+        int b = 0;
+        S.fb[1] = 0;
+        for (int i = 1; i <= ntc; ++i) {
+            b += S.fb[i + 1];
+            S.fb[i + 1] = b;
+        }
+    }
+    group_sync<NT, BAR>();
+    // while the copies fly: the candidate list of each target cell i, rows 0..8 in
+    // order, each row's cells i-1 .. i+1 in staging order
+    for (int e = tid; e < 9 * ntc; e += NT) {
+        const int i = e / 9 + 1, r = e - (e / 9) * 9;
+        int pos = S.fb[i];
+        for (int q = 0; q < r; ++q) pos += S.seg_off[q][i + 2] - S.seg_off[q][i - 1];
+        const int a0 = S.seg_off[r][i - 1], n = S.seg_off[r][i + 2] - a0;
+        const int st = S.row_base[r] + a0;
+        for (int l = 0; l < n; ++l) S.flat[pos + l] = (uint16_t)((st + l) << FSH);
+    }
+    // bounded wait for the staged bytes (phase 0); the outcome is made block-uniform,
+    // and the block barrier also publishes the candidate lists
+    uint32_t done = 0;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+    }
+    c.ok = group_sync_and<NT, BAR>((int)done) != 0;
+    if (!c.ok) {
+        if (tid == 0) atomicOr(&a.ctr->err, kErrNearStage);
+        // let the copies in flight land before the CTA exits (again bounded)
+        for (int it = 0; it < (1 << 22) && !done; ++it)
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                : "=r"(done)
+                : "r"(bar)
+                : "memory");
+    }
+    return c;
+}
+
+// Targets of a tile whose neighbourhood did not fit the staging buffer (or whose cell build
+// overflowed): one thread per particle from global memory.  Returns the thread's energy.
+template <int NT, bool F64>
+__device__ __forceinline__ double tile_fallback(const NearArgs &a, const TileCtx &c, int tid) {
+    double Ufall = 0.0;
+    for (uint32_t g = c.g_first + tid; g < c.g_end; g += NT) {
+        double U = 0.0;
+        if constexpr (F64) {
+            double F[3] = {0.0, 0.0, 0.0};
+            if (!c.overflow) near_one_f64(a, g, F, U);
+            double *Fn = (double *)a.Fn;
+            Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
+        } else {
+            float F[3] = {0.f, 0.f, 0.f};
+            if (!c.overflow) near_one_f32(a, g, F, U);
+            float *Fn = (float *)a.Fn;
+            Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
+        }
+        Ufall += U;
+    }
+    return Ufall;
+}
+
+// A group of the persistent step reuses its shared memory for its next tile, which
+// initialises the mbarrier again: invalidate it once every thread is done with it.
+template <int NT, int BAR, class TS>
+__device__ __forceinline__ void tile_release(const TileCtx &c, TS &S, int tid) {
+    if constexpr (BAR != 0) {
+        if (c.staged && c.region_n > 0) {
+            group_sync<NT, BAR>();
+            if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
+        }
+    }
+}
+
+// DOT selects the form of the pre-filter test (see the threshold below): the expanded
+// one takes fewer instructions, the direct one fewer registers.
+// The tile is handled by NT threads (tid 0 .. NT-1) synchronised by barrier BAR.
+template <int CAP, int NT, int MW, bool DOT, bool FR, int BAR = 0, bool F64 = false>
+__device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
+                                               TileSmem<CAP, NT, MW, FR, F64> &S, int tid) {
+    using RecT = typename TileRec<F64>::T;
+    using RO = TileRec<F64>;
+    const int lane = tid & 31, wid = tid >> 5;
+    const unsigned full = 0xffffffffu;
+    const TileCtx c = tile_stage<NT, BAR, 0>(a, W, tiles_x, blk, S, tid);
+    const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
+    const int x0 = c.x0, wn = c.wn, cy = c.cy, cz = c.cz;
+    const uint32_t g_first = c.g_first;
     float sumU = 0.f;
     double sumUd = 0.0;            // FP64 build
     double Ufall = 0.0;
-    if (staged) {
-        bool ok = true;
-        if (region_n > 0) {
-            const uint32_t bar = smem_u32(&S.mbar);
-            if (tid == 0) {                              // start the bulk copies of the region
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                             "r"((uint32_t)region_n * kRecBytes) : "memory");
-                const RecT *rec = (const RecT *)a.rec;
-                for (int r = 0; r < 9; ++r) {
-                    uint32_t dst = (uint32_t)S.row_base[r];
-                    for (int h = 0; h < (FR ? 3 : 2); ++h) {
-                        const uint32_t n = S.chunk_n[r][h];
-                        if (n) {
-                            asm volatile(
-                                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-                                "[%3];" ::"r"(smem_u32(&S.stage[dst])),
-                                "l"(rec + S.chunk_g[r][h]), "r"(n * kRecBytes), "r"(bar) : "memory");
-                            dst += n;
-                        }
-                    }
-                }
-            }
-            // offsets of the target cells' candidate lists: fb[i] = sum of the 27-cell counts
-            // of target cells 1 .. i-1.  A staged particle is a candidate of at most 3 target
-            // cells, so all lists together fit 3 CAP entries.  (The barriers below also make
-            // thread 0's mbarrier initialisation visible before any thread polls it.)
-            if (tid < ntc) {
-                const int i = tid + 1;
-                int tot = 0;
-                for (int r = 0; r < 9; ++r) tot += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
-                S.fb[i + 1] = tot;
-            }
-            group_sync<NT, BAR>();
-            if (tid == 0) {
-                int b = 0;
-                S.fb[1] = 0;
-                for (int i = 1; i <= ntc; ++i) {
-                    b += S.fb[i + 1];
-                    S.fb[i + 1] = b;
-                }
-            }
-            group_sync<NT, BAR>();
-            // while the copies fly: the candidate list of each target cell i, rows 0..8 in
-            // order, each row's cells i-1 .. i+1 in staging order
-            for (int e = tid; e < 9 * ntc; e += NT) {
-                const int i = e / 9 + 1, r = e - (e / 9) * 9;
-                int pos = S.fb[i];
-                for (int q = 0; q < r; ++q) pos += S.seg_off[q][i + 2] - S.seg_off[q][i - 1];
-                const int a0 = S.seg_off[r][i - 1], n = S.seg_off[r][i + 2] - a0;
-                const int st = S.row_base[r] + a0;
-                for (int l = 0; l < n; ++l) S.flat[pos + l] = (uint16_t)(st + l);
-            }
-            // bounded wait for the staged bytes (phase 0); the outcome is made block-uniform,
-            // and the block barrier also publishes the candidate lists
-            uint32_t done = 0;
-            for (int it = 0; it < (1 << 22) && !done; ++it) {
-                asm volatile(
-                    "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                    : "=r"(done)
-                    : "r"(bar)
-                    : "memory");
-            }
-            ok = group_sync_and<NT, BAR>((int)done) != 0;
-            if (!ok) {
-                if (tid == 0) atomicOr(&a.ctr->err, kErrNearStage);
-                // let the copies in flight land before the CTA exits (again bounded)
-                for (int it = 0; it < (1 << 22) && !done; ++it)
-                    asm volatile(
-                        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                        : "=r"(done)
-                        : "r"(bar)
-                        : "memory");
-            }
-        }
+    if (c.staged) {
+        const bool ok = c.ok;
         if (ok) {
             const int rb4 = S.row_base[4];
             const int t0 = rb4 + S.seg_off[4][1];
@@ -791,38 +865,485 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             }
         }
     } else {
-        // neighbourhood larger than the staging buffer (or an overflowing cell): global path
-        for (uint32_t g = g_first + tid; g < g_end; g += NT) {
-            double U = 0.0;
-            if constexpr (F64) {
-                double F[3] = {0.0, 0.0, 0.0};
-                if (!overflow) near_one_f64(a, g, F, U);
-                double *Fn = (double *)a.Fn;
-                Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
-            } else {
-                float F[3] = {0.f, 0.f, 0.f};
-                if (!overflow) near_one_f32(a, g, F, U);
-                float *Fn = (float *)a.Fn;
-                Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
-            }
-            Ufall += U;
-        }
+        Ufall = tile_fallback<NT, F64>(a, c, tid);
     }
-    if constexpr (BAR != 0) {
-        // a group of the persistent step reuses its shared memory for its next tile, which
-        // initialises the mbarrier again: invalidate it once every thread is done with it
-        if (staged && region_n > 0) {
-            group_sync<NT, BAR>();
-            if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
-        }
-    }
+    tile_release<NT, BAR>(c, S, tid);
     if constexpr (F64) warp_partial(sumUd + Ufall, a.U_part, blk, tid, NT);
     else warp_partial((double)sumU + Ufall, a.U_part, blk, tid, NT);
 }
 
-__global__ void __launch_bounds__(kTileThreads, 6) k_near_tiled(NearArgs a, int W, int tiles_x) {
+// Lower bound of cell k (any integer, unwrapped) of n in the 2^32 fixed point:
+// ceil(k 2^32 / n), the least s with floor(s n / 2^32) = k.
+__device__ __forceinline__ long long cell_lo(int k, int n) {
+    const long long num = (long long)k << 32;
+    return num >= 0 ? (num + n - 1) / n : -((-num) / n);
+}
+
+// ---------------------------------------------------------------- FP32 brick tiles
+// One CTA owns a brick of target cells: a run of W cells along x in each of by x bz
+// adjacent (y, z) rows.  Its neighbourhood is (by + 2)(bz + 2) rows of W + 2 cells, each
+// row one or two contiguous slices of the cell-sorted records, staged by bulk copies
+// completing on one mbarrier: about 4 staged particles per target, where a single row of
+// targets stages about 10.  Then:
+//   (0) every staged particle's offset c from the brick centre in FP32, with -|c|^2/2;
+//   (1) pre-filter, one target cell per warp at a time: the lanes hold the cell's
+//       candidates (32 per slot, each loaded once), the cell's targets sit in registers
+//       (8 at a time, two per packed FP32x2 lane), and each test is three packed FMAs
+//       against the expanded form of |t - c|^2 < thr; one ballot mask per (slot, target);
+//   (2) pairs, one thread per target: its masks in candidate order, two hits per pass,
+//       the exact separation from the fixed-point coordinates, the exact r < r_c test,
+//       packed FP32x2 pair terms with the SOG constants read from the kernel parameters,
+//       the pass's two contributions added in FP32 and then one compensated add.
+// The pairs are those of a plain loop over the 27 cells in its order; which two share a
+// pass follows the pre-filter's hits, so the pre-filter changes the rounding of the sums,
+// never the set of pairs.
+
+// Shared-memory loads by 32-bit shared address (OFF: a constant byte offset folded into the
+// instruction).
+template <int OFF = 0>
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u16 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+__device__ __forceinline__ float4 lds_f4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint4 lds_u4(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+
+// Bounded wait for phase 0 of the mbarrier at bar: each try suspends the thread for at most
+// 100 us and returns as soon as the phase completes; gives up after `tries`.  1: complete.
+__device__ __forceinline__ uint32_t mbar_wait0(uint32_t bar, int tries) {
+    uint32_t done = 0;
+    for (int it = 0; it < tries && !done; ++it)
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0, %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(bar), "n"(100000)
+            : "memory");
+    return done;
+}
+
+// Store four hit masks to shared address a from lane 0.
+__device__ __forceinline__ void sts4_lane0(int lane, uint32_t a, uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3) {
+    asm volatile("{ .reg .pred p; setp.eq.u32 p, %0, 0; @p st.shared.v4.u32 [%1], {%2, %3, %4, %5}; }" ::"r"(lane),
+                 "r"(a), "r"(m0), "r"(m1), "r"(m2), "r"(m3)
+                 : "memory");
+}
+
+// W: run length in cells along x; tiles_x, tiles_y: bricks per row and per y-layer;
+// by, bz: rows of a brick along y and z (the last brick of a layer may have fewer)
+struct BrickGeom {
+    int W, tiles_x, tiles_y, by, bz;
+};
+
+constexpr int kBrickSlots = 16;        // candidate slots (32 each) of a target cell: 512
+
+template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX>
+struct BrickSmem {
+    static constexpr int NR = (BY + 2) * (BZ + 2);     // neighbourhood rows
+    static constexpr int NTR = BY * BZ;                // target rows
+    static constexpr int NC = NTR * MW;                // target cells
+    static_assert(CAP * 32 <= 65535, "shared addresses of the offsets are 16-bit");
+    static_assert(CAP <= 4096 && NC <= 256 && TMX <= 1024 && NR <= 256, "packed descriptors");
+    uint4 stage[CAP];                       // staged records
+    float4 off[CAP];                        // FP32 offsets c from the brick centre (x, y, z, -|c|^2/2)
+    uint16_t flat[FCAP];                    // per target cell: shared addresses of its candidates' offsets
+    uint32_t mask[kBrickSlots][TMX];        // per target: hit bits (a cell's targets take 4-aligned columns)
+    int seg_off[NR][MW + 3];                // per row: offset of each region cell within the row
+    uint32_t cstart[NR][MW + 2];            // per row: global start of each region cell
+    int row_tot[NR];                        // per row: staged particles
+    int row_base[NR + 1];                   // per row: offset of the row in the staging buffer
+    uint32_t cinfo[NC];                     // target cell tc: region row | region cell << 8 |
+                                            // first neighbour row << 16 | target row << 24
+    int cnt[NC];                            // target cell tc: its targets
+    int fb[NC + 1];                         // target cell tc: candidates flat[fb[tc] .. fb[tc+1])
+    int ccol[NC];                           // target cell tc: first mask column of its targets
+    int tp[NTR + 1];                        // target row tr: brick targets tp[tr] .. tp[tr+1]
+    uint2 tinfo[TMX];                       // brick target t: global index, staged index | cell
+                                            // << 12 | mask column << 20
+    long long ref[3];                       // fixed-point brick centre
+    int staged, next;                       // staging decision; next target cell to filter
+    unsigned long long mbar;
+};
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX>
+__device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &nf, const BrickGeom &bg,
+                                                unsigned blk, BrickSmem<CAP, FCAP, NT, MW, BY, BZ, TMX> &S,
+                                                int tid) {
+    constexpr int NW = NT / 32;
+    const int lane = tid & 31, wid = tid >> 5;
+    const unsigned full = 0xffffffffu;
+    const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
+    const uint32_t *cs = a.cell_start;
+    const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
+    // brick: x cells x0 .. x1-1, rows y0 .. y0+by-1, z0 .. z0+bz-1
+    const int tx = (int)(blk % (unsigned)bg.tiles_x);
+    const int rest = (int)(blk / (unsigned)bg.tiles_x);
+    const int x0 = tx * bg.W, x1 = min(x0 + bg.W, nx);
+    const int y0 = (rest % bg.tiles_y) * bg.by, z0 = (rest / bg.tiles_y) * bg.bz;
+    const int by = min(bg.by, ny - y0), bz = min(bg.bz, nz - z0);
+    const int wn = x1 - x0 + 2, ntc = wn - 2;  // region cells x0-1 .. x1; target cells 1 .. wn-2
+    const int nry = by + 2, nr = nry * (bz + 2), ntr = by * bz, ncells = ntr * ntc;
+    // (a) one region row (y0-1 + r % nry, z0-1 + r / nry) per warp at a time, one cell per
+    // lane: global starts, populations and their prefix within the row; the reference point
+    // (threads 0..2: the centre of the region's extent on each axis, exact in the fixed point)
+    for (int r = wid; r < nr; r += NW) {
+        const int yr = (y0 - 1 + r % nry + ny) % ny, zr = (z0 - 1 + r / nry + nz) % nz;
+        const int rowbase = nx * (yr + ny * zr);
+        int n = 0;
+        if (lane < wn) {
+            int x = x0 - 1 + lane;
+            x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+            const uint32_t c0 = cs[rowbase + x];
+            S.cstart[r][lane] = c0;
+            n = (int)(cs[rowbase + x + 1] - c0);
+        }
+        n = warp_incl_scan(n, lane);
+        if (lane < wn) S.seg_off[r][lane + 1] = n;
+        if (lane == 0) S.seg_off[r][0] = 0;
+        if (lane == 31) S.row_tot[r] = n;
+    }
+    if (tid < 3) {
+        const int lo = tid == 0 ? x0 - 1 : (tid == 1 ? y0 - 1 : z0 - 1);
+        const int hi = tid == 0 ? x1 + 1 : (tid == 1 ? y0 + by + 1 : z0 + bz + 1);
+        S.ref[tid] = (cell_lo(lo, a.box.nc[tid]) + cell_lo(hi, a.box.nc[tid]) ) >> 1;
+    }
+    if (tid == 32) S.next = 0;
+    group_sync<NT, 0>();
+    // (b) warp 0: row offsets in the staging buffer; warp 1: targets per target row (target
+    // row tr = ty + by tz sits in region row (tz+1) nry + ty+1); the other warps: per target
+    // cell tc = tr * ntc + i - 1 its descriptor, its targets and the size of its 27-cell list
+    // (neighbour row q = 0..8 of target row tr is region row (tz + q/3) nry + ty + q%3)
+    if (wid == 0) {
+        const int v = lane < nr ? S.row_tot[lane] : 0;
+        const int inc = warp_incl_scan(v, lane);
+        if (lane < nr) S.row_base[lane] = inc - v;
+        if (lane == 31) S.row_base[nr] = inc;
+    } else if (wid == 1) {
+        int v = 0;
+        if (lane < ntr) {
+            const int rt = (lane / by + 1) * nry + lane % by + 1;
+            v = S.seg_off[rt][wn - 1] - S.seg_off[rt][1];
+        }
+        const int inc = warp_incl_scan(v, lane);
+        if (lane < ntr) S.tp[lane] = inc - v;
+        if (lane == 31) S.tp[ntr] = inc;
+    } else {
+        for (int tc = tid - 64; tc < ncells; tc += NT - 64) {
+            const int tr = tc / ntc, i = tc - tr * ntc + 1;
+            const int rb = (tr / by) * nry + tr % by;
+            const int rt = rb + nry + 1;
+            int tot = 0;
+            for (int q = 0; q < 9; ++q) {
+                const int r = rb + (q / 3) * nry + q % 3;
+                tot += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
+            }
+            S.cinfo[tc] = (uint32_t)rt | (uint32_t)i << 8 | (uint32_t)rb << 16 | (uint32_t)tr << 24;
+            S.cnt[tc] = S.seg_off[rt][i + 1] - S.seg_off[rt][i];
+            S.fb[tc + 1] = tot;
+        }
+    }
+    group_sync<NT, 0>();
+    // (c) warp 0: offsets of the candidate lists and the mask columns (4 per started group
+    // of 4 targets) of the target cells; the staging decision
+    if (wid == 0) {
+        int fcarry = 0, ccarry = 0, lmax = 0;
+        for (int base = 0; base < ncells; base += 32) {
+            const int tc = base + lane;
+            const int len = tc < ncells ? S.fb[tc + 1] : 0;
+            const int nc4 = tc < ncells ? (S.cnt[tc] + 3) & ~3 : 0;
+            lmax = max(lmax, len);
+            const int fi = warp_incl_scan(len, lane), ci = warp_incl_scan(nc4, lane);
+            if (tc < ncells) {
+                S.fb[tc + 1] = fcarry + fi;
+                S.ccol[tc] = ccarry + ci - nc4;
+            }
+            fcarry += __shfl_sync(full, fi, 31);
+            ccarry += __shfl_sync(full, ci, 31);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(full, lmax, o));
+        if (lane == 0) {
+            S.fb[0] = 0;
+            const int region_n = S.row_base[nr];
+            // (the candidate lists hold 16-bit shared addresses of the offsets: the buffer
+            // sits at the start of the block's shared memory, far below 64 KB)
+            const int st = !overflow && region_n <= CAP && fcarry <= FCAP && lmax <= 32 * kBrickSlots &&
+                           ccarry <= TMX && smem_u32(&S.off[CAP]) <= 65536u;
+            S.staged = st;
+            if (st && region_n > 0) {
+                const uint32_t bar = smem_u32(&S.mbar);
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                             "r"((uint32_t)region_n * 16u) : "memory");
+            }
+        }
+    }
+    group_sync<NT, 0>();
+    const int region_n = S.row_base[nr];
+    const int T = S.tp[ntr];
+    if (!S.staged) {
+        // neighbourhood larger than the buffers (or an overflowing cell): per particle
+        double Ufall = 0.0;
+        for (int t = tid; t < T; t += NT) {
+            int tr = 0;
+            while (tr + 1 < ntr && t >= S.tp[tr + 1]) ++tr;
+            const int rt = (tr / by + 1) * nry + tr % by + 1;
+            const uint32_t g = S.cstart[rt][1] + (uint32_t)(t - S.tp[tr]);
+            double U = 0.0;
+            float F[3] = {0.f, 0.f, 0.f};
+            if (!overflow) near_one_f32(a, g, F, U);
+            float *Fn = (float *)a.Fn;
+            Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
+            Ufall += U;
+        }
+        warp_partial(Ufall, a.U_part, blk, tid, NT);
+        return;
+    }
+    if (region_n == 0) {
+        warp_partial(0.0, a.U_part, blk, tid, NT);
+        return;
+    }
+    const uint32_t bar = smem_u32(&S.mbar);
+    // (d) the bulk copies, one row per lane of warp 0 (a row is one slice, or two across the
+    // periodic seam: cells before the one at x = 0, then the rest); meanwhile the candidate
+    // lists of the target cells, rows q = 0..8 in order, each row's cells i-1 .. i+1 in
+    // staging order
+    if (tid < nr) {
+        const uint4 *rec = (const uint4 *)a.rec;
+        const int is = x0 == 0 ? 1 : (x1 == nx ? wn - 1 : wn);
+        const uint32_t n0 = (uint32_t)S.seg_off[tid][is], n1 = (uint32_t)(S.seg_off[tid][wn] - S.seg_off[tid][is]);
+        const uint32_t dst = (uint32_t)S.row_base[tid];
+        if (n0)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(&S.stage[dst])),
+                "l"(rec + S.cstart[tid][0]), "r"(n0 * 16u), "r"(bar)
+                : "memory");
+        if (n1)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(&S.stage[dst + n0])),
+                "l"(rec + S.cstart[tid][is]), "r"(n1 * 16u), "r"(bar)
+                : "memory");
+    }
+    for (int e = tid; e < 9 * ncells; e += NT) {
+        const int tc = e / 9, q = e - tc * 9;
+        const uint32_t ci = S.cinfo[tc];
+        const int i = (int)((ci >> 8) & 0xffu), rb = (int)((ci >> 16) & 0xffu);
+        int pos = S.fb[tc];
+        for (int u = 0; u < q; ++u) {
+            const int r = rb + (u / 3) * nry + u % 3;
+            pos += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
+        }
+        const int r = rb + (q / 3) * nry + q % 3;
+        const int a0 = S.seg_off[r][i - 1], n = S.seg_off[r][i + 2] - a0;
+        const uint32_t oa = smem_u32(&S.off[S.row_base[r] + a0]);
+        for (int l = 0; l < n; ++l) S.flat[pos + l] = (uint16_t)(oa + 16u * (uint32_t)l);
+    }
+    // bounded wait for the staged bytes (phase 0, at most about 2 s), made block-uniform
+    uint32_t done = mbar_wait0(bar, 20000);
+    if (!group_sync_and<NT, 0>((int)done)) {
+        if (tid == 0) atomicOr(&a.ctr->err, kErrNearStage);
+        if (!done) done = mbar_wait0(bar, 20000);     // let the copies in flight land
+        warp_partial(0.0, a.U_part, blk, tid, NT);
+        return;
+    }
+    // (e) FP32 offsets from the brick centre.  The region spans at most the box on each
+    // axis (W <= nx - 2, by <= ny - 2, bz <= nz - 2), so offsets from the centre taken
+    // modulo 2^32 are the exact fixed-point differences, rounded once to FP32.
+    const float sx = a.box.L_2m32f[0], sy = a.box.L_2m32f[1], sz = a.box.L_2m32f[2];
+    {
+        const uint32_t rx = (uint32_t)S.ref[0], ry = (uint32_t)S.ref[1], rz = (uint32_t)S.ref[2];
+        for (int e = tid; e < region_n; e += NT) {
+            const uint4 p = S.stage[e];
+            const float X = (float)(int)(p.x - rx) * sx, Y = (float)(int)(p.y - ry) * sy,
+                        Z = (float)(int)(p.z - rz) * sz;
+            S.off[e] = make_float4(X, Y, Z, -0.5f * fmaf(X, X, fmaf(Y, Y, Z * Z)));
+        }
+    }
+    group_sync<NT, 0>();
+    const float rc2 = a.nc.rc2_f;
+    // Pre-filter: accept candidate c of target t when t.c - |c|^2/2 > (|t|^2 - thr)/2, which
+    // is |t - c|^2 < thr, with thr = r_c^2 (1 + 1e-3).  Offsets from the centre are at most
+    // (MW/2 + 1) c = 9 c along x and 2.5 c along y and z (c < 4/3 r_c, the cell width, as
+    // n_c = floor(L / r_c) >= 3), each within 2.4e-7 of its size after two roundings; the
+    // ten roundings of the test's terms (each at most 141 c^2) and the offsets' own errors
+    // move the decision by less than 4e-4 r_c^2 in r^2, so every pair that the exact test
+    // accepts passes.
+    static_assert(MW <= 16, "pre-filter margin");
+    const float hthr = 0.5f * (rc2 * 1.001f);
+    const uint32_t flat_s = smem_u32(S.flat);
+    // (f) pre-filter, target cells taken by the warps in turn; the cell's targets in chunks
+    // of 8 (two groups of 4 mask columns), a chunk of at most 4 with half the work.  Each cell
+    // also records its targets' descriptors.
+    constexpr uint32_t kRowBytes = 4u * TMX;                   // bytes between mask slots
+    while (true) {
+        int c = 0;
+        if (lane == 0) c = atomicAdd(&S.next, 1);
+        c = __shfl_sync(full, c, 0);
+        if (c >= ncells) break;
+        const uint32_t ci = S.cinfo[c];
+        const int rt = (int)(ci & 0xffu), i = (int)((ci >> 8) & 0xffu), tr = (int)(ci >> 24);
+        const int ts = S.row_base[rt] + S.seg_off[rt][i];                   // first target, staged
+        const int nt = S.cnt[c];
+        const int f0 = S.fb[c], len = S.fb[c + 1] - f0;
+        const int nsl = (len + 31) >> 5;
+        const int col0 = S.ccol[c];
+        const int tbase = S.tp[tr] + S.seg_off[rt][i] - S.seg_off[rt][1];    // its brick index
+        for (int k = lane; k < nt; k += 32)
+            S.tinfo[tbase + k] = make_uint2(S.cstart[rt][i] + (uint32_t)k,
+                                            (uint32_t)(ts + k) | ((uint32_t)c << 12) | ((uint32_t)(col0 + k) << 20));
+        const uint32_t mcol = smem_u32(&S.mask[0][col0]);
+        for (int t0 = 0; t0 < nt; t0 += 8) {
+            const int nct = min(8, nt - t0);
+            // the chunk's targets, two per packed register: x, y, z and the bound
+            // (|t|^2 - thr)/2 = -h - thr/2 (h = -|t|^2/2); past the chunk, its last target
+            unsigned long long TX[4], TY[4], TZ[4], TK[4];
+#pragma unroll
+            for (int pr = 0; pr < 4; ++pr) {
+                const float4 ta = S.off[ts + t0 + min(2 * pr, nct - 1)];
+                const float4 tb = S.off[ts + t0 + min(2 * pr + 1, nct - 1)];
+                TX[pr] = pk2(ta.x, tb.x);
+                TY[pr] = pk2(ta.y, tb.y);
+                TZ[pr] = pk2(ta.z, tb.z);
+                TK[pr] = pk2(-ta.w - hthr, -tb.w - hthr);
+            }
+            uint32_t ma = mcol + 4u * (uint32_t)t0;
+            // a lane past the list tests its last candidate with h = -inf: never above
+            const uint32_t fl = flat_s + 2u * (uint32_t)(f0 + len - 1);
+            uint32_t fa = flat_s + 2u * (uint32_t)(f0 + lane);
+            if (nct > 4) {
+                for (int s = 0; s < nsl; ++s, ma += kRowBytes, fa += 64u) {
+                    const float4 cf = lds_f4(lds_u16(min(fa, fl)));
+                    const float h = fa <= fl ? cf.w : -3e38f;
+                    const unsigned long long X2 = pk2(cf.x, cf.x), Y2 = pk2(cf.y, cf.y), Z2 = pk2(cf.z, cf.z),
+                                             H2 = pk2(h, h);
+                    uint32_t m[8];
+#pragma unroll
+                    for (int pr = 0; pr < 4; ++pr) {
+                        float va, vb, ka, kb;
+                        upk2(fma2(Z2, TZ[pr], fma2(Y2, TY[pr], fma2(X2, TX[pr], H2))), va, vb);
+                        upk2(TK[pr], ka, kb);
+                        m[2 * pr] = __ballot_sync(full, va > ka);
+                        m[2 * pr + 1] = __ballot_sync(full, vb > kb);
+                    }
+                    sts4_lane0(lane, ma, m[0], m[1], m[2], m[3]);
+                    sts4_lane0(lane, ma + 16u, m[4], m[5], m[6], m[7]);
+                }
+            } else {
+                for (int s = 0; s < nsl; ++s, ma += kRowBytes, fa += 64u) {
+                    const float4 cf = lds_f4(lds_u16(min(fa, fl)));
+                    const float h = fa <= fl ? cf.w : -3e38f;
+                    const unsigned long long X2 = pk2(cf.x, cf.x), Y2 = pk2(cf.y, cf.y), Z2 = pk2(cf.z, cf.z),
+                                             H2 = pk2(h, h);
+                    uint32_t m[4];
+#pragma unroll
+                    for (int pr = 0; pr < 2; ++pr) {
+                        float va, vb, ka, kb;
+                        upk2(fma2(Z2, TZ[pr], fma2(Y2, TY[pr], fma2(X2, TX[pr], H2))), va, vb);
+                        upk2(TK[pr], ka, kb);
+                        m[2 * pr] = __ballot_sync(full, va > ka);
+                        m[2 * pr + 1] = __ballot_sync(full, vb > kb);
+                    }
+                    sts4_lane0(lane, ma, m[0], m[1], m[2], m[3]);
+                }
+            }
+        }
+    }
+    group_sync<NT, 0>();
+    // (g) pairs, one thread per target
+    float *Fn = (float *)a.Fn;
+    const unsigned long long sx2 = dup2(sx), sy2 = dup2(sy), sz2 = dup2(sz);
+    constexpr uint32_t kStageBack = 16u * CAP;                   // stage[i] = off[i] - kStageBack
+    float sumU = 0.f;
+    for (int wlo = 32 * wid; wlo < T; wlo += NT) {
+        const int t = wlo + lane;
+        const bool has = t < T;
+        const uint2 tinf = S.tinfo[has ? t : wlo];
+        const int j = (int)(tinf.y & 0xfffu), tc = (int)((tinf.y >> 12) & 0xffu), col = (int)(tinf.y >> 20);
+        const uint32_t fbase = flat_s + 2u * (uint32_t)S.fb[tc];
+        const int nsl = has ? (S.fb[tc + 1] - S.fb[tc] + 31) >> 5 : 0;
+        const uint32_t jo = smem_u32(&S.off[j]);                 // the target's own entry
+        const uint4 ri = S.stage[j];
+        const float qi = __uint_as_float(ri.w);
+        unsigned long long Fxy = 0ull, Cxy = 0ull, Fzu = 0ull, Czu = 0ull;
+        uint32_t m = 0;
+        int s = -1;
+        while (true) {
+            uint32_t kA = 0, kB = jo;
+            while (m == 0 && ++s < nsl) m = S.mask[s][col];
+            if (m == 0) break;
+            kA = lds_u16(fbase + 2u * (uint32_t)(32 * s + __ffs(m) - 1));
+            m &= m - 1;
+            while (m == 0 && ++s < nsl) m = S.mask[s][col];
+            if (m != 0) {
+                kB = lds_u16(fbase + 2u * (uint32_t)(32 * s + __ffs(m) - 1));
+                m &= m - 1;
+            }
+            const uint4 pa = lds_u4(kA - kStageBack), pb = lds_u4(kB - kStageBack);
+            const unsigned long long d0 = mul2(pk2((float)(int)(ri.x - pa.x), (float)(int)(ri.x - pb.x)), sx2);
+            const unsigned long long d1 = mul2(pk2((float)(int)(ri.y - pa.y), (float)(int)(ri.y - pb.y)), sy2);
+            const unsigned long long d2 = mul2(pk2((float)(int)(ri.z - pa.z), (float)(int)(ri.z - pb.z)), sz2);
+            float a0, b0, a1, b1, a2, b2, r2a, r2b;
+            upk2(d0, a0, b0);
+            upk2(d1, a1, b1);
+            upk2(d2, a2, b2);
+            upk2(fma2(d2, d2, fma2(d1, d1, mul2(d0, d0))), r2a, r2b);
+            const bool va = kA != jo && r2a < rc2, vb = kB != jo && r2b < rc2;
+            // a pass slot without a pair: zero charge product at a finite r^2
+            unsigned long long g2, u2;
+            pair_terms2(nf, pk2(va ? qi * __uint_as_float(pa.w) : 0.f, vb ? qi * __uint_as_float(pb.w) : 0.f),
+                        pk2(va ? r2a : rc2, vb ? r2b : rc2), g2, u2);
+            float ga, gb, ua, ub;
+            upk2(g2, ga, gb);
+            upk2(u2, ua, ub);
+            kahan2(Fxy, Cxy, fma2(dup2(ga), pk2(a0, a1), mul2(dup2(gb), pk2(b0, b1))));
+            kahan2(Fzu, Czu, fma2(pk2(ga, 1.f), pk2(a2, ua), mul2(pk2(gb, 1.f), pk2(b2, ub))));
+        }
+        if (has) {
+            const uint32_t g = tinf.x;
+            float fx, fy, fz, us, cx, cy, cz_, uc;
+            upk2(Fxy, fx, fy);
+            upk2(Cxy, cx, cy);
+            upk2(Fzu, fz, us);
+            upk2(Czu, cz_, uc);
+            Fn[g] = fx - cx;
+            Fn[a.stride + g] = fy - cy;
+            Fn[2 * (size_t)a.stride + g] = fz - cz_;
+            sumU += 0.5f * (us - uc);        // each pair counted from both ends
+        }
+    }
+    warp_partial((double)sumU, a.U_part, blk, tid, NT);
+}
+
+constexpr int kBrickThreads = 256, kBrickCap = 1088, kBrickFCap = 7296, kBrickMW = 16, kBrickB = 3,
+              kBrickTmax = 288;
+using BrickSmemSingle = BrickSmem<kBrickCap, kBrickFCap, kBrickThreads, kBrickMW, kBrickB, kBrickB, kBrickTmax>;
+// three bricks per SM: 3 x (size + 1 KB reserved per block) within the SM's 228 KB
+static_assert(sizeof(BrickSmemSingle) + 1024 <= 228 * 1024 / 3, "three bricks per SM");
+__global__ void __launch_bounds__(kBrickThreads, 3)
+    k_near_bricks(const __grid_constant__ NearArgs a, const __grid_constant__ NearF nf, BrickGeom g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true, false>(a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false> *>(smem_raw), (int)threadIdx.x);
+    near_brick_body(a, nf, g, blockIdx.x, *reinterpret_cast<BrickSmemSingle *>(smem_raw), (int)threadIdx.x);
 }
 
 // FP64 build: the same tiles with the 32-byte records (the staging buffer holds 1280 of
@@ -893,13 +1414,61 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
 static void set_tile_smem_attr() {
     static bool done = false;
     if (!done) {
-        cudaFuncSetAttribute(k_near_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false>));
         cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true>));
         cudaFuncSetAttribute(k_near_tiled64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem64));
+        cudaFuncSetAttribute(k_near_bricks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BrickSmemSingle));
         done = true;
     }
+}
+
+// The FP32 pair constants of the tiled kernels, each duplicated into both halves of a
+// 64-bit word for packed FP32x2 arithmetic.
+static unsigned long long dup2_host(float f) {
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return ((unsigned long long)b << 32) | b;
+}
+static NearF near_f32_consts(const NearConsts &c) {
+    NearF f;
+    std::memset(&f, 0, sizeof(f));
+    f.mtot = c.mtot;
+    f.two = c.two;
+    f.nl2 = dup2_host(-c.inv_lam_log2e_f);
+    f.il2 = dup2_host(c.inv_lam_f);
+    f.ly1 = dup2_host(c.ly1_f);
+    f.nl2b = dup2_host(-c.inv_lam2_log2e_f);
+    f.il2b = dup2_host(c.inv_lam2_f);
+    f.ly2 = dup2_host(c.ly2_f);
+    f.sg2 = dup2_host(c.sgn2_f);
+    for (int g = 0; g < c.mtot; ++g) {
+        f.nb[g] = dup2_host(-c.bl2f[g]);
+        f.naf[g] = dup2_host(-c.af[g]);
+        f.cf[g] = dup2_host(c.cf[g]);
+    }
+    return f;
+}
+
+// Bricks of one system (at least 3 cells per axis): about 230 targets per brick (0.9 of
+// its threads), the staged region and the candidate lists within 0.88 and 0.87 of their
+// buffers on average, which leaves about four standard deviations of room.
+static uint32_t brick_geometry(const Box &box, uint32_t N, BrickGeom *g) {
+    const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
+    g->by = std::min(kBrickB, ny - 2);
+    g->bz = std::min(kBrickB, nz - 2);
+    double occ = (double)N / (double)box.ncell;
+    if (occ < 1e-9) occ = 1e-9;
+    const double tr = (double)(g->by * g->bz);
+    int W = (int)(0.9 * kBrickThreads / (tr * occ) + 0.5);
+    W = std::min(W, (int)(0.88 * kBrickCap / ((g->by + 2) * (g->bz + 2) * occ)) - 2);
+    W = std::min(W, (int)(0.87 * kBrickFCap / (tr * 27.0 * occ)));
+    W = std::min(std::min(W, kBrickMW), nx - 2);
+    if (W < 1) W = 1;
+    g->tiles_x = (nx + W - 1) / W;
+    g->W = (nx + g->tiles_x - 1) / g->tiles_x;
+    g->tiles_y = (ny + g->by - 1) / g->by;
+    const int tiles_z = (nz + g->bz - 1) / g->bz;
+    return (uint32_t)g->tiles_x * (uint32_t)g->tiles_y * (uint32_t)tiles_z;
 }
 
 int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
@@ -908,8 +1477,10 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     near_geometry(a.box, a.N, &tiled, &W, &tiles_x, &nb);
     if (prec == 1 && tiled) {
         set_tile_smem_attr();
-        k_near_tiled<<<nb, kTileThreads, sizeof(TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false>), st>>>(a, W, tiles_x);
-        return (int)nb * kWarpsPerBlock;
+        BrickGeom g;
+        nb = brick_geometry(a.box, a.N, &g);
+        k_near_bricks<<<nb, kBrickThreads, sizeof(BrickSmemSingle), st>>>(a, near_f32_consts(a.nc), g);
+        return (int)nb * (kBrickThreads / 32);
     }
     if (prec == 0 && tiled) {
         set_tile_smem_attr();

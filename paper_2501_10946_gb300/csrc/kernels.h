@@ -155,7 +155,7 @@ struct NearArgs {
     double *U_part;            // near energy partials, one per warp
     DevCounters *ctr;          // error bits: skip the pair loops when the cell build overflowed
 };
-int launch_near(int prec, const NearArgs &a, cudaStream_t st);   // returns #energy partials (4 per block)
+int launch_near(int prec, const NearArgs &a, cudaStream_t st);   // returns #energy partials (one per warp)
 struct RhoArgs {
     const void *rec;
     uint32_t N;

@@ -741,7 +741,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         dalloc(c, &c->inject_m, 3 * (size_t)p.P) || dalloc(c, &c->coef, (size_t)p.P) ||
         dalloc(c, &c->partial, (size_t)c->G * 8 * p.P) || dalloc(c, &c->rho, (size_t)p.P) ||
         dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, (size_t)p.P) ||
-        dalloc(c, &c->U_part, 4 * std::max((n + 127) / 128, (size_t)bx.ncell) + 4) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
+        dalloc(c, &c->U_part, 8 * std::max((n + 127) / 128, (size_t)bx.ncell) + 8) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
         dalloc(c, &c->energy, 8) || dalloc(c, &c->escratch, 3 * (size_t)kEnergyBlocks) || dalloc(c, &c->edone, 1) ||
         dalloc(c, &c->ctr, 1)) {
         g_init_error = "device allocation failed";

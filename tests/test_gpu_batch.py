@@ -87,8 +87,10 @@ def test_batch_forces_match_single_contexts_and_the_oracle():
             R.rbsog_set_ksample(c.h, modes[i])
             Fs = np.zeros((w.N, 3))
             es = R.rbsog_forces(c.h, Fs, energy=True)
-        # same cells, same near kernel and block shapes: the near energy is bit-identical
-        assert e[i]["U_near"] == es["U_near"], i
+        # same cells and the same pairs in the same order per particle; the tile shapes of
+        # the two near kernels differ, and with them which two pairs share a pass, so the
+        # near energies agree to FP32 rounding
+        assert abs(e[i]["U_near"] - es["U_near"]) <= 1e-7 * abs(es["U_near"]), i
         assert e[i]["U_self"] == es["U_self"], i
         assert core.rel_l2(Fi, Fs) <= FP32_TOL, i
         assert abs(e[i]["U_far"] - es["U_far"]) <= FP32_TOL * abs(es["U_far"]), i

@@ -126,5 +126,6 @@ def test_egs_system_in_a_batch_matches_a_single_context():
             R.rbsog_set_ksample(c.h, modes[i])
             Fs = np.zeros((w.N, 3))
             es = R.rbsog_forces(c.h, Fs, energy=True)
-        assert eb[i]["U_near"] == es["U_near"], i
+        # different tile shapes, the same pairs per particle: FP32 rounding of the pass sums
+        assert abs(eb[i]["U_near"] - es["U_near"]) <= 1e-7 * abs(es["U_near"]), i
         assert core.rel_l2(F[p_off[i]:p_off[i + 1]], Fs) <= FP32_TOL, i
