@@ -969,7 +969,8 @@ struct BrickSmem {
     uint2 tinfo[TMX];                       // brick target t: global index, staged index | cell
                                             // << 12 | mask column << 20
     long long ref[3];                       // fixed-point brick centre
-    int staged, next;                       // staging decision; next target cell to filter
+    int staged, next, copied;               // staging decision; next target cell to filter;
+                                            // bulk copies started
     unsigned long long mbar;
 };
 
@@ -1026,7 +1027,9 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     }
     if (tid == 32) S.next = 0;
     group_sync<NT, 0>();
-    // (b) warp 0: row offsets in the staging buffer; warp 1: targets per target row (target
+    // (b) warp 0: row offsets in the staging buffer and, when the region fits the buffer, the
+    // bulk copies, one row per lane (a row is one slice, or two across the periodic seam:
+    // cells before the one at x = 0, then the rest); warp 1: targets per target row (target
     // row tr = ty + by tz sits in region row (tz+1) nry + ty+1); the other warps: per target
     // cell tc = tr * ntc + i - 1 its descriptor, its targets and the size of its 27-cell list
     // (neighbour row q = 0..8 of target row tr is region row (tz + q/3) nry + ty + q%3)
@@ -1034,7 +1037,41 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
         const int v = lane < nr ? S.row_tot[lane] : 0;
         const int inc = warp_incl_scan(v, lane);
         if (lane < nr) S.row_base[lane] = inc - v;
+        const int region = __shfl_sync(full, inc, 31);
         if (lane == 31) S.row_base[nr] = inc;
+        const bool copy = !overflow && region > 0 && region <= CAP;
+        if (lane == 0) {
+            S.copied = copy;
+            if (copy) {
+                const uint32_t bar = smem_u32(&S.mbar);
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                             "r"((uint32_t)region * 16u) : "memory");
+            }
+        }
+        __syncwarp();
+        if (copy && lane < nr) {
+            const uint32_t bar = smem_u32(&S.mbar);
+            const uint4 *rec = (const uint4 *)a.rec;
+            const int is = x0 == 0 ? 1 : (x1 == nx ? wn - 1 : wn);
+            const uint32_t n0 = (uint32_t)S.seg_off[lane][is];
+            const uint32_t n1 = (uint32_t)(S.seg_off[lane][wn] - S.seg_off[lane][is]);
+            const uint32_t dst = (uint32_t)(inc - v);
+            if (n0)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(&S.stage[dst])),
+                    "l"(rec + S.cstart[lane][0]), "r"(n0 * 16u), "r"(bar)
+                    : "memory");
+            if (n1)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(&S.stage[dst + n0])),
+                    "l"(rec + S.cstart[lane][is]), "r"(n1 * 16u), "r"(bar)
+                    : "memory");
+        }
     } else if (wid == 1) {
         int v = 0;
         if (lane < ntr) {
@@ -1084,17 +1121,8 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
             const int region_n = S.row_base[nr];
             // (the candidate lists hold 16-bit shared addresses of the offsets: the buffer
             // sits at the start of the block's shared memory, far below 64 KB)
-            const int st = !overflow && region_n <= CAP && fcarry <= FCAP && lmax <= 32 * kBrickSlots &&
-                           ccarry <= TMX && smem_u32(&S.off[CAP]) <= 65536u;
-            S.staged = st;
-            if (st && region_n > 0) {
-                const uint32_t bar = smem_u32(&S.mbar);
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                             "r"((uint32_t)region_n * 16u) : "memory");
-            }
+            S.staged = !overflow && region_n <= CAP && fcarry <= FCAP && lmax <= 32 * kBrickSlots &&
+                       ccarry <= TMX && smem_u32(&S.off[CAP]) <= 65536u;
         }
     }
     group_sync<NT, 0>();
@@ -1115,6 +1143,7 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
             Fn[g] = F[0]; Fn[a.stride + g] = F[1]; Fn[2 * (size_t)a.stride + g] = F[2];
             Ufall += U;
         }
+        if (S.copied) mbar_wait0(smem_u32(&S.mbar), 20000);   // copies in flight land first
         warp_partial(Ufall, a.U_part, blk, tid, NT);
         return;
     }
@@ -1123,28 +1152,8 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
         return;
     }
     const uint32_t bar = smem_u32(&S.mbar);
-    // (d) the bulk copies, one row per lane of warp 0 (a row is one slice, or two across the
-    // periodic seam: cells before the one at x = 0, then the rest); meanwhile the candidate
-    // lists of the target cells, rows q = 0..8 in order, each row's cells i-1 .. i+1 in
-    // staging order
-    if (tid < nr) {
-        const uint4 *rec = (const uint4 *)a.rec;
-        const int is = x0 == 0 ? 1 : (x1 == nx ? wn - 1 : wn);
-        const uint32_t n0 = (uint32_t)S.seg_off[tid][is], n1 = (uint32_t)(S.seg_off[tid][wn] - S.seg_off[tid][is]);
-        const uint32_t dst = (uint32_t)S.row_base[tid];
-        if (n0)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(&S.stage[dst])),
-                "l"(rec + S.cstart[tid][0]), "r"(n0 * 16u), "r"(bar)
-                : "memory");
-        if (n1)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(&S.stage[dst + n0])),
-                "l"(rec + S.cstart[tid][is]), "r"(n1 * 16u), "r"(bar)
-                : "memory");
-    }
+    // (d) while the copies fly: the candidate lists of the target cells, rows q = 0..8 in
+    // order, each row's cells i-1 .. i+1 in staging order
     for (int e = tid; e < 9 * ncells; e += NT) {
         const int tc = e / 9, q = e - tc * 9;
         const uint32_t ci = S.cinfo[tc];
