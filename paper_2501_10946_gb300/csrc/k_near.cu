@@ -875,8 +875,12 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
 // Lower bound of cell k (any integer, unwrapped) of n in the 2^32 fixed point:
 // ceil(k 2^32 / n), the least s with floor(s n / 2^32) = k.
 __device__ __forceinline__ long long cell_lo(int k, int n) {
+    // the FP64 quotient is within one of the exact one; integer products settle it
     const long long num = (long long)k << 32;
-    return num >= 0 ? (num + n - 1) / n : -((-num) / n);
+    long long q = (long long)floor((double)k * (4294967296.0 / (double)n));
+    while (q * n < num) ++q;
+    while ((q - 1) * n >= num) --q;
+    return q;
 }
 
 // ---------------------------------------------------------------- FP32 brick tiles
@@ -937,10 +941,10 @@ __device__ __forceinline__ void sts4_lane0(int lane, uint32_t a, uint32_t m0, ui
                  : "memory");
 }
 
-// W: run length in cells along x; tiles_x, tiles_y: bricks per row and per y-layer;
-// by, bz: rows of a brick along y and z (the last brick of a layer may have fewer)
+// W: run length in cells along x; tiles_x, tiles_y, tiles_z: bricks along each axis (the
+// grid); by, bz: rows of a brick along y and z (the last brick along an axis may have fewer)
 struct BrickGeom {
-    int W, tiles_x, tiles_y, by, bz;
+    int W, tiles_x, tiles_y, tiles_z, by, bz;
 };
 
 constexpr int kBrickSlots = 16;        // candidate slots (32 each) of a target cell: 512
@@ -993,19 +997,23 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
     const uint32_t *cs = a.cell_start;
     const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
-    // brick: x cells x0 .. x1-1, rows y0 .. y0+by-1, z0 .. z0+bz-1
-    const int tx = (int)(blk % (unsigned)bg.tiles_x);
-    const int rest = (int)(blk / (unsigned)bg.tiles_x);
-    const int x0 = tx * bg.W, x1 = min(x0 + bg.W, nx);
-    const int y0 = (rest % bg.tiles_y) * bg.by, z0 = (rest / bg.tiles_y) * bg.bz;
+    // brick (grid index x, y, z): x cells x0 .. x1-1, rows y0 .. y0+by-1, z0 .. z0+bz-1
+    const int x0 = (int)blockIdx.x * bg.W, x1 = min(x0 + bg.W, nx);
+    const int y0 = (int)blockIdx.y * bg.by, z0 = (int)blockIdx.z * bg.bz;
     const int by = min(bg.by, ny - y0), bz = min(bg.bz, nz - z0);
     const int wn = x1 - x0 + 2, ntc = wn - 2;  // region cells x0-1 .. x1; target cells 1 .. wn-2
     const int nry = by + 2, nr = nry * (bz + 2), ntr = by * bz, ncells = ntr * ntc;
     // (a) one region row (y0-1 + r % nry, z0-1 + r / nry) per warp at a time, one cell per
     // lane: global starts, populations and their prefix within the row; the reference point
     // (threads 0..2: the centre of the region's extent on each axis, exact in the fixed point)
+    // (quotients of small integers by float reciprocals: exact, as the operands are far
+    // from multiples of the divisor)
+    const float inry = 1.f / (float)nry, intc = 1.f / (float)ntc, inby = 1.f / (float)by;
     for (int r = wid; r < nr; r += NW) {
-        const int yr = (y0 - 1 + r % nry + ny) % ny, zr = (z0 - 1 + r / nry + nz) % nz;
+        const int rz = __float2int_rz(((float)r + 0.5f) * inry), ry = r - rz * nry;
+        int yr = y0 - 1 + ry, zr = z0 - 1 + rz;
+        yr = yr < 0 ? yr + ny : (yr >= ny ? yr - ny : yr);
+        zr = zr < 0 ? zr + nz : (zr >= nz ? zr - nz : zr);
         const int rowbase = nx * (yr + ny * zr);
         int n = 0;
         if (lane < wn) {
@@ -1075,7 +1083,8 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     } else if (wid == 1) {
         int v = 0;
         if (lane < ntr) {
-            const int rt = (lane / by + 1) * nry + lane % by + 1;
+            const int tz = __float2int_rz(((float)lane + 0.5f) * inby);
+            const int rt = (tz + 1) * nry + lane - tz * by + 1;
             v = S.seg_off[rt][wn - 1] - S.seg_off[rt][1];
         }
         const int inc = warp_incl_scan(v, lane);
@@ -1083,8 +1092,9 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
         if (lane == 31) S.tp[ntr] = inc;
     } else {
         for (int tc = tid - 64; tc < ncells; tc += NT - 64) {
-            const int tr = tc / ntc, i = tc - tr * ntc + 1;
-            const int rb = (tr / by) * nry + tr % by;
+            const int tr = __float2int_rz(((float)tc + 0.5f) * intc), i = tc - tr * ntc + 1;
+            const int tz = __float2int_rz(((float)tr + 0.5f) * inby);
+            const int rb = tz * nry + tr - tz * by;
             const int rt = rb + nry + 1;
             int tot = 0;
             for (int q = 0; q < 9; ++q) {
@@ -1153,20 +1163,33 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     }
     const uint32_t bar = smem_u32(&S.mbar);
     // (d) while the copies fly: the candidate lists of the target cells, rows q = 0..8 in
-    // order, each row's cells i-1 .. i+1 in staging order
-    for (int e = tid; e < 9 * ncells; e += NT) {
-        const int tc = e / 9, q = e - tc * 9;
-        const uint32_t ci = S.cinfo[tc];
-        const int i = (int)((ci >> 8) & 0xffu), rb = (int)((ci >> 16) & 0xffu);
-        int pos = S.fb[tc];
-        for (int u = 0; u < q; ++u) {
-            const int r = rb + (u / 3) * nry + u % 3;
-            pos += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
+    // order, each row's cells i-1 .. i+1 in staging order; three cells per warp at a time,
+    // nine lanes per cell (one per row, each writing its row's stretch)
+    {
+        const int grp = lane / 9, q = lane - 9 * grp;
+        for (int tc0 = 3 * wid; tc0 < ncells; tc0 += 3 * NW) {
+            const int tc = tc0 + grp;
+            const bool act = grp < 3 && tc < ncells;
+            int n = 0, a0 = 0, r = 0;
+            if (act) {
+                const uint32_t ci = S.cinfo[tc];
+                const int i = (int)((ci >> 8) & 0xffu), rb = (int)((ci >> 16) & 0xffu);
+                r = rb + (q / 3) * nry + q % 3;
+                a0 = S.seg_off[r][i - 1];
+                n = S.seg_off[r][i + 2] - a0;
+            }
+            int inc = n;                                     // prefix within the nine lanes
+#pragma unroll
+            for (int o = 1; o < 9; o <<= 1) {
+                const int v = __shfl_up_sync(full, inc, o);
+                if (q >= o) inc += v;
+            }
+            if (act) {
+                const int pos = S.fb[tc] + inc - n;
+                const uint32_t oa = smem_u32(&S.off[S.row_base[r] + a0]);
+                for (int l = 0; l < n; ++l) S.flat[pos + l] = (uint16_t)(oa + 16u * (uint32_t)l);
+            }
         }
-        const int r = rb + (q / 3) * nry + q % 3;
-        const int a0 = S.seg_off[r][i - 1], n = S.seg_off[r][i + 2] - a0;
-        const uint32_t oa = smem_u32(&S.off[S.row_base[r] + a0]);
-        for (int l = 0; l < n; ++l) S.flat[pos + l] = (uint16_t)(oa + 16u * (uint32_t)l);
     }
     // bounded wait for the staged bytes (phase 0, at most about 2 s), made block-uniform
     uint32_t done = mbar_wait0(bar, 20000);
@@ -1352,7 +1375,8 @@ static_assert(sizeof(BrickSmemSingle) + 1024 <= 228 * 1024 / 3, "three bricks pe
 __global__ void __launch_bounds__(kBrickThreads, 3)
     k_near_bricks(const __grid_constant__ NearArgs a, const __grid_constant__ NearF nf, BrickGeom g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_brick_body(a, nf, g, blockIdx.x, *reinterpret_cast<BrickSmemSingle *>(smem_raw), (int)threadIdx.x);
+    near_brick_body(a, nf, g, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                    *reinterpret_cast<BrickSmemSingle *>(smem_raw), (int)threadIdx.x);
 }
 
 // FP64 build: the same tiles with the 32-byte records (the staging buffer holds 1280 of
@@ -1476,8 +1500,8 @@ static uint32_t brick_geometry(const Box &box, uint32_t N, BrickGeom *g) {
     g->tiles_x = (nx + W - 1) / W;
     g->W = (nx + g->tiles_x - 1) / g->tiles_x;
     g->tiles_y = (ny + g->by - 1) / g->by;
-    const int tiles_z = (nz + g->bz - 1) / g->bz;
-    return (uint32_t)g->tiles_x * (uint32_t)g->tiles_y * (uint32_t)tiles_z;
+    g->tiles_z = (nz + g->bz - 1) / g->bz;
+    return (uint32_t)g->tiles_x * (uint32_t)g->tiles_y * (uint32_t)g->tiles_z;
 }
 
 int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
@@ -1488,7 +1512,8 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
         set_tile_smem_attr();
         BrickGeom g;
         nb = brick_geometry(a.box, a.N, &g);
-        k_near_bricks<<<nb, kBrickThreads, sizeof(BrickSmemSingle), st>>>(a, near_f32_consts(a.nc), g);
+        k_near_bricks<<<dim3(g.tiles_x, g.tiles_y, g.tiles_z), kBrickThreads, sizeof(BrickSmemSingle), st>>>(
+            a, near_f32_consts(a.nc), g);
         return (int)nb * (kBrickThreads / 32);
     }
     if (prec == 0 && tiled) {
