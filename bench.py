@@ -36,6 +36,7 @@ MUFU_PER_CLK_SM = 16            # sin/cos and rsqrt special-function results per
 EX2_PER_CLK_SM = 32             # ex2 results per clock per SM (measured)
 FP32_PER_CLK_SM = 128           # FP32 lanes per SM
 NEAR_FP32_OPS_PER_PAIR = 25     # separation, r^2, Yukawa and Gaussian terms, force accumulation
+NEAR_FILTER_OPS = 4             # pre-filter test of one candidate of one target: three FMAs, a compare
 KERNELS_PER_STEP = 11
 # DRAM bytes per launch of each kernel group from an ncu capture, with the SHA-256 of the
 # kernel's source file at capture time: a kernel whose source has changed since gets no
@@ -443,10 +444,11 @@ def roofline(prof, w, pk, mtot):
         xu_s = pairs * (1.0 / MUFU_PER_CLK_SM + (1.0 + mtot) / EX2_PER_CLK_SM) / (SMS * clk)
         extra["xu"] = {"frac": xu_s / avg_s, "basis": f"1 rsqrt at {MUFU_PER_CLK_SM}/clk/SM + {1 + mtot} ex2 at "
                                                       f"{EX2_PER_CLK_SM}/clk/SM per in-range pair"}
+        # the pre-filter tests each candidate of a target with three FMAs and a compare
         cand = near_candidates(w)
         extra["overhead"] = {"candidates_per_particle": cand / w.N, "pairs_per_particle": pairs / w.N,
-                             "filter_ops_per_candidate": 6,
-                             "frac_with_filter_ops": (units + 6.0 * cand) / avg_s / 1e9 / peak}
+                             "filter_ops_per_candidate": NEAR_FILTER_OPS,
+                             "frac_with_filter_ops": (units + NEAR_FILTER_OPS * cand) / avg_s / 1e9 / peak}
     else:
         units, peak, basis = None, None, ""
     achieved = units / avg_s / 1e9 if units else None
