@@ -947,19 +947,18 @@ struct BrickGeom {
     int W, tiles_x, tiles_y, tiles_z, by, bz;
 };
 
-constexpr int kBrickSlots = 16;        // candidate slots (32 each) of a target cell: 512
-
-template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX>
+template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX, int MP>
 struct BrickSmem {
     static constexpr int NR = (BY + 2) * (BZ + 2);     // neighbourhood rows
     static constexpr int NTR = BY * BZ;                // target rows
     static constexpr int NC = NTR * MW;                // target cells
     static_assert(CAP * 32 <= 65535, "shared addresses of the offsets are 16-bit");
-    static_assert(CAP <= 4096 && NC <= 256 && TMX <= 1024 && NR <= 256, "packed descriptors");
+    static_assert(CAP <= 4096 && NC <= 256 && NR <= 32 && NTR <= 32, "packed descriptors, one row per lane");
     uint4 stage[CAP];                       // staged records
     float4 off[CAP];                        // FP32 offsets c from the brick centre (x, y, z, -|c|^2/2)
     uint16_t flat[FCAP];                    // per target cell: shared addresses of its candidates' offsets
-    uint32_t mask[kBrickSlots][TMX];        // per target: hit bits (a cell's targets take 4-aligned columns)
+    uint32_t mpool[MP];                     // hit masks: per target cell a block of slots x stride
+                                            // words (stride: its targets rounded up to 4)
     int seg_off[NR][MW + 3];                // per row: offset of each region cell within the row
     uint32_t cstart[NR][MW + 2];            // per row: global start of each region cell
     int row_tot[NR];                        // per row: staged particles
@@ -968,10 +967,10 @@ struct BrickSmem {
                                             // first neighbour row << 16 | target row << 24
     int cnt[NC];                            // target cell tc: its targets
     int fb[NC + 1];                         // target cell tc: candidates flat[fb[tc] .. fb[tc+1])
-    int ccol[NC];                           // target cell tc: first mask column of its targets
+    int mbase[NC];                          // target cell tc: first word of its mask block
     int tp[NTR + 1];                        // target row tr: brick targets tp[tr] .. tp[tr+1]
     uint2 tinfo[TMX];                       // brick target t: global index, staged index | cell
-                                            // << 12 | mask column << 20
+                                            // << 12 | index within the cell << 20
     long long ref[3];                       // fixed-point brick centre
     int staged, next, copied;               // staging decision; next target cell to filter;
                                             // bulk copies started
@@ -987,9 +986,9 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX>
+template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX, int MP>
 __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &nf, const BrickGeom &bg,
-                                                unsigned blk, BrickSmem<CAP, FCAP, NT, MW, BY, BZ, TMX> &S,
+                                                unsigned blk, BrickSmem<CAP, FCAP, NT, MW, BY, BZ, TMX, MP> &S,
                                                 int tid) {
     constexpr int NW = NT / 32;
     const int lane = tid & 31, wid = tid >> 5;
@@ -1107,32 +1106,29 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
         }
     }
     group_sync<NT, 0>();
-    // (c) warp 0: offsets of the candidate lists and the mask columns (4 per started group
-    // of 4 targets) of the target cells; the staging decision
+    // (c) warp 0: offsets of the candidate lists and of the mask blocks (slots of 32
+    // candidates x targets rounded up to 4) of the target cells; the staging decision
     if (wid == 0) {
-        int fcarry = 0, ccarry = 0, lmax = 0;
+        int fcarry = 0, mcarry = 0;
         for (int base = 0; base < ncells; base += 32) {
             const int tc = base + lane;
             const int len = tc < ncells ? S.fb[tc + 1] : 0;
-            const int nc4 = tc < ncells ? (S.cnt[tc] + 3) & ~3 : 0;
-            lmax = max(lmax, len);
-            const int fi = warp_incl_scan(len, lane), ci = warp_incl_scan(nc4, lane);
+            const int words = tc < ncells ? ((len + 31) >> 5) * ((S.cnt[tc] + 3) & ~3) : 0;
+            const int fi = warp_incl_scan(len, lane), mi = warp_incl_scan(words, lane);
             if (tc < ncells) {
                 S.fb[tc + 1] = fcarry + fi;
-                S.ccol[tc] = ccarry + ci - nc4;
+                S.mbase[tc] = mcarry + mi - words;
             }
             fcarry += __shfl_sync(full, fi, 31);
-            ccarry += __shfl_sync(full, ci, 31);
+            mcarry += __shfl_sync(full, mi, 31);
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) lmax = max(lmax, __shfl_xor_sync(full, lmax, o));
         if (lane == 0) {
             S.fb[0] = 0;
             const int region_n = S.row_base[nr];
             // (the candidate lists hold 16-bit shared addresses of the offsets: the buffer
             // sits at the start of the block's shared memory, far below 64 KB)
-            S.staged = !overflow && region_n <= CAP && fcarry <= FCAP && lmax <= 32 * kBrickSlots &&
-                       ccarry <= TMX && smem_u32(&S.off[CAP]) <= 65536u;
+            S.staged = !overflow && region_n <= CAP && fcarry <= FCAP && mcarry <= MP && S.tp[ntr] <= TMX &&
+                       smem_u32(&S.off[CAP]) <= 65536u;
         }
     }
     group_sync<NT, 0>();
@@ -1216,9 +1212,9 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     const float rc2 = a.nc.rc2_f;
     // Pre-filter: accept candidate c of target t when t.c - |c|^2/2 > (|t|^2 - thr)/2, which
     // is |t - c|^2 < thr, with thr = r_c^2 (1 + 1e-3).  Offsets from the centre are at most
-    // (MW/2 + 1) c = 9 c along x and 2.5 c along y and z (c < 4/3 r_c, the cell width, as
+    // (MW/2 + 1) c = 9 c along x and 3 c along y and z (c < 4/3 r_c, the cell width, as
     // n_c = floor(L / r_c) >= 3), each within 2.4e-7 of its size after two roundings; the
-    // ten roundings of the test's terms (each at most 141 c^2) and the offsets' own errors
+    // ten roundings of the test's terms (each at most 150 c^2) and the offsets' own errors
     // move the decision by less than 4e-4 r_c^2 in r^2, so every pair that the exact test
     // accepts passes.
     static_assert(MW <= 16, "pre-filter margin");
@@ -1227,7 +1223,6 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     // (f) pre-filter, target cells taken by the warps in turn; the cell's targets in chunks
     // of 8 (two groups of 4 mask columns), a chunk of at most 4 with half the work.  Each cell
     // also records its targets' descriptors.
-    constexpr uint32_t kRowBytes = 4u * TMX;                   // bytes between mask slots
     while (true) {
         int c = 0;
         if (lane == 0) c = atomicAdd(&S.next, 1);
@@ -1239,12 +1234,12 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
         const int nt = S.cnt[c];
         const int f0 = S.fb[c], len = S.fb[c + 1] - f0;
         const int nsl = (len + 31) >> 5;
-        const int col0 = S.ccol[c];
+        const uint32_t kRowBytes = 4u * (uint32_t)((nt + 3) & ~3);        // bytes between mask slots
         const int tbase = S.tp[tr] + S.seg_off[rt][i] - S.seg_off[rt][1];    // its brick index
         for (int k = lane; k < nt; k += 32)
             S.tinfo[tbase + k] = make_uint2(S.cstart[rt][i] + (uint32_t)k,
-                                            (uint32_t)(ts + k) | ((uint32_t)c << 12) | ((uint32_t)(col0 + k) << 20));
-        const uint32_t mcol = smem_u32(&S.mask[0][col0]);
+                                            (uint32_t)(ts + k) | ((uint32_t)c << 12) | ((uint32_t)k << 20));
+        const uint32_t mcol = smem_u32(&S.mpool[S.mbase[c]]);
         for (int t0 = 0; t0 < nt; t0 += 8) {
             const int nct = min(8, nt - t0);
             // the chunk's targets, two per packed register: x, y, z and the bound
@@ -1311,9 +1306,11 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
         const int t = wlo + lane;
         const bool has = t < T;
         const uint2 tinf = S.tinfo[has ? t : wlo];
-        const int j = (int)(tinf.y & 0xfffu), tc = (int)((tinf.y >> 12) & 0xffu), col = (int)(tinf.y >> 20);
+        const int j = (int)(tinf.y & 0xfffu), tc = (int)((tinf.y >> 12) & 0xffu), kk = (int)(tinf.y >> 20);
         const uint32_t fbase = flat_s + 2u * (uint32_t)S.fb[tc];
         const int nsl = has ? (S.fb[tc + 1] - S.fb[tc] + 31) >> 5 : 0;
+        const uint32_t *mrow = &S.mpool[S.mbase[tc] + kk];       // its masks, one per slot
+        const int mstride = (S.cnt[tc] + 3) & ~3;
         const uint32_t jo = smem_u32(&S.off[j]);                 // the target's own entry
         const uint4 ri = S.stage[j];
         const float qi = __uint_as_float(ri.w);
@@ -1322,11 +1319,11 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
         int s = -1;
         while (true) {
             uint32_t kA = 0, kB = jo;
-            while (m == 0 && ++s < nsl) m = S.mask[s][col];
+            while (m == 0 && ++s < nsl) m = mrow[s * mstride];
             if (m == 0) break;
             kA = lds_u16(fbase + 2u * (uint32_t)(32 * s + __ffs(m) - 1));
             m &= m - 1;
-            while (m == 0 && ++s < nsl) m = S.mask[s][col];
+            while (m == 0 && ++s < nsl) m = mrow[s * mstride];
             if (m != 0) {
                 kB = lds_u16(fbase + 2u * (uint32_t)(32 * s + __ffs(m) - 1));
                 m &= m - 1;
@@ -1367,9 +1364,10 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     warp_partial((double)sumU, a.U_part, blk, tid, NT);
 }
 
-constexpr int kBrickThreads = 256, kBrickCap = 1088, kBrickFCap = 7296, kBrickMW = 16, kBrickB = 3,
-              kBrickTmax = 288;
-using BrickSmemSingle = BrickSmem<kBrickCap, kBrickFCap, kBrickThreads, kBrickMW, kBrickB, kBrickB, kBrickTmax>;
+constexpr int kBrickThreads = 256, kBrickCap = 1216, kBrickFCap = 7680, kBrickMW = 16, kBrickBY = 2, kBrickBZ = 4,
+              kBrickTmax = 288, kBrickMaskWords = 2560;
+using BrickSmemSingle =
+    BrickSmem<kBrickCap, kBrickFCap, kBrickThreads, kBrickMW, kBrickBY, kBrickBZ, kBrickTmax, kBrickMaskWords>;
 // three bricks per SM: 3 x (size + 1 KB reserved per block) within the SM's 228 KB
 static_assert(sizeof(BrickSmemSingle) + 1024 <= 228 * 1024 / 3, "three bricks per SM");
 __global__ void __launch_bounds__(kBrickThreads, 3)
@@ -1487,8 +1485,8 @@ static NearF near_f32_consts(const NearConsts &c) {
 // buffers on average, which leaves about four standard deviations of room.
 static uint32_t brick_geometry(const Box &box, uint32_t N, BrickGeom *g) {
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
-    g->by = std::min(kBrickB, ny - 2);
-    g->bz = std::min(kBrickB, nz - 2);
+    g->by = std::min(kBrickBY, ny - 2);
+    g->bz = std::min(kBrickBZ, nz - 2);
     double occ = (double)N / (double)box.ncell;
     if (occ < 1e-9) occ = 1e-9;
     const double tr = (double)(g->by * g->bz);
