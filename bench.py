@@ -351,8 +351,16 @@ def served_stream(torch, R, n_jobs=64, rate=50.0, plain=True):
     out = {"workload": f"yocp_stream{n_jobs}", "jobs": n_jobs, "arrival_rate_per_s": rate,
            "N_range": [min(w.N for w, _, _ in js), max(w.N for w, _, _ in js)],
            "steps_range": [min(n for _, n, _ in js), max(n for _, n, _ in js)], "particle_steps": work}
-    inputs = [(R.make_params(w, precision=R.RBSOG_FP32, device=dev.index), W.charges(w), W.masses(w),
-               W.positions(w), W.velocities(w)) for w, _, _ in js]
+    wl = [w for w, _, _ in js]
+    if len(wl) > 64:
+        # long streams: the placements with a minimum separation in worker processes
+        # (started by spawn: this process already holds a CUDA context)
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            data = pool.map(W.job_inputs, wl, chunksize=8)
+    else:
+        data = [W.job_inputs(w) for w in wl]
+    inputs = [(R.make_params(w, precision=R.RBSOG_FP32, device=dev.index),) + d for w, d in zip(wl, data)]
     cap = 6_000_000
     cfg = R.make_server_config(cap, cap // 4, 64 * 256, 64, steps_per_round=32, device=dev.index)
     s = R.rbsog_server_create(cfg)

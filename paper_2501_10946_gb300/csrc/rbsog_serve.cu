@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <deque>
+#include <memory>
 #include <string>
 #include <thread>
 #include <vector>
@@ -36,6 +37,7 @@ struct Job {
     std::string message;
     size_t footprint = 0;
     rbsog_energy energy{};
+    std::shared_ptr<HostSystem> hs;      // set up on its first admission attempt, kept while it waits
 };
 
 std::string g_server_init_error;
@@ -129,20 +131,27 @@ int admit(rbsog_server *s) {
     for (auto it = s->waiting.begin(); it != s->waiting.end();) {
         Job &j = s->jobs[*it];
         if (j.t_arrival > t) break;
-        const auto tp = std::chrono::steady_clock::now();
-        HostSystem hs;
+        auto tp = std::chrono::steady_clock::now();
         std::string err;
-        int code = setup_system(j.p, j.N, j.q.data(), j.m.data(), &hs, &err);
-        if (code == RBSOG_OK && hs.p.precision != RBSOG_FP32) {
-            code = RBSOG_EUNSUPPORTED;
-            err = "served jobs run the FP32 path";
+        int code = RBSOG_OK;
+        if (!j.hs) {
+            // the host setup (SOG, sampler tables) once per job: a job that does not fit yet
+            // keeps it until it does
+            auto hs = std::make_shared<HostSystem>();
+            code = setup_system(j.p, j.N, j.q.data(), j.m.data(), hs.get(), &err);
+            if (code == RBSOG_OK && hs->p.precision != RBSOG_FP32) {
+                code = RBSOG_EUNSUPPORTED;
+                err = "served jobs run the FP32 path";
+            }
+            if (code == RBSOG_OK && (hs->p.sampler != RBSOG_SAMPLER_IID || hs->p.temperature != RBSOG_KT_TARGET ||
+                                     hs->p.q2_total != 0.0)) {
+                code = RBSOG_EUNSUPPORTED;
+                err = "served jobs draw i.i.d. modes at the target temperature";
+            }
+            if (code == RBSOG_OK) j.hs = hs;
+            s->stats[7] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tp).count();
         }
-        if (code == RBSOG_OK && (hs.p.sampler != RBSOG_SAMPLER_IID || hs.p.temperature != RBSOG_KT_TARGET ||
-                                 hs.p.q2_total != 0.0)) {
-            code = RBSOG_EUNSUPPORTED;
-            err = "served jobs draw i.i.d. modes at the target temperature";
-        }
-        if (code == RBSOG_OK && !engine_fits(b, hs) && b->R == 0) {
+        if (code == RBSOG_OK && !engine_fits(b, *j.hs) && b->R == 0) {
             code = RBSOG_ENOMEM;
             err = "job larger than the server's arenas";
         }
@@ -151,16 +160,20 @@ int admit(rbsog_server *s) {
             j.error = code;
             j.message = err;
             j.t_done = now_s(s);
+            j.hs.reset();
             it = s->waiting.erase(it);
             continue;
         }
-        if (!engine_fits(b, hs)) {
+        if (!engine_fits(b, *j.hs)) {
             ++it;
             continue;
         }
+        tp = std::chrono::steady_clock::now();
+        HostSystem &hs = *j.hs;
         if ((code = system_S(&hs, &err)) != RBSOG_OK) return sfail(s, code, err);
         j.footprint = engine_footprint(b, hs);
         if ((code = engine_append(b, std::move(hs))) != RBSOG_OK) return sfail(s, code, b->err);
+        j.hs.reset();
         s->stats[7] += std::chrono::duration<double>(std::chrono::steady_clock::now() - tp).count();
         s->resident.push_back(j.id);
         admitted.push_back(j.id);

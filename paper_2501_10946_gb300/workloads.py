@@ -211,3 +211,9 @@ def cfg_stream(n_jobs: int = 64, rate: float = 50.0, seed: int = 501) -> list:
                      "uniform", s + 1, s + 2, s + 3, min_sep=0.5)
         out.append((w, nsteps, t))
     return out
+
+
+def job_inputs(w: Workload) -> tuple:
+    """(charges, masses, positions, velocities) of one workload: the inputs a job submits."""
+    return charges(w), masses(w), positions(w), velocities(w)
+
