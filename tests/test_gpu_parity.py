@@ -137,6 +137,29 @@ def test_near_field_all_tile_geometries(nc):
     assert worst <= 1e-3, worst
 
 
+@pytest.mark.parametrize("ncells,occ", [((12, 3, 3), 2.0), ((5, 4, 7), 6.5), ((20, 6, 5), 3.0), ((3, 12, 4), 6.5),
+                                         ((9, 9, 3), 1.0), ((7, 5, 13), 9.0), ((6, 6, 6), 24.0)],
+                         ids=["x12y3z3", "x5y4z7", "x20y6z5", "x3y12z4", "x9y9z3", "x7y5z13", "dense6"])
+def test_near_field_brick_geometries(ncells, occ):
+    """FP32 near field of one system in bricks of up to 2 x 4 rows: boxes of 3 to 20 cells
+    per axis (bricks with fewer rows, seams along every axis, one brick spanning a whole
+    axis) and a dense one whose neighbourhood exceeds the staging buffer (the per-particle
+    fallback), against the oracle, with the missing-pair check."""
+    rc = 1.5
+    box = tuple(n * rc * 1.03 for n in ncells)
+    N = int(occ * ncells[0] * ncells[1] * ncells[2])
+    w = workload(N, None, rc=rc, P=16, seed=sum(ncells), box=box)
+    r = W.positions(w)
+    g = run_forces(w, R.RBSOG_FP32, r, modes_for(w, w.P, 2))
+    assert list(g["cells"][0]) == list(ncells)
+    Ft, Fn, Ff, e, S_ = oracle_forces(w, r, W.charges(w), modes_for(w, w.P, 2))
+    check_forces(g["Fn"], Fn, FP32_TOL, ("near", ncells))
+    check_energy(g["e"]["U_near"], e["U_N"], FP32_TOL, ("U_near", ncells))
+    rms = float(np.sqrt(np.mean(np.sum(Fn * Fn, axis=1))))
+    worst = np.max(np.linalg.norm(g["Fn"] - Fn, axis=1) / (np.linalg.norm(Fn, axis=1) + 0.1 * rms))
+    assert worst <= 1e-3, worst
+
+
 def test_host_and_device_pointers_agree(gpu):
     torch = gpu
     w = workload(600, 8.0, P=32)
