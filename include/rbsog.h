@@ -401,9 +401,10 @@ int rbsog_batch_layout(const rbsog_batch *b, int64_t *p_off, int64_t *m_off, int
  * captured graph.  Synchronous. */
 int rbsog_batch_set_rho_chunk(rbsog_batch *b, const int32_t *rho_chunk);
 
-/* Launch shapes of every system: near_target is the number of particles a near-field
- * CTA aims at (the tile width in cells follows from each system's cell occupancy,
- * capped by the shared-memory staging buffer; default 96), rho_target the particles
+/* Launch shapes of every system: near_target is the number of target particles a
+ * near-field brick (one 256-thread CTA: a run of cells in each of up to 2 x 4 rows) aims
+ * at, up to 230 (the run length follows from each system's cell occupancy, capped by the
+ * brick's shared-memory buffers; default 230), rho_target the particles
  * per structure-factor block (each system's chunk is its N split evenly near that
  * size; default 512).  The near-field shape changes only the order of the near-energy
  * sum; the structure-factor shape the order of rho(k).  Drops the captured graph.
@@ -473,7 +474,7 @@ typedef struct rbsog_server_config {
     int64_t max_particles;   /* resident particles (sum of N), >= 2 */
     int64_t max_cells;       /* resident cells (sum of the jobs' cell counts) */
     int64_t max_modes;       /* resident modes (sum of P) */
-    double near_target;      /* near-field shape (see rbsog_batch_set_shapes); 0 selects 96 */
+    double near_target;      /* near-field shape (see rbsog_batch_set_shapes); 0 selects 230 */
     int32_t max_jobs;        /* resident jobs at once, 1 .. 65536 */
     int32_t steps_per_round; /* steps between admission points, >= 1 */
     int32_t rho_target;      /* structure-factor shape; 0 selects 512 */

@@ -38,7 +38,7 @@ struct rbsog_batch {
     std::vector<rbsog::HostSystem> sys;
     std::vector<uint32_t> p_off{0}, c_off{0}, m_off{0};   // R + 1 entries
     std::vector<int> rho_chunk;                          // particles per structure-factor block
-    double near_target = 96.0;                           // particles per near-field CTA
+    double near_target = rbsog::kNearBrickTarget;        // targets per near-field brick
     int rho_target = 512;
     bool dirty = true;                                   // arguments need rebuilding
     bool force_valid = false;                            // batch API: forces of the state evaluated
@@ -72,6 +72,7 @@ struct rbsog_batch {
     rbsog::EnergyArgs *d_energy[2] = {nullptr, nullptr};
     rbsog::SampleArgs *d_sample = nullptr;
     rbsog::NearArgs *d_near = nullptr;
+    rbsog::NearF *d_nearf = nullptr;                     // each system's FP32 pair constants
     rbsog::NearBatchGeom *d_geom = nullptr;
     rbsog::RhoArgs *d_rho = nullptr;
     int *d_chunk = nullptr;

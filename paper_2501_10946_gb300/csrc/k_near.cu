@@ -33,22 +33,6 @@ constexpr int kGlobalThreads = 128;
 constexpr int kTileThreads = 128;
 constexpr int kSlots = 8;              // candidate slots (32 candidates each) per filter round
 
-// FP32 pair constants of one system, copied to shared memory by each tiled CTA (a batch
-// reads its systems' arguments from global memory, and the pair loop reads them per
-// Gaussian).  Each constant is stored twice in one 64-bit word, for packed arithmetic on
-// two pairs at once.
-struct alignas(16) NearF {
-    int mtot;
-    int two;                                // a second Yukawa term (EGS screening)
-    unsigned long long nl2;                 // -log2(e)/lambda
-    unsigned long long il2;                 // 1/lambda
-    unsigned long long ly1;                 // log2 of the first term's weight
-    unsigned long long nl2b, il2b, ly2, sg2;   // second term: -log2(e)/lambda_2, 1/lambda_2, log2|y2|, sign
-    unsigned long long nb[kMaxGauss];       // -b_m log2(e)
-    unsigned long long naf[kMaxGauss];      // -a_m (the energy's SOG sum is accumulated negated)
-    unsigned long long cf[kMaxGauss];       // c_m
-};
-
 __device__ __forceinline__ unsigned long long dup2(float a) { return pk2(a, a); }
 
 // Compensated sum of two lanes at once (the steps of kahan_add on each lane).
@@ -941,12 +925,6 @@ __device__ __forceinline__ void sts4_lane0(int lane, uint32_t a, uint32_t m0, ui
                  : "memory");
 }
 
-// W: run length in cells along x; tiles_x, tiles_y, tiles_z: bricks along each axis (the
-// grid); by, bz: rows of a brick along y and z (the last brick along an axis may have fewer)
-struct BrickGeom {
-    int W, tiles_x, tiles_y, tiles_z, by, bz;
-};
-
 template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX, int MP>
 struct BrickSmem {
     static constexpr int NR = (BY + 2) * (BZ + 2);     // neighbourhood rows
@@ -974,6 +952,7 @@ struct BrickSmem {
     long long ref[3];                       // fixed-point brick centre
     int staged, next, copied;               // staging decision; next target cell to filter;
                                             // bulk copies started
+    NearF nf;                               // a batched system's pair constants
     unsigned long long mbar;
 };
 
@@ -986,19 +965,32 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
     return v;
 }
 
-template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX, int MP>
-__device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &nf, const BrickGeom &bg,
-                                                unsigned blk, BrickSmem<CAP, FCAP, NT, MW, BY, BZ, TMX, MP> &S,
-                                                int tid) {
+// Brick (bx, byi, bzi) of a system whose geometry is bg; blk: its block index among the
+// system's bricks (energy partials).  PERSIST: the persistent step reuses S for its next
+// brick, so the mbarrier is invalidated once every thread is done with it.
+template <int CAP, int FCAP, int NT, int MW, int BY, int BZ, int TMX, int MP, bool PERSIST = false>
+__device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &nf, const NearBatchGeom &bg, int bx,
+                                                int byi, int bzi, unsigned blk,
+                                                BrickSmem<CAP, FCAP, NT, MW, BY, BZ, TMX, MP> &S, int tid) {
     constexpr int NW = NT / 32;
     const int lane = tid & 31, wid = tid >> 5;
     const unsigned full = 0xffffffffu;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
     const uint32_t *cs = a.cell_start;
     const bool overflow = (a.ctr->err & kErrCellOverflow) != 0;
-    // brick (grid index x, y, z): x cells x0 .. x1-1, rows y0 .. y0+by-1, z0 .. z0+bz-1
-    const int x0 = (int)blockIdx.x * bg.W, x1 = min(x0 + bg.W, nx);
-    const int y0 = (int)blockIdx.y * bg.by, z0 = (int)blockIdx.z * bg.bz;
+    // brick: x cells x0 .. x1-1, rows y0 .. y0+by-1, z0 .. z0+bz-1
+    const int x0 = bx * bg.W, x1 = min(x0 + bg.W, nx);
+    const int y0 = byi * bg.by, z0 = bzi * bg.bz;
+    // (persistent step) the mbarrier of a brick whose copies were started, invalidated once
+    // every thread is past its last use
+    auto release = [&]() {
+        if constexpr (PERSIST) {
+            if (S.copied) {
+                group_sync<NT, 0>();
+                if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
+            }
+        }
+    };
     const int by = min(bg.by, ny - y0), bz = min(bg.bz, nz - z0);
     const int wn = x1 - x0 + 2, ntc = wn - 2;  // region cells x0-1 .. x1; target cells 1 .. wn-2
     const int nry = by + 2, nr = nry * (bz + 2), ntr = by * bz, ncells = ntr * ntc;
@@ -1150,6 +1142,7 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
             Ufall += U;
         }
         if (S.copied) mbar_wait0(smem_u32(&S.mbar), 20000);   // copies in flight land first
+        release();
         warp_partial(Ufall, a.U_part, blk, tid, NT);
         return;
     }
@@ -1192,6 +1185,7 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
     if (!group_sync_and<NT, 0>((int)done)) {
         if (tid == 0) atomicOr(&a.ctr->err, kErrNearStage);
         if (!done) done = mbar_wait0(bar, 20000);     // let the copies in flight land
+        release();
         warp_partial(0.0, a.U_part, blk, tid, NT);
         return;
     }
@@ -1361,19 +1355,22 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
             sumU += 0.5f * (us - uc);        // each pair counted from both ends
         }
     }
+    release();
     warp_partial((double)sumU, a.U_part, blk, tid, NT);
 }
 
-constexpr int kBrickThreads = 256, kBrickCap = 1216, kBrickFCap = 7680, kBrickMW = 16, kBrickBY = 2, kBrickBZ = 4,
+static_assert(kNearBrickThreads == 256, "brick CTA");
+constexpr int kBrickThreads = kNearBrickThreads, kBrickCap = 1216, kBrickFCap = 7680, kBrickMW = 16, kBrickBY = 2, kBrickBZ = 4,
               kBrickTmax = 288, kBrickMaskWords = 2560;
 using BrickSmemSingle =
     BrickSmem<kBrickCap, kBrickFCap, kBrickThreads, kBrickMW, kBrickBY, kBrickBZ, kBrickTmax, kBrickMaskWords>;
 // three bricks per SM: 3 x (size + 1 KB reserved per block) within the SM's 228 KB
 static_assert(sizeof(BrickSmemSingle) + 1024 <= 228 * 1024 / 3, "three bricks per SM");
 __global__ void __launch_bounds__(kBrickThreads, 3)
-    k_near_bricks(const __grid_constant__ NearArgs a, const __grid_constant__ NearF nf, BrickGeom g) {
+    k_near_bricks(const __grid_constant__ NearArgs a, const __grid_constant__ NearF nf, NearBatchGeom g) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_brick_body(a, nf, g, blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+    near_brick_body(a, nf, g, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z,
+                    blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
                     *reinterpret_cast<BrickSmemSingle *>(smem_raw), (int)threadIdx.x);
 }
 
@@ -1387,14 +1384,26 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_near_tiled64(NearArgs a, in
         a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem64 *>(smem_raw), (int)threadIdx.x);
 }
 
-// Batched systems: block -> (system, local block); each system uses tiles or the
-// per-particle path as its geometry says.  geom.W doubles as the first global record
-// index of the system for the per-particle path.
-// Small systems make tiles of few targets (a 1024-particle buffer holds tiles of about
-// 60 to 100), so the batch runs three-warp CTAs: each warp has targets of its own, where
-// four-warp CTAs left one or two idle.  8 CTAs per SM (80 registers, a small spill).
-__global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near_batch(const NearArgs *args, const NearBatchGeom *geom,
-                                                            const uint32_t *items, int R) {
+// Batched systems: block -> (system, its brick); a system of fewer than 3 cells on an axis
+// runs the per-particle path (its first global record index in geom.W).  The system's pair
+// constants are copied to shared memory.
+__device__ __forceinline__ void near_batch_block(const NearArgs &a, const NearF &nfg, const NearBatchGeom &g,
+                                                 unsigned blk, BrickSmemSingle &S, int tid) {
+    if (g.tiled) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&nfg);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&S.nf);
+        for (int i = tid; i < (int)(sizeof(NearF) / 4); i += kBrickThreads) dst[i] = src[i];
+        const int bx = (int)(blk % (unsigned)g.tiles_x);
+        const int rest = (int)(blk / (unsigned)g.tiles_x);
+        near_brick_body(a, S.nf, g, bx, rest % g.tiles_y, rest / g.tiles_y, blk, S, tid);
+    } else {
+        near_global_block<1>(a, (uint32_t)g.W, blk, tid, kBrickThreads);
+    }
+}
+
+__global__ void __launch_bounds__(kBrickThreads, 3) k_near_batch(const NearArgs *args, const NearF *nf,
+                                                                 const NearBatchGeom *geom, const uint32_t *items,
+                                                                 int R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int lo = 0, hi = R - 1;
     while (lo < hi) {
@@ -1402,12 +1411,8 @@ __global__ void __launch_bounds__(kNearBatchThreads, kNearBatchMinBlocks) k_near
         if (items[mid] <= blockIdx.x) lo = mid;
         else hi = mid - 1;
     }
-    const NearArgs &a = args[lo];
-    const NearBatchGeom g = geom[lo];
-    const unsigned blk = blockIdx.x - items[lo];
-    if (g.tiled)
-        near_tile_body<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, false, true>(a, g.W, g.tiles_x, blk, *reinterpret_cast<TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true> *>(smem_raw), (int)threadIdx.x);
-    else near_global_block<1>(a, (uint32_t)g.W, blk);
+    near_batch_block(args[lo], nf[lo], geom[lo], blockIdx.x - items[lo], *reinterpret_cast<BrickSmemSingle *>(smem_raw),
+                     (int)threadIdx.x);
 }
 
 }  // namespace
@@ -1445,8 +1450,7 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
 static void set_tile_smem_attr() {
     static bool done = false;
     if (!done) {
-        cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true>));
+        cudaFuncSetAttribute(k_near_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BrickSmemSingle));
         cudaFuncSetAttribute(k_near_tiled64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileSmem64));
         cudaFuncSetAttribute(k_near_bricks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BrickSmemSingle));
         done = true;
@@ -1460,7 +1464,7 @@ static unsigned long long dup2_host(float f) {
     std::memcpy(&b, &f, 4);
     return ((unsigned long long)b << 32) | b;
 }
-static NearF near_f32_consts(const NearConsts &c) {
+NearF near_f32_consts(const NearConsts &c) {
     NearF f;
     std::memset(&f, 0, sizeof(f));
     f.mtot = c.mtot;
@@ -1480,17 +1484,20 @@ static NearF near_f32_consts(const NearConsts &c) {
     return f;
 }
 
-// Bricks of one system (at least 3 cells per axis): about 230 targets per brick (0.9 of
-// its threads), the staged region and the candidate lists within 0.88 and 0.87 of their
-// buffers on average, which leaves about four standard deviations of room.
-static uint32_t brick_geometry(const Box &box, uint32_t N, BrickGeom *g) {
+// Bricks of one system (at least 3 cells per axis): about `target` targets per brick, the
+// staged region and the candidate lists within 0.88 and 0.87 of their buffers on average,
+// which leaves about four standard deviations of room.
+uint32_t near_bricks(const Box &box, uint32_t N, double target, NearBatchGeom *g) {
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
+    *g = NearBatchGeom{};
+    if (nx < 3 || ny < 3 || nz < 3) return 0;
+    g->tiled = 1;
     g->by = std::min(kBrickBY, ny - 2);
     g->bz = std::min(kBrickBZ, nz - 2);
     double occ = (double)N / (double)box.ncell;
     if (occ < 1e-9) occ = 1e-9;
     const double tr = (double)(g->by * g->bz);
-    int W = (int)(0.9 * kBrickThreads / (tr * occ) + 0.5);
+    int W = (int)(std::min(target, 0.9 * kBrickThreads) / (tr * occ) + 0.5);
     W = std::min(W, (int)(0.88 * kBrickCap / ((g->by + 2) * (g->bz + 2) * occ)) - 2);
     W = std::min(W, (int)(0.87 * kBrickFCap / (tr * 27.0 * occ)));
     W = std::min(std::min(W, kBrickMW), nx - 2);
@@ -1508,8 +1515,8 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     near_geometry(a.box, a.N, &tiled, &W, &tiles_x, &nb);
     if (prec == 1 && tiled) {
         set_tile_smem_attr();
-        BrickGeom g;
-        nb = brick_geometry(a.box, a.N, &g);
+        NearBatchGeom g;
+        nb = near_bricks(a.box, a.N, kNearBrickTarget, &g);
         k_near_bricks<<<dim3(g.tiles_x, g.tiles_y, g.tiles_z), kBrickThreads, sizeof(BrickSmemSingle), st>>>(
             a, near_f32_consts(a.nc), g);
         return (int)nb * (kBrickThreads / 32);
@@ -1525,10 +1532,10 @@ int launch_near(int prec, const NearArgs &a, cudaStream_t st) {
     return (int)nb * kWarpsPerBlock;
 }
 
-void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
-                       uint32_t nblocks, cudaStream_t st) {
+void launch_near_batch(const NearArgs *args, const NearF *nf, const NearBatchGeom *geom, const uint32_t *items,
+                       int R, uint32_t nblocks, cudaStream_t st) {
     set_tile_smem_attr();
-    k_near_batch<<<nblocks, kNearBatchThreads, sizeof(TileSmem<kNearCapBatch, kNearBatchThreads, kNearMaxWBatch, true>), st>>>(args, geom, items, R);
+    k_near_batch<<<nblocks, kBrickThreads, sizeof(BrickSmemSingle), st>>>(args, nf, geom, items, R);
 }
 
 }  // namespace rbsog

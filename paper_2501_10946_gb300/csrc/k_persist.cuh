@@ -7,8 +7,8 @@
 //   1  sample (every system's P modes) and bin (integrator first half, cells)
 //   2  per-tile cell counts          3  scan -> cell_start
 //   4  scatter of the sort keys      5  gather into the cell order
-//   6  near field (two 128-thread tiles per CTA side by side) then the structure factor,
-//      both from work counters that CTAs take items from as they finish
+//   6  near field (one brick per CTA at a time) then the structure factor, both from work
+//      counters that CTAs take items from as they finish
 //   7  rho_final                      8  far gather + closing half kick
 //   9  close (step counters, forces-valid flags)
 // Each work item of a phase is a (system, local block) of the batched kernels, found
@@ -22,12 +22,11 @@ namespace rbsog {
 namespace {
 
 constexpr int kPersistThreads = 256;
-constexpr int kPersistNearThreads = kPersistNearThreadsHost;    // threads of one near-field tile (two per CTA)
-using PersistTile = TileSmem<kNearCapBatch, kPersistNearThreads, kNearMaxWBatch, true>;
+static_assert(kPersistThreads == kNearBrickThreads, "one near-field brick per CTA");
 
 struct PersistSmem {
     union {
-        PersistTile near[2];
+        BrickSmemSingle brick;
         uint4 rho_sp[kRhoTile];
         double2 rf_sh[8][32];
         struct {
@@ -77,26 +76,6 @@ __device__ __forceinline__ bool grid_barrier(GridBar *b, long long limit, bool r
     return S.ok != 0;
 }
 
-template <int HALF>
-__device__ __forceinline__ void persist_near_items(const PersistArgs &a, PersistSmem &S, int htid) {
-    while (true) {
-        if (htid == 0) S.item[HALF] = atomicAdd(&a.bar->q_near, 1u);
-        group_sync<kPersistNearThreads, 1 + HALF>();
-        const unsigned vb = S.item[HALF];
-        group_sync<kPersistNearThreads, 1 + HALF>();
-        if (vb >= a.nb_near) break;
-        const int r = item_system(a.it_near, a.R, vb);
-        const NearArgs &na = a.near[r];
-        const NearBatchGeom g = a.geom[r];
-        const unsigned blk = vb - a.it_near[r];
-        if (g.tiled)
-            near_tile_body<kNearCapBatch, kPersistNearThreads, kNearMaxWBatch, false, true, 1 + HALF>(
-                na, g.W, g.tiles_x, blk, S.u.near[HALF], htid);
-        else
-            near_global_block<1>(na, (uint32_t)g.W, blk, htid, kPersistNearThreads);
-    }
-}
-
 __global__ void __launch_bounds__(kPersistThreads, 3) k_step_persist(PersistArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PersistSmem &S = *reinterpret_cast<PersistSmem *>(smem_raw);
@@ -133,8 +112,28 @@ __global__ void __launch_bounds__(kPersistThreads, 3) k_step_persist(PersistArgs
     for (uint32_t i = blockIdx.x * kPersistThreads + tid; i < a.N; i += G * kPersistThreads) gather_one<1>(a.gather, i);
     if (!grid_barrier(a.bar, lim, false, S)) return;
     // 6: near field, then the structure factor
-    if (tid < kPersistNearThreads) persist_near_items<0>(a, S, tid);
-    else persist_near_items<1>(a, S, tid - kPersistNearThreads);
+    while (true) {
+        if (tid == 0) S.item[0] = atomicAdd(&a.bar->q_near, 1u);
+        __syncthreads();
+        const unsigned vb = S.item[0];
+        __syncthreads();
+        if (vb >= a.nb_near) break;
+        const int r = item_system(a.it_near, a.R, vb);
+        const NearBatchGeom g = a.geom[r];
+        const unsigned blk = vb - a.it_near[r];
+        if (g.tiled) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&a.nearf[r]);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&S.u.brick.nf);
+            for (int i = tid; i < (int)(sizeof(NearF) / 4); i += kPersistThreads) dst[i] = src[i];
+            const int bx = (int)(blk % (unsigned)g.tiles_x);
+            const int rest = (int)(blk / (unsigned)g.tiles_x);
+            near_brick_body<kBrickCap, kBrickFCap, kBrickThreads, kBrickMW, kBrickBY, kBrickBZ, kBrickTmax,
+                            kBrickMaskWords, true>(a.near[r], S.u.brick.nf, g, bx, rest % g.tiles_y,
+                                                   rest / g.tiles_y, blk, S.u.brick, tid);
+        } else {
+            near_global_block<1>(a.near[r], (uint32_t)g.W, blk, tid, kPersistThreads);
+        }
+    }
     __syncthreads();
     while (true) {
         if (tid == 0) S.item[0] = atomicAdd(&a.bar->q_rho, 1u);

@@ -225,26 +225,44 @@ constexpr size_t kGTab32Bytes = 32;   // one FP32 gather-table entry (int4 + flo
 // concatenated buffers.
 void launch_bin_batch(const BinArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st);
 void launch_sample_batch(const SampleArgs *args, const uint32_t *items, int R, uint32_t nblocks, cudaStream_t st);
-struct NearBatchGeom {
-    int tiled;                 // 1: shared-memory tiles, 0: per-particle global path
-    int W, tiles_x;
+// FP32 pair constants of one system for the near-field bricks, each duplicated into both
+// halves of a 64-bit word for packed FP32x2 arithmetic (near_f32_consts builds them).
+struct alignas(16) NearF {
+    int mtot;
+    int two;                                // a second Yukawa term (EGS screening)
+    unsigned long long nl2;                 // -log2(e)/lambda
+    unsigned long long il2;                 // 1/lambda
+    unsigned long long ly1;                 // log2 of the first term's weight
+    unsigned long long nl2b, il2b, ly2, sg2;   // second term: -log2(e)/lambda_2, 1/lambda_2, log2|y2|, sign
+    unsigned long long nb[kMaxGauss];       // -b_m log2(e)
+    unsigned long long naf[kMaxGauss];      // -a_m (the energy's SOG sum is accumulated negated)
+    unsigned long long cf[kMaxGauss];       // c_m
 };
-// Staged particles per near-field CTA: one large system, and the batched kernel.
+NearF near_f32_consts(const NearConsts &c);
+// Near-field geometry of one system: bricks of W cells along x in each of by x bz rows
+// (tiles_x x tiles_y x tiles_z of them), or the per-particle path (tiled = 0: fewer than 3
+// cells on an axis; W then holds the system's first global record index in a batch).
+struct NearBatchGeom {
+    int tiled;
+    int W, tiles_x, tiles_y, tiles_z, by, bz;
+};
+constexpr int kNearBrickThreads = 256;      // threads per near-field brick (CTA)
+constexpr double kNearBrickTarget = 230.0;  // targets per brick aimed at by default
+// Bricks of one system aiming at `target` targets each (capped by the brick's buffers);
+// returns their number (0 when the box has fewer than 3 cells on an axis).
+uint32_t near_bricks(const Box &box, uint32_t N, double target, NearBatchGeom *g);
+// Row tiles of the FP64 build: staged particles per CTA and the widest tile in cells.
 constexpr int kNearCapSingle = 1280;
-constexpr int kNearMaxWSingle = 48;      // widest tile in cells
-constexpr int kNearCapBatch = 1024;
-constexpr int kNearBatchThreads = 96;     // threads per CTA of the batched near kernel
-constexpr int kNearBatchMinBlocks = 7;    // launch bound: CTAs per SM (80 registers; 8 fit)
-constexpr int kNearBatchWarps = kNearBatchThreads / 32;   // energy partials per CTA
-constexpr int kNearMaxWBatch = 16;
+constexpr int kNearMaxWSingle = 48;
 // target: particles per CTA the tile width aims at (capped by the staging buffer `cap`);
 // threads: threads per CTA of the per-particle path (boxes under 3 cells per axis);
 // max_w: widest tile in cells; full_rows: tiles may span a whole row of cells
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks,
                    double target = 110.0, int cap = kNearCapSingle, int threads = 128,
                    int max_w = kNearMaxWSingle, bool full_rows = false);
-void launch_near_batch(const NearArgs *args, const NearBatchGeom *geom, const uint32_t *items, int R,
-                       uint32_t nblocks, cudaStream_t st);
+// one brick (or per-particle block) per CTA of every system; nf: the systems' pair constants
+void launch_near_batch(const NearArgs *args, const NearF *nf, const NearBatchGeom *geom, const uint32_t *items,
+                       int R, uint32_t nblocks, cudaStream_t st);
 void launch_rho_batch(const RhoArgs *args, const int *chunk, const uint32_t *items, int R, uint32_t nblocks,
                       cudaStream_t st);
 void launch_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int R, uint32_t nblocks,
@@ -263,14 +281,13 @@ struct GridBar {
     int status;
     int pad[3];
 };
-constexpr int kPersistNearThreadsHost = 128;   // threads of one near-field tile in the persistent step
 struct PersistArgs {
     const BinArgs *bin; const uint32_t *it_bin; uint32_t nb_bin;
     const SampleArgs *sample; const uint32_t *it_sample; uint32_t nb_sample;   // 4-slot sample blocks
     uint32_t *count, *tile_sums, *cell_start; int ncell, ntiles; uint32_t N;
     const uint32_t *cell, *slot, *id; unsigned long long *keys;
     GatherArgs gather;
-    const NearArgs *near; const NearBatchGeom *geom; const uint32_t *it_near; uint32_t nb_near;
+    const NearArgs *near; const NearF *nearf; const NearBatchGeom *geom; const uint32_t *it_near; uint32_t nb_near;
     const RhoArgs *rho; const int *chunk; const uint32_t *it_rho; uint32_t nb_rho;
     const RhoFinalArgs *rf; const uint32_t *it_rf; uint32_t nb_rf;
     const FarArgs *far; const uint32_t *it_far; uint32_t nb_far;

@@ -83,19 +83,18 @@ int chunk_for(uint32_t N, int target) {
 }
 
 struct SysShape {
-    int tiled, W, tiles_x;
+    NearBatchGeom ng;          // near-field bricks (or the per-particle path)
     uint32_t near_blocks;
     int G;
 };
 
-// Threads of one near-field block: the batched kernel's CTA, or half a CTA of the
-// persistent step.
-int near_threads(const rbsog_batch *b) { return b->persistent ? kPersistNearThreadsHost : kNearBatchThreads; }
+// Threads of one near-field block: a brick of the batched kernel or of the persistent step.
+int near_threads(const rbsog_batch *) { return kNearBrickThreads; }
 
 SysShape shape_of(const HostSystem &h, double near_target, int chunk, int nthreads) {
     SysShape s{};
-    near_geometry(h.box, h.N, &s.tiled, &s.W, &s.tiles_x, &s.near_blocks, near_target, kNearCapBatch,
-                  nthreads, kNearMaxWBatch, true);
+    s.near_blocks = near_bricks(h.box, h.N, near_target, &s.ng);
+    if (!s.ng.tiled) s.near_blocks = (h.N + (uint32_t)nthreads - 1) / (uint32_t)nthreads;
     s.G = (int)((h.N + (uint32_t)chunk - 1) / (uint32_t)chunk);
     return s;
 }
@@ -115,6 +114,7 @@ int build_args(rbsog_batch *b) {
     }
     std::vector<SampleArgs> sa(R);
     std::vector<NearArgs> na(R);
+    std::vector<NearF> nfs(R);
     std::vector<NearBatchGeom> geom(R);
     std::vector<RhoArgs> ra(R);
     std::vector<RhoFinalArgs> rf(R);
@@ -178,7 +178,9 @@ int build_args(rbsog_batch *b) {
             a.coef_out = b->coef + mo;
         }
         // near field: global record and force indices, this system's cell range
-        geom[r] = NearBatchGeom{sh.tiled, sh.tiled ? sh.W : (int)po, sh.tiles_x};
+        geom[r] = sh.ng;
+        if (!sh.ng.tiled) geom[r].W = (int)po;
+        nfs[r] = near_f32_consts(h.nconsts);
         {
             NearArgs &a = na[r];
             a.nc = h.nconsts;
@@ -268,6 +270,7 @@ int build_args(rbsog_batch *b) {
     BCK(upload(b->d_energy[1], en[1]), "upload arguments");
     BCK(upload(b->d_sample, sa), "upload arguments");
     BCK(upload(b->d_near, na), "upload arguments");
+    BCK(upload(b->d_nearf, nfs), "upload arguments");
     BCK(upload(b->d_geom, geom), "upload arguments");
     BCK(upload(b->d_rho, ra), "upload arguments");
     BCK(upload(b->d_chunk, std::vector<int>(b->rho_chunk.begin(), b->rho_chunk.begin() + R)), "upload arguments");
@@ -435,7 +438,7 @@ int engine_alloc(rbsog_batch *b, const EngineCaps &caps, int device) {
         balloc(b, &b->ctr, R) || balloc(b, &b->d_bin[0], R) || balloc(b, &b->d_bin[1], R) ||
         balloc(b, &b->d_far[0], R) || balloc(b, &b->d_far[1], R) || balloc(b, &b->d_far_user, R) ||
         balloc(b, &b->d_energy[0], R) || balloc(b, &b->d_energy[1], R) || balloc(b, &b->d_sample, R) ||
-        balloc(b, &b->d_near, R) || balloc(b, &b->d_geom, R) || balloc(b, &b->d_rho, R) ||
+        balloc(b, &b->d_near, R) || balloc(b, &b->d_nearf, R) || balloc(b, &b->d_geom, R) || balloc(b, &b->d_rho, R) ||
         balloc(b, &b->d_chunk, R) || balloc(b, &b->d_rf, R) || balloc(b, &b->d_state, R) ||
         balloc(b, &b->d_items, 6 * (R + 1)) || balloc(b, &b->d_coff, R + 1) || balloc(b, &b->d_off2, 2 * (R + 1)) ||
         balloc(b, &b->d_sub_items, R + 1) || balloc(b, &b->bar, 1))
@@ -671,7 +674,7 @@ int enqueue_persistent(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *
     GatherArgs &g = a.gather;
     g.in = b->work; g.out = b->rest; g.keys = b->keys; g.cell = b->cell; g.cell_start = b->cell_start; g.ctr = b->ctr;
     g.c_off = b->d_coff; g.R = R; g.rec_w = b->rec_w; g.rec = b->rec; g.N = b->Ntot;
-    a.near = b->d_near; a.geom = b->d_geom; a.it_near = items_of(b, kItNear); a.nb_near = b->nb[kItNear];
+    a.near = b->d_near; a.nearf = b->d_nearf; a.geom = b->d_geom; a.it_near = items_of(b, kItNear); a.nb_near = b->nb[kItNear];
     a.rho = b->d_rho; a.chunk = b->d_chunk; a.it_rho = items_of(b, kItRho); a.nb_rho = b->nb[kItRho];
     a.rf = b->d_rf; a.it_rf = items_of(b, kItRhoFinal); a.nb_rf = b->nb[kItRhoFinal];
     a.far = far ? far : b->d_far[set]; a.it_far = items_of(b, kItFar); a.nb_far = b->nb[kItFar];
@@ -725,7 +728,7 @@ int engine_enqueue(rbsog_batch *b, cudaStream_t st, int set, const FarArgs *far,
     mark(4);
     if (!fork) launch_sample_batch(b->d_sample, items_of(b, kItSample), R, b->nb[kItSample], st);
     mark(5);
-    launch_near_batch(b->d_near, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
+    launch_near_batch(b->d_near, b->d_nearf, b->d_geom, items_of(b, kItNear), R, b->nb[kItNear], st);
     mark(6);
     if (fork) {
         BCK(cudaEventRecord(b->ev_join, sr), "join the structure-factor stream");
@@ -1021,7 +1024,7 @@ int rbsog_batch_tune(rbsog_batch *b, int32_t reps, double *near_target, int32_t 
     BCK(cudaStreamSynchronize(st), "synchronize");
     std::vector<DevCounters> saved;
     if (int code = engine_counters(b, &saved)) return code;
-    const double near_c[] = {48.0, 64.0, 96.0, 128.0};
+    const double near_c[] = {128.0, 160.0, 192.0, 230.0};
     const int rho_c[] = {256, 512, 1024, 2048};
     double best_near = b->near_target, best_near_ms = 1e30;
     int best_rho = b->rho_target;

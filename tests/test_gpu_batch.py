@@ -213,7 +213,7 @@ def test_tuner_leaves_no_trace_in_the_trajectory():
         ra = np.zeros((b.Ntot, 3))
         R.rbsog_batch_get_state(b.h, ra)
         m_a, _ = R.rbsog_batch_get_ksample(b.h, b.Ptot)
-    assert near_t in (48.0, 64.0, 96.0, 128.0) and rho_t in (256, 512, 1024, 2048)
+    assert near_t in (128.0, 160.0, 192.0, 230.0) and rho_t in (256, 512, 1024, 2048)
     with Batch(ws) as b:
         R.rbsog_batch_set_shapes(b.h, near_t, rho_t)
         R.rbsog_batch_set_state(b.h, r, v)
@@ -231,7 +231,7 @@ def test_near_shape_changes_no_force():
     r, _ = state(ws)
     modes = np.concatenate([modes_for(w, w.P, 400 + i) for i, w in enumerate(ws)])
     Fs, Us = [], []
-    for near_t in (48.0, 160.0):
+    for near_t in (64.0, 230.0):
         with Batch(ws) as b:
             R.rbsog_batch_set_shapes(b.h, near_t, 512)
             R.rbsog_batch_set_state(b.h, r)
