@@ -5,12 +5,13 @@
 // 27-cell neighbourhood of their target cells with TMA bulk copies completing on one
 // mbarrier, pre-filtering candidates in FP32 with ballot masks, and evaluating the exact
 // pairs two per pass in packed FP32x2 (FP64 in the FP64 build):
+//   * bricks (near_brick_body): a run of W cells in each of by x bz rows, (by + 2)(bz + 2)
+//     neighbour rows staged, about 4.5 staged particles per target, which leaves room for
+//     precomputed FP32 offsets; the FP32 build uses them for one system (k_near_bricks), a
+//     batch of systems (k_near_batch) and the persistent batched step;
 //   * row tiles (near_tile_body): a run of W cells in one (y, z) row, its 9 neighbour rows
-//     staged; the batched kernels, the persistent step and the FP64 build use them;
-//   * bricks (near_brick_body, k_near_bricks): a run of W cells in each of by x bz rows,
-//     (by + 2)(bz + 2) neighbour rows staged, about 4 staged particles per target instead
-//     of 10, which leaves room for precomputed FP32 offsets; one large FP32 system uses
-//     them.  The layout of each is described above its body.
+//     staged; the FP64 build uses them (k_near_tiled64).
+// The layout of each is described above its body.
 // In both, the pairs of a target are those of a plain loop over the 27 cells in its order;
 // which two share a pass follows the pre-filter's hits, so the pre-filter changes the
 // rounding of the sums, never the set of pairs.
@@ -310,10 +311,10 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
 //       test and accumulates the pair forces: the two of a pass added in FP32, then one
 //       compensated FP32 add (FP64 build: plain FP64 sums, one pair at a time).
 // Neighbourhoods larger than 8 slots (256 candidates) run in several such rounds.
-// CAP: staged particles per CTA; NT: threads per CTA (batches of many, mostly small,
-// systems stage 1024 with 96).  FR: tiles may span a whole row of cells (a third staging
-// slice per row).  F64: the FP64 build's 32-byte records (u64 coordinates), else the FP32
-// build's 16-byte ones.
+// CAP: staged particles per CTA; NT: threads per CTA.  FR: tiles may span a whole row of
+// cells (a third staging slice per row).  BAR: the barrier of a group of NT threads that
+// shares a CTA with others.  F64: the FP64 build's 32-byte records (u64 coordinates), else
+// the FP32 build's 16-byte ones.
 template <bool F64>
 struct TileRec;
 template <>
