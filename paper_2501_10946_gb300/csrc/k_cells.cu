@@ -106,26 +106,55 @@ __device__ __forceinline__ void noise_words(const BinArgs &a, uint32_t id, U4 &w
     w1 = philox10(id, 0x40000001u, (uint32_t)n, (uint32_t)(n >> 32), k0, k1);
 }
 
-// Returns the particle's kinetic energy m |v|^2 / 2 after the update when a.K_part is set
-// (else 0).
+// The inputs of one particle's update, all loaded before any of it is computed
+struct BinIn {
+    double r[3], v[3], invm, q;
+    uint32_t id;
+    int integrate;
+    float f32[3];
+    double f64[3];
+};
+
 template <int PREC>
-__device__ __forceinline__ double bin_body(const BinArgs &a, uint32_t k) {
+__device__ __forceinline__ void bin_load(const BinArgs &a, uint32_t k, BinIn &b) {
     const uint32_t N = a.stride;
-    double r[3] = {a.in.rx[k], a.in.ry[k], a.in.rz[k]};
-    double v[3] = {a.in.vx[k], a.in.vy[k], a.in.vz[k]};
-    const double invm = a.in.invm[k];
-    const uint32_t id = a.in.id[k];
+    b.r[0] = a.in.rx[k]; b.r[1] = a.in.ry[k]; b.r[2] = a.in.rz[k];
+    b.v[0] = a.in.vx[k]; b.v[1] = a.in.vy[k]; b.v[2] = a.in.vz[k];
+    b.invm = a.in.invm[k];
+    b.q = a.in.q[k];
+    b.id = a.in.id[k];
     // a system whose forces were never evaluated (fvalid = 0) only rebuilds its cells
-    const int integrate = a.ctr->fvalid ? a.integrate : 0;
+    b.integrate = a.ctr->fvalid ? a.integrate : 0;
+    if (b.integrate) {
+        if (PREC == 1) {
+            const float *Ff = (const float *)a.F;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) b.f32[d] = Ff[(size_t)d * N + k];
+        } else {
+            const double *Fd = (const double *)a.F;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) b.f64[d] = Fd[(size_t)d * N + k];
+        }
+    }
+}
+
+// The update of particle k: returns its cell and sets ke to its kinetic energy
+// m |v|^2 / 2 after the update when a.K_part is set (else 0).
+template <int PREC>
+__device__ __forceinline__ uint32_t bin_update(const BinArgs &a, uint32_t k, const BinIn &b, double &ke) {
+    double r[3] = {b.r[0], b.r[1], b.r[2]};
+    double v[3] = {b.v[0], b.v[1], b.v[2]};
+    const double invm = b.invm;
+    const uint32_t id = b.id;
+    const int integrate = b.integrate;
     if (PREC == 1 && integrate) {
         // FP32 build: kick, drift increments and the O step in FP32 (the forces carry FP32
         // errors already); the positions add those increments in FP64.
-        const float *Ff = (const float *)a.F;
         const float im = d2f_int(invm);
         float vf[3] = {d2f_int(v[0]), d2f_int(v[1]), d2f_int(v[2])};
         const float hk = a.hdt_f * im;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) vf[d] = fmaf(hk, Ff[(size_t)d * N + k], vf[d]);
+        for (int d = 0; d < 3; ++d) vf[d] = fmaf(hk, b.f32[d], vf[d]);
         float dr[3];
         if (integrate == 1) {
 #pragma unroll
@@ -156,8 +185,7 @@ __device__ __forceinline__ double bin_body(const BinArgs &a, uint32_t k) {
         }
     } else if (integrate) {
         // FP64 build
-        const double *Fd = (const double *)a.F;
-        const double F[3] = {Fd[k], Fd[N + k], Fd[2 * (size_t)N + k]};
+        const double F[3] = {b.f64[0], b.f64[1], b.f64[2]};
         const double hk = 0.5 * a.dt * invm;
 #pragma unroll
         for (int d = 0; d < 3; ++d) v[d] += hk * F[d];
@@ -212,7 +240,7 @@ __device__ __forceinline__ double bin_body(const BinArgs &a, uint32_t k) {
     a.out.rx[k] = r[0]; a.out.ry[k] = r[1]; a.out.rz[k] = r[2];
     a.out.vx[k] = v[0]; a.out.vy[k] = v[1]; a.out.vz[k] = v[2];
     a.out.invm[k] = invm;
-    const double q = a.in.q[k];
+    const double q = b.q;
     a.out.q[k] = q;
     // the particle record, at this position for the gather (which moves it into the cell
     // order) and at the particle's id for the structure factor: the order of the rho sums
@@ -229,10 +257,39 @@ __device__ __forceinline__ double bin_body(const BinArgs &a, uint32_t k) {
         ((Rec64 *)a.rec_id)[id] = rw;
     }
     a.out.id[k] = id;
-    uint32_t c = a.cell_base + cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);
+    ke = a.K_part ? 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm : 0.0;
+    return a.cell_base + cc[0] + (uint32_t)a.box.nc[0] * (cc[1] + (uint32_t)a.box.nc[1] * cc[2]);
+}
+
+// One particle: update, then its slot in the cell from the cell's counter.  Returns the
+// kinetic energy (0 unless a.K_part is set).
+template <int PREC>
+__device__ __forceinline__ double bin_body(const BinArgs &a, uint32_t k) {
+    BinIn b;
+    bin_load<PREC>(a, k, b);
+    double ke;
+    const uint32_t c = bin_update<PREC>(a, k, b, ke);
     a.cell[k] = c;
     a.slot[k] = atomicAdd(&a.count[c], 1u);
-    return a.K_part ? 0.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / invm : 0.0;
+    return ke;
+}
+
+// Two FP32-build particles (of one system or two) in one thread, for a grid that runs few
+// threads per SM: both loads before either update, both counter increments before either
+// slot store.
+__device__ __forceinline__ void bin_two(const BinArgs &a0, uint32_t k0, const BinArgs &a1, uint32_t k1) {
+    BinIn b0, b1;
+    bin_load<1>(a0, k0, b0);
+    bin_load<1>(a1, k1, b1);
+    double ke;
+    const uint32_t c0 = bin_update<1>(a0, k0, b0, ke);
+    const uint32_t c1 = bin_update<1>(a1, k1, b1, ke);
+    const uint32_t s0 = atomicAdd(&a0.count[c0], 1u);
+    const uint32_t s1 = atomicAdd(&a1.count[c1], 1u);
+    a0.cell[k0] = c0;
+    a0.slot[k0] = s0;
+    a1.cell[k1] = c1;
+    a1.slot[k1] = s1;
 }
 
 template <int PREC>
@@ -422,28 +479,101 @@ __global__ void __launch_bounds__(256) k_scatter(const uint32_t *cell, const uin
 // so the ranks of a cell are a permutation of 0 .. n-1: particles in ascending id order,
 // as a stable sort by id would leave them.  A cell above kMaxCellOcc keeps the scatter
 // order and sets kErrCellOverflow (in the counter of the system that owns the cell when
-// c_off is given).
+// c_off is given).  The particle's state and record are loaded as soon as src is known,
+// so their loads overlap the cell lookups and the rank count.
+template <int PREC> struct RecOf { using T = uint4; };
+template <> struct RecOf<0> { using T = Rec64; };
+
+template <int PREC>
+struct GatherVals {
+    double rx, ry, rz, vx, vy, vz, invm, q;
+    uint32_t id;
+    typename RecOf<PREC>::T rec;
+};
+
+template <int PREC>
+__device__ __forceinline__ void gather_load(const GatherArgs &g, uint32_t src, GatherVals<PREC> &v) {
+    v.rx = g.in.rx[src]; v.ry = g.in.ry[src]; v.rz = g.in.rz[src];
+    v.vx = g.in.vx[src]; v.vy = g.in.vy[src]; v.vz = g.in.vz[src];
+    v.invm = g.in.invm[src];
+    v.q = g.in.q[src];
+    v.id = g.in.id[src];
+    v.rec = ((const typename RecOf<PREC>::T *)g.rec_w)[src];
+}
+
+template <int PREC>
+__device__ __forceinline__ void gather_store(const GatherArgs &g, uint32_t p, const GatherVals<PREC> &v) {
+    g.out.rx[p] = v.rx; g.out.ry[p] = v.ry; g.out.rz[p] = v.rz;
+    g.out.vx[p] = v.vx; g.out.vy[p] = v.vy; g.out.vz[p] = v.vz;
+    g.out.invm[p] = v.invm;
+    g.out.q[p] = v.q;
+    g.out.id[p] = v.id;
+    ((typename RecOf<PREC>::T *)g.rec)[p] = v.rec;
+}
+
+// keys[j] < key for j = t0 .. t0 + 3 inside [lo, hi) (a key past hi counts as none)
+__device__ __forceinline__ uint32_t count_below4(const unsigned long long *keys, uint32_t j, uint32_t hi,
+                                                 unsigned long long key) {
+    const unsigned long long k0 = j < hi ? keys[j] : ~0ull;
+    const unsigned long long k1 = j + 1 < hi ? keys[j + 1] : ~0ull;
+    const unsigned long long k2 = j + 2 < hi ? keys[j + 2] : ~0ull;
+    const unsigned long long k3 = j + 3 < hi ? keys[j + 3] : ~0ull;
+    return (uint32_t)(k0 < key) + (uint32_t)(k1 < key) + (uint32_t)(k2 < key) + (uint32_t)(k3 < key);
+}
+
+// Place of key i in the new order (i itself for an overflowing cell)
+__device__ __forceinline__ uint32_t gather_place(const GatherArgs &g, uint32_t i, unsigned long long key,
+                                                 uint32_t c, uint32_t lo, uint32_t hi) {
+    if (hi - lo <= (uint32_t)kMaxCellOcc) {
+        uint32_t p = lo;
+        for (uint32_t j = lo; j < hi; j += 4) p += count_below4(g.keys, j, hi, key);
+        return p;
+    }
+    if (i == lo) {
+        const int r = g.c_off ? item_system(g.c_off, g.R, c) : 0;
+        atomicOr(&g.ctr[r].err, kErrCellOverflow);
+    }
+    return i;
+}
+
 template <int PREC>
 __device__ __forceinline__ void gather_one(const GatherArgs &g, uint32_t i) {
     const unsigned long long key = g.keys[i];
     const uint32_t src = (uint32_t)key;
     const uint32_t c = g.cell[src];
+    GatherVals<PREC> v;
+    gather_load<PREC>(g, src, v);
     const uint32_t lo = g.cell_start[c], hi = g.cell_start[c + 1];
-    uint32_t p = i;
-    if (hi - lo <= (uint32_t)kMaxCellOcc) {
-        p = lo;
-        for (uint32_t j = lo; j < hi; ++j) p += g.keys[j] < key ? 1u : 0u;
-    } else if (i == lo) {
-        const int r = g.c_off ? item_system(g.c_off, g.R, c) : 0;
-        atomicOr(&g.ctr[r].err, kErrCellOverflow);
+    gather_store<PREC>(g, gather_place(g, i, key, c, lo, hi), v);
+}
+
+// Keys i0 and i1 (FP32 records) in one thread, each lookup of the two in flight together:
+// for a grid that runs few threads per SM.
+__device__ __forceinline__ void gather_two(const GatherArgs &g, uint32_t i0, uint32_t i1) {
+    const unsigned long long key0 = g.keys[i0], key1 = g.keys[i1];
+    const uint32_t src0 = (uint32_t)key0, src1 = (uint32_t)key1;
+    const uint32_t c0 = g.cell[src0], c1 = g.cell[src1];
+    GatherVals<1> v0, v1;
+    gather_load<1>(g, src0, v0);
+    gather_load<1>(g, src1, v1);
+    const uint32_t lo0 = g.cell_start[c0], hi0 = g.cell_start[c0 + 1];
+    const uint32_t lo1 = g.cell_start[c1], hi1 = g.cell_start[c1 + 1];
+    uint32_t p0 = i0, p1 = i1;
+    const bool r0 = hi0 - lo0 <= (uint32_t)kMaxCellOcc, r1 = hi1 - lo1 <= (uint32_t)kMaxCellOcc;
+    if (r0 && r1) {
+        p0 = lo0;
+        p1 = lo1;
+        const uint32_t n = max(hi0 - lo0, hi1 - lo1);
+        for (uint32_t t = 0; t < n; t += 4) {
+            p0 += count_below4(g.keys, lo0 + t, hi0, key0);
+            p1 += count_below4(g.keys, lo1 + t, hi1, key1);
+        }
+    } else {
+        p0 = gather_place(g, i0, key0, c0, lo0, hi0);
+        p1 = gather_place(g, i1, key1, c1, lo1, hi1);
     }
-    g.out.rx[p] = g.in.rx[src]; g.out.ry[p] = g.in.ry[src]; g.out.rz[p] = g.in.rz[src];
-    g.out.vx[p] = g.in.vx[src]; g.out.vy[p] = g.in.vy[src]; g.out.vz[p] = g.in.vz[src];
-    g.out.invm[p] = g.in.invm[src];
-    g.out.q[p] = g.in.q[src];
-    g.out.id[p] = g.in.id[src];
-    if (PREC == 1) ((uint4 *)g.rec)[p] = ((const uint4 *)g.rec_w)[src];
-    else ((Rec64 *)g.rec)[p] = ((const Rec64 *)g.rec_w)[src];
+    gather_store<1>(g, p0, v0);
+    gather_store<1>(g, p1, v1);
 }
 
 template <int PREC>

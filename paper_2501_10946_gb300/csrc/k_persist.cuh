@@ -91,11 +91,24 @@ __global__ void __launch_bounds__(kPersistThreads, 3) k_step_persist(PersistArgs
             const int l = (int)(vb - a.it_sample[r]) * 4 + w;
             if (l < sa.P) sample_warp(sa, l);
         }
-        for (unsigned vb = blockIdx.x; vb < a.nb_bin; vb += G) {
-            const int r = item_system(a.it_bin, a.R, vb);
-            const BinArgs &ba = a.bin[r];
-            const uint32_t k = (vb - a.it_bin[r]) * kPersistThreads + tid;
-            if (k < ba.N) bin_body<1>(ba, k);
+        // items vb and vb + G together (two particles per thread: this grid runs 768
+        // threads per SM, so each thread keeps two sets of loads in flight)
+        for (unsigned vb = blockIdx.x; vb < a.nb_bin; vb += 2 * G) {
+            const int r0 = item_system(a.it_bin, a.R, vb);
+            const BinArgs &b0 = a.bin[r0];
+            const uint32_t k0 = (vb - a.it_bin[r0]) * kPersistThreads + tid;
+            const bool v0 = k0 < b0.N;
+            bool v1 = false;
+            uint32_t k1 = 0;
+            int r1 = r0;
+            if (vb + G < a.nb_bin) {
+                r1 = item_system(a.it_bin, a.R, vb + G);
+                k1 = (vb + G - a.it_bin[r1]) * kPersistThreads + tid;
+                v1 = k1 < a.bin[r1].N;
+            }
+            if (v0 && v1) bin_two(b0, k0, a.bin[r1], k1);
+            else if (v0) bin_body<1>(b0, k0);
+            else if (v1) bin_body<1>(a.bin[r1], k1);
         }
     }
     if (!grid_barrier(a.bar, lim, false, S)) return;
@@ -109,7 +122,13 @@ __global__ void __launch_bounds__(kPersistThreads, 3) k_step_persist(PersistArgs
     for (uint32_t k = blockIdx.x * kPersistThreads + tid; k < a.N; k += G * kPersistThreads)
         scatter_one(a.cell, a.slot, a.cell_start, a.id, a.keys, k);
     if (!grid_barrier(a.bar, lim, true, S)) return;
-    for (uint32_t i = blockIdx.x * kPersistThreads + tid; i < a.N; i += G * kPersistThreads) gather_one<1>(a.gather, i);
+    {
+        const uint32_t stride = G * kPersistThreads;
+        for (uint32_t i = blockIdx.x * kPersistThreads + tid; i < a.N; i += 2 * stride) {
+            if (i + stride < a.N) gather_two(a.gather, i, i + stride);
+            else gather_one<1>(a.gather, i);
+        }
+    }
     if (!grid_barrier(a.bar, lim, false, S)) return;
     // 6: near field, then the structure factor
     while (true) {

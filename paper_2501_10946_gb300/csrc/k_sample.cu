@@ -87,6 +87,27 @@ __device__ __forceinline__ double At_of(const SampleArgs &a, double A, double k2
     return a.y.n == 1 ? __dmul_rn(A, __dadd_rn(k2, a.y.inv_lam2[0])) : __ddiv_rn(A, psi_of(a.y, k2));
 }
 
+// FP32 pre-test of the acceptance test u (A t + Q2a) < A t, A t = A (k^2 + lambda^-2).
+// With D = A t - u (A t + Q2a) in real arithmetic on the FP64 operands, the FP64 test
+// accepts when D > 2^-52 (A t + Q2a) and rejects when D < -2^-52 (A t + Q2a) (two
+// roundings of the product).  The FP32 value D32 = fma(-u32, den, At32) differs from D by
+// at most 2e-6 (A t + Q2a): 2 pi / L, lambda^-2, Q2a and A each rounded to FP32 (2^-24
+// relative), k^2 in three roundings, A t in two more, den = At32 + Q2a32 in one, u
+// truncated to its leading 24 bits (u - u32 in [0, 2^-24)) and the fused product and
+// difference in one, with every operand normal (the range checks here and in
+// sample_set_prefilter).  So |D32| > 1e-5 den decides as the FP64 test does; the rest
+// (about 2e-5 of the draws) take the FP64 test.  Returns 1 accept, 0 reject, -1 open.
+__device__ __forceinline__ int accept_pretest(const SampleArgs &a, float Af, const int n[3], U4 wa) {
+    const float u32 = (float)(((wa.x >> 11) << 3) | (wa.y >> 29)) * 5.9604644775390625e-8f;
+    const float kx = a.tplf[0] * (float)n[0], ky = a.tplf[1] * (float)n[1], kz = a.tplf[2] * (float)n[2];
+    const float k2 = fmaf(kz, kz, fmaf(ky, ky, kx * kx));
+    const float At = Af * (k2 + a.il2f);
+    const float den = At + a.Q2af;
+    if (!(At >= 1e-25f && den <= 1e30f)) return -1;
+    const float D = fmaf(-u32, den, At), m = 1e-5f * den;
+    return D > m ? 1 : (D < -m ? 0 : -1);
+}
+
 // One slot l per warp: lane j tries attempt att0 + j, so 32 consecutive attempts run at
 // once and the slot takes the accepted attempt with the smallest index, exactly the draw
 // a sequential loop over attempts returns (the random words depend only on the counter).
@@ -94,6 +115,8 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
     const int lane = threadIdx.x & 31;
     const double A = a.temp ? a.temp[0] : a.A;
     const double S = a.temp ? a.temp[1] : a.S;
+    const bool pre = a.f32pre && A >= 1e-30 && A <= 1e30;
+    const float Af = (float)A;
     int m[3] = {1, 0, 0};
     if (a.ctr->inject) {
         m[0] = a.inject_m[3 * l]; m[1] = a.inject_m[3 * l + 1]; m[2] = a.inject_m[3 * l + 2];
@@ -116,11 +139,16 @@ __device__ __forceinline__ void sample_warp(const SampleArgs &a, int l) {
             bool ok = !(n[0] == 0 && n[1] == 0 && n[2] == 0);
             if (ok && (a.measure == 0 || a.measure == 3)) {
                 U4 wa = philox10((uint32_t)l, cb + 4u, d0, d1, k0, k1);
-                double u = u53_of(wa.x, wa.y);
-                // u < A / (A + Q2 psi), evaluated without division as u (A t + Q2) < A t
-                // with t = 1/psi = k^2 + lambda^-2 for one Yukawa term
-                const double At = At_of(a, A, k2_rn(a, n));
-                ok = __dmul_rn(u, __dadd_rn(At, a.Q2a)) < At;
+                const int t = pre ? accept_pretest(a, Af, n, wa) : -1;
+                if (t >= 0) {
+                    ok = t != 0;
+                } else {
+                    double u = u53_of(wa.x, wa.y);
+                    // u < A / (A + Q2 psi), evaluated without division as u (A t + Q2) < A t
+                    // with t = 1/psi = k^2 + lambda^-2 for one Yukawa term
+                    const double At = At_of(a, A, k2_rn(a, n));
+                    ok = __dmul_rn(u, __dadd_rn(At, a.Q2a)) < At;
+                }
             }
             const unsigned acc = __ballot_sync(0xffffffffu, ok);
             if (acc) {
@@ -313,6 +341,22 @@ __global__ void __launch_bounds__(256) k_S(SArgs a, double *partials) {
 }
 
 }  // namespace
+
+// The FP32 pre-test needs calF of Eq. 62 with one Yukawa term and FP32 copies of 2 pi / L,
+// lambda^-2 and Q2a that are normal (or zero) and far from the FP32 overflow, so that
+// every rounding in it is relative; A is checked on the device (it may be the
+// instantaneous temperature's).
+void sample_set_prefilter(SampleArgs *a) {
+    auto normal = [](double x) { return x >= 1e-30 && x <= 1e30; };
+    bool ok = (a->measure == 0 || a->measure == 3) && a->y.n == 1 && a->nfh == 0;
+    for (int d = 0; d < 3; ++d) ok = ok && a->tpl[d] >= 1e-15 && a->tpl[d] <= 1e15;
+    const double il2 = a->y.inv_lam2[0];
+    ok = ok && (il2 == 0.0 || normal(il2)) && (a->Q2a == 0.0 || normal(a->Q2a));
+    a->f32pre = ok ? 1 : 0;
+    for (int d = 0; d < 3; ++d) a->tplf[d] = (float)a->tpl[d];
+    a->il2f = (float)il2;
+    a->Q2af = (float)a->Q2a;
+}
 
 void launch_sample(const SampleArgs &a, cudaStream_t st) {
     k_sample<<<(a.P + kSampleWarps - 1) / kSampleWarps, 128, 0, st>>>(a);

@@ -103,7 +103,13 @@ struct SampleArgs {
     double *coef_out;         // [P]
     const double *temp;       // nullptr, or {k_B T V, S} of this evaluation at the instantaneous
                               // temperature (launch_temperature), which replace A and S
+    // FP32 pre-test of the acceptance test (calF of Eq. 62 with one Yukawa term): FP32
+    // copies of 2 pi / L, lambda^-2 and Q2a, and whether their ranges allow it
+    // (sample_set_prefilter); the FP64 test still decides every draw the pre-test leaves open
+    float tplf[3], il2f, Q2af;
+    int f32pre;
 };
+void sample_set_prefilter(SampleArgs *a);
 void launch_sample(const SampleArgs &a, cudaStream_t st);
 // Metropolis-Hastings chains (one per batch slot): state m and proposals made t (t = 0: the
 // chain has not started)

@@ -546,6 +546,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     fill_signed_fhat(c->y, c->sA, c->sb, &sa);
     sa.measure = c->p.sampling;
     sa.Q2a = c->p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * kPi) * c->Q2 : c->Q2;
+    sample_set_prefilter(&sa);
     sa.ctr = c->ctr; sa.inject_m = c->inject_m; sa.m_out = c->modes; sa.coef_out = c->coef;
     sa.temp = c->instT ? c->temp_out : nullptr;
     TempArgs ta{};

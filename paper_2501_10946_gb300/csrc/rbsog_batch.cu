@@ -172,6 +172,7 @@ int build_args(rbsog_batch *b) {
             a.V = h.V;
             a.measure = h.p.sampling;
             a.Q2a = h.p.sampling == RBSOG_SAMPLING_DEBYE ? (4.0 * 3.14159265358979323846) * h.Q2 : h.Q2;
+            sample_set_prefilter(&a);
             a.ctr = ctr;
             a.inject_m = b->inject_m + 3 * mo;
             a.m_out = b->modes + 3 * mo;
