@@ -204,6 +204,28 @@ struct GTab64 {
     double re, im;
 };
 
+// rho, the U*_F term and the gather-table entry of mode l from its summed rho
+template <int PREC>
+__device__ __forceinline__ void rho_final_write(const RhoFinalArgs &a, int l, double re, double im) {
+    a.rho[l] = make_double2(re, im);
+    const double coef = a.coef[l];
+    a.Ufar[l] = 0.5 * coef * (re * re + im * im);
+    const int mx = a.m[3 * l], my = a.m[3 * l + 1], mz = a.m[3 * l + 2];
+    const double kx = a.tpl[0] * mx, ky = a.tpl[1] * my, kz = a.tpl[2] * mz;
+    if (PREC == 1) {
+        GTab32 t;
+        t.m = make_int4(mx, my, mz, __float_as_int((float)im));
+        t.f = make_float4((float)(coef * kx), (float)(coef * ky), (float)(coef * kz), (float)re);
+        ((GTab32 *)a.gtab)[l] = t;
+    } else {
+        GTab64 t;
+        t.m = make_int4(mx, my, mz, 0);
+        t.ck[0] = coef * kx; t.ck[1] = coef * ky; t.ck[2] = coef * kz;
+        t.re = re; t.im = im;
+        ((GTab64 *)a.gtab)[l] = t;
+    }
+}
+
 // Block b sums modes 32b .. 32b+31: warp w adds the partials of blocks w, w+8, ... in
 // order, then warp 0 adds the 8 warp sums in order (fixed, deterministic).  Writes rho,
 // the gather table and u_l = coef_l |rho_l|^2 / 2 (summed by k_energy).
@@ -247,23 +269,7 @@ __device__ __forceinline__ void rho_final_body(const RhoFinalArgs &a, int ML, un
             re += sh[w][lane].x;
             im += sh[w][lane].y;
         }
-        a.rho[l] = make_double2(re, im);
-        const double coef = a.coef[l];
-        a.Ufar[l] = 0.5 * coef * (re * re + im * im);
-        const int mx = a.m[3 * l], my = a.m[3 * l + 1], mz = a.m[3 * l + 2];
-        const double kx = a.tpl[0] * mx, ky = a.tpl[1] * my, kz = a.tpl[2] * mz;
-        if (PREC == 1) {
-            GTab32 t;
-            t.m = make_int4(mx, my, mz, __float_as_int((float)im));
-            t.f = make_float4((float)(coef * kx), (float)(coef * ky), (float)(coef * kz), (float)re);
-            ((GTab32 *)a.gtab)[l] = t;
-        } else {
-            GTab64 t;
-            t.m = make_int4(mx, my, mz, 0);
-            t.ck[0] = coef * kx; t.ck[1] = coef * ky; t.ck[2] = coef * kz;
-            t.re = re; t.im = im;
-            ((GTab64 *)a.gtab)[l] = t;
-        }
+        rho_final_write<PREC>(a, l, re, im);
     }
     if (bump && threadIdx.x == 0) {
         a.ctr->draw += 1ull;
@@ -271,10 +277,74 @@ __device__ __forceinline__ void rho_final_body(const RhoFinalArgs &a, int ML, un
     }
 }
 
+// rho_final_body with the eight warps' sums of each 32 modes in eight blocks: block
+// (x, w) holds warp w's eight accumulators in its warps u = 0..7 (each the same sequence
+// of additions), adds them in the same tree, and stores the group sum; the last of the
+// eight blocks to arrive adds the group sums in order w = 0..7.  Every addition is the
+// one-block form's, in its order, so rho is bit-identical; the FP64 additions of a
+// mode's G nsub partials spread over eight SMs instead of one.
+template <int PREC>
+__device__ __forceinline__ void rho_final_split_body(const RhoFinalArgs &a, int ML, double2 (*sh)[32]) {
+    __shared__ int last;
+    const int u = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = (int)blockIdx.y;
+    const int l = (int)blockIdx.x * 32 + lane;
+    double re = 0.0, im = 0.0;
+    if (l < a.P) {
+        const int pass_base = (l / (256 * ML)) * 256 * ML;
+        int ngroups, nsub;
+        rho_split(a.P, pass_base, ML, ngroups, nsub);
+        for (int b0 = w; b0 < a.G; b0 += 64) {
+            const int b = b0 + 8 * u;
+            if (b < a.G)
+                for (int s = 0; s < nsub; ++s) {
+                    const double2 v = a.partial[((size_t)b * 8 + s) * a.P + l];
+                    re += v.x;
+                    im += v.y;
+                }
+        }
+    }
+    sh[u][lane] = make_double2(re, im);
+    __syncthreads();
+    if (u == 0) {
+        if (l < a.P) {
+            re = ((sh[0][lane].x + sh[1][lane].x) + (sh[2][lane].x + sh[3][lane].x)) +
+                 ((sh[4][lane].x + sh[5][lane].x) + (sh[6][lane].x + sh[7][lane].x));
+            im = ((sh[0][lane].y + sh[1][lane].y) + (sh[2][lane].y + sh[3][lane].y)) +
+                 ((sh[4][lane].y + sh[5][lane].y) + (sh[6][lane].y + sh[7][lane].y));
+            a.wsum[(size_t)w * a.P + l] = make_double2(re, im);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) last = atomicAdd(&a.wdone[blockIdx.x], 1u) == 7u;
+        __syncwarp();
+        if (last) {
+            __threadfence();
+            if (l < a.P) {
+                re = 0.0;
+                im = 0.0;
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const double2 g = __ldcg(&a.wsum[(size_t)v * a.P + l]);
+                    re += g.x;
+                    im += g.y;
+                }
+                rho_final_write<PREC>(a, l, re, im);
+            }
+            if (lane == 0) a.wdone[blockIdx.x] = 0u;
+            if (blockIdx.x == 0 && lane == 0 && !a.keep_draw) {
+                a.ctr->draw += 1ull;
+                a.ctr->inject = 0;
+            }
+        }
+    }
+}
+
+
 template <int PREC>
 __global__ void __launch_bounds__(256) k_rho_final(RhoFinalArgs a, int ML) {
     __shared__ double2 sh[8][32];
-    rho_final_body<PREC>(a, ML, blockIdx.x, blockIdx.x == 0 && !a.keep_draw, sh);
+    rho_final_split_body<PREC>(a, ML, sh);
 }
 
 __global__ void __launch_bounds__(256) k_rho_final_batch(const RhoFinalArgs *args, const uint32_t *items, int R) {
@@ -622,9 +692,9 @@ void launch_rho(int prec, const RhoArgs &a, cudaStream_t st) {
 }
 
 void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st) {
-    const int nb = (a.P + 31) / 32;
-    if (prec == 1) k_rho_final<1><<<nb, 256, 0, st>>>(a, rho_ml(a.P));
-    else k_rho_final<0><<<nb, 256, 0, st>>>(a, 1);
+    const dim3 grid((unsigned)((a.P + 31) / 32), 8);
+    if (prec == 1) k_rho_final<1><<<grid, 256, 0, st>>>(a, rho_ml(a.P));
+    else k_rho_final<0><<<grid, 256, 0, st>>>(a, 1);
 }
 
 int launch_far(int prec, const FarArgs &a, cudaStream_t st) {

@@ -183,6 +183,11 @@ struct RhoFinalArgs {
     double *Ufar;              // [P]: coef_l |rho_l|^2 / 2
     DevCounters *ctr;
     int keep_draw;             // 1: the draw counter is not advanced (a reduced rho set from outside)
+    // launch_rho_final: the eight warp groups of each 32 modes in blocks of their own, the
+    // group sums in wsum [8][P] and the groups' arrivals in wdone [ceil(P/32)] (zero between
+    // launches: the last block of each 32 modes resets its counter)
+    double2 *wsum;
+    unsigned int *wdone;
 };
 void launch_rho_final(int prec, const RhoFinalArgs &a, cudaStream_t st);
 struct FarArgs {

@@ -49,7 +49,8 @@ struct rbsog_ctx {
     int *mix_alias = nullptr, *ax_off = nullptr, *ax_nmax = nullptr, *ax_alias = nullptr;
     int *modes = nullptr, *inject_m = nullptr;
     double *coef = nullptr;
-    double2 *partial = nullptr, *rho = nullptr;
+    double2 *partial = nullptr, *rho = nullptr, *rho_wsum = nullptr;
+    unsigned int *rho_wdone = nullptr;
     void *gtab = nullptr;
     double *Ufar = nullptr, *U_part = nullptr, *K_part = nullptr, *energy = nullptr, *escratch = nullptr;
     unsigned int *edone = nullptr;
@@ -571,6 +572,7 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
     for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
     rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr;
+    rf.wsum = c->rho_wsum; rf.wdone = c->rho_wdone;
     // The structure factor needs the particle records (in id order) and the k-sample, not
     // the cell list: outside profiling the sample runs on a side stream from the start of
     // the step, and rho and rho_final follow there as soon as k_bin has written the
@@ -741,6 +743,8 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         dalloc(c, &c->keys, n) || dalloc(c, &c->modes, 3 * (size_t)p.P) ||
         dalloc(c, &c->inject_m, 3 * (size_t)p.P) || dalloc(c, &c->coef, (size_t)p.P) ||
         dalloc(c, &c->partial, (size_t)c->G * 8 * p.P) || dalloc(c, &c->rho, (size_t)p.P) ||
+        dalloc(c, &c->rho_wsum, 8 * (size_t)p.P) || dalloc(c, &c->rho_wdone, ((size_t)p.P + 31) / 32) ||
+        cudaMemset(c->rho_wdone, 0, sizeof(unsigned int) * (((size_t)p.P + 31) / 32)) != cudaSuccess ||
         dalloc(c, (unsigned char **)&c->gtab, gtab_bytes) || dalloc(c, &c->Ufar, (size_t)p.P) ||
         dalloc(c, &c->U_part, 8 * std::max((n + 127) / 128, (size_t)bx.ncell) + 8) || dalloc(c, &c->K_part, (n + 255) / 256 + 1) ||
         dalloc(c, &c->energy, 8) || dalloc(c, &c->escratch, 3 * (size_t)kEnergyBlocks) || dalloc(c, &c->edone, 1) ||
@@ -1009,6 +1013,7 @@ int rbsog_forces_complete(rbsog_ctx *c, const double *rho, double *F, void *stre
     rf.partial = c->partial; rf.G = c->G; rf.P = c->p.P; rf.m = c->modes; rf.coef = c->coef;
     for (int d = 0; d < 3; ++d) rf.tpl[d] = c->box.tpl[d];
     rf.rho = c->rho; rf.gtab = c->gtab; rf.Ufar = c->Ufar; rf.ctr = c->ctr; rf.keep_draw = 1;
+    rf.wsum = c->rho_wsum; rf.wdone = c->rho_wdone;
     launch_rho_final(prec, rf, st);
     const size_t bytes = 3 * (size_t)c->N * sizeof(double);
     double *Fd = nullptr;
