@@ -15,7 +15,13 @@
  *     there is no CPU fallback: if the GPU path cannot run, the call fails.
  *   - Vectors are [N][3] row-major float64 in the caller's particle order.
  *   - Pointers marked "host or device" may point to host memory (pageable or pinned)
- *     or to device memory on the context's device (unified addressing decides).
+ *     or to device memory on the context's device (unified addressing decides).  The
+ *     single-context calls that move [N][3] rows (rbsog_set_state*, rbsog_get_state,
+ *     rbsog_get_forces*) read and write device memory and pinned host memory from
+ *     their kernels directly (pinned memory through its mapped device address, in
+ *     whole lines over the host link) and stage pageable memory through a device
+ *     buffer and a copy.  An enqueued call reads its inputs when the stream reaches
+ *     it: keep them unchanged until then.
  *   - Pointers marked "host" must be host memory; "device" must be device memory.
  *   - The caller owns every pointer it passes; the library copies what it keeps.
  *     The library owns all of its internal device buffers and frees them in

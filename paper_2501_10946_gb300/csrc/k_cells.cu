@@ -595,10 +595,57 @@ __device__ __forceinline__ void set_state_body(const double *r, const double *v,
     rest.id[k] = k;
 }
 
-__global__ void __launch_bounds__(256) k_set_state(const double *r, const double *v, const double *q_user,
-                                                   const double *m_user, State rest, uint32_t N, Box box) {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) set_state_body(r, v, q_user, m_user, rest, box, k);
+// Caller rows [N][3] in and out of one context, 256 caller indices per block: the block's
+// 768 values of an array move between the caller's buffer and shared memory in order (one
+// lane per consecutive value), so a caller buffer in pinned host memory, read or written
+// by the kernel through its mapped address, is moved in whole lines over the host link.
+constexpr int kRowBlock = 256;
+
+template <typename T>
+__device__ __forceinline__ void rows_in(const T *src, uint32_t base, uint32_t n, T *sh) {
+    const size_t o = 3 * (size_t)base;
+    for (uint32_t i = threadIdx.x; i < 3 * n; i += kRowBlock) sh[i] = src[o + i];
+}
+
+template <typename T>
+__device__ __forceinline__ void rows_out(const T *sh, uint32_t base, uint32_t n, T *dst) {
+    const size_t o = 3 * (size_t)base;
+    for (uint32_t i = threadIdx.x; i < 3 * n; i += kRowBlock) dst[o + i] = sh[i];
+}
+
+__device__ __forceinline__ float conv_to_f(double x) { return d2f_int(x); }
+__device__ __forceinline__ float conv_to_f(float x) { return x; }
+__device__ __forceinline__ double conv_to_d(float x) { return f2d_int(x); }
+__device__ __forceinline__ double conv_to_d(double x) { return x; }
+template <typename To, typename Ti> __device__ __forceinline__ To conv(Ti x);
+template <> __device__ __forceinline__ float conv<float, double>(double x) { return conv_to_f(x); }
+template <> __device__ __forceinline__ float conv<float, float>(float x) { return x; }
+template <> __device__ __forceinline__ double conv<double, float>(float x) { return conv_to_d(x); }
+template <> __device__ __forceinline__ double conv<double, double>(double x) { return x; }
+
+// A state upload: the particles take the caller's order (id = caller index), positions
+// wrapped into [0, L) (wrap_near: the same values as wrap_coord), 1/m from the stored
+// inverse masses.
+__global__ void __launch_bounds__(kRowBlock) k_set_state(const double *r, const double *v, const double *q_user,
+                                                         const double *invm_user, State rest, uint32_t N, Box box) {
+    __shared__ double sr[3 * kRowBlock], sv[3 * kRowBlock];
+    const uint32_t base = blockIdx.x * kRowBlock;
+    const uint32_t n = min((uint32_t)kRowBlock, N - base);
+    rows_in(r, base, n, sr);
+    if (v) rows_in(v, base, n, sv);
+    __syncthreads();
+    const uint32_t t = threadIdx.x;
+    if (t >= n) return;
+    const uint32_t k = base + t;
+    rest.rx[k] = wrap_near(sr[3 * t], box.L[0], box.invL[0]);
+    rest.ry[k] = wrap_near(sr[3 * t + 1], box.L[1], box.invL[1]);
+    rest.rz[k] = wrap_near(sr[3 * t + 2], box.L[2], box.invL[2]);
+    rest.vx[k] = v ? sv[3 * t] : 0.0;
+    rest.vy[k] = v ? sv[3 * t + 1] : 0.0;
+    rest.vz[k] = v ? sv[3 * t + 2] : 0.0;
+    rest.invm[k] = invm_user[k];
+    rest.q[k] = q_user[k];
+    rest.id[k] = k;
 }
 
 // New positions and velocities for a particle already resident at position k of the rest
@@ -667,55 +714,64 @@ __device__ __forceinline__ void get_state_body(const State &rest, size_t base, u
     if (v_out) { v_out[u] = rest.vx[k]; v_out[u + 1] = rest.vy[k]; v_out[u + 2] = rest.vz[k]; }
 }
 
-// Forces at an uploaded state: caller order [N][3] doubles into the SoA force buffer of
-// the rest order, which is the caller order right after a state upload; marks the forces
-// valid (after the counter reset of the upload, on the same stream).
-template <int PREC>
-__global__ void __launch_bounds__(256) k_set_forces(const double *F_in, void *F, uint32_t N, DevCounters *ctr) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) {
+// Forces at an uploaded state: caller rows [N][3] into the SoA force buffer of the rest
+// order, which is the caller order right after a state upload; marks the forces valid
+// (after the counter reset of the upload, on the same stream).  FP64 values into the FP32
+// build's buffer are rounded to nearest; FP32 into FP32 are copied.
+template <typename Ti, typename To>
+__global__ void __launch_bounds__(kRowBlock) k_set_forces(const Ti *F_in, To *F, uint32_t N, DevCounters *ctr) {
+    __shared__ Ti sf[3 * kRowBlock];
+    const uint32_t base = blockIdx.x * kRowBlock;
+    if (base == 0 && threadIdx.x == 0) ctr->fvalid = 1;
+    if (base >= N) return;
+    const uint32_t n = min((uint32_t)kRowBlock, N - base);
+    rows_in(F_in, base, n, sf);
+    __syncthreads();
+    const uint32_t t = threadIdx.x;
+    if (t >= n) return;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const double f = F_in[3 * (size_t)k + d];
-            if (PREC == 1) ((float *)F)[(size_t)d * N + k] = d2f_int(f);
-            else ((double *)F)[(size_t)d * N + k] = f;
-        }
+    for (int d = 0; d < 3; ++d) F[(size_t)d * N + base + t] = conv<To>(sf[3 * t + d]);
+}
+
+// Place in the rest order of each caller index: the inverse of rest.id.
+__global__ void __launch_bounds__(256) k_rest_pos(const uint32_t *id, uint32_t N, uint32_t *pos) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) pos[id[k]] = k;
+}
+
+// The state in caller rows: thread t of the block takes caller index base + t from its
+// place in the rest order.
+__global__ void __launch_bounds__(kRowBlock) k_get_state(State rest, const uint32_t *pos, uint32_t N, double *r_out,
+                                                         double *v_out) {
+    __shared__ double sr[3 * kRowBlock], sv[3 * kRowBlock];
+    const uint32_t base = blockIdx.x * kRowBlock;
+    const uint32_t n = min((uint32_t)kRowBlock, N - base);
+    const uint32_t t = threadIdx.x;
+    if (t < n) {
+        const uint32_t k = pos[base + t];
+        if (r_out) { sr[3 * t] = rest.rx[k]; sr[3 * t + 1] = rest.ry[k]; sr[3 * t + 2] = rest.rz[k]; }
+        if (v_out) { sv[3 * t] = rest.vx[k]; sv[3 * t + 1] = rest.vy[k]; sv[3 * t + 2] = rest.vz[k]; }
     }
-    if (k == 0) ctr->fvalid = 1;
+    __syncthreads();
+    if (r_out) rows_out(sr, base, n, r_out);
+    if (v_out) rows_out(sv, base, n, v_out);
 }
 
-// The forces of the rest order into the caller's order [N][3].
-template <int PREC>
-__global__ void __launch_bounds__(256) k_get_forces(State rest, const void *F, uint32_t N, double *F_out) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const size_t u = 3 * (size_t)rest.id[k];
+// The forces of the rest order in caller rows (FP32 values widened exactly to FP64 for the
+// FP64 form; copied for the FP32 form).
+template <typename Ti, typename To>
+__global__ void __launch_bounds__(kRowBlock) k_get_forces(const uint32_t *pos, const Ti *F, uint32_t N, To *F_out) {
+    __shared__ To sf[3 * kRowBlock];
+    const uint32_t base = blockIdx.x * kRowBlock;
+    const uint32_t n = min((uint32_t)kRowBlock, N - base);
+    const uint32_t t = threadIdx.x;
+    if (t < n) {
+        const uint32_t k = pos[base + t];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
-        F_out[u + d] = PREC == 1 ? f2d_int(((const float *)F)[(size_t)d * N + k]) : ((const double *)F)[(size_t)d * N + k];
-}
-
-// FP32 forms for the FP32 build, whose forces are FP32 values: no conversion either way.
-__global__ void __launch_bounds__(256) k_set_forces_f32(const float *F_in, float *F, uint32_t N, DevCounters *ctr) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) {
-#pragma unroll
-        for (int d = 0; d < 3; ++d) F[(size_t)d * N + k] = F_in[3 * (size_t)k + d];
+        for (int d = 0; d < 3; ++d) sf[3 * t + d] = conv<To>(F[(size_t)d * N + k]);
     }
-    if (k == 0) ctr->fvalid = 1;
-}
-
-__global__ void __launch_bounds__(256) k_get_forces_f32(State rest, const float *F, uint32_t N, float *F_out) {
-    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    const size_t u = 3 * (size_t)rest.id[k];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) F_out[u + d] = F[(size_t)d * N + k];
-}
-
-__global__ void __launch_bounds__(256) k_get_state(State rest, uint32_t N, double *r_out, double *v_out) {
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) get_state_body(rest, 0, k, r_out, v_out);
+    __syncthreads();
+    rows_out(sf, base, n, F_out);
 }
 
 __global__ void __launch_bounds__(256) k_get_state_batch(const SysStateArgs *args, const uint32_t *items, int R,
@@ -760,9 +816,9 @@ void launch_gather(int prec, const GatherArgs &g, cudaStream_t st) {
     else k_gather<0><<<blocks_for(g.N, 256), 256, 0, st>>>(g);
 }
 
-void launch_set_state(const double *r, const double *v, const double *q_user, const double *m_user, State rest,
+void launch_set_state(const double *r, const double *v, const double *q_user, const double *invm_user, State rest,
                       uint32_t N, Box box, DevCounters *ctr, cudaStream_t st) {
-    k_set_state<<<blocks_for(N, 256), 256, 0, st>>>(r, v, q_user, m_user, rest, N, box);
+    k_set_state<<<blocks_for(N, kRowBlock), kRowBlock, 0, st>>>(r, v, q_user, invm_user, rest, N, box);
     k_reset_counters<<<1, 1, 0, st>>>(ctr);
 }
 
@@ -779,27 +835,32 @@ void launch_get_state_batch(const SysStateArgs *args, const uint32_t *items, int
     k_get_state_batch<<<nblocks, 256, 0, st>>>(args, items, R, r_out, v_out);
 }
 
-void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st) {
-    k_get_state<<<blocks_for(N, 256), 256, 0, st>>>(rest, N, r_out, v_out);
+void launch_rest_pos(const uint32_t *id, uint32_t N, uint32_t *pos, cudaStream_t st) {
+    k_rest_pos<<<blocks_for(N, 256), 256, 0, st>>>(id, N, pos);
+}
+
+void launch_get_state(State rest, const uint32_t *pos, uint32_t N, double *r_out, double *v_out, cudaStream_t st) {
+    k_get_state<<<blocks_for(N, kRowBlock), kRowBlock, 0, st>>>(rest, pos, N, r_out, v_out);
 }
 
 void launch_set_forces(int prec, const double *F_in, void *F, uint32_t N, DevCounters *ctr, cudaStream_t st) {
-    const unsigned nb = blocks_for(N > 0 ? N : 1, 256);
-    if (prec == 1) k_set_forces<1><<<nb, 256, 0, st>>>(F_in, F, N, ctr);
-    else k_set_forces<0><<<nb, 256, 0, st>>>(F_in, F, N, ctr);
+    const unsigned nb = blocks_for(N > 0 ? N : 1, kRowBlock);
+    if (prec == 1) k_set_forces<double, float><<<nb, kRowBlock, 0, st>>>(F_in, (float *)F, N, ctr);
+    else k_set_forces<double, double><<<nb, kRowBlock, 0, st>>>(F_in, (double *)F, N, ctr);
 }
 
 void launch_set_forces_f32(const float *F_in, float *F, uint32_t N, DevCounters *ctr, cudaStream_t st) {
-    k_set_forces_f32<<<blocks_for(N > 0 ? N : 1, 256), 256, 0, st>>>(F_in, F, N, ctr);
+    k_set_forces<float, float><<<blocks_for(N > 0 ? N : 1, kRowBlock), kRowBlock, 0, st>>>(F_in, F, N, ctr);
 }
 
-void launch_get_forces_f32(State rest, const float *F, uint32_t N, float *F_out, cudaStream_t st) {
-    k_get_forces_f32<<<blocks_for(N, 256), 256, 0, st>>>(rest, F, N, F_out);
+void launch_get_forces_f32(const uint32_t *pos, const float *F, uint32_t N, float *F_out, cudaStream_t st) {
+    k_get_forces<float, float><<<blocks_for(N, kRowBlock), kRowBlock, 0, st>>>(pos, F, N, F_out);
 }
 
-void launch_get_forces(int prec, State rest, const void *F, uint32_t N, double *F_out, cudaStream_t st) {
-    if (prec == 1) k_get_forces<1><<<blocks_for(N, 256), 256, 0, st>>>(rest, F, N, F_out);
-    else k_get_forces<0><<<blocks_for(N, 256), 256, 0, st>>>(rest, F, N, F_out);
+void launch_get_forces(int prec, const uint32_t *pos, const void *F, uint32_t N, double *F_out, cudaStream_t st) {
+    const unsigned nb = blocks_for(N, kRowBlock);
+    if (prec == 1) k_get_forces<float, double><<<nb, kRowBlock, 0, st>>>(pos, (const float *)F, N, F_out);
+    else k_get_forces<double, double><<<nb, kRowBlock, 0, st>>>(pos, (const double *)F, N, F_out);
 }
 
 }  // namespace rbsog

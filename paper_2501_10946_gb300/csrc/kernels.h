@@ -61,16 +61,21 @@ struct GatherArgs {
     uint32_t N;
 };
 void launch_gather(int prec, const GatherArgs &g, cudaStream_t st);
-void launch_set_state(const double *r, const double *v, const double *q_user, const double *m_user, State rest,
+// Caller rows [N][3] (r, v, F) in and out of one context.  Each pointer is device memory or
+// the mapped address of pinned host memory: the kernels move whole lines either way.
+// A state upload: particle k = caller index k, 1/m from the inverse masses invm_user.
+void launch_set_state(const double *r, const double *v, const double *q_user, const double *invm_user, State rest,
                       uint32_t N, Box box, DevCounters *ctr, cudaStream_t st);
-void launch_get_state(State rest, uint32_t N, double *r_out, double *v_out, cudaStream_t st);
+// pos[caller index] = place in the rest order (the inverse of rest.id), for the reads below
+void launch_rest_pos(const uint32_t *id, uint32_t N, uint32_t *pos, cudaStream_t st);
+void launch_get_state(State rest, const uint32_t *pos, uint32_t N, double *r_out, double *v_out, cudaStream_t st);
 // F_in ([N][3] doubles, caller order = the rest order after a state upload) into the SoA
 // force buffer F of the build's precision; sets ctr->fvalid
 void launch_set_forces(int prec, const double *F_in, void *F, uint32_t N, DevCounters *ctr, cudaStream_t st);
 // the SoA forces of the rest order into F_out ([N][3] doubles, caller order)
-void launch_get_forces(int prec, State rest, const void *F, uint32_t N, double *F_out, cudaStream_t st);
+void launch_get_forces(int prec, const uint32_t *pos, const void *F, uint32_t N, double *F_out, cudaStream_t st);
 void launch_set_forces_f32(const float *F_in, float *F, uint32_t N, DevCounters *ctr, cudaStream_t st);
-void launch_get_forces_f32(State rest, const float *F, uint32_t N, float *F_out, cudaStream_t st);
+void launch_get_forces_f32(const uint32_t *pos, const float *F, uint32_t N, float *F_out, cudaStream_t st);
 
 // ---- sampler and normalisation (k_sample.cu) ----
 // A mixture of separable components: component c has weight mix and per-axis alias

@@ -40,7 +40,9 @@ struct rbsog_ctx {
     Yterms y{};                   // the kernel's Yukawa terms
     // device buffers
     State rest{}, work{};
-    double *q_user = nullptr, *m_user = nullptr;
+    double *q_user = nullptr, *invm_user = nullptr;   // caller-order charges and 1/m
+    uint32_t *pos = nullptr;       // place in the rest order of each caller index
+    bool pos_valid = false;        // pos belongs to the current rest order
     double *stage_a = nullptr, *stage_b = nullptr, *stage_c = nullptr;
     void *F = nullptr, *Fn = nullptr, *rec_w = nullptr, *rec_id = nullptr, *rec = nullptr;   // records: work, id, cell order
     uint32_t *cell = nullptr, *slot = nullptr, *count = nullptr, *tile_sums = nullptr, *cell_start = nullptr;
@@ -479,6 +481,29 @@ bool is_device_ptr(const void *ptr) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The address a kernel reads or writes ptr through: ptr for device and managed memory,
+// the mapped device address of pinned host memory, nullptr for memory the device cannot
+// address (pageable host memory goes through a staging buffer and a copy).
+template <typename T>
+T *device_view(T *ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return ptr;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) return (T *)at.devicePointer;
+    return nullptr;
+}
+
+// pos for the current rest order, computed once per order (a state upload and every force
+// evaluation reorder the particles)
+void ensure_pos(rbsog_ctx *c, cudaStream_t st) {
+    if (c->pos_valid) return;
+    launch_rest_pos(c->rest.id, c->N, c->pos, st);
+    c->pos_valid = true;
+}
+
 int build_sampler(rbsog_ctx *c, const HostSystem &hs) {
     const int mt = (int)hs.mix_prob.size();   // mixture components
     const std::vector<unsigned long long> mp = alias_thresholds(hs.mix_prob), axp = alias_thresholds(hs.ax_prob);
@@ -530,6 +555,7 @@ struct ProfScope {
 // part = 1: stop after the structure factor (the first half of a domain's evaluation)
 int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double *Fn_user, double *Ff_user,
             int advance, int part = 0) {
+    c->pos_valid = false;   // the cell sort reorders the particles
     const int prec = c->prec;
     const uint32_t N = c->N;
     BinArgs b{};
@@ -735,7 +761,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
     const int ntiles = (bx.ncell + kScanTile - 1) / kScanTile;
     c->G = rho_blocks(c->prec, c->N, p.P);
     const size_t gtab_bytes = (size_t)p.P * 64;
-    if (dalloc(c, &c->q_user, n) || dalloc(c, &c->m_user, n) || dalloc(c, &c->stage_a, n3) ||
+    if (dalloc(c, &c->q_user, n) || dalloc(c, &c->invm_user, n) || dalloc(c, &c->pos, n) || dalloc(c, &c->stage_a, n3) ||
         dalloc(c, &c->stage_b, n3) || dalloc(c, &c->stage_c, n3) || dalloc(c, &Fb, n3 * real) ||
         dalloc(c, &Fnb, n3 * real) || dalloc(c, &recwb, n * 4 * real) || dalloc(c, &recib, n * 4 * real) || dalloc(c, &recb, n * 4 * real) ||
         dalloc(c, &c->cell, n) || dalloc(c, &c->slot, n) || dalloc(c, &c->count, (size_t)bx.ncell) ||
@@ -772,11 +798,13 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
             return bail(RBSOG_ENOMEM);
         }
     }
+    std::vector<double> invm_host(n);
+    for (size_t i = 0; i < n; ++i) invm_host[i] = 1.0 / m_host[i];
     if (cudaMemset(c->count, 0, sizeof(uint32_t) * bx.ncell) != cudaSuccess ||
         cudaMemset(c->ctr, 0, sizeof(DevCounters)) != cudaSuccess ||
         cudaMemset(c->edone, 0, sizeof(unsigned int)) != cudaSuccess ||
         cudaMemcpy(c->q_user, q_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(c->m_user, m_host, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->invm_user, invm_host.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -810,7 +838,7 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         g_init_error = "device initialisation failed";
         return bail(RBSOG_ECUDA);
     }
-    launch_set_state(c->stage_a, nullptr, c->q_user, c->m_user, c->rest, c->N, c->box, c->ctr, 0);
+    launch_set_state(c->stage_a, nullptr, c->q_user, c->invm_user, c->rest, c->N, c->box, c->ctr, 0);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         g_init_error = "device initialisation failed";
         return bail(RBSOG_ECUDA);
@@ -819,24 +847,28 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
     return RBSOG_OK;
 }
 
+// Caller buffers: device memory and pinned host memory are read and written by the kernels
+// themselves (the latter through its mapped address, in whole lines over the host link);
+// other host memory goes through a staging buffer and a copy.
 int rbsog_set_state(rbsog_ctx *c, const double *r, const double *v, void *stream) {
     if (!c || !r) return fail(c, RBSOG_EINVAL, "ctx or r is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = 3 * (size_t)c->N * sizeof(double);
-    const double *rd = r, *vd = v;
-    if (!is_device_ptr(r)) {
+    const double *rd = device_view(r), *vd = v ? device_view(v) : nullptr;
+    if (!rd) {
         CK(cudaMemcpyAsync(c->stage_a, r, bytes, cudaMemcpyDefault, st), "copy r");
         rd = c->stage_a;
     }
-    if (v && !is_device_ptr(v)) {
+    if (v && !vd) {
         CK(cudaMemcpyAsync(c->stage_b, v, bytes, cudaMemcpyDefault, st), "copy v");
         vd = c->stage_b;
     }
-    launch_set_state(rd, vd, c->q_user, c->m_user, c->rest, c->N, c->box, c->ctr, st);
+    launch_set_state(rd, vd, c->q_user, c->invm_user, c->rest, c->N, c->box, c->ctr, st);
     CK(cudaGetLastError(), "set_state");
     c->force_valid = false;
     c->energy_valid = false;
     c->partial_done = false;
+    c->pos_valid = false;
     return RBSOG_OK;
 }
 
@@ -844,8 +876,8 @@ int rbsog_set_state_forces(rbsog_ctx *c, const double *r, const double *v, const
     if (int code = rbsog_set_state(c, r, v, stream)) return code;
     if (!F) return RBSOG_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const double *Fd = F;
-    if (!is_device_ptr(F)) {
+    const double *Fd = device_view(F);
+    if (!Fd) {
         CK(cudaMemcpyAsync(c->stage_c, F, 3 * (size_t)c->N * sizeof(double), cudaMemcpyDefault, st), "copy F");
         Fd = c->stage_c;
     }
@@ -859,10 +891,12 @@ int rbsog_get_forces(rbsog_ctx *c, double *F, void *stream) {
     if (!c || !F) return fail(c, RBSOG_EINVAL, "ctx or F is NULL");
     if (!c->force_valid) return fail(c, RBSOG_EINVAL, "no forces at the current state yet");
     cudaStream_t st = (cudaStream_t)stream;
-    double *Fd = is_device_ptr(F) ? F : c->stage_c;
-    launch_get_forces(c->prec, c->rest, c->F, c->N, Fd, st);
+    double *Fv = device_view(F);
+    double *Fd = Fv ? Fv : c->stage_c;
+    ensure_pos(c, st);
+    launch_get_forces(c->prec, c->pos, c->F, c->N, Fd, st);
     CK(cudaGetLastError(), "get forces");
-    if (Fd != F) CK(cudaMemcpyAsync(F, Fd, 3 * (size_t)c->N * sizeof(double), cudaMemcpyDefault, st), "copy F out");
+    if (!Fv) CK(cudaMemcpyAsync(F, Fd, 3 * (size_t)c->N * sizeof(double), cudaMemcpyDefault, st), "copy F out");
     CK(cudaStreamSynchronize(st), "synchronize");
     return check_device_errors(c);
 }
@@ -873,8 +907,8 @@ int rbsog_set_state_forces_f32(rbsog_ctx *c, const double *r, const double *v, c
     if (int code = rbsog_set_state(c, r, v, stream)) return code;
     if (!F) return RBSOG_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const float *Fd = F;
-    if (!is_device_ptr(F)) {
+    const float *Fd = device_view(F);
+    if (!Fd) {
         CK(cudaMemcpyAsync(c->stage_c, F, 3 * (size_t)c->N * sizeof(float), cudaMemcpyDefault, st), "copy F");
         Fd = (const float *)c->stage_c;
     }
@@ -889,10 +923,12 @@ int rbsog_get_forces_f32(rbsog_ctx *c, float *F, void *stream) {
     if (c->prec != RBSOG_FP32) return fail(c, RBSOG_EINVAL, "FP32 forces need precision RBSOG_FP32");
     if (!c->force_valid) return fail(c, RBSOG_EINVAL, "no forces at the current state yet");
     cudaStream_t st = (cudaStream_t)stream;
-    float *Fd = is_device_ptr(F) ? F : (float *)c->stage_c;
-    launch_get_forces_f32(c->rest, (const float *)c->F, c->N, Fd, st);
+    float *Fv = device_view(F);
+    float *Fd = Fv ? Fv : (float *)c->stage_c;
+    ensure_pos(c, st);
+    launch_get_forces_f32(c->pos, (const float *)c->F, c->N, Fd, st);
     CK(cudaGetLastError(), "get forces");
-    if (Fd != F) CK(cudaMemcpyAsync(F, Fd, 3 * (size_t)c->N * sizeof(float), cudaMemcpyDefault, st), "copy F out");
+    if (!Fv) CK(cudaMemcpyAsync(F, Fd, 3 * (size_t)c->N * sizeof(float), cudaMemcpyDefault, st), "copy F out");
     CK(cudaStreamSynchronize(st), "synchronize");
     return check_device_errors(c);
 }
@@ -901,10 +937,13 @@ int rbsog_get_state(rbsog_ctx *c, double *r, double *v, uint64_t *step, void *st
     if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = 3 * (size_t)c->N * sizeof(double);
-    launch_get_state(c->rest, c->N, r ? c->stage_a : nullptr, v ? c->stage_b : nullptr, st);
+    double *rv = r ? device_view(r) : nullptr, *vv = v ? device_view(v) : nullptr;
+    double *rd = r ? (rv ? rv : c->stage_a) : nullptr, *vd = v ? (vv ? vv : c->stage_b) : nullptr;
+    ensure_pos(c, st);
+    launch_get_state(c->rest, c->pos, c->N, rd, vd, st);
     CK(cudaGetLastError(), "get_state");
-    if (r) CK(cudaMemcpyAsync(r, c->stage_a, bytes, cudaMemcpyDefault, st), "copy r out");
-    if (v) CK(cudaMemcpyAsync(v, c->stage_b, bytes, cudaMemcpyDefault, st), "copy v out");
+    if (r && !rv) CK(cudaMemcpyAsync(r, rd, bytes, cudaMemcpyDefault, st), "copy r out");
+    if (v && !vv) CK(cudaMemcpyAsync(v, vd, bytes, cudaMemcpyDefault, st), "copy v out");
     DevCounters hc;
     CK(cudaMemcpyAsync(&hc, c->ctr, sizeof hc, cudaMemcpyDeviceToHost, st), "read counters");
     CK(cudaStreamSynchronize(st), "synchronize");
@@ -971,6 +1010,7 @@ int rbsog_step(rbsog_ctx *c, int32_t nsteps, rbsog_energy *e, void *stream) {
         cudaGraphDestroy(g);
         CK(e3, "graph instantiate");
     }
+    if (nsteps > 0) c->pos_valid = false;
     for (int i = 0; i < nsteps; ++i) CK(cudaGraphLaunch(c->graph, st), "graph launch");
     if (e) return read_energy(c, e, st);
     return RBSOG_OK;
