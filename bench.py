@@ -188,9 +188,7 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
 
             def e2e_step():
                 set_sf(ctx, hr, hv, hF, stream=stream)
-                R.rbsog_step(ctx, 1, stream=stream)
-                R.rbsog_get_state(ctx, hr, hv, stream=stream)
-                get_f(ctx, hF, stream=stream)
+                R.rbsog_step_get(ctx, 1, hr, hv, hF, stream=stream)
 
             e2e_step()
             torch.cuda.synchronize(dev)
@@ -203,9 +201,10 @@ def rbsog_replica(w, precision, steps, warmup, rank, torch, R, profile_steps=10,
             nbytes = hr.numel() * hr.element_size() + hv.numel() * hv.element_size() + hF.numel() * hF.element_size()
             out["e2e_h2d"] = nbytes
             out["e2e_d2h"] = nbytes
-            out["e2e_path"] = (f"{set_sf.__name__}(host r, v FP64; F {'FP32' if f32 else 'FP64'}) + rbsog_step(1) + "
-                               f"rbsog_get_state(host r, v) + {get_f.__name__}(host F), pinned buffers, each step's "
-                               "outputs the next step's inputs (one force evaluation per step)")
+            out["e2e_path"] = (f"{set_sf.__name__}(host r, v FP64; F {'FP32' if f32 else 'FP64'}) + "
+                               "rbsog_step_get(1; host r read back beside the step's force kernels, host v and F "
+                               "after it), pinned buffers, each step's outputs the next step's inputs (one force "
+                               "evaluation per step)")
     finally:
         R.rbsog_free(ctx)
     return out

@@ -212,6 +212,17 @@ int rbsog_forces_split(rbsog_ctx *ctx, double *F_near, double *F_far, rbsog_ener
  * evaluation at the uploaded state yet) an energy request fails with RBSOG_EINVAL. */
 int rbsog_step(rbsog_ctx *ctx, int32_t nsteps, rbsog_energy *e, void *stream);
 
+/* Advance nsteps >= 1 steps as rbsog_step and read back the state after them, as
+ * rbsog_get_state and rbsog_get_forces(_f32) would: positions r and velocities v
+ * ([N][3] doubles), forces F ([N][3], floats when f32 != 0 (FP32 build only), else
+ * doubles), all in the caller's order, host or device; any may be NULL; energies to *e
+ * when e is not NULL.  The positions are final once the last step has rebuilt its cell
+ * list, so they are copied back (copy engine, from a device staging buffer) while that
+ * step's forces are computed; velocities and forces follow the step.  Synchronous.
+ * RBSOG_EINVAL for nsteps < 1. */
+int rbsog_step_get(rbsog_ctx *ctx, int32_t nsteps, double *r, double *v, void *F, int32_t f32, rbsog_energy *e,
+                   void *stream);
+
 /* Inject the next force evaluation's modes: m_host is P triples (m_x, m_y, m_z) of
  * integers, not all zero, k = 2 pi (m_x/L_x, m_y/L_y, m_z/L_z).  Used once, then
  * sampling resumes.  P must equal the context's P.  Host pointer; synchronous. */

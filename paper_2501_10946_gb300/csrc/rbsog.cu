@@ -63,6 +63,12 @@ struct rbsog_ctx {
     // the structure factor runs beside the near field on this stream inside a step
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_bin = nullptr, ev_join = nullptr;
+    // rbsog_step_get: the positions' read-back runs on dl_stream from ev_sorted (recorded
+    // after the cell sort of the last step, when enqueue is given it) while the forces
+    // are computed; ev_dl marks the inverse order ready for the velocities and forces
+    cudaStream_t dl_stream = nullptr;
+    cudaEvent_t ev_sorted = nullptr, ev_dl = nullptr;
+    bool mark_sorted = false;
     cudaGraphExec_t graph = nullptr;
     bool force_valid = false;
     bool energy_valid = false;     // the energy partials belong to the current state
@@ -630,6 +636,8 @@ int enqueue(rbsog_ctx *c, cudaStream_t st, int integrate, double *F_user, double
     g.in = c->work; g.out = c->rest; g.keys = c->keys; g.cell = c->cell; g.cell_start = c->cell_start; g.ctr = c->ctr;
     g.c_off = nullptr; g.R = 1; g.rec_w = c->rec_w; g.rec = c->rec; g.N = N;
     { ProfScope ps(c, st, 3); launch_gather(prec, g, st); }
+    if (c->mark_sorted && cudaEventRecord(c->ev_sorted, st) != cudaSuccess)
+        return fail(c, RBSOG_ECUDA, "record the sorted state");
     if (!fork) { ProfScope ps(c, st, 4); sample(st); }
     NearArgs na{};
     na.nc = c->nconsts; na.rec = c->rec; na.cell_start = c->cell_start; na.box = c->box; na.N = N; na.stride = N;
@@ -807,6 +815,9 @@ int rbsog_init(const rbsog_params *params, int64_t N, const double *q_host, cons
         cudaMemcpy(c->invm_user, invm_host.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->dl_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_dl, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_bin, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
@@ -1016,6 +1027,66 @@ int rbsog_step(rbsog_ctx *c, int32_t nsteps, rbsog_energy *e, void *stream) {
     return RBSOG_OK;
 }
 
+int rbsog_step_get(rbsog_ctx *c, int32_t nsteps, double *r, double *v, void *F, int32_t f32, rbsog_energy *e,
+                   void *stream) {
+    if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
+    if (nsteps < 1) return fail(c, RBSOG_EINVAL, "nsteps < 1");
+    if (F && f32 && c->prec != RBSOG_FP32) return fail(c, RBSOG_EINVAL, "FP32 forces need precision RBSOG_FP32");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nsteps > 1)
+        if (int code = rbsog_step(c, nsteps - 1, nullptr, stream)) return code;
+    if (!c->force_valid) {
+        if (int code = enqueue(c, st, 0, nullptr, nullptr, nullptr, 0)) return code;
+        c->force_valid = true;
+    }
+    // the last step launched one kernel at a time, with an event once the cell sort has
+    // put the new positions in their final order
+    const int mode = c->p.ensemble == RBSOG_LANGEVIN ? 2 : 1;
+    c->mark_sorted = true;
+    const int code = enqueue(c, st, mode, nullptr, nullptr, nullptr, 1);
+    c->mark_sorted = false;
+    if (code) return code;
+    const size_t N = c->N;
+    // positions (final after the sort) and the inverse order, beside the force kernels;
+    // the copy engine moves them so that no SM is taken from the forces
+    cudaStream_t dl = c->dl_stream;
+    CK(cudaStreamWaitEvent(dl, c->ev_sorted, 0), "wait for the sorted state");
+    launch_rest_pos(c->rest.id, c->N, c->pos, dl);
+    if (r) {
+        double *rv = device_view(r);
+        const bool dev = rv && is_device_ptr(r);
+        launch_get_state(c->rest, c->pos, c->N, dev ? rv : c->stage_a, nullptr, dl);
+        if (!dev) CK(cudaMemcpyAsync(r, c->stage_a, 3 * N * sizeof(double), cudaMemcpyDefault, dl), "copy r out");
+    }
+    CK(cudaGetLastError(), "positions read-back");
+    CK(cudaEventRecord(c->ev_dl, dl), "positions read-back");
+    CK(cudaStreamWaitEvent(st, c->ev_dl, 0), "join the read-back");
+    c->pos_valid = true;
+    // velocities (final after the closing kick) and forces, after the step
+    if (v) {
+        double *vv = device_view(v);
+        launch_get_state(c->rest, c->pos, c->N, nullptr, vv ? vv : c->stage_b, st);
+        if (!vv) CK(cudaMemcpyAsync(v, c->stage_b, 3 * N * sizeof(double), cudaMemcpyDefault, st), "copy v out");
+    }
+    if (F) {
+        if (f32) {
+            float *Fv = device_view((float *)F);
+            float *Fd = Fv ? Fv : (float *)c->stage_c;
+            launch_get_forces_f32(c->pos, (const float *)c->F, c->N, Fd, st);
+            if (!Fv) CK(cudaMemcpyAsync(F, Fd, 3 * N * sizeof(float), cudaMemcpyDefault, st), "copy F out");
+        } else {
+            double *Fv = device_view((double *)F);
+            double *Fd = Fv ? Fv : c->stage_c;
+            launch_get_forces(c->prec, c->pos, c->F, c->N, Fd, st);
+            if (!Fv) CK(cudaMemcpyAsync(F, Fd, 3 * N * sizeof(double), cudaMemcpyDefault, st), "copy F out");
+        }
+    }
+    CK(cudaGetLastError(), "read-back");
+    if (e) return read_energy(c, e, st);
+    CK(cudaStreamSynchronize(st), "synchronize");
+    return check_device_errors(c);
+}
+
 int rbsog_set_owned(rbsog_ctx *c, int64_t n_owned) {
     if (!c) return fail(c, RBSOG_EINVAL, "ctx is NULL");
     if (n_owned < 1 || n_owned > (int64_t)c->N) return fail(c, RBSOG_EINVAL, "n_owned must be in [1, N]");
@@ -1222,6 +1293,9 @@ void rbsog_free(rbsog_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
+    if (c->dl_stream) cudaStreamDestroy(c->dl_stream);
+    if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
+    if (c->ev_dl) cudaEventDestroy(c->ev_dl);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_bin) cudaEventDestroy(c->ev_bin);
     if (c->ev_join) cudaEventDestroy(c->ev_join);

@@ -68,7 +68,7 @@ class RbsogError(RuntimeError):
 
 
 _lib = None
-EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_set_state_forces", "rbsog_get_forces", "rbsog_set_state_forces_f32", "rbsog_get_forces_f32", "rbsog_forces", "rbsog_forces_split", "rbsog_step",
+EXPORTS = ["rbsog_init", "rbsog_set_state", "rbsog_get_state", "rbsog_set_state_forces", "rbsog_get_forces", "rbsog_set_state_forces_f32", "rbsog_get_forces_f32", "rbsog_forces", "rbsog_forces_split", "rbsog_step", "rbsog_step_get",
            "rbsog_set_ksample", "rbsog_get_ksample", "rbsog_get_rho", "rbsog_get_cells", "rbsog_get_sog", "rbsog_get_temperature", "rbsog_set_owned", "rbsog_forces_partial", "rbsog_forces_complete", "rbsog_slab_split",
            "rbsog_build_sog", "rbsog_profile", "rbsog_profile_read", "rbsog_profile_name", "rbsog_rho_noalloc",
            "rbsog_last_error", "rbsog_free", "rbsog_batch_init", "rbsog_batch_set_state", "rbsog_batch_get_state",
@@ -106,6 +106,7 @@ def load(build_if_missing: bool = True):
     L.rbsog_forces.argtypes = [vp, vp, C.POINTER(rbsog_energy), vp]
     L.rbsog_forces_split.argtypes = [vp, vp, vp, C.POINTER(rbsog_energy), vp]
     L.rbsog_step.argtypes = [vp, i32, C.POINTER(rbsog_energy), vp]
+    L.rbsog_step_get.argtypes = [vp, i32, vp, vp, vp, i32, C.POINTER(rbsog_energy), vp]
     L.rbsog_set_ksample.argtypes = [vp, vp, i32]
     L.rbsog_get_ksample.argtypes = [vp, vp, vp]
     L.rbsog_get_rho.argtypes = [vp, vp]
@@ -243,6 +244,19 @@ def rbsog_forces_split(ctx, F_near=None, F_far=None, energy: bool = False, strea
 def rbsog_step(ctx, nsteps: int, energy: bool = False, stream=None):
     e = rbsog_energy()
     _check(ctx, load().rbsog_step(ctx, int(nsteps), C.byref(e) if energy else None, _stream(stream)))
+    return e.as_dict() if energy else None
+
+
+def rbsog_step_get(ctx, nsteps: int, r=None, v=None, F=None, energy: bool = False, stream=None):
+    """nsteps steps, then r, v ([N][3] float64) and F ([N][3], float32 for the FP32 form,
+    else float64) in the caller's order; any may be None.  Returns the energies when asked."""
+    f32 = 0
+    if F is not None:
+        dt = getattr(F, "dtype", None)
+        f32 = 1 if str(dt) in ("float32", "torch.float32") else 0
+    e = rbsog_energy()
+    _check(ctx, load().rbsog_step_get(ctx, int(nsteps), _ptr(r), _ptr(v), _ptr(F), f32,
+                                      C.byref(e) if energy else None, _stream(stream)))
     return e.as_dict() if energy else None
 
 

@@ -115,3 +115,41 @@ def test_force_rows_round_trip(torch, prec):
                     F = empty(torch, kout, (N, 3), np.float32)
                     R.rbsog_get_forces_f32(c.h, F)
                     np.testing.assert_array_equal(host(F), F32in, err_msg=f"{kin} in, {kout} out")
+
+
+@pytest.mark.parametrize("prec,nsteps", [(R.RBSOG_FP32, 1), (R.RBSOG_FP32, 3), (R.RBSOG_FP64, 2)])
+def test_step_get_equals_step_then_reads(torch, prec, nsteps):
+    """rbsog_step_get (positions read back beside the last step's force kernels) returns
+    the bits of rbsog_step followed by rbsog_get_state and rbsog_get_forces(_f32), energies
+    included, for every kind of buffer; the context continues from the same state."""
+    w, r0, v0 = case()
+    N = w.N
+    fdt = np.float32 if prec == R.RBSOG_FP32 else np.float64
+    with Ctx(w, prec) as ref:
+        R.rbsog_set_state(ref.h, r0, v0)
+        e_ref = R.rbsog_step(ref.h, nsteps, energy=True)
+        r_ref, v_ref = np.zeros((N, 3)), np.zeros((N, 3))
+        R.rbsog_get_state(ref.h, r_ref, v_ref)
+        F_ref = np.zeros((N, 3), dtype=fdt)
+        (R.rbsog_get_forces_f32 if fdt == np.float32 else R.rbsog_get_forces)(ref.h, F_ref)
+        e2_ref = R.rbsog_step(ref.h, 1, energy=True)
+        for kind in KINDS:
+            with Ctx(w, prec) as c:
+                R.rbsog_set_state(c.h, r0, v0)
+                r = empty(torch, kind, (N, 3), np.float64)
+                v = empty(torch, kind, (N, 3), np.float64)
+                F = empty(torch, kind, (N, 3), fdt)
+                e = R.rbsog_step_get(c.h, nsteps, r, v, F, energy=True)
+                np.testing.assert_array_equal(host(r), r_ref, err_msg=kind)
+                np.testing.assert_array_equal(host(v), v_ref, err_msg=kind)
+                np.testing.assert_array_equal(host(F), F_ref, err_msg=kind)
+                assert e == e_ref, (kind, e, e_ref)
+                assert R.rbsog_step(c.h, 1, energy=True) == e2_ref, kind
+
+
+def test_step_get_refuses_zero_steps(torch):
+    w, r0, v0 = case()
+    with Ctx(w, R.RBSOG_FP32) as c:
+        R.rbsog_set_state(c.h, r0, v0)
+        with pytest.raises(R.RbsogError, match="EINVAL"):
+            R.rbsog_step_get(c.h, 0, np.zeros((w.N, 3)))
