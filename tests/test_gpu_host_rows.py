@@ -39,9 +39,9 @@ def host(x):
     return x.cpu().numpy() if hasattr(x, "cpu") else x
 
 
-def case():
+def case(ensemble="nve"):
     # 3001 particles: 11 full blocks of 256 rows and one of 185
-    w = workload(3001, L, P=32, dt=0.005)
+    w = workload(3001, L, P=32, dt=0.005, ensemble=ensemble)
     r0 = W.positions(w).copy()
     # positions outside [0, L): within one box length, and one beyond
     r0[::7] -= L
@@ -117,12 +117,14 @@ def test_force_rows_round_trip(torch, prec):
                     np.testing.assert_array_equal(host(F), F32in, err_msg=f"{kin} in, {kout} out")
 
 
-@pytest.mark.parametrize("prec,nsteps", [(R.RBSOG_FP32, 1), (R.RBSOG_FP32, 3), (R.RBSOG_FP64, 2)])
-def test_step_get_equals_step_then_reads(torch, prec, nsteps):
+@pytest.mark.parametrize("prec,nsteps,ensemble", [(R.RBSOG_FP32, 1, "nve"), (R.RBSOG_FP32, 3, "nve"),
+                                                   (R.RBSOG_FP64, 2, "nve"), (R.RBSOG_FP32, 2, "langevin")])
+def test_step_get_equals_step_then_reads(torch, prec, nsteps, ensemble):
     """rbsog_step_get (positions read back beside the last step's force kernels) returns
     the bits of rbsog_step followed by rbsog_get_state and rbsog_get_forces(_f32), energies
-    included, for every kind of buffer; the context continues from the same state."""
-    w, r0, v0 = case()
+    included, for every kind of buffer (velocity Verlet and BAOAB); the context continues
+    from the same state."""
+    w, r0, v0 = case(ensemble)
     N = w.N
     fdt = np.float32 if prec == R.RBSOG_FP32 else np.float64
     with Ctx(w, prec) as ref:
