@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "devmath.cuh"
@@ -1253,15 +1254,18 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
             // a lane past the list tests its last candidate with h = -inf: never above
             const uint32_t fl = flat_s + 2u * (uint32_t)(f0 + len - 1);
             uint32_t fa = flat_s + 2u * (uint32_t)(f0 + lane);
-            if (nct > 4) {
+            // NPR packed pairs of target columns per slot: 2 for at most 4 targets, 3 for 5 or
+            // 6, 4 for more; the two words past 6 columns stay zero (no target reads them)
+            auto slots = [&](auto npr_c) {
+                constexpr int NPR = decltype(npr_c)::value;
                 for (int s = 0; s < nsl; ++s, ma += kRowBytes, fa += 64u) {
                     const float4 cf = lds_f4(lds_u16(min(fa, fl)));
                     const float h = fa <= fl ? cf.w : -3e38f;
                     const unsigned long long X2 = pk2(cf.x, cf.x), Y2 = pk2(cf.y, cf.y), Z2 = pk2(cf.z, cf.z),
                                              H2 = pk2(h, h);
-                    uint32_t m[8];
+                    uint32_t m[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
 #pragma unroll
-                    for (int pr = 0; pr < 4; ++pr) {
+                    for (int pr = 0; pr < NPR; ++pr) {
                         float va, vb, ka, kb;
                         upk2(fma2(Z2, TZ[pr], fma2(Y2, TY[pr], fma2(X2, TX[pr], H2))), va, vb);
                         upk2(TK[pr], ka, kb);
@@ -1269,26 +1273,12 @@ __device__ __forceinline__ void near_brick_body(const NearArgs &a, const NearF &
                         m[2 * pr + 1] = __ballot_sync(full, vb > kb);
                     }
                     sts4_lane0(lane, ma, m[0], m[1], m[2], m[3]);
-                    sts4_lane0(lane, ma + 16u, m[4], m[5], m[6], m[7]);
+                    if (NPR > 2) sts4_lane0(lane, ma + 16u, m[4], m[5], m[6], m[7]);
                 }
-            } else {
-                for (int s = 0; s < nsl; ++s, ma += kRowBytes, fa += 64u) {
-                    const float4 cf = lds_f4(lds_u16(min(fa, fl)));
-                    const float h = fa <= fl ? cf.w : -3e38f;
-                    const unsigned long long X2 = pk2(cf.x, cf.x), Y2 = pk2(cf.y, cf.y), Z2 = pk2(cf.z, cf.z),
-                                             H2 = pk2(h, h);
-                    uint32_t m[4];
-#pragma unroll
-                    for (int pr = 0; pr < 2; ++pr) {
-                        float va, vb, ka, kb;
-                        upk2(fma2(Z2, TZ[pr], fma2(Y2, TY[pr], fma2(X2, TX[pr], H2))), va, vb);
-                        upk2(TK[pr], ka, kb);
-                        m[2 * pr] = __ballot_sync(full, va > ka);
-                        m[2 * pr + 1] = __ballot_sync(full, vb > kb);
-                    }
-                    sts4_lane0(lane, ma, m[0], m[1], m[2], m[3]);
-                }
-            }
+            };
+            if (nct > 6) slots(std::integral_constant<int, 4>{});
+            else if (nct > 4) slots(std::integral_constant<int, 3>{});
+            else slots(std::integral_constant<int, 2>{});
         }
     }
     group_sync<NT, 0>();
