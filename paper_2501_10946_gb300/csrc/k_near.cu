@@ -250,9 +250,8 @@ __device__ __forceinline__ void warp_partial(double v, double *U_part, unsigned 
     if ((tid & 31) == 0) U_part[(size_t)blk * (unsigned)(nt >> 5) + (unsigned)(tid >> 5)] = v;
 }
 
-// Barriers of a group of NT threads: the whole CTA (barrier 0 with NT = blockDim.x), or a
-// part of a larger CTA with its own barrier BAR (the persistent batched step runs two
-// near-field tiles per CTA side by side).
+// Barrier BAR of a group of NT threads (the near-field kernels use barrier 0 over the whole
+// CTA, NT = blockDim.x).
 template <int NT, int BAR>
 __device__ __forceinline__ void group_sync() {
     asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NT) : "memory");
@@ -312,10 +311,8 @@ __global__ void __launch_bounds__(kGlobalThreads) k_near_global(NearArgs a) {
 //       test and accumulates the pair forces: the two of a pass added in FP32, then one
 //       compensated FP32 add (FP64 build: plain FP64 sums, one pair at a time).
 // Neighbourhoods larger than 8 slots (256 candidates) run in several such rounds.
-// CAP: staged particles per CTA; NT: threads per CTA.  FR: tiles may span a whole row of
-// cells (a third staging slice per row).  BAR: the barrier of a group of NT threads that
-// shares a CTA with others.  F64: the FP64 build's 32-byte records (u64 coordinates), else
-// the FP32 build's 16-byte ones.
+// CAP: staged particles per CTA; NT: threads per CTA.  F64: the FP64 build's 32-byte
+// records (u64 coordinates), else the FP32 build's 16-byte ones.
 template <bool F64>
 struct TileRec;
 template <>
@@ -334,10 +331,9 @@ struct TileRec<true> {
     __device__ static __forceinline__ uint32_t z(const Rec64 &r) { return (uint32_t)(r.s[2] >> 32); }
 };
 
-template <int CAP, int NT, int MW, bool FR, bool F64 = false>
+template <int CAP, int NT, int MW, bool F64 = false>
 struct TileSmem {
     using Rec = typename TileRec<F64>::T;
-    static constexpr bool kFR = FR;
     Rec stage[CAP];                         // staged records
     uint32_t mask[kSlots][NT];    // per target (column = owning thread): hit bits of a round
     uint16_t flat[3 * CAP];                 // per target cell: staging indices of its 27-cell candidates
@@ -345,8 +341,8 @@ struct TileSmem {
     NearF nf;                               // the system's FP32 pair constants
     int seg_off[9][MW + 3];                 // per row: offset of each region cell within the row
     int row_base[10];                       // per row: offset of the row in the staging buffer
-    uint32_t chunk_g[9][FR ? 3 : 2];        // per row: global start of up to two (three) slices
-    uint32_t chunk_n[9][FR ? 3 : 2];        // per row: particle count of each slice
+    uint32_t chunk_g[9][2];                 // per row: global start of up to two slices
+    uint32_t chunk_n[9][2];                 // per row: particle count of each slice
     unsigned long long mbar;
 };
 
@@ -375,15 +371,14 @@ struct TileCtx {
     bool ok;                                // staged, and the copies landed
 };
 
-// Prologue of a tile (NT threads tid 0 .. NT-1, barrier BAR): cell populations of the
+// Prologue of a tile (NT threads tid 0 .. NT-1): cell populations of the
 // 9 x wn region, the row slices, the bulk copies of the region into S.stage, the system's
 // pair constants, and per target cell the list of its 27-cell candidates (staging index
 // << FSH, rows 0..8 in order, each row's cells i-1 .. i+1 in staging order) in S.flat.
-template <int NT, int BAR, int FSH, class TS>
+template <int NT, int FSH, class TS>
 __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tiles_x, unsigned blk, TS &S,
                                               int tid) {
     using RecT = typename TS::Rec;
-    constexpr bool FR = TS::kFR;
     constexpr uint32_t kRecBytes = (uint32_t)sizeof(RecT);
     TileCtx c;
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
@@ -424,7 +419,7 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
         S.nf.naf[g] = dup2(-a.nc.af[g]);
         S.nf.cf[g] = dup2(a.nc.cf[g]);
     }
-    group_sync<NT, BAR>();
+    group_sync<NT, 0>();
     // per-row prefix sums and the global slices of each row (a short serial loop per row
     // measured faster here than warp-wide scans)
     if (tid < 9) {
@@ -436,20 +431,10 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
             off += S.seg_off[tid][i];
             S.seg_off[tid][i] = off;
         }
-        if constexpr (FR) { S.chunk_g[tid][2] = 0; S.chunk_n[tid][2] = 0; }
         if (x0 >= 1 && x1 <= nx - 1) {           // one slice: cells x0-1 .. x1
             S.chunk_g[tid][0] = cs[rowbase + x0 - 1];
             S.chunk_n[tid][0] = cs[rowbase + x1 + 1] - cs[rowbase + x0 - 1];
             S.chunk_g[tid][1] = 0; S.chunk_n[tid][1] = 0;
-        } else if (FR && x0 == 0 && x1 == nx) {  // the whole row: cell nx-1, cells 0 .. nx-1, cell 0
-            S.chunk_g[tid][0] = cs[rowbase + nx - 1];
-            S.chunk_n[tid][0] = cs[rowbase + nx] - cs[rowbase + nx - 1];
-            S.chunk_g[tid][1] = cs[rowbase];
-            S.chunk_n[tid][1] = cs[rowbase + nx] - cs[rowbase];
-            if constexpr (FR) {
-                S.chunk_g[tid][2] = cs[rowbase];
-                S.chunk_n[tid][2] = cs[rowbase + 1] - cs[rowbase];
-            }
         } else if (x0 == 0) {                    // cell nx-1, then cells 0 .. x1
             S.chunk_g[tid][0] = cs[rowbase + nx - 1];
             S.chunk_n[tid][0] = cs[rowbase + nx] - cs[rowbase + nx - 1];
@@ -462,7 +447,7 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
             S.chunk_n[tid][1] = cs[rowbase + 1] - cs[rowbase];
         }
     }
-    group_sync<NT, BAR>();
+    group_sync<NT, 0>();
     if (tid == 0) {
         int b = 0;
         for (int r = 0; r < 9; ++r) {
@@ -471,7 +456,7 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
         }
         S.row_base[9] = b;
     }
-    group_sync<NT, BAR>();
+    group_sync<NT, 0>();
     const int region_n = S.row_base[9];
     c.region_n = region_n;
     c.staged = !c.overflow && region_n <= (int)(sizeof(S.stage) / sizeof(RecT));
@@ -491,7 +476,7 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
         const RecT *rec = (const RecT *)a.rec;
         for (int r = 0; r < 9; ++r) {
             uint32_t dst = (uint32_t)S.row_base[r];
-            for (int h = 0; h < (FR ? 3 : 2); ++h) {
+            for (int h = 0; h < 2; ++h) {
                 const uint32_t n = S.chunk_n[r][h];
                 if (n) {
                     asm volatile(
@@ -513,7 +498,7 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
         for (int r = 0; r < 9; ++r) tot += S.seg_off[r][i + 2] - S.seg_off[r][i - 1];
         S.fb[i + 1] = tot;
     }
-    group_sync<NT, BAR>();
+    group_sync<NT, 0>();
     if (tid == 0) {
         int b = 0;
         S.fb[1] = 0;
@@ -522,7 +507,7 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
             S.fb[i + 1] = b;
         }
     }
-    group_sync<NT, BAR>();
+    group_sync<NT, 0>();
     // while the copies fly: the candidate list of each target cell i, rows 0..8 in
     // order, each row's cells i-1 .. i+1 in staging order
     for (int e = tid; e < 9 * ntc; e += NT) {
@@ -543,7 +528,7 @@ __device__ __forceinline__ TileCtx tile_stage(const NearArgs &a, int W, int tile
             : "r"(bar)
             : "memory");
     }
-    c.ok = group_sync_and<NT, BAR>((int)done) != 0;
+    c.ok = group_sync_and<NT, 0>((int)done) != 0;
     if (!c.ok) {
         if (tid == 0) atomicOr(&a.ctr->err, kErrNearStage);
         // let the copies in flight land before the CTA exits (again bounded)
@@ -580,29 +565,15 @@ __device__ __forceinline__ double tile_fallback(const NearArgs &a, const TileCtx
     return Ufall;
 }
 
-// A group of the persistent step reuses its shared memory for its next tile, which
-// initialises the mbarrier again: invalidate it once every thread is done with it.
-template <int NT, int BAR, class TS>
-__device__ __forceinline__ void tile_release(const TileCtx &c, TS &S, int tid) {
-    if constexpr (BAR != 0) {
-        if (c.staged && c.region_n > 0) {
-            group_sync<NT, BAR>();
-            if (tid == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&S.mbar)) : "memory");
-        }
-    }
-}
-
-// DOT selects the form of the pre-filter test (see the threshold below): the expanded
-// one takes fewer instructions, the direct one fewer registers.
-// The tile is handled by NT threads (tid 0 .. NT-1) synchronised by barrier BAR.
-template <int CAP, int NT, int MW, bool DOT, bool FR, int BAR = 0, bool F64 = false>
+// The tile is handled by the CTA's NT threads (tid 0 .. NT-1).
+template <int CAP, int NT, int MW, bool F64 = false>
 __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int tiles_x, unsigned blk,
-                                               TileSmem<CAP, NT, MW, FR, F64> &S, int tid) {
+                                               TileSmem<CAP, NT, MW, F64> &S, int tid) {
     using RecT = typename TileRec<F64>::T;
     using RO = TileRec<F64>;
     const int lane = tid & 31, wid = tid >> 5;
     const unsigned full = 0xffffffffu;
-    const TileCtx c = tile_stage<NT, BAR, 0>(a, W, tiles_x, blk, S, tid);
+    const TileCtx c = tile_stage<NT, 0>(a, W, tiles_x, blk, S, tid);
     const int nx = a.box.nc[0], ny = a.box.nc[1], nz = a.box.nc[2];
     const int x0 = c.x0, wn = c.wn, cy = c.cy, cz = c.cz;
     const uint32_t g_first = c.g_first;
@@ -617,14 +588,11 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
             const int t1 = rb4 + S.seg_off[4][wn - 1];
             float *Fn = (float *)a.Fn;
             const float rc2 = a.nc.rc2_f;
-            // Pre-filter threshold thr = r_c^2 (1 + 4e-5).  An FP32 offset from the cell
-            // centre is within 1.8e-7 c of the exact one (|offset| <= 1.5 c per axis, two
-            // roundings; c < 4/3 r_c because n_c = floor(L / r_c) >= 3).  Either form of the
-            // test then decides within 3.3e-6 r_c^2 of the exact comparison, roundings of the
-            // expanded form included, so every pair that the exact test accepts passes:
-            //   direct:   |t - c|^2 < thr
-            //   expanded: t.c - |c|^2/2 > (|t|^2 - thr)/2, with |c|^2/2 once per candidate
-            //             and the right side once per target: 3 FMAs per test instead of 6.
+            // Pre-filter |t - c|^2 < thr with thr = r_c^2 (1 + 4e-5).  An FP32 offset from the
+            // cell centre is within 1.8e-7 c of the exact one (|offset| <= 1.5 c per axis, two
+            // roundings; c < 4/3 r_c because n_c = floor(L / r_c) >= 3), so the test decides
+            // within 3.3e-6 r_c^2 of the exact comparison and every pair that the exact test
+            // accepts passes.
             const float rcf2 = rc2 * 1.00004f;
             const float sx = a.box.L_2m32f[0], sy = a.box.L_2m32f[1], sz = a.box.L_2m32f[2];
             const unsigned long long sx2 = dup2(sx), sy2 = dup2(sy), sz2 = dup2(sz);
@@ -665,30 +633,27 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                         more = more || total > base + 32 * kSlots;
                         const int nsl = min(kSlots, (total - base + 31) >> 5);
                         const uint32_t ox = __float2uint_rz(((float)(x0 - 1 + i) + 0.5f) * cwx);
-                        // no candidate: far away (direct form) or never above the bound (expanded)
-                        float X[kSlots], Y[kSlots], Z[kSlots], H[kSlots];
+                        // no candidate: far away
+                        float X[kSlots], Y[kSlots], Z[kSlots];
 #pragma unroll
                         for (int s = 0; s < kSlots; ++s) {
-                            X[s] = DOT ? 0.f : 3e30f;
+                            X[s] = 3e30f;
                             Y[s] = 0.f;
                             Z[s] = 0.f;
-                            H[s] = -3e38f;
                             const int f = base + 32 * s + lane;
                             if (s < nsl && f < total) {
                                 const RecT rk = S.stage[S.flat[cb + f]];
                                 X[s] = (float)(int)(RO::x(rk) - ox) * sx;
                                 Y[s] = (float)(int)(RO::y(rk) - oy) * sy;
                                 Z[s] = (float)(int)(RO::z(rk) - oz) * sz;
-                                if (DOT) H[s] = -0.5f * fmaf(X[s], X[s], fmaf(Y[s], Y[s], Z[s] * Z[s]));
                             }
                         }
-                        unsigned long long X2[kSlots / 2], Y2[kSlots / 2], Z2[kSlots / 2], H2[kSlots / 2];
+                        unsigned long long X2[kSlots / 2], Y2[kSlots / 2], Z2[kSlots / 2];
 #pragma unroll
                         for (int h = 0; h < kSlots / 2; ++h) {
                             X2[h] = pk2(X[2 * h], X[2 * h + 1]);
                             Y2[h] = pk2(Y[2 * h], Y[2 * h + 1]);
                             Z2[h] = pk2(Z[2 * h], Z[2 * h + 1]);
-                            if (DOT) H2[h] = pk2(H[2 * h], H[2 * h + 1]);
                         }
 
                         int t = ta;
@@ -700,32 +665,25 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                                         zb = (float)(int)(RO::z(pb) - oz) * sz;
                             const unsigned long long xa2 = pk2(xa, xa), ya2 = pk2(ya, ya), za2 = pk2(za, za);
                             const unsigned long long xb2 = pk2(xb, xb), yb2 = pk2(yb, yb), zb2 = pk2(zb, zb);
-                            // expanded: accept t.c - |c|^2/2 > k; direct: accept |t - c|^2 < k
-                            const float ka = DOT ? 0.5f * (fmaf(xa, xa, fmaf(ya, ya, za * za)) - rcf2) : rcf2;
-                            const float kb = DOT ? 0.5f * (fmaf(xb, xb, fmaf(yb, yb, zb * zb)) - rcf2) : rcf2;
+                            // accept |t - c|^2 < thr
                             const int col = 32 * wid + (t - wlo);
 #pragma unroll
                             for (int h = 0; h < kSlots / 2; ++h) {
                                 if (2 * h < nsl) {
                                     float a0, a1, b0, b1;
-                                    if constexpr (DOT) {
-                                        upk2(fma2(xa2, X2[h], fma2(ya2, Y2[h], fma2(za2, Z2[h], H2[h]))), a0, a1);
-                                        upk2(fma2(xb2, X2[h], fma2(yb2, Y2[h], fma2(zb2, Z2[h], H2[h]))), b0, b1);
-                                    } else {
-                                        const unsigned long long dxa = sub2(xa2, X2[h]), dya = sub2(ya2, Y2[h]), dza = sub2(za2, Z2[h]);
-                                        const unsigned long long dxb = sub2(xb2, X2[h]), dyb = sub2(yb2, Y2[h]), dzb = sub2(zb2, Z2[h]);
-                                        upk2(fma2(dza, dza, fma2(dya, dya, mul2(dxa, dxa))), a0, a1);
-                                        upk2(fma2(dzb, dzb, fma2(dyb, dyb, mul2(dxb, dxb))), b0, b1);
-                                    }
-                                    const uint32_t ma0 = __ballot_sync(full, DOT ? a0 > ka : a0 < ka);
-                                    const uint32_t mb0 = __ballot_sync(full, DOT ? b0 > kb : b0 < kb);
+                                    const unsigned long long dxa = sub2(xa2, X2[h]), dya = sub2(ya2, Y2[h]), dza = sub2(za2, Z2[h]);
+                                    const unsigned long long dxb = sub2(xb2, X2[h]), dyb = sub2(yb2, Y2[h]), dzb = sub2(zb2, Z2[h]);
+                                    upk2(fma2(dza, dza, fma2(dya, dya, mul2(dxa, dxa))), a0, a1);
+                                    upk2(fma2(dzb, dzb, fma2(dyb, dyb, mul2(dxb, dxb))), b0, b1);
+                                    const uint32_t ma0 = __ballot_sync(full, a0 < rcf2);
+                                    const uint32_t mb0 = __ballot_sync(full, b0 < rcf2);
                                     if (lane == 0) {
                                         S.mask[2 * h][col] = ma0;
                                         S.mask[2 * h][col + 1] = mb0;
                                     }
                                     if (2 * h + 1 < nsl) {
-                                        const uint32_t ma1 = __ballot_sync(full, DOT ? a1 > ka : a1 < ka);
-                                        const uint32_t mb1 = __ballot_sync(full, DOT ? b1 > kb : b1 < kb);
+                                        const uint32_t ma1 = __ballot_sync(full, a1 < rcf2);
+                                        const uint32_t mb1 = __ballot_sync(full, b1 < rcf2);
                                         if (lane == 0) {
                                             S.mask[2 * h + 1][col] = ma1;
                                             S.mask[2 * h + 1][col + 1] = mb1;
@@ -740,22 +698,17 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
                             const float yt = (float)(int)(RO::y(rt) - oy) * sy;
                             const float zt = (float)(int)(RO::z(rt) - oz) * sz;
                             const unsigned long long xt2 = pk2(xt, xt), yt2 = pk2(yt, yt), zt2 = pk2(zt, zt);
-                            const float kt = DOT ? 0.5f * (fmaf(xt, xt, fmaf(yt, yt, zt * zt)) - rcf2) : rcf2;
                             const int col = 32 * wid + (t - wlo);
 #pragma unroll
                             for (int h = 0; h < kSlots / 2; ++h) {
                                 if (2 * h < nsl) {
                                     float ra, rb;
-                                    if constexpr (DOT) {
-                                        upk2(fma2(xt2, X2[h], fma2(yt2, Y2[h], fma2(zt2, Z2[h], H2[h]))), ra, rb);
-                                    } else {
-                                        const unsigned long long dx = sub2(xt2, X2[h]), dy = sub2(yt2, Y2[h]), dz = sub2(zt2, Z2[h]);
-                                        upk2(fma2(dz, dz, fma2(dy, dy, mul2(dx, dx))), ra, rb);
-                                    }
-                                    const uint32_t ma = __ballot_sync(full, DOT ? ra > kt : ra < kt);
+                                    const unsigned long long dx = sub2(xt2, X2[h]), dy = sub2(yt2, Y2[h]), dz = sub2(zt2, Z2[h]);
+                                    upk2(fma2(dz, dz, fma2(dy, dy, mul2(dx, dx))), ra, rb);
+                                    const uint32_t ma = __ballot_sync(full, ra < rcf2);
                                     if (lane == 0) S.mask[2 * h][col] = ma;
                                     if (2 * h + 1 < nsl) {
-                                        const uint32_t mb = __ballot_sync(full, DOT ? rb > kt : rb < kt);
+                                        const uint32_t mb = __ballot_sync(full, rb < rcf2);
                                         if (lane == 0) S.mask[2 * h + 1][col] = mb;
                                     }
                                 }
@@ -853,7 +806,6 @@ __device__ __forceinline__ void near_tile_body(const NearArgs &a, int W, int til
     } else {
         Ufall = tile_fallback<NT, F64>(a, c, tid);
     }
-    tile_release<NT, BAR>(c, S, tid);
     if constexpr (F64) warp_partial(sumUd + Ufall, a.U_part, blk, tid, NT);
     else warp_partial((double)sumU + Ufall, a.U_part, blk, tid, NT);
 }
@@ -878,7 +830,7 @@ __device__ __forceinline__ long long cell_lo(int k, int n) {
 //   (0) every staged particle's offset c from the brick centre in FP32, with -|c|^2/2;
 //   (1) pre-filter, one target cell per warp at a time: the lanes hold the cell's
 //       candidates (32 per slot, each loaded once), the cell's targets sit in registers
-//       (8 at a time, two per packed FP32x2 lane), and each test is three packed FMAs
+//       (chunks of 4, 6 or 8, two per packed FP32x2 lane), and each test is three packed FMAs
 //       against the expanded form of |t - c|^2 < thr; one ballot mask per (slot, target);
 //   (2) pairs, one thread per target: its masks in candidate order, two hits per pass,
 //       the exact separation from the fixed-point coordinates, the exact r < r_c test,
@@ -1368,10 +1320,10 @@ __global__ void __launch_bounds__(kBrickThreads, 3)
 // FP64 build: the same tiles with the 32-byte records (the staging buffer holds 1280 of
 // them, 40 KB); the pre-filter takes the high 32 bits of the coordinates, the pairs the full
 // 2^64 fixed point and FP64 arithmetic.
-using TileSmem64 = TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, false, true>;
+using TileSmem64 = TileSmem<kNearCapSingle, kTileThreads, kNearMaxWSingle, true>;
 __global__ void __launch_bounds__(kTileThreads, 4) k_near_tiled64(NearArgs a, int W, int tiles_x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, false, false, 0, true>(
+    near_tile_body<kNearCapSingle, kTileThreads, kNearMaxWSingle, true>(
         a, W, tiles_x, blockIdx.x, *reinterpret_cast<TileSmem64 *>(smem_raw), (int)threadIdx.x);
 }
 
@@ -1409,7 +1361,7 @@ __global__ void __launch_bounds__(kBrickThreads, 3) k_near_batch(const NearArgs 
 }  // namespace
 
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks, double target,
-                   int cap, int threads, int max_w, bool full_rows) {
+                   int cap, int threads, int max_w) {
     const int nx = box.nc[0], ny = box.nc[1], nz = box.nc[2];
     if (nx >= 3 && ny >= 3 && nz >= 3) {
         // tile width: about `target` (default 110) targets per CTA and about 1000 staged
@@ -1420,11 +1372,8 @@ void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x,
         int Wcap = (int)(0.78 * cap / (9.0 * (occ > 1e-9 ? occ : 1e-9))) - 2;
         if (Wt > Wcap) Wt = Wcap;
         if (Wt > max_w) Wt = max_w;
-        // A tile of the whole row (W = nx) stages cells nx-1 and 0 twice, as its two halo
-        // cells; every target cell still sees three distinct cells per row (nx >= 3).  It
-        // fills the CTAs of small boxes in a batch; one small system alone keeps tiles of at
-        // most nx - 2 cells, whose larger number of CTAs it needs.
-        if (Wt > (full_rows ? nx : nx - 2)) Wt = full_rows ? nx : nx - 2;
+        // at most nx - 2 cells, so that a tile's two halo cells are distinct from its own
+        if (Wt > nx - 2) Wt = nx - 2;
         if (Wt < 1) Wt = 1;
         *tiles_x = (nx + Wt - 1) / Wt;
         *W = (nx + *tiles_x - 1) / *tiles_x;

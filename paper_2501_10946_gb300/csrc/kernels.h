@@ -272,10 +272,10 @@ constexpr int kNearCapSingle = 1280;
 constexpr int kNearMaxWSingle = 48;
 // target: particles per CTA the tile width aims at (capped by the staging buffer `cap`);
 // threads: threads per CTA of the per-particle path (boxes under 3 cells per axis);
-// max_w: widest tile in cells; full_rows: tiles may span a whole row of cells
+// max_w: widest tile in cells (tiles span at most n_x - 2 cells)
 void near_geometry(const Box &box, uint32_t N, int *tiled, int *W, int *tiles_x, uint32_t *nblocks,
                    double target = 110.0, int cap = kNearCapSingle, int threads = 128,
-                   int max_w = kNearMaxWSingle, bool full_rows = false);
+                   int max_w = kNearMaxWSingle);
 // one brick (or per-particle block) per CTA of every system; nf: the systems' pair constants
 void launch_near_batch(const NearArgs *args, const NearF *nf, const NearBatchGeom *geom, const uint32_t *items,
                        int R, uint32_t nblocks, cudaStream_t st);
